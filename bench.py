@@ -1,0 +1,361 @@
+"""Benchmark: periodized Stokes SLP+DLP layer-potential sum at N = 128,768 on one GB300.
+
+One step = one stokes_sum_eval (density pack, tiled pair kernel over 3 images, FP64
+cross-split reduction with the wall curvature diagonal and the FP64 Kress self term) on the
+paper-scale channel: walls y = +-(1 + 0.4 sin x + 0.15 sin 3x) with 16,384 nodes each and
+750 vesicles x 128 nodes.  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MB write) before every timed step.  The metric is pair-image evaluations per
+second, 3 N_t N_s per step (Gpair-evals/s).
+
+Under torchrun each rank runs an independent replica (the sum has no exchange step on one
+node); value = pairs processed by all ranks / max-over-ranks time.
+
+``--impl reference`` times the FP64 CPU oracle (the test oracle, a plain double loop) on the
+host cores, on bounded target samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper_n128k"
+WORKLOAD_DESC = ("channel walls y=+-(1+0.4 sin x+0.15 sin 3x), 2 x 16384 nodes; 750 vesicles x 128 "
+                 "nodes (volume fraction 0.15, gap >= 5h); period 2pi, images m=-1,0,1; N=128768")
+METRIC = "Stokes SLP+DLP Gpair-evals/s at N≈128k: FP32-comp vs FP64, rel err ≤1e-6"
+# Nominal FP32 work of one pair-image evaluation (r, r^2, 1/r^2, log or (r.n), r.q, the
+# tensor-vector product and the accumulation), counting every add, multiply, reciprocal and
+# log as one flop; used for the roofline's achieved rate.
+FLOPS_PER_PAIR = 20
+SMS, LANES = 152, 128
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_pair.cu", "stokes_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1510_05616_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it still
+    describes the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "pair_f32k_paper_n128k.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not hm or hm.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_sample_oracle(geom, slp, dlp, budget_s, seed=0):
+    """Time the FP64 oracle on a random target sample sized to ~budget_s seconds."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    n = 64
+    sel = np.sort(rng.choice(geom.n_nodes, n, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    O.sum_nodes(geom, slp, dlp, select=sel, threads=threads)
+    t1 = time.perf_counter() - t0
+    n2 = int(min(geom.n_nodes, max(n, n * budget_s / max(t1, 1e-3))))
+    sel = np.sort(rng.choice(geom.n_nodes, n2, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    ref = O.sum_nodes(geom, slp, dlp, select=sel, threads=threads)
+    dt = time.perf_counter() - t0
+    pairs = (3.0 if geom.period else 1.0) * n2 * geom.n_nodes
+    return sel, ref, pairs, dt, threads
+
+
+def rel_err_by_kind(out, ref, geom, sel):
+    wall = geom.kind_mask(0)[sel]
+    res = {}
+    for name, m in (("wall", wall), ("vesicle", ~wall)):
+        if m.any():
+            scale = np.abs(ref[m]).max(0)
+            res[name] = [float(v) for v in np.abs(out[sel][m] - ref[m]).max(0) / scale]
+    return res
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1510_05616_gb300 import inputs as I
+    from oracle import oracle as O
+    O.build()
+    g, slp, dlp = I.workload(WORKLOAD)
+    budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample_oracle(g, slp, dlp, min(budget, 2.0), seed=1)
+    total_pairs, total_t, threads, samples = 0.0, 0.0, 1, []
+    for k in range(args.steps):
+        sel, _, pairs, dt, threads = cpu_sample_oracle(g, slp, dlp, budget, seed=100 + k)
+        total_pairs += pairs
+        total_t += dt
+        samples.append(len(sel))
+    val = total_pairs / total_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gpair-evals/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "N": g.n_nodes, "sample": "random target nodes per step"},
+        "cpu_baseline": {"value": val, "unit": "Gpair-evals/s", "cores": threads, "kind": "oracle",
+                         "sample": "%s target nodes x all %d sources x 3 images per step"
+                                   % (samples, g.n_nodes)},
+        "e2e": {"value": val, "unit": "Gpair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32k", choices=["fp32k", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    B.build()
+
+    g, slp, dlp = I.workload(WORKLOAD)
+    dev = torch.device("cuda", local)
+    s = P.StokesSum(g, device=local)
+    ts = torch.as_tensor(slp, device=dev)
+    td = torch.as_tensor(dlp, device=dev)
+    out = torch.empty((g.n_nodes, 2), dtype=torch.float64, device=dev)
+    prec = P.PRECISIONS[args.precision]
+    pairs = P.stokes_pair_count(s.h)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        P.stokes_sum_eval(s.h, prec, ts, td, 0.0, out)
+    P.stokes_sync(s.h)
+
+    # timed region: K steps, each preceded by an L2 flush outside its events
+    P.stokes_set_profiling(s.h, True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    pair_ms = []
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        P.stokes_sum_eval(s.h, prec, ts, td, 0.0, out)
+        ev1[k].record(stream)
+        pair_ms.append(P.stokes_last_timing(s.h)[1])
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    P.stokes_set_profiling(s.h, False)
+    P.stokes_sync(s.h)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_total = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = ws * pairs * args.steps / t_total / 1e9
+    pair_avg = statistics.mean(pair_ms)
+    gpu_out = out.cpu().numpy()
+
+    # FP64 GPU path on the same inputs (the "beats FP64" comparison)
+    fp64 = None
+    if args.precision == "fp32k" and args.fp64_steps > 0:
+        out64 = torch.empty_like(out)
+        P.stokes_sum_eval(s.h, P.STOKES_FP64, ts, td, 0.0, out64)
+        P.stokes_sync(s.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t64 = 0.0
+        for _ in range(args.fp64_steps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            P.stokes_sum_eval(s.h, P.STOKES_FP64, ts, td, 0.0, out64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 += e0.elapsed_time(e1) / 1e3
+        P.stokes_sync(s.h)
+        fp64 = {"value": pairs * args.fp64_steps / t64 / 1e9, "unit": "Gpair-evals/s",
+                "ms_per_step": 1e3 * t64 / args.fp64_steps}
+        d = np.abs(gpu_out - out64.cpu().numpy()).max(0) / np.abs(out64.cpu().numpy()).max(0)
+        fp64["fp32k_rel_diff_vs_fp64"] = [float(v) for v in d]
+
+    # end to end through the host-buffer C entry point (pinned host memory)
+    hs = torch.as_tensor(slp).pin_memory()
+    hd = torch.as_tensor(dlp).pin_memory()
+    ho = torch.empty((g.n_nodes, 2), dtype=torch.float64).pin_memory()
+    P.stokes_sum_eval_host(s.h, prec, hs, hd, 0.0, ho)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.stokes_sum_eval_host(s.h, prec, hs, hd, 0.0, ho)
+    te = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([te], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": ws * pairs * args.steps / te / 1e9, "unit": "Gpair-evals/s",
+           "h2d_bytes_per_step": int(hs.numel() * 8 + hd.numel() * 8),
+           "d2h_bytes_per_step": int(ho.numel() * 8)}
+
+    if rank != 0:
+        s.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * LANES * 2 * sm_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * pairs / (pair_avg / 1e3) / 1e12
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpair-evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32k" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "N": g.n_nodes, "pairs_per_step": pairs,
+                   "precision": args.precision, "l2": "flushed before each timed step (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "pair_f32k_kernel" if args.precision == "fp32k" else "pair_f64_kernel",
+                     "kernel_ms": pair_avg,
+                     "peak_basis": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peak_kind,
+                     "flops_per_pair": FLOPS_PER_PAIR},
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "fp64_path": fp64,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        sel, ref, cpairs, dt, threads = cpu_sample_oracle(g, slp, dlp, args.cpu_budget)
+        line["cpu_baseline"] = {"value": cpairs / dt / 1e9, "unit": "Gpair-evals/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": "%d random target nodes x all %d sources x 3 images"
+                                          % (len(sel), g.n_nodes)}
+        line["rel_err_vs_oracle"] = rel_err_by_kind(gpu_out, ref, g, sel)
+    print(json.dumps(line))
+    s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,275 @@
+"""GB300-native periodized 2-D Stokes layer-potential sum (Marple, Barnett, Gillman,
+Veerapaneni): Python binding of the C ABI in ``include/stokes.h``.
+
+The functions below carry the C names and only marshal arguments (torch tensors -> device
+pointers, current CUDA stream -> cudaStream_t); every step of the sum runs in libstokes'
+CUDA kernels.  There is no CPU fallback: without the built library or a CUDA device the
+calls raise :class:`StokesError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstokes.so")
+
+STOKES_OK = 0
+STOKES_ERR_ARG = -1
+STOKES_ERR_CUDA = -2
+STOKES_ERR_NO_GEOM = -3
+STOKES_ERR_ODD_N = -4
+STOKES_ERR_NONFINITE = -5
+STOKES_ERR_TIMEOUT = -6
+STOKES_ERR_NOT_CONVERGED = -7
+STOKES_ERR_OOM = -8
+
+STOKES_FP64 = 0
+STOKES_FP32_KAHAN = 1
+STOKES_KIND_WALL = 0
+STOKES_KIND_VESICLE = 1
+
+PRECISIONS = {"fp64": STOKES_FP64, "fp32k": STOKES_FP32_KAHAN}
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libstokes status %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_SIGNATURES = {
+    "stokes_create": [_c_int, ctypes.POINTER(_vp)],
+    "stokes_destroy": [_vp],
+    "stokes_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "stokes_geom_set": [_vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _c_double, _c_double, _vp],
+    "stokes_sum_eval": [_vp, _c_int, _vp, _vp, _c_double, _vp, _vp],
+    "stokes_sum_eval_targets": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
+    "stokes_sum_eval_host": [_vp, _c_int, _vp, _vp, _c_double, _vp],
+    "stokes_sync": [_vp, _vp],
+    "stokes_num_nodes": [_vp],
+    "stokes_set_launch": [_vp, _c_int, _c_int],
+    "stokes_pair_count": [_vp, _c_int, ctypes.POINTER(_c_double)],
+    "stokes_set_profiling": [_vp, _c_int],
+    "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
+}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree libstokes.so (built by ``build.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise StokesError(STOKES_ERR_CUDA, "libstokes.so is not built (%s)" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, argt in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = argt
+            fn.restype = _c_int
+        _lib = lib
+    return _lib
+
+
+def _err(h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    if h:
+        load().stokes_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(h, code: int):
+    if code != STOKES_OK:
+        raise StokesError(code, _err(h))
+    return code
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t, name, shape_tail=None, allow_none=False):
+    import torch
+    if t is None:
+        if allow_none:
+            return None
+        raise StokesError(STOKES_ERR_ARG, "%s is None" % name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise StokesError(STOKES_ERR_ARG, "%s must be a CUDA float64 tensor" % name)
+    if not t.is_contiguous():
+        raise StokesError(STOKES_ERR_ARG, "%s must be contiguous" % name)
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise StokesError(STOKES_ERR_ARG, "%s has shape %s" % (name, tuple(t.shape)))
+    return _vp(t.data_ptr()) if t.numel() else None
+
+
+# ---------------------------------------------------------------------------
+# C-named functions (argument marshalling only)
+# ---------------------------------------------------------------------------
+def stokes_create(device: int = 0):
+    h = _vp()
+    code = load().stokes_create(int(device), ctypes.byref(h))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_create(device=%d) failed" % device)
+    return h
+
+
+def stokes_destroy(h):
+    return _check(h, load().stokes_destroy(h))
+
+
+def stokes_geom_set(h, curve_offset, curve_kind, nodes, weights, normals, curvature, period,
+                    mu, stream=None):
+    import numpy as np
+    off = np.ascontiguousarray(curve_offset, dtype=np.int32)
+    kind = np.ascontiguousarray(curve_kind, dtype=np.int32)
+    code = load().stokes_geom_set(
+        h, int(kind.shape[0]), _vp(off.ctypes.data), _vp(kind.ctypes.data),
+        _dptr(nodes, "nodes", (2,)), _dptr(weights, "weights"), _dptr(normals, "normals", (2,)),
+        _dptr(curvature, "curvature", allow_none=True), float(period), float(mu), _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sum_eval(h, precision, slp_density, dlp_density, jump, out_velocity, stream=None):
+    code = load().stokes_sum_eval(h, int(precision),
+                                  _dptr(slp_density, "slp_density", (2,), True),
+                                  _dptr(dlp_density, "dlp_density", (2,), True), float(jump),
+                                  _dptr(out_velocity, "out_velocity", (2,)), _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sum_eval_targets(h, precision, slp_density, dlp_density, targets, out_velocity,
+                            stream=None):
+    n = int(targets.shape[0])
+    code = load().stokes_sum_eval_targets(h, int(precision),
+                                          _dptr(slp_density, "slp_density", (2,), True),
+                                          _dptr(dlp_density, "dlp_density", (2,), True), n,
+                                          _dptr(targets, "targets", (2,), True),
+                                          _dptr(out_velocity, "out_velocity", (2,), True),
+                                          _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sum_eval_host(h, precision, slp_density_host, dlp_density_host, jump, out_host):
+    """Host-buffer evaluation: NumPy (or pinned torch CPU) float64 arrays."""
+    import numpy as np
+
+    def hp(a, name):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if a.dtype.__str__() != "torch.float64" or not a.is_contiguous() or a.is_cuda:
+                raise StokesError(STOKES_ERR_ARG, "%s must be a contiguous CPU float64 tensor" % name)
+            return _vp(a.data_ptr()) if a.numel() else None
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise StokesError(STOKES_ERR_ARG, "%s must be a C-contiguous float64 array" % name)
+        return _vp(a.ctypes.data) if a.size else None
+
+    code = load().stokes_sum_eval_host(h, int(precision), hp(slp_density_host, "slp"),
+                                       hp(dlp_density_host, "dlp"), float(jump),
+                                       hp(out_host, "out"))
+    return _check(h, code)
+
+
+def stokes_last_error(h) -> str:
+    return _err(h)
+
+
+def stokes_sync(h, stream=None):
+    return _check(h, load().stokes_sync(h, _stream(stream)))
+
+
+def stokes_num_nodes(h) -> int:
+    return int(load().stokes_num_nodes(h))
+
+
+def stokes_set_launch(h, precision, source_splits):
+    return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits)))
+
+
+def stokes_set_profiling(h, on: bool = True):
+    return _check(h, load().stokes_set_profiling(h, int(bool(on))))
+
+
+def stokes_last_timing(h):
+    """(pack_ms, pair_ms, finish_ms) of the last profiled call."""
+    ms = (_c_double * 3)()
+    _check(h, load().stokes_last_timing(h, ms))
+    return tuple(float(v) for v in ms)
+
+
+def stokes_pair_count(h, n_targets: int = 0) -> float:
+    v = _c_double()
+    _check(h, load().stokes_pair_count(h, int(n_targets), ctypes.byref(v)))
+    return float(v.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class StokesSum:
+    """One libstokes context with a geometry resident on the GPU.
+
+    ``geom`` is any object with ``curve_offset``, ``curve_kind``, ``nodes``, ``weights``,
+    ``normals``, ``curvature`` (NumPy), ``period`` and ``mu`` (e.g. ``inputs.Geometry``).
+    """
+
+    def __init__(self, geom=None, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise StokesError(STOKES_ERR_CUDA, "no CUDA device: libstokes runs on the GPU only")
+        self.device = torch.device("cuda", device)
+        self.h = stokes_create(device)
+        self.N = 0
+        if geom is not None:
+            self.set_geometry(geom)
+
+    def set_geometry(self, geom):
+        import torch
+        dev = self.device
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
+        self._geom_tensors = (t(geom.nodes), t(geom.weights), t(geom.normals), t(geom.curvature))
+        x, w, n, k = self._geom_tensors
+        stokes_geom_set(self.h, geom.curve_offset, geom.curve_kind, x, w, n, k, geom.period,
+                        geom.mu)
+        self.N = stokes_num_nodes(self.h)
+
+    def eval(self, slp, dlp, precision="fp32k", jump=0.0, out=None, sync=True):
+        import torch
+        prec = PRECISIONS.get(precision, precision)
+        if out is None:
+            out = torch.empty((self.N, 2), dtype=torch.float64, device=self.device)
+        stokes_sum_eval(self.h, prec, slp, dlp, jump, out)
+        if sync:
+            stokes_sync(self.h)
+        return out
+
+    def eval_targets(self, slp, dlp, targets, precision="fp32k", out=None, sync=True):
+        import torch
+        prec = PRECISIONS.get(precision, precision)
+        if out is None:
+            out = torch.empty((int(targets.shape[0]), 2), dtype=torch.float64, device=self.device)
+        stokes_sum_eval_targets(self.h, prec, slp, dlp, targets, out)
+        if sync:
+            stokes_sync(self.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            stokes_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

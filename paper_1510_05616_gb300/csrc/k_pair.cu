@@ -1,0 +1,499 @@
+// k_pair.cu -- tiled N-body pair kernels of the near-image layer-potential sum.
+//
+// One block owns a block of targets and one split (contiguous range of source tiles).
+// Source tiles are staged into shared memory by 1-D bulk async copies (cp.async.bulk,
+// completion on an mbarrier) through a ring of kStages stages; every thread then reads
+// each source record with two broadcast 16-byte shared loads and evaluates it against
+// its targets for all images m in {-1, 0, +1} at once (the near-image sums of
+// Eq. (Dnr) and Eq. (utotrep)).  Tiles hold one source kind only, so the stokeslet
+// (Eq. (S)) / stresslet (Eq. (D)) branch is uniform over the block.
+//
+// FP32 path (STOKES_FP32_KAHAN):
+//   * coordinates as (hi, lo) float pairs, targets pre-shifted by -m d in FP64 before the
+//     split, so r = (x_hi - y_hi) + (x_lo - y_lo) is accurate to a few ulp of |r| even for
+//     adjacent wall nodes (where r . n ~ kappa r^2 / 2 would otherwise be noise);
+//   * 1/r^2 and log2(r^2) from the MUFU approximations (rcp.approx, lg2.approx);
+//   * the three image terms of one source are added in FP32, and that per-source sum
+//     enters a per-thread Kahan-compensated accumulator;
+//   * each (split, target) partial leaves the kernel as FP64 and is reduced across splits
+//     in FP64, in fixed order, by the finishing kernel.
+// FP64 path (STOKES_FP64): the same tiling in double precision, plain accumulation.
+//
+// Skips of the definition: a vesicle target skips the m = 0 image of its own curve's
+// nodes (those are replaced by the Kress self rule); a wall target's own node at m = 0
+// gives r = 0 exactly and contributes 0 (r2 carries a tiny floor so 1/r^2 stays finite
+// while r . n = r . q = 0).
+#include "stokes_internal.cuh"
+
+namespace stokes {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier, bulk async copy, MUFU approximations
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after ~0.5 s (returns false).
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > 500000000ull) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Floor on r^2: keeps 1/r^2 and (1/r^2)^2 finite for the coincident wall self pair.
+constexpr float kTiny32 = 1e-19f;
+constexpr double kTiny64 = 1e-150;
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pair evaluation
+// ---------------------------------------------------------------------------
+template <int NIMG>
+struct TgtF32 {
+  float xh[NIMG], xl[NIMG];  // x - m d, split hi/lo
+  float yh, yl;
+  int2 skip;                 // own-curve source slots skipped at m = 0
+};
+
+template <int NIMG>
+__device__ __forceinline__ void load_target_f32(const PairArgs &a, int i, TgtF32<NIMG> &t) {
+  const double2 p = a.tgt[i];
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const double m = (NIMG == 3) ? double(k - 1) : 0.0;
+    const double xm = p.x - m * a.period;
+    const float h = __double2float_rn(xm);
+    t.xh[k] = h;
+    t.xl[k] = __double2float_rn(xm - double(h));
+  }
+  const float h = __double2float_rn(p.y);
+  t.yh = h;
+  t.yl = __double2float_rn(p.y - double(h));
+  t.skip = a.tgt_skip ? a.tgt_skip[i] : make_int2(-1, -1);
+}
+
+// Stokeslet source (Eq. (S)); val = (q1, q2, p1, p2), q = w f / (4 pi mu), p = -(ln 2 / 2) q.
+// Term per image: log2(r^2) p + r (r . q) / r^2.
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_source_f32(const TgtF32<NIMG> &t, const float4 pos,
+                                               const float4 val, bool skip0, float &tx,
+                                               float &ty) {
+  const float dy = (t.yh - pos.y) + (t.yl - pos.w);
+  const float dyq = dy * val.y;
+  const float dy2 = fmaf(dy, dy, kTiny32);
+  float ax = -0.0f, ay = -0.0f;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    if (MASK0 && k == NIMG / 2 && skip0) continue;
+    const float dx = (t.xh[k] - pos.x) + (t.xl[k] - pos.z);
+    const float r2 = fmaf(dx, dx, dy2);
+    const float inv = rcp_approx(r2);
+    const float lg = lg2_approx(r2);
+    const float s = fmaf(dx, val.x, dyq) * inv;
+    ax = fmaf(lg, val.z, ax);
+    ax = fmaf(s, dx, ax);
+    ay = fmaf(lg, val.w, ay);
+    ay = fmaf(s, dy, ay);
+  }
+  tx = ax;
+  ty = ay;
+}
+
+// Stresslet source (Eq. (D)); val = (q1, q2, n1, n2), q = w tau / pi.
+// Term per image: r (r . n)(r . q) / r^4.
+template <int NIMG>
+__device__ __forceinline__ void dlp_source_f32(const TgtF32<NIMG> &t, const float4 pos,
+                                               const float4 val, float &tx, float &ty) {
+  const float dy = (t.yh - pos.y) + (t.yl - pos.w);
+  const float dyn = dy * val.w;
+  const float dyq = dy * val.y;
+  const float dy2 = fmaf(dy, dy, kTiny32);
+  float ax = -0.0f, ay = -0.0f;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const float dx = (t.xh[k] - pos.x) + (t.xl[k] - pos.z);
+    const float r2 = fmaf(dx, dx, dy2);
+    const float inv = rcp_approx(r2);
+    const float rn = fmaf(dx, val.z, dyn);
+    const float rq = fmaf(dx, val.x, dyq);
+    const float f = (rn * rq) * (inv * inv);
+    ax = fmaf(f, dx, ax);
+    ay = fmaf(f, dy, ay);
+  }
+  tx = ax;
+  ty = ay;
+}
+
+template <int NIMG, int TPT>
+__global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
+  __shared__ __align__(128) float4 s_pos[kStages][kTileF32];
+  __shared__ __align__(128) float4 s_val[kStages][kTileF32];
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+
+  const int split = blockIdx.y;
+  const int tile0 = split * a.tiles_per_split;
+  const int ntl = min(a.n_tiles, tile0 + a.tiles_per_split) - tile0;
+
+  TgtF32<NIMG> tg[TPT];
+  float sx[TPT], cx[TPT], sy[TPT], cy[TPT];
+  const int base = blockIdx.x * (kThreadsF32 * TPT) + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int i = min(base + q * kThreadsF32, a.n_targets - 1);
+    load_target_f32<NIMG>(a, i, tg[q]);
+    sx[q] = cx[q] = sy[q] = cy[q] = 0.0f;
+  }
+
+  const float4 *gpos = static_cast<const float4 *>(a.src_pos);
+  const float4 *gval = static_cast<const float4 *>(a.src_val);
+  constexpr uint32_t kBytes = kTileF32 * sizeof(float4);
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages && s < ntl; ++s) {
+      mbar_arrive_expect_tx(&s_bar[s], 2 * kBytes);
+      bulk_g2s(s_pos[s], gpos + size_t(tile0 + s) * kTileF32, kBytes, &s_bar[s]);
+      bulk_g2s(s_val[s], gval + size_t(tile0 + s) * kTileF32, kBytes, &s_bar[s]);
+    }
+  }
+
+  for (int it = 0; it < ntl; ++it) {
+    const int st = it % kStages;
+    const uint32_t par = (it / kStages) & 1u;
+    const bool ok = mbar_wait_bounded(&s_bar[st], par);
+    if (ok) {
+      const int tile = tile0 + it;
+      const float4 *P = s_pos[st];
+      const float4 *V = s_val[st];
+      if (tile < a.n_wall_tiles) {
+#pragma unroll 2
+        for (int j = 0; j < kTileF32; ++j) {
+          const float4 p = P[j], v = V[j];
+#pragma unroll
+          for (int q = 0; q < TPT; ++q) {
+            float tx, ty;
+            dlp_source_f32<NIMG>(tg[q], p, v, tx, ty);
+            kahan_add(sx[q], cx[q], tx);
+            kahan_add(sy[q], cy[q], ty);
+          }
+        }
+      } else {
+        const int slot0 = tile * kTileF32;
+        bool mine = false;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q)
+          mine |= (tg[q].skip.x < slot0 + kTileF32) && (tg[q].skip.y > slot0);
+        if (__any_sync(0xffffffffu, mine)) {
+          for (int j = 0; j < kTileF32; ++j) {
+            const float4 p = P[j], v = V[j];
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+              const bool s0 = (slot0 + j >= tg[q].skip.x) && (slot0 + j < tg[q].skip.y);
+              float tx, ty;
+              slp_source_f32<NIMG, true>(tg[q], p, v, s0, tx, ty);
+              kahan_add(sx[q], cx[q], tx);
+              kahan_add(sy[q], cy[q], ty);
+            }
+          }
+        } else {
+#pragma unroll 2
+          for (int j = 0; j < kTileF32; ++j) {
+            const float4 p = P[j], v = V[j];
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+              float tx, ty;
+              slp_source_f32<NIMG, false>(tg[q], p, v, false, tx, ty);
+              kahan_add(sx[q], cx[q], tx);
+              kahan_add(sy[q], cy[q], ty);
+            }
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      // A stage never arrived: record it, let the copies still in flight land, and leave.
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        for (int r = it; r < ntl && r < it + kStages; ++r)
+          mbar_wait_bounded(&s_bar[r % kStages], (r / kStages) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0 && it + kStages < ntl) {
+      const int nt = tile0 + it + kStages;
+      mbar_arrive_expect_tx(&s_bar[st], 2 * kBytes);
+      bulk_g2s(s_pos[st], gpos + size_t(nt) * kTileF32, kBytes, &s_bar[st]);
+      bulk_g2s(s_val[st], gval + size_t(nt) * kTileF32, kBytes, &s_bar[st]);
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int i = base + q * kThreadsF32;
+    if (i < a.n_targets)
+      a.partial[size_t(split) * a.n_targets + i] =
+          make_double2(double(sx[q]) - double(cx[q]), double(sy[q]) - double(cy[q]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pair evaluation
+// ---------------------------------------------------------------------------
+template <int NIMG>
+struct TgtF64 {
+  double x[NIMG];
+  double y;
+  int2 skip;
+};
+
+// Stokeslet; val = (q1, q2, p1, p2) with q = w f / (4 pi mu), p = -q / 2.
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_source_f64(const TgtF64<NIMG> &t, const double2 pos,
+                                               const double4_32a val, bool skip0, double &ax,
+                                               double &ay) {
+  const double dy = t.y - pos.y;
+  const double dyq = dy * val.y;
+  const double dy2 = fma(dy, dy, kTiny64);
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    if (MASK0 && k == NIMG / 2 && skip0) continue;
+    const double dx = t.x[k] - pos.x;
+    const double r2 = fma(dx, dx, dy2);
+    const double inv = __drcp_rn(r2);
+    const double lg = log(r2);
+    const double s = fma(dx, val.x, dyq) * inv;
+    ax = fma(lg, val.z, ax);
+    ax = fma(s, dx, ax);
+    ay = fma(lg, val.w, ay);
+    ay = fma(s, dy, ay);
+  }
+}
+
+// Stresslet; val = (q1, q2, n1, n2) with q = w tau / pi.
+template <int NIMG>
+__device__ __forceinline__ void dlp_source_f64(const TgtF64<NIMG> &t, const double2 pos,
+                                               const double4_32a val, double &ax, double &ay) {
+  const double dy = t.y - pos.y;
+  const double dyn = dy * val.w;
+  const double dyq = dy * val.y;
+  const double dy2 = fma(dy, dy, kTiny64);
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const double dx = t.x[k] - pos.x;
+    const double r2 = fma(dx, dx, dy2);
+    const double inv = __drcp_rn(r2);
+    const double rn = fma(dx, val.z, dyn);
+    const double rq = fma(dx, val.x, dyq);
+    const double f = (rn * rq) * (inv * inv);
+    ax = fma(f, dx, ax);
+    ay = fma(f, dy, ay);
+  }
+}
+
+template <int NIMG>
+__global__ void __launch_bounds__(kThreadsF64) pair_f64_kernel(PairArgs a) {
+  __shared__ __align__(128) double2 s_pos[kStages][kTileF64];
+  __shared__ __align__(128) double4_32a s_val[kStages][kTileF64];
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+
+  const int split = blockIdx.y;
+  const int tile0 = split * a.tiles_per_split;
+  const int ntl = min(a.n_tiles, tile0 + a.tiles_per_split) - tile0;
+
+  const int i_out = blockIdx.x * kThreadsF64 + threadIdx.x;
+  const int i = min(i_out, a.n_targets - 1);
+  TgtF64<NIMG> t;
+  {
+    const double2 p = a.tgt[i];
+#pragma unroll
+    for (int k = 0; k < NIMG; ++k) t.x[k] = p.x - ((NIMG == 3) ? double(k - 1) : 0.0) * a.period;
+    t.y = p.y;
+    t.skip = a.tgt_skip ? a.tgt_skip[i] : make_int2(-1, -1);
+  }
+  double ux = 0.0, uy = 0.0;
+
+  const double2 *gpos = static_cast<const double2 *>(a.src_pos);
+  const double4_32a *gval = static_cast<const double4_32a *>(a.src_val);
+  constexpr uint32_t kBp = kTileF64 * sizeof(double2);
+  constexpr uint32_t kBv = kTileF64 * sizeof(double4_32a);
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages && s < ntl; ++s) {
+      mbar_arrive_expect_tx(&s_bar[s], kBp + kBv);
+      bulk_g2s(s_pos[s], gpos + size_t(tile0 + s) * kTileF64, kBp, &s_bar[s]);
+      bulk_g2s(s_val[s], gval + size_t(tile0 + s) * kTileF64, kBv, &s_bar[s]);
+    }
+  }
+
+  for (int it = 0; it < ntl; ++it) {
+    const int st = it % kStages;
+    const uint32_t par = (it / kStages) & 1u;
+    const bool ok = mbar_wait_bounded(&s_bar[st], par);
+    if (ok) {
+      const int tile = tile0 + it;
+      if (tile < a.n_wall_tiles) {
+        for (int j = 0; j < kTileF64; ++j) dlp_source_f64<NIMG>(t, s_pos[st][j], s_val[st][j], ux, uy);
+      } else {
+        const int slot0 = tile * kTileF64;
+        const bool mine = (t.skip.x < slot0 + kTileF64) && (t.skip.y > slot0);
+        if (__any_sync(0xffffffffu, mine)) {
+          for (int j = 0; j < kTileF64; ++j) {
+            const bool s0 = (slot0 + j >= t.skip.x) && (slot0 + j < t.skip.y);
+            slp_source_f64<NIMG, true>(t, s_pos[st][j], s_val[st][j], s0, ux, uy);
+          }
+        } else {
+          for (int j = 0; j < kTileF64; ++j)
+            slp_source_f64<NIMG, false>(t, s_pos[st][j], s_val[st][j], false, ux, uy);
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        for (int r = it; r < ntl && r < it + kStages; ++r)
+          mbar_wait_bounded(&s_bar[r % kStages], (r / kStages) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0 && it + kStages < ntl) {
+      const int nt = tile0 + it + kStages;
+      mbar_arrive_expect_tx(&s_bar[st], kBp + kBv);
+      bulk_g2s(s_pos[st], gpos + size_t(nt) * kTileF64, kBp, &s_bar[st]);
+      bulk_g2s(s_val[st], gval + size_t(nt) * kTileF64, kBv, &s_bar[st]);
+    }
+  }
+  if (i_out < a.n_targets) a.partial[size_t(split) * a.n_targets + i_out] = make_double2(ux, uy);
+}
+
+// ---------------------------------------------------------------------------
+// launcher
+// ---------------------------------------------------------------------------
+cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
+                        const int2 *skip, int splits, cudaStream_t s) {
+  PairArgs a{};
+  a.n_targets = n_targets;
+  a.tgt = tgt;
+  a.tgt_skip = skip;
+  a.period = c->period;
+  a.partial = c->d_partial;
+  a.status = c->d_status;
+  const bool img = c->period != 0.0;
+  if (precision == STOKES_FP32_KAHAN) {
+    a.n_wall_tiles = c->wall_slots / kTileF32;
+    a.n_tiles = a.n_wall_tiles + c->ves_slots_f32 / kTileF32;
+    a.src_pos = c->d_src_pos32;
+    a.src_val = c->d_src_val32;
+    a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
+    const int eff = (a.n_tiles + a.tiles_per_split - 1) / a.tiles_per_split;
+    if (eff != splits) return cudaErrorInvalidValue;  // callers pass effective_splits() values
+    dim3 grid((n_targets + kThreadsF32 * kTptF32 - 1) / (kThreadsF32 * kTptF32), eff);
+    if (img)
+      pair_f32k_kernel<3, kTptF32><<<grid, kThreadsF32, 0, s>>>(a);
+    else
+      pair_f32k_kernel<1, kTptF32><<<grid, kThreadsF32, 0, s>>>(a);
+  } else {
+    a.n_wall_tiles = c->wall_slots_f64 / kTileF64;
+    a.n_tiles = a.n_wall_tiles + c->ves_slots_f64 / kTileF64;
+    a.src_pos = c->d_src_pos64;
+    a.src_val = c->d_src_val64;
+    a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
+    const int eff = (a.n_tiles + a.tiles_per_split - 1) / a.tiles_per_split;
+    if (eff != splits) return cudaErrorInvalidValue;
+    dim3 grid((n_targets + kThreadsF64 - 1) / kThreadsF64, eff);
+    if (img)
+      pair_f64_kernel<3><<<grid, kThreadsF64, 0, s>>>(a);
+    else
+      pair_f64_kernel<1><<<grid, kThreadsF64, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Effective number of splits actually launched for a requested count.
+int effective_splits(stokes_ctx *c, int precision, int splits) {
+  int n_tiles = (precision == STOKES_FP32_KAHAN)
+                    ? (c->wall_slots + c->ves_slots_f32) / kTileF32
+                    : (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
+  if (splits < 1) splits = 1;
+  if (splits > n_tiles) splits = n_tiles;
+  const int tps = (n_tiles + splits - 1) / splits;
+  return (n_tiles + tps - 1) / tps;
+}
+
+}  // namespace stokes

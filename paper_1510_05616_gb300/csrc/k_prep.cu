@@ -1,0 +1,299 @@
+// k_prep.cu -- geometry preparation, per-call density packing and the FP64 finishing pass.
+//
+//  * geometry prep (once per stokes_geom_set): FP32 (hi, lo) source coordinates, FP64
+//    source coordinates, Kress product-rule tables, a finiteness check of the geometry;
+//  * pack (every call): source density records q = w f / (4 pi mu) (stokeslet, Eq. (S))
+//    and q = w tau / pi (stresslet, Eq. (D)), with a finiteness check of the densities;
+//  * finish (every call): the FP64 cross-split reduction of the pair-kernel partials in
+//    fixed order, plus the wall Nystrom diagonal -kappa/(2 pi) t t^T w tau and jump * tau
+//    (Sec. 2.3, Eq. (JR)), plus the FP64 Kress self term of the single layer on each
+//    vesicle (Sec. 3.2).
+#include "stokes_internal.cuh"
+
+namespace stokes {
+
+// ---------------------------------------------------------------------------
+// geometry preparation
+// ---------------------------------------------------------------------------
+__global__ void src_pos32_kernel(int slots, const int *slot_node, const double2 *x, float4 *pos) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= slots) return;
+  const int i = slot_node[s];
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i >= 0) {
+    const double2 p = x[i];
+    const float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
+    r = make_float4(xh, yh, __double2float_rn(p.x - double(xh)), __double2float_rn(p.y - double(yh)));
+  }
+  pos[s] = r;
+}
+
+__global__ void src_pos64_kernel(int slots, const int *slot_node, const double2 *x, double2 *pos) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= slots) return;
+  const int i = slot_node[s];
+  pos[s] = (i >= 0) ? x[i] : make_double2(0.0, 0.0);
+}
+
+// Kress table of a closed curve with n nodes (n even):
+//   T_0 = -R_0 / 2,  T_j = -R_j / 2 + (pi / n) log(4 sin^2(pi j / n))  (j >= 1),
+//   R_j = -(4 pi / n) sum_{p=1}^{n/2-1} cos(2 pi p j / n) / p - (4 pi / n^2) (-1)^j.
+// The self term then reads  sum_k [T_{(i-k) mod n} - (pi/n) log |x_i - x_k|^2] g_k + ...
+__global__ void kress_table_kernel(int n, double *T) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int p = 1; p <= n / 2 - 1; ++p) {
+    const long long k = (static_cast<long long>(p) * j) % n;  // cos(2 pi p j / n) exactly reduced
+    acc += cospi(2.0 * double(k) / double(n)) / double(p);
+  }
+  const double R = -(4.0 * kPi / n) * acc - (4.0 * kPi / (double(n) * n)) * ((j & 1) ? -1.0 : 1.0);
+  double t = -0.5 * R;
+  if (j > 0) {
+    const double sn = sinpi(double(j) / double(n));
+    t += (kPi / n) * log(4.0 * sn * sn);
+  }
+  T[j] = t;
+}
+
+__global__ void geom_check_kernel(int n, const double2 *x, const double2 *nrm, const double *w,
+                                  const double *kap, unsigned *status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool ok = isfinite(x[i].x) && isfinite(x[i].y) && isfinite(nrm[i].x) && isfinite(nrm[i].y) &&
+            isfinite(w[i]);
+  if (kap) ok = ok && isfinite(kap[i]);
+  if (!ok) atomicOr(status, kStatusNonfinite);
+}
+
+// ---------------------------------------------------------------------------
+// per-call density packing
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  int slots, wall_slots;
+  const int *slot_node;
+  const int *node_dens;
+  const double *w;
+  const double2 *nrm;
+  const double *slp, *dlp;
+  double c_slp;  // 1 / (4 pi mu)
+  unsigned *status;
+};
+
+__global__ void pack_f32_kernel(PackArgs a, float4 *val) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.slots) return;
+  const int i = a.slot_node[s];
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i >= 0) {
+    const int row = a.node_dens[i];
+    const double w = a.w[i];
+    if (s < a.wall_slots) {
+      const double t1 = a.dlp[2 * row], t2 = a.dlp[2 * row + 1];
+      if (!isfinite(t1) || !isfinite(t2)) atomicOr(a.status, kStatusNonfinite);
+      const double2 n = a.nrm[i];
+      const double c = w / kPi;
+      r = make_float4(__double2float_rn(c * t1), __double2float_rn(c * t2), __double2float_rn(n.x),
+                      __double2float_rn(n.y));
+    } else {
+      const double f1 = a.slp[2 * row], f2 = a.slp[2 * row + 1];
+      if (!isfinite(f1) || !isfinite(f2)) atomicOr(a.status, kStatusNonfinite);
+      const double c = w * a.c_slp;
+      const double h = -0.5 * 0.69314718055994530942;  // -(ln 2)/2: log(1/r) = h log2(r^2)
+      r = make_float4(__double2float_rn(c * f1), __double2float_rn(c * f2),
+                      __double2float_rn(h * c * f1), __double2float_rn(h * c * f2));
+    }
+  }
+  val[s] = r;
+}
+
+__global__ void pack_f64_kernel(PackArgs a, double4_32a *val) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.slots) return;
+  const int i = a.slot_node[s];
+  double4_32a r = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+  if (i >= 0) {
+    const int row = a.node_dens[i];
+    const double w = a.w[i];
+    if (s < a.wall_slots) {
+      const double t1 = a.dlp[2 * row], t2 = a.dlp[2 * row + 1];
+      if (!isfinite(t1) || !isfinite(t2)) atomicOr(a.status, kStatusNonfinite);
+      const double2 n = a.nrm[i];
+      const double c = w / kPi;
+      r = make_double4_32a(c * t1, c * t2, n.x, n.y);
+    } else {
+      const double f1 = a.slp[2 * row], f2 = a.slp[2 * row + 1];
+      if (!isfinite(f1) || !isfinite(f2)) atomicOr(a.status, kStatusNonfinite);
+      const double c = w * a.c_slp;
+      r = make_double4_32a(c * f1, c * f2, -0.5 * c * f1, -0.5 * c * f2);  // log(1/r) = -log(r^2)/2
+    }
+  }
+  val[s] = r;
+}
+
+// ---------------------------------------------------------------------------
+// finishing pass
+// ---------------------------------------------------------------------------
+__global__ void finish_walls_kernel(int n_wall, const int *wall_nodes, int N, int splits,
+                                    const double2 *partial, const int *node_dens,
+                                    const double2 *nrm, const double *w, const double *kap,
+                                    const double *dlp, double jump, double2 *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_wall) return;
+  const int i = wall_nodes[t];
+  double ux = 0.0, uy = 0.0;
+  for (int k = 0; k < splits; ++k) {
+    const double2 p = partial[size_t(k) * N + i];
+    ux += p.x;
+    uy += p.y;
+  }
+  const int row = node_dens[i];
+  const double t1 = dlp[2 * row], t2 = dlp[2 * row + 1];
+  const double2 n = nrm[i];
+  const double tx = -n.y, ty = n.x;  // unit tangent
+  const double c = -kap[i] / (2.0 * kPi) * w[i] * (tx * t1 + ty * t2);
+  out[i] = make_double2(ux + c * tx + jump * t1, uy + c * ty + jump * t2);
+}
+
+// One block per vesicle: FP64 reduction of its nodes' partials plus the Kress self term.
+__global__ void finish_vesicles_kernel(const int *ves_curves, const CurveDev *curves,
+                                       const double *kress, int N, int splits,
+                                       const double2 *partial, const double2 *x,
+                                       const double2 *nrm, const double *w, const double *slp,
+                                       double c_slp, double2 *out) {
+  extern __shared__ double sh[];
+  const CurveDev cv = curves[ves_curves[blockIdx.x]];
+  const int n = cv.n;
+  double *sx = sh, *sy = sh + n, *g1 = sh + 2 * n, *g2 = sh + 3 * n;
+  const double h = 2.0 * kPi / n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int j = cv.node_begin + k;
+    const double2 p = x[j];
+    sx[k] = p.x;
+    sy[k] = p.y;
+    const double s = w[j] / h;  // speed |x'(t_k)|
+    const int row = cv.dens_begin + k;
+    g1[k] = c_slp * s * slp[2 * row];
+    g2[k] = c_slp * s * slp[2 * row + 1];
+  }
+  __syncthreads();
+  const double *T = kress + cv.kress_off;
+  const double pin = kPi / n;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    const int i = cv.node_begin + a;
+    double ux = 0.0, uy = 0.0;
+    for (int k = 0; k < splits; ++k) {
+      const double2 p = partial[size_t(k) * N + i];
+      ux += p.x;
+      uy += p.y;
+    }
+    const double xa = sx[a], ya = sy[a];
+    double vx = 0.0, vy = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double gx = g1[k], gy = g2[k];
+      double coef, m11, m12, m22;
+      if (k == a) {
+        const double s = w[i] / h;
+        const double2 nn = nrm[i];
+        const double tx = -nn.y, ty = nn.x;
+        coef = T[0] - pin * log(s * s);
+        m11 = tx * tx;
+        m12 = tx * ty;
+        m22 = ty * ty;
+      } else {
+        const double rx = xa - sx[k], ry = ya - sy[k];
+        const double rr = rx * rx + ry * ry;
+        const double inv = 1.0 / rr;
+        int dj = a - k;
+        if (dj < 0) dj += n;
+        coef = T[dj] - pin * log(rr);
+        m11 = rx * rx * inv;
+        m12 = rx * ry * inv;
+        m22 = ry * ry * inv;
+      }
+      vx += coef * gx + h * (m11 * gx + m12 * gy);
+      vy += coef * gy + h * (m12 * gx + m22 * gy);
+    }
+    out[i] = make_double2(ux + vx, uy + vy);
+  }
+}
+
+__global__ void finish_free_kernel(int T, int splits, const double2 *partial, double2 *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double ux = 0.0, uy = 0.0;
+  for (int k = 0; k < splits; ++k) {
+    const double2 p = partial[size_t(k) * T + t];
+    ux += p.x;
+    uy += p.y;
+  }
+  out[t] = make_double2(ux, uy);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s) {
+  const int s32 = c->wall_slots + c->ves_slots_f32;
+  const int s64 = c->wall_slots_f64 + c->ves_slots_f64;
+  geom_check_kernel<<<nblk(c->N, 256), 256, 0, s>>>(c->N, c->d_x, c->d_nrm, c->d_w,
+                                                    c->n_wall_nodes ? c->d_kap : nullptr,
+                                                    c->d_status);
+  src_pos32_kernel<<<nblk(s32, 256), 256, 0, s>>>(s32, c->d_slot_node32, c->d_x, c->d_src_pos32);
+  src_pos64_kernel<<<nblk(s64, 256), 256, 0, s>>>(s64, c->d_slot_node64, c->d_x, c->d_src_pos64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kress_table(int n, double *T, cudaStream_t s) {
+  kress_table_kernel<<<nblk(n, 128), 128, 0, s>>>(n, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                        cudaStream_t s) {
+  PackArgs a{};
+  a.node_dens = c->d_node_dens;
+  a.w = c->d_w;
+  a.nrm = c->d_nrm;
+  a.slp = slp;
+  a.dlp = dlp;
+  a.c_slp = 1.0 / (4.0 * kPi * c->mu);
+  a.status = c->d_status;
+  if (precision == STOKES_FP32_KAHAN) {
+    a.slots = c->wall_slots + c->ves_slots_f32;
+    a.wall_slots = c->wall_slots;
+    a.slot_node = c->d_slot_node32;
+    pack_f32_kernel<<<nblk(a.slots, 256), 256, 0, s>>>(a, c->d_src_val32);
+  } else {
+    a.slots = c->wall_slots_f64 + c->ves_slots_f64;
+    a.wall_slots = c->wall_slots_f64;
+    a.slot_node = c->d_slot_node64;
+    pack_f64_kernel<<<nblk(a.slots, 256), 256, 0, s>>>(a, c->d_src_val64);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
+                                double jump, double2 *out, cudaStream_t s) {
+  if (c->n_wall_nodes > 0)
+    finish_walls_kernel<<<nblk(c->n_wall_nodes, 256), 256, 0, s>>>(
+        c->n_wall_nodes, c->d_wall_nodes, c->N, splits, c->d_partial, c->d_node_dens, c->d_nrm,
+        c->d_w, c->d_kap, dlp, jump, out);
+  if (c->n_ves_curves > 0) {
+    const size_t smem = size_t(4) * c->max_ves_n * sizeof(double);
+    finish_vesicles_kernel<<<c->n_ves_curves, 128, smem, s>>>(
+        c->d_ves_curve_ids, c->d_curves, c->d_kress, c->N, splits, c->d_partial, c->d_x,
+        c->d_nrm, c->d_w, slp, 1.0 / (4.0 * kPi * c->mu), out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2 *out,
+                               cudaStream_t s) {
+  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(n_targets, splits, c->d_partial, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stokes

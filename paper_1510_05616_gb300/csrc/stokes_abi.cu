@@ -1,0 +1,461 @@
+// stokes_abi.cu -- the C ABI of libstokes (host side): validation, layout planning,
+// device memory of a context, and the launch sequence of one layer-potential sum.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+
+#include "stokes_internal.cuh"
+
+namespace stokes {
+cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
+int effective_splits(stokes_ctx *c, int precision, int splits);
+}  // namespace stokes
+
+using namespace stokes;
+
+namespace {
+
+int fail(stokes_ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(stokes_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(stokes_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(c, STOKES_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(c, STOKES_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_geometry(stokes_ctx *c) {
+  dfree(c->d_x);
+  dfree(c->d_nrm);
+  dfree(c->d_w);
+  dfree(c->d_kap);
+  dfree(c->d_tgt_skip32);
+  dfree(c->d_tgt_skip64);
+  dfree(c->d_node_dens);
+  dfree(c->d_wall_nodes);
+  dfree(c->d_curves);
+  dfree(c->d_ves_curve_ids);
+  dfree(c->d_kress);
+  dfree(c->d_slot_node32);
+  dfree(c->d_src_pos32);
+  dfree(c->d_src_val32);
+  dfree(c->d_slot_node64);
+  dfree(c->d_src_pos64);
+  dfree(c->d_src_val64);
+  dfree(c->d_h_slp);
+  dfree(c->d_h_dlp);
+  dfree(c->d_h_out);
+  c->have_geom = false;
+  c->N = 0;
+}
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(&p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+template <class T>
+cudaError_t upload(T *&p, const std::vector<T> &v, cudaStream_t s) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int ensure_partial(stokes_ctx *c, size_t elems) {
+  if (elems <= c->partial_cap) return STOKES_OK;
+  CK(cudaDeviceSynchronize());
+  dfree(c->d_partial);
+  c->partial_cap = 0;
+  CK(dalloc(c->d_partial, elems));
+  c->partial_cap = elems;
+  return STOKES_OK;
+}
+
+// Default source splits: enough (target block, split) blocks for ~4 waves of the pair
+// kernel, with at least 4 tiles per split where the source range allows it.
+int default_splits(stokes_ctx *c, int precision) {
+  const bool f32 = precision == STOKES_FP32_KAHAN;
+  const int per_block = f32 ? kThreadsF32 * kTptF32 : kThreadsF64;
+  const int resident = f32 ? 8 : 6;
+  const int tblocks = (c->N + per_block - 1) / per_block;
+  const int n_tiles = f32 ? (c->wall_slots + c->ves_slots_f32) / kTileF32
+                          : (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
+  long want = (4L * resident * std::max(c->num_sms, 1) + tblocks - 1) / tblocks;
+  want = std::min<long>(want, std::max(1, n_tiles / 4));
+  want = std::max<long>(want, 1);
+  return effective_splits(c, precision, int(want));
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int read_status(stokes_ctx *c, cudaStream_t s) {
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    if (st & kStatusTimeout)
+      return fail(c, STOKES_ERR_TIMEOUT, "a device pipeline wait exceeded its bound");
+    return fail(c, STOKES_ERR_NONFINITE, "non-finite input value");
+  }
+  return STOKES_OK;
+}
+
+int check_density_args(stokes_ctx *c, int precision, const double *slp, const double *dlp) {
+  if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
+  if (c->n_ves_nodes > 0 && !slp) return fail(c, STOKES_ERR_ARG, "slp_density is NULL");
+  if (c->n_wall_nodes > 0 && !dlp) return fail(c, STOKES_ERR_ARG, "dlp_density is NULL");
+  return STOKES_OK;
+}
+
+int mark(stokes_ctx *c, int k, cudaStream_t s) {
+  if (!c->profiling) return STOKES_OK;
+  CK(cudaEventRecord(c->ev[k], s));
+  if (k == 3) c->timed = true;
+  return STOKES_OK;
+}
+
+#define MARK(k)                  \
+  do {                           \
+    int st_ = mark(c, (k), s);   \
+    if (st_) return st_;         \
+  } while (0)
+
+int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
+              double *out, cudaStream_t s) {
+  const int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
+  MARK(0);
+  CK(launch_pack(c, precision, slp, dlp, s));
+  MARK(1);
+  CK(launch_pair(c, precision, c->N, c->d_x,
+                 precision == STOKES_FP32_KAHAN ? c->d_tgt_skip32 : c->d_tgt_skip64, splits, s));
+  MARK(2);
+  CK(launch_finish_nodes(c, splits, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
+  MARK(3);
+  return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_create(int device, stokes_ctx **out) {
+  if (!out) return STOKES_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return STOKES_ERR_CUDA;
+  stokes_ctx *c = new stokes_ctx();
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void **>(&c->d_status), sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return STOKES_ERR_CUDA;
+  }
+  *out = c;
+  return STOKES_OK;
+}
+
+int stokes_destroy(stokes_ctx *c) {
+  if (!c) return STOKES_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  free_geometry(c);
+  dfree(c->d_partial);
+  dfree(c->d_status);
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  return STOKES_OK;
+}
+
+int stokes_last_error(const stokes_ctx *c, char *buf, size_t len) {
+  if (!c || !buf || len == 0) return STOKES_ERR_ARG;
+  snprintf(buf, len, "%s", c->err.c_str());
+  return STOKES_OK;
+}
+
+int stokes_num_nodes(const stokes_ctx *c) { return (c && c->have_geom) ? c->N : 0; }
+
+int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
+                    const int32_t *curve_kind, const double *nodes, const double *weights,
+                    const double *normals, const double *curvature, double period, double mu,
+                    void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  if (n_curves < 1 || !curve_offset || !curve_kind)
+    return fail(c, STOKES_ERR_ARG, "need n_curves >= 1 and host curve_offset / curve_kind");
+  if (!(isfinite(period) && period >= 0.0)) return fail(c, STOKES_ERR_ARG, "period must be finite and >= 0");
+  if (!(isfinite(mu) && mu > 0.0)) return fail(c, STOKES_ERR_ARG, "mu must be finite and > 0");
+  if (curve_offset[0] != 0) return fail(c, STOKES_ERR_ARG, "curve_offset[0] must be 0");
+  int n_wall = 0, n_ves = 0, max_ves = 0;
+  for (int k = 0; k < n_curves; ++k) {
+    const int n = curve_offset[k + 1] - curve_offset[k];
+    if (n <= 0) return fail(c, STOKES_ERR_ARG, "curve %d is empty or offsets decrease", k);
+    if (curve_kind[k] == STOKES_KIND_WALL) {
+      n_wall += n;
+    } else if (curve_kind[k] == STOKES_KIND_VESICLE) {
+      if (n < 4 || (n & 1))
+        return fail(c, STOKES_ERR_ODD_N, "vesicle curve %d has %d nodes; the Kress rule needs an even n >= 4", k, n);
+      if (n > kMaxVesicleNodes)
+        return fail(c, STOKES_ERR_ARG, "vesicle curve %d has %d > %d nodes", k, n, kMaxVesicleNodes);
+      n_ves += n;
+      max_ves = std::max(max_ves, n);
+    } else {
+      return fail(c, STOKES_ERR_ARG, "curve %d has unknown kind %d", k, curve_kind[k]);
+    }
+  }
+  const int N = curve_offset[n_curves];
+  if (!nodes || !weights || !normals) return fail(c, STOKES_ERR_ARG, "NULL geometry pointer");
+  if (n_wall > 0 && !curvature) return fail(c, STOKES_ERR_ARG, "curvature is required when walls are present");
+  if (!aligned16(nodes) || !aligned16(normals))
+    return fail(c, STOKES_ERR_ARG, "nodes and normals must be 16-byte aligned");
+
+  free_geometry(c);
+  c->N = N;
+  c->n_curves = n_curves;
+  c->n_wall_nodes = n_wall;
+  c->n_ves_nodes = n_ves;
+  c->max_ves_n = max_ves;
+  c->period = period;
+  c->mu = mu;
+  c->off.assign(curve_offset, curve_offset + n_curves + 1);
+  c->kind.assign(curve_kind, curve_kind + n_curves);
+
+  // ---- layout planning (host) ----
+  auto pad = [](int n, int t) { return (n + t - 1) / t * t; };
+  c->wall_slots = pad(n_wall, kTileF32);
+  c->ves_slots_f32 = pad(n_ves, kTileF32);
+  c->wall_slots_f64 = pad(n_wall, kTileF64);
+  c->ves_slots_f64 = pad(n_ves, kTileF64);
+  std::vector<int> slot32(size_t(c->wall_slots + c->ves_slots_f32), -1);
+  std::vector<int> slot64(size_t(c->wall_slots_f64 + c->ves_slots_f64), -1);
+  std::vector<int2> skip32(N, make_int2(-1, -1)), skip64(N, make_int2(-1, -1));
+  std::vector<int> node_dens(N), wall_nodes, ves_ids;
+  std::vector<CurveDev> curves(n_curves);
+  std::map<int, int> kress_off;
+  int kress_len = 0;
+  int ws = 0, vs = 0;
+  for (int k = 0; k < n_curves; ++k) {
+    const int b = curve_offset[k], n = curve_offset[k + 1] - b;
+    CurveDev cd{b, n, curve_kind[k], 0, -1};
+    if (curve_kind[k] == STOKES_KIND_WALL) {
+      cd.dens_begin = ws;
+      for (int a = 0; a < n; ++a) {
+        slot32[ws + a] = b + a;
+        slot64[ws + a] = b + a;
+        node_dens[b + a] = ws + a;
+        wall_nodes.push_back(b + a);
+      }
+      ws += n;
+    } else {
+      cd.dens_begin = vs;
+      const int s32 = c->wall_slots + vs, s64 = c->wall_slots_f64 + vs;
+      for (int a = 0; a < n; ++a) {
+        slot32[s32 + a] = b + a;
+        slot64[s64 + a] = b + a;
+        node_dens[b + a] = vs + a;
+        skip32[b + a] = make_int2(s32, s32 + n);
+        skip64[b + a] = make_int2(s64, s64 + n);
+      }
+      vs += n;
+      if (!kress_off.count(n)) {
+        kress_off[n] = kress_len;
+        kress_len += n;
+      }
+      cd.kress_off = kress_off[n];
+      ves_ids.push_back(k);
+    }
+    curves[k] = cd;
+  }
+  c->n_wall_curves = n_curves - int(ves_ids.size());
+  c->n_ves_curves = int(ves_ids.size());
+
+  // ---- device buffers ----
+  CK(dalloc(c->d_x, N));
+  CK(dalloc(c->d_nrm, N));
+  CK(dalloc(c->d_w, N));
+  CK(dalloc(c->d_kap, N));
+  CK(cudaMemcpyAsync(c->d_x, nodes, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->d_nrm, normals, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->d_w, weights, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  if (curvature)
+    CK(cudaMemcpyAsync(c->d_kap, curvature, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemsetAsync(c->d_kap, 0, sizeof(double) * N, s));
+  CK(upload(c->d_slot_node32, slot32, s));
+  CK(upload(c->d_slot_node64, slot64, s));
+  CK(upload(c->d_tgt_skip32, skip32, s));
+  CK(upload(c->d_tgt_skip64, skip64, s));
+  CK(upload(c->d_node_dens, node_dens, s));
+  CK(upload(c->d_wall_nodes, wall_nodes, s));
+  CK(upload(c->d_curves, curves, s));
+  CK(upload(c->d_ves_curve_ids, ves_ids, s));
+  CK(dalloc(c->d_kress, kress_len));
+  CK(dalloc(c->d_src_pos32, slot32.size()));
+  CK(dalloc(c->d_src_val32, slot32.size()));
+  CK(dalloc(c->d_src_pos64, slot64.size()));
+  CK(dalloc(c->d_src_val64, slot64.size()));
+  CK(dalloc(c->d_h_slp, size_t(2) * n_ves));
+  CK(dalloc(c->d_h_dlp, size_t(2) * n_wall));
+  CK(dalloc(c->d_h_out, size_t(2) * N));
+  for (auto &kv : kress_off) CK(launch_kress_table(kv.first, c->d_kress + kv.second, s));
+  CK(launch_geom_prep(c, s));
+  CK(cudaStreamSynchronize(s));
+
+  c->have_geom = true;
+  c->splits_f32 = default_splits(c, STOKES_FP32_KAHAN);
+  c->splits_f64 = default_splits(c, STOKES_FP64);
+  int st = ensure_partial(c, size_t(std::max(c->splits_f32, c->splits_f64)) * N);
+  if (st) return st;
+  st = read_status(c, s);
+  if (st) {
+    free_geometry(c);
+    return fail(c, STOKES_ERR_NONFINITE, "non-finite geometry value");
+  }
+  return STOKES_OK;
+}
+
+int stokes_sum_eval(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                    double jump, double *out, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  int st = check_density_args(c, precision, slp, dlp);
+  if (st) return st;
+  if (!out || !aligned16(out)) return fail(c, STOKES_ERR_ARG, "out_velocity must be a 16-byte aligned device pointer");
+  if (!isfinite(jump)) return fail(c, STOKES_ERR_ARG, "jump must be finite");
+  CK(cudaSetDevice(c->device));
+  return run_nodes(c, precision, slp, dlp, jump, out, as_stream(stream));
+}
+
+int stokes_sum_eval_targets(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                            int n_targets, const double *targets, double *out, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  int st = check_density_args(c, precision, slp, dlp);
+  if (st) return st;
+  if (n_targets < 0) return fail(c, STOKES_ERR_ARG, "n_targets < 0");
+  if (n_targets == 0) return STOKES_OK;
+  if (!targets || !out || !aligned16(targets) || !aligned16(out))
+    return fail(c, STOKES_ERR_ARG, "targets and out_velocity must be 16-byte aligned device pointers");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
+  st = ensure_partial(c, size_t(splits) * n_targets);
+  if (st) return st;
+  MARK(0);
+  CK(launch_pack(c, precision, slp, dlp, s));
+  MARK(1);
+  CK(launch_pair(c, precision, n_targets, reinterpret_cast<const double2 *>(targets), nullptr,
+                 splits, s));
+  MARK(2);
+  CK(launch_finish_free(c, splits, n_targets, reinterpret_cast<double2 *>(out), s));
+  MARK(3);
+  return STOKES_OK;
+}
+
+int stokes_sum_eval_host(stokes_ctx *c, int precision, const double *slp_h, const double *dlp_h,
+                         double jump, double *out_h) {
+  if (!c) return STOKES_ERR_ARG;
+  int st = check_density_args(c, precision, slp_h, dlp_h);
+  if (st) return st;
+  if (!out_h) return fail(c, STOKES_ERR_ARG, "out_host is NULL");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = c->own_stream;
+  if (c->n_ves_nodes)
+    CK(cudaMemcpyAsync(c->d_h_slp, slp_h, sizeof(double) * 2 * c->n_ves_nodes, cudaMemcpyHostToDevice, s));
+  if (c->n_wall_nodes)
+    CK(cudaMemcpyAsync(c->d_h_dlp, dlp_h, sizeof(double) * 2 * c->n_wall_nodes, cudaMemcpyHostToDevice, s));
+  st = run_nodes(c, precision, c->d_h_slp, c->d_h_dlp, jump, c->d_h_out, s);
+  if (st) return st;
+  CK(cudaMemcpyAsync(out_h, c->d_h_out, sizeof(double) * 2 * c->N, cudaMemcpyDeviceToHost, s));
+  return read_status(c, s);
+}
+
+int stokes_sync(stokes_ctx *c, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(as_stream(stream)));
+  return read_status(c, as_stream(stream));
+}
+
+int stokes_set_launch(stokes_ctx *c, int precision, int splits) {
+  if (!c) return STOKES_ERR_ARG;
+  if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
+  if (splits < 0) return fail(c, STOKES_ERR_ARG, "source_splits < 0");
+  if (splits == 0) return STOKES_OK;
+  CK(cudaSetDevice(c->device));
+  const int eff = effective_splits(c, precision, splits);
+  int st = ensure_partial(c, size_t(eff) * c->N);
+  if (st) return st;
+  (precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64) = eff;
+  return STOKES_OK;
+}
+
+int stokes_set_profiling(stokes_ctx *c, int on) {
+  if (!c) return STOKES_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  if (on && !c->ev[0])
+    for (auto &e : c->ev) CK(cudaEventCreate(&e));
+  c->profiling = on != 0;
+  c->timed = false;
+  return STOKES_OK;
+}
+
+int stokes_last_timing(stokes_ctx *c, double *ms) {
+  if (!c || !ms) return STOKES_ERR_ARG;
+  if (!c->timed) return fail(c, STOKES_ERR_ARG, "no timed call (enable stokes_set_profiling first)");
+  CK(cudaSetDevice(c->device));
+  CK(cudaEventSynchronize(c->ev[3]));
+  for (int k = 0; k < 3; ++k) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]));
+    ms[k] = t;
+  }
+  return STOKES_OK;
+}
+
+int stokes_pair_count(const stokes_ctx *c, int n_targets, double *pairs) {
+  if (!c || !pairs) return STOKES_ERR_ARG;
+  if (!c->have_geom) return STOKES_ERR_NO_GEOM;
+  const double nt = n_targets > 0 ? double(n_targets) : double(c->N);
+  *pairs = (c->period != 0.0 ? 3.0 : 1.0) * nt * double(c->N);
+  return STOKES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every declared call."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"STOKES_API\s+int\s+(\w+)\s*\(", src)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1510_05616_gb300 import build
+    build.build()
+    import paper_1510_05616_gb300 as P
+    return P.load()
+
+
+def test_header_declares_calls():
+    names = _declared()
+    for must in ("stokes_create", "stokes_geom_set", "stokes_sum_eval", "stokes_sum_eval_targets",
+                 "stokes_sum_eval_host", "stokes_sync"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_abi():
+    import paper_1510_05616_gb300 as P
+    for n in _declared():
+        assert callable(getattr(P, n, None)), n
+
+
+def test_null_handle_is_rejected_without_gpu(lib):
+    import ctypes
+    import paper_1510_05616_gb300 as P
+    assert lib.stokes_sum_eval(None, 0, None, None, 0.0, None, None) == P.STOKES_ERR_ARG
+    assert lib.stokes_destroy(None) == P.STOKES_OK
+    assert lib.stokes_num_nodes(None) == 0
+    h = ctypes.c_void_p()
+    # no GPU in a CPU-only run: creation must fail cleanly, never fall back
+    if not os.environ.get("CUDA_VISIBLE_DEVICES_FORCE"):
+        import torch
+        if not torch.cuda.is_available():
+            assert lib.stokes_create(0, ctypes.byref(h)) == P.STOKES_ERR_CUDA
+
+
+def test_binding_refuses_without_cuda():
+    import torch
+    import paper_1510_05616_gb300 as P
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.StokesError):
+        P.StokesSum(None)
