@@ -32,8 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "paper_n128k"
-WORKLOAD_DESC = ("channel walls y=+-(1+0.4 sin x+0.15 sin 3x), 2 x 16384 nodes; 750 vesicles x 128 "
-                 "nodes (volume fraction 0.15, gap >= 5h); period 2pi, images m=-1,0,1; N=128768")
+WORKLOAD_DESCS = {
+    "paper_n128k": ("channel walls y=+-(1+0.4 sin x+0.15 sin 3x), 2 x 16384 nodes; 750 vesicles x 128 "
+                    "nodes (volume fraction 0.15, gap >= 5h); period 2pi, images m=-1,0,1; N=128768"),
+    "mid_n16k": ("channel walls y=+-(1+0.3 sin x), 2 x 4096 nodes; 128 vesicles x 64 nodes "
+                 "(volume fraction 0.15); period 2pi, images m=-1,0,1; N=16384 (profiling case)"),
+    "small_n1280": ("channel walls y=+-(1+0.3 sin x), 2 x 512 nodes; 4 vesicles x 64 nodes; "
+                    "period 2pi, images m=-1,0,1; N=1280"),
+}
 METRIC = "Stokes SLP+DLP Gpair-evals/s at N≈128k: FP32-comp vs FP64, rel err ≤1e-6"
 # Nominal FP32 work of one pair-image evaluation (r, r^2, 1/r^2, log or (r.n), r.q, the
 # tensor-vector product and the accumulation), counting every add, multiply, reciprocal and
@@ -185,7 +191,7 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "N": g.n_nodes, "sample": "random target nodes per step"},
+        "config": {"workload": WORKLOAD_DESCS[WORKLOAD], "N": g.n_nodes, "sample": "random target nodes per step"},
         "cpu_baseline": {"value": val, "unit": "Gpair-evals/s", "cores": threads, "kind": "oracle",
                          "sample": "%s target nodes x all %d sources x 3 images per step"
                                    % (samples, g.n_nodes)},
@@ -205,6 +211,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -224,7 +231,7 @@ def main():
         torch.distributed.barrier()
     B.build()
 
-    g, slp, dlp = I.workload(WORKLOAD)
+    g, slp, dlp = I.workload(args.workload)
     dev = torch.device("cuda", local)
     s = P.StokesSum(g, device=local)
     ts = torch.as_tensor(slp, device=dev)
@@ -329,7 +336,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32k" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "N": g.n_nodes, "pairs_per_step": pairs,
+        "config": {"workload": WORKLOAD_DESCS[args.workload], "N": g.n_nodes, "pairs_per_step": pairs,
                    "precision": args.precision, "l2": "flushed before each timed step (256 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
