@@ -120,7 +120,7 @@ def kernel_source_hash():
 def profiled_traffic():
     """DRAM bytes per pair-kernel launch from the committed ncu summary, if it still
     describes the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "pair_f32k_paper_n128k.md")
+    p = os.path.join(ROOT, "profiles", "pair_f32k_paper_n128k.traffic.txt")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
