@@ -160,6 +160,31 @@ STOKES_API int stokes_sync(stokes_ctx *ctx, void *stream);
 STOKES_API int stokes_set_profiling(stokes_ctx *ctx, int on);
 STOKES_API int stokes_last_timing(stokes_ctx *ctx, double *ms);
 
+/*
+ * stokes_sum_eval_targets without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc where they evaluate -- code that
+ * records a CUDA graph by stream capture, hosts that own all device memory through their own
+ * pool, real-time loops that must not block on the allocator.  (stokes_sum_eval_targets may
+ * grow the context's scratch buffer, with a device synchronisation, when it sees more
+ * targets than before.)
+ *   Arguments, layout and results are those of stokes_sum_eval_targets; the context (created
+ *   and given a geometry beforehand) supplies the geometry and its preallocated source buffers.
+ *   The cross-split partial sums live in a fixed device array inside the library of
+ *   262,144 x 16 B = 4 MiB, held by every device that loads the library until the process
+ *   exits.  n_targets may be at most 262,144 (STOKES_ERR_ARG beyond, with a message); for
+ *   large n_targets fewer source splits are used so that splits x n_targets fits.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture.
+ *   All calls, from every context on a device, share the one array: calls whose kernels can
+ *   overlap on the GPU (different streams without ordering between them) race on it and
+ *   must be serialised by the caller.  Nothing in the array needs clearing between calls.
+ */
+STOKES_API int stokes_sum_eval_targets_noalloc(stokes_ctx *ctx, int precision,
+                                               const double *slp_density,
+                                               const double *dlp_density, int n_targets,
+                                               const double *targets, double *out_velocity,
+                                               void *stream);
+
 /* Number of nodes N of the current geometry (0 when none). */
 STOKES_API int stokes_num_nodes(const stokes_ctx *ctx);
 

@@ -49,6 +49,7 @@ _SIGNATURES = {
     "stokes_sum_eval": [_vp, _c_int, _vp, _vp, _c_double, _vp, _vp],
     "stokes_sum_eval_targets": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sum_eval_host": [_vp, _c_int, _vp, _vp, _c_double, _vp],
+    "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sync": [_vp, _vp],
     "stokes_num_nodes": [_vp],
     "stokes_set_launch": [_vp, _c_int, _c_int],
@@ -156,6 +157,20 @@ def stokes_sum_eval_targets(h, precision, slp_density, dlp_density, targets, out
                                           _dptr(targets, "targets", (2,), True),
                                           _dptr(out_velocity, "out_velocity", (2,), True),
                                           _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sum_eval_targets_noalloc(h, precision, slp_density, dlp_density, targets,
+                                    out_velocity, stream=None):
+    """Free-point evaluation that allocates no device memory (for callers that cannot call
+    cudaMalloc, e.g. while recording a CUDA graph); at most 262,144 targets."""
+    n = int(targets.shape[0])
+    code = load().stokes_sum_eval_targets_noalloc(h, int(precision),
+                                                  _dptr(slp_density, "slp_density", (2,), True),
+                                                  _dptr(dlp_density, "dlp_density", (2,), True),
+                                                  n, _dptr(targets, "targets", (2,), True),
+                                                  _dptr(out_velocity, "out_velocity", (2,), True),
+                                                  _stream(stream))
     return _check(h, code)
 
 

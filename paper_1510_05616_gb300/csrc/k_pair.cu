@@ -497,3 +497,18 @@ int effective_splits(stokes_ctx *c, int precision, int splits) {
 }
 
 }  // namespace stokes
+
+namespace stokes {
+
+// Same launch as launch_pair, with the FP64 partials written to a caller-chosen buffer
+// (the no-allocation entry point passes the address of its static device array).
+cudaError_t launch_pair_scratch(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
+                                int splits, double2 *partial, cudaStream_t s) {
+  double2 *keep = c->d_partial;
+  c->d_partial = partial;
+  const cudaError_t e = launch_pair(c, precision, n_targets, tgt, nullptr, splits, s);
+  c->d_partial = keep;
+  return e;
+}
+
+}  // namespace stokes

@@ -297,3 +297,14 @@ cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2
 }
 
 }  // namespace stokes
+
+namespace stokes {
+
+// Same as launch_finish_free, reading the partials from a caller-chosen buffer.
+cudaError_t launch_finish_free_scratch(int splits, int n_targets, const double2 *partial,
+                                       double2 *out, cudaStream_t s) {
+  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(n_targets, splits, partial, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stokes
