@@ -189,12 +189,19 @@ STOKES_API int stokes_sum_eval_targets_noalloc(stokes_ctx *ctx, int precision,
 STOKES_API int stokes_num_nodes(const stokes_ctx *ctx);
 
 /*
- * Kernel-shape knobs of the pair sum for `precision`: source tile length (sources per
- * pipeline stage), source splits (chunks of the source range summed by separate blocks and
- * reduced in FP64 in fixed order).  0 keeps the current value.  Used by the tuner;
- * results do not depend on them beyond FP64 rounding of the cross-split reduction.
+ * Kernel-shape knobs of the pair sum for `precision` (used by the tuner):
+ *   source_splits       chunks of the source range summed by separate blocks and reduced in
+ *                       FP64 in fixed order; 0 = the occupancy/wave model's default
+ *   targets_per_thread  FP32 path only: 1, 2 or 4 (0 keeps the current value)
+ *   kahan_group         FP32 path only: sources (all images) summed in FP32 before each Kahan
+ *                       update, 1, 2 or 4 (0 keeps the current value)
+ * Results depend on these only through FP32/FP64 rounding.  May grow the context's scratch
+ * buffer (device synchronisation).
  */
-STOKES_API int stokes_set_launch(stokes_ctx *ctx, int precision, int source_splits);
+STOKES_API int stokes_set_launch(stokes_ctx *ctx, int precision, int source_splits,
+                                 int targets_per_thread, int kahan_group);
+STOKES_API int stokes_get_launch(const stokes_ctx *ctx, int precision, int *source_splits,
+                                 int *targets_per_thread, int *kahan_group);
 
 /* Nominal pair-image evaluations of one stokes_sum_eval: 3 N_t N_s (1 N_t N_s when period
  * is 0), counting skipped and self pairs.  Written to *pairs. */

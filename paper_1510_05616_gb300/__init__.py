@@ -52,7 +52,9 @@ _SIGNATURES = {
     "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sync": [_vp, _vp],
     "stokes_num_nodes": [_vp],
-    "stokes_set_launch": [_vp, _c_int, _c_int],
+    "stokes_set_launch": [_vp, _c_int, _c_int, _c_int, _c_int],
+    "stokes_get_launch": [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                          ctypes.POINTER(_c_int)],
     "stokes_pair_count": [_vp, _c_int, ctypes.POINTER(_c_double)],
     "stokes_set_profiling": [_vp, _c_int],
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
@@ -207,8 +209,17 @@ def stokes_num_nodes(h) -> int:
     return int(load().stokes_num_nodes(h))
 
 
-def stokes_set_launch(h, precision, source_splits):
-    return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits)))
+def stokes_set_launch(h, precision, source_splits=0, targets_per_thread=0, kahan_group=0):
+    return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits),
+                                              int(targets_per_thread), int(kahan_group)))
+
+
+def stokes_get_launch(h, precision):
+    """(source_splits, targets_per_thread, kahan_group) of the current launch shape."""
+    a, b, c = _c_int(), _c_int(), _c_int()
+    _check(h, load().stokes_get_launch(h, int(precision), ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def stokes_set_profiling(h, on: bool = True):

@@ -137,15 +137,14 @@ __device__ __forceinline__ void load_target_f32(const PairArgs &a, int i, TgtF32
 }
 
 // Stokeslet source (Eq. (S)); val = (q1, q2, p1, p2), q = w f / (4 pi mu), p = -(ln 2 / 2) q.
-// Term per image: log2(r^2) p + r (r . q) / r^2.
+// Adds, for every image, log2(r^2) p + r (r . q) / r^2 to (ax, ay).
 template <int NIMG, bool MASK0>
 __device__ __forceinline__ void slp_source_f32(const TgtF32<NIMG> &t, const float4 pos,
-                                               const float4 val, bool skip0, float &tx,
-                                               float &ty) {
+                                               const float4 val, bool skip0, float &ax,
+                                               float &ay) {
   const float dy = (t.yh - pos.y) + (t.yl - pos.w);
   const float dyq = dy * val.y;
   const float dy2 = fmaf(dy, dy, kTiny32);
-  float ax = -0.0f, ay = -0.0f;
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
     if (MASK0 && k == NIMG / 2 && skip0) continue;
@@ -159,20 +158,17 @@ __device__ __forceinline__ void slp_source_f32(const TgtF32<NIMG> &t, const floa
     ay = fmaf(lg, val.w, ay);
     ay = fmaf(s, dy, ay);
   }
-  tx = ax;
-  ty = ay;
 }
 
 // Stresslet source (Eq. (D)); val = (q1, q2, n1, n2), q = w tau / pi.
-// Term per image: r (r . n)(r . q) / r^4.
+// Adds, for every image, r (r . n)(r . q) / r^4 to (ax, ay).
 template <int NIMG>
 __device__ __forceinline__ void dlp_source_f32(const TgtF32<NIMG> &t, const float4 pos,
-                                               const float4 val, float &tx, float &ty) {
+                                               const float4 val, float &ax, float &ay) {
   const float dy = (t.yh - pos.y) + (t.yl - pos.w);
   const float dyn = dy * val.w;
   const float dyq = dy * val.y;
   const float dy2 = fmaf(dy, dy, kTiny32);
-  float ax = -0.0f, ay = -0.0f;
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
     const float dx = (t.xh[k] - pos.x) + (t.xl[k] - pos.z);
@@ -184,11 +180,45 @@ __device__ __forceinline__ void dlp_source_f32(const TgtF32<NIMG> &t, const floa
     ax = fmaf(f, dx, ax);
     ay = fmaf(f, dy, ay);
   }
-  tx = ax;
-  ty = ay;
 }
 
-template <int NIMG, int TPT>
+// Sum over one tile: KG consecutive sources (all images) are added in FP32 into a group
+// sum, and each group sum enters the Kahan-compensated per-target accumulator.
+template <int NIMG, int TPT, int KG, int KIND>  // KIND: 0 stresslet, 1 stokeslet, 2 stokeslet
+                                                // with the own-curve m = 0 skip
+__device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], const float4 *P,
+                                             const float4 *V, int slot0, float (&sx)[TPT],
+                                             float (&cx)[TPT], float (&sy)[TPT],
+                                             float (&cy)[TPT]) {
+#pragma unroll(KIND == 2 ? 1 : 2)
+  for (int j = 0; j < kTileF32; j += KG) {
+    float gx[TPT], gy[TPT];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) gx[q] = gy[q] = -0.0f;
+#pragma unroll
+    for (int u = 0; u < KG; ++u) {
+      const float4 p = P[j + u], v = V[j + u];
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        if (KIND == 0) {
+          dlp_source_f32<NIMG>(tg[q], p, v, gx[q], gy[q]);
+        } else if (KIND == 1) {
+          slp_source_f32<NIMG, false>(tg[q], p, v, false, gx[q], gy[q]);
+        } else {
+          const bool s0 = (slot0 + j + u >= tg[q].skip.x) && (slot0 + j + u < tg[q].skip.y);
+          slp_source_f32<NIMG, true>(tg[q], p, v, s0, gx[q], gy[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      kahan_add(sx[q], cx[q], gx[q]);
+      kahan_add(sy[q], cy[q], gy[q]);
+    }
+  }
+}
+
+template <int NIMG, int TPT, int KG>
 __global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
   __shared__ __align__(128) float4 s_pos[kStages][kTileF32];
   __shared__ __align__(128) float4 s_val[kStages][kTileF32];
@@ -232,51 +262,20 @@ __global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
     const bool ok = mbar_wait_bounded(&s_bar[st], par);
     if (ok) {
       const int tile = tile0 + it;
+      const int slot0 = tile * kTileF32;
       const float4 *P = s_pos[st];
       const float4 *V = s_val[st];
       if (tile < a.n_wall_tiles) {
-#pragma unroll 2
-        for (int j = 0; j < kTileF32; ++j) {
-          const float4 p = P[j], v = V[j];
-#pragma unroll
-          for (int q = 0; q < TPT; ++q) {
-            float tx, ty;
-            dlp_source_f32<NIMG>(tg[q], p, v, tx, ty);
-            kahan_add(sx[q], cx[q], tx);
-            kahan_add(sy[q], cy[q], ty);
-          }
-        }
+        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, slot0, sx, cx, sy, cy);
       } else {
-        const int slot0 = tile * kTileF32;
         bool mine = false;
 #pragma unroll
         for (int q = 0; q < TPT; ++q)
           mine |= (tg[q].skip.x < slot0 + kTileF32) && (tg[q].skip.y > slot0);
-        if (__any_sync(0xffffffffu, mine)) {
-          for (int j = 0; j < kTileF32; ++j) {
-            const float4 p = P[j], v = V[j];
-#pragma unroll
-            for (int q = 0; q < TPT; ++q) {
-              const bool s0 = (slot0 + j >= tg[q].skip.x) && (slot0 + j < tg[q].skip.y);
-              float tx, ty;
-              slp_source_f32<NIMG, true>(tg[q], p, v, s0, tx, ty);
-              kahan_add(sx[q], cx[q], tx);
-              kahan_add(sy[q], cy[q], ty);
-            }
-          }
-        } else {
-#pragma unroll 2
-          for (int j = 0; j < kTileF32; ++j) {
-            const float4 p = P[j], v = V[j];
-#pragma unroll
-            for (int q = 0; q < TPT; ++q) {
-              float tx, ty;
-              slp_source_f32<NIMG, false>(tg[q], p, v, false, tx, ty);
-              kahan_add(sx[q], cx[q], tx);
-              kahan_add(sy[q], cy[q], ty);
-            }
-          }
-        }
+        if (__any_sync(0xffffffffu, mine))
+          tile_sum_f32<NIMG, TPT, KG, 2>(tg, P, V, slot0, sx, cx, sy, cy);
+        else
+          tile_sum_f32<NIMG, TPT, KG, 1>(tg, P, V, slot0, sx, cx, sy, cy);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -445,6 +444,30 @@ __global__ void __launch_bounds__(kThreadsF64) pair_f64_kernel(PairArgs a) {
 // ---------------------------------------------------------------------------
 // launcher
 // ---------------------------------------------------------------------------
+template <int NIMG, int TPT>
+void launch_f32k_kg(int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
+  switch (kg) {
+    case 1: pair_f32k_kernel<NIMG, TPT, 1><<<grid, kThreadsF32, 0, s>>>(a); break;
+    case 2: pair_f32k_kernel<NIMG, TPT, 2><<<grid, kThreadsF32, 0, s>>>(a); break;
+    default: pair_f32k_kernel<NIMG, TPT, 4><<<grid, kThreadsF32, 0, s>>>(a); break;
+  }
+}
+
+template <int NIMG>
+void launch_f32k_tpt(int tpt, int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
+  switch (tpt) {
+    case 1: launch_f32k_kg<NIMG, 1>(kg, grid, a, s); break;
+    case 4: launch_f32k_kg<NIMG, 4>(kg, grid, a, s); break;
+    default: launch_f32k_kg<NIMG, 2>(kg, grid, a, s); break;
+  }
+}
+
+void launch_f32k_variant(bool img, int tpt, int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
+  if (img)
+    launch_f32k_tpt<3>(tpt, kg, grid, a, s);
+  else
+    launch_f32k_tpt<1>(tpt, kg, grid, a, s);
+}
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
                         const int2 *skip, int splits, cudaStream_t s) {
   PairArgs a{};
@@ -463,11 +486,9 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
     a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
     const int eff = (a.n_tiles + a.tiles_per_split - 1) / a.tiles_per_split;
     if (eff != splits) return cudaErrorInvalidValue;  // callers pass effective_splits() values
-    dim3 grid((n_targets + kThreadsF32 * kTptF32 - 1) / (kThreadsF32 * kTptF32), eff);
-    if (img)
-      pair_f32k_kernel<3, kTptF32><<<grid, kThreadsF32, 0, s>>>(a);
-    else
-      pair_f32k_kernel<1, kTptF32><<<grid, kThreadsF32, 0, s>>>(a);
+    const int tpt = c->tpt_f32;
+    dim3 grid((n_targets + kThreadsF32 * tpt - 1) / (kThreadsF32 * tpt), eff);
+    launch_f32k_variant(img, tpt, c->kgroup_f32, grid, a, s);
   } else {
     a.n_wall_tiles = c->wall_slots_f64 / kTileF64;
     a.n_tiles = a.n_wall_tiles + c->ves_slots_f64 / kTileF64;
@@ -483,6 +504,33 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
       pair_f64_kernel<1><<<grid, kThreadsF64, 0, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+// Resident blocks per SM of the pair-kernel variant the context would launch.
+int pair_blocks_per_sm(stokes_ctx *c, int precision) {
+  int nb = 0;
+  const bool img = c->period != 0.0;
+  cudaError_t e;
+  if (precision == STOKES_FP32_KAHAN) {
+    const void *f = nullptr;
+#define STOKES_PICK(NI, TP, KG_)                                                   \
+  if (img == (NI == 3) && c->tpt_f32 == TP && c->kgroup_f32 == KG_)                 \
+    f = reinterpret_cast<const void *>(&pair_f32k_kernel<NI, TP, KG_>);
+    STOKES_PICK(3, 1, 1) STOKES_PICK(3, 1, 2) STOKES_PICK(3, 1, 4)
+    STOKES_PICK(3, 2, 1) STOKES_PICK(3, 2, 2) STOKES_PICK(3, 2, 4)
+    STOKES_PICK(3, 4, 1) STOKES_PICK(3, 4, 2) STOKES_PICK(3, 4, 4)
+    STOKES_PICK(1, 1, 1) STOKES_PICK(1, 1, 2) STOKES_PICK(1, 1, 4)
+    STOKES_PICK(1, 2, 1) STOKES_PICK(1, 2, 2) STOKES_PICK(1, 2, 4)
+    STOKES_PICK(1, 4, 1) STOKES_PICK(1, 4, 2) STOKES_PICK(1, 4, 4)
+#undef STOKES_PICK
+    if (!f) return 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreadsF32, 0);
+  } else {
+    const void *f = img ? reinterpret_cast<const void *>(&pair_f64_kernel<3>)
+                        : reinterpret_cast<const void *>(&pair_f64_kernel<1>);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreadsF64, 0);
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 // Effective number of splits actually launched for a requested count.

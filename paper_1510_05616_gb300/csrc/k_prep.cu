@@ -155,12 +155,13 @@ __global__ void finish_walls_kernel(int n_wall, const int *wall_nodes, int N, in
   out[i] = make_double2(ux + c * tx + jump * t1, uy + c * ty + jump * t2);
 }
 
-// One block per vesicle: FP64 reduction of its nodes' partials plus the Kress self term.
-__global__ void finish_vesicles_kernel(const int *ves_curves, const CurveDev *curves,
-                                       const double *kress, int N, int splits,
-                                       const double2 *partial, const double2 *x,
-                                       const double2 *nrm, const double *w, const double *slp,
-                                       double c_slp, double2 *out) {
+// Kress self term of the single layer (Sec. 3.2), FP64, one block per vesicle; writes
+// u_self to self[row] (row = the node's row in the vesicle density array).  Runs on a side
+// stream, concurrently with the pair kernel (FP64 pipe vs FP32/MUFU pipes).
+__global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
+                                  const double *kress, const double2 *x, const double2 *nrm,
+                                  const double *w, const double *slp, double c_slp,
+                                  double2 *self) {
   extern __shared__ double sh[];
   const CurveDev cv = curves[ves_curves[blockIdx.x]];
   const int n = cv.n;
@@ -181,12 +182,6 @@ __global__ void finish_vesicles_kernel(const int *ves_curves, const CurveDev *cu
   const double pin = kPi / n;
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
     const int i = cv.node_begin + a;
-    double ux = 0.0, uy = 0.0;
-    for (int k = 0; k < splits; ++k) {
-      const double2 p = partial[size_t(k) * N + i];
-      ux += p.x;
-      uy += p.y;
-    }
     const double xa = sx[a], ya = sy[a];
     double vx = 0.0, vy = 0.0;
     for (int k = 0; k < n; ++k) {
@@ -214,8 +209,25 @@ __global__ void finish_vesicles_kernel(const int *ves_curves, const CurveDev *cu
       vx += coef * gx + h * (m11 * gx + m12 * gy);
       vy += coef * gy + h * (m12 * gx + m22 * gy);
     }
-    out[i] = make_double2(ux + vx, uy + vy);
+    self[cv.dens_begin + a] = make_double2(vx, vy);
   }
+}
+
+// Vesicle nodes: FP64 fixed-order reduction of the split partials plus the self term.
+__global__ void finish_vesicle_nodes_kernel(int n_ves, const int *ves_nodes, int N, int splits,
+                                            const double2 *partial, const int *node_dens,
+                                            const double2 *self, double2 *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_ves) return;
+  const int i = ves_nodes[t];
+  double ux = 0.0, uy = 0.0;
+  for (int k = 0; k < splits; ++k) {
+    const double2 p = partial[size_t(k) * N + i];
+    ux += p.x;
+    uy += p.y;
+  }
+  const double2 v = self[node_dens[i]];
+  out[i] = make_double2(ux + v.x, uy + v.y);
 }
 
 __global__ void finish_free_kernel(int T, int splits, const double2 *partial, double2 *out) {
@@ -275,18 +287,28 @@ cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const d
   return cudaGetLastError();
 }
 
+cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s) {
+  if (c->n_ves_curves > 0) {
+    const size_t smem = size_t(4) * c->max_ves_n * sizeof(double);
+    self_kress_kernel<<<c->n_ves_curves, 128, smem, s>>>(c->d_ves_curve_ids, c->d_curves,
+                                                         c->d_kress, c->d_x, c->d_nrm, c->d_w,
+                                                         slp, 1.0 / (4.0 * kPi * c->mu),
+                                                         c->d_self);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
                                 double jump, double2 *out, cudaStream_t s) {
+  (void)slp;
   if (c->n_wall_nodes > 0)
     finish_walls_kernel<<<nblk(c->n_wall_nodes, 256), 256, 0, s>>>(
         c->n_wall_nodes, c->d_wall_nodes, c->N, splits, c->d_partial, c->d_node_dens, c->d_nrm,
         c->d_w, c->d_kap, dlp, jump, out);
-  if (c->n_ves_curves > 0) {
-    const size_t smem = size_t(4) * c->max_ves_n * sizeof(double);
-    finish_vesicles_kernel<<<c->n_ves_curves, 128, smem, s>>>(
-        c->d_ves_curve_ids, c->d_curves, c->d_kress, c->N, splits, c->d_partial, c->d_x,
-        c->d_nrm, c->d_w, slp, 1.0 / (4.0 * kPi * c->mu), out);
-  }
+  if (c->n_ves_nodes > 0)
+    finish_vesicle_nodes_kernel<<<nblk(c->n_ves_nodes, 256), 256, 0, s>>>(
+        c->n_ves_nodes, c->d_ves_nodes, c->N, splits, c->d_partial, c->d_node_dens, c->d_self,
+        out);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 namespace stokes {
 cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
+int pair_blocks_per_sm(stokes_ctx *c, int precision);
 }  // namespace stokes
 
 using namespace stokes;
@@ -59,6 +60,8 @@ void free_geometry(stokes_ctx *c) {
   dfree(c->d_tgt_skip64);
   dfree(c->d_node_dens);
   dfree(c->d_wall_nodes);
+  dfree(c->d_ves_nodes);
+  dfree(c->d_self);
   dfree(c->d_curves);
   dfree(c->d_ves_curve_ids);
   dfree(c->d_kress);
@@ -99,19 +102,31 @@ int ensure_partial(stokes_ctx *c, size_t elems) {
   return STOKES_OK;
 }
 
-// Default source splits: enough (target block, split) blocks for ~4 waves of the pair
-// kernel, with at least 4 tiles per split where the source range allows it.
+// Default source splits.  The pair kernel runs (target blocks x splits) equal-cost blocks in
+// waves of `slots` = resident blocks per SM x SMs; the time is ~ waves x (1 / splits), so the
+// split count minimising ceil(tb s / slots) / s wastes the least of the last wave.  At least
+// 4 tiles per split keep the per-block prologue and the partial traffic small.
 int default_splits(stokes_ctx *c, int precision) {
   const bool f32 = precision == STOKES_FP32_KAHAN;
-  const int per_block = f32 ? kThreadsF32 * kTptF32 : kThreadsF64;
-  const int resident = f32 ? 8 : 6;
-  const int tblocks = (c->N + per_block - 1) / per_block;
+  const int per_block = f32 ? kThreadsF32 * c->tpt_f32 : kThreadsF64;
+  const long slots = long(pair_blocks_per_sm(c, precision)) * std::max(c->num_sms, 1);
+  const long tb = (c->N + per_block - 1) / per_block;
   const int n_tiles = f32 ? (c->wall_slots + c->ves_slots_f32) / kTileF32
                           : (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
-  long want = (4L * resident * std::max(c->num_sms, 1) + tblocks - 1) / tblocks;
-  want = std::min<long>(want, std::max(1, n_tiles / 4));
-  want = std::max<long>(want, 1);
-  return effective_splits(c, precision, int(want));
+  const int smax = std::max(1, std::min(n_tiles / 4, 256));
+  int best = 1;
+  double best_cost = 1e300;
+  for (int sp = 1; sp <= smax; ++sp) {
+    const int eff = effective_splits(c, precision, sp);
+    if (eff != sp) continue;
+    const double waves = double((tb * eff + slots - 1) / slots);
+    const double cost = waves / eff + 2e-4 * eff;
+    if (cost < best_cost - 1e-12) {
+      best_cost = cost;
+      best = eff;
+    }
+  }
+  return best;
 }
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -156,11 +171,19 @@ int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp
               double *out, cudaStream_t s) {
   const int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
   MARK(0);
+  // fork: the FP64 Kress self pass runs on the side stream beside the pair kernel
+  if (c->n_ves_curves > 0) {
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    CK(launch_self(c, slp, c->side_stream));
+    CK(cudaEventRecord(c->ev_join, c->side_stream));
+  }
   CK(launch_pack(c, precision, slp, dlp, s));
   MARK(1);
   CK(launch_pair(c, precision, c->N, c->d_x,
                  precision == STOKES_FP32_KAHAN ? c->d_tgt_skip32 : c->d_tgt_skip64, splits, s));
   MARK(2);
+  if (c->n_ves_curves > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   CK(launch_finish_nodes(c, splits, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
   MARK(3);
   return STOKES_OK;
@@ -179,6 +202,9 @@ int stokes_create(int device, stokes_ctx **out) {
   c->device = device;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void **>(&c->d_status), sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -199,6 +225,9 @@ int stokes_destroy(stokes_ctx *c) {
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
   return STOKES_OK;
 }
@@ -266,7 +295,7 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
   std::vector<int> slot32(size_t(c->wall_slots + c->ves_slots_f32), -1);
   std::vector<int> slot64(size_t(c->wall_slots_f64 + c->ves_slots_f64), -1);
   std::vector<int2> skip32(N, make_int2(-1, -1)), skip64(N, make_int2(-1, -1));
-  std::vector<int> node_dens(N), wall_nodes, ves_ids;
+  std::vector<int> node_dens(N), wall_nodes, ves_nodes, ves_ids;
   std::vector<CurveDev> curves(n_curves);
   std::map<int, int> kress_off;
   int kress_len = 0;
@@ -291,6 +320,7 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
         slot64[s64 + a] = b + a;
         node_dens[b + a] = vs + a;
         skip32[b + a] = make_int2(s32, s32 + n);
+        ves_nodes.push_back(b + a);
         skip64[b + a] = make_int2(s64, s64 + n);
       }
       vs += n;
@@ -324,6 +354,8 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
   CK(upload(c->d_tgt_skip64, skip64, s));
   CK(upload(c->d_node_dens, node_dens, s));
   CK(upload(c->d_wall_nodes, wall_nodes, s));
+  CK(upload(c->d_ves_nodes, ves_nodes, s));
+  CK(dalloc(c->d_self, n_ves));
   CK(upload(c->d_curves, curves, s));
   CK(upload(c->d_ves_curve_ids, ves_ids, s));
   CK(dalloc(c->d_kress, kress_len));
@@ -412,18 +444,37 @@ int stokes_sync(stokes_ctx *c, void *stream) {
   return read_status(c, as_stream(stream));
 }
 
-int stokes_set_launch(stokes_ctx *c, int precision, int splits) {
+int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_thread,
+                      int kahan_group) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
     return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
   if (splits < 0) return fail(c, STOKES_ERR_ARG, "source_splits < 0");
-  if (splits == 0) return STOKES_OK;
+  if (targets_per_thread != 0 && targets_per_thread != 1 && targets_per_thread != 2 &&
+      targets_per_thread != 4)
+    return fail(c, STOKES_ERR_ARG, "targets_per_thread must be 0, 1, 2 or 4");
+  if (kahan_group != 0 && kahan_group != 1 && kahan_group != 2 && kahan_group != 4)
+    return fail(c, STOKES_ERR_ARG, "kahan_group must be 0, 1, 2 or 4");
   CK(cudaSetDevice(c->device));
-  const int eff = effective_splits(c, precision, splits);
+  if (precision == STOKES_FP32_KAHAN) {
+    if (targets_per_thread) c->tpt_f32 = targets_per_thread;
+    if (kahan_group) c->kgroup_f32 = kahan_group;
+  }
+  int eff = splits ? effective_splits(c, precision, splits) : default_splits(c, precision);
   int st = ensure_partial(c, size_t(eff) * c->N);
   if (st) return st;
   (precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64) = eff;
+  return STOKES_OK;
+}
+
+int stokes_get_launch(const stokes_ctx *c, int precision, int *splits, int *targets_per_thread,
+                      int *kahan_group) {
+  if (!c || !splits || !targets_per_thread || !kahan_group) return STOKES_ERR_ARG;
+  const bool f32 = precision == STOKES_FP32_KAHAN;
+  *splits = f32 ? c->splits_f32 : c->splits_f64;
+  *targets_per_thread = f32 ? c->tpt_f32 : 1;
+  *kahan_group = f32 ? c->kgroup_f32 : 0;
   return STOKES_OK;
 }
 

@@ -23,7 +23,7 @@ constexpr int kStages = 3;      // ring of shared-memory stages per block
 
 // Pair-kernel block shape.
 constexpr int kThreadsF32 = 128;
-constexpr int kTptF32 = 2;      // targets per thread
+constexpr int kTptF32 = 4;      // default targets per thread
 constexpr int kThreadsF64 = 128;
 constexpr int kTptF64 = 1;
 
@@ -62,6 +62,8 @@ struct stokes_ctx {
   int device = 0;
   std::string err;
   cudaStream_t own_stream = nullptr;
+  cudaStream_t side_stream = nullptr;   // runs the FP64 self pass beside the pair kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // geometry (host metadata)
   bool have_geom = false;
@@ -73,6 +75,8 @@ struct stokes_ctx {
   int wall_slots_f64 = 0;
   int max_ves_n = 0;
   int splits_f32 = 0, splits_f64 = 0;
+  int tpt_f32 = stokes::kTptF32;       // targets per thread of the FP32 pair kernel: 1, 2 or 4
+  int kgroup_f32 = 4;          // sources summed in FP32 before each Kahan update: 1, 2 or 4
 
   // device geometry
   double2 *d_x = nullptr;        // [N] nodes
@@ -83,6 +87,8 @@ struct stokes_ctx {
   int2 *d_tgt_skip64 = nullptr;  // [N] skip range in FP64 slot space
   int *d_node_dens = nullptr;    // [N] row in the node kind's density array
   int *d_wall_nodes = nullptr;   // [n_wall_nodes] node indices of wall nodes
+  int *d_ves_nodes = nullptr;    // [n_ves_nodes] node indices of vesicle nodes
+  double2 *d_self = nullptr;     // [n_ves_nodes] Kress self term, by vesicle density row
   stokes::CurveDev *d_curves = nullptr;  // [n_curves]
   int *d_ves_curve_ids = nullptr;        // [n_ves_curves]
   double *d_kress = nullptr;             // concatenated Kress tables T_j per vesicle size
@@ -117,6 +123,7 @@ cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const d
                         cudaStream_t s);
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
                         const int2 *skip, int splits, cudaStream_t s);
+cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s);
 cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
                                 double jump, double2 *out, cudaStream_t s);
 cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2 *out,

@@ -226,3 +226,28 @@ def test_errors_are_reported(P, small):
         s.set_geometry(odd)
     assert e.value.code == P.STOKES_ERR_ODD_N
     s.close()
+
+
+@pytest.mark.parametrize("tpt", [1, 2, 4])
+@pytest.mark.parametrize("kg", [1, 2, 4])
+def test_fp32_launch_shapes(P, oracle_mod, tpt, kg):
+    """Every compiled FP32 kernel shape (targets per thread x Kahan group) meets the bound,
+    on the ragged interleaved geometry (partial target blocks, padded tiles)."""
+    g, slp, dlp = _ragged()
+    ref = oracle_mod.sum_nodes(g, slp, dlp)
+    s = P.StokesSum(g)
+    P.stokes_set_launch(s.h, P.STOKES_FP32_KAHAN, 0, tpt, kg)
+    assert P.stokes_get_launch(s.h, P.STOKES_FP32_KAHAN)[1:] == (tpt, kg)
+    out = s.eval(dev(P, slp), dev(P, dlp), precision="fp32k").cpu().numpy()
+    s.close()
+    check(out, ref, g, "fp32k")
+
+
+def test_launch_knob_validation(P, small):
+    g, slp, dlp, _ = small
+    s = P.StokesSum(g)
+    for bad in ((0, 3, 0), (0, 0, 3), (-1, 0, 0)):
+        with pytest.raises(P.StokesError) as e:
+            P.stokes_set_launch(s.h, P.STOKES_FP32_KAHAN, *bad)
+        assert e.value.code == P.STOKES_ERR_ARG
+    s.close()
