@@ -201,6 +201,86 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """64 independent channels: one persistent graph-replayed launch vs the plain form
+    (one stokes_sum_eval per instance, back to back on one stream)."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    B.build()
+    ens = I.ensemble(workers=min(16, os.cpu_count() or 1))
+    geoms = [g for g, _, _ in ens]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    b = P.StokesBatch(geoms)
+    ts = torch.as_tensor(P.StokesBatch.stack([s for _, s, _ in ens]), device=dev)
+    td = torch.as_tensor(P.StokesBatch.stack([d for _, _, d in ens]), device=dev)
+    out = torch.empty((b.N, 2), dtype=torch.float64, device=dev)
+    pairs = P.stokes_pair_count(b.h)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps):
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    res = {}
+    for prec_name in ("fp32k", "fp64"):
+        prec = P.PRECISIONS[prec_name]
+        steps = args.steps if prec_name == "fp32k" else max(1, args.fp64_steps)
+        for _ in range(max(1, args.warmup if prec_name == "fp32k" else 1)):
+            P.stokes_batch_eval(b.h, prec, ts, td, 0.0, out, True)
+        P.stokes_sync(b.h)
+        g_ms = timed(lambda: P.stokes_batch_eval(b.h, prec, ts, td, 0.0, out, True), steps)
+        d_ms = timed(lambda: P.stokes_batch_eval(b.h, prec, ts, td, 0.0, out, False), steps)
+        res[prec_name] = {"graph_ms": statistics.median(g_ms), "direct_ms": statistics.median(d_ms),
+                          "graph_gpairs": pairs / statistics.median(g_ms) / 1e6,
+                          "items": P.stokes_batch_info(b.h, prec)[0],
+                          "blocks": P.stokes_batch_info(b.h, prec)[1]}
+    b.close()
+    # plain form: one single-instance context per channel, evaluated back to back
+    singles = [P.StokesSum(g) for g in geoms]
+    dens = [(torch.as_tensor(s, device=dev), torch.as_tensor(d, device=dev)) for _, s, d in ens]
+    outs = [torch.empty((g.n_nodes, 2), dtype=torch.float64, device=dev) for g in geoms]
+    for prec_name in ("fp32k",):
+        prec = P.PRECISIONS[prec_name]
+        for h, (s_, d_), o in zip(singles, dens, outs):
+            P.stokes_sum_eval(h.h, prec, s_, d_, 0.0, o)
+        torch.cuda.synchronize()
+
+        def plain():
+            for h, (s_, d_), o in zip(singles, dens, outs):
+                P.stokes_sum_eval(h.h, prec, s_, d_, 0.0, o)
+        p_ms = timed(plain, args.steps)
+        per = []
+        for h, (s_, d_), o, g in zip(singles, dens, outs, geoms):
+            ms = timed(lambda: P.stokes_sum_eval(h.h, prec, s_, d_, 0.0, o), 3)
+            per.append(P.stokes_pair_count(h.h) / min(ms) / 1e6)
+        res[prec_name]["plain_ms"] = statistics.median(p_ms)
+        res[prec_name]["plain_gpairs"] = pairs / statistics.median(p_ms) / 1e6
+        res[prec_name]["per_instance_gpairs"] = {"min": min(per), "median": statistics.median(per),
+                                                 "max": max(per)}
+    for h in singles:
+        h.close()
+    line = {"metric": "batched ensemble Gpair-evals/s (64 channels, one persistent graph launch)",
+            "value": res["fp32k"]["graph_gpairs"], "unit": "Gpair-evals/s", "n_gpus": 1,
+            "steps": args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 channels: wall nodes {1024..8192}/wall, vesicles U[10,400] x "
+                                   "{32..256} nodes, fill U[0.05,0.15]", "instances": len(geoms),
+                       "N_total": int(sum(g.n_nodes for g in geoms)), "pairs_per_step": pairs},
+            "results": res}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -212,9 +292,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
+    ap.add_argument("--batch", action="store_true",
+                    help="time the 64-channel batched ensemble instead (separate JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
 
     import torch
     ws, rank, local = dist_env()

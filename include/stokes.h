@@ -189,6 +189,43 @@ STOKES_API int stokes_sum_eval_targets_noalloc(stokes_ctx *ctx, int precision,
 STOKES_API int stokes_num_nodes(const stokes_ctx *ctx);
 
 /*
+ * Batched evaluation of many independent channel instances in one launch.
+ *
+ * stokes_batch_set: like stokes_geom_set for n_inst instances at once.  Instance k owns the
+ *   curves [inst_curve_offset[k], inst_curve_offset[k+1]) of the flattened curve list
+ *   (HOST int32[n_inst + 1], from 0 to n_curves) and has its own period periods[k] (HOST
+ *   double[n_inst]; all > 0 or all 0); mu is shared.  Sources of one instance never act on
+ *   targets of another.  The library plans (target block x source split) work items per
+ *   instance, sized so that every item costs about the same, and sorts them largest first.
+ *   Synchronizes `stream`.  With n_inst = 1 this is stokes_geom_set.
+ * stokes_batch_eval: velocities at every node of every instance (node order of the flattened
+ *   list), computed by one persistent pair-kernel launch whose blocks take items from a work
+ *   counter.  use_graph != 0 replays a CUDA graph of the whole evaluation (captured on the
+ *   first call per precision and jump; the densities are copied into and the result out of
+ *   the graph's own buffers on `stream`); use_graph = 0 launches the same kernels directly.
+ *   stokes_sum_eval on a batched context takes the direct route.
+ * stokes_batch_set_shape: the tuner's knobs of the batched launch for `precision`:
+ *   targets_per_thread (FP32: 1, 2, 4; 0 keeps) and items_per_slot (work items per resident
+ *   block the planner aims for, 1..64; 0 keeps).  Rebuilds the item tables and drops graphs.
+ * stokes_batch_info: number of items, resident blocks of the persistent launch, and the
+ *   current shape.
+ * Free-point evaluation and stokes_set_launch are not available on a batched context.
+ */
+STOKES_API int stokes_batch_set(stokes_ctx *ctx, int n_inst, const int32_t *inst_curve_offset,
+                                int n_curves, const int32_t *curve_offset,
+                                const int32_t *curve_kind, const double *nodes,
+                                const double *weights, const double *normals,
+                                const double *curvature, const double *periods, double mu,
+                                void *stream);
+STOKES_API int stokes_batch_eval(stokes_ctx *ctx, int precision, const double *slp_density,
+                                 const double *dlp_density, double jump, double *out_velocity,
+                                 int use_graph, void *stream);
+STOKES_API int stokes_batch_set_shape(stokes_ctx *ctx, int precision, int targets_per_thread,
+                                      int items_per_slot);
+STOKES_API int stokes_batch_info(const stokes_ctx *ctx, int precision, int *n_items,
+                                 int *blocks, int *targets_per_thread, int *items_per_slot);
+
+/*
  * Kernel-shape knobs of the pair sum for `precision` (used by the tuner):
  *   source_splits       chunks of the source range summed by separate blocks and reduced in
  *                       FP64 in fixed order; 0 = the occupancy/wave model's default

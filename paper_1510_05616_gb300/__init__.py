@@ -57,6 +57,11 @@ _SIGNATURES = {
                           ctypes.POINTER(_c_int)],
     "stokes_pair_count": [_vp, _c_int, ctypes.POINTER(_c_double)],
     "stokes_set_profiling": [_vp, _c_int],
+    "stokes_batch_set": [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _c_double,
+                         _vp],
+    "stokes_batch_eval": [_vp, _c_int, _vp, _vp, _c_double, _vp, _c_int, _vp],
+    "stokes_batch_set_shape": [_vp, _c_int, _c_int, _c_int],
+    "stokes_batch_info": [_vp, _c_int] + [ctypes.POINTER(_c_int)] * 4,
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
 }
 
@@ -239,8 +244,45 @@ def stokes_pair_count(h, n_targets: int = 0) -> float:
     return float(v.value)
 
 
+def stokes_batch_set(h, inst_curve_offset, curve_offset, curve_kind, nodes, weights, normals,
+                     curvature, periods, mu, stream=None):
+    import numpy as np
+    ioff = np.ascontiguousarray(inst_curve_offset, dtype=np.int32)
+    off = np.ascontiguousarray(curve_offset, dtype=np.int32)
+    kind = np.ascontiguousarray(curve_kind, dtype=np.int32)
+    per = np.ascontiguousarray(periods, dtype=np.float64)
+    code = load().stokes_batch_set(
+        h, int(ioff.shape[0] - 1), _vp(ioff.ctypes.data), int(kind.shape[0]), _vp(off.ctypes.data),
+        _vp(kind.ctypes.data), _dptr(nodes, "nodes", (2,)), _dptr(weights, "weights"),
+        _dptr(normals, "normals", (2,)), _dptr(curvature, "curvature", allow_none=True),
+        _vp(per.ctypes.data), float(mu), _stream(stream))
+    return _check(h, code)
+
+
+def stokes_batch_eval(h, precision, slp_density, dlp_density, jump, out_velocity, use_graph=True,
+                      stream=None):
+    code = load().stokes_batch_eval(h, int(precision),
+                                    _dptr(slp_density, "slp_density", (2,), True),
+                                    _dptr(dlp_density, "dlp_density", (2,), True), float(jump),
+                                    _dptr(out_velocity, "out_velocity", (2,)),
+                                    int(bool(use_graph)), _stream(stream))
+    return _check(h, code)
+
+
+def stokes_batch_set_shape(h, precision, targets_per_thread=0, items_per_slot=0):
+    return _check(h, load().stokes_batch_set_shape(h, int(precision), int(targets_per_thread),
+                                                   int(items_per_slot)))
+
+
+def stokes_batch_info(h, precision):
+    """(n_items, blocks, targets_per_thread, items_per_slot) of the batched launch."""
+    v = [_c_int() for _ in range(4)]
+    _check(h, load().stokes_batch_info(h, int(precision), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
 # ---------------------------------------------------------------------------
-# convenience wrapper
+# convenience wrappers
 # ---------------------------------------------------------------------------
 class StokesSum:
     """One libstokes context with a geometry resident on the GPU.
@@ -285,6 +327,64 @@ class StokesSum:
         if out is None:
             out = torch.empty((int(targets.shape[0]), 2), dtype=torch.float64, device=self.device)
         stokes_sum_eval_targets(self.h, prec, slp, dlp, targets, out)
+        if sync:
+            stokes_sync(self.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            stokes_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StokesBatch:
+    """Many independent channel instances evaluated by one persistent launch.
+
+    ``geoms`` is a list of geometry objects (as for :class:`StokesSum`) sharing one ``mu``.
+    Densities and results are the instances' arrays stacked in order (vesicle rows of all
+    instances, wall rows of all instances, node rows of all instances).
+    """
+
+    def __init__(self, geoms, device: int = 0):
+        import numpy as np
+        import torch
+        if not torch.cuda.is_available():
+            raise StokesError(STOKES_ERR_CUDA, "no CUDA device: libstokes runs on the GPU only")
+        self.device = torch.device("cuda", device)
+        self.h = stokes_create(device)
+        curves = [c for g in geoms for c in g.curves]
+        ioff = np.zeros(len(geoms) + 1, dtype=np.int32)
+        ioff[1:] = np.cumsum([len(g.curves) for g in geoms])
+        off = np.zeros(len(curves) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([c.n for c in curves])
+        kind = np.array([c.kind for c in curves], dtype=np.int32)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).to(self.device)
+        cat = lambda name: np.concatenate([getattr(c, name) for c in curves])
+        self._geom_tensors = (t(cat("nodes")), t(cat("weights")), t(cat("normals")),
+                              t(cat("curvature")))
+        x, w, n, k = self._geom_tensors
+        stokes_batch_set(self.h, ioff, off, kind, x, w, n, k, [g.period for g in geoms],
+                         geoms[0].mu)
+        self.N = int(off[-1])
+        self.sizes = [g.n_nodes for g in geoms]
+
+    @staticmethod
+    def stack(per_instance):
+        import numpy as np
+        return np.ascontiguousarray(np.concatenate([np.asarray(a).reshape(-1, 2) for a in per_instance]))
+
+    def eval(self, slp, dlp, precision="fp32k", jump=0.0, use_graph=True, out=None, sync=True):
+        import torch
+        prec = PRECISIONS.get(precision, precision)
+        if out is None:
+            out = torch.empty((self.N, 2), dtype=torch.float64, device=self.device)
+        stokes_batch_eval(self.h, prec, slp, dlp, jump, out, use_graph)
         if sync:
             stokes_sync(self.h)
         return out

@@ -218,54 +218,62 @@ __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], cons
   }
 }
 
+// Shared memory of the FP32 kernels: kStages source tiles and their mbarriers.
+struct SmemF32 {
+  __align__(128) float4 pos[kStages][kTileF32];
+  __align__(128) float4 val[kStages][kTileF32];
+  __align__(8) uint64_t bar[kStages];
+};
+
+__device__ __forceinline__ int item_tile(const ItemDesc &it, int vt) {
+  return vt < it.nw ? it.wb + vt : it.vb + (vt - it.nw);
+}
+
+// One work item: targets [tgt_begin, +tgt_count) against virtual tiles [vt_begin, vt_end).
+// `g` counts the tiles this block has consumed so far; stage = g mod kStages and the
+// mbarrier parity = (g / kStages) mod 2, so the barriers carry over from item to item.
+// Returns false when a stage wait timed out (the block must then leave; uniform).
 template <int NIMG, int TPT, int KG>
-__global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
-  __shared__ __align__(128) float4 s_pos[kStages][kTileF32];
-  __shared__ __align__(128) float4 s_val[kStages][kTileF32];
-  __shared__ __align__(8) uint64_t s_bar[kStages];
-
-  const int split = blockIdx.y;
-  const int tile0 = split * a.tiles_per_split;
-  const int ntl = min(a.n_tiles, tile0 + a.tiles_per_split) - tile0;
-
+__device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &it, SmemF32 &sm,
+                                             uint32_t &g) {
+  const int ntl = it.vt_end - it.vt_begin;
   TgtF32<NIMG> tg[TPT];
   float sx[TPT], cx[TPT], sy[TPT], cy[TPT];
-  const int base = blockIdx.x * (kThreadsF32 * TPT) + threadIdx.x;
+  {
+    PairArgs b = a;
+    b.period = it.period;
 #pragma unroll
-  for (int q = 0; q < TPT; ++q) {
-    const int i = min(base + q * kThreadsF32, a.n_targets - 1);
-    load_target_f32<NIMG>(a, i, tg[q]);
-    sx[q] = cx[q] = sy[q] = cy[q] = 0.0f;
+    for (int q = 0; q < TPT; ++q) {
+      const int loc = min(q * kThreadsF32 + int(threadIdx.x), it.tgt_count - 1);
+      load_target_f32<NIMG>(b, it.tgt_begin + loc, tg[q]);
+      sx[q] = cx[q] = sy[q] = cy[q] = 0.0f;
+    }
   }
-
   const float4 *gpos = static_cast<const float4 *>(a.src_pos);
   const float4 *gval = static_cast<const float4 *>(a.src_val);
   constexpr uint32_t kBytes = kTileF32 * sizeof(float4);
 
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages && s < ntl; ++s) {
-      mbar_arrive_expect_tx(&s_bar[s], 2 * kBytes);
-      bulk_g2s(s_pos[s], gpos + size_t(tile0 + s) * kTileF32, kBytes, &s_bar[s]);
-      bulk_g2s(s_val[s], gval + size_t(tile0 + s) * kTileF32, kBytes, &s_bar[s]);
+    for (int r = 0; r < kStages && r < ntl; ++r) {
+      const int st = (g + r) % kStages;
+      const int tile = item_tile(it, it.vt_begin + r);
+      mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
     }
   }
 
-  for (int it = 0; it < ntl; ++it) {
-    const int st = it % kStages;
-    const uint32_t par = (it / kStages) & 1u;
-    const bool ok = mbar_wait_bounded(&s_bar[st], par);
+  for (int r = 0; r < ntl; ++r) {
+    const uint32_t gr = g + r;
+    const int st = gr % kStages;
+    const bool ok = mbar_wait_bounded(&sm.bar[st], (gr / kStages) & 1u);
     if (ok) {
-      const int tile = tile0 + it;
+      const int vt = it.vt_begin + r;
+      const int tile = item_tile(it, vt);
       const int slot0 = tile * kTileF32;
-      const float4 *P = s_pos[st];
-      const float4 *V = s_val[st];
-      if (tile < a.n_wall_tiles) {
+      const float4 *P = sm.pos[st];
+      const float4 *V = sm.val[st];
+      if (vt < it.nw) {
         tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, slot0, sx, cx, sy, cy);
       } else {
         bool mine = false;
@@ -282,26 +290,74 @@ __global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
       // A stage never arrived: record it, let the copies still in flight land, and leave.
       if (threadIdx.x == 0) {
         atomicOr(a.status, kStatusTimeout);
-        for (int r = it; r < ntl && r < it + kStages; ++r)
-          mbar_wait_bounded(&s_bar[r % kStages], (r / kStages) & 1u);
+        for (int q = r; q < ntl && q < r + kStages; ++q)
+          mbar_wait_bounded(&sm.bar[(g + q) % kStages], ((g + q) / kStages) & 1u);
       }
       __syncthreads();
-      return;
+      return false;
     }
-    if (threadIdx.x == 0 && it + kStages < ntl) {
-      const int nt = tile0 + it + kStages;
-      mbar_arrive_expect_tx(&s_bar[st], 2 * kBytes);
-      bulk_g2s(s_pos[st], gpos + size_t(nt) * kTileF32, kBytes, &s_bar[st]);
-      bulk_g2s(s_val[st], gval + size_t(nt) * kTileF32, kBytes, &s_bar[st]);
+    if (threadIdx.x == 0 && r + kStages < ntl) {
+      const int tile = item_tile(it, it.vt_begin + r + kStages);
+      mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
     }
   }
+  g += ntl;
 
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
-    const int i = base + q * kThreadsF32;
-    if (i < a.n_targets)
-      a.partial[size_t(split) * a.n_targets + i] =
+    const int loc = q * kThreadsF32 + int(threadIdx.x);
+    if (loc < it.tgt_count)
+      a.partial[it.part_off + it.tgt_begin + loc] =
           make_double2(double(sx[q]) - double(cx[q]), double(sy[q]) - double(cy[q]));
+  }
+  return true;
+}
+
+__device__ __forceinline__ void init_barriers(uint64_t *bar) {
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// Single instance: blockIdx.x = target block, blockIdx.y = source split.
+template <int NIMG, int TPT, int KG>
+__global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
+  __shared__ SmemF32 sm;
+  init_barriers(sm.bar);
+  ItemDesc it;
+  it.tgt_begin = blockIdx.x * (kThreadsF32 * TPT);
+  it.tgt_count = min(kThreadsF32 * TPT, a.n_targets - it.tgt_begin);
+  it.vt_begin = blockIdx.y * a.tiles_per_split;
+  it.vt_end = min(a.n_tiles, it.vt_begin + a.tiles_per_split);
+  it.wb = 0;
+  it.nw = a.n_wall_tiles;
+  it.vb = a.n_wall_tiles;
+  it.part_off = (long long)blockIdx.y * a.n_targets;
+  it.period = a.period;
+  uint32_t g = 0;
+  run_item_f32<NIMG, TPT, KG>(a, it, sm, g);
+}
+
+// Batched instances: a persistent grid takes items from the table through a work counter.
+template <int NIMG, int TPT, int KG>
+__global__ void __launch_bounds__(kThreadsF32) pair_f32k_batch_kernel(PairArgs a) {
+  __shared__ SmemF32 sm;
+  __shared__ int s_item;
+  init_barriers(sm.bar);
+  uint32_t g = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int k = s_item;
+    __syncthreads();
+    if (k >= a.n_items) break;
+    const ItemDesc it = a.items[k];
+    if (!run_item_f32<NIMG, TPT, KG>(a, it, sm, g)) return;
   }
 }
 
@@ -359,115 +415,160 @@ __device__ __forceinline__ void dlp_source_f64(const TgtF64<NIMG> &t, const doub
   }
 }
 
+struct SmemF64 {
+  __align__(128) double2 pos[kStages][kTileF64];
+  __align__(128) double4_32a val[kStages][kTileF64];
+  __align__(8) uint64_t bar[kStages];
+};
+
 template <int NIMG>
-__global__ void __launch_bounds__(kThreadsF64) pair_f64_kernel(PairArgs a) {
-  __shared__ __align__(128) double2 s_pos[kStages][kTileF64];
-  __shared__ __align__(128) double4_32a s_val[kStages][kTileF64];
-  __shared__ __align__(8) uint64_t s_bar[kStages];
-
-  const int split = blockIdx.y;
-  const int tile0 = split * a.tiles_per_split;
-  const int ntl = min(a.n_tiles, tile0 + a.tiles_per_split) - tile0;
-
-  const int i_out = blockIdx.x * kThreadsF64 + threadIdx.x;
-  const int i = min(i_out, a.n_targets - 1);
+__device__ __forceinline__ bool run_item_f64(const PairArgs &a, const ItemDesc &it, SmemF64 &sm,
+                                             uint32_t &g) {
+  const int ntl = it.vt_end - it.vt_begin;
+  const int loc = threadIdx.x;
+  const int i = it.tgt_begin + min(loc, it.tgt_count - 1);
   TgtF64<NIMG> t;
   {
     const double2 p = a.tgt[i];
 #pragma unroll
-    for (int k = 0; k < NIMG; ++k) t.x[k] = p.x - ((NIMG == 3) ? double(k - 1) : 0.0) * a.period;
+    for (int k = 0; k < NIMG; ++k) t.x[k] = p.x - ((NIMG == 3) ? double(k - 1) : 0.0) * it.period;
     t.y = p.y;
     t.skip = a.tgt_skip ? a.tgt_skip[i] : make_int2(-1, -1);
   }
   double ux = 0.0, uy = 0.0;
-
   const double2 *gpos = static_cast<const double2 *>(a.src_pos);
   const double4_32a *gval = static_cast<const double4_32a *>(a.src_val);
   constexpr uint32_t kBp = kTileF64 * sizeof(double2);
   constexpr uint32_t kBv = kTileF64 * sizeof(double4_32a);
 
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages && s < ntl; ++s) {
-      mbar_arrive_expect_tx(&s_bar[s], kBp + kBv);
-      bulk_g2s(s_pos[s], gpos + size_t(tile0 + s) * kTileF64, kBp, &s_bar[s]);
-      bulk_g2s(s_val[s], gval + size_t(tile0 + s) * kTileF64, kBv, &s_bar[s]);
+    for (int r = 0; r < kStages && r < ntl; ++r) {
+      const int st = (g + r) % kStages;
+      const int tile = item_tile(it, it.vt_begin + r);
+      mbar_arrive_expect_tx(&sm.bar[st], kBp + kBv);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF64, kBp, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF64, kBv, &sm.bar[st]);
     }
   }
-
-  for (int it = 0; it < ntl; ++it) {
-    const int st = it % kStages;
-    const uint32_t par = (it / kStages) & 1u;
-    const bool ok = mbar_wait_bounded(&s_bar[st], par);
+  for (int r = 0; r < ntl; ++r) {
+    const uint32_t gr = g + r;
+    const int st = gr % kStages;
+    const bool ok = mbar_wait_bounded(&sm.bar[st], (gr / kStages) & 1u);
     if (ok) {
-      const int tile = tile0 + it;
-      if (tile < a.n_wall_tiles) {
-        for (int j = 0; j < kTileF64; ++j) dlp_source_f64<NIMG>(t, s_pos[st][j], s_val[st][j], ux, uy);
+      const int vt = it.vt_begin + r;
+      const int tile = item_tile(it, vt);
+      if (vt < it.nw) {
+        for (int j = 0; j < kTileF64; ++j) dlp_source_f64<NIMG>(t, sm.pos[st][j], sm.val[st][j], ux, uy);
       } else {
         const int slot0 = tile * kTileF64;
         const bool mine = (t.skip.x < slot0 + kTileF64) && (t.skip.y > slot0);
         if (__any_sync(0xffffffffu, mine)) {
           for (int j = 0; j < kTileF64; ++j) {
             const bool s0 = (slot0 + j >= t.skip.x) && (slot0 + j < t.skip.y);
-            slp_source_f64<NIMG, true>(t, s_pos[st][j], s_val[st][j], s0, ux, uy);
+            slp_source_f64<NIMG, true>(t, sm.pos[st][j], sm.val[st][j], s0, ux, uy);
           }
         } else {
           for (int j = 0; j < kTileF64; ++j)
-            slp_source_f64<NIMG, false>(t, s_pos[st][j], s_val[st][j], false, ux, uy);
+            slp_source_f64<NIMG, false>(t, sm.pos[st][j], sm.val[st][j], false, ux, uy);
         }
       }
     }
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(a.status, kStatusTimeout);
-        for (int r = it; r < ntl && r < it + kStages; ++r)
-          mbar_wait_bounded(&s_bar[r % kStages], (r / kStages) & 1u);
+        for (int q = r; q < ntl && q < r + kStages; ++q)
+          mbar_wait_bounded(&sm.bar[(g + q) % kStages], ((g + q) / kStages) & 1u);
       }
       __syncthreads();
-      return;
+      return false;
     }
-    if (threadIdx.x == 0 && it + kStages < ntl) {
-      const int nt = tile0 + it + kStages;
-      mbar_arrive_expect_tx(&s_bar[st], kBp + kBv);
-      bulk_g2s(s_pos[st], gpos + size_t(nt) * kTileF64, kBp, &s_bar[st]);
-      bulk_g2s(s_val[st], gval + size_t(nt) * kTileF64, kBv, &s_bar[st]);
+    if (threadIdx.x == 0 && r + kStages < ntl) {
+      const int tile = item_tile(it, it.vt_begin + r + kStages);
+      mbar_arrive_expect_tx(&sm.bar[st], kBp + kBv);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF64, kBp, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF64, kBv, &sm.bar[st]);
     }
   }
-  if (i_out < a.n_targets) a.partial[size_t(split) * a.n_targets + i_out] = make_double2(ux, uy);
+  g += ntl;
+  if (loc < it.tgt_count) a.partial[it.part_off + it.tgt_begin + loc] = make_double2(ux, uy);
+  return true;
+}
+
+template <int NIMG>
+__global__ void __launch_bounds__(kThreadsF64) pair_f64_kernel(PairArgs a) {
+  __shared__ SmemF64 sm;
+  init_barriers(sm.bar);
+  ItemDesc it;
+  it.tgt_begin = blockIdx.x * kThreadsF64;
+  it.tgt_count = min(kThreadsF64, a.n_targets - it.tgt_begin);
+  it.vt_begin = blockIdx.y * a.tiles_per_split;
+  it.vt_end = min(a.n_tiles, it.vt_begin + a.tiles_per_split);
+  it.wb = 0;
+  it.nw = a.n_wall_tiles;
+  it.vb = a.n_wall_tiles;
+  it.part_off = (long long)blockIdx.y * a.n_targets;
+  it.period = a.period;
+  uint32_t g = 0;
+  run_item_f64<NIMG>(a, it, sm, g);
+}
+
+template <int NIMG>
+__global__ void __launch_bounds__(kThreadsF64) pair_f64_batch_kernel(PairArgs a) {
+  __shared__ SmemF64 sm;
+  __shared__ int s_item;
+  init_barriers(sm.bar);
+  uint32_t g = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int k = s_item;
+    __syncthreads();
+    if (k >= a.n_items) break;
+    const ItemDesc it = a.items[k];
+    if (!run_item_f64<NIMG>(a, it, sm, g)) return;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // launcher
 // ---------------------------------------------------------------------------
-template <int NIMG, int TPT>
-void launch_f32k_kg(int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
-  switch (kg) {
-    case 1: pair_f32k_kernel<NIMG, TPT, 1><<<grid, kThreadsF32, 0, s>>>(a); break;
-    case 2: pair_f32k_kernel<NIMG, TPT, 2><<<grid, kThreadsF32, 0, s>>>(a); break;
-    default: pair_f32k_kernel<NIMG, TPT, 4><<<grid, kThreadsF32, 0, s>>>(a); break;
-  }
-}
+typedef void (*PairKernel)(PairArgs);
 
-template <int NIMG>
-void launch_f32k_tpt(int tpt, int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
-  switch (tpt) {
-    case 1: launch_f32k_kg<NIMG, 1>(kg, grid, a, s); break;
-    case 4: launch_f32k_kg<NIMG, 4>(kg, grid, a, s); break;
-    default: launch_f32k_kg<NIMG, 2>(kg, grid, a, s); break;
-  }
-}
-
-void launch_f32k_variant(bool img, int tpt, int kg, dim3 grid, const PairArgs &a, cudaStream_t s) {
-  if (img)
-    launch_f32k_tpt<3>(tpt, kg, grid, a, s);
+template <bool BATCH, int NIMG, int TPT, int KG>
+PairKernel f32_kernel() {
+  if constexpr (BATCH)
+    return pair_f32k_batch_kernel<NIMG, TPT, KG>;
   else
-    launch_f32k_tpt<1>(tpt, kg, grid, a, s);
+    return pair_f32k_kernel<NIMG, TPT, KG>;
 }
+
+template <bool BATCH, int NIMG, int TPT>
+PairKernel f32_by_kg(int kg) {
+  if constexpr (BATCH) {
+    return f32_kernel<true, NIMG, TPT, 4>();  // the batched launch always groups by 4
+  } else {
+    return kg == 1 ? f32_kernel<false, NIMG, TPT, 1>()
+                   : kg == 2 ? f32_kernel<false, NIMG, TPT, 2>() : f32_kernel<false, NIMG, TPT, 4>();
+  }
+}
+
+template <bool BATCH, int NIMG>
+PairKernel f32_by_tpt(int tpt, int kg) {
+  return tpt == 1 ? f32_by_kg<BATCH, NIMG, 1>(kg)
+                  : tpt == 2 ? f32_by_kg<BATCH, NIMG, 2>(kg) : f32_by_kg<BATCH, NIMG, 4>(kg);
+}
+
+// The FP32 kernel variant for (batched launch?, images?, targets per thread, Kahan group).
+PairKernel pick_f32(bool batch, bool img, int tpt, int kg) {
+  if (batch) return img ? f32_by_tpt<true, 3>(tpt, kg) : f32_by_tpt<true, 1>(tpt, kg);
+  return img ? f32_by_tpt<false, 3>(tpt, kg) : f32_by_tpt<false, 1>(tpt, kg);
+}
+
+PairKernel pick_f64(bool batch, bool img) {
+  if (batch) return img ? pair_f64_batch_kernel<3> : pair_f64_batch_kernel<1>;
+  return img ? pair_f64_kernel<3> : pair_f64_kernel<1>;
+}
+
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
                         const int2 *skip, int splits, cudaStream_t s) {
   PairArgs a{};
@@ -488,7 +589,7 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
     if (eff != splits) return cudaErrorInvalidValue;  // callers pass effective_splits() values
     const int tpt = c->tpt_f32;
     dim3 grid((n_targets + kThreadsF32 * tpt - 1) / (kThreadsF32 * tpt), eff);
-    launch_f32k_variant(img, tpt, c->kgroup_f32, grid, a, s);
+    pick_f32(false, img, tpt, c->kgroup_f32)<<<grid, kThreadsF32, 0, s>>>(a);
   } else {
     a.n_wall_tiles = c->wall_slots_f64 / kTileF64;
     a.n_tiles = a.n_wall_tiles + c->ves_slots_f64 / kTileF64;
@@ -498,39 +599,61 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
     const int eff = (a.n_tiles + a.tiles_per_split - 1) / a.tiles_per_split;
     if (eff != splits) return cudaErrorInvalidValue;
     dim3 grid((n_targets + kThreadsF64 - 1) / kThreadsF64, eff);
-    if (img)
-      pair_f64_kernel<3><<<grid, kThreadsF64, 0, s>>>(a);
-    else
-      pair_f64_kernel<1><<<grid, kThreadsF64, 0, s>>>(a);
+    pick_f64(false, img)<<<grid, kThreadsF64, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
+// Persistent launch over the context's item table (batched instances): `blocks` resident
+// blocks take items in table order (largest first) through a zeroed work counter.
+cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStream_t s) {
+  PairArgs a{};
+  a.n_targets = c->N;
+  a.tgt = c->d_x;
+  a.partial = c->d_partial;
+  a.status = c->d_status;
+  a.counter = c->d_counter;
+  const bool img = c->period != 0.0;
+  cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (precision == STOKES_FP32_KAHAN) {
+    a.tgt_skip = c->d_tgt_skip32;
+    a.src_pos = c->d_src_pos32;
+    a.src_val = c->d_src_val32;
+    a.items = c->d_items32;
+    a.n_items = c->n_items32;
+    pick_f32(true, img, c->tpt_f32, 4)<<<blocks, kThreadsF32, 0, s>>>(a);
+  } else {
+    a.tgt_skip = c->d_tgt_skip64;
+    a.src_pos = c->d_src_pos64;
+    a.src_val = c->d_src_val64;
+    a.items = c->d_items64;
+    a.n_items = c->n_items64;
+    pick_f64(true, img)<<<blocks, kThreadsF64, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+static int occupancy(PairKernel f, int threads) {
+  int nb = 0;
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, reinterpret_cast<const void *>(f), threads, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
 // Resident blocks per SM of the pair-kernel variant the context would launch.
 int pair_blocks_per_sm(stokes_ctx *c, int precision) {
-  int nb = 0;
   const bool img = c->period != 0.0;
-  cudaError_t e;
-  if (precision == STOKES_FP32_KAHAN) {
-    const void *f = nullptr;
-#define STOKES_PICK(NI, TP, KG_)                                                   \
-  if (img == (NI == 3) && c->tpt_f32 == TP && c->kgroup_f32 == KG_)                 \
-    f = reinterpret_cast<const void *>(&pair_f32k_kernel<NI, TP, KG_>);
-    STOKES_PICK(3, 1, 1) STOKES_PICK(3, 1, 2) STOKES_PICK(3, 1, 4)
-    STOKES_PICK(3, 2, 1) STOKES_PICK(3, 2, 2) STOKES_PICK(3, 2, 4)
-    STOKES_PICK(3, 4, 1) STOKES_PICK(3, 4, 2) STOKES_PICK(3, 4, 4)
-    STOKES_PICK(1, 1, 1) STOKES_PICK(1, 1, 2) STOKES_PICK(1, 1, 4)
-    STOKES_PICK(1, 2, 1) STOKES_PICK(1, 2, 2) STOKES_PICK(1, 2, 4)
-    STOKES_PICK(1, 4, 1) STOKES_PICK(1, 4, 2) STOKES_PICK(1, 4, 4)
-#undef STOKES_PICK
-    if (!f) return 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreadsF32, 0);
-  } else {
-    const void *f = img ? reinterpret_cast<const void *>(&pair_f64_kernel<3>)
-                        : reinterpret_cast<const void *>(&pair_f64_kernel<1>);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreadsF64, 0);
-  }
-  return (e == cudaSuccess && nb > 0) ? nb : 1;
+  if (precision == STOKES_FP32_KAHAN)
+    return occupancy(pick_f32(false, img, c->tpt_f32, c->kgroup_f32), kThreadsF32);
+  return occupancy(pick_f64(false, img), kThreadsF64);
+}
+
+int pair_batch_blocks_per_sm(stokes_ctx *c, int precision) {
+  const bool img = c->period != 0.0;
+  if (precision == STOKES_FP32_KAHAN)
+    return occupancy(pick_f32(true, img, c->tpt_f32, 4), kThreadsF32);
+  return occupancy(pick_f64(true, img), kThreadsF64);
 }
 
 // Effective number of splits actually launched for a requested count.

@@ -134,19 +134,47 @@ __global__ void pack_f64_kernel(PackArgs a, double4_32a *val) {
 // ---------------------------------------------------------------------------
 // finishing pass
 // ---------------------------------------------------------------------------
-__global__ void finish_walls_kernel(int n_wall, const int *wall_nodes, int N, int splits,
+// Where the split partials of a target live: one instance (partial[k * N + i], k < splits),
+// or batched instances (each with its own split count, stride and offset).
+struct PartLoc {
+  const int *node_inst;   // NULL for a single instance
+  const InstDev *inst;
+  int f64;
+  int N, splits;
+};
+
+__device__ __forceinline__ void part_sum(const PartLoc &L, const double2 *partial, int i,
+                                         double &ux, double &uy) {
+  long long base;
+  int stride, cnt;
+  if (L.node_inst) {
+    const InstDev &I = L.inst[L.node_inst[i]];
+    base = (L.f64 ? I.part_off64 : I.part_off32) + (i - I.node_begin);
+    stride = I.N;
+    cnt = L.f64 ? I.splits64 : I.splits32;
+  } else {
+    base = i;
+    stride = L.N;
+    cnt = L.splits;
+  }
+  ux = 0.0;
+  uy = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const double2 p = partial[base + (long long)k * stride];
+    ux += p.x;
+    uy += p.y;
+  }
+}
+
+__global__ void finish_walls_kernel(int n_wall, const int *wall_nodes, PartLoc L,
                                     const double2 *partial, const int *node_dens,
                                     const double2 *nrm, const double *w, const double *kap,
                                     const double *dlp, double jump, double2 *out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_wall) return;
   const int i = wall_nodes[t];
-  double ux = 0.0, uy = 0.0;
-  for (int k = 0; k < splits; ++k) {
-    const double2 p = partial[size_t(k) * N + i];
-    ux += p.x;
-    uy += p.y;
-  }
+  double ux, uy;
+  part_sum(L, partial, i, ux, uy);
   const int row = node_dens[i];
   const double t1 = dlp[2 * row], t2 = dlp[2 * row + 1];
   const double2 n = nrm[i];
@@ -214,18 +242,14 @@ __global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
 }
 
 // Vesicle nodes: FP64 fixed-order reduction of the split partials plus the self term.
-__global__ void finish_vesicle_nodes_kernel(int n_ves, const int *ves_nodes, int N, int splits,
+__global__ void finish_vesicle_nodes_kernel(int n_ves, const int *ves_nodes, PartLoc L,
                                             const double2 *partial, const int *node_dens,
                                             const double2 *self, double2 *out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_ves) return;
   const int i = ves_nodes[t];
-  double ux = 0.0, uy = 0.0;
-  for (int k = 0; k < splits; ++k) {
-    const double2 p = partial[size_t(k) * N + i];
-    ux += p.x;
-    uy += p.y;
-  }
+  double ux, uy;
+  part_sum(L, partial, i, ux, uy);
   const double2 v = self[node_dens[i]];
   out[i] = make_double2(ux + v.x, uy + v.y);
 }
@@ -298,18 +322,29 @@ cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static cudaError_t finish_nodes(stokes_ctx *c, const PartLoc &L, const double *dlp, double jump,
+                                double2 *out, cudaStream_t s) {
+  if (c->n_wall_nodes > 0)
+    finish_walls_kernel<<<nblk(c->n_wall_nodes, 256), 256, 0, s>>>(
+        c->n_wall_nodes, c->d_wall_nodes, L, c->d_partial, c->d_node_dens, c->d_nrm, c->d_w,
+        c->d_kap, dlp, jump, out);
+  if (c->n_ves_nodes > 0)
+    finish_vesicle_nodes_kernel<<<nblk(c->n_ves_nodes, 256), 256, 0, s>>>(
+        c->n_ves_nodes, c->d_ves_nodes, L, c->d_partial, c->d_node_dens, c->d_self, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
                                 double jump, double2 *out, cudaStream_t s) {
   (void)slp;
-  if (c->n_wall_nodes > 0)
-    finish_walls_kernel<<<nblk(c->n_wall_nodes, 256), 256, 0, s>>>(
-        c->n_wall_nodes, c->d_wall_nodes, c->N, splits, c->d_partial, c->d_node_dens, c->d_nrm,
-        c->d_w, c->d_kap, dlp, jump, out);
-  if (c->n_ves_nodes > 0)
-    finish_vesicle_nodes_kernel<<<nblk(c->n_ves_nodes, 256), 256, 0, s>>>(
-        c->n_ves_nodes, c->d_ves_nodes, c->N, splits, c->d_partial, c->d_node_dens, c->d_self,
-        out);
-  return cudaGetLastError();
+  const PartLoc L{nullptr, nullptr, 0, c->N, splits};
+  return finish_nodes(c, L, dlp, jump, out, s);
+}
+
+cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp, double jump,
+                                double2 *out, cudaStream_t s) {
+  const PartLoc L{c->d_node_inst, c->d_inst, precision == STOKES_FP64 ? 1 : 0, c->N, 0};
+  return finish_nodes(c, L, dlp, jump, out, s);
 }
 
 cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2 *out,

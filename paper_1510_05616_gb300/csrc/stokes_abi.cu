@@ -62,6 +62,21 @@ void free_geometry(stokes_ctx *c) {
   dfree(c->d_wall_nodes);
   dfree(c->d_ves_nodes);
   dfree(c->d_self);
+  dfree(c->d_node_inst);
+  dfree(c->d_inst);
+  dfree(c->d_items32);
+  dfree(c->d_items64);
+  dfree(c->d_b_slp);
+  dfree(c->d_b_dlp);
+  dfree(c->d_b_out);
+  for (auto &g : c->graph_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  c->n_inst = 1;
+  c->inst.clear();
+  c->n_items32 = c->n_items64 = 0;
   dfree(c->d_curves);
   dfree(c->d_ves_curve_ids);
   dfree(c->d_kress);
@@ -167,8 +182,30 @@ int mark(stokes_ctx *c, int k, cudaStream_t s) {
     if (st_) return st_;         \
   } while (0)
 
+// Batched instances: the same phases, with the persistent item-table pair kernel.
+int run_batch(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
+              double *out, cudaStream_t s) {
+  MARK(0);
+  if (c->n_ves_curves > 0) {
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    CK(launch_self(c, slp, c->side_stream));
+    CK(cudaEventRecord(c->ev_join, c->side_stream));
+  }
+  CK(launch_pack(c, precision, slp, dlp, s));
+  MARK(1);
+  const int blocks = pair_batch_blocks_per_sm(c, precision) * std::max(c->num_sms, 1);
+  CK(launch_pair_batch(c, precision, blocks, s));
+  MARK(2);
+  if (c->n_ves_curves > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  CK(launch_finish_batch(c, precision, dlp, jump, reinterpret_cast<double2 *>(out), s));
+  MARK(3);
+  return STOKES_OK;
+}
+
 int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
               double *out, cudaStream_t s) {
+  if (c->n_inst > 1) return run_batch(c, precision, slp, dlp, jump, out, s);
   const int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
   MARK(0);
   // fork: the FP64 Kress self pass runs on the side stream beside the pair kernel
@@ -222,6 +259,7 @@ int stokes_destroy(stokes_ctx *c) {
   free_geometry(c);
   dfree(c->d_partial);
   dfree(c->d_status);
+  dfree(c->d_counter);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -240,18 +278,34 @@ int stokes_last_error(const stokes_ctx *c, char *buf, size_t len) {
 
 int stokes_num_nodes(const stokes_ctx *c) { return (c && c->have_geom) ? c->N : 0; }
 
-int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
-                    const int32_t *curve_kind, const double *nodes, const double *weights,
-                    const double *normals, const double *curvature, double period, double mu,
-                    void *stream) {
-  if (!c) return STOKES_ERR_ARG;
-  CK(cudaSetDevice(c->device));
-  cudaStream_t s = as_stream(stream);
+}  // extern "C"
+
+namespace stokes {
+
+// Validate and upload a geometry of n_inst independent instances (instance k owns curves
+// [inst_curve_off[k], inst_curve_off[k+1])), and build the source-slot layout: the wall tiles
+// of every instance, then the vesicle tiles of every instance, each instance's run padded to
+// the tile length with zero-weight dummies.
+int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const double *periods,
+                 int n_curves, const int32_t *curve_offset, const int32_t *curve_kind,
+                 const double *nodes, const double *weights, const double *normals,
+                 const double *curvature, double mu, cudaStream_t s) {
   if (n_curves < 1 || !curve_offset || !curve_kind)
     return fail(c, STOKES_ERR_ARG, "need n_curves >= 1 and host curve_offset / curve_kind");
-  if (!(isfinite(period) && period >= 0.0)) return fail(c, STOKES_ERR_ARG, "period must be finite and >= 0");
   if (!(isfinite(mu) && mu > 0.0)) return fail(c, STOKES_ERR_ARG, "mu must be finite and > 0");
   if (curve_offset[0] != 0) return fail(c, STOKES_ERR_ARG, "curve_offset[0] must be 0");
+  if (n_inst < 1 || inst_curve_off[0] != 0 || inst_curve_off[n_inst] != n_curves)
+    return fail(c, STOKES_ERR_ARG, "instance curve offsets must run from 0 to n_curves");
+  bool any_img = false, any_flat = false;
+  for (int k = 0; k < n_inst; ++k) {
+    if (inst_curve_off[k + 1] <= inst_curve_off[k])
+      return fail(c, STOKES_ERR_ARG, "instance %d has no curves", k);
+    if (!(isfinite(periods[k]) && periods[k] >= 0.0))
+      return fail(c, STOKES_ERR_ARG, "period of instance %d must be finite and >= 0", k);
+    (periods[k] != 0.0 ? any_img : any_flat) = true;
+  }
+  if (any_img && any_flat)
+    return fail(c, STOKES_ERR_ARG, "instances must all have a period > 0 or all have period 0");
   int n_wall = 0, n_ves = 0, max_ves = 0;
   for (int k = 0; k < n_curves; ++k) {
     const int n = curve_offset[k + 1] - curve_offset[k];
@@ -281,60 +335,97 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
   c->n_wall_nodes = n_wall;
   c->n_ves_nodes = n_ves;
   c->max_ves_n = max_ves;
-  c->period = period;
+  c->period = periods[0];
   c->mu = mu;
   c->off.assign(curve_offset, curve_offset + n_curves + 1);
   c->kind.assign(curve_kind, curve_kind + n_curves);
+  c->n_inst = n_inst;
 
   // ---- layout planning (host) ----
   auto pad = [](int n, int t) { return (n + t - 1) / t * t; };
-  c->wall_slots = pad(n_wall, kTileF32);
-  c->ves_slots_f32 = pad(n_ves, kTileF32);
-  c->wall_slots_f64 = pad(n_wall, kTileF64);
-  c->ves_slots_f64 = pad(n_ves, kTileF64);
-  std::vector<int> slot32(size_t(c->wall_slots + c->ves_slots_f32), -1);
-  std::vector<int> slot64(size_t(c->wall_slots_f64 + c->ves_slots_f64), -1);
+  std::vector<InstHost> inst(n_inst);
+  std::vector<int> inst_wall(n_inst, 0), inst_ves(n_inst, 0);
+  for (int k = 0; k < n_inst; ++k) {
+    for (int cc = inst_curve_off[k]; cc < inst_curve_off[k + 1]; ++cc)
+      (curve_kind[cc] == STOKES_KIND_WALL ? inst_wall[k] : inst_ves[k]) +=
+          curve_offset[cc + 1] - curve_offset[cc];
+    InstHost &I = inst[k];
+    I = InstHost{};
+    I.node_begin = curve_offset[inst_curve_off[k]];
+    I.N = curve_offset[inst_curve_off[k + 1]] - I.node_begin;
+    I.period = periods[k];
+  }
+  int t32 = 0, t64 = 0;
+  for (int k = 0; k < n_inst; ++k) {  // wall runs
+    inst[k].wb32 = t32;
+    inst[k].nw32 = pad(inst_wall[k], kTileF32) / kTileF32;
+    t32 += inst[k].nw32;
+    inst[k].wb64 = t64;
+    inst[k].nw64 = pad(inst_wall[k], kTileF64) / kTileF64;
+    t64 += inst[k].nw64;
+  }
+  c->wall_slots = t32 * kTileF32;
+  c->wall_slots_f64 = t64 * kTileF64;
+  for (int k = 0; k < n_inst; ++k) {  // vesicle runs
+    inst[k].vb32 = t32;
+    inst[k].nv32 = pad(inst_ves[k], kTileF32) / kTileF32;
+    t32 += inst[k].nv32;
+    inst[k].vb64 = t64;
+    inst[k].nv64 = pad(inst_ves[k], kTileF64) / kTileF64;
+    t64 += inst[k].nv64;
+  }
+  c->ves_slots_f32 = t32 * kTileF32 - c->wall_slots;
+  c->ves_slots_f64 = t64 * kTileF64 - c->wall_slots_f64;
+  std::vector<int> slot32(size_t(t32) * kTileF32, -1);
+  std::vector<int> slot64(size_t(t64) * kTileF64, -1);
   std::vector<int2> skip32(N, make_int2(-1, -1)), skip64(N, make_int2(-1, -1));
-  std::vector<int> node_dens(N), wall_nodes, ves_nodes, ves_ids;
+  std::vector<int> node_dens(N), node_inst(N), wall_nodes, ves_nodes, ves_ids;
   std::vector<CurveDev> curves(n_curves);
   std::map<int, int> kress_off;
   int kress_len = 0;
   int ws = 0, vs = 0;
-  for (int k = 0; k < n_curves; ++k) {
-    const int b = curve_offset[k], n = curve_offset[k + 1] - b;
-    CurveDev cd{b, n, curve_kind[k], 0, -1};
-    if (curve_kind[k] == STOKES_KIND_WALL) {
-      cd.dens_begin = ws;
-      for (int a = 0; a < n; ++a) {
-        slot32[ws + a] = b + a;
-        slot64[ws + a] = b + a;
-        node_dens[b + a] = ws + a;
-        wall_nodes.push_back(b + a);
+  for (int k = 0; k < n_inst; ++k) {
+    int wloc = 0, vloc = 0;
+    for (int cc = inst_curve_off[k]; cc < inst_curve_off[k + 1]; ++cc) {
+      const int b = curve_offset[cc], n = curve_offset[cc + 1] - b;
+      CurveDev cd{b, n, curve_kind[cc], 0, -1};
+      for (int a = 0; a < n; ++a) node_inst[b + a] = k;
+      if (curve_kind[cc] == STOKES_KIND_WALL) {
+        cd.dens_begin = ws;
+        for (int a = 0; a < n; ++a) {
+          slot32[size_t(inst[k].wb32) * kTileF32 + wloc + a] = b + a;
+          slot64[size_t(inst[k].wb64) * kTileF64 + wloc + a] = b + a;
+          node_dens[b + a] = ws + a;
+          wall_nodes.push_back(b + a);
+        }
+        ws += n;
+        wloc += n;
+      } else {
+        cd.dens_begin = vs;
+        const int s32 = inst[k].vb32 * kTileF32 + vloc, s64 = inst[k].vb64 * kTileF64 + vloc;
+        for (int a = 0; a < n; ++a) {
+          slot32[s32 + a] = b + a;
+          slot64[s64 + a] = b + a;
+          node_dens[b + a] = vs + a;
+          skip32[b + a] = make_int2(s32, s32 + n);
+          skip64[b + a] = make_int2(s64, s64 + n);
+          ves_nodes.push_back(b + a);
+        }
+        vs += n;
+        vloc += n;
+        if (!kress_off.count(n)) {
+          kress_off[n] = kress_len;
+          kress_len += n;
+        }
+        cd.kress_off = kress_off[n];
+        ves_ids.push_back(cc);
       }
-      ws += n;
-    } else {
-      cd.dens_begin = vs;
-      const int s32 = c->wall_slots + vs, s64 = c->wall_slots_f64 + vs;
-      for (int a = 0; a < n; ++a) {
-        slot32[s32 + a] = b + a;
-        slot64[s64 + a] = b + a;
-        node_dens[b + a] = vs + a;
-        skip32[b + a] = make_int2(s32, s32 + n);
-        ves_nodes.push_back(b + a);
-        skip64[b + a] = make_int2(s64, s64 + n);
-      }
-      vs += n;
-      if (!kress_off.count(n)) {
-        kress_off[n] = kress_len;
-        kress_len += n;
-      }
-      cd.kress_off = kress_off[n];
-      ves_ids.push_back(k);
+      curves[cc] = cd;
     }
-    curves[k] = cd;
   }
   c->n_wall_curves = n_curves - int(ves_ids.size());
   c->n_ves_curves = int(ves_ids.size());
+  c->inst = inst;
 
   // ---- device buffers ----
   CK(dalloc(c->d_x, N));
@@ -355,9 +446,10 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
   CK(upload(c->d_node_dens, node_dens, s));
   CK(upload(c->d_wall_nodes, wall_nodes, s));
   CK(upload(c->d_ves_nodes, ves_nodes, s));
-  CK(dalloc(c->d_self, n_ves));
   CK(upload(c->d_curves, curves, s));
   CK(upload(c->d_ves_curve_ids, ves_ids, s));
+  if (n_inst > 1) CK(upload(c->d_node_inst, node_inst, s));
+  CK(dalloc(c->d_self, n_ves));
   CK(dalloc(c->d_kress, kress_len));
   CK(dalloc(c->d_src_pos32, slot32.size()));
   CK(dalloc(c->d_src_val32, slot32.size()));
@@ -383,6 +475,21 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
   return STOKES_OK;
 }
 
+}  // namespace stokes
+
+extern "C" {
+
+int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
+                    const int32_t *curve_kind, const double *nodes, const double *weights,
+                    const double *normals, const double *curvature, double period, double mu,
+                    void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  const int inst_off[2] = {0, n_curves};
+  return set_geometry(c, 1, inst_off, &period, n_curves, curve_offset, curve_kind, nodes, weights,
+                      normals, curvature, mu, as_stream(stream));
+}
+
 int stokes_sum_eval(stokes_ctx *c, int precision, const double *slp, const double *dlp,
                     double jump, double *out, void *stream) {
   if (!c) return STOKES_ERR_ARG;
@@ -403,6 +510,8 @@ int stokes_sum_eval_targets(stokes_ctx *c, int precision, const double *slp, con
   if (n_targets == 0) return STOKES_OK;
   if (!targets || !out || !aligned16(targets) || !aligned16(out))
     return fail(c, STOKES_ERR_ARG, "targets and out_velocity must be 16-byte aligned device pointers");
+  if (c->n_inst > 1)
+    return fail(c, STOKES_ERR_ARG, "free-point evaluation needs a single-instance geometry");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
   int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
@@ -451,6 +560,8 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
     return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
   if (splits < 0) return fail(c, STOKES_ERR_ARG, "source_splits < 0");
+  if (c->n_inst > 1)
+    return fail(c, STOKES_ERR_ARG, "batched geometry: use stokes_batch_set_shape");
   if (targets_per_thread != 0 && targets_per_thread != 1 && targets_per_thread != 2 &&
       targets_per_thread != 4)
     return fail(c, STOKES_ERR_ARG, "targets_per_thread must be 0, 1, 2 or 4");
@@ -504,8 +615,201 @@ int stokes_last_timing(stokes_ctx *c, double *ms) {
 int stokes_pair_count(const stokes_ctx *c, int n_targets, double *pairs) {
   if (!c || !pairs) return STOKES_ERR_ARG;
   if (!c->have_geom) return STOKES_ERR_NO_GEOM;
+  const double img = c->period != 0.0 ? 3.0 : 1.0;
+  if (c->n_inst > 1) {
+    double p = 0.0;
+    for (const auto &I : c->inst) p += img * double(I.N) * double(I.N);
+    *pairs = p;
+    return STOKES_OK;
+  }
   const double nt = n_targets > 0 ? double(n_targets) : double(c->N);
-  *pairs = (c->period != 0.0 ? 3.0 : 1.0) * nt * double(c->N);
+  *pairs = img * nt * double(c->N);
+  return STOKES_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched instances
+// ---------------------------------------------------------------------------
+namespace {
+
+// Item table of one precision: every instance's (target block x source split) items, with the
+// split count chosen so that an item costs about total / (resident blocks x items_per_slot)
+// target-tile evaluations; items sorted by cost, largest first, for the work counter.
+int build_items(stokes_ctx *c, int precision, size_t *partial_elems) {
+  const bool f32 = precision == STOKES_FP32_KAHAN;
+  const long B = f32 ? long(kThreadsF32) * c->tpt_f32 : long(kThreadsF64);
+  const long slots = long(pair_batch_blocks_per_sm(c, precision)) * std::max(c->num_sms, 1);
+  const int ips = f32 ? c->batch_ips32 : c->batch_ips64;
+  double total = 0.0;
+  for (const auto &I : c->inst) {
+    const long T = f32 ? I.nw32 + I.nv32 : I.nw64 + I.nv64;
+    total += double((I.N + B - 1) / B) * double(B) * double(T);
+  }
+  const double target = std::max(1.0, total / double(slots * std::max(ips, 1)));
+  const long tps_goal = std::max(1L, long(target / double(B)));
+  std::vector<ItemDesc> items;
+  long long off = 0;
+  for (auto &I : c->inst) {
+    const int T = f32 ? I.nw32 + I.nv32 : I.nw64 + I.nv64;
+    int splits = int(std::min<long>(T, std::max<long>(1, (T + tps_goal - 1) / tps_goal)));
+    const int tps = (T + splits - 1) / splits;
+    splits = (T + tps - 1) / tps;
+    (f32 ? I.splits32 : I.splits64) = splits;
+    (f32 ? I.part_off32 : I.part_off64) = off;
+    for (int t0 = 0; t0 < I.N; t0 += int(B)) {
+      for (int k = 0; k < splits; ++k) {
+        ItemDesc it{};
+        it.tgt_begin = I.node_begin + t0;
+        it.tgt_count = int(std::min<long>(B, I.N - t0));
+        it.vt_begin = k * tps;
+        it.vt_end = std::min(T, (k + 1) * tps);
+        it.wb = f32 ? I.wb32 : I.wb64;
+        it.nw = f32 ? I.nw32 : I.nw64;
+        it.vb = f32 ? I.vb32 : I.vb64;
+        it.part_off = off + (long long)k * I.N - I.node_begin;
+        it.period = I.period;
+        items.push_back(it);
+      }
+    }
+    off += (long long)splits * I.N;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const ItemDesc &x, const ItemDesc &y) {
+    return (long long)x.tgt_count * (x.vt_end - x.vt_begin) >
+           (long long)y.tgt_count * (y.vt_end - y.vt_begin);
+  });
+  ItemDesc *&dst = f32 ? c->d_items32 : c->d_items64;
+  dfree(dst);
+  CK(upload(dst, items, c->own_stream));
+  (f32 ? c->n_items32 : c->n_items64) = int(items.size());
+  *partial_elems = size_t(off);
+  return STOKES_OK;
+}
+
+int build_batch_tables(stokes_ctx *c) {
+  size_t p32 = 0, p64 = 0;
+  int st = build_items(c, STOKES_FP32_KAHAN, &p32);
+  if (st) return st;
+  st = build_items(c, STOKES_FP64, &p64);
+  if (st) return st;
+  dfree(c->d_inst);
+  CK(upload(c->d_inst, c->inst, c->own_stream));
+  if (!c->d_counter) CK(dalloc(c->d_counter, 1));
+  CK(cudaStreamSynchronize(c->own_stream));
+  st = ensure_partial(c, std::max(p32, p64));
+  if (st) return st;
+  for (auto &g : c->graph_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return STOKES_OK;
+}
+
+int capture_batch_graph(stokes_ctx *c, int precision, double jump) {
+  const int k = precision == STOKES_FP32_KAHAN ? 1 : 0;
+  if (c->graph_exec[k] && c->graph_jump[k] == jump) return STOKES_OK;
+  if (c->graph_exec[k]) {
+    cudaGraphExecDestroy(c->graph_exec[k]);
+    c->graph_exec[k] = nullptr;
+  }
+  if (!c->d_b_out) {
+    CK(dalloc(c->d_b_slp, size_t(2) * std::max(c->n_ves_nodes, 1)));
+    CK(dalloc(c->d_b_dlp, size_t(2) * std::max(c->n_wall_nodes, 1)));
+    CK(dalloc(c->d_b_out, size_t(2) * c->N));
+  }
+  const bool prof = c->profiling;
+  c->profiling = false;  // events of the timing API stay outside the graph
+  cudaStream_t s = c->own_stream;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int st = run_batch(c, precision, c->d_b_slp, c->d_b_dlp, jump, c->d_b_out, s);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  c->profiling = prof;
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&c->graph_exec[k], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaGraphInstantiate");
+  c->graph_jump[k] = jump;
+  return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_batch_set(stokes_ctx *c, int n_inst, const int32_t *inst_curve_offset, int n_curves,
+                     const int32_t *curve_offset, const int32_t *curve_kind, const double *nodes,
+                     const double *weights, const double *normals, const double *curvature,
+                     const double *periods, double mu, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  if (n_inst < 1 || !inst_curve_offset || !periods)
+    return fail(c, STOKES_ERR_ARG, "need n_inst >= 1 and host inst_curve_offset / periods");
+  CK(cudaSetDevice(c->device));
+  int st = set_geometry(c, n_inst, inst_curve_offset, periods, n_curves, curve_offset, curve_kind,
+                        nodes, weights, normals, curvature, mu, as_stream(stream));
+  if (st) return st;
+  if (n_inst == 1) return STOKES_OK;
+  return build_batch_tables(c);
+}
+
+int stokes_batch_set_shape(stokes_ctx *c, int precision, int targets_per_thread,
+                           int items_per_slot) {
+  if (!c) return STOKES_ERR_ARG;
+  if (!c->have_geom || c->n_inst < 2) return fail(c, STOKES_ERR_NO_GEOM, "no batched geometry set");
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
+  if (targets_per_thread != 0 && targets_per_thread != 1 && targets_per_thread != 2 &&
+      targets_per_thread != 4)
+    return fail(c, STOKES_ERR_ARG, "targets_per_thread must be 0, 1, 2 or 4");
+  if (items_per_slot < 0 || items_per_slot > 64)
+    return fail(c, STOKES_ERR_ARG, "items_per_slot must be in [0, 64]");
+  CK(cudaSetDevice(c->device));
+  if (precision == STOKES_FP32_KAHAN) {
+    if (targets_per_thread) c->tpt_f32 = targets_per_thread;
+    if (items_per_slot) c->batch_ips32 = items_per_slot;
+  } else if (items_per_slot) {
+    c->batch_ips64 = items_per_slot;
+  }
+  return build_batch_tables(c);
+}
+
+int stokes_batch_info(const stokes_ctx *c, int precision, int *n_items, int *blocks,
+                      int *targets_per_thread, int *items_per_slot) {
+  if (!c || !n_items || !blocks || !targets_per_thread || !items_per_slot) return STOKES_ERR_ARG;
+  if (!c->have_geom || c->n_inst < 2) return STOKES_ERR_NO_GEOM;
+  const bool f32 = precision == STOKES_FP32_KAHAN;
+  *n_items = f32 ? c->n_items32 : c->n_items64;
+  *blocks = pair_batch_blocks_per_sm(const_cast<stokes_ctx *>(c), precision) * std::max(c->num_sms, 1);
+  *targets_per_thread = f32 ? c->tpt_f32 : 1;
+  *items_per_slot = f32 ? c->batch_ips32 : c->batch_ips64;
+  return STOKES_OK;
+}
+
+int stokes_batch_eval(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                      double jump, double *out, int use_graph, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  int st = check_density_args(c, precision, slp, dlp);
+  if (st) return st;
+  if (c->n_inst < 2) return fail(c, STOKES_ERR_NO_GEOM, "no batched geometry set");
+  if (!out || !aligned16(out)) return fail(c, STOKES_ERR_ARG, "out_velocity must be a 16-byte aligned device pointer");
+  if (!isfinite(jump)) return fail(c, STOKES_ERR_ARG, "jump must be finite");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  if (!use_graph) return run_batch(c, precision, slp, dlp, jump, out, s);
+  st = capture_batch_graph(c, precision, jump);
+  if (st) return st;
+  if (c->n_ves_nodes)
+    CK(cudaMemcpyAsync(c->d_b_slp, slp, sizeof(double) * 2 * c->n_ves_nodes, cudaMemcpyDeviceToDevice, s));
+  if (c->n_wall_nodes)
+    CK(cudaMemcpyAsync(c->d_b_dlp, dlp, sizeof(double) * 2 * c->n_wall_nodes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGraphLaunch(c->graph_exec[precision == STOKES_FP32_KAHAN ? 1 : 0], s));
+  CK(cudaMemcpyAsync(out, c->d_b_out, sizeof(double) * 2 * c->N, cudaMemcpyDeviceToDevice, s));
   return STOKES_OK;
 }
 

@@ -38,6 +38,19 @@ struct CurveDev {
   int kress_off;    // offset of the curve's Kress table (vesicles), -1 for walls
 };
 
+// One unit of pair-kernel work: a block of consecutive targets of one instance against a
+// contiguous range of that instance's source tiles.  An instance lists its wall tiles, then
+// its vesicle tiles ("virtual" tile index vt); vt < nw maps to global tile wb + vt (stresslet
+// tiles), otherwise to vb + vt - nw (stokeslet tiles).
+struct ItemDesc {
+  int tgt_begin, tgt_count;
+  int vt_begin, vt_end;
+  int wb, nw, vb;
+  int pad_;
+  long long part_off;       // this split's partial of target i is partial[part_off + i]
+  double period;
+};
+
 // Arguments of the pair kernels (both precisions).
 struct PairArgs {
   // targets
@@ -45,18 +58,36 @@ struct PairArgs {
   const double2 *tgt;       // FP64 target points
   const int2 *tgt_skip;     // per target: source-slot range [x, y) skipped at image 0 (or NULL)
   double period;
-  // sources (slot order: wall tiles then vesicle tiles, each padded to the tile length)
+  // single-instance grid launch: blockIdx.x = target block, blockIdx.y = split
   int n_tiles;
   int n_wall_tiles;
   int tiles_per_split;
+  // persistent launch over an item table (batched instances)
+  const ItemDesc *items;
+  int n_items;
+  int *counter;             // zeroed before the launch; blocks take items in table order
+  // sources (slot order: wall tiles of every instance, then vesicle tiles of every instance,
+  // each instance's run padded to the tile length)
   const void *src_pos;      // FP32: float4 (x_hi, y_hi, x_lo, y_lo); FP64: double2 (x, y)
   const void *src_val;      // FP32: float4 (q1, q2, p1|n1, p2|n2); FP64: double4_32a
   // outputs
-  double2 *partial;         // [split][n_targets]
+  double2 *partial;
   unsigned *status;
 };
 
+// Per instance of a batched geometry (host and device copies).
+struct InstDev {
+  int node_begin, N;
+  int wb32, nw32, vb32, nv32;   // wall / vesicle tile runs, FP32 tiles
+  int wb64, nw64, vb64, nv64;   // the same in FP64 tiles
+  int splits32, splits64;
+  long long part_off32, part_off64;  // first partial of the instance
+  double period;
+};
+
 }  // namespace stokes
+
+using InstHost = stokes::InstDev;
 
 struct stokes_ctx {
   int device = 0;
@@ -110,11 +141,32 @@ struct stokes_ctx {
 
   int num_sms = 0;
 
+  // batched instances (stokes_batch_set); n_inst = 1 for stokes_geom_set
+  int n_inst = 1;
+  std::vector<InstHost> inst;
+  stokes::InstDev *d_inst = nullptr;
+  int *d_node_inst = nullptr;            // [N] instance of each node
+  stokes::ItemDesc *d_items32 = nullptr, *d_items64 = nullptr;
+  int n_items32 = 0, n_items64 = 0;
+  int *d_counter = nullptr;              // work counter of the persistent launch
+  int batch_ips32 = 4, batch_ips64 = 4;  // items per resident block the tables aim for
+  // CUDA graphs of one batched evaluation, per precision (built on first use)
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  double graph_jump[2] = {0.0, 0.0};
+  double *d_b_slp = nullptr, *d_b_dlp = nullptr, *d_b_out = nullptr;  // graph staging
+
   // phase timing (stokes_set_profiling)
   bool profiling = false;
   bool timed = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+
+namespace stokes {
+int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const double *periods,
+                 int n_curves, const int32_t *curve_offset, const int32_t *curve_kind,
+                 const double *nodes, const double *weights, const double *normals,
+                 const double *curvature, double mu, cudaStream_t s);
+}  // namespace stokes
 
 // Launchers implemented in the .cu files.
 namespace stokes {
@@ -128,4 +180,9 @@ cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, co
                                 double jump, double2 *out, cudaStream_t s);
 cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2 *out,
                                cudaStream_t s);
+cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int slots, cudaStream_t s);
+cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp, double jump,
+                                double2 *out, cudaStream_t s);
+int pair_blocks_per_sm(stokes_ctx *c, int precision);
+int pair_batch_blocks_per_sm(stokes_ctx *c, int precision);
 }  // namespace stokes

@@ -187,7 +187,7 @@ def _shape_xy(theta, a, b, pert):
     return p, p1, p2
 
 
-def _area(a, b, pert, m=2048):
+def _area(a, b, pert, m=128):
     th = TWO_PI * np.arange(m) / m
     p, p1, _ = _shape_xy(th, a, b, pert)
     return 0.5 * np.mean(p[:, 0] * p1[:, 1] - p[:, 1] * p1[:, 0]) * TWO_PI
@@ -263,8 +263,12 @@ def place_vesicles(rng, walls, modes, period, count, n_v, area, gap_factor=5.0,
     """
     tree = _wall_tree(walls, period)
     h_wall = max(c.spacing() for c in walls)
-    placed = []  # (curve, center, bounding radius, h)
-    for _ in range(count):
+    placed = []
+    cen = np.zeros((count, 2))
+    bnd = np.zeros(count)
+    hs = np.zeros(count)
+    shifts = np.array([-period, 0.0, period])
+    for v in range(count):
         for _attempt in range(max_attempts):
             a, b, pert = vesicle_shape(rng, n_v, area)
             ang = rng.uniform(0, TWO_PI)
@@ -285,28 +289,29 @@ def place_vesicles(rng, walls, modes, period, count, n_v, area, gap_factor=5.0,
             dmin, _ = tree.query(cv.nodes, k=1)
             if np.min(dmin) < gap:
                 continue
-            ok = True
             bound = np.max(np.hypot(*(cv.nodes - np.array([xc, yc])).T))
-            for (cu, cc, cb, ch) in placed:
-                g2 = gap_factor * max(h_v, ch)
-                for m in (-1, 0, 1):
-                    dx = xc - (cc[0] + m * period)
-                    dy = yc - cc[1]
-                    if math.hypot(dx, dy) > bound + cb + g2:
-                        continue
-                    other = cu.nodes + np.array([m * period, 0.0])
-                    dd = cv.nodes[:, None, :] - other[None, :, :]
-                    if np.min(np.einsum("ijk,ijk->ij", dd, dd)) < g2 * g2:
-                        ok = False
-                        break
-                if not ok:
-                    break
+            ok = True
+            if v:
+                g2 = gap_factor * np.maximum(h_v, hs[:v])
+                dx = xc - (cen[:v, 0][:, None] + shifts[None, :])
+                dy = (yc - cen[:v, 1])[:, None]
+                jj, mm = np.nonzero(np.hypot(dx, dy) <= (bound + bnd[:v] + g2)[:, None])
+                if jj.size:
+                    from scipy.spatial import cKDTree
+                    others = np.concatenate([placed[j].nodes + np.array([shifts[m], 0.0])
+                                             for j, m in zip(jj, mm)])
+                    thr = np.concatenate([np.full(placed[j].n, g2[j]) for j in jj])
+                    dist, _ = cKDTree(cv.nodes).query(others, k=1)
+                    ok = bool(np.all(dist >= thr))
             if ok:
-                placed.append((cv, (xc, yc), bound, h_v))
+                placed.append(cv)
+                cen[v] = (xc, yc)
+                bnd[v] = bound
+                hs[v] = h_v
                 break
         else:
             raise RuntimeError("vesicle placement failed; volume fraction too high")
-    return [p[0] for p in placed]
+    return placed
 
 
 # --------------------------------------------------------------------------
@@ -355,12 +360,13 @@ WORKLOADS = {
 WORKLOAD_SEED = {"small_n1280": SEED_BASE + 0, "mid_n16k": SEED_BASE + 1, "paper_n128k": SEED_BASE + 2}
 
 
-def channel(n_w, modes, n_ves, n_v, area, seed, period=TWO_PI, mu=1.0) -> Geometry:
+def channel(n_w, modes, n_ves, n_v, area, seed, period=TWO_PI, mu=1.0, gap_factor=5.0) -> Geometry:
     ss = np.random.SeedSequence(seed)
     s_geo, _, _ = ss.spawn(3)
     rng = np.random.Generator(np.random.PCG64(s_geo))
     lower, upper = wall_curves(n_w, modes, period)
-    ves = place_vesicles(rng, [lower, upper], modes, period, n_ves, n_v, area) if n_ves else []
+    ves = place_vesicles(rng, [lower, upper], modes, period, n_ves, n_v, area,
+                         gap_factor=gap_factor) if n_ves else []
     return Geometry([lower, upper] + ves, period, mu,
                     dict(n_w=n_w, modes=modes, n_ves=n_ves, n_v=n_v, area=area, seed=seed))
 
@@ -381,29 +387,45 @@ def workload(name: str, seed: int | None = None):
     return _CACHE[key]
 
 
-def ensemble(count: int = 64, seed: int = SEED_BASE + 3, size_scale: float = 1.0):
+ENSEMBLE_GAP = 2.0  # node gap >= 2h: 5h with 32-node vesicles at 15% fill nears jamming
+
+
+def _ensemble_member(args):
+    n_w, modes, nv, n_v, area, s = args
+    g = channel(n_w, modes, nv, n_v, area, s, gap_factor=ENSEMBLE_GAP)
+    slp, dlp = densities(g, s)
+    return g, slp, dlp
+
+
+def ensemble(count: int = 64, seed: int = SEED_BASE + 3, size_scale: float = 1.0,
+             workers: int = 0):
     """Independent channel instances of mixed sizes (batched workload).
 
     Wall nodes per wall from {1024, 2048, 4096, 8192}, vesicle counts
     U[10, 400], nodes per vesicle from {32, 64, 128, 256}, volume fraction
     U[0.05, 0.15]; walls alternate between the small and large shapes.
-    ``size_scale`` < 1 shrinks node and vesicle counts for quick tests.
+    ``size_scale`` < 1 shrinks node and vesicle counts for quick tests.  The
+    instances are independent, so ``workers`` > 1 builds them in a process pool
+    (spawned, so it is safe after CUDA has been initialised); the result does not
+    depend on ``workers``.
     """
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
-    out = []
+    jobs = []
     for i in range(count):
         n_w = int(rng.choice([1024, 2048, 4096, 8192]))
         nv = int(rng.integers(10, 401))
         n_v = int(rng.choice([32, 64, 128, 256]))
         phi = rng.uniform(0.05, 0.15)
+        area = phi * CELL_AREA / nv  # vesicle size of the full-size instance
         if size_scale != 1.0:
             n_w = max(64, int(n_w * size_scale) // 32 * 32)
             nv = max(1, int(nv * size_scale))
             n_v = max(16, int(n_v * size_scale) // 2 * 2)
         modes = WALL_SHAPE_SMALL if i % 2 == 0 else WALL_SHAPE_LARGE
-        area = phi * CELL_AREA / nv
-        s = int(rng.integers(0, 2**31))
-        g = channel(n_w, modes, nv, n_v, area, s)
-        slp, dlp = densities(g, s)
-        out.append((g, slp, dlp))
-    return out
+        jobs.append((n_w, modes, nv, n_v, area, int(rng.integers(0, 2**31))))
+    if workers and workers > 1 and count > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_ensemble_member, jobs))
+    return [_ensemble_member(j) for j in jobs]
