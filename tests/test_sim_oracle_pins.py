@@ -1,0 +1,240 @@
+"""Pins of the channel-response and time-step oracle (oracle/sim_oracle.py).
+
+Channel response: the traction kernels are the tractions of their velocity/pressure pairs
+(finite differences), the exact Poiseuille flow is reproduced (Sec. 5.1 test), and the
+total flow of vesicle forces plus response is periodic in velocity and traction with the
+prescribed pressure drop.  Step: spectral differentiation, area correction, the
+arc-length correction bound of Theorem A.2, reparameterization, and the solved system.
+"""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from paper_1510_05616_gb300 import inputs as I
+
+warnings.filterwarnings("ignore", category=RuntimeWarning)
+PI = math.pi
+MU = 0.7
+D = 2 * PI
+
+
+@pytest.fixture(scope="module")
+def S():
+    from oracle import sim_oracle
+    return sim_oracle
+
+
+def _pressure_slp(x, y):
+    r = x - y
+    return r / (2 * PI * (r @ r))
+
+
+def _pressure_dlp(x, y, ny):
+    r = x - y
+    rr = r @ r
+    return (MU / PI) * (-ny / rr + 2 * (r @ ny) * r / rr ** 2)
+
+
+def _fd_traction(ufun, pfun, x, n, h=1e-5):
+    g = np.zeros((2, 2))
+    for j in range(2):
+        e = np.zeros(2)
+        e[j] = h
+        g[:, j] = (ufun(x + e) - ufun(x - e)) / (2 * h)
+    return -pfun(x) * n + MU * ((g + g.T) @ n)
+
+
+def test_traction_kernels_match_finite_differences(S):
+    """Eq. (K) and Eq. (T) against sigma(u, p) n of Eq. (Tup) with (S, Q) and (D, P)."""
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        x, y = rng.normal(size=2), rng.normal(size=2)
+        nx = rng.normal(size=2)
+        nx /= np.linalg.norm(nx)
+        ny = rng.normal(size=2)
+        ny /= np.linalg.norm(ny)
+        for F in np.eye(2):
+            fdK = _fd_traction(lambda z: S.stokeslet(z, y, MU) @ F, lambda z: _pressure_slp(z, y) @ F, x, nx)
+            assert np.allclose(S.slp_traction(x, y, nx) @ F, fdK, rtol=1e-7, atol=1e-8)
+            fdT = _fd_traction(lambda z: S.stresslet(z, y, ny) @ F, lambda z: _pressure_dlp(z, y, ny) @ F, x, nx)
+            assert np.allclose(S.dlp_traction(x, y, nx, ny, MU) @ F, fdT, rtol=1e-6, atol=1e-7)
+
+
+def _poiseuille(p_drive):
+    """u = (-p_drive/(2 mu d) y^2, 0), p = -p_drive x / d: Stokes, pressure drop p_drive per period."""
+    return lambda p: np.stack([-(p_drive / (2 * MU * D)) * p[:, 1] ** 2, 0 * p[:, 1]], 1)
+
+
+PTS = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0], [2.0, 0.5], [5.0, -0.4]])
+
+
+@pytest.mark.parametrize("n_w", [96, 160])
+def test_poiseuille_exact_lstsq(S, n_w):
+    """The discretised extended system reproduces the exact flow to round-off (Sec. 5.1)."""
+    lo, up = I.wall_curves(n_w, I.WALL_SHAPE_SMALL)
+    W = S.Walls(lo, up, D, MU, K=32, M=128)
+    pd = 2 * MU * D * 0.2
+    ue = _poiseuille(pd)
+    _, g = S.empty_channel_rhs(W, pd)
+    tau, c = W.solve_lstsq(ue(W.x).reshape(-1), g)
+    err = np.abs(W.velocity(tau, c, PTS) - ue(PTS)).max() / np.abs(ue(W.x)).max()
+    assert err < 1e-11
+
+
+def test_poiseuille_block_solve_within_paper_accuracy(S):
+    """The block elimination with a pseudo-inverse of the Schur complement (Sec. 4.1) is
+    limited by the truncation of S's small singular values: 1e-6-level, as the paper's
+    solver errors (Sec. 5, fast direct solver table) are."""
+    lo, up = I.wall_curves(128, I.WALL_SHAPE_SMALL)
+    W = S.Walls(lo, up, D, MU, K=32, M=128)
+    pd = 2 * MU * D * 0.2
+    ue = _poiseuille(pd)
+    _, g = S.empty_channel_rhs(W, pd)
+    tau, c = W.solve(ue(W.x).reshape(-1), g)
+    err = np.abs(W.velocity(tau, c, PTS) - ue(PTS)).max() / np.abs(ue(W.x)).max()
+    assert err < 5e-6
+
+
+def test_pressure_drive_direction(S):
+    """With no vesicles and zero wall velocity, p_drive > 0 drives flow towards +x."""
+    lo, up = I.wall_curves(96, I.WALL_SHAPE_SMALL)
+    W = S.Walls(lo, up, D, MU, K=24, M=96)
+    v, g = S.empty_channel_rhs(W, 1.0)
+    tau, c = W.solve_lstsq(v, g)
+    u = W.velocity(tau, c, np.array([[1.0, 0.0], [4.0, 0.1]]))
+    assert np.all(u[:, 0] > 0)
+
+
+def _ves_case(seed=3, n_w=96, n_ves=3, n_v=16):
+    g = I.channel(n_w, I.WALL_SHAPE_SMALL, n_ves, n_v, 0.05, seed)
+    slp, _ = I.densities(g, seed)
+    walls = [c for c in g.curves if c.kind == I.KIND_DLP]
+    ves = [c for c in g.curves if c.kind == I.KIND_SLP]
+    return walls, ves, slp
+
+
+def test_total_flow_is_periodic_with_vesicles(S):
+    """u = S^near f + u_resp satisfies u_R = u_L and T_R - T_L = p_drive n (Eq. (vesU)-(vesgT)),
+    and vanishes on the walls' interior limit by construction."""
+    walls, ves, f = _ves_case()
+    W = S.Walls(walls[0], walls[1], D, MU, K=24, M=96)
+    xv = np.vstack([c.nodes for c in ves])
+    wv = np.concatenate([c.weights for c in ves])
+    pd = 0.8
+    v, g = S.vesicle_rhs(W, xv, wv, f, pd)
+    tau, c = W.solve_lstsq(v, g)
+    q = f * wv[:, None]
+
+    def total_u(p):
+        u = W.velocity(tau, c, p)
+        for m in (-1, 0, 1):
+            y = xv + np.array([m * D, 0.0])
+            u += np.einsum("pjik,jk->pi", S.stokeslet(p[:, None], y[None], MU), q)
+        return u
+
+    def total_t(p):
+        t = W.traction(tau, c, p, W.side_n)
+        for m in (-1, 0, 1):
+            y = xv + np.array([m * D, 0.0])
+            t += np.einsum("pjik,jk->pi", S.slp_traction(p[:, None], y[None], W.side_n), q)
+        return t
+
+    uR, uL = total_u(W.R), total_u(W.L)
+    scale = np.abs(uL).max()
+    assert np.abs(uR - uL).max() < 1e-9 * max(scale, 1.0)
+    tR, tL = total_t(W.R), total_t(W.L)
+    assert np.abs((tR - tL) - pd * W.side_n).max() < 1e-8 * max(np.abs(tL).max(), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# time step
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [8, 16, 64])
+def test_fourier_diff_exact_on_trig_polynomials(S, n):
+    a = 2 * PI * np.arange(n) / n
+    Dm = S.fourier_diff(n)
+    for k in range(1, n // 2):
+        assert np.abs(Dm @ np.sin(k * a) - k * np.cos(k * a)).max() < 1e-11 * n
+        assert np.abs(Dm @ np.cos(k * a) + k * np.sin(k * a)).max() < 1e-11 * n
+    assert np.abs(Dm @ np.ones(n)).max() < 1e-13
+
+
+def test_area_and_perimeter_of_ellipse(S):
+    c = I.closed_curve(128, 0.7, 0.3, (1.0, -0.5), 0.4)
+    assert abs(S.area(c.nodes) - PI * 0.7 * 0.3) < 1e-13
+    # Ramanujan-free check: perimeter from the generator's own fine quadrature
+    assert abs(S.perimeter(c.nodes) - I._perimeter(0.7, 0.3, (), m=4096)) < 1e-12
+
+
+def test_area_correction_restores_area(S):
+    c = I.closed_curve(64, 0.5, 0.3, (0.0, 0.0), 0.2, ((3, 0.01, 0.5),))
+    A0 = S.area(c.nodes)
+    rng = np.random.default_rng(1)
+    x = c.nodes * 1.003 + 1e-3 * rng.normal(size=c.nodes.shape) * 0
+    x = x + 2e-4 * np.stack([np.cos(3 * c.tparam), np.sin(2 * c.tparam)], 1)
+    xc = S.area_correct(x, A0)
+    assert abs(S.area(xc) - A0) < 1e-13 * A0
+    assert np.abs(xc - x).max() < 1e-2
+
+
+def test_reparametrize_keeps_curve_and_equalises_spacing(S):
+    c = I.closed_curve(64, 0.6, 0.25, (0.0, 0.0), 0.0, ((2, 0.03, 0.0), (5, 0.02, 1.0)))
+    x = c.nodes
+    # distort the parameterisation: nodes bunched by alpha -> alpha + 0.3 sin(alpha)
+    a = 2 * PI * np.arange(64) / 64
+    xb = S.fourier_interp(x, a + 0.3 * np.sin(a))
+    xr = S.reparametrize(xb)
+    sp = lambda z: np.hypot(*np.diff(np.vstack([z, z[:1]]), axis=0).T)
+    assert sp(xr).max() / sp(xr).min() < 1.05 < sp(xb).max() / sp(xb).min()
+    assert abs(S.area(xr) - S.area(x)) < 1e-6 * S.area(x)
+    assert abs(S.perimeter(xr) - S.perimeter(x)) < 1e-5 * S.perimeter(x)
+
+
+def _free_ellipse(n=32):
+    return [I.closed_curve(n, 0.3, 0.15, (0.0, 0.0), 0.3).nodes]
+
+
+def test_step_solution_satisfies_constraint_and_symmetry(S):
+    """The solved (u, sigma) meets x_s . u_s = (L0 - Lk)/(dt Lk); a centred, point-symmetric
+    ellipse in free space has zero mean velocity (no self-propulsion)."""
+    xs = _free_ellipse()
+    L0 = [S.perimeter(xs[0]) * 0.999]
+    A0 = [S.area(xs[0])]
+    sig = [np.zeros(32)]
+    dt = 1e-3
+    M, Sop, rhs2 = S.step_system(xs, dt, 1.0, 1.0, 0.0, L0)
+    out_x, out_s, u, sg, _ = S.step(xs, sig, L0, A0, dt, 1.0, 1.0, 0.0)
+    _, Ds, xsv = S.arclength_ops(xs[0])
+    cons = (xsv * (Ds @ u)).sum(1)
+    assert np.abs(cons - rhs2).max() < 1e-9 * np.abs(rhs2).max()
+    assert np.abs(u.mean(0)).max() < 1e-10 * np.abs(u).max()
+
+
+def test_arc_length_correction_bound(S):
+    """Theorem A.2: |L_k - L_0| / L_0 <= dt^2 C^2 / (2 - dt^2 C^2) with C = max |u_s|, while
+    the uncorrected constraint (x_s . u_s = 0) lets L drift further."""
+    xs = [I.closed_curve(32, 0.3, 0.12, (0.0, 0.0), 0.0).nodes]
+    L0 = [S.perimeter(xs[0])]
+    A0 = [S.area(xs[0])]
+    dt, steps = 2e-3, 12
+    x, sig, C, errs = xs, [np.zeros(32)], 0.0, []
+    for _ in range(steps):
+        x, sig, u, _, _ = S.step(x, sig, L0, A0, dt, 1.0, 1.0, 0.0)
+        _, Ds, _ = S.arclength_ops(x[0])
+        C = max(C, np.abs(np.hypot(*(Ds @ u).T)).max())
+        errs.append(abs(S.perimeter(x[0]) - L0[0]) / L0[0])
+    bound = dt * dt * C * C / (2 - dt * dt * C * C)
+    assert max(errs) <= bound * 1.05 + 1e-12
+
+
+def test_step_operator_equals_pinned_pair_oracle(S, oracle_mod):
+    """The step oracle's dense S^near_{gamma,gamma} (Kress blocks + images) applied to f equals
+    the C oracle's node sum on the vesicle-only geometry (itself pinned by Green's identity,
+    image tiling and reciprocity)."""
+    walls, ves, f = _ves_case(n_ves=4, n_v=16)
+    g = I.Geometry(ves, D, MU)
+    Sop = S.slp_operator([c.nodes for c in ves], D, MU)
+    ref = oracle_mod.sum_nodes(g, f, np.zeros((0, 2)))
+    assert np.abs((Sop @ f.reshape(-1)).reshape(-1, 2) - ref).max() < 1e-13 * np.abs(ref).max()
