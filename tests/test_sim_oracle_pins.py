@@ -234,6 +234,12 @@ def test_step_operator_equals_pinned_pair_oracle(S, oracle_mod):
     the C oracle's node sum on the vesicle-only geometry (itself pinned by Green's identity,
     image tiling and reciprocity)."""
     walls, ves, f = _ves_case(n_ves=4, n_v=16)
+    # the step works from nodes alone: give the C oracle the same spectral weights and normals
+    cs = []
+    for c in ves:
+        nr, w = S.curve_normals_weights(c.nodes)
+        cs.append(I.Curve(I.KIND_SLP, c.nodes, w, nr, c.curvature, c.tparam))
+    ves = cs
     g = I.Geometry(ves, D, MU)
     Sop = S.slp_operator([c.nodes for c in ves], D, MU)
     ref = oracle_mod.sum_nodes(g, f, np.zeros((0, 2)))
