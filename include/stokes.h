@@ -110,6 +110,16 @@ STOKES_API int stokes_geom_set(stokes_ctx *ctx, int n_curves, const int32_t *cur
                                const double *curvature, double period, double mu, void *stream);
 
 /*
+ * Replace the node data of the current geometry (same curves, same node counts): nodes,
+ * weights, normals (DEVICE, as in stokes_geom_set) and curvature (DEVICE, may be NULL when
+ * there is no wall).  Asynchronous on `stream`; no allocation, no re-planning.  Used by the
+ * time stepper after every position update.  A non-finite value is reported by the next
+ * stokes_sync.
+ */
+STOKES_API int stokes_geom_update(stokes_ctx *ctx, const double *nodes, const double *weights,
+                                  const double *normals, const double *curvature, void *stream);
+
+/*
  * Velocity at every node of the geometry, self terms included (the Nystrom operator).
  *   precision     stokes_precision
  *   slp_density   DEVICE double[N_ves][2]  vesicle force density f, rows in node order of the
@@ -243,6 +253,77 @@ STOKES_API int stokes_get_launch(const stokes_ctx *ctx, int precision, int *sour
 /* Nominal pair-image evaluations of one stokes_sum_eval: 3 N_t N_s (1 N_t N_s when period
  * is 0), counting skipped and self pairs.  Written to *pairs. */
 STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *pairs);
+
+/* ===========================================================================================
+ * Channel response and semi-implicit vesicle time stepping (built on the sums above).
+ *
+ * A stokes_sim holds one periodic channel (walls U, D) and V vesicles of n nodes each.
+ *
+ * Channel response (Sec. 2.2-2.3 and the three-step procedure of Sec. 3.1): the response
+ * u_resp = D^near tau + sum_m c_m S(., y_m) (Eq. (urep)) to vesicle forces f and the pressure
+ * drop p_drive per period (flow towards +x for p_drive > 0; g_T = p_drive (1, 0)).  The blocks
+ * of the extended linear system [A B; C Q] (Eq. (BIEU), (BIED), (BIEgu), (BIEgT)) are
+ * assembled in FP64 at stokes_sim_set_walls; A is LU-factored, S = Q - C A^-1 B is
+ * pseudo-inverted (SVD, singular values below 1e-13 sigma_max dropped), and a solve is the
+ * block elimination c = S^+ (g - C A^-1 v), tau = A^-1 v - A^-1 B c (Sec. 4.1, with LU in
+ * place of the fast direct solver).  Side points: K Gauss-Legendre nodes across the inlet
+ * x = 0 and their copies at x = d; proxies: M >= 2K points on a circle of radius R_p about
+ * (d/2, 0).  Dense storage: (4 N_w)^2 doubles for A (N_w nodes per wall).
+ *
+ * Time step (Algorithm 1 steps 2-9): forces f_b = -kappa_B x_ssss, f = f_b + (sigma x_s)_s;
+ * u_resp of f; GMRES (FP64, right preconditioned by each vesicle's self interaction) on
+ * Eq. (tsteplinsys) with the arc-length correction Eq. (ALC):
+ *   [I + dt kappa_B S d_ssss, -S d_s(x_s .); x_s . d_s, 0] [u; sigma] = [S f_b + u_resp; (L0-Lk)/(dt Lk)]
+ * where S is the single layer of all vesicles with +-d images and Kress self terms
+ * (stokes_sum_eval in the requested precision); then x += dt u, area correction (App. B) and
+ * reparameterization (App. C, Algorithm 2).  d/ds = |x_alpha|^-1 d/d alpha by Fourier
+ * differentiation.  The unknown vector, guesses and solutions are laid out per vesicle as
+ * [u_x (n), u_y (n), sigma (n)], vesicle after vesicle (3 n V doubles).
+ * Host pointers are used for set-up and state transfer; f, u_resp, guesses are DEVICE
+ * pointers.  Calls are synchronous.  Errors as in the rest of this header;
+ * STOKES_ERR_NOT_CONVERGED when GMRES reaches max_iter above tol.
+ * ===========================================================================================
+ */
+typedef struct stokes_sim stokes_sim;
+
+typedef struct {
+    int iterations;      /* GMRES iterations (matvecs inside the Krylov loop)            */
+    double residual;     /* final relative residual |b - A z| / |b|                     */
+    double setup_ms;     /* forces, channel response, right-hand side, preconditioner   */
+    double gmres_ms;     /* Krylov solve                                                 */
+    double total_ms;     /* whole step including the position update                    */
+} stokes_step_stats;
+
+STOKES_API int stokes_sim_create(int device, stokes_sim **out);
+STOKES_API int stokes_sim_destroy(stokes_sim *sim);
+STOKES_API int stokes_sim_last_error(const stokes_sim *sim, char *buf, size_t len);
+/* Walls: HOST arrays of 2 n_per_wall nodes (lower wall then upper wall, each starting on the
+ * inlet x = 0), weights, normals (out of the fluid), curvature; period > 0, mu > 0. */
+STOKES_API int stokes_sim_set_walls(stokes_sim *sim, int n_per_wall, const double *nodes,
+                                    const double *weights, const double *normals,
+                                    const double *curvature, double period, double mu, int K,
+                                    int M, double proxy_radius);
+/* Vesicles: HOST positions (V n x 2, counter-clockwise, equispaced parameter), n even in
+ * [8, 256]; kappa_B, mu and period (0 = no images, else equal to the walls'). */
+STOKES_API int stokes_sim_set_vesicles(stokes_sim *sim, int V, int n, const double *x,
+                                       double kappa_b, double mu, double period);
+/* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
+STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
+                                           double *u_resp);
+/* Flow of the channel alone with wall velocity data v_walls (DEVICE, 2 N_w x 2, or NULL = 0),
+ * g_u = 0, g_T = p_drive n, at n_targets DEVICE points. */
+STOKES_API int stokes_sim_empty_channel(stokes_sim *sim, double p_drive, const double *v_walls,
+                                        int n_targets, const double *targets, double *u_out);
+/* One time step; guess = DEVICE initial GMRES iterate (3 n V, layout above) or NULL (zero). */
+STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive,
+                                      const double *guess, double tol, int max_iter,
+                                      int precision, stokes_step_stats *stats);
+/* State transfer (HOST, any may be NULL): positions (V n x 2), tension (V n), and the last
+ * step's solution [u_x, u_y, sigma] per vesicle (3 n V). */
+STOKES_API int stokes_sim_get_state(stokes_sim *sim, double *x, double *sigma, double *solution);
+STOKES_API int stokes_sim_set_state(stokes_sim *sim, const double *x, const double *sigma);
+STOKES_API int stokes_sim_sizes(const stokes_sim *sim, int *n_vesicles, int *nodes_per_vesicle,
+                                int *wall_nodes);
 
 #ifdef __cplusplus
 }

@@ -47,6 +47,7 @@ _SIGNATURES = {
     "stokes_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_geom_set": [_vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _c_double, _c_double, _vp],
     "stokes_sum_eval": [_vp, _c_int, _vp, _vp, _c_double, _vp, _vp],
+    "stokes_geom_update": [_vp, _vp, _vp, _vp, _vp, _vp],
     "stokes_sum_eval_targets": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sum_eval_host": [_vp, _c_int, _vp, _vp, _c_double, _vp],
     "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
@@ -62,6 +63,18 @@ _SIGNATURES = {
     "stokes_batch_eval": [_vp, _c_int, _vp, _vp, _c_double, _vp, _c_int, _vp],
     "stokes_batch_set_shape": [_vp, _c_int, _c_int, _c_int],
     "stokes_batch_info": [_vp, _c_int] + [ctypes.POINTER(_c_int)] * 4,
+    "stokes_sim_create": [_c_int, ctypes.POINTER(_vp)],
+    "stokes_sim_destroy": [_vp],
+    "stokes_sim_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "stokes_sim_set_walls": [_vp, _c_int, _vp, _vp, _vp, _vp, _c_double, _c_double, _c_int, _c_int,
+                             _c_double],
+    "stokes_sim_set_vesicles": [_vp, _c_int, _c_int, _vp, _c_double, _c_double, _c_double],
+    "stokes_sim_channel_response": [_vp, _vp, _c_double, _vp],
+    "stokes_sim_empty_channel": [_vp, _c_double, _vp, _c_int, _vp, _vp],
+    "vesicle_step_warmstart": [_vp, _c_double, _c_double, _vp, _c_double, _c_int, _c_int, _vp],
+    "stokes_sim_get_state": [_vp, _vp, _vp, _vp],
+    "stokes_sim_set_state": [_vp, _vp, _vp],
+    "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
 }
 
@@ -144,6 +157,13 @@ def stokes_geom_set(h, curve_offset, curve_kind, nodes, weights, normals, curvat
         h, int(kind.shape[0]), _vp(off.ctypes.data), _vp(kind.ctypes.data),
         _dptr(nodes, "nodes", (2,)), _dptr(weights, "weights"), _dptr(normals, "normals", (2,)),
         _dptr(curvature, "curvature", allow_none=True), float(period), float(mu), _stream(stream))
+    return _check(h, code)
+
+
+def stokes_geom_update(h, nodes, weights, normals, curvature=None, stream=None):
+    code = load().stokes_geom_update(h, _dptr(nodes, "nodes", (2,)), _dptr(weights, "weights"),
+                                     _dptr(normals, "normals", (2,)),
+                                     _dptr(curvature, "curvature", allow_none=True), _stream(stream))
     return _check(h, code)
 
 
@@ -279,6 +299,112 @@ def stokes_batch_info(h, precision):
     v = [_c_int() for _ in range(4)]
     _check(h, load().stokes_batch_info(h, int(precision), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+# ---------------------------------------------------------------------------
+# channel response and time stepping
+# ---------------------------------------------------------------------------
+class StepStats(ctypes.Structure):
+    _fields_ = [("iterations", _c_int), ("residual", _c_double), ("setup_ms", _c_double),
+                ("gmres_ms", _c_double), ("total_ms", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sim_err(h) -> str:
+    buf = ctypes.create_string_buffer(512)
+    if h:
+        load().stokes_sim_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _sim_check(h, code):
+    if code != STOKES_OK:
+        raise StokesError(code, _sim_err(h))
+    return code
+
+
+def _host(a, name, dtype="float64"):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, _vp(a.ctypes.data)
+
+
+def stokes_sim_create(device: int = 0):
+    h = _vp()
+    code = load().stokes_sim_create(int(device), ctypes.byref(h))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_sim_create(device=%d) failed" % device)
+    return h
+
+
+def stokes_sim_destroy(h):
+    return _sim_check(h, load().stokes_sim_destroy(h))
+
+
+def stokes_sim_last_error(h) -> str:
+    return _sim_err(h)
+
+
+def stokes_sim_set_walls(h, n_per_wall, nodes, weights, normals, curvature, period, mu, K=32,
+                         M=128, proxy_radius=None):
+    keep = [_host(a, "w") for a in (nodes, weights, normals, curvature)]
+    code = load().stokes_sim_set_walls(h, int(n_per_wall), *[p for _, p in keep], float(period),
+                                       float(mu), int(K), int(M),
+                                       float(period if proxy_radius is None else proxy_radius))
+    return _sim_check(h, code)
+
+
+def stokes_sim_set_vesicles(h, V, n, x, kappa_b, mu, period):
+    a, p = _host(x, "x")
+    return _sim_check(h, load().stokes_sim_set_vesicles(h, int(V), int(n), p, float(kappa_b),
+                                                        float(mu), float(period)))
+
+
+def stokes_sim_channel_response(h, f, p_drive, u_resp):
+    return _sim_check(h, load().stokes_sim_channel_response(h, _dptr(f, "f", (2,)), float(p_drive),
+                                                            _dptr(u_resp, "u_resp", (2,))))
+
+
+def stokes_sim_empty_channel(h, p_drive, v_walls, targets, u_out):
+    return _sim_check(h, load().stokes_sim_empty_channel(
+        h, float(p_drive), _dptr(v_walls, "v_walls", (2,), True), int(targets.shape[0]),
+        _dptr(targets, "targets", (2,)), _dptr(u_out, "u_out", (2,))))
+
+
+def vesicle_step_warmstart(h, dt, p_drive, guess=None, tol=1e-10, max_iter=300,
+                           precision=STOKES_FP64):
+    st = StepStats()
+    code = load().vesicle_step_warmstart(h, float(dt), float(p_drive),
+                                         _dptr(guess, "guess", None, True), float(tol),
+                                         int(max_iter), int(precision), ctypes.byref(st))
+    _sim_check(h, code)
+    return st.as_dict()
+
+
+def stokes_sim_sizes(h):
+    v = [_c_int() for _ in range(3)]
+    _sim_check(h, load().stokes_sim_sizes(h, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def stokes_sim_get_state(h):
+    """(positions (V n, 2), tension (V n), last solution (3 n V)) as NumPy arrays."""
+    import numpy as np
+    V, n, _ = stokes_sim_sizes(h)
+    x = np.zeros((V * n, 2))
+    sg = np.zeros(V * n)
+    sol = np.zeros(3 * V * n)
+    _sim_check(h, load().stokes_sim_get_state(h, _vp(x.ctypes.data), _vp(sg.ctypes.data),
+                                              _vp(sol.ctypes.data)))
+    return x, sg, sol
+
+
+def stokes_sim_set_state(h, x=None, sigma=None):
+    kx = _host(x, "x") if x is not None else (None, None)
+    ks = _host(sigma, "sigma") if sigma is not None else (None, None)
+    return _sim_check(h, load().stokes_sim_set_state(h, kx[1], ks[1]))
 
 
 # ---------------------------------------------------------------------------

@@ -61,7 +61,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if log.strip():
                 print(log)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results] + [
+        "-lcublas", "-lcusolver", "-Xlinker", "-rpath=" + os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

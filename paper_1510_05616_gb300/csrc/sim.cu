@@ -1,0 +1,1317 @@
+// sim.cu -- channel response (extended linear system) and the semi-implicit vesicle step.
+//
+// Channel response (Sec. 2.2, 2.3, three-step procedure of Sec. 3.1):
+//   u = D^near tau + sum_m c_m S(., y_m) (Eq. (urep)); the blocks A, B, C, Q of
+//   [A B; C Q][tau; c] = [v; g] (Eq. (BIEU), (BIED), (BIEgu), (BIEgT)) are assembled densely in
+//   FP64 by kernels; A is LU-factored (cuSOLVER), W = A^-1 B, S = Q - C W, and S's
+//   pseudo-inverse comes from an SVD with singular values below 1e-13 sigma_max dropped; a
+//   solve is c = S^+ (g - C A^-1 v), tau = A^-1 v - W c (the block elimination of Sec. 4.1,
+//   with LU in place of the paper's fast direct solver).  Side points: K Gauss-Legendre nodes
+//   across the inlet at x = 0, R = L + d, normal (1, 0); proxies: M points on a circle of
+//   radius R_p about (d/2, 0).  The pressure drive p_drive (pressure drop per period) enters
+//   as g_T = p_drive n.
+// Vesicle step (Sec. 3.2, Eq. (tsteplinsys), Eq. (ALC), Algorithm 1 steps 2-9, App. B, C):
+//   Fourier differentiation d/ds = (1/|x_alpha|) D_alpha per vesicle; forces, channel
+//   response of the explicit forces, right-preconditioned GMRES on
+//   [I + dt kB S d_ssss, -S d_s(x_s .); x_s . d_s, 0][u; sigma] = [S f_b + u_resp; rhs_ALC]
+//   whose matvec calls the layer-potential sum (stokes_sum_eval) of all vesicles, with a
+//   block-diagonal preconditioner made of each vesicle's self interaction (dense, batched
+//   LU inverse); then x += dt u, area correction, reparameterization.
+// The traction kernel of the double layer is Eq. (T) with d_x = (r . n_x) / r^2 (target) and
+// d_y = (r . n_y) / r^2 (source), which makes it the traction of the (D, P) pair.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "stokes_internal.cuh"
+
+namespace stokes {
+cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
+}
+
+using namespace stokes;
+
+struct stokes_sim {
+  int device = 0;
+  std::string err;
+  cudaStream_t s = nullptr;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t sol = nullptr;
+  double mu = 1.0, period = 0.0;
+  // walls and the extended system
+  bool have_walls = false;
+  int Nt = 0, K = 0, M = 0, nA = 0;
+  stokes_ctx *ctx_w = nullptr;         // walls only (double-layer sums at vesicle nodes)
+  double2 *d_wx = nullptr;             // wall nodes (free targets of the vesicle sums)
+  double2 *d_side = nullptr;           // [2K]: L points then R points
+  double2 *d_proxy = nullptr;          // [M]
+  double *d_LU = nullptr, *d_W = nullptr, *d_C = nullptr, *d_Spinv = nullptr;
+  int *d_piv = nullptr, *d_info = nullptr;
+  // vesicles
+  bool have_ves = false;
+  int V = 0, n = 0, Nv = 0;
+  double kappa_b = 1.0;
+  stokes_ctx *ctx_v = nullptr;         // vesicles only (single-layer sums, Kress self terms)
+  double2 *d_x = nullptr, *d_nrm = nullptr, *d_xs = nullptr;
+  double *d_w = nullptr, *d_spd = nullptr, *d_sigma = nullptr, *d_D = nullptr, *d_kress = nullptr;
+  double *d_L0 = nullptr, *d_A0 = nullptr, *d_Lk = nullptr;
+  double2 *d_f = nullptr, *d_fb = nullptr, *d_ures = nullptr, *d_tmp2 = nullptr, *d_tmp3 = nullptr;
+  double *d_vrhs = nullptr, *d_g = nullptr, *d_y = nullptr, *d_r = nullptr, *d_c = nullptr;
+  double *d_tau = nullptr;
+  // preconditioner (per vesicle 3n x 3n) and GMRES workspace
+  double *d_G = nullptr, *d_Ds = nullptr, *d_D2 = nullptr, *d_D4 = nullptr, *d_T = nullptr;
+  double *d_P = nullptr, *d_Pinv = nullptr;
+  double **d_Pptr = nullptr, **d_Piptr = nullptr;
+  int *d_ppiv = nullptr, *d_pinfo = nullptr;
+  int gm_m = 0;
+  double *d_V = nullptr, *d_z = nullptr, *d_b = nullptr, *d_wk = nullptr, *d_h = nullptr;
+  double *d_xsol = nullptr;            // last solution [u_x, u_y, sigma] per vesicle
+};
+
+namespace {
+
+constexpr double kPiD = 3.14159265358979323846;
+constexpr int kMaxN = 256;  // nodes per vesicle supported by the step kernels
+
+int fail(stokes_sim *m, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (m) m->err = buf;
+  return code;
+}
+
+#define SK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(m, e_ == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA, \
+                  "%s: %s", #call, cudaGetErrorString(e_));                          \
+  } while (0)
+#define BK(call)                                                                   \
+  do {                                                                             \
+    cublasStatus_t e_ = (call);                                                    \
+    if (e_ != CUBLAS_STATUS_SUCCESS) return fail(m, STOKES_ERR_CUDA, "%s: cublas %d", #call, int(e_)); \
+  } while (0)
+#define QK(call)                                                                   \
+  do {                                                                             \
+    cusolverStatus_t e_ = (call);                                                  \
+    if (e_ != CUSOLVER_STATUS_SUCCESS) return fail(m, STOKES_ERR_CUDA, "%s: cusolver %d", #call, int(e_)); \
+  } while (0)
+#define ST(call)                  \
+  do {                            \
+    int st_ = (call);             \
+    if (st_) return st_;          \
+  } while (0)
+
+template <class T>
+void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t count) {
+  dfree(p);
+  return cudaMalloc(reinterpret_cast<void **>(&p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+inline int nb(long n, int b) { return int((n + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// 2x2 kernel tensors, FP64 (row-major a[0..3] = (11, 12, 21, 22))
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void k_stokeslet(double rx, double ry, double cmu, double *a) {
+  const double rr = rx * rx + ry * ry;
+  const double lg = -0.5 * log(rr);
+  a[0] = cmu * (lg + rx * rx / rr);
+  a[1] = a[2] = cmu * rx * ry / rr;
+  a[3] = cmu * (lg + ry * ry / rr);
+}
+
+__device__ __forceinline__ void k_stresslet(double rx, double ry, double nx, double ny, double *a) {
+  const double rr = rx * rx + ry * ry;
+  const double c = (rx * nx + ry * ny) / (kPiD * rr * rr);
+  a[0] = c * rx * rx;
+  a[1] = a[2] = c * rx * ry;
+  a[3] = c * ry * ry;
+}
+
+__device__ __forceinline__ void k_slp_traction(double rx, double ry, double nx, double ny, double *a) {
+  const double rr = rx * rx + ry * ry;
+  const double c = -(rx * nx + ry * ny) / (kPiD * rr * rr);
+  a[0] = c * rx * rx;
+  a[1] = a[2] = c * rx * ry;
+  a[3] = c * ry * ry;
+}
+
+// Eq. (T): traction at x (normal nx) of the double layer at y (normal ny).
+__device__ __forceinline__ void k_dlp_traction(double rx, double ry, double nxx, double nxy,
+                                               double nyx, double nyy, double mu, double *a) {
+  const double rr = rx * rx + ry * ry;
+  const double dx = (rx * nxx + ry * nxy) / rr;
+  const double dy = (rx * nyx + ry * nyy) / rr;
+  const double nn = nxx * nyx + nxy * nyy;
+  const double r[2] = {rx, ry}, nX[2] = {nxx, nxy}, nY[2] = {nyx, nyy};
+  const double c1 = (nn / rr - 8.0 * dx * dy) / rr;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      a[2 * i + k] = (mu / kPiD) * (c1 * r[i] * r[k] + (i == k ? dx * dy : 0.0) + nX[i] * nY[k] / rr +
+                                   dx * r[k] * nY[i] / rr + dy * r[i] * nX[k] / rr);
+}
+
+// ---------------------------------------------------------------------------
+// assembly of the extended system (column-major)
+// ---------------------------------------------------------------------------
+__global__ void assemble_A_kernel(int Nt, const double2 *x, const double2 *nrm, const double *w,
+                                  const double *kap, double d, double *A) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= Nt) return;
+  const long lda = 2L * Nt;
+  double s[4] = {0, 0, 0, 0}, t[4];
+  for (int m = -1; m <= 1; ++m) {
+    if (m == 0 && i == j) continue;
+    k_stresslet(x[i].x - (x[j].x + m * d), x[i].y - x[j].y, nrm[j].x, nrm[j].y, t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += t[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s[q] *= w[j];
+  if (i == j) {
+    const double tx = -nrm[j].y, ty = nrm[j].x, c = -kap[j] / (2.0 * kPiD) * w[j];
+    s[0] += c * tx * tx - 0.5;
+    s[1] += c * tx * ty;
+    s[2] += c * tx * ty;
+    s[3] += c * ty * ty - 0.5;
+  }
+  A[(2 * i) + (2L * j) * lda] = s[0];
+  A[(2 * i) + (2L * j + 1) * lda] = s[1];
+  A[(2 * i + 1) + (2L * j) * lda] = s[2];
+  A[(2 * i + 1) + (2L * j + 1) * lda] = s[3];
+}
+
+__global__ void assemble_B_kernel(int Nt, int M, const double2 *x, const double2 *proxy, double cmu,
+                                  double *B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (i >= Nt) return;
+  const long ld = 2L * Nt;
+  double a[4];
+  k_stokeslet(x[i].x - proxy[m].x, x[i].y - proxy[m].y, cmu, a);
+  B[2 * i + (2L * m) * ld] = a[0];
+  B[2 * i + (2L * m + 1) * ld] = a[1];
+  B[2 * i + 1 + (2L * m) * ld] = a[2];
+  B[2 * i + 1 + (2L * m + 1) * ld] = a[3];
+}
+
+__global__ void assemble_C_kernel(int Nt, int K, const double2 *x, const double2 *nrm,
+                                  const double *w, const double2 *side, double d, double mu,
+                                  double *C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (j >= Nt) return;
+  const long ld = 4L * K;
+  const double2 L = side[k], R = side[K + k];
+  double a[4], b[4];
+  // velocity discrepancy D(x_R, y - d) - D(x_L, y + d)
+  k_stresslet(R.x - (x[j].x - d), R.y - x[j].y, nrm[j].x, nrm[j].y, a);
+  k_stresslet(L.x - (x[j].x + d), L.y - x[j].y, nrm[j].x, nrm[j].y, b);
+  C[2 * k + (2L * j) * ld] = w[j] * (a[0] - b[0]);
+  C[2 * k + (2L * j + 1) * ld] = w[j] * (a[1] - b[1]);
+  C[2 * k + 1 + (2L * j) * ld] = w[j] * (a[2] - b[2]);
+  C[2 * k + 1 + (2L * j + 1) * ld] = w[j] * (a[3] - b[3]);
+  // traction discrepancy with the side normal (1, 0)
+  k_dlp_traction(R.x - (x[j].x - d), R.y - x[j].y, 1.0, 0.0, nrm[j].x, nrm[j].y, mu, a);
+  k_dlp_traction(L.x - (x[j].x + d), L.y - x[j].y, 1.0, 0.0, nrm[j].x, nrm[j].y, mu, b);
+  const int r0 = 2 * K + 2 * k;
+  C[r0 + (2L * j) * ld] = w[j] * (a[0] - b[0]);
+  C[r0 + (2L * j + 1) * ld] = w[j] * (a[1] - b[1]);
+  C[r0 + 1 + (2L * j) * ld] = w[j] * (a[2] - b[2]);
+  C[r0 + 1 + (2L * j + 1) * ld] = w[j] * (a[3] - b[3]);
+}
+
+__global__ void assemble_Q_kernel(int K, int M, const double2 *side, const double2 *proxy,
+                                  double cmu, double *Q) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (k >= K) return;
+  const long ld = 4L * K;
+  const double2 L = side[k], R = side[K + k], y = proxy[m];
+  double a[4], b[4];
+  k_stokeslet(R.x - y.x, R.y - y.y, cmu, a);
+  k_stokeslet(L.x - y.x, L.y - y.y, cmu, b);
+  Q[2 * k + (2L * m) * ld] = a[0] - b[0];
+  Q[2 * k + (2L * m + 1) * ld] = a[1] - b[1];
+  Q[2 * k + 1 + (2L * m) * ld] = a[2] - b[2];
+  Q[2 * k + 1 + (2L * m + 1) * ld] = a[3] - b[3];
+  k_slp_traction(R.x - y.x, R.y - y.y, 1.0, 0.0, a);
+  k_slp_traction(L.x - y.x, L.y - y.y, 1.0, 0.0, b);
+  const int r0 = 2 * K + 2 * k;
+  Q[r0 + (2L * m) * ld] = a[0] - b[0];
+  Q[r0 + (2L * m + 1) * ld] = a[1] - b[1];
+  Q[r0 + 1 + (2L * m) * ld] = a[2] - b[2];
+  Q[r0 + 1 + (2L * m + 1) * ld] = a[3] - b[3];
+}
+
+// S^+ = U diag(1/sigma, truncated) V^T from the SVD S^T = U Sigma V^T:  scale U's columns.
+__global__ void scale_columns_kernel(int rows, int cols, const double *sig, double cutoff,
+                                     double *U) {
+  const long t = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= long(rows) * cols) return;
+  const int c = int(t / rows);
+  const double s = sig[c];
+  U[t] = (s > cutoff) ? U[t] / s : 0.0;
+}
+
+__global__ void transpose_kernel(int rows, int cols, const double *in, double *out) {
+  const long t = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= long(rows) * cols) return;
+  const int r = int(t % rows), c = int(t / rows);
+  out[c + long(r) * cols] = in[t];
+}
+
+// Data g of the response to vesicle forces (Eq. (vesgu), (vesgT)) at the side points; one
+// block per side point, fixed-order tree reduction over the vesicle nodes.
+__global__ void side_rhs_kernel(int K, int Nv, const double2 *side, const double2 *xv,
+                                const double *wv, const double2 *f, double d, double cmu,
+                                double p_drive, double *g) {
+  __shared__ double red[4][256];
+  const int k = blockIdx.x;
+  const double2 L = side[k], R = side[K + k];
+  double acc[4] = {0, 0, 0, 0};
+  for (int j = threadIdx.x; j < Nv; j += blockDim.x) {
+    const double qx = wv[j] * f[j].x, qy = wv[j] * f[j].y;
+    double a[4], b[4];
+    k_stokeslet(R.x - (xv[j].x - d), R.y - xv[j].y, cmu, a);
+    k_stokeslet(L.x - (xv[j].x + d), L.y - xv[j].y, cmu, b);
+    acc[0] += -(a[0] * qx + a[1] * qy) + (b[0] * qx + b[1] * qy);
+    acc[1] += -(a[2] * qx + a[3] * qy) + (b[2] * qx + b[3] * qy);
+    k_slp_traction(R.x - (xv[j].x - d), R.y - xv[j].y, 1.0, 0.0, a);
+    k_slp_traction(L.x - (xv[j].x + d), L.y - xv[j].y, 1.0, 0.0, b);
+    acc[2] += -(a[0] * qx + a[1] * qy) + (b[0] * qx + b[1] * qy);
+    acc[3] += -(a[2] * qx + a[3] * qy) + (b[2] * qx + b[3] * qy);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    g[2 * k] = red[0][0];
+    g[2 * k + 1] = red[1][0];
+    g[2 * K + 2 * k] = red[2][0] + p_drive;  // + p_drive n, n = (1, 0)
+    g[2 * K + 2 * k + 1] = red[3][0];
+  }
+}
+
+__global__ void empty_rhs_kernel(int K, double p_drive, double *g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * K) return;
+  g[t] = (t >= 2 * K && ((t - 2 * K) & 1) == 0) ? p_drive : 0.0;
+}
+
+// u_i += sum_m S(x_i, y_m) c_m (proxy part of Eq. (urep)).
+__global__ void proxy_eval_kernel(int n_t, const double2 *xt, int M, const double2 *proxy,
+                                  const double *c, double cmu, double2 *u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_t) return;
+  double ux = 0.0, uy = 0.0, a[4];
+  for (int m = 0; m < M; ++m) {
+    k_stokeslet(xt[i].x - proxy[m].x, xt[i].y - proxy[m].y, cmu, a);
+    ux += a[0] * c[2 * m] + a[1] * c[2 * m + 1];
+    uy += a[2] * c[2 * m] + a[3] * c[2 * m + 1];
+  }
+  u[i].x += ux;
+  u[i].y += uy;
+}
+
+__global__ void axpby_kernel(long n, double a, const double *x, double b, double *y) {
+  const long t = long(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = a * x[t] + b * y[t];
+}
+
+// ---------------------------------------------------------------------------
+// per-vesicle spectral kernels (one block per vesicle, blockDim = n)
+// ---------------------------------------------------------------------------
+__global__ void fourier_diff_kernel(int n, double *D) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int a = t / n, k = t % n, q = a - k;
+  D[t] = (q == 0) ? 0.0 : 0.5 * ((q & 1) ? -1.0 : 1.0) / tan(q * kPiD / n);
+}
+
+// out = D in over one vesicle's n values held in shared memory (row-major D).
+__device__ __forceinline__ double drow(const double *D, const double *in, int n, int a) {
+  double s = 0.0;
+  const double *row = D + size_t(a) * n;
+  for (int k = 0; k < n; ++k) s += row[k] * in[k];
+  return s;
+}
+
+// Geometry of the current positions: speed, unit tangent, outward normal, weights.
+__global__ void ves_geom_kernel(int n, const double2 *x, const double *D, double *spd,
+                                double2 *xs, double2 *nrm, double *w) {
+  __shared__ double X[kMaxN], Y[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  X[a] = x[i].x;
+  Y[a] = x[i].y;
+  __syncthreads();
+  const double xa = drow(D, X, n, a), ya = drow(D, Y, n, a);
+  const double s = sqrt(xa * xa + ya * ya);
+  spd[i] = s;
+  xs[i] = make_double2(xa / s, ya / s);
+  nrm[i] = make_double2(ya / s, -xa / s);
+  w[i] = s * 2.0 * kPiD / n;
+}
+
+// Forces of Algorithm 1 step 2: f_b = -kB x_ssss, f = f_b + (sigma x_s)_s.
+__global__ void ves_forces_kernel(int n, const double2 *x, const double *sigma, const double *D,
+                                  const double *spd, const double2 *xs, double kb, double2 *fb,
+                                  double2 *f) {
+  __shared__ double X[kMaxN], Y[kMaxN], TX[kMaxN], TY[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  const double s = spd[i];
+  X[a] = x[i].x;
+  Y[a] = x[i].y;
+  __syncthreads();
+  for (int r = 0; r < 4; ++r) {  // d/ds four times
+    const double dx = drow(D, X, n, a) / s, dy = drow(D, Y, n, a) / s;
+    __syncthreads();
+    X[a] = dx;
+    Y[a] = dy;
+    __syncthreads();
+  }
+  const double bx = -kb * X[a], by = -kb * Y[a];
+  TX[a] = sigma[i] * xs[i].x;
+  TY[a] = sigma[i] * xs[i].y;
+  __syncthreads();
+  const double sx = drow(D, TX, n, a) / s, sy = drow(D, TY, n, a) / s;
+  fb[i] = make_double2(bx, by);
+  f[i] = make_double2(bx + sx, by + sy);
+}
+
+// Matvec, first half: g = dt kB u_ssss - (sigma x_s)_s from z = [u_x, u_y, sigma] per vesicle.
+__global__ void ves_mv_pre_kernel(int n, const double *z, const double *D, const double *spd,
+                                  const double2 *xs, double dtkb, double2 *g) {
+  __shared__ double X[kMaxN], Y[kMaxN], TX[kMaxN], TY[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  const double *zv = z + size_t(3) * n * v;
+  const double s = spd[i];
+  X[a] = zv[a];
+  Y[a] = zv[n + a];
+  TX[a] = zv[2 * n + a] * xs[i].x;
+  TY[a] = zv[2 * n + a] * xs[i].y;
+  __syncthreads();
+  const double sx = drow(D, TX, n, a) / s, sy = drow(D, TY, n, a) / s;
+  for (int r = 0; r < 4; ++r) {
+    const double dx = drow(D, X, n, a) / s, dy = drow(D, Y, n, a) / s;
+    __syncthreads();
+    X[a] = dx;
+    Y[a] = dy;
+    __syncthreads();
+  }
+  g[i] = make_double2(dtkb * X[a] - sx, dtkb * Y[a] - sy);
+}
+
+// Matvec, second half: [u + S g; x_s . u_s].
+__global__ void ves_mv_post_kernel(int n, const double *z, const double2 *Sg, const double *D,
+                                   const double *spd, const double2 *xs, double *out) {
+  __shared__ double X[kMaxN], Y[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  const double *zv = z + size_t(3) * n * v;
+  double *ov = out + size_t(3) * n * v;
+  X[a] = zv[a];
+  Y[a] = zv[n + a];
+  __syncthreads();
+  const double s = spd[i];
+  const double ux = drow(D, X, n, a) / s, uy = drow(D, Y, n, a) / s;
+  ov[a] = X[a] + Sg[i].x;
+  ov[n + a] = Y[a] + Sg[i].y;
+  ov[2 * n + a] = xs[i].x * ux + xs[i].y * uy;
+}
+
+// Right-hand side: [S f_b + u_resp; (L0 - Lk) / (dt Lk)] (Eq. (ALC)).
+__global__ void ves_rhs_kernel(int n, const double2 *Sfb, const double2 *ures, const double *w,
+                               const double *L0, double dt, double *b, double *Lk_out) {
+  __shared__ double red[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  red[a] = w[i];
+  __syncthreads();
+  if (a == 0) {
+    double L = 0.0;
+    for (int k = 0; k < n; ++k) L += red[k];
+    red[0] = L;
+    Lk_out[v] = L;
+  }
+  __syncthreads();
+  const double Lk = red[0];
+  double *bv = b + size_t(3) * n * v;
+  bv[a] = Sfb[i].x + (ures ? ures[i].x : 0.0);
+  bv[n + a] = Sfb[i].y + (ures ? ures[i].y : 0.0);
+  bv[2 * n + a] = (L0[v] - Lk) / (dt * Lk);
+}
+
+// Perimeter L = sum w and area A = int x y_alpha of every vesicle (initial values).
+__global__ void ves_LA_kernel(int n, const double2 *x, const double *D, const double *w, double *L,
+                              double *A) {
+  __shared__ double X[kMaxN], Y[kMaxN], P[kMaxN], W[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  X[a] = x[i].x;
+  Y[a] = x[i].y;
+  W[a] = w[i];
+  __syncthreads();
+  P[a] = X[a] * drow(D, Y, n, a);
+  __syncthreads();
+  if (a == 0) {
+    double l = 0.0, s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      l += W[k];
+      s += P[k];
+    }
+    L[v] = l;
+    A[v] = s * 2.0 * kPiD / n;
+  }
+}
+
+// x <- x + dt u, then the area correction of App. B (root of the quadratic closest to 0).
+__global__ void ves_advance_kernel(int n, double2 *x, const double *z, const double *D,
+                                   const double *A0, double dt) {
+  __shared__ double X[kMaxN], Y[kMaxN], XA[kMaxN], YA[kMaxN], P[4][kMaxN];
+  __shared__ double cc;
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  const double *zv = z + size_t(3) * n * v;
+  X[a] = x[i].x + dt * zv[a];
+  Y[a] = x[i].y + dt * zv[n + a];
+  __syncthreads();
+  XA[a] = drow(D, X, n, a);
+  YA[a] = drow(D, Y, n, a);
+  __syncthreads();
+  const double xaa = drow(D, XA, n, a);
+  P[0][a] = X[a] * YA[a];
+  P[1][a] = X[a] * xaa;
+  P[2][a] = YA[a] * YA[a];
+  P[3][a] = YA[a] * xaa;
+  __syncthreads();
+  if (a == 0) {
+    double I[4] = {0, 0, 0, 0};
+    for (int k = 0; k < n; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) I[q] += P[q][k];
+    const double h = 2.0 * kPiD / n;
+    const double a0 = I[0] * h - A0[v], a1 = (-I[1] + I[2]) * h, a2 = -I[3] * h;
+    double c;
+    if (fabs(a2) < 1e-300) {
+      c = -a0 / a1;
+    } else {
+      const double disc = sqrt(fmax(a1 * a1 - 4.0 * a2 * a0, 0.0));
+      const double r1 = (-a1 + disc) / (2.0 * a2), r2 = (-a1 - disc) / (2.0 * a2);
+      c = fabs(r1) < fabs(r2) ? r1 : r2;
+    }
+    cc = c;
+  }
+  __syncthreads();
+  x[i] = make_double2(X[a] + cc * YA[a], Y[a] - cc * XA[a]);
+}
+
+// App. C, Algorithm 2: nearly equal arc-length nodes (piecewise-linear inversion of s(alpha),
+// Fourier interpolation of x at the new parameters).
+__global__ void ves_reparam_kernel(int n, double2 *x, const double *D) {
+  __shared__ double X[kMaxN], Y[kMaxN], S[kMaxN], Cr[kMaxN], Ci[kMaxN], SJ[kMaxN + 1];
+  __shared__ double Xr[kMaxN], Xi[kMaxN], Yr[kMaxN], Yi[kMaxN], AS[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  const double h = 2.0 * kPiD / n;
+  X[a] = x[i].x;
+  Y[a] = x[i].y;
+  __syncthreads();
+  const double xa = drow(D, X, n, a), ya = drow(D, Y, n, a);
+  S[a] = sqrt(xa * xa + ya * ya);
+  __syncthreads();
+  // Fourier coefficients (frequency index a; a > n/2 means a - n) of speed and position
+  {
+    double cr = 0, ci = 0, xr = 0, xi = 0, yr = 0, yi = 0;
+    for (int k = 0; k < n; ++k) {
+      double sn, cs;
+      sincospi(-2.0 * double((long(a) * k) % n) / n, &sn, &cs);
+      cr += S[k] * cs;
+      ci += S[k] * sn;
+      xr += X[k] * cs;
+      xi += X[k] * sn;
+      yr += Y[k] * cs;
+      yi += Y[k] * sn;
+    }
+    Cr[a] = cr / n;
+    Ci[a] = ci / n;
+    Xr[a] = xr / n;
+    Xi[a] = xi / n;
+    Yr[a] = yr / n;
+    Yi[a] = yi / n;
+  }
+  __syncthreads();
+  // s at alpha_a = C0 alpha + sum_{k != 0, n/2} Re[C_k (e^{ik alpha} - 1) / (ik)]
+  {
+    const double al = h * a;
+    double s = Cr[0] * al;
+    for (int q = 1; q < n; ++q) {
+      if (q == n / 2) continue;
+      const int kf = q < n / 2 ? q : q - n;
+      double sn, cs;
+      sincos(kf * al, &sn, &cs);
+      // (C (e - 1)) / (i k) = (Cr + i Ci)((cs - 1) + i sn) / (i k)
+      const double re = Cr[q] * (cs - 1.0) - Ci[q] * sn, im = Cr[q] * sn + Ci[q] * (cs - 1.0);
+      s += im / kf;  // Re[(re + i im) / (i k)] = im / k
+      (void)re;
+    }
+    SJ[a] = s;
+    if (a == 0) SJ[n] = Cr[0] * 2.0 * kPiD;
+  }
+  __syncthreads();
+  if (a == 0) {
+    const double total = SJ[n];
+    AS[0] = 0.0;
+    int j = 0;
+    for (int q = 1; q < n; ++q) {
+      const double tg = total / n * q;
+      while (j < n - 1 && !(SJ[j] <= tg && tg < SJ[j + 1])) ++j;
+      AS[q] = h * (j + (tg - SJ[j]) / (SJ[j + 1] - SJ[j]));
+    }
+  }
+  __syncthreads();
+  const double al = AS[a];
+  double nx = 0.0, ny = 0.0;
+  for (int q = 0; q < n; ++q) {
+    if (q == n / 2) {
+      const double c = cos(0.5 * n * al);
+      nx += Xr[q] * c;
+      ny += Yr[q] * c;
+      continue;
+    }
+    const int kf = q < n / 2 ? q : q - n;
+    double sn, cs;
+    sincos(kf * al, &sn, &cs);
+    nx += Xr[q] * cs - Xi[q] * sn;
+    ny += Yr[q] * cs - Yi[q] * sn;
+  }
+  x[i] = make_double2(nx, ny);
+}
+
+// ---------------------------------------------------------------------------
+// block-diagonal preconditioner: per vesicle the self-only operator (3n x 3n, column-major,
+// unknown order [u_x, u_y, sigma])
+// ---------------------------------------------------------------------------
+// Kress self single-layer blocks G_ij (n x n column-major each) and D_s = diag(1/s) D.
+__global__ void pc_parts_kernel(int n, const double2 *x, const double2 *xs, const double *spd,
+                                const double *kress, const double *D, double cmu, double *G,
+                                double *Ds) {
+  const int v = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int a = t % n, k = t / n;  // row a, column k (column-major)
+  const int ia = v * n + a, ik = v * n + k;
+  const double h = 2.0 * kPiD / n;
+  double coef, m11, m12, m22;
+  if (a == k) {
+    const double s = spd[ia];
+    coef = kress[0] - (kPiD / n) * log(s * s);
+    const double tx = xs[ia].x, ty = xs[ia].y;
+    m11 = tx * tx;
+    m12 = tx * ty;
+    m22 = ty * ty;
+  } else {
+    const double rx = x[ia].x - x[ik].x, ry = x[ia].y - x[ik].y, rr = rx * rx + ry * ry;
+    int dj = a - k;
+    if (dj < 0) dj += n;
+    coef = kress[dj] - (kPiD / n) * log(rr);
+    m11 = rx * rx / rr;
+    m12 = rx * ry / rr;
+    m22 = ry * ry / rr;
+  }
+  const double sk = cmu * spd[ik];
+  const size_t nn = size_t(n) * n, base = size_t(v) * 4 * nn + t;
+  G[base + 0 * nn] = (coef + h * m11) * sk;  // G_11
+  G[base + 1 * nn] = (h * m12) * sk;         // G_12
+  G[base + 2 * nn] = (h * m12) * sk;         // G_21
+  G[base + 3 * nn] = (coef + h * m22) * sk;  // G_22
+  Ds[size_t(v) * nn + t] = D[size_t(a) * n + k] / spd[ia];
+}
+
+// T_c = D_s diag(x_s,c)  (c = 0, 1), stored as two n x n blocks per vesicle.
+__global__ void pc_T_kernel(int n, const double *Ds, const double2 *xs, double *T) {
+  const int v = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int k = t / n;
+  const size_t nn = size_t(n) * n;
+  const double d = Ds[size_t(v) * nn + t];
+  T[size_t(v) * 2 * nn + t] = d * xs[v * n + k].x;
+  T[size_t(v) * 2 * nn + nn + t] = d * xs[v * n + k].y;
+}
+
+// Fill the constraint rows [diag(x_s,1) D_s, diag(x_s,2) D_s, 0] and add the identity of the
+// u block.
+__global__ void pc_fill_kernel(int n, const double *Ds, const double2 *xs, double *P) {
+  const int v = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = 3 * n;
+  if (t >= m * n) return;
+  const int row = 2 * n + t % n, col = t / n;  // constraint rows, all 3n columns
+  const size_t mm = size_t(m) * m;
+  double *Pv = P + size_t(v) * mm;
+  const int a = row - 2 * n;
+  double val = 0.0;
+  if (col < 2 * n) {
+    const int c = col / n, k = col % n;
+    const double xsc = c == 0 ? xs[v * n + a].x : xs[v * n + a].y;
+    val = xsc * Ds[size_t(v) * n * n + size_t(k) * n + a];
+  }
+  Pv[row + size_t(col) * m] = val;
+  if (t < 2 * n) Pv[t + size_t(t) * m] += 1.0;
+}
+
+__global__ void extract_sigma_kernel(int n, const double *z, double *sigma) {
+  const int v = blockIdx.x, a = threadIdx.x;
+  sigma[v * n + a] = z[size_t(3) * n * v + 2 * n + a];
+}
+
+__global__ void set_ptrs_kernel(int count, double *base, size_t stride, double **ptrs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) ptrs[t] = base + stride * t;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes on [-1, 1] (Newton iteration on the Legendre recurrence).
+std::vector<double> gauss_legendre(int K) {
+  std::vector<double> x(K);
+  for (int i = 0; i < K; ++i) {
+    double z = cos(kPiD * (i + 0.75) / (K + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= K; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double dp = K * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[K - 1 - i] = z;
+  }
+  return x;
+}
+
+int set_stream_handles(stokes_sim *m) {
+  BK(cublasSetStream(m->blas, m->s));
+  QK(cusolverDnSetStream(m->sol, m->s));
+  return STOKES_OK;
+}
+
+// Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.
+int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out) {
+  const double cmu = 1.0 / (4.0 * kPiD * m->mu);
+  // v = -S^near f at the wall nodes (vesicle sums at free targets)
+  ST(stokes_sum_eval_targets(m->ctx_v, STOKES_FP64, reinterpret_cast<const double *>(f), nullptr,
+                             m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
+  side_rhs_kernel<<<m->K, 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w, f, m->period,
+                                          cmu, p_drive, m->d_g);
+  SK(cudaGetLastError());
+  // y = A^-1 (-v)
+  axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, -1.0, m->d_vrhs, 0.0, m->d_y);
+  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, 1, m->d_LU, m->nA, m->d_piv, m->d_y, m->nA,
+                      m->d_info));
+  // r = g - C y ; c = S^+ r ; tau = y - W c
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, m->d_y, 1, &one,
+                 m->d_g, 1));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 2 * m->M, 4 * m->K, &one, m->d_Spinv, 2 * m->M, m->d_g, 1,
+                 &zero, m->d_c, 1));
+  SK(cudaMemcpyAsync(m->d_tau, m->d_y, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, m->d_c, 1, &one,
+                 m->d_tau, 1));
+  // u_resp = D^near tau + sum_m c_m S(., y_m) at the vesicle nodes
+  ST(stokes_sum_eval_targets(m->ctx_w, STOKES_FP64, nullptr, m->d_tau, m->Nv,
+                             reinterpret_cast<const double *>(m->d_x),
+                             reinterpret_cast<double *>(u_out), m->s));
+  proxy_eval_kernel<<<nb(m->Nv, 128), 128, 0, m->s>>>(m->Nv, m->d_x, m->M, m->d_proxy, m->d_c,
+                                                      cmu, u_out);
+  SK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+// z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).
+int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, double *zout) {
+  ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
+                                             m->d_tmp2);
+  SK(cudaGetLastError());
+  ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
+                     0.0, reinterpret_cast<double *>(m->d_tmp3), m->s));
+  ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
+                                              zout);
+  SK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+int precond_apply(stokes_sim *m, const double *zin, double *zout) {
+  const int k = 3 * m->n;
+  const double one = 1.0, zero = 0.0;
+  BK(cublasDgemvStridedBatched(m->blas, CUBLAS_OP_N, k, k, &one, m->d_Pinv, k, size_t(k) * k, zin, 1,
+                               k, &zero, zout, 1, k, m->V));
+  return STOKES_OK;
+}
+
+int precond_build(stokes_sim *m, double dt) {
+  const int n = m->n, V = m->V, k = 3 * n;
+  const size_t nn = size_t(n) * n, kk = size_t(k) * k;
+  const double cmu = 1.0 / (4.0 * kPiD * m->mu);
+  dim3 g2(nb(n * n, 256), V);
+  pc_parts_kernel<<<g2, 256, 0, m->s>>>(n, m->d_x, m->d_xs, m->d_spd, m->d_kress, m->d_D, cmu,
+                                        m->d_G, m->d_Ds);
+  SK(cudaGetLastError());
+  const double one = 1.0, zero = 0.0, mone = -1.0, dtkb = dt * m->kappa_b;
+  // D2 = Ds Ds, D4 = D2 D2
+  BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, m->d_Ds, n, nn,
+                               m->d_Ds, n, nn, &zero, m->d_D2, n, nn, V));
+  BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, m->d_D2, n, nn,
+                               m->d_D2, n, nn, &zero, m->d_D4, n, nn, V));
+  pc_T_kernel<<<g2, 256, 0, m->s>>>(n, m->d_Ds, m->d_xs, m->d_T);
+  SK(cudaGetLastError());
+  // u block: dt kB G_ij D4 ; sigma column block: -(G_i1 T_1 + G_i2 T_2)
+  for (int i = 0; i < 2; ++i) {
+    for (int j = 0; j < 2; ++j) {
+      BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &dtkb,
+                                   m->d_G + (2 * i + j) * nn, n, 4 * nn, m->d_D4, n, nn, &zero,
+                                   m->d_P + i * n + size_t(j) * n * k, k, kk, V));
+      BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &mone,
+                                   m->d_G + (2 * i + j) * nn, n, 4 * nn, m->d_T + j * nn, n, 2 * nn,
+                                   j == 0 ? &zero : &one, m->d_P + i * n + size_t(2 * n) * k, k, kk,
+                                   V));
+    }
+  }
+  pc_fill_kernel<<<dim3(nb(3 * n * n, 256), V), 256, 0, m->s>>>(n, m->d_Ds, m->d_xs, m->d_P);
+  SK(cudaGetLastError());
+  BK(cublasDgetrfBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_pinfo, V));
+  BK(cublasDgetriBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_Piptr, k, m->d_pinfo, V));
+  return STOKES_OK;
+}
+
+double dnrm(stokes_sim *m, long len, const double *x, int *st) {
+  double r = 0.0;
+  if (cublasDnrm2(m->blas, int(len), x, 1, &r) != CUBLAS_STATUS_SUCCESS) *st = STOKES_ERR_CUDA;
+  return r;
+}
+
+// Right-preconditioned restarted GMRES (classical Gram-Schmidt, twice) on z; FP64.
+int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, double tol,
+          int max_iter, int *iters, double *relres) {
+  const long len = 3L * m->Nv;
+  const int mr = m->gm_m;
+  int st = STOKES_OK;
+  const double bn = dnrm(m, len, b, &st);
+  if (st) return fail(m, st, "cublasDnrm2 failed");
+  *iters = 0;
+  *relres = 0.0;
+  if (bn == 0.0) {
+    SK(cudaMemsetAsync(x, 0, sizeof(double) * len, m->s));
+    return STOKES_OK;
+  }
+  std::vector<double> H(size_t(mr + 1) * mr), cs(mr), sn(mr), gg(mr + 1), hcol(mr + 1),
+      hcol2(mr + 1);
+  const double one = 1.0, zero = 0.0, mone = -1.0;
+  while (true) {
+    // r = b - A x
+    ST(step_matvec(m, dt, precision, x, m->d_wk));
+    SK(cudaMemcpyAsync(m->d_V, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+    BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_V, 1));
+    const double beta = dnrm(m, len, m->d_V, &st);
+    if (st) return fail(m, st, "cublasDnrm2 failed");
+    *relres = beta / bn;
+    if (*relres <= tol) return STOKES_OK;
+    if (*iters >= max_iter) return fail(m, STOKES_ERR_NOT_CONVERGED, "GMRES: %d iterations, relative residual %.3e", *iters, *relres);
+    const double ib = 1.0 / beta;
+    BK(cublasDscal(m->blas, int(len), &ib, m->d_V, 1));
+    std::fill(gg.begin(), gg.end(), 0.0);
+    gg[0] = beta;
+    int j = 0;
+    for (; j < mr && *iters < max_iter; ++j) {
+      double *vj = m->d_V + size_t(j) * len, *vn = m->d_V + size_t(j + 1) * len;
+      ST(precond_apply(m, vj, m->d_z));
+      ST(step_matvec(m, dt, precision, m->d_z, vn));
+      // CGS2
+      BK(cublasDgemv(m->blas, CUBLAS_OP_T, int(len), j + 1, &one, m->d_V, int(len), vn, 1, &zero,
+                     m->d_h, 1));
+      BK(cublasDgemv(m->blas, CUBLAS_OP_N, int(len), j + 1, &mone, m->d_V, int(len), m->d_h, 1, &one,
+                     vn, 1));
+      SK(cudaMemcpyAsync(hcol.data(), m->d_h, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, m->s));
+      BK(cublasDgemv(m->blas, CUBLAS_OP_T, int(len), j + 1, &one, m->d_V, int(len), vn, 1, &zero,
+                     m->d_h, 1));
+      BK(cublasDgemv(m->blas, CUBLAS_OP_N, int(len), j + 1, &mone, m->d_V, int(len), m->d_h, 1, &one,
+                     vn, 1));
+      SK(cudaMemcpyAsync(hcol2.data(), m->d_h, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, m->s));
+      const double hn = dnrm(m, len, vn, &st);  // synchronises the stream
+      if (st) return fail(m, st, "cublasDnrm2 failed");
+      for (int q = 0; q <= j; ++q) hcol[q] += hcol2[q];
+      hcol[j + 1] = hn;
+      if (hn > 0.0) {
+        const double ih = 1.0 / hn;
+        BK(cublasDscal(m->blas, int(len), &ih, vn, 1));
+      }
+      // Givens rotations
+      for (int q = 0; q < j; ++q) {
+        const double t = cs[q] * hcol[q] + sn[q] * hcol[q + 1];
+        hcol[q + 1] = -sn[q] * hcol[q] + cs[q] * hcol[q + 1];
+        hcol[q] = t;
+      }
+      const double den = hypot(hcol[j], hcol[j + 1]);
+      cs[j] = den > 0 ? hcol[j] / den : 1.0;
+      sn[j] = den > 0 ? hcol[j + 1] / den : 0.0;
+      hcol[j] = den;
+      hcol[j + 1] = 0.0;
+      gg[j + 1] = -sn[j] * gg[j];
+      gg[j] = cs[j] * gg[j];
+      for (int q = 0; q <= j; ++q) H[size_t(j) * (mr + 1) + q] = hcol[q];
+      ++*iters;
+      if (fabs(gg[j + 1]) / bn <= tol * 0.5 || hn == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += P^-1 (V y)
+    std::vector<double> yv(j);
+    for (int q = j - 1; q >= 0; --q) {
+      double s = gg[q];
+      for (int p = q + 1; p < j; ++p) s -= H[size_t(p) * (mr + 1) + q] * yv[p];
+      yv[q] = s / H[size_t(q) * (mr + 1) + q];
+    }
+    SK(cudaMemcpyAsync(m->d_h, yv.data(), sizeof(double) * j, cudaMemcpyHostToDevice, m->s));
+    BK(cublasDgemv(m->blas, CUBLAS_OP_N, int(len), j, &one, m->d_V, int(len), m->d_h, 1, &zero,
+                   m->d_wk, 1));
+    ST(precond_apply(m, m->d_wk, m->d_z));
+    BK(cublasDaxpy(m->blas, int(len), &one, m->d_z, 1, x, 1));
+    SK(cudaStreamSynchronize(m->s));
+  }
+}
+
+void free_walls(stokes_sim *m) {
+  if (m->ctx_w) stokes_destroy(m->ctx_w);
+  m->ctx_w = nullptr;
+  dfree(m->d_wx);
+  dfree(m->d_side);
+  dfree(m->d_proxy);
+  dfree(m->d_LU);
+  dfree(m->d_W);
+  dfree(m->d_C);
+  dfree(m->d_Spinv);
+  dfree(m->d_piv);
+  dfree(m->d_vrhs);
+  dfree(m->d_g);
+  dfree(m->d_y);
+  dfree(m->d_c);
+  dfree(m->d_tau);
+  m->have_walls = false;
+}
+
+void free_vesicles(stokes_sim *m) {
+  if (m->ctx_v) stokes_destroy(m->ctx_v);
+  m->ctx_v = nullptr;
+  double2 **p2[] = {&m->d_x, &m->d_nrm, &m->d_xs, &m->d_f, &m->d_fb, &m->d_ures, &m->d_tmp2, &m->d_tmp3};
+  for (auto p : p2) dfree(*p);
+  double **p1[] = {&m->d_w, &m->d_spd, &m->d_sigma, &m->d_D, &m->d_kress, &m->d_L0, &m->d_A0, &m->d_Lk,
+                   &m->d_G, &m->d_Ds, &m->d_D2, &m->d_D4, &m->d_T, &m->d_P, &m->d_Pinv, &m->d_V,
+                   &m->d_z, &m->d_b, &m->d_wk, &m->d_h, &m->d_xsol};
+  for (auto p : p1) dfree(*p);
+  dfree(m->d_Pptr);
+  dfree(m->d_Piptr);
+  dfree(m->d_ppiv);
+  dfree(m->d_pinfo);
+  m->have_ves = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_sim_create(int device, stokes_sim **out) {
+  if (!out) return STOKES_ERR_ARG;
+  *out = nullptr;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) return STOKES_ERR_CUDA;
+  stokes_sim *m = new stokes_sim();
+  m->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cublasCreate(&m->blas) != CUBLAS_STATUS_SUCCESS ||
+      cusolverDnCreate(&m->sol) != CUSOLVER_STATUS_SUCCESS ||
+      cudaMalloc(reinterpret_cast<void **>(&m->d_info), sizeof(int)) != cudaSuccess) {
+    delete m;
+    return STOKES_ERR_CUDA;
+  }
+  if (set_stream_handles(m) != STOKES_OK) {
+    delete m;
+    return STOKES_ERR_CUDA;
+  }
+  *out = m;
+  return STOKES_OK;
+}
+
+int stokes_sim_destroy(stokes_sim *m) {
+  if (!m) return STOKES_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  free_walls(m);
+  free_vesicles(m);
+  dfree(m->d_info);
+  if (m->blas) cublasDestroy(m->blas);
+  if (m->sol) cusolverDnDestroy(m->sol);
+  if (m->s) cudaStreamDestroy(m->s);
+  delete m;
+  return STOKES_OK;
+}
+
+int stokes_sim_last_error(const stokes_sim *m, char *buf, size_t len) {
+  if (!m || !buf || len == 0) return STOKES_ERR_ARG;
+  snprintf(buf, len, "%s", m->err.c_str());
+  return STOKES_OK;
+}
+
+int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, const double *weights,
+                         const double *normals, const double *curvature, double period, double mu,
+                         int K, int M, double proxy_radius) {
+  if (!m) return STOKES_ERR_ARG;
+  if (n_per_wall < 4 || !nodes || !weights || !normals || !curvature)
+    return fail(m, STOKES_ERR_ARG, "need n_per_wall >= 4 and host wall arrays");
+  if (!(period > 0.0) || !(mu > 0.0) || K < 2 || M < 2 || !(proxy_radius > 0.0))
+    return fail(m, STOKES_ERR_ARG, "need period > 0, mu > 0, K >= 2, M >= 2, proxy radius > 0");
+  if (m->have_ves && mu != m->mu) return fail(m, STOKES_ERR_ARG, "mu differs from the vesicles'");
+  if (fabs(nodes[0]) > 1e-12 || fabs(nodes[2 * n_per_wall]) > 1e-12)
+    return fail(m, STOKES_ERR_ARG, "each wall's first node must lie on x = 0 (the inlet)");
+  SK(cudaSetDevice(m->device));
+  free_walls(m);
+  const int Nt = 2 * n_per_wall, nA = 2 * Nt;
+  m->Nt = Nt;
+  m->nA = nA;
+  m->K = K;
+  m->M = M;
+  m->mu = mu;
+  m->period = period;
+  // walls-only context (double-layer sums at vesicle nodes)
+  ST(stokes_create(m->device, &m->ctx_w));
+  double *dx = nullptr, *dw = nullptr, *dn = nullptr, *dk = nullptr;
+  SK(dalloc(dx, 2 * Nt));
+  SK(dalloc(dw, Nt));
+  SK(dalloc(dn, 2 * Nt));
+  SK(dalloc(dk, Nt));
+  SK(cudaMemcpy(dx, nodes, sizeof(double) * 2 * Nt, cudaMemcpyHostToDevice));
+  SK(cudaMemcpy(dw, weights, sizeof(double) * Nt, cudaMemcpyHostToDevice));
+  SK(cudaMemcpy(dn, normals, sizeof(double) * 2 * Nt, cudaMemcpyHostToDevice));
+  SK(cudaMemcpy(dk, curvature, sizeof(double) * Nt, cudaMemcpyHostToDevice));
+  const int32_t off[3] = {0, n_per_wall, Nt}, kind[2] = {STOKES_KIND_WALL, STOKES_KIND_WALL};
+  int st = stokes_geom_set(m->ctx_w, 2, off, kind, dx, dw, dn, dk, period, mu, m->s);
+  if (st) {
+    char b[256];
+    stokes_last_error(m->ctx_w, b, sizeof(b));
+    cudaFree(dw);
+    cudaFree(dn);
+    cudaFree(dk);
+    cudaFree(dx);
+    return fail(m, st, "walls: %s", b);
+  }
+  m->d_wx = reinterpret_cast<double2 *>(dx);
+  // side points and proxies (host setup)
+  const double ylo = nodes[1], yhi = nodes[2 * n_per_wall + 1];
+  std::vector<double> gl = gauss_legendre(K);
+  std::vector<double2> side(2 * K), prox(M);
+  for (int k = 0; k < K; ++k) {
+    const double y = 0.5 * (ylo + yhi) + 0.5 * (yhi - ylo) * gl[k];
+    side[k] = make_double2(0.0, y);
+    side[K + k] = make_double2(period, y);
+  }
+  for (int q = 0; q < M; ++q)
+    prox[q] = make_double2(0.5 * period + proxy_radius * cos(2.0 * kPiD * q / M),
+                           proxy_radius * sin(2.0 * kPiD * q / M));
+  SK(dalloc(m->d_side, 2 * K));
+  SK(dalloc(m->d_proxy, M));
+  SK(cudaMemcpy(m->d_side, side.data(), sizeof(double2) * 2 * K, cudaMemcpyHostToDevice));
+  SK(cudaMemcpy(m->d_proxy, prox.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
+  // assemble A, B, C, Q
+  double *dQ = nullptr, *dS = nullptr, *dU = nullptr, *dVt = nullptr, *dsig = nullptr;
+  SK(dalloc(m->d_LU, size_t(nA) * nA));
+  SK(dalloc(m->d_W, size_t(nA) * 2 * M));
+  SK(dalloc(m->d_C, size_t(4) * K * nA));
+  SK(dalloc(dQ, size_t(4) * K * 2 * M));
+  SK(dalloc(m->d_piv, nA));
+  const double cmu = 1.0 / (4.0 * kPiD * mu);
+  const double2 *wx = m->d_wx, *wn = reinterpret_cast<const double2 *>(dn);
+  assemble_A_kernel<<<dim3(nb(Nt, 128), Nt), 128, 0, m->s>>>(Nt, wx, wn, dw, dk, period, m->d_LU);
+  assemble_B_kernel<<<dim3(nb(Nt, 128), M), 128, 0, m->s>>>(Nt, M, wx, m->d_proxy, cmu, m->d_W);
+  assemble_C_kernel<<<dim3(nb(Nt, 128), K), 128, 0, m->s>>>(Nt, K, wx, wn, dw, m->d_side, period, mu,
+                                                           m->d_C);
+  assemble_Q_kernel<<<dim3(nb(K, 64), M), 64, 0, m->s>>>(K, M, m->d_side, m->d_proxy, cmu, dQ);
+  SK(cudaGetLastError());
+  // LU of A; W = A^-1 B
+  int lwork = 0;
+  QK(cusolverDnDgetrf_bufferSize(m->sol, nA, nA, m->d_LU, nA, &lwork));
+  double *work = nullptr;
+  SK(dalloc(work, lwork));
+  QK(cusolverDnDgetrf(m->sol, nA, nA, m->d_LU, nA, work, m->d_piv, m->d_info));
+  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, nA, 2 * M, m->d_LU, nA, m->d_piv, m->d_W, nA, m->d_info));
+  // S = Q - C W  (4K x 2M); SVD of S^T (2M x 4K, needs rows >= cols)
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  BK(cublasDgemm(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, 4 * K, 2 * M, nA, &mone, m->d_C, 4 * K, m->d_W,
+                 nA, &one, dQ, 4 * K));
+  const int rS = 2 * M, cS = 4 * K;
+  if (rS < cS) return fail(m, STOKES_ERR_ARG, "need M >= 2K proxy points");
+  SK(dalloc(dS, size_t(rS) * cS));
+  transpose_kernel<<<nb(long(cS) * rS, 256), 256, 0, m->s>>>(cS, rS, dQ, dS);
+  SK(dalloc(dU, size_t(rS) * cS));
+  SK(dalloc(dVt, size_t(cS) * cS));
+  SK(dalloc(dsig, cS));
+  int lw2 = 0;
+  QK(cusolverDnDgesvd_bufferSize(m->sol, rS, cS, &lw2));
+  double *work2 = nullptr;
+  SK(dalloc(work2, lw2));
+  QK(cusolverDnDgesvd(m->sol, 'S', 'S', rS, cS, dS, rS, dsig, dU, rS, dVt, cS, work2, lw2, nullptr,
+                      m->d_info));
+  double smax = 0.0;
+  SK(cudaMemcpyAsync(&smax, dsig, sizeof(double), cudaMemcpyDeviceToHost, m->s));
+  SK(cudaStreamSynchronize(m->s));
+  int info = 0;
+  SK(cudaMemcpy(&info, m->d_info, sizeof(int), cudaMemcpyDeviceToHost));
+  scale_columns_kernel<<<nb(long(rS) * cS, 256), 256, 0, m->s>>>(rS, cS, dsig, 1e-13 * smax, dU);
+  // S^+ = U diag(1/sigma) V^T  (2M x 4K)
+  SK(dalloc(m->d_Spinv, size_t(rS) * cS));
+  BK(cublasDgemm(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, rS, cS, cS, &one, dU, rS, dVt, cS, &zero,
+                 m->d_Spinv, rS));
+  SK(cudaStreamSynchronize(m->s));
+  for (double *p : {dQ, dS, dU, dVt, dsig, work, work2, dw, dn, dk}) cudaFree(p);
+  SK(dalloc(m->d_vrhs, nA));
+  SK(dalloc(m->d_g, 4 * K));
+  SK(dalloc(m->d_y, nA));
+  SK(dalloc(m->d_c, 2 * M));
+  SK(dalloc(m->d_tau, nA));
+  if (info != 0) return fail(m, STOKES_ERR_CUDA, "SVD of the Schur complement did not converge (%d)", info);
+  m->have_walls = true;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double kappa_b,
+                            double mu, double period) {
+  if (!m) return STOKES_ERR_ARG;
+  if (V < 1 || n < 8 || (n & 1) || n > kMaxN || !x)
+    return fail(m, STOKES_ERR_ARG, "need V >= 1 vesicles with an even n in [8, %d] nodes", kMaxN);
+  if (!(mu > 0.0) || !(period >= 0.0)) return fail(m, STOKES_ERR_ARG, "need mu > 0, period >= 0");
+  if (m->have_walls && (mu != m->mu || period != m->period))
+    return fail(m, STOKES_ERR_ARG, "mu and period must match the walls'");
+  SK(cudaSetDevice(m->device));
+  free_vesicles(m);
+  m->V = V;
+  m->n = n;
+  m->Nv = V * n;
+  m->kappa_b = kappa_b;
+  m->mu = mu;
+  m->period = period;
+  const int Nv = m->Nv;
+  SK(dalloc(m->d_x, Nv));
+  SK(dalloc(m->d_nrm, Nv));
+  SK(dalloc(m->d_xs, Nv));
+  SK(dalloc(m->d_w, Nv));
+  SK(dalloc(m->d_spd, Nv));
+  SK(dalloc(m->d_sigma, Nv));
+  SK(dalloc(m->d_D, n * n));
+  SK(dalloc(m->d_kress, n));
+  SK(dalloc(m->d_L0, V));
+  SK(dalloc(m->d_A0, V));
+  SK(dalloc(m->d_Lk, V));
+  for (double2 **p : {&m->d_f, &m->d_fb, &m->d_ures, &m->d_tmp2, &m->d_tmp3}) SK(dalloc(*p, Nv));
+  SK(cudaMemcpy(m->d_x, x, sizeof(double2) * Nv, cudaMemcpyHostToDevice));
+  SK(cudaMemsetAsync(m->d_sigma, 0, sizeof(double) * Nv, m->s));
+  fourier_diff_kernel<<<nb(n * n, 256), 256, 0, m->s>>>(n, m->d_D);
+  SK(launch_kress_table(n, m->d_kress, m->s));
+  ves_geom_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D, m->d_spd, m->d_xs, m->d_nrm, m->d_w);
+  ves_LA_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D, m->d_w, m->d_L0, m->d_A0);
+  SK(cudaGetLastError());
+  // vesicles-only context (single-layer sums with Kress self terms)
+  ST(stokes_create(m->device, &m->ctx_v));
+  std::vector<int32_t> off(V + 1), kind(V, STOKES_KIND_VESICLE);
+  for (int v = 0; v <= V; ++v) off[v] = v * n;
+  SK(cudaStreamSynchronize(m->s));
+  int st = stokes_geom_set(m->ctx_v, V, off.data(), kind.data(), reinterpret_cast<double *>(m->d_x),
+                           m->d_w, reinterpret_cast<double *>(m->d_nrm), nullptr, period, mu, m->s);
+  if (st) {
+    char b[256];
+    stokes_last_error(m->ctx_v, b, sizeof(b));
+    return fail(m, st, "vesicles: %s", b);
+  }
+  // preconditioner and GMRES workspace
+  const int k = 3 * n;
+  const size_t nn = size_t(n) * n, kk = size_t(k) * k;
+  SK(dalloc(m->d_G, 4 * nn * V));
+  SK(dalloc(m->d_Ds, nn * V));
+  SK(dalloc(m->d_D2, nn * V));
+  SK(dalloc(m->d_D4, nn * V));
+  SK(dalloc(m->d_T, 2 * nn * V));
+  SK(dalloc(m->d_P, kk * V));
+  SK(dalloc(m->d_Pinv, kk * V));
+  SK(dalloc(m->d_Pptr, V));
+  SK(dalloc(m->d_Piptr, V));
+  SK(dalloc(m->d_ppiv, size_t(k) * V));
+  SK(dalloc(m->d_pinfo, V));
+  set_ptrs_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_P, kk, m->d_Pptr);
+  set_ptrs_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_Pinv, kk, m->d_Piptr);
+  m->gm_m = 80;
+  const long len = 3L * Nv;
+  SK(dalloc(m->d_V, size_t(len) * (m->gm_m + 1)));
+  SK(dalloc(m->d_z, len));
+  SK(dalloc(m->d_b, len));
+  SK(dalloc(m->d_wk, len));
+  SK(dalloc(m->d_h, m->gm_m + 1));
+  SK(dalloc(m->d_xsol, len));
+  SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
+  SK(cudaStreamSynchronize(m->s));
+  m->have_ves = true;
+  return STOKES_OK;
+}
+
+int stokes_sim_channel_response(stokes_sim *m, const double *f, double p_drive, double *u_resp) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_walls || !m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "walls and vesicles must be set");
+  if (!f || !u_resp) return fail(m, STOKES_ERR_ARG, "NULL device pointer");
+  SK(cudaSetDevice(m->device));
+  ST(channel_response(m, reinterpret_cast<const double2 *>(f), p_drive,
+                      reinterpret_cast<double2 *>(u_resp)));
+  SK(cudaStreamSynchronize(m->s));
+  return STOKES_OK;
+}
+
+int stokes_sim_empty_channel(stokes_sim *m, double p_drive, const double *v_walls, int n_targets,
+                             const double *targets, double *u_out) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_walls) return fail(m, STOKES_ERR_NO_GEOM, "walls must be set");
+  if (n_targets < 1 || !targets || !u_out) return fail(m, STOKES_ERR_ARG, "need targets and output");
+  SK(cudaSetDevice(m->device));
+  empty_rhs_kernel<<<nb(4 * m->K, 128), 128, 0, m->s>>>(m->K, p_drive, m->d_g);
+  if (v_walls)
+    SK(cudaMemcpyAsync(m->d_y, v_walls, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
+  else
+    SK(cudaMemsetAsync(m->d_y, 0, sizeof(double) * m->nA, m->s));
+  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, 1, m->d_LU, m->nA, m->d_piv, m->d_y, m->nA, m->d_info));
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, m->d_y, 1, &one, m->d_g, 1));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 2 * m->M, 4 * m->K, &one, m->d_Spinv, 2 * m->M, m->d_g, 1, &zero, m->d_c, 1));
+  SK(cudaMemcpyAsync(m->d_tau, m->d_y, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, m->d_c, 1, &one, m->d_tau, 1));
+  ST(stokes_sum_eval_targets(m->ctx_w, STOKES_FP64, nullptr, m->d_tau, n_targets, targets, u_out, m->s));
+  proxy_eval_kernel<<<nb(n_targets, 128), 128, 0, m->s>>>(n_targets, reinterpret_cast<const double2 *>(targets), m->M,
+                                                         m->d_proxy, m->d_c, 1.0 / (4.0 * kPiD * m->mu),
+                                                         reinterpret_cast<double2 *>(u_out));
+  SK(cudaGetLastError());
+  SK(cudaStreamSynchronize(m->s));
+  return STOKES_OK;
+}
+
+int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, const double *guess,
+                           double tol, int max_iter, int precision, stokes_step_stats *out) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  if (!(dt > 0.0) || !(tol > 0.0) || max_iter < 1)
+    return fail(m, STOKES_ERR_ARG, "need dt > 0, tol > 0, max_iter >= 1");
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fail(m, STOKES_ERR_ARG, "unknown precision");
+  SK(cudaSetDevice(m->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int V = m->V, n = m->n;
+  const long len = 3L * m->Nv;
+  // geometry at x^k (weights/normals feed the sums)
+  ves_geom_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D, m->d_spd, m->d_xs, m->d_nrm, m->d_w);
+  SK(cudaGetLastError());
+  ST(stokes_geom_update(m->ctx_v, reinterpret_cast<double *>(m->d_x), m->d_w,
+                        reinterpret_cast<double *>(m->d_nrm), nullptr, m->s));
+  // step 2: forces
+  ves_forces_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_sigma, m->d_D, m->d_spd, m->d_xs, m->kappa_b,
+                                       m->d_fb, m->d_f);
+  SK(cudaGetLastError());
+  // steps 3-5: channel response of the explicit forces
+  if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures));
+  // right-hand side [S f_b + u_resp; ALC]
+  ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
+                     reinterpret_cast<double *>(m->d_tmp3), m->s));
+  ves_rhs_kernel<<<V, n, 0, m->s>>>(n, m->d_tmp3, m->have_walls ? m->d_ures : nullptr, m->d_w,
+                                    m->d_L0, dt, m->d_b, m->d_Lk);
+  SK(cudaGetLastError());
+  // step 6: GMRES with the block-diagonal self preconditioner
+  ST(precond_build(m, dt));
+  if (guess)
+    SK(cudaMemcpyAsync(m->d_xsol, guess, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  else
+    SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
+  SK(cudaStreamSynchronize(m->s));
+  const auto t1 = std::chrono::steady_clock::now();
+  int iters = 0;
+  double rel = 0.0;
+  const int gst = gmres(m, dt, precision, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
+  const auto t2 = std::chrono::steady_clock::now();
+  if (out) {
+    out->iterations = iters;
+    out->residual = rel;
+    out->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    out->gmres_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  }
+  if (gst) return gst;
+  // steps 7-9: x <- x + dt u, area correction, reparameterization; sigma <- sigma^{k+1}
+  ves_advance_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_xsol, m->d_D, m->d_A0, dt);
+  ves_reparam_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D);
+  extract_sigma_kernel<<<V, n, 0, m->s>>>(n, m->d_xsol, m->d_sigma);
+  SK(cudaGetLastError());
+  SK(cudaStreamSynchronize(m->s));
+  if (out)
+    out->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return STOKES_OK;
+}
+
+int stokes_sim_get_state(stokes_sim *m, double *x_host, double *sigma_host, double *solution_host) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  SK(cudaSetDevice(m->device));
+  SK(cudaStreamSynchronize(m->s));
+  if (x_host) SK(cudaMemcpy(x_host, m->d_x, sizeof(double2) * m->Nv, cudaMemcpyDeviceToHost));
+  if (sigma_host) SK(cudaMemcpy(sigma_host, m->d_sigma, sizeof(double) * m->Nv, cudaMemcpyDeviceToHost));
+  if (solution_host)
+    SK(cudaMemcpy(solution_host, m->d_xsol, sizeof(double) * 3 * m->Nv, cudaMemcpyDeviceToHost));
+  return STOKES_OK;
+}
+
+int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigma_host) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  SK(cudaSetDevice(m->device));
+  if (x_host) SK(cudaMemcpy(m->d_x, x_host, sizeof(double2) * m->Nv, cudaMemcpyHostToDevice));
+  if (sigma_host) SK(cudaMemcpy(m->d_sigma, sigma_host, sizeof(double) * m->Nv, cudaMemcpyHostToDevice));
+  return STOKES_OK;
+}
+
+int stokes_sim_sizes(const stokes_sim *m, int *n_vesicles, int *nodes_per_vesicle,
+                     int *wall_nodes) {
+  if (!m || !n_vesicles || !nodes_per_vesicle || !wall_nodes) return STOKES_ERR_ARG;
+  *n_vesicles = m->have_ves ? m->V : 0;
+  *nodes_per_vesicle = m->have_ves ? m->n : 0;
+  *wall_nodes = m->have_walls ? m->Nt : 0;
+  return STOKES_OK;
+}
+
+}  // extern "C"

@@ -490,6 +490,30 @@ int stokes_geom_set(stokes_ctx *c, int n_curves, const int32_t *curve_offset,
                       normals, curvature, mu, as_stream(stream));
 }
 
+int stokes_geom_update(stokes_ctx *c, const double *nodes, const double *weights,
+                       const double *normals, const double *curvature, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
+  if (!nodes || !weights || !normals || !aligned16(nodes) || !aligned16(normals))
+    return fail(c, STOKES_ERR_ARG, "nodes, weights and normals must be device pointers (16-byte aligned 2-vectors)");
+  if (c->n_wall_nodes > 0 && !curvature)
+    return fail(c, STOKES_ERR_ARG, "curvature is required when walls are present");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  const int N = c->N;
+  CK(cudaMemcpyAsync(c->d_x, nodes, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->d_nrm, normals, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->d_w, weights, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  if (curvature) CK(cudaMemcpyAsync(c->d_kap, curvature, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  CK(launch_geom_prep(c, s));
+  for (auto &g : c->graph_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return STOKES_OK;
+}
+
 int stokes_sum_eval(stokes_ctx *c, int precision, const double *slp, const double *dlp,
                     double jump, double *out, void *stream) {
   if (!c) return STOKES_ERR_ARG;

@@ -1,0 +1,183 @@
+"""GPU channel response and semi-implicit step against the NumPy FP64 oracle."""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from paper_1510_05616_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+warnings.filterwarnings("ignore", category=RuntimeWarning)
+PI = math.pi
+D = 2 * PI
+MU = 0.7
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_05616_gb300 import build
+    build.build()
+    import paper_1510_05616_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def S():
+    from oracle import sim_oracle
+    return sim_oracle
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def make_sim(P, walls=None, ves=None, kappa_b=1.0, K=24, M=96, period=D):
+    h = P.stokes_sim_create(0)
+    if walls is not None:
+        lo, up = walls
+        P.stokes_sim_set_walls(h, lo.n, np.vstack([lo.nodes, up.nodes]),
+                               np.concatenate([lo.weights, up.weights]),
+                               np.vstack([lo.normals, up.normals]),
+                               np.concatenate([lo.curvature, up.curvature]), period, MU, K, M)
+    if ves is not None:
+        x = np.vstack([c.nodes for c in ves])
+        P.stokes_sim_set_vesicles(h, len(ves), ves[0].n, x, kappa_b, MU, period)
+    return h
+
+
+def _case(seed=3, n_w=96, n_ves=3, n_v=16):
+    g = I.channel(n_w, I.WALL_SHAPE_SMALL, n_ves, n_v, 0.05, seed)
+    walls = [c for c in g.curves if c.kind == I.KIND_DLP]
+    ves = [c for c in g.curves if c.kind == I.KIND_SLP]
+    return walls, ves
+
+
+PTS = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0], [2.0, 0.5], [5.0, -0.4]])
+
+
+def test_poiseuille_on_gpu(P, S):
+    """The GPU block solve reproduces the exact Poiseuille flow at the paper's accuracy level,
+    and agrees with the oracle's block solve."""
+    import torch
+    lo, up = I.wall_curves(128, I.WALL_SHAPE_SMALL)
+    pd = 2 * MU * D * 0.2
+    ue = lambda p: np.stack([-(pd / (2 * MU * D)) * p[:, 1] ** 2, 0 * p[:, 1]], 1)
+    h = make_sim(P, (lo, up), K=32, M=128)
+    xw = np.vstack([lo.nodes, up.nodes])
+    out = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
+    P.stokes_sim_empty_channel(h, pd, dev(ue(xw)), dev(PTS), out)
+    u = out.cpu().numpy()
+    P.stokes_sim_destroy(h)
+    scale = np.abs(ue(xw)).max()
+    assert np.abs(u - ue(PTS)).max() / scale < 5e-6
+    W = S.Walls(lo, up, D, MU, K=32, M=128)
+    _, g = S.empty_channel_rhs(W, pd)
+    tau, c = W.solve(ue(xw).reshape(-1), g)
+    ref = W.velocity(tau, c, PTS)
+    assert np.abs(u - ref).max() / scale < 5e-6
+
+
+def test_channel_response_parity(P, S):
+    import torch
+    walls, ves = _case()
+    rng = np.random.default_rng(4)
+    f = rng.normal(size=(sum(c.n for c in ves), 2))
+    h = make_sim(P, walls, ves)
+    out = torch.zeros_like(dev(f))
+    P.stokes_sim_channel_response(h, dev(f), 0.8, out)
+    u = out.cpu().numpy()
+    P.stokes_sim_destroy(h)
+    W = S.Walls(walls[0], walls[1], D, MU, K=24, M=96)
+    xv = np.vstack([c.nodes for c in ves])
+    wv = np.concatenate([S.curve_normals_weights(c.nodes)[1] for c in ves])
+    v, g = S.vesicle_rhs(W, xv, wv, f, 0.8)
+    tau, c = W.solve(v, g)
+    ref = W.velocity(tau, c, xv)
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-6
+
+
+def _oracle_step(S, ves_x, dt, walls=None, p_drive=0.0, period=D, kappa_b=1.0, K=24, M=96):
+    L0 = [S.perimeter(x) for x in ves_x]
+    A0 = [S.area(x) for x in ves_x]
+    W = S.Walls(walls[0], walls[1], D, MU, K=K, M=M) if walls is not None else None
+    sig = [np.zeros(x.shape[0]) for x in ves_x]
+    return S.step(ves_x, sig, L0, A0, dt, kappa_b, MU, period, W, p_drive)
+
+
+@pytest.mark.parametrize("period", [D, 0.0])
+def test_free_step_parity(P, S, period):
+    """No walls: one step of GPU GMRES (FP64 sums) equals the oracle's direct solve."""
+    _, ves = _case(n_ves=3, n_v=16)
+    dt = 1e-3
+    h = make_sim(P, None, ves, period=period)
+    st = P.vesicle_step_warmstart(h, dt, 0.0, None, 1e-12, 200)
+    x, sg, sol = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    ox, osg, u, sig, _ = _oracle_step(S, [c.nodes for c in ves], dt, period=period)
+    assert st["residual"] <= 1e-12 and st["iterations"] > 0
+    n = ves[0].n
+    gu = np.concatenate([np.stack([sol[3 * n * v:3 * n * v + n], sol[3 * n * v + n:3 * n * v + 2 * n]], 1)
+                         for v in range(len(ves))])
+    assert np.abs(gu - u).max() < 1e-8 * np.abs(u).max()
+    assert np.abs(sg - sig).max() < 1e-8 * np.abs(sig).max()
+    assert np.abs(x - np.vstack(ox)).max() < 1e-10
+
+
+def test_channel_step_parity(P, S):
+    walls, ves = _case(n_ves=2, n_v=16, n_w=64)
+    dt, pd = 1e-3, 0.5
+    h = make_sim(P, walls, ves)
+    st = P.vesicle_step_warmstart(h, dt, pd, None, 1e-12, 200)
+    x, sg, sol = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    ox, osg, u, sig, ures = _oracle_step(S, [c.nodes for c in ves], dt, walls, pd)
+    n = ves[0].n
+    gu = np.concatenate([np.stack([sol[3 * n * v:3 * n * v + n], sol[3 * n * v + n:3 * n * v + 2 * n]], 1)
+                         for v in range(len(ves))])
+    assert np.abs(gu - u).max() < 1e-6 * np.abs(u).max()
+    assert np.abs(sg - sig).max() < 1e-6 * np.abs(sig).max()
+    assert np.abs(x - np.vstack(ox)).max() < 1e-8
+
+
+def test_warm_start_with_solution_converges_at_once(P):
+    import torch
+    walls, ves = _case(n_ves=3, n_v=16)
+    h = make_sim(P, walls, ves)
+    x0 = np.vstack([c.nodes for c in ves])
+    st0 = P.vesicle_step_warmstart(h, 1e-3, 0.5, None, 1e-10, 200)
+    _, _, sol = P.stokes_sim_get_state(h)
+    P.stokes_sim_set_state(h, x0, np.zeros(len(x0)))
+    st1 = P.vesicle_step_warmstart(h, 1e-3, 0.5, dev(sol), 1e-10, 200)
+    P.stokes_sim_destroy(h)
+    assert st0["iterations"] >= 3 and st1["iterations"] <= 1
+
+
+def test_several_steps_conserve_area_and_length(P, S):
+    walls, ves = _case(n_ves=3, n_v=32, n_w=96)
+    h = make_sim(P, walls, ves)
+    x0 = [c.nodes for c in ves]
+    A0 = [S.area(x) for x in x0]
+    L0 = [S.perimeter(x) for x in x0]
+    for _ in range(5):
+        P.vesicle_step_warmstart(h, 1e-3, 1.0, None, 1e-10, 300)
+    x, _, _ = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    for v in range(3):
+        xv = x[32 * v:32 * (v + 1)]
+        assert abs(S.area(xv) - A0[v]) < 1e-10 * A0[v]
+        assert abs(S.perimeter(xv) - L0[v]) < 1e-4 * L0[v]
+
+
+def test_sim_errors(P):
+    h = P.stokes_sim_create(0)
+    with pytest.raises(P.StokesError) as e:
+        P.vesicle_step_warmstart(h, 1e-3, 0.0)
+    assert e.value.code == P.STOKES_ERR_NO_GEOM
+    with pytest.raises(P.StokesError):
+        P.stokes_sim_set_vesicles(h, 1, 15, np.zeros((15, 2)), 1.0, 1.0, 0.0)
+    P.stokes_sim_destroy(h)
