@@ -285,6 +285,15 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  * ===========================================================================================
  */
 typedef struct stokes_sim stokes_sim;
+typedef struct stokes_mlp stokes_mlp;
+
+/* Initial iterate of the step's GMRES. */
+typedef enum {
+    STOKES_GUESS_ZERO = 0,      /* zero (the paper's plain method)                             */
+    STOKES_GUESS_PREVIOUS = 1,  /* the previous step's solution                                */
+    STOKES_GUESS_MLP = 2,       /* the warm-start network's prediction from the step's features */
+    STOKES_GUESS_USER = 3       /* the caller's DEVICE vector `guess`                          */
+} stokes_guess;
 
 typedef struct {
     int iterations;      /* GMRES iterations (matvecs inside the Krylov loop)            */
@@ -314,10 +323,44 @@ STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, dou
  * g_u = 0, g_T = p_drive n, at n_targets DEVICE points. */
 STOKES_API int stokes_sim_empty_channel(stokes_sim *sim, double p_drive, const double *v_walls,
                                         int n_targets, const double *targets, double *u_out);
-/* One time step; guess = DEVICE initial GMRES iterate (3 n V, layout above) or NULL (zero). */
-STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive,
-                                      const double *guess, double tol, int max_iter,
-                                      int precision, stokes_step_stats *stats);
+/* One time step.  guess_mode is a stokes_guess; model is required for STOKES_GUESS_MLP
+ * (n >= 16) and guess (DEVICE, 3 n V, layout above) for STOKES_GUESS_USER.  GMRES always runs
+ * to tol, so every guess only changes the iteration count, not the answer's tolerance. */
+STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive, int guess_mode,
+                                      stokes_mlp *model, const double *guess, double tol,
+                                      int max_iter, int precision, stokes_step_stats *stats);
+/* Warm-start features and targets of the last step (DEVICE FP32; either may be NULL):
+ * features (V x 64): per vesicle, in its principal-axes frame (centre c, angle theta of the
+ *   second moments, length l = sqrt(A0 / pi)), the Fourier modes k = -8..7 (re, im) of the
+ *   complex shape (x' + i y') / l, then of the step's explicit velocity (S f_b + u_resp)
+ *   rotated to the frame over U = kappa_B / (mu l^2);
+ * targets (V x 48): modes k = -8..7 of the solved velocity (frame, / U), then k = 0..7 of the
+ *   tension / (kappa_B / l^2).  The network predicts targets from features. */
+STOKES_API int stokes_sim_last_features(stokes_sim *sim, float *features, float *targets);
+
+/* Warm-start network: 64 -> H -> H -> 48 with SiLU, BF16 weights, FP32 accumulation, FP32
+ * master parameters updated by Adam (flattened W1, b1, W2, b2, W3, b3; W row-major (out, in)),
+ * input/output standardisation (mu_in, sd_in, mu_out, sd_out).  Host pointers for parameters
+ * and normalisation; DEVICE FP32 pointers for data.  Synchronous. */
+STOKES_API int stokes_mlp_create(int device, int n_in, int n_hidden, int n_out, stokes_mlp **out);
+STOKES_API int stokes_mlp_destroy(stokes_mlp *mlp);
+STOKES_API int stokes_mlp_last_error(const stokes_mlp *mlp, char *buf, size_t len);
+STOKES_API int stokes_mlp_num_params(const stokes_mlp *mlp);
+STOKES_API int stokes_mlp_set_params(stokes_mlp *mlp, const float *theta);
+STOKES_API int stokes_mlp_get_params(stokes_mlp *mlp, float *theta);
+STOKES_API int stokes_mlp_set_normalization(stokes_mlp *mlp, const float *norm);
+STOKES_API int stokes_mlp_get_normalization(stokes_mlp *mlp, float *norm);
+/* Column means / standard deviations of X (rows x n_in) and T (rows x n_out) as normalisation. */
+STOKES_API int stokes_mlp_fit_normalization(stokes_mlp *mlp, int rows, const float *X, const float *T);
+/* Predictions Y (batch x n_out) of X (batch x n_in). */
+STOKES_API int stokes_mlp_forward(stokes_mlp *mlp, int batch, const float *X, float *Y);
+/* Loss (1/B) sum (1/2)|y_hat - t_hat|^2 of rows idx[0..batch) (DEVICE int32; NULL = the first
+ * batch rows) of X, T and its gradient (n_params FP32, host or device; either may be NULL). */
+STOKES_API int stokes_mlp_loss_grad(stokes_mlp *mlp, int rows, const float *X, const float *T,
+                                    const int *idx, int batch, float *grad, float *loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss with learning rate lr. */
+STOKES_API int stokes_mlp_train_step(stokes_mlp *mlp, int rows, const float *X, const float *T,
+                                     const int *idx, int batch, float lr, float *loss);
 /* State transfer (HOST, any may be NULL): positions (V n x 2), tension (V n), and the last
  * step's solution [u_x, u_y, sigma] per vesicle (3 n V). */
 STOKES_API int stokes_sim_get_state(stokes_sim *sim, double *x, double *sigma, double *solution);

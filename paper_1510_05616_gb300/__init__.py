@@ -29,6 +29,13 @@ STOKES_FP32_KAHAN = 1
 STOKES_KIND_WALL = 0
 STOKES_KIND_VESICLE = 1
 
+STOKES_GUESS_ZERO = 0
+STOKES_GUESS_PREVIOUS = 1
+STOKES_GUESS_MLP = 2
+STOKES_GUESS_USER = 3
+N_FEATURES = 64
+N_TARGETS = 48
+
 PRECISIONS = {"fp64": STOKES_FP64, "fp32k": STOKES_FP32_KAHAN}
 
 
@@ -71,7 +78,21 @@ _SIGNATURES = {
     "stokes_sim_set_vesicles": [_vp, _c_int, _c_int, _vp, _c_double, _c_double, _c_double],
     "stokes_sim_channel_response": [_vp, _vp, _c_double, _vp],
     "stokes_sim_empty_channel": [_vp, _c_double, _vp, _c_int, _vp, _vp],
-    "vesicle_step_warmstart": [_vp, _c_double, _c_double, _vp, _c_double, _c_int, _c_int, _vp],
+    "vesicle_step_warmstart": [_vp, _c_double, _c_double, _c_int, _vp, _vp, _c_double, _c_int,
+                               _c_int, _vp],
+    "stokes_sim_last_features": [_vp, _vp, _vp],
+    "stokes_mlp_create": [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)],
+    "stokes_mlp_destroy": [_vp],
+    "stokes_mlp_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "stokes_mlp_num_params": [_vp],
+    "stokes_mlp_set_params": [_vp, _vp],
+    "stokes_mlp_get_params": [_vp, _vp],
+    "stokes_mlp_set_normalization": [_vp, _vp],
+    "stokes_mlp_get_normalization": [_vp, _vp],
+    "stokes_mlp_fit_normalization": [_vp, _c_int, _vp, _vp],
+    "stokes_mlp_forward": [_vp, _c_int, _vp, _vp],
+    "stokes_mlp_loss_grad": [_vp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp],
+    "stokes_mlp_train_step": [_vp, _c_int, _vp, _vp, _vp, _c_int, ctypes.c_float, _vp],
     "stokes_sim_get_state": [_vp, _vp, _vp, _vp],
     "stokes_sim_set_state": [_vp, _vp, _vp],
     "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
@@ -373,14 +394,119 @@ def stokes_sim_empty_channel(h, p_drive, v_walls, targets, u_out):
         _dptr(targets, "targets", (2,)), _dptr(u_out, "u_out", (2,))))
 
 
-def vesicle_step_warmstart(h, dt, p_drive, guess=None, tol=1e-10, max_iter=300,
-                           precision=STOKES_FP64):
+def vesicle_step_warmstart(h, dt, p_drive, guess_mode=STOKES_GUESS_ZERO, model=None, guess=None,
+                           tol=1e-10, max_iter=300, precision=STOKES_FP64):
     st = StepStats()
-    code = load().vesicle_step_warmstart(h, float(dt), float(p_drive),
+    code = load().vesicle_step_warmstart(h, float(dt), float(p_drive), int(guess_mode),
+                                         model if model else None,
                                          _dptr(guess, "guess", None, True), float(tol),
                                          int(max_iter), int(precision), ctypes.byref(st))
     _sim_check(h, code)
     return st.as_dict()
+
+
+def _fptr(t, name, allow_none=False):
+    import torch
+    if t is None:
+        if allow_none:
+            return None
+        raise StokesError(STOKES_ERR_ARG, "%s is None" % name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.float32, torch.int32) \
+            or not t.is_contiguous():
+        raise StokesError(STOKES_ERR_ARG, "%s must be a contiguous CUDA float32/int32 tensor" % name)
+    return _vp(t.data_ptr()) if t.numel() else None
+
+
+def stokes_sim_last_features(h, features, targets):
+    return _sim_check(h, load().stokes_sim_last_features(h, _fptr(features, "features", True),
+                                                         _fptr(targets, "targets", True)))
+
+
+def _mlp_err(h):
+    buf = ctypes.create_string_buffer(512)
+    if h:
+        load().stokes_mlp_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _mlp_check(h, code):
+    if code != STOKES_OK:
+        raise StokesError(code, _mlp_err(h))
+    return code
+
+
+def stokes_mlp_create(device, n_in, n_hidden, n_out):
+    h = _vp()
+    code = load().stokes_mlp_create(int(device), int(n_in), int(n_hidden), int(n_out), ctypes.byref(h))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_mlp_create failed")
+    return h
+
+
+def stokes_mlp_destroy(h):
+    return _mlp_check(h, load().stokes_mlp_destroy(h))
+
+
+def stokes_mlp_last_error(h):
+    return _mlp_err(h)
+
+
+def stokes_mlp_num_params(h):
+    return int(load().stokes_mlp_num_params(h))
+
+
+def stokes_mlp_set_params(h, theta):
+    a, p = _host(theta, "theta", "float32")
+    return _mlp_check(h, load().stokes_mlp_set_params(h, p))
+
+
+def stokes_mlp_get_params(h):
+    import numpy as np
+    out = np.zeros(stokes_mlp_num_params(h), dtype=np.float32)
+    _mlp_check(h, load().stokes_mlp_get_params(h, _vp(out.ctypes.data)))
+    return out
+
+
+def stokes_mlp_set_normalization(h, norm):
+    a, p = _host(norm, "norm", "float32")
+    return _mlp_check(h, load().stokes_mlp_set_normalization(h, p))
+
+
+def stokes_mlp_get_normalization(h, n_in=N_FEATURES, n_out=N_TARGETS):
+    import numpy as np
+    out = np.zeros(2 * (n_in + n_out), dtype=np.float32)
+    _mlp_check(h, load().stokes_mlp_get_normalization(h, _vp(out.ctypes.data)))
+    return out
+
+
+def stokes_mlp_fit_normalization(h, X, T):
+    return _mlp_check(h, load().stokes_mlp_fit_normalization(h, int(X.shape[0]), _fptr(X, "X"),
+                                                             _fptr(T, "T")))
+
+
+def stokes_mlp_forward(h, X, Y):
+    return _mlp_check(h, load().stokes_mlp_forward(h, int(X.shape[0]), _fptr(X, "X"), _fptr(Y, "Y")))
+
+
+def stokes_mlp_loss_grad(h, X, T, idx=None, batch=None):
+    """(loss, gradient as a NumPy array) of rows idx (CUDA int32) or the first `batch` rows."""
+    import numpy as np
+    b = int(idx.shape[0]) if idx is not None else int(batch if batch else X.shape[0])
+    g = np.zeros(stokes_mlp_num_params(h), dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _mlp_check(h, load().stokes_mlp_loss_grad(h, int(X.shape[0]), _fptr(X, "X"), _fptr(T, "T"),
+                                              _fptr(idx, "idx", True), b, _vp(g.ctypes.data),
+                                              _vp(loss.ctypes.data)))
+    return float(loss[0]), g
+
+
+def stokes_mlp_train_step(h, X, T, idx, lr):
+    import numpy as np
+    loss = np.zeros(1, dtype=np.float32)
+    _mlp_check(h, load().stokes_mlp_train_step(h, int(X.shape[0]), _fptr(X, "X"), _fptr(T, "T"),
+                                               _fptr(idx, "idx"), int(idx.shape[0]), float(lr),
+                                               _vp(loss.ctypes.data)))
+    return float(loss[0])
 
 
 def stokes_sim_sizes(h):

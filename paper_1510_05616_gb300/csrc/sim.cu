@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "stokes_internal.cuh"
+#include "stokes_mlp_internal.cuh"
 
 namespace stokes {
 cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
@@ -72,6 +73,9 @@ struct stokes_sim {
   int gm_m = 0;
   double *d_V = nullptr, *d_z = nullptr, *d_b = nullptr, *d_wk = nullptr, *d_h = nullptr;
   double *d_xsol = nullptr;            // last solution [u_x, u_y, sigma] per vesicle
+  // warm-start features / targets of the last step
+  float *d_feat = nullptr, *d_targ = nullptr, *d_pred = nullptr;
+  double *d_frame = nullptr;           // per vesicle: cx, cy, theta, l, U, sigma scale
 };
 
 namespace {
@@ -682,6 +686,131 @@ __global__ void pc_fill_kernel(int n, const double *Ds, const double2 *xs, doubl
   if (t < 2 * n) Pv[t + size_t(t) * m] += 1.0;
 }
 
+// ---------------------------------------------------------------------------
+// warm-start features, targets and guesses (per vesicle, principal-axes frame)
+// ---------------------------------------------------------------------------
+constexpr int kModes = 16;  // Fourier modes k = -8..7
+constexpr int kFeat = 64, kTarg = 48;
+
+// Frame of one vesicle from its nodes in shared memory: centre, angle of the second moments'
+// major axis, length l = sqrt(A0 / pi), velocity scale U = kB / (mu l^2), tension scale kB / l^2.
+__device__ void vesicle_frame(int n, const double *X, const double *Y, double A0, double kb,
+                              double mu, double *fr) {
+  double cx = 0, cy = 0;
+  for (int k = 0; k < n; ++k) {
+    cx += X[k];
+    cy += Y[k];
+  }
+  cx /= n;
+  cy /= n;
+  double sxx = 0, sxy = 0, syy = 0;
+  for (int k = 0; k < n; ++k) {
+    const double dx = X[k] - cx, dy = Y[k] - cy;
+    sxx += dx * dx;
+    sxy += dx * dy;
+    syy += dy * dy;
+  }
+  const double th = 0.5 * atan2(2.0 * sxy, sxx - syy);
+  const double l = sqrt(A0 / kPiD);
+  fr[0] = cx;
+  fr[1] = cy;
+  fr[2] = th;
+  fr[3] = l;
+  fr[4] = kb / (mu * l * l);
+  fr[5] = kb / (l * l);
+}
+
+// (1/n) sum_a (re_a + i im_a) e^{-i k alpha_a}
+__device__ void dft_mode(int n, int k, const double *re, const double *im, double *out) {
+  double sr = 0, si = 0;
+  for (int a = 0; a < n; ++a) {
+    double sn, cs;
+    sincospi(-2.0 * double(((long(k) * a) % n + n) % n) / n, &sn, &cs);
+    sr += re[a] * cs - im[a] * sn;
+    si += re[a] * sn + im[a] * cs;
+  }
+  out[0] = sr / n;
+  out[1] = si / n;
+}
+
+__global__ void ves_features_kernel(int n, const double2 *x, const double *b, const double *A0,
+                                    double kb, double mu, double *frame, float *feat) {
+  __shared__ double X[kMaxN], Y[kMaxN], ZR[kMaxN], ZI[kMaxN], WR[kMaxN], WI[kMaxN];
+  __shared__ double fr[6];
+  const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  X[a] = x[i].x;
+  Y[a] = x[i].y;
+  __syncthreads();
+  if (a == 0) vesicle_frame(n, X, Y, A0[v], kb, mu, fr);
+  __syncthreads();
+  const double c = cos(fr[2]), s = sin(fr[2]);
+  const double dx = X[a] - fr[0], dy = Y[a] - fr[1];
+  ZR[a] = (c * dx + s * dy) / fr[3];
+  ZI[a] = (-s * dx + c * dy) / fr[3];
+  const double *bv = b + size_t(3) * n * v;
+  WR[a] = (c * bv[a] + s * bv[n + a]) / fr[4];
+  WI[a] = (-s * bv[a] + c * bv[n + a]) / fr[4];
+  __syncthreads();
+  if (a < kModes) {
+    double o[2];
+    dft_mode(n, a - 8, ZR, ZI, o);
+    feat[size_t(v) * kFeat + 2 * a] = float(o[0]);
+    feat[size_t(v) * kFeat + 2 * a + 1] = float(o[1]);
+    dft_mode(n, a - 8, WR, WI, o);
+    feat[size_t(v) * kFeat + 32 + 2 * a] = float(o[0]);
+    feat[size_t(v) * kFeat + 32 + 2 * a + 1] = float(o[1]);
+  }
+  if (a < 6) frame[v * 6 + a] = fr[a];
+}
+
+__global__ void ves_targets_kernel(int n, const double *z, const double *frame, float *targ) {
+  __shared__ double UR[kMaxN], UI[kMaxN], SG[kMaxN], ZERO[kMaxN];
+  const int v = blockIdx.x, a = threadIdx.x;
+  const double *fr = frame + v * 6;
+  const double c = cos(fr[2]), s = sin(fr[2]);
+  const double *zv = z + size_t(3) * n * v;
+  UR[a] = (c * zv[a] + s * zv[n + a]) / fr[4];
+  UI[a] = (-s * zv[a] + c * zv[n + a]) / fr[4];
+  SG[a] = zv[2 * n + a] / fr[5];
+  ZERO[a] = 0.0;
+  __syncthreads();
+  double o[2];
+  if (a < kModes) {
+    dft_mode(n, a - 8, UR, UI, o);
+    targ[size_t(v) * kTarg + 2 * a] = float(o[0]);
+    targ[size_t(v) * kTarg + 2 * a + 1] = float(o[1]);
+  } else if (a < kModes + 8) {
+    dft_mode(n, a - kModes, SG, ZERO, o);
+    targ[size_t(v) * kTarg + 32 + 2 * (a - kModes)] = float(o[0]);
+    targ[size_t(v) * kTarg + 32 + 2 * (a - kModes) + 1] = float(o[1]);
+  }
+}
+
+// Inverse of the targets' representation: predicted modes -> [u_x, u_y, sigma] at the nodes.
+__global__ void ves_guess_kernel(int n, const float *pred, const double *frame, double *z) {
+  const int v = blockIdx.x, a = threadIdx.x;
+  const double *fr = frame + v * 6;
+  const float *p = pred + size_t(v) * kTarg;
+  const double al = 2.0 * kPiD * a / n;
+  double ur = 0, ui = 0, sg = 0;
+  for (int q = 0; q < kModes; ++q) {
+    double sn, cs;
+    sincos((q - 8) * al, &sn, &cs);
+    ur += p[2 * q] * cs - p[2 * q + 1] * sn;
+    ui += p[2 * q] * sn + p[2 * q + 1] * cs;
+  }
+  for (int q = 0; q < 8; ++q) {
+    double sn, cs;
+    sincos(q * al, &sn, &cs);
+    sg += (q == 0 ? 1.0 : 2.0) * (p[32 + 2 * q] * cs - p[32 + 2 * q + 1] * sn);
+  }
+  const double c = cos(fr[2]), s = sin(fr[2]);
+  double *zv = z + size_t(3) * n * v;
+  zv[a] = fr[4] * (c * ur - s * ui);
+  zv[n + a] = fr[4] * (s * ur + c * ui);
+  zv[2 * n + a] = fr[5] * sg;
+}
+
 __global__ void extract_sigma_kernel(int n, const double *z, double *sigma) {
   const int v = blockIdx.x, a = threadIdx.x;
   sigma[v * n + a] = z[size_t(3) * n * v + 2 * n + a];
@@ -936,6 +1065,10 @@ void free_vesicles(stokes_sim *m) {
                    &m->d_G, &m->d_Ds, &m->d_D2, &m->d_D4, &m->d_T, &m->d_P, &m->d_Pinv, &m->d_V,
                    &m->d_z, &m->d_b, &m->d_wk, &m->d_h, &m->d_xsol};
   for (auto p : p1) dfree(*p);
+  dfree(m->d_feat);
+  dfree(m->d_targ);
+  dfree(m->d_pred);
+  dfree(m->d_frame);
   dfree(m->d_Pptr);
   dfree(m->d_Piptr);
   dfree(m->d_ppiv);
@@ -1183,6 +1316,10 @@ int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double
   SK(dalloc(m->d_h, m->gm_m + 1));
   SK(dalloc(m->d_xsol, len));
   SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
+  SK(dalloc(m->d_feat, size_t(V) * kFeat));
+  SK(dalloc(m->d_targ, size_t(V) * kTarg));
+  SK(dalloc(m->d_pred, size_t(V) * kTarg));
+  SK(dalloc(m->d_frame, size_t(V) * 6));
   SK(cudaStreamSynchronize(m->s));
   m->have_ves = true;
   return STOKES_OK;
@@ -1225,10 +1362,21 @@ int stokes_sim_empty_channel(stokes_sim *m, double p_drive, const double *v_wall
   return STOKES_OK;
 }
 
-int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, const double *guess,
-                           double tol, int max_iter, int precision, stokes_step_stats *out) {
+int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_mode,
+                           stokes_mlp *model, const double *guess, double tol, int max_iter,
+                           int precision, stokes_step_stats *out) {
   if (!m) return STOKES_ERR_ARG;
   if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  if (guess_mode < STOKES_GUESS_ZERO || guess_mode > STOKES_GUESS_USER)
+    return fail(m, STOKES_ERR_ARG, "unknown guess mode %d", guess_mode);
+  if (guess_mode == STOKES_GUESS_USER && !guess) return fail(m, STOKES_ERR_ARG, "guess is NULL");
+  if (guess_mode == STOKES_GUESS_MLP) {
+    if (!model) return fail(m, STOKES_ERR_ARG, "model is NULL");
+    int ni = 0, no = 0;
+    mlp_dims(model, &ni, &no);
+    if (ni != kFeat || no != kTarg || m->n < kModes)
+      return fail(m, STOKES_ERR_ARG, "model must map %d features to %d targets (n >= %d)", kFeat, kTarg, kModes);
+  }
   if (!(dt > 0.0) || !(tol > 0.0) || max_iter < 1)
     return fail(m, STOKES_ERR_ARG, "need dt > 0, tol > 0, max_iter >= 1");
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
@@ -1254,12 +1402,24 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, const doubl
   ves_rhs_kernel<<<V, n, 0, m->s>>>(n, m->d_tmp3, m->have_walls ? m->d_ures : nullptr, m->d_w,
                                     m->d_L0, dt, m->d_b, m->d_Lk);
   SK(cudaGetLastError());
-  // step 6: GMRES with the block-diagonal self preconditioner
+  // warm-start features of this step (principal-axes frame)
+  if (n >= kModes) {
+    ves_features_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_b, m->d_A0, m->kappa_b, m->mu,
+                                           m->d_frame, m->d_feat);
+    SK(cudaGetLastError());
+  }
+  // step 6: GMRES with the block-diagonal self preconditioner, from the chosen initial iterate
   ST(precond_build(m, dt));
-  if (guess)
+  if (guess_mode == STOKES_GUESS_USER) {
     SK(cudaMemcpyAsync(m->d_xsol, guess, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
-  else
+  } else if (guess_mode == STOKES_GUESS_MLP) {
+    int st = mlp_infer(model, V, m->d_feat, m->d_pred, m->s);
+    if (st) return fail(m, st, "warm-start network inference failed");
+    ves_guess_kernel<<<V, n, 0, m->s>>>(n, m->d_pred, m->d_frame, m->d_xsol);
+    SK(cudaGetLastError());
+  } else if (guess_mode == STOKES_GUESS_ZERO) {
     SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
+  }  // STOKES_GUESS_PREVIOUS: keep the previous solution in d_xsol
   SK(cudaStreamSynchronize(m->s));
   const auto t1 = std::chrono::steady_clock::now();
   int iters = 0;
@@ -1273,6 +1433,10 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, const doubl
     out->gmres_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
   }
   if (gst) return gst;
+  if (n >= kModes) {
+    ves_targets_kernel<<<V, n, 0, m->s>>>(n, m->d_xsol, m->d_frame, m->d_targ);
+    SK(cudaGetLastError());
+  }
   // steps 7-9: x <- x + dt u, area correction, reparameterization; sigma <- sigma^{k+1}
   ves_advance_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_xsol, m->d_D, m->d_A0, dt);
   ves_reparam_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D);
@@ -1281,6 +1445,19 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, const doubl
   SK(cudaStreamSynchronize(m->s));
   if (out)
     out->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return STOKES_OK;
+}
+
+int stokes_sim_last_features(stokes_sim *m, float *features, float *targets) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  if (m->n < kModes) return fail(m, STOKES_ERR_ARG, "features need n >= %d nodes per vesicle", kModes);
+  SK(cudaSetDevice(m->device));
+  if (features)
+    SK(cudaMemcpyAsync(features, m->d_feat, sizeof(float) * m->V * kFeat, cudaMemcpyDeviceToDevice, m->s));
+  if (targets)
+    SK(cudaMemcpyAsync(targets, m->d_targ, sizeof(float) * m->V * kTarg, cudaMemcpyDeviceToDevice, m->s));
+  SK(cudaStreamSynchronize(m->s));
   return STOKES_OK;
 }
 

@@ -1,0 +1,146 @@
+"""Learned warm start of the semi-implicit vesicle step: data, training, evaluation.
+
+Orchestration only: every numerical step runs in libstokes (the time step, the feature and
+target transforms, the network's forward/backward/Adam kernels).  PyTorch holds the device
+buffers; the shuffles are seeded NumPy permutations passed to the training kernels.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
+               STOKES_GUESS_ZERO, stokes_mlp_create, stokes_mlp_destroy,
+               stokes_mlp_fit_normalization, stokes_mlp_num_params, stokes_mlp_set_params,
+               stokes_mlp_train_step, stokes_sim_create, stokes_sim_destroy,
+               stokes_sim_get_state, stokes_sim_last_features, stokes_sim_set_state,
+               stokes_sim_set_vesicles, stokes_sim_set_walls, stokes_sim_sizes,
+               vesicle_step_warmstart)
+
+GUESS_NAMES = {"zero": STOKES_GUESS_ZERO, "previous": STOKES_GUESS_PREVIOUS, "mlp": STOKES_GUESS_MLP}
+
+
+class Simulation:
+    """A channel with vesicles (from an inputs.Geometry) on the GPU."""
+
+    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0):
+        walls = [c for c in geom.curves if c.kind == 0]
+        ves = [c for c in geom.curves if c.kind == 1]
+        self.h = stokes_sim_create(device)
+        self.mu, self.period = geom.mu, geom.period
+        if walls:
+            lo, up = walls
+            stokes_sim_set_walls(self.h, lo.n, np.vstack([lo.nodes, up.nodes]),
+                                 np.concatenate([lo.weights, up.weights]),
+                                 np.vstack([lo.normals, up.normals]),
+                                 np.concatenate([lo.curvature, up.curvature]), geom.period,
+                                 geom.mu, K, M)
+        self.x0 = np.vstack([c.nodes for c in ves])
+        stokes_sim_set_vesicles(self.h, len(ves), ves[0].n, self.x0, kappa_b, geom.mu, geom.period)
+        self.V, self.n, _ = stokes_sim_sizes(self.h)
+
+    def step(self, dt, p_drive, guess="zero", model=None, tol=1e-10, max_iter=500,
+             precision=STOKES_FP64):
+        return vesicle_step_warmstart(self.h, dt, p_drive, GUESS_NAMES[guess], model, None, tol,
+                                      max_iter, precision)
+
+    def state(self):
+        return stokes_sim_get_state(self.h)
+
+    def set_state(self, x, sigma):
+        stokes_sim_set_state(self.h, x, sigma)
+
+    def features(self, feat, targ):
+        stokes_sim_last_features(self.h, feat, targ)
+
+    def close(self):
+        if getattr(self, "h", None):
+            stokes_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def collect(sim: Simulation, steps, dt, p_drive, guess="previous", tol=1e-10):
+    """Run plain steps; return device tensors (features, targets) of every vesicle state and
+    the per-step statistics."""
+    import torch
+    V = sim.V
+    X = torch.empty((steps * V, N_FEATURES), dtype=torch.float32, device="cuda")
+    T = torch.empty((steps * V, N_TARGETS), dtype=torch.float32, device="cuda")
+    stats = []
+    for k in range(steps):
+        stats.append(sim.step(dt, p_drive, guess, tol=tol))
+        sim.features(X[k * V:(k + 1) * V], T[k * V:(k + 1) * V])
+    return X, T, stats
+
+
+class WarmStartNet:
+    """The 64 -> H -> H -> 48 network; parameters initialised from a seeded NumPy draw."""
+
+    def __init__(self, hidden=256, seed=0, device=0):
+        self.h = stokes_mlp_create(device, N_FEATURES, hidden, N_TARGETS)
+        self.hidden = hidden
+        rng = np.random.default_rng(seed)
+        theta = []
+        for fan_in, fan_out in ((N_FEATURES, hidden), (hidden, hidden), (hidden, N_TARGETS)):
+            lim = np.sqrt(6.0 / (fan_in + fan_out))
+            theta.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+            theta.append(np.zeros(fan_out))
+        stokes_mlp_set_params(self.h, np.concatenate(theta).astype(np.float32))
+        assert stokes_mlp_num_params(self.h) == sum(t.size for t in theta)
+
+    def fit(self, X, T, epochs=30, batch=256, lr=2e-3, seed=1, lr_decay=0.97):
+        """Adam on shuffled minibatches; returns the per-epoch mean losses."""
+        import torch
+        stokes_mlp_fit_normalization(self.h, X, T)
+        rng = np.random.default_rng(seed)
+        rows = X.shape[0]
+        losses = []
+        for ep in range(epochs):
+            perm = torch.as_tensor(rng.permutation(rows).astype(np.int32), device="cuda")
+            tot, cnt = 0.0, 0
+            for b0 in range(0, rows - batch + 1, batch):
+                tot += stokes_mlp_train_step(self.h, X, T, perm[b0:b0 + batch], lr)
+                cnt += 1
+            losses.append(tot / max(cnt, 1))
+            lr *= lr_decay
+        return losses
+
+    def close(self):
+        if getattr(self, "h", None):
+            stokes_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def evaluate(sim: Simulation, x_start, sigma_start, steps, dt, p_drive, model=None,
+             guesses=("zero", "previous", "mlp"), tol=1e-10):
+    """From the same start state, run `steps` steps per guess kind; iterations and times."""
+    out = {}
+    for gname in guesses:
+        if gname == "mlp" and model is None:
+            continue
+        sim.set_state(x_start, sigma_start)
+        its, tms, gms = [], [], []
+        for k in range(steps):
+            # the first step of a "previous" run has no previous solution: start from zero
+            g = "zero" if (gname == "previous" and k == 0) else gname
+            t0 = time.perf_counter()
+            st = sim.step(dt, p_drive, g, model=model.h if model is not None else None, tol=tol)
+            tms.append(1e3 * (time.perf_counter() - t0))
+            its.append(st["iterations"])
+            gms.append(st["gmres_ms"])
+        out[gname] = {"iterations": its, "mean_iterations": float(np.mean(its)),
+                      "step_ms": float(np.mean(tms)), "gmres_ms": float(np.mean(gms))}
+    return out

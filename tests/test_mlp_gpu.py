@@ -1,0 +1,122 @@
+"""Warm-start network kernels against the FP64 oracle, and the gain of the trained network."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1510_05616_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_05616_gb300 import build
+    build.build()
+    import paper_1510_05616_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def M():
+    from oracle import mlp_oracle
+    return mlp_oracle
+
+
+def cuda32(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _net(P, rng, n_in=64, H=96, n_out=48):
+    h = P.stokes_mlp_create(0, n_in, H, n_out)
+    n = P.stokes_mlp_num_params(h)
+    theta = (rng.normal(scale=0.15, size=n)).astype(np.float32)
+    P.stokes_mlp_set_params(h, theta)
+    norm = np.concatenate([rng.normal(size=n_in), rng.uniform(0.5, 2, n_in),
+                           rng.normal(size=n_out), rng.uniform(0.5, 2, n_out)]).astype(np.float32)
+    P.stokes_mlp_set_normalization(h, norm)
+    return h, theta, norm, (n_in, H, n_out)
+
+
+def test_forward_and_gradient_match_oracle(P, M):
+    rng = np.random.default_rng(0)
+    h, theta, norm, dims = _net(P, rng)
+    n_in, H, n_out = dims
+    B = 37  # ragged against the 32-wide GEMM tiles
+    X = rng.normal(size=(B, n_in)).astype(np.float32)
+    T = rng.normal(size=(B, n_out)).astype(np.float32)
+    mu_i, sd_i = norm[:n_in], norm[n_in:2 * n_in]
+    mu_o, sd_o = norm[2 * n_in:2 * n_in + n_out], norm[2 * n_in + n_out:]
+    xh = (X.astype(np.float64) - mu_i) / sd_i
+    th = (T.astype(np.float64) - mu_o) / sd_o
+    # forward
+    import torch
+    Y = torch.empty((B, n_out), dtype=torch.float32, device="cuda")
+    P.stokes_mlp_forward(h, cuda32(X), Y)
+    yo, _ = M.forward(theta.astype(np.float64), dims, xh)
+    ref = mu_o + sd_o * yo
+    assert np.abs(Y.cpu().numpy() - ref).max() < 1e-4 * np.abs(ref).max()
+    # loss and gradient
+    loss, g = P.stokes_mlp_loss_grad(h, cuda32(X), cuda32(T), batch=B)
+    lo, go = M.loss_and_grad(theta.astype(np.float64), dims, xh, th)
+    assert abs(loss - lo) < 1e-5 * lo
+    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+    P.stokes_mlp_destroy(h)
+
+
+def test_gather_and_adam_step_match_oracle(P, M):
+    rng = np.random.default_rng(1)
+    h, theta, norm, dims = _net(P, rng, H=40)
+    n_in, H, n_out = dims
+    rows = 300
+    X = rng.normal(size=(rows, n_in)).astype(np.float32)
+    T = rng.normal(size=(rows, n_out)).astype(np.float32)
+    idx = rng.permutation(rows)[:64].astype(np.int32)
+    import torch
+    lr = 1e-3
+    loss0, g_gpu = P.stokes_mlp_loss_grad(h, cuda32(X), cuda32(T), torch.as_tensor(idx, device="cuda"))
+    mu_i, sd_i = norm[:n_in], norm[n_in:2 * n_in]
+    mu_o, sd_o = norm[2 * n_in:2 * n_in + n_out], norm[2 * n_in + n_out:]
+    lo, go = M.loss_and_grad(theta.astype(np.float64), dims, (X[idx] - mu_i) / sd_i, (T[idx] - mu_o) / sd_o)
+    assert abs(loss0 - lo) < 1e-5 * lo
+    P.stokes_mlp_train_step(h, cuda32(X), cuda32(T), torch.as_tensor(idx, device="cuda"), lr)
+    th1 = P.stokes_mlp_get_params(h)
+    ref, _, _ = M.adam(theta.astype(np.float64), g_gpu.astype(np.float64), np.zeros(len(theta)),
+                       np.zeros(len(theta)), 1, lr)
+    assert np.abs(th1 - ref).max() < 1e-6
+    P.stokes_mlp_destroy(h)
+
+
+def _sim(P, seed):
+    from paper_1510_05616_gb300 import warmstart as WS
+    g = I.channel(96, I.WALL_SHAPE_SMALL, 8, 32, 0.04, seed)
+    return WS.Simulation(g, kappa_b=1.0, K=24, M=96)
+
+
+def test_trained_warm_start_saves_gmres_iterations(P):
+    """Trained on plain runs of two channels, the network's guess needs fewer GMRES iterations
+    than the zero guess on a third, unseen channel, at the same tolerance."""
+    import torch
+    from paper_1510_05616_gb300 import warmstart as WS
+    dt, pd = 1e-3, 2.0 * 1.0 * 2 * math.pi * 0.2
+    Xs, Ts = [], []
+    for seed in (11, 12):
+        sim = _sim(P, seed)
+        X, T, _ = WS.collect(sim, 60, dt, pd)
+        Xs.append(X)
+        Ts.append(T)
+        sim.close()
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    net = WS.WarmStartNet(hidden=128, seed=0)
+    losses = net.fit(X, T, epochs=60, batch=64, lr=2e-3)
+    assert losses[-1] < 0.2 * losses[0]
+    sim = _sim(P, 13)
+    x0, s0, _ = sim.state()
+    res = WS.evaluate(sim, x0, s0, 8, dt, pd, model=net, guesses=("zero", "mlp"))
+    sim.close()
+    net.close()
+    assert res["mlp"]["mean_iterations"] < res["zero"]["mean_iterations"], res

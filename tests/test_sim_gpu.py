@@ -117,7 +117,7 @@ def test_free_step_parity(P, S, period):
     _, ves = _case(n_ves=3, n_v=16)
     dt = 1e-3
     h = make_sim(P, None, ves, period=period)
-    st = P.vesicle_step_warmstart(h, dt, 0.0, None, 1e-12, 200)
+    st = P.vesicle_step_warmstart(h, dt, 0.0, tol=1e-12, max_iter=200)
     x, sg, sol = P.stokes_sim_get_state(h)
     P.stokes_sim_destroy(h)
     ox, osg, u, sig, _ = _oracle_step(S, [c.nodes for c in ves], dt, period=period)
@@ -134,7 +134,7 @@ def test_channel_step_parity(P, S):
     walls, ves = _case(n_ves=2, n_v=16, n_w=64)
     dt, pd = 1e-3, 0.5
     h = make_sim(P, walls, ves)
-    st = P.vesicle_step_warmstart(h, dt, pd, None, 1e-12, 200)
+    st = P.vesicle_step_warmstart(h, dt, pd, tol=1e-12, max_iter=200)
     x, sg, sol = P.stokes_sim_get_state(h)
     P.stokes_sim_destroy(h)
     ox, osg, u, sig, ures = _oracle_step(S, [c.nodes for c in ves], dt, walls, pd)
@@ -151,10 +151,10 @@ def test_warm_start_with_solution_converges_at_once(P):
     walls, ves = _case(n_ves=3, n_v=16)
     h = make_sim(P, walls, ves)
     x0 = np.vstack([c.nodes for c in ves])
-    st0 = P.vesicle_step_warmstart(h, 1e-3, 0.5, None, 1e-10, 200)
+    st0 = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-10, max_iter=200)
     _, _, sol = P.stokes_sim_get_state(h)
     P.stokes_sim_set_state(h, x0, np.zeros(len(x0)))
-    st1 = P.vesicle_step_warmstart(h, 1e-3, 0.5, dev(sol), 1e-10, 200)
+    st1 = P.vesicle_step_warmstart(h, 1e-3, 0.5, P.STOKES_GUESS_USER, guess=dev(sol), tol=1e-10, max_iter=200)
     P.stokes_sim_destroy(h)
     assert st0["iterations"] >= 3 and st1["iterations"] <= 1
 
@@ -166,7 +166,7 @@ def test_several_steps_conserve_area_and_length(P, S):
     A0 = [S.area(x) for x in x0]
     L0 = [S.perimeter(x) for x in x0]
     for _ in range(5):
-        P.vesicle_step_warmstart(h, 1e-3, 1.0, None, 1e-10, 300)
+        P.vesicle_step_warmstart(h, 1e-3, 1.0, tol=1e-10, max_iter=300)
     x, _, _ = P.stokes_sim_get_state(h)
     P.stokes_sim_destroy(h)
     for v in range(3):
