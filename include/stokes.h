@@ -291,7 +291,7 @@ typedef struct stokes_mlp stokes_mlp;
 typedef enum {
     STOKES_GUESS_ZERO = 0,      /* zero (the paper's plain method)                             */
     STOKES_GUESS_PREVIOUS = 1,  /* the previous step's solution                                */
-    STOKES_GUESS_MLP = 2,       /* the warm-start network's prediction from the step's features */
+    STOKES_GUESS_MLP = 2,       /* previous solution + the network's predicted change           */
     STOKES_GUESS_USER = 3       /* the caller's DEVICE vector `guess`                          */
 } stokes_guess;
 
@@ -329,13 +329,16 @@ STOKES_API int stokes_sim_empty_channel(stokes_sim *sim, double p_drive, const d
 STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive, int guess_mode,
                                       stokes_mlp *model, const double *guess, double tol,
                                       int max_iter, int precision, stokes_step_stats *stats);
-/* Warm-start features and targets of the last step (DEVICE FP32; either may be NULL):
+/* Warm-start features and targets of the last step (DEVICE FP32; either may be NULL).  The
+ * network predicts the change of the solution since the previous step (the learned guess is
+ * z_prev + predicted change; z_prev = 0 and b_prev = 0 after stokes_sim_set_vesicles or
+ * stokes_sim_set_state):
  * features (V x 64): per vesicle, in its principal-axes frame (centre c, angle theta of the
  *   second moments, length l = sqrt(A0 / pi)), the Fourier modes k = -8..7 (re, im) of the
- *   complex shape (x' + i y') / l, then of the step's explicit velocity (S f_b + u_resp)
- *   rotated to the frame over U = kappa_B / (mu l^2);
- * targets (V x 48): modes k = -8..7 of the solved velocity (frame, / U), then k = 0..7 of the
- *   tension / (kappa_B / l^2).  The network predicts targets from features. */
+ *   complex shape (x' + i y') / l, then of the change of the step's explicit velocity
+ *   (S f_b + u_resp) since the previous step, rotated to the frame, over U = kappa_B/(mu l^2);
+ * targets (V x 48): modes k = -8..7 of the change of the solved velocity (frame, / U), then
+ *   k = 0..7 of the change of the tension / (kappa_B / l^2). */
 STOKES_API int stokes_sim_last_features(stokes_sim *sim, float *features, float *targets);
 
 /* Warm-start network: 64 -> H -> H -> 48 with SiLU, BF16 weights, FP32 accumulation, FP32

@@ -76,6 +76,7 @@ struct stokes_sim {
   // warm-start features / targets of the last step
   float *d_feat = nullptr, *d_targ = nullptr, *d_pred = nullptr;
   double *d_frame = nullptr;           // per vesicle: cx, cy, theta, l, U, sigma scale
+  double *d_bprev = nullptr, *d_zprev = nullptr;  // previous step's right-hand side and solution
 };
 
 namespace {
@@ -733,8 +734,9 @@ __device__ void dft_mode(int n, int k, const double *re, const double *im, doubl
   out[1] = si / n;
 }
 
-__global__ void ves_features_kernel(int n, const double2 *x, const double *b, const double *A0,
-                                    double kb, double mu, double *frame, float *feat) {
+__global__ void ves_features_kernel(int n, const double2 *x, const double *b, const double *bprev,
+                                    const double *A0, double kb, double mu, double *frame,
+                                    float *feat) {
   __shared__ double X[kMaxN], Y[kMaxN], ZR[kMaxN], ZI[kMaxN], WR[kMaxN], WI[kMaxN];
   __shared__ double fr[6];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
@@ -747,9 +749,10 @@ __global__ void ves_features_kernel(int n, const double2 *x, const double *b, co
   const double dx = X[a] - fr[0], dy = Y[a] - fr[1];
   ZR[a] = (c * dx + s * dy) / fr[3];
   ZI[a] = (-s * dx + c * dy) / fr[3];
-  const double *bv = b + size_t(3) * n * v;
-  WR[a] = (c * bv[a] + s * bv[n + a]) / fr[4];
-  WI[a] = (-s * bv[a] + c * bv[n + a]) / fr[4];
+  const double *bv = b + size_t(3) * n * v, *pv = bprev + size_t(3) * n * v;
+  const double dbx = bv[a] - pv[a], dby = bv[n + a] - pv[n + a];
+  WR[a] = (c * dbx + s * dby) / fr[4];
+  WI[a] = (-s * dbx + c * dby) / fr[4];
   __syncthreads();
   if (a < kModes) {
     double o[2];
@@ -763,15 +766,17 @@ __global__ void ves_features_kernel(int n, const double2 *x, const double *b, co
   if (a < 6) frame[v * 6 + a] = fr[a];
 }
 
-__global__ void ves_targets_kernel(int n, const double *z, const double *frame, float *targ) {
+__global__ void ves_targets_kernel(int n, const double *z, const double *zprev, const double *frame,
+                                   float *targ) {
   __shared__ double UR[kMaxN], UI[kMaxN], SG[kMaxN], ZERO[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x;
   const double *fr = frame + v * 6;
   const double c = cos(fr[2]), s = sin(fr[2]);
-  const double *zv = z + size_t(3) * n * v;
-  UR[a] = (c * zv[a] + s * zv[n + a]) / fr[4];
-  UI[a] = (-s * zv[a] + c * zv[n + a]) / fr[4];
-  SG[a] = zv[2 * n + a] / fr[5];
+  const double *zv = z + size_t(3) * n * v, *pv = zprev + size_t(3) * n * v;
+  const double dux = zv[a] - pv[a], duy = zv[n + a] - pv[n + a];
+  UR[a] = (c * dux + s * duy) / fr[4];
+  UI[a] = (-s * dux + c * duy) / fr[4];
+  SG[a] = (zv[2 * n + a] - pv[2 * n + a]) / fr[5];
   ZERO[a] = 0.0;
   __syncthreads();
   double o[2];
@@ -786,8 +791,9 @@ __global__ void ves_targets_kernel(int n, const double *z, const double *frame, 
   }
 }
 
-// Inverse of the targets' representation: predicted modes -> [u_x, u_y, sigma] at the nodes.
-__global__ void ves_guess_kernel(int n, const float *pred, const double *frame, double *z) {
+// Inverse of the targets' representation: z = z_prev + (predicted change at the nodes).
+__global__ void ves_guess_kernel(int n, const float *pred, const double *frame, const double *zprev,
+                                 double *z) {
   const int v = blockIdx.x, a = threadIdx.x;
   const double *fr = frame + v * 6;
   const float *p = pred + size_t(v) * kTarg;
@@ -806,9 +812,10 @@ __global__ void ves_guess_kernel(int n, const float *pred, const double *frame, 
   }
   const double c = cos(fr[2]), s = sin(fr[2]);
   double *zv = z + size_t(3) * n * v;
-  zv[a] = fr[4] * (c * ur - s * ui);
-  zv[n + a] = fr[4] * (s * ur + c * ui);
-  zv[2 * n + a] = fr[5] * sg;
+  const double *pv = zprev + size_t(3) * n * v;
+  zv[a] = pv[a] + fr[4] * (c * ur - s * ui);
+  zv[n + a] = pv[n + a] + fr[4] * (s * ur + c * ui);
+  zv[2 * n + a] = pv[2 * n + a] + fr[5] * sg;
 }
 
 __global__ void extract_sigma_kernel(int n, const double *z, double *sigma) {
@@ -1069,6 +1076,8 @@ void free_vesicles(stokes_sim *m) {
   dfree(m->d_targ);
   dfree(m->d_pred);
   dfree(m->d_frame);
+  dfree(m->d_bprev);
+  dfree(m->d_zprev);
   dfree(m->d_Pptr);
   dfree(m->d_Piptr);
   dfree(m->d_ppiv);
@@ -1320,6 +1329,10 @@ int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double
   SK(dalloc(m->d_targ, size_t(V) * kTarg));
   SK(dalloc(m->d_pred, size_t(V) * kTarg));
   SK(dalloc(m->d_frame, size_t(V) * 6));
+  SK(dalloc(m->d_bprev, len));
+  SK(dalloc(m->d_zprev, len));
+  SK(cudaMemsetAsync(m->d_bprev, 0, sizeof(double) * len, m->s));
+  SK(cudaMemsetAsync(m->d_zprev, 0, sizeof(double) * len, m->s));
   SK(cudaStreamSynchronize(m->s));
   m->have_ves = true;
   return STOKES_OK;
@@ -1404,8 +1417,8 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   SK(cudaGetLastError());
   // warm-start features of this step (principal-axes frame)
   if (n >= kModes) {
-    ves_features_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_b, m->d_A0, m->kappa_b, m->mu,
-                                           m->d_frame, m->d_feat);
+    ves_features_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_b, m->d_bprev, m->d_A0, m->kappa_b,
+                                           m->mu, m->d_frame, m->d_feat);
     SK(cudaGetLastError());
   }
   // step 6: GMRES with the block-diagonal self preconditioner, from the chosen initial iterate
@@ -1415,11 +1428,13 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   } else if (guess_mode == STOKES_GUESS_MLP) {
     int st = mlp_infer(model, V, m->d_feat, m->d_pred, m->s);
     if (st) return fail(m, st, "warm-start network inference failed");
-    ves_guess_kernel<<<V, n, 0, m->s>>>(n, m->d_pred, m->d_frame, m->d_xsol);
+    ves_guess_kernel<<<V, n, 0, m->s>>>(n, m->d_pred, m->d_frame, m->d_zprev, m->d_xsol);
     SK(cudaGetLastError());
   } else if (guess_mode == STOKES_GUESS_ZERO) {
     SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
-  }  // STOKES_GUESS_PREVIOUS: keep the previous solution in d_xsol
+  } else {
+    SK(cudaMemcpyAsync(m->d_xsol, m->d_zprev, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  }
   SK(cudaStreamSynchronize(m->s));
   const auto t1 = std::chrono::steady_clock::now();
   int iters = 0;
@@ -1434,9 +1449,11 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   }
   if (gst) return gst;
   if (n >= kModes) {
-    ves_targets_kernel<<<V, n, 0, m->s>>>(n, m->d_xsol, m->d_frame, m->d_targ);
+    ves_targets_kernel<<<V, n, 0, m->s>>>(n, m->d_xsol, m->d_zprev, m->d_frame, m->d_targ);
     SK(cudaGetLastError());
   }
+  SK(cudaMemcpyAsync(m->d_bprev, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  SK(cudaMemcpyAsync(m->d_zprev, m->d_xsol, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
   // steps 7-9: x <- x + dt u, area correction, reparameterization; sigma <- sigma^{k+1}
   ves_advance_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_xsol, m->d_D, m->d_A0, dt);
   ves_reparam_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D);
@@ -1479,6 +1496,9 @@ int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigm
   SK(cudaSetDevice(m->device));
   if (x_host) SK(cudaMemcpy(m->d_x, x_host, sizeof(double2) * m->Nv, cudaMemcpyHostToDevice));
   if (sigma_host) SK(cudaMemcpy(m->d_sigma, sigma_host, sizeof(double) * m->Nv, cudaMemcpyHostToDevice));
+  // a new start: no previous step
+  SK(cudaMemset(m->d_bprev, 0, sizeof(double) * 3 * m->Nv));
+  SK(cudaMemset(m->d_zprev, 0, sizeof(double) * 3 * m->Nv));
   return STOKES_OK;
 }
 

@@ -98,13 +98,14 @@ def _sim(P, seed):
 
 
 def test_trained_warm_start_saves_gmres_iterations(P):
-    """Trained on plain runs of two channels, the network's guess needs fewer GMRES iterations
-    than the zero guess on a third, unseen channel, at the same tolerance."""
+    """Trained on plain runs of four channels, the network's guess (previous solution plus the
+    predicted change) needs fewer GMRES iterations than the paper's zero guess on a fifth,
+    unseen channel, at the same tolerance."""
     import torch
     from paper_1510_05616_gb300 import warmstart as WS
     dt, pd = 1e-3, 2.0 * 1.0 * 2 * math.pi * 0.2
     Xs, Ts = [], []
-    for seed in (11, 12):
+    for seed in (11, 12, 14, 15):
         sim = _sim(P, seed)
         X, T, _ = WS.collect(sim, 60, dt, pd)
         Xs.append(X)
@@ -112,11 +113,11 @@ def test_trained_warm_start_saves_gmres_iterations(P):
         sim.close()
     X, T = torch.cat(Xs), torch.cat(Ts)
     net = WS.WarmStartNet(hidden=128, seed=0)
-    losses = net.fit(X, T, epochs=60, batch=64, lr=2e-3)
+    losses = net.fit(X, T, epochs=80, batch=64, lr=2e-3)
     assert losses[-1] < 0.2 * losses[0]
     sim = _sim(P, 13)
     x0, s0, _ = sim.state()
-    res = WS.evaluate(sim, x0, s0, 8, dt, pd, model=net, guesses=("zero", "mlp"))
+    res = WS.evaluate(sim, x0, s0, 10, dt, pd, model=net, guesses=("zero", "mlp"))
     sim.close()
     net.close()
     assert res["mlp"]["mean_iterations"] < res["zero"]["mean_iterations"], res
