@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -281,6 +282,63 @@ def run_batch(args):
     return 0
 
 
+def run_step(args):
+    """Algorithm 1 on a channel (walls, channel response, GMRES to 1e-10): plain runs give the
+    training states, the network is trained with the library's kernels, and a held-out channel
+    is stepped from the same state with the zero, previous-step and network guesses."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    from paper_1510_05616_gb300 import warmstart as WS
+    B.build()
+    n_w, modes, nv, n_v, area = I.WORKLOADS[args.step_workload]
+    dt, mu = 1e-3, 1.0
+    pd = 2 * mu * 2 * math.pi * 0.2
+    res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "tol": 1e-10}
+    t0 = time.perf_counter()
+    Xs, Ts, plain_its = [], [], []
+    for r in range(args.train_runs):
+        g = I.channel(n_w, modes, nv, n_v, area, 1000 + r, mu=mu)
+        ts = time.perf_counter()
+        sim = WS.Simulation(g)
+        res.setdefault("setup_s", time.perf_counter() - ts)
+        X, T, st = WS.collect(sim, args.train_steps, dt, pd)
+        plain_its += [x["iterations"] for x in st]
+        Xs.append(X)
+        Ts.append(T)
+        sim.close()
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    res["collect_s"] = time.perf_counter() - t0
+    net = WS.WarmStartNet(hidden=256, seed=0)
+    t1 = time.perf_counter()
+    losses = net.fit(X, T, epochs=40, batch=256, lr=2e-3)
+    torch.cuda.synchronize()
+    res["train"] = {"samples": int(X.shape[0]), "epochs": 40, "batch": 256,
+                    "adam_steps": 40 * (int(X.shape[0]) // 256), "seconds": time.perf_counter() - t1,
+                    "loss_first": losses[0], "loss_last": losses[-1]}
+    g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
+    sim = WS.Simulation(g)
+    x0, s0, _ = sim.state()
+    ev = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net)
+    sim.close()
+    net.close()
+    res["eval"] = ev
+    z = ev["zero"]
+    line = {"metric": "semi-implicit vesicle step, GMRES to 1e-10: mean iterations and ms per step",
+            "value": z["step_ms"], "unit": "ms/step (zero guess)", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESCS[args.step_workload], "vesicles": nv,
+                       "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w},
+            "guesses": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
+                            "gmres_ms": v["gmres_ms"]} for k, v in ev.items()},
+            "iterations_saved_vs_zero": {k: z["mean_iterations"] - v["mean_iterations"]
+                                         for k, v in ev.items()},
+            "details": res}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,11 +352,18 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
     ap.add_argument("--batch", action="store_true",
                     help="time the 64-channel batched ensemble instead (separate JSON line)")
+    ap.add_argument("--step", action="store_true",
+                    help="time the semi-implicit vesicle step with the learned warm start instead")
+    ap.add_argument("--step-workload", default="mid_n16k", choices=["mid_n16k", "small_n1280"])
+    ap.add_argument("--train-runs", type=int, default=2)
+    ap.add_argument("--train-steps", type=int, default=40)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.step:
+        return run_step(args)
 
     import torch
     ws, rank, local = dist_env()
