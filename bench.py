@@ -293,15 +293,18 @@ def run_step(args):
     from paper_1510_05616_gb300 import warmstart as WS
     B.build()
     n_w, modes, nv, n_v, area = I.WORKLOADS[args.step_workload]
-    dt, mu = 1e-3, 1.0
+    # bending modulus scaled to the vesicle size: with kappa_B = 1 the bending velocity
+    # kappa_B / (mu R^2) of R ~ 0.07 vesicles is ~200, and the explicit channel response moves a
+    # vesicle across its wall gap within one step of dt = 1e-3
+    dt, mu, kb = 1e-3, 1.0, 0.01
     pd = 2 * mu * 2 * math.pi * 0.2
-    res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "tol": 1e-10}
+    res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
         g = I.channel(n_w, modes, nv, n_v, area, 1000 + r, mu=mu)
         ts = time.perf_counter()
-        sim = WS.Simulation(g)
+        sim = WS.Simulation(g, kappa_b=kb, restart=200)
         res.setdefault("setup_s", time.perf_counter() - ts)
         X, T, st = WS.collect(sim, args.train_steps, dt, pd)
         plain_its += [x["iterations"] for x in st]
@@ -318,7 +321,7 @@ def run_step(args):
                     "adam_steps": 40 * (int(X.shape[0]) // 256), "seconds": time.perf_counter() - t1,
                     "loss_first": losses[0], "loss_last": losses[-1]}
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
-    sim = WS.Simulation(g)
+    sim = WS.Simulation(g, kappa_b=kb, restart=200)
     x0, s0, _ = sim.state()
     ev = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net)
     sim.close()

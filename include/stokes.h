@@ -368,6 +368,8 @@ STOKES_API int stokes_mlp_train_step(stokes_mlp *mlp, int rows, const float *X, 
  * step's solution [u_x, u_y, sigma] per vesicle (3 n V). */
 STOKES_API int stokes_sim_get_state(stokes_sim *sim, double *x, double *sigma, double *solution);
 STOKES_API int stokes_sim_set_state(stokes_sim *sim, const double *x, const double *sigma);
+/* Krylov subspace length of the step's restarted GMRES (default 80; storage 3 n V (m + 1)). */
+STOKES_API int stokes_sim_set_restart(stokes_sim *sim, int restart);
 STOKES_API int stokes_sim_sizes(const stokes_sim *sim, int *n_vesicles, int *nodes_per_vesicle,
                                 int *wall_nodes);
 

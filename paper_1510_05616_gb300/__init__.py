@@ -96,6 +96,7 @@ _SIGNATURES = {
     "stokes_sim_get_state": [_vp, _vp, _vp, _vp],
     "stokes_sim_set_state": [_vp, _vp, _vp],
     "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
+    "stokes_sim_set_restart": [_vp, _c_int],
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
 }
 
@@ -507,6 +508,10 @@ def stokes_mlp_train_step(h, X, T, idx, lr):
                                                _fptr(idx, "idx"), int(idx.shape[0]), float(lr),
                                                _vp(loss.ctypes.data)))
     return float(loss[0])
+
+
+def stokes_sim_set_restart(h, restart):
+    return _sim_check(h, load().stokes_sim_set_restart(h, int(restart)))
 
 
 def stokes_sim_sizes(h):

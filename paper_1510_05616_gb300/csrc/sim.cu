@@ -1502,6 +1502,18 @@ int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigm
   return STOKES_OK;
 }
 
+int stokes_sim_set_restart(stokes_sim *m, int restart) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  if (restart < 2 || restart > 2000) return fail(m, STOKES_ERR_ARG, "restart must be in [2, 2000]");
+  SK(cudaSetDevice(m->device));
+  SK(cudaStreamSynchronize(m->s));
+  SK(dalloc(m->d_V, size_t(3) * m->Nv * (restart + 1)));
+  SK(dalloc(m->d_h, restart + 1));
+  m->gm_m = restart;
+  return STOKES_OK;
+}
+
 int stokes_sim_sizes(const stokes_sim *m, int *n_vesicles, int *nodes_per_vesicle,
                      int *wall_nodes) {
   if (!m || !n_vesicles || !nodes_per_vesicle || !wall_nodes) return STOKES_ERR_ARG;

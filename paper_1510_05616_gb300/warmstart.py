@@ -11,7 +11,7 @@ import time
 import numpy as np
 
 from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
-               STOKES_GUESS_ZERO, stokes_mlp_create, stokes_mlp_destroy,
+               STOKES_GUESS_ZERO, stokes_mlp_create, stokes_mlp_destroy, stokes_sim_set_restart,
                stokes_mlp_fit_normalization, stokes_mlp_num_params, stokes_mlp_set_params,
                stokes_mlp_train_step, stokes_sim_create, stokes_sim_destroy,
                stokes_sim_get_state, stokes_sim_last_features, stokes_sim_set_state,
@@ -24,7 +24,7 @@ GUESS_NAMES = {"zero": STOKES_GUESS_ZERO, "previous": STOKES_GUESS_PREVIOUS, "ml
 class Simulation:
     """A channel with vesicles (from an inputs.Geometry) on the GPU."""
 
-    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0):
+    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80):
         walls = [c for c in geom.curves if c.kind == 0]
         ves = [c for c in geom.curves if c.kind == 1]
         self.h = stokes_sim_create(device)
@@ -39,6 +39,8 @@ class Simulation:
         self.x0 = np.vstack([c.nodes for c in ves])
         stokes_sim_set_vesicles(self.h, len(ves), ves[0].n, self.x0, kappa_b, geom.mu, geom.period)
         self.V, self.n, _ = stokes_sim_sizes(self.h)
+        if restart != 80:
+            stokes_sim_set_restart(self.h, restart)
 
     def step(self, dt, p_drive, guess="zero", model=None, tol=1e-10, max_iter=500,
              precision=STOKES_FP64):
