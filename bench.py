@@ -324,9 +324,11 @@ def run_step(args):
     sim = WS.Simulation(g, kappa_b=kb, restart=200)
     x0, s0, _ = sim.state()
     ev = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net)
+    ev32 = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=P.STOKES_FP32_KAHAN)
     sim.close()
     net.close()
     res["eval"] = ev
+    res["eval_mixed_precision"] = ev32
     z = ev["zero"]
     line = {"metric": "semi-implicit vesicle step, GMRES to 1e-10: mean iterations and ms per step",
             "value": z["step_ms"], "unit": "ms/step (zero guess)", "higher_is_better": False,
@@ -337,6 +339,8 @@ def run_step(args):
                             "gmres_ms": v["gmres_ms"]} for k, v in ev.items()},
             "iterations_saved_vs_zero": {k: z["mean_iterations"] - v["mean_iterations"]
                                          for k, v in ev.items()},
+            "mixed_precision": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
+                                    "gmres_ms": v["gmres_ms"]} for k, v in ev32.items()},
             "details": res}
     print(json.dumps(line))
     return 0

@@ -328,7 +328,7 @@ def stokes_batch_info(h, precision):
 # ---------------------------------------------------------------------------
 class StepStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("residual", _c_double), ("setup_ms", _c_double),
-                ("gmres_ms", _c_double), ("total_ms", _c_double)]
+                ("gmres_ms", _c_double), ("total_ms", _c_double), ("refinements", _c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

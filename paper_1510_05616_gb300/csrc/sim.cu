@@ -73,6 +73,7 @@ struct stokes_sim {
   int gm_m = 0;
   double *d_V = nullptr, *d_z = nullptr, *d_b = nullptr, *d_wk = nullptr, *d_h = nullptr;
   double *d_xsol = nullptr;            // last solution [u_x, u_y, sigma] per vesicle
+  double *d_rr = nullptr, *d_dd = nullptr;  // refinement residual and correction
   // warm-start features / targets of the last step
   float *d_feat = nullptr, *d_targ = nullptr, *d_pred = nullptr;
   double *d_frame = nullptr;           // per vesicle: cx, cy, theta, l, U, sigma scale
@@ -1070,7 +1071,7 @@ void free_vesicles(stokes_sim *m) {
   for (auto p : p2) dfree(*p);
   double **p1[] = {&m->d_w, &m->d_spd, &m->d_sigma, &m->d_D, &m->d_kress, &m->d_L0, &m->d_A0, &m->d_Lk,
                    &m->d_G, &m->d_Ds, &m->d_D2, &m->d_D4, &m->d_T, &m->d_P, &m->d_Pinv, &m->d_V,
-                   &m->d_z, &m->d_b, &m->d_wk, &m->d_h, &m->d_xsol};
+                   &m->d_z, &m->d_b, &m->d_wk, &m->d_h, &m->d_xsol, &m->d_rr, &m->d_dd};
   for (auto p : p1) dfree(*p);
   dfree(m->d_feat);
   dfree(m->d_targ);
@@ -1324,6 +1325,8 @@ int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double
   SK(dalloc(m->d_wk, len));
   SK(dalloc(m->d_h, m->gm_m + 1));
   SK(dalloc(m->d_xsol, len));
+  SK(dalloc(m->d_rr, len));
+  SK(dalloc(m->d_dd, len));
   SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
   SK(dalloc(m->d_feat, size_t(V) * kFeat));
   SK(dalloc(m->d_targ, size_t(V) * kTarg));
@@ -1437,15 +1440,49 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   }
   SK(cudaStreamSynchronize(m->s));
   const auto t1 = std::chrono::steady_clock::now();
-  int iters = 0;
+  int iters = 0, refinements = 0;
   double rel = 0.0;
-  const int gst = gmres(m, dt, precision, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
+  int gst = STOKES_OK;
+  if (precision == STOKES_FP64) {
+    gst = gmres(m, dt, STOKES_FP64, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
+  } else {
+    // Mixed precision: corrections from GMRES with FP32-Kahan pair sums, residuals of the FP64
+    // operator (iterative refinement), until the FP64 relative residual meets tol.
+    int st = STOKES_OK;
+    const double bn = dnrm(m, len, m->d_b, &st);
+    if (st) return fail(m, st, "cublasDnrm2 failed");
+    const double one = 1.0, mone = -1.0;
+    for (;;) {
+      ST(step_matvec(m, dt, STOKES_FP64, m->d_xsol, m->d_wk));
+      SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+      BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
+      const double rn = dnrm(m, len, m->d_rr, &st);
+      if (st) return fail(m, st, "cublasDnrm2 failed");
+      rel = bn > 0.0 ? rn / bn : 0.0;
+      if (rel <= tol) break;
+      if (iters >= max_iter || refinements >= 20) {
+        gst = fail(m, STOKES_ERR_NOT_CONVERGED, "mixed-precision GMRES: %d iterations, relative residual %.3e", iters, rel);
+        break;
+      }
+      // inner solve to 1e-6 relative (about the FP32-Kahan operator's accuracy), or just past tol
+      const double tin = std::max(1e-6, 0.5 * tol / rel);
+      SK(cudaMemsetAsync(m->d_dd, 0, sizeof(double) * len, m->s));
+      int it_in = 0;
+      double rel_in = 0.0;
+      const int gs = gmres(m, dt, STOKES_FP32_KAHAN, m->d_rr, m->d_dd, tin, max_iter - iters, &it_in, &rel_in);
+      iters += it_in;
+      ++refinements;
+      if (gs && gs != STOKES_ERR_NOT_CONVERGED) return gs;
+      BK(cublasDaxpy(m->blas, int(len), &one, m->d_dd, 1, m->d_xsol, 1));
+    }
+  }
   const auto t2 = std::chrono::steady_clock::now();
   if (out) {
     out->iterations = iters;
     out->residual = rel;
     out->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     out->gmres_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    out->refinements = refinements;
   }
   if (gst) return gst;
   if (n >= kModes) {

@@ -127,7 +127,7 @@ class WarmStartNet:
 
 
 def evaluate(sim: Simulation, x_start, sigma_start, steps, dt, p_drive, model=None,
-             guesses=("zero", "previous", "mlp"), tol=1e-10):
+             guesses=("zero", "previous", "mlp"), tol=1e-10, precision=STOKES_FP64):
     """From the same start state, run `steps` steps per guess kind; iterations and times."""
     out = {}
     for gname in guesses:
@@ -139,7 +139,8 @@ def evaluate(sim: Simulation, x_start, sigma_start, steps, dt, p_drive, model=No
             # the first step of a "previous" run has no previous solution: start from zero
             g = "zero" if (gname == "previous" and k == 0) else gname
             t0 = time.perf_counter()
-            st = sim.step(dt, p_drive, g, model=model.h if model is not None else None, tol=tol)
+            st = sim.step(dt, p_drive, g, model=model.h if model is not None else None, tol=tol,
+                          precision=precision)
             tms.append(1e3 * (time.perf_counter() - t0))
             its.append(st["iterations"])
             gms.append(st["gmres_ms"])

@@ -184,3 +184,20 @@ def test_sim_errors(P):
     with pytest.raises(P.StokesError):
         P.stokes_sim_set_vesicles(h, 1, 15, np.zeros((15, 2)), 1.0, 1.0, 0.0)
     P.stokes_sim_destroy(h)
+
+
+def test_mixed_precision_step_meets_fp64_tolerance(P):
+    """FP32-Kahan Krylov iterations wrapped in FP64 refinement reach the same FP64 residual and
+    the same solution as the all-FP64 solve."""
+    walls, ves = _case(n_ves=4, n_v=32, n_w=96)
+    x0 = np.vstack([c.nodes for c in ves])
+    h = make_sim(P, walls, ves)
+    st64 = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300)
+    _, _, sol64 = P.stokes_sim_get_state(h)
+    P.stokes_sim_set_state(h, x0, np.zeros(len(x0)))
+    st32 = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300,
+                                    precision=P.STOKES_FP32_KAHAN)
+    _, _, sol32 = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    assert st32["residual"] <= 1e-11 and st32["refinements"] >= 1
+    assert np.abs(sol32 - sol64).max() < 1e-9 * np.abs(sol64).max()
