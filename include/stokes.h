@@ -276,9 +276,9 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  *   [I + dt kappa_B S d_ssss, -S d_s(x_s .); x_s . d_s, 0] [u; sigma] = [S f_b + u_resp; (L0-Lk)/(dt Lk)]
  * where S is the single layer of all vesicles with +-d images and Kress self terms.  With
  * precision STOKES_FP64 every GMRES matvec uses FP64 sums; with STOKES_FP32_KAHAN GMRES runs on
- * FP32-Kahan sums to 1e-6 and is wrapped in iterative refinement whose residuals use the FP64
- * operator, so the returned relative residual still meets tol in FP64.  Then x += dt u, area
- * correction (App. B) and
+ * FP32-Kahan sums to 1e-6 inside iterative refinement with FP64 residuals while each refinement
+ * cuts the residual 10x, then FP64 GMRES finishes from that iterate; either way the returned
+ * relative residual meets tol in FP64.  Then x += dt u, area correction (App. B) and
  * reparameterization (App. C, Algorithm 2).  d/ds = |x_alpha|^-1 d/d alpha by Fourier
  * differentiation.  The unknown vector, guesses and solutions are laid out per vesicle as
  * [u_x (n), u_y (n), sigma (n)], vesicle after vesicle (3 n V doubles).
@@ -304,7 +304,7 @@ typedef struct {
     double setup_ms;     /* forces, channel response, right-hand side, preconditioner   */
     double gmres_ms;     /* Krylov solve                                                 */
     double total_ms;     /* whole step including the position update                    */
-    int refinements;     /* FP64 residual refinements (STOKES_FP32_KAHAN steps), else 0  */
+    int refinements;     /* FP32-Kahan refinement sweeps (STOKES_FP32_KAHAN steps), else 0 */
 } stokes_step_stats;
 
 STOKES_API int stokes_sim_create(int device, stokes_sim **out);
