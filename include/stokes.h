@@ -276,7 +276,8 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  *   [I + dt kappa_B S d_ssss, -S d_s(x_s .); x_s . d_s, 0] [u; sigma] = [S f_b + u_resp; (L0-Lk)/(dt Lk)]
  * where S is the single layer of all vesicles with +-d images and Kress self terms.  With
  * precision STOKES_FP64 every GMRES matvec uses FP64 sums; with STOKES_FP32_KAHAN GMRES runs on
- * FP32-Kahan sums to 1e-6 inside iterative refinement with FP64 residuals while each refinement
+ * FP32-Kahan sums (to 1e-3, at most 40 iterations a sweep) inside iterative refinement with FP64
+ * residuals while each refinement
  * cuts the residual 10x, then FP64 GMRES finishes from that iterate; either way the returned
  * relative residual meets tol in FP64.  Then x += dt u, area correction (App. B) and
  * reparameterization (App. C, Algorithm 2).  d/ds = |x_alpha|^-1 d/d alpha by Fourier

@@ -1469,11 +1469,13 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
         break;
       }
       prev = rel;
-      const double tin = std::max(1e-6, 0.5 * tol / rel);
+      // inner solve to 1e-3: about what the FP32-Kahan operator resolves on stiff densities
+      const double tin = std::max(1e-3, 0.5 * tol / rel);
       SK(cudaMemsetAsync(m->d_dd, 0, sizeof(double) * len, m->s));
       int it_in = 0;
       double rel_in = 0.0;
-      const int gs = gmres(m, dt, STOKES_FP32_KAHAN, m->d_rr, m->d_dd, tin, max_iter - iters, &it_in, &rel_in);
+      const int gs = gmres(m, dt, STOKES_FP32_KAHAN, m->d_rr, m->d_dd, tin,
+                           std::min(40, max_iter - iters), &it_in, &rel_in);
       iters += it_in;
       ++refinements;
       if (gs && gs != STOKES_ERR_NOT_CONVERGED) return gs;
