@@ -110,6 +110,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(seconds, device=None):
+    """The slowest rank's time (all ranks must call); the single-rank value when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds)
+    t = torch.tensor([float(seconds)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world_size, seconds_max):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return world_size * units_per_rank / seconds_max
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("k_pair.cu", "stokes_internal.cuh"):
@@ -428,12 +445,8 @@ def main():
     P.stokes_set_profiling(s.h, False)
     P.stokes_sync(s.h)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_total = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = ws * pairs * args.steps / t_total / 1e9
+    t_total = max_over_ranks(sum(step_ms) / 1e3, dev)
+    value = aggregate_rate(pairs * args.steps, ws, t_total) / 1e9
     pair_avg = statistics.mean(pair_ms)
     gpu_out = out.cpu().numpy()
 
@@ -467,12 +480,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         P.stokes_sum_eval_host(s.h, prec, hs, hd, 0.0, ho)
-    te = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([te], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": ws * pairs * args.steps / te / 1e9, "unit": "Gpair-evals/s",
+    te = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate_rate(pairs * args.steps, ws, te) / 1e9, "unit": "Gpair-evals/s",
            "h2d_bytes_per_step": int(hs.numel() * 8 + hd.numel() * 8),
            "d2h_bytes_per_step": int(ho.numel() * 8)}
 
