@@ -375,7 +375,7 @@ struct TgtF64 {
 template <int NIMG, bool MASK0>
 __device__ __forceinline__ void slp_source_f64(const TgtF64<NIMG> &t, const double2 pos,
                                                const double4_32a val, bool skip0, double &ax,
-                                               double &ay) {
+                                               double &ay, const LogTab *lt) {
   const double dy = t.y - pos.y;
   const double dyq = dy * val.y;
   const double dy2 = fma(dy, dy, kTiny64);
@@ -385,7 +385,7 @@ __device__ __forceinline__ void slp_source_f64(const TgtF64<NIMG> &t, const doub
     const double dx = t.x[k] - pos.x;
     const double r2 = fma(dx, dx, dy2);
     const double inv = __drcp_rn(r2);
-    const double lg = log(r2);
+    const double lg = flog64(r2, lt);
     const double s = fma(dx, val.x, dyq) * inv;
     ax = fma(lg, val.z, ax);
     ax = fma(s, dx, ax);
@@ -465,11 +465,11 @@ __device__ __forceinline__ bool run_item_f64(const PairArgs &a, const ItemDesc &
         if (__any_sync(0xffffffffu, mine)) {
           for (int j = 0; j < kTileF64; ++j) {
             const bool s0 = (slot0 + j >= t.skip.x) && (slot0 + j < t.skip.y);
-            slp_source_f64<NIMG, true>(t, sm.pos[st][j], sm.val[st][j], s0, ux, uy);
+            slp_source_f64<NIMG, true>(t, sm.pos[st][j], sm.val[st][j], s0, ux, uy, a.logtab);
           }
         } else {
           for (int j = 0; j < kTileF64; ++j)
-            slp_source_f64<NIMG, false>(t, sm.pos[st][j], sm.val[st][j], false, ux, uy);
+            slp_source_f64<NIMG, false>(t, sm.pos[st][j], sm.val[st][j], false, ux, uy, a.logtab);
         }
       }
     }
@@ -578,6 +578,7 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
   a.period = c->period;
   a.partial = c->d_partial;
   a.status = c->d_status;
+  a.logtab = c->d_logtab;
   const bool img = c->period != 0.0;
   if (precision == STOKES_FP32_KAHAN) {
     a.n_wall_tiles = c->wall_slots / kTileF32;
@@ -613,6 +614,7 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
   a.partial = c->d_partial;
   a.status = c->d_status;
   a.counter = c->d_counter;
+  a.logtab = c->d_logtab;
   const bool img = c->period != 0.0;
   cudaError_t e = cudaMemsetAsync(c->d_counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;

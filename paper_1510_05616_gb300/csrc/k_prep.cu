@@ -189,7 +189,7 @@ __global__ void finish_walls_kernel(int n_wall, const int *wall_nodes, PartLoc L
 __global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
                                   const double *kress, const double2 *x, const double2 *nrm,
                                   const double *w, const double *slp, double c_slp,
-                                  double2 *self) {
+                                  double2 *self, const LogTab *lt) {
   extern __shared__ double sh[];
   const CurveDev cv = curves[ves_curves[blockIdx.x]];
   const int n = cv.n;
@@ -219,7 +219,7 @@ __global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
         const double s = w[i] / h;
         const double2 nn = nrm[i];
         const double tx = -nn.y, ty = nn.x;
-        coef = T[0] - pin * log(s * s);
+        coef = T[0] - pin * flog64(s * s, lt);
         m11 = tx * tx;
         m12 = tx * ty;
         m22 = ty * ty;
@@ -229,7 +229,7 @@ __global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
         const double inv = 1.0 / rr;
         int dj = a - k;
         if (dj < 0) dj += n;
-        coef = T[dj] - pin * log(rr);
+        coef = T[dj] - pin * flog64(rr, lt);
         m11 = rx * rx * inv;
         m12 = rx * ry * inv;
         m22 = ry * ry * inv;
@@ -282,6 +282,27 @@ cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void logtab_init_kernel(LogTab *t) {
+  const int k = threadIdx.x;
+  if (k < kLogTab) {
+    const double a = 1.0 + (k + 0.5) / kLogTab;
+    t->a[k] = a;
+    t->inv_a[k] = 1.0 / a;
+    t->log_a[k] = log(a);
+  }
+  if (k == 0) {
+    const double l2 = log(2.0);
+    const double hi = __longlong_as_double(__double_as_longlong(l2) & ~0x1FFFFFLL);  // 32 bits
+    t->ln2_hi = hi;
+    t->ln2_lo = l2 - hi;
+  }
+}
+
+cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s) {
+  logtab_init_kernel<<<1, kLogTab, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kress_table(int n, double *T, cudaStream_t s) {
   kress_table_kernel<<<nblk(n, 128), 128, 0, s>>>(n, T);
   return cudaGetLastError();
@@ -317,7 +338,7 @@ cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s) {
     self_kress_kernel<<<c->n_ves_curves, 128, smem, s>>>(c->d_ves_curve_ids, c->d_curves,
                                                          c->d_kress, c->d_x, c->d_nrm, c->d_w,
                                                          slp, 1.0 / (4.0 * kPi * c->mu),
-                                                         c->d_self);
+                                                         c->d_self, c->d_logtab);
   }
   return cudaGetLastError();
 }

@@ -12,6 +12,7 @@
 
 namespace stokes {
 cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
+cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
 }  // namespace stokes
@@ -244,6 +245,9 @@ int stokes_create(int device, stokes_ctx **out) {
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void **>(&c->d_status), sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void **>(&c->d_logtab), sizeof(LogTab)) != cudaSuccess ||
+      launch_logtab_init(c->d_logtab, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete c;
     return STOKES_ERR_CUDA;
@@ -260,6 +264,7 @@ int stokes_destroy(stokes_ctx *c) {
   dfree(c->d_partial);
   dfree(c->d_status);
   dfree(c->d_counter);
+  dfree(c->d_logtab);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/stokes.h"
+#include "flog64.cuh"
 
 namespace stokes {
 
@@ -73,6 +74,7 @@ struct PairArgs {
   // outputs
   double2 *partial;
   unsigned *status;
+  const LogTab *logtab;     // FP64 logarithm table (flog64)
 };
 
 // Per instance of a batched geometry (host and device copies).
@@ -140,6 +142,7 @@ struct stokes_ctx {
   double *d_h_slp = nullptr, *d_h_dlp = nullptr, *d_h_out = nullptr;
 
   int num_sms = 0;
+  stokes::LogTab *d_logtab = nullptr;
 
   // batched instances (stokes_batch_set); n_inst = 1 for stokes_geom_set
   int n_inst = 1;
