@@ -13,8 +13,12 @@
 //     split, so r = (x_hi - y_hi) + (x_lo - y_lo) is accurate to a few ulp of |r| even for
 //     adjacent wall nodes (where r . n ~ kappa r^2 / 2 would otherwise be noise);
 //   * 1/r^2 and log2(r^2) from the MUFU approximations (rcp.approx, lg2.approx);
-//   * the three image terms of one source are added in FP32, and that per-source sum
-//     enters a per-thread Kahan-compensated accumulator;
+//   * the image terms of KG consecutive sources are added in FP32, and that group sum
+//     enters a per-target Kahan-compensated accumulator;
+//   * each thread owns TPT targets and evaluates them two at a time with the packed
+//     .f32x2 add/sub/mul/fma instructions (one instruction for both targets; the MUFU
+//     approximations stay scalar), so source records are staged with every value
+//     duplicated into both halves of a 64-bit pair;
 //   * each (split, target) partial leaves the kernel as FP64 and is reduced across splits
 //     in FP64, in fixed order, by the finishing kernel.
 // FP64 path (STOKES_FP64): the same tiling in double precision, plain accumulation.
@@ -145,6 +149,29 @@ __device__ __forceinline__ void slp_source_f32(const TgtF32<NIMG> &t, const floa
   const float dy = (t.yh - pos.y) + (t.yl - pos.w);
   const float dyq = dy * val.y;
   const float dy2 = fmaf(dy, dy, kTiny32);
+  if constexpr (NIMG == 3) {
+    // One rcp and one lg2 for the three images (see slp_source_x2).
+    const float dx0 = (t.xh[0] - pos.x) + (t.xl[0] - pos.z);
+    const float dx1 = (t.xh[1] - pos.x) + (t.xl[1] - pos.z);
+    const float dx2 = (t.xh[2] - pos.x) + (t.xl[2] - pos.z);
+    const float a = fmaf(dx0, dx0, dy2);
+    const float b = (MASK0 && skip0) ? 1.0f : fmaf(dx1, dx1, dy2);
+    const float c = fmaf(dx2, dx2, dy2);
+    const float ab = a * b;
+    const float abc = ab * c;
+    const float inv = rcp_approx(abc);
+    const float lg = lg2_approx(abc);
+    const float s0 = fmaf(dx0, val.x, dyq) * ((b * c) * inv);
+    const float s1 = (MASK0 && skip0) ? 0.0f : fmaf(dx1, val.x, dyq) * ((a * c) * inv);
+    const float s2 = fmaf(dx2, val.x, dyq) * (ab * inv);
+    ax = fmaf(lg, val.z, ax);
+    ax = fmaf(s0, dx0, ax);
+    ax = fmaf(s1, dx1, ax);
+    ax = fmaf(s2, dx2, ax);
+    ay = fmaf(lg, val.w, ay);
+    ay = fmaf((s0 + s1) + s2, dy, ay);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
     if (MASK0 && k == NIMG / 2 && skip0) continue;
@@ -182,46 +209,252 @@ __device__ __forceinline__ void dlp_source_f32(const TgtF32<NIMG> &t, const floa
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed two-target FP32 evaluation (add/sub/mul/fma .f32x2): two targets share every
+// instruction except the MUFU approximations, which stay scalar.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;  // two floats; the first in the low word
+
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 rcp2(f2 v) {
+  float a, b;
+  f2_unpack(v, a, b);
+  return f2_pack(rcp_approx(a), rcp_approx(b));
+}
+__device__ __forceinline__ f2 lg22(f2 v) {
+  float a, b;
+  f2_unpack(v, a, b);
+  return f2_pack(lg2_approx(a), lg2_approx(b));
+}
+
+__device__ __forceinline__ void kahan_add2(f2 &s, f2 &c, f2 v) {
+  const f2 y = sub2(v, c);
+  const f2 t = add2(s, y);
+  c = sub2(sub2(t, s), y);
+  s = t;
+}
+
+// Two targets, packed: (x - m d) hi/lo per image, y hi/lo.
+template <int NIMG>
+struct TgtF32x2 {
+  f2 xh[NIMG], xl[NIMG];
+  f2 yh, yl;
+};
+
+template <int NIMG>
+__device__ __forceinline__ TgtF32x2<NIMG> pack_targets(const TgtF32<NIMG> &a, const TgtF32<NIMG> &b) {
+  TgtF32x2<NIMG> t;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    t.xh[k] = f2_pack(a.xh[k], b.xh[k]);
+    t.xl[k] = f2_pack(a.xl[k], b.xl[k]);
+  }
+  t.yh = f2_pack(a.yh, b.yh);
+  t.yl = f2_pack(a.yl, b.yl);
+  return t;
+}
+
+// A source record as packed duplicates: coordinates (x_hi, y_hi), (x_lo, y_lo) and
+// values (q1, q2), (p1|n1, p2|n2), each half of a pair holding the same float.
+struct SrcX2 {
+  f2 xh, yh, xl, yl, v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ SrcX2 load_src_x2(const float4 *P, const float4 *V, int j) {
+  const ulonglong2 a = reinterpret_cast<const ulonglong2 *>(P)[2 * j];
+  const ulonglong2 b = reinterpret_cast<const ulonglong2 *>(P)[2 * j + 1];
+  const ulonglong2 c = reinterpret_cast<const ulonglong2 *>(V)[2 * j];
+  const ulonglong2 d = reinterpret_cast<const ulonglong2 *>(V)[2 * j + 1];
+  return SrcX2{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
+}
+
+// Stokeslet source against two targets: as slp_source_f32, v0..v3 = (q1, q2, p1, p2).
+// With MASK0, the m = 0 image is dropped (per target) where sa / sb is set.
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const SrcX2 &src, bool sa,
+                                              bool sb, f2 &ax, f2 &ay) {
+  const f2 dy = add2(sub2(t.yh, src.yh), sub2(t.yl, src.yl));
+  const f2 dyq = mul2(dy, src.v1);
+  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+  if constexpr (NIMG == 3) {
+    // Three images share one MUFU pair: with a, b, c the squared distances to the images
+    // m = -1, 0, +1, the log terms sum to p log2(abc) and 1/a = bc/(abc), 1/b = ac/(abc),
+    // 1/c = ab/(abc).  A masked m = 0 image enters the product as b = 1 and its r r^T / r^2
+    // term is dropped.  (abc stays a normal float while no two images of one source lie
+    // within ~1e-10 of a target, i.e. for any period above the curves' node spacing.)
+    const f2 dx0 = add2(sub2(t.xh[0], src.xh), sub2(t.xl[0], src.xl));
+    const f2 dx1 = add2(sub2(t.xh[1], src.xh), sub2(t.xl[1], src.xl));
+    const f2 dx2 = add2(sub2(t.xh[2], src.xh), sub2(t.xl[2], src.xl));
+    const f2 a = fma2(dx0, dx0, dy2);
+    f2 b = fma2(dx1, dx1, dy2);
+    const f2 c = fma2(dx2, dx2, dy2);
+    if (MASK0 && (sa || sb)) {
+      float b0, b1;
+      f2_unpack(b, b0, b1);
+      b = f2_pack(sa ? 1.0f : b0, sb ? 1.0f : b1);
+    }
+    const f2 ab = mul2(a, b);
+    const f2 abc = mul2(ab, c);
+    const f2 inv = rcp2(abc);
+    const f2 lg = lg22(abc);
+    const f2 ia = mul2(mul2(b, c), inv);
+    f2 ib = mul2(mul2(a, c), inv);
+    const f2 ic = mul2(ab, inv);
+    if (MASK0 && (sa || sb)) {
+      float i0, i1;
+      f2_unpack(ib, i0, i1);
+      ib = f2_pack(sa ? 0.0f : i0, sb ? 0.0f : i1);
+    }
+    const f2 s0 = mul2(fma2(dx0, src.v0, dyq), ia);
+    const f2 s1 = mul2(fma2(dx1, src.v0, dyq), ib);
+    const f2 s2 = mul2(fma2(dx2, src.v0, dyq), ic);
+    ax = fma2(lg, src.v2, ax);
+    ax = fma2(s0, dx0, ax);
+    ax = fma2(s1, dx1, ax);
+    ax = fma2(s2, dx2, ax);
+    ay = fma2(lg, src.v3, ay);
+    ay = fma2(add2(add2(s0, s1), s2), dy, ay);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const f2 ax0 = ax, ay0 = ay;
+    const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+    const f2 r2 = fma2(dx, dx, dy2);
+    const f2 inv = rcp2(r2);
+    const f2 lg = lg22(r2);
+    const f2 s = mul2(fma2(dx, src.v0, dyq), inv);
+    ax = fma2(lg, src.v2, ax);
+    ax = fma2(s, dx, ax);
+    ay = fma2(lg, src.v3, ay);
+    ay = fma2(s, dy, ay);
+    if (MASK0 && k == NIMG / 2 && (sa || sb)) {
+      float n0, n1, o0, o1;
+      f2_unpack(ax, n0, n1);
+      f2_unpack(ax0, o0, o1);
+      ax = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
+      f2_unpack(ay, n0, n1);
+      f2_unpack(ay0, o0, o1);
+      ay = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
+    }
+  }
+}
+
+// Stresslet source against two targets: as dlp_source_f32, v0..v3 = (q1, q2, n1, n2).
+template <int NIMG>
+__device__ __forceinline__ void dlp_source_x2(const TgtF32x2<NIMG> &t, const SrcX2 &src, f2 &ax,
+                                              f2 &ay) {
+  const f2 dy = add2(sub2(t.yh, src.yh), sub2(t.yl, src.yl));
+  const f2 dyn = mul2(dy, src.v3);
+  const f2 dyq = mul2(dy, src.v1);
+  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+    const f2 r2 = fma2(dx, dx, dy2);
+    const f2 inv = rcp2(r2);
+    const f2 rn = fma2(dx, src.v2, dyn);
+    const f2 rq = fma2(dx, src.v0, dyq);
+    const f2 f = mul2(mul2(rn, rq), mul2(inv, inv));
+    ax = fma2(f, dx, ax);
+    ay = fma2(f, dy, ay);
+  }
+}
+
 // Sum over one tile: KG consecutive sources (all images) are added in FP32 into a group
-// sum, and each group sum enters the Kahan-compensated per-target accumulator.
+// sum, and each group sum enters the Kahan-compensated per-target accumulator.  Targets
+// are taken two at a time in packed arithmetic; an odd TPT leaves one scalar target.
+// Accumulators: packed pairs (sx2, cx2, sy2, cy2)[TPT / 2]; the scalar one in (sx, cx, sy, cy).
 template <int NIMG, int TPT, int KG, int KIND>  // KIND: 0 stresslet, 1 stokeslet, 2 stokeslet
                                                 // with the own-curve m = 0 skip
 __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], const float4 *P,
-                                             const float4 *V, int slot0, float (&sx)[TPT],
-                                             float (&cx)[TPT], float (&sy)[TPT],
-                                             float (&cy)[TPT]) {
+                                             const float4 *V, int slot0, f2 (&acc)[TPT / 2 + 1][4],
+                                             float (&acc1)[4]) {
+  constexpr int NP = TPT / 2;
+  TgtF32x2<NIMG> tp[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int h = 0; h < NP; ++h) tp[h] = pack_targets<NIMG>(tg[2 * h], tg[2 * h + 1]);
 #pragma unroll(KIND == 2 ? 1 : 2)
   for (int j = 0; j < kTileF32; j += KG) {
-    float gx[TPT], gy[TPT];
+    f2 gx[NP > 0 ? NP : 1], gy[NP > 0 ? NP : 1];
+    float hx = -0.0f, hy = -0.0f;
 #pragma unroll
-    for (int q = 0; q < TPT; ++q) gx[q] = gy[q] = -0.0f;
+    for (int h = 0; h < NP; ++h) gx[h] = gy[h] = f2_pack(-0.0f, -0.0f);
 #pragma unroll
     for (int u = 0; u < KG; ++u) {
-      const float4 p = P[j + u], v = V[j + u];
+      const SrcX2 src = load_src_x2(P, V, j + u);
+      const int slot = slot0 + j + u;
 #pragma unroll
-      for (int q = 0; q < TPT; ++q) {
+      for (int h = 0; h < NP; ++h) {
         if (KIND == 0) {
-          dlp_source_f32<NIMG>(tg[q], p, v, gx[q], gy[q]);
+          dlp_source_x2<NIMG>(tp[h], src, gx[h], gy[h]);
         } else if (KIND == 1) {
-          slp_source_f32<NIMG, false>(tg[q], p, v, false, gx[q], gy[q]);
+          slp_source_x2<NIMG, false>(tp[h], src, false, false, gx[h], gy[h]);
         } else {
-          const bool s0 = (slot0 + j + u >= tg[q].skip.x) && (slot0 + j + u < tg[q].skip.y);
-          slp_source_f32<NIMG, true>(tg[q], p, v, s0, gx[q], gy[q]);
+          const TgtF32<NIMG> &ta = tg[2 * h], &tb = tg[2 * h + 1];
+          const bool sa = slot >= ta.skip.x && slot < ta.skip.y;
+          const bool sb = slot >= tb.skip.x && slot < tb.skip.y;
+          slp_source_x2<NIMG, true>(tp[h], src, sa, sb, gx[h], gy[h]);
+        }
+      }
+      if (TPT & 1) {
+        const TgtF32<NIMG> &t = tg[TPT - 1];
+        const float4 a = P[2 * (j + u)], b = P[2 * (j + u) + 1];
+        const float4 c = V[2 * (j + u)], d = V[2 * (j + u) + 1];
+        const float4 p = make_float4(a.x, a.z, b.x, b.z), v = make_float4(c.x, c.z, d.x, d.z);
+        if (KIND == 0) {
+          dlp_source_f32<NIMG>(t, p, v, hx, hy);
+        } else if (KIND == 1) {
+          slp_source_f32<NIMG, false>(t, p, v, false, hx, hy);
+        } else {
+          const bool s0 = slot >= t.skip.x && slot < t.skip.y;
+          slp_source_f32<NIMG, true>(t, p, v, s0, hx, hy);
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-      kahan_add(sx[q], cx[q], gx[q]);
-      kahan_add(sy[q], cy[q], gy[q]);
+    for (int h = 0; h < NP; ++h) {
+      kahan_add2(acc[h][0], acc[h][1], gx[h]);
+      kahan_add2(acc[h][2], acc[h][3], gy[h]);
+    }
+    if (TPT & 1) {
+      kahan_add(acc1[0], acc1[1], hx);
+      kahan_add(acc1[2], acc1[3], hy);
     }
   }
 }
 
 // Shared memory of the FP32 kernels: kStages source tiles and their mbarriers.
 struct SmemF32 {
-  __align__(128) float4 pos[kStages][kTileF32];
-  __align__(128) float4 val[kStages][kTileF32];
+  __align__(128) float4 pos[kStages][2 * kTileF32];
+  __align__(128) float4 val[kStages][2 * kTileF32];
   __align__(8) uint64_t bar[kStages];
 };
 
@@ -238,7 +471,8 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
                                              uint32_t &g) {
   const int ntl = it.vt_end - it.vt_begin;
   TgtF32<NIMG> tg[TPT];
-  float sx[TPT], cx[TPT], sy[TPT], cy[TPT];
+  f2 acc[TPT / 2 + 1][4];  // packed (s_x, c_x, s_y, c_y) of target pairs
+  float acc1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   {
     PairArgs b = a;
     b.period = it.period;
@@ -246,20 +480,23 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
     for (int q = 0; q < TPT; ++q) {
       const int loc = min(q * kThreadsF32 + int(threadIdx.x), it.tgt_count - 1);
       load_target_f32<NIMG>(b, it.tgt_begin + loc, tg[q]);
-      sx[q] = cx[q] = sy[q] = cy[q] = 0.0f;
     }
+#pragma unroll
+    for (int h = 0; h <= TPT / 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[h][c] = f2_pack(0.0f, 0.0f);
   }
   const float4 *gpos = static_cast<const float4 *>(a.src_pos);
   const float4 *gval = static_cast<const float4 *>(a.src_val);
-  constexpr uint32_t kBytes = kTileF32 * sizeof(float4);
+  constexpr uint32_t kBytes = 2 * kTileF32 * sizeof(float4);
 
   if (threadIdx.x == 0) {
     for (int r = 0; r < kStages && r < ntl; ++r) {
       const int st = (g + r) % kStages;
       const int tile = item_tile(it, it.vt_begin + r);
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
-      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
-      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
     }
   }
 
@@ -274,16 +511,16 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
       const float4 *P = sm.pos[st];
       const float4 *V = sm.val[st];
       if (vt < it.nw) {
-        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, slot0, sx, cx, sy, cy);
+        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, slot0, acc, acc1);
       } else {
         bool mine = false;
 #pragma unroll
         for (int q = 0; q < TPT; ++q)
           mine |= (tg[q].skip.x < slot0 + kTileF32) && (tg[q].skip.y > slot0);
         if (__any_sync(0xffffffffu, mine))
-          tile_sum_f32<NIMG, TPT, KG, 2>(tg, P, V, slot0, sx, cx, sy, cy);
+          tile_sum_f32<NIMG, TPT, KG, 2>(tg, P, V, slot0, acc, acc1);
         else
-          tile_sum_f32<NIMG, TPT, KG, 1>(tg, P, V, slot0, sx, cx, sy, cy);
+          tile_sum_f32<NIMG, TPT, KG, 1>(tg, P, V, slot0, acc, acc1);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -299,18 +536,39 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
     if (threadIdx.x == 0 && r + kStages < ntl) {
       const int tile = item_tile(it, it.vt_begin + r + kStages);
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
-      bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
-      bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
+      bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
     }
   }
   g += ntl;
 
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
+    float sx, cx, sy, cy;
+    if ((TPT & 1) && q == TPT - 1) {
+      sx = acc1[0];
+      cx = acc1[1];
+      sy = acc1[2];
+      cy = acc1[3];
+    } else {
+      float o;
+      const int h = q / 2;
+      if (q & 1) {
+        f2_unpack(acc[h][0], o, sx);
+        f2_unpack(acc[h][1], o, cx);
+        f2_unpack(acc[h][2], o, sy);
+        f2_unpack(acc[h][3], o, cy);
+      } else {
+        f2_unpack(acc[h][0], sx, o);
+        f2_unpack(acc[h][1], cx, o);
+        f2_unpack(acc[h][2], sy, o);
+        f2_unpack(acc[h][3], cy, o);
+      }
+    }
     const int loc = q * kThreadsF32 + int(threadIdx.x);
     if (loc < it.tgt_count)
       a.partial[it.part_off + it.tgt_begin + loc] =
-          make_double2(double(sx[q]) - double(cx[q]), double(sy[q]) - double(cy[q]));
+          make_double2(double(sx) - double(cx), double(sy) - double(cy));
   }
   return true;
 }

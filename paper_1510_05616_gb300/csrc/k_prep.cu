@@ -1,6 +1,7 @@
 // k_prep.cu -- geometry preparation, per-call density packing and the FP64 finishing pass.
 //
-//  * geometry prep (once per stokes_geom_set): FP32 (hi, lo) source coordinates, FP64
+//  * geometry prep (once per stokes_geom_set): FP32 (hi, lo) source coordinates (each value
+//    duplicated for the packed two-target arithmetic of the FP32 pair kernel), FP64
 //    source coordinates, Kress product-rule tables, a finiteness check of the geometry;
 //  * pack (every call): source density records q = w f / (4 pi mu) (stokeslet, Eq. (S))
 //    and q = w tau / pi (stresslet, Eq. (D)), with a finiteness check of the densities;
@@ -15,17 +16,22 @@ namespace stokes {
 // ---------------------------------------------------------------------------
 // geometry preparation
 // ---------------------------------------------------------------------------
+// FP32 source coordinates, every value duplicated into both halves of a packed pair:
+// pos[2s] = (x_hi, x_hi, y_hi, y_hi), pos[2s+1] = (x_lo, x_lo, y_lo, y_lo).
 __global__ void src_pos32_kernel(int slots, const int *slot_node, const double2 *x, float4 *pos) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= slots) return;
   const int i = slot_node[s];
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
   if (i >= 0) {
     const double2 p = x[i];
     const float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
-    r = make_float4(xh, yh, __double2float_rn(p.x - double(xh)), __double2float_rn(p.y - double(yh)));
+    const float xl = __double2float_rn(p.x - double(xh)), yl = __double2float_rn(p.y - double(yh));
+    hi = make_float4(xh, xh, yh, yh);
+    lo = make_float4(xl, xl, yl, yl);
   }
-  pos[s] = r;
+  pos[2 * s] = hi;
+  pos[2 * s + 1] = lo;
 }
 
 __global__ void src_pos64_kernel(int slots, const int *slot_node, const double2 *x, double2 *pos) {
@@ -80,11 +86,13 @@ struct PackArgs {
   unsigned *status;
 };
 
+// FP32 source records, duplicated like the coordinates: val[2s] = (q1, q1, q2, q2) and
+// val[2s+1] = (p1, p1, p2, p2) for a stokeslet source, (n1, n1, n2, n2) for a stresslet source.
 __global__ void pack_f32_kernel(PackArgs a, float4 *val) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.slots) return;
   const int i = a.slot_node[s];
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
   if (i >= 0) {
     const int row = a.node_dens[i];
     const double w = a.w[i];
@@ -93,18 +101,23 @@ __global__ void pack_f32_kernel(PackArgs a, float4 *val) {
       if (!isfinite(t1) || !isfinite(t2)) atomicOr(a.status, kStatusNonfinite);
       const double2 n = a.nrm[i];
       const double c = w / kPi;
-      r = make_float4(__double2float_rn(c * t1), __double2float_rn(c * t2), __double2float_rn(n.x),
-                      __double2float_rn(n.y));
+      v0 = __double2float_rn(c * t1);
+      v1 = __double2float_rn(c * t2);
+      v2 = __double2float_rn(n.x);
+      v3 = __double2float_rn(n.y);
     } else {
       const double f1 = a.slp[2 * row], f2 = a.slp[2 * row + 1];
       if (!isfinite(f1) || !isfinite(f2)) atomicOr(a.status, kStatusNonfinite);
       const double c = w * a.c_slp;
       const double h = -0.5 * 0.69314718055994530942;  // -(ln 2)/2: log(1/r) = h log2(r^2)
-      r = make_float4(__double2float_rn(c * f1), __double2float_rn(c * f2),
-                      __double2float_rn(h * c * f1), __double2float_rn(h * c * f2));
+      v0 = __double2float_rn(c * f1);
+      v1 = __double2float_rn(c * f2);
+      v2 = __double2float_rn(h * c * f1);
+      v3 = __double2float_rn(h * c * f2);
     }
   }
-  val[s] = r;
+  val[2 * s] = make_float4(v0, v0, v1, v1);
+  val[2 * s + 1] = make_float4(v2, v2, v3, v3);
 }
 
 __global__ void pack_f64_kernel(PackArgs a, double4_32a *val) {

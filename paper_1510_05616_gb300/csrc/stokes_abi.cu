@@ -456,8 +456,8 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   if (n_inst > 1) CK(upload(c->d_node_inst, node_inst, s));
   CK(dalloc(c->d_self, n_ves));
   CK(dalloc(c->d_kress, kress_len));
-  CK(dalloc(c->d_src_pos32, slot32.size()));
-  CK(dalloc(c->d_src_val32, slot32.size()));
+  CK(dalloc(c->d_src_pos32, 2 * slot32.size()));
+  CK(dalloc(c->d_src_val32, 2 * slot32.size()));
   CK(dalloc(c->d_src_pos64, slot64.size()));
   CK(dalloc(c->d_src_val64, slot64.size()));
   CK(dalloc(c->d_h_slp, size_t(2) * n_ves));

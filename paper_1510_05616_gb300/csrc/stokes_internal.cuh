@@ -69,8 +69,10 @@ struct PairArgs {
   int *counter;             // zeroed before the launch; blocks take items in table order
   // sources (slot order: wall tiles of every instance, then vesicle tiles of every instance,
   // each instance's run padded to the tile length)
-  const void *src_pos;      // FP32: float4 (x_hi, y_hi, x_lo, y_lo); FP64: double2 (x, y)
-  const void *src_val;      // FP32: float4 (q1, q2, p1|n1, p2|n2); FP64: double4_32a
+  const void *src_pos;      // FP32: 2 float4 per slot, (x_hi, x_hi, y_hi, y_hi), (x_lo, x_lo, y_lo,
+                            //   y_lo); FP64: double2 (x, y)
+  const void *src_val;      // FP32: 2 float4 per slot, (q1, q1, q2, q2), (p1|n1, p1|n1, p2|n2,
+                            //   p2|n2); FP64: double4_32a
   // outputs
   double2 *partial;
   unsigned *status;
