@@ -66,9 +66,18 @@ typedef enum {
 
 typedef enum {
     STOKES_FP64 = 0,        /* pair sum in FP64                                              */
-    STOKES_FP32_KAHAN = 1   /* pair sum in FP32 with hi/lo coordinates and Kahan-compensated
+    STOKES_FP32_KAHAN = 1,  /* pair sum in FP32 with hi/lo coordinates and Kahan-compensated
                                per-thread accumulation; FP64 cross-tile reduction and FP64
                                self terms                                                    */
+    STOKES_DOUBLE_FLOAT = 2 /* pair sum in double-float arithmetic on the FP32 pipes
+                               (unevaluated float pairs, ~48-bit significands): coordinates
+                               split exactly into three floats on fixed grids so r = x - y
+                               is exact, error-free sums and FMA products, a table-driven
+                               double-float logarithm; accuracy of the FP64 path (relative
+                               error <= 1e-12) at a multiple of its speed on GPUs whose FP64
+                               rate is a small fraction of their FP32 rate.  Single-instance
+                               geometries (stokes_geom_set) only; FP64 self terms and
+                               reduction as above                                            */
 } stokes_precision;
 
 typedef enum {

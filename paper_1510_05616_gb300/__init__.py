@@ -26,6 +26,7 @@ STOKES_ERR_OOM = -8
 
 STOKES_FP64 = 0
 STOKES_FP32_KAHAN = 1
+STOKES_DOUBLE_FLOAT = 2
 STOKES_KIND_WALL = 0
 STOKES_KIND_VESICLE = 1
 
@@ -36,7 +37,7 @@ STOKES_GUESS_USER = 3
 N_FEATURES = 64
 N_TARGETS = 48
 
-PRECISIONS = {"fp64": STOKES_FP64, "fp32k": STOKES_FP32_KAHAN}
+PRECISIONS = {"fp64": STOKES_FP64, "fp32k": STOKES_FP32_KAHAN, "df": STOKES_DOUBLE_FLOAT}
 
 
 class StokesError(RuntimeError):

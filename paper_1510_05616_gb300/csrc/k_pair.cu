@@ -28,79 +28,9 @@
 // gives r = 0 exactly and contributes 0 (r2 carries a tiny floor so 1/r^2 stays finite
 // while r . n = r . q = 0).
 #include "stokes_internal.cuh"
+#include "bulk_pipe.cuh"
 
 namespace stokes {
-
-// ---------------------------------------------------------------------------
-// PTX helpers: mbarrier, bulk async copy, MUFU approximations
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for phase `parity` of `bar`, giving up after ~0.5 s (returns false).
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 500000000ull) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 // Floor on r^2: keeps 1/r^2 and (1/r^2)^2 finite for the coincident wall self pair.
 constexpr float kTiny32 = 1e-19f;
@@ -170,20 +100,20 @@ __device__ __forceinline__ void slp_source_f32(const TgtF32<NIMG> &t, const floa
     ax = fmaf(s2, dx2, ax);
     ay = fmaf(lg, val.w, ay);
     ay = fmaf((s0 + s1) + s2, dy, ay);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int k = 0; k < NIMG; ++k) {
-    if (MASK0 && k == NIMG / 2 && skip0) continue;
-    const float dx = (t.xh[k] - pos.x) + (t.xl[k] - pos.z);
-    const float r2 = fmaf(dx, dx, dy2);
-    const float inv = rcp_approx(r2);
-    const float lg = lg2_approx(r2);
-    const float s = fmaf(dx, val.x, dyq) * inv;
-    ax = fmaf(lg, val.z, ax);
-    ax = fmaf(s, dx, ax);
-    ay = fmaf(lg, val.w, ay);
-    ay = fmaf(s, dy, ay);
+    for (int k = 0; k < NIMG; ++k) {
+      if (MASK0 && k == NIMG / 2 && skip0) continue;
+      const float dx = (t.xh[k] - pos.x) + (t.xl[k] - pos.z);
+      const float r2 = fmaf(dx, dx, dy2);
+      const float inv = rcp_approx(r2);
+      const float lg = lg2_approx(r2);
+      const float s = fmaf(dx, val.x, dyq) * inv;
+      ax = fmaf(lg, val.z, ax);
+      ax = fmaf(s, dx, ax);
+      ay = fmaf(lg, val.w, ay);
+      ay = fmaf(s, dy, ay);
+    }
   }
 }
 
@@ -341,28 +271,28 @@ __device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const Src
     ax = fma2(s2, dx2, ax);
     ay = fma2(lg, src.v3, ay);
     ay = fma2(add2(add2(s0, s1), s2), dy, ay);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int k = 0; k < NIMG; ++k) {
-    const f2 ax0 = ax, ay0 = ay;
-    const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
-    const f2 r2 = fma2(dx, dx, dy2);
-    const f2 inv = rcp2(r2);
-    const f2 lg = lg22(r2);
-    const f2 s = mul2(fma2(dx, src.v0, dyq), inv);
-    ax = fma2(lg, src.v2, ax);
-    ax = fma2(s, dx, ax);
-    ay = fma2(lg, src.v3, ay);
-    ay = fma2(s, dy, ay);
-    if (MASK0 && k == NIMG / 2 && (sa || sb)) {
-      float n0, n1, o0, o1;
-      f2_unpack(ax, n0, n1);
-      f2_unpack(ax0, o0, o1);
-      ax = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
-      f2_unpack(ay, n0, n1);
-      f2_unpack(ay0, o0, o1);
-      ay = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
+    for (int k = 0; k < NIMG; ++k) {
+      const f2 ax0 = ax, ay0 = ay;
+      const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+      const f2 r2 = fma2(dx, dx, dy2);
+      const f2 inv = rcp2(r2);
+      const f2 lg = lg22(r2);
+      const f2 s = mul2(fma2(dx, src.v0, dyq), inv);
+      ax = fma2(lg, src.v2, ax);
+      ax = fma2(s, dx, ax);
+      ay = fma2(lg, src.v3, ay);
+      ay = fma2(s, dy, ay);
+      if (MASK0 && k == NIMG / 2 && (sa || sb)) {
+        float n0, n1, o0, o1;
+        f2_unpack(ax, n0, n1);
+        f2_unpack(ax0, o0, o1);
+        ax = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
+        f2_unpack(ay, n0, n1);
+        f2_unpack(ay0, o0, o1);
+        ay = f2_pack(sa ? o0 : n0, sb ? o1 : n1);
+      }
     }
   }
 }
@@ -571,15 +501,6 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
           make_double2(double(sx) - double(cx), double(sy) - double(cy));
   }
   return true;
-}
-
-__device__ __forceinline__ void init_barriers(uint64_t *bar) {
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
 }
 
 // Single instance: blockIdx.x = target block, blockIdx.y = source split.
@@ -829,6 +750,7 @@ PairKernel pick_f64(bool batch, bool img) {
 
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
                         const int2 *skip, int splits, cudaStream_t s) {
+  if (precision == STOKES_DOUBLE_FLOAT) return launch_pair_df(c, n_targets, tgt, skip, splits, s);
   PairArgs a{};
   a.n_targets = n_targets;
   a.tgt = tgt;
@@ -866,6 +788,7 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
 // Persistent launch over the context's item table (batched instances): `blocks` resident
 // blocks take items in table order (largest first) through a zeroed work counter.
 cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStream_t s) {
+  if (precision == STOKES_DOUBLE_FLOAT) return launch_pair_batch_df(c, blocks, s);
   PairArgs a{};
   a.n_targets = c->N;
   a.tgt = c->d_x;
@@ -903,6 +826,7 @@ static int occupancy(PairKernel f, int threads) {
 
 // Resident blocks per SM of the pair-kernel variant the context would launch.
 int pair_blocks_per_sm(stokes_ctx *c, int precision) {
+  if (precision == STOKES_DOUBLE_FLOAT) return pair_df_blocks_per_sm(c);
   const bool img = c->period != 0.0;
   if (precision == STOKES_FP32_KAHAN)
     return occupancy(pick_f32(false, img, c->tpt_f32, c->kgroup_f32), kThreadsF32);
@@ -910,6 +834,7 @@ int pair_blocks_per_sm(stokes_ctx *c, int precision) {
 }
 
 int pair_batch_blocks_per_sm(stokes_ctx *c, int precision) {
+  if (precision == STOKES_DOUBLE_FLOAT) return pair_df_batch_blocks_per_sm(c);
   const bool img = c->period != 0.0;
   if (precision == STOKES_FP32_KAHAN)
     return occupancy(pick_f32(true, img, c->tpt_f32, 4), kThreadsF32);

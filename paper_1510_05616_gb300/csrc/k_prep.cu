@@ -292,7 +292,9 @@ cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s) {
                                                     c->d_status);
   src_pos32_kernel<<<nblk(s32, 256), 256, 0, s>>>(s32, c->d_slot_node32, c->d_x, c->d_src_pos32);
   src_pos64_kernel<<<nblk(s64, 256), 256, 0, s>>>(s64, c->d_slot_node64, c->d_x, c->d_src_pos64);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_geom_prep_df(c, s);
 }
 
 __global__ void logtab_init_kernel(LogTab *t) {
@@ -331,6 +333,7 @@ cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const d
   a.dlp = dlp;
   a.c_slp = 1.0 / (4.0 * kPi * c->mu);
   a.status = c->d_status;
+  if (precision == STOKES_DOUBLE_FLOAT) return launch_pack_df(c, slp, dlp, s);
   if (precision == STOKES_FP32_KAHAN) {
     a.slots = c->wall_slots + c->ves_slots_f32;
     a.wall_slots = c->wall_slots;
@@ -377,7 +380,7 @@ cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, co
 
 cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp, double jump,
                                 double2 *out, cudaStream_t s) {
-  const PartLoc L{c->d_node_inst, c->d_inst, precision == STOKES_FP64 ? 1 : 0, c->N, 0};
+  const PartLoc L{c->d_node_inst, c->d_inst, precision != STOKES_FP32_KAHAN ? 1 : 0, c->N, 0};
   return finish_nodes(c, L, dlp, jump, out, s);
 }
 

@@ -65,7 +65,8 @@ extern "C" int stokes_sum_eval_targets_noalloc(stokes_ctx *c, int precision, con
                                                void *stream) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom) return set_err(c, STOKES_ERR_NO_GEOM, "no geometry set");
-  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
+      precision != STOKES_DOUBLE_FLOAT)
     return set_err(c, STOKES_ERR_ARG, "unknown precision");
   if (c->n_ves_nodes > 0 && !slp) return set_err(c, STOKES_ERR_ARG, "slp_density is NULL");
   if (c->n_wall_nodes > 0 && !dlp) return set_err(c, STOKES_ERR_ARG, "dlp_density is NULL");
@@ -91,7 +92,9 @@ extern "C" int stokes_sum_eval_targets_noalloc(stokes_ctx *c, int precision, con
   // As many source splits as the context uses, capped by the scratch capacity; every
   // (split, target) element is written by the pair kernel before the finish pass reads it,
   // so nothing has to be cleared between calls.
-  const int want = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
+  const int want = precision == STOKES_FP32_KAHAN ? c->splits_f32
+                   : precision == STOKES_FP64     ? c->splits_f64
+                                                  : c->splits_df;
   const int splits = effective_splits(c, precision, std::min(want, kNoAllocPartials / n_targets));
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   e = launch_pack(c, precision, slp, dlp, s);

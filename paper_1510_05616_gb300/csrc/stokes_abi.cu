@@ -87,6 +87,8 @@ void free_geometry(stokes_ctx *c) {
   dfree(c->d_slot_node64);
   dfree(c->d_src_pos64);
   dfree(c->d_src_val64);
+  dfree(c->d_src_pos_df);
+  dfree(c->d_src_val_df);
   dfree(c->d_h_slp);
   dfree(c->d_h_dlp);
   dfree(c->d_h_out);
@@ -124,7 +126,8 @@ int ensure_partial(stokes_ctx *c, size_t elems) {
 // 4 tiles per split keep the per-block prologue and the partial traffic small.
 int default_splits(stokes_ctx *c, int precision) {
   const bool f32 = precision == STOKES_FP32_KAHAN;
-  const int per_block = f32 ? kThreadsF32 * c->tpt_f32 : kThreadsF64;
+  const int per_block = f32 ? kThreadsF32 * c->tpt_f32
+                            : precision == STOKES_DOUBLE_FLOAT ? kThreadsDF * kTptDF : kThreadsF64;
   const long slots = long(pair_blocks_per_sm(c, precision)) * std::max(c->num_sms, 1);
   const long tb = (c->N + per_block - 1) / per_block;
   const int n_tiles = f32 ? (c->wall_slots + c->ves_slots_f32) / kTileF32
@@ -145,6 +148,12 @@ int default_splits(stokes_ctx *c, int precision) {
   return best;
 }
 
+int splits_of(const stokes_ctx *c, int precision) {
+  return precision == STOKES_FP32_KAHAN ? c->splits_f32
+         : precision == STOKES_FP64     ? c->splits_f64
+                                        : c->splits_df;
+}
+
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int read_status(stokes_ctx *c, cudaStream_t s) {
@@ -163,7 +172,8 @@ int read_status(stokes_ctx *c, cudaStream_t s) {
 
 int check_density_args(stokes_ctx *c, int precision, const double *slp, const double *dlp) {
   if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
-  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
+      precision != STOKES_DOUBLE_FLOAT)
     return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
   if (c->n_ves_nodes > 0 && !slp) return fail(c, STOKES_ERR_ARG, "slp_density is NULL");
   if (c->n_wall_nodes > 0 && !dlp) return fail(c, STOKES_ERR_ARG, "dlp_density is NULL");
@@ -207,7 +217,7 @@ int run_batch(stokes_ctx *c, int precision, const double *slp, const double *dlp
 int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
               double *out, cudaStream_t s) {
   if (c->n_inst > 1) return run_batch(c, precision, slp, dlp, jump, out, s);
-  const int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
+  const int splits = splits_of(c, precision);
   MARK(0);
   // fork: the FP64 Kress self pass runs on the side stream beside the pair kernel
   if (c->n_ves_curves > 0) {
@@ -247,6 +257,8 @@ int stokes_create(int device, stokes_ctx **out) {
       cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void **>(&c->d_logtab), sizeof(LogTab)) != cudaSuccess ||
       launch_logtab_init(c->d_logtab, nullptr) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void **>(&c->d_dfc), sizeof(DFConst)) != cudaSuccess ||
+      launch_df_init(c->d_dfc, nullptr) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete c;
@@ -265,6 +277,7 @@ int stokes_destroy(stokes_ctx *c) {
   dfree(c->d_status);
   dfree(c->d_counter);
   dfree(c->d_logtab);
+  dfree(c->d_dfc);
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -460,6 +473,8 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   CK(dalloc(c->d_src_val32, 2 * slot32.size()));
   CK(dalloc(c->d_src_pos64, slot64.size()));
   CK(dalloc(c->d_src_val64, slot64.size()));
+  CK(dalloc(c->d_src_pos_df, 2 * slot64.size()));
+  CK(dalloc(c->d_src_val_df, 2 * slot64.size()));
   CK(dalloc(c->d_h_slp, size_t(2) * n_ves));
   CK(dalloc(c->d_h_dlp, size_t(2) * n_wall));
   CK(dalloc(c->d_h_out, size_t(2) * N));
@@ -470,7 +485,8 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   c->have_geom = true;
   c->splits_f32 = default_splits(c, STOKES_FP32_KAHAN);
   c->splits_f64 = default_splits(c, STOKES_FP64);
-  int st = ensure_partial(c, size_t(std::max(c->splits_f32, c->splits_f64)) * N);
+  c->splits_df = default_splits(c, STOKES_DOUBLE_FLOAT);
+  int st = ensure_partial(c, size_t(std::max({c->splits_f32, c->splits_f64, c->splits_df})) * N);
   if (st) return st;
   st = read_status(c, s);
   if (st) {
@@ -543,7 +559,7 @@ int stokes_sum_eval_targets(stokes_ctx *c, int precision, const double *slp, con
     return fail(c, STOKES_ERR_ARG, "free-point evaluation needs a single-instance geometry");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
-  int splits = precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64;
+  int splits = splits_of(c, precision);
   st = ensure_partial(c, size_t(splits) * n_targets);
   if (st) return st;
   MARK(0);
@@ -586,7 +602,8 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
                       int kahan_group) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom) return fail(c, STOKES_ERR_NO_GEOM, "no geometry set");
-  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
+      precision != STOKES_DOUBLE_FLOAT)
     return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
   if (splits < 0) return fail(c, STOKES_ERR_ARG, "source_splits < 0");
   if (c->n_inst > 1)
@@ -604,7 +621,9 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
   int eff = splits ? effective_splits(c, precision, splits) : default_splits(c, precision);
   int st = ensure_partial(c, size_t(eff) * c->N);
   if (st) return st;
-  (precision == STOKES_FP32_KAHAN ? c->splits_f32 : c->splits_f64) = eff;
+  (precision == STOKES_FP32_KAHAN ? c->splits_f32
+   : precision == STOKES_FP64    ? c->splits_f64
+                                 : c->splits_df) = eff;
   return STOKES_OK;
 }
 
@@ -612,8 +631,8 @@ int stokes_get_launch(const stokes_ctx *c, int precision, int *splits, int *targ
                       int *kahan_group) {
   if (!c || !splits || !targets_per_thread || !kahan_group) return STOKES_ERR_ARG;
   const bool f32 = precision == STOKES_FP32_KAHAN;
-  *splits = f32 ? c->splits_f32 : c->splits_f64;
-  *targets_per_thread = f32 ? c->tpt_f32 : 1;
+  *splits = splits_of(c, precision);
+  *targets_per_thread = f32 ? c->tpt_f32 : precision == STOKES_DOUBLE_FLOAT ? kTptDF : 1;
   *kahan_group = f32 ? c->kgroup_f32 : 0;
   return STOKES_OK;
 }
@@ -737,7 +756,7 @@ int build_batch_tables(stokes_ctx *c) {
 }
 
 int capture_batch_graph(stokes_ctx *c, int precision, double jump) {
-  const int k = precision == STOKES_FP32_KAHAN ? 1 : 0;
+  const int k = precision;
   if (c->graph_exec[k] && c->graph_jump[k] == jump) return STOKES_OK;
   if (c->graph_exec[k]) {
     cudaGraphExecDestroy(c->graph_exec[k]);
@@ -791,7 +810,8 @@ int stokes_batch_set_shape(stokes_ctx *c, int precision, int targets_per_thread,
                            int items_per_slot) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom || c->n_inst < 2) return fail(c, STOKES_ERR_NO_GEOM, "no batched geometry set");
-  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
+      precision != STOKES_DOUBLE_FLOAT)
     return fail(c, STOKES_ERR_ARG, "unknown precision %d", precision);
   if (targets_per_thread != 0 && targets_per_thread != 1 && targets_per_thread != 2 &&
       targets_per_thread != 4)
@@ -815,7 +835,7 @@ int stokes_batch_info(const stokes_ctx *c, int precision, int *n_items, int *blo
   const bool f32 = precision == STOKES_FP32_KAHAN;
   *n_items = f32 ? c->n_items32 : c->n_items64;
   *blocks = pair_batch_blocks_per_sm(const_cast<stokes_ctx *>(c), precision) * std::max(c->num_sms, 1);
-  *targets_per_thread = f32 ? c->tpt_f32 : 1;
+  *targets_per_thread = f32 ? c->tpt_f32 : precision == STOKES_DOUBLE_FLOAT ? kTptDF : 1;
   *items_per_slot = f32 ? c->batch_ips32 : c->batch_ips64;
   return STOKES_OK;
 }
@@ -837,7 +857,7 @@ int stokes_batch_eval(stokes_ctx *c, int precision, const double *slp, const dou
     CK(cudaMemcpyAsync(c->d_b_slp, slp, sizeof(double) * 2 * c->n_ves_nodes, cudaMemcpyDeviceToDevice, s));
   if (c->n_wall_nodes)
     CK(cudaMemcpyAsync(c->d_b_dlp, dlp, sizeof(double) * 2 * c->n_wall_nodes, cudaMemcpyDeviceToDevice, s));
-  CK(cudaGraphLaunch(c->graph_exec[precision == STOKES_FP32_KAHAN ? 1 : 0], s));
+  CK(cudaGraphLaunch(c->graph_exec[precision], s));
   CK(cudaMemcpyAsync(out, c->d_b_out, sizeof(double) * 2 * c->N, cudaMemcpyDeviceToDevice, s));
   return STOKES_OK;
 }

@@ -27,6 +27,8 @@ constexpr int kThreadsF32 = 128;
 constexpr int kTptF32 = 4;      // default targets per thread
 constexpr int kThreadsF64 = 128;
 constexpr int kTptF64 = 1;
+constexpr int kThreadsDF = 64;  // double-float path: 64 threads x 2 targets, FP64 tiles/slots
+constexpr int kTptDF = 2;
 
 constexpr int kMaxVesicleNodes = 1024;  // Kress self pass stages one curve in shared memory
 
@@ -52,7 +54,9 @@ struct ItemDesc {
   double period;
 };
 
-// Arguments of the pair kernels (both precisions).
+struct DFConst;
+
+// Arguments of the pair kernels (all precisions).
 struct PairArgs {
   // targets
   int n_targets;
@@ -77,6 +81,21 @@ struct PairArgs {
   double2 *partial;
   unsigned *status;
   const LogTab *logtab;     // FP64 logarithm table (flog64)
+  const DFConst *dfc;       // double-float path: coordinate grids and logarithm tables
+};
+
+// Constants of the double-float path (device, one per context).  Coordinates are split as
+// v = h + m + l with h on the grid g_h (a power of two chosen so every |coordinate| and every
+// |target - source| fits 24 bits of it) and m on g_m = g_h 2^-24, which makes h_t - h_s and
+// m_t - m_s exact float differences.  The logarithm tables: for k = 0..127,
+// a_k = 1 + (k + 1/2)/128 and kt[k] = (1/a_k hi, lo, log a_k hi, lo); for every biased float
+// exponent e, et[e] = ((e - 127) ln 2 hi, lo).
+struct DFConst {
+  float4 kt[128];
+  float2 et[256];
+  double g_h, g_m;
+  unsigned maxabs_bits;      // float bits of an upper bound of |coordinate| + |period|
+  unsigned pad_[3];
 };
 
 // Per instance of a batched geometry (host and device copies).
@@ -109,7 +128,7 @@ struct stokes_ctx {
   int wall_slots = 0, ves_slots_f32 = 0, ves_slots_f64 = 0;  // padded slot counts
   int wall_slots_f64 = 0;
   int max_ves_n = 0;
-  int splits_f32 = 0, splits_f64 = 0;
+  int splits_f32 = 0, splits_f64 = 0, splits_df = 0;
   int tpt_f32 = stokes::kTptF32;       // targets per thread of the FP32 pair kernel: 1, 2 or 4
   int kgroup_f32 = 4;          // sources summed in FP32 before each Kahan update: 1, 2 or 4
 
@@ -135,6 +154,10 @@ struct stokes_ctx {
   int *d_slot_node64 = nullptr;
   double2 *d_src_pos64 = nullptr;
   double4_32a *d_src_val64 = nullptr;
+  // double-float source slots (FP64 slot layout): 2 float4 each of position and value
+  float4 *d_src_pos_df = nullptr;
+  float4 *d_src_val_df = nullptr;
+  stokes::DFConst *d_dfc = nullptr;
 
   // scratch
   double2 *d_partial = nullptr;
@@ -156,8 +179,8 @@ struct stokes_ctx {
   int *d_counter = nullptr;              // work counter of the persistent launch
   int batch_ips32 = 4, batch_ips64 = 4;  // items per resident block the tables aim for
   // CUDA graphs of one batched evaluation, per precision (built on first use)
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-  double graph_jump[2] = {0.0, 0.0};
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};  // indexed by precision
+  double graph_jump[3] = {0.0, 0.0, 0.0};
   double *d_b_slp = nullptr, *d_b_dlp = nullptr, *d_b_out = nullptr;  // graph staging
 
   // phase timing (stokes_set_profiling)
@@ -190,4 +213,13 @@ cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp,
                                 double2 *out, cudaStream_t s);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
 int pair_batch_blocks_per_sm(stokes_ctx *c, int precision);
+// double-float path (k_pair_df.cu)
+cudaError_t launch_df_init(stokes::DFConst *d, cudaStream_t s);
+cudaError_t launch_geom_prep_df(stokes_ctx *c, cudaStream_t s);
+cudaError_t launch_pack_df(stokes_ctx *c, const double *slp, const double *dlp, cudaStream_t s);
+cudaError_t launch_pair_df(stokes_ctx *c, int n_targets, const double2 *tgt, const int2 *skip,
+                           int splits, cudaStream_t s);
+cudaError_t launch_pair_batch_df(stokes_ctx *c, int blocks, cudaStream_t s);
+int pair_df_blocks_per_sm(stokes_ctx *c);
+int pair_df_batch_blocks_per_sm(stokes_ctx *c);
 }  // namespace stokes

@@ -63,3 +63,13 @@ def test_binding_refuses_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(P.StokesError):
         P.StokesSum(None)
+
+
+def test_binding_constants_match_header_enums():
+    """Every STOKES_* enumerator of the header has the same value in the Python binding."""
+    import paper_1510_05616_gb300 as P
+    src = open(os.path.join(ROOT, "include", "stokes.h")).read()
+    found = re.findall(r"\b(STOKES_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)
+    assert len(found) >= 15
+    for name, value in found:
+        assert getattr(P, name) == int(value), name

@@ -9,7 +9,7 @@ from paper_1510_05616_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32k": 1e-6}
+TOL = {"fp64": 1e-12, "fp32k": 1e-6, "df": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +61,7 @@ def _dens(P, e):
     return dev(P.StokesBatch.stack([s for _, s, _ in e])), dev(P.StokesBatch.stack([d for _, _, d in e]))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_batch_matches_oracle(P, ens, prec, use_graph):
     e, refs = ens
@@ -78,7 +78,7 @@ def test_graph_equals_direct_and_is_repeatable(P, ens):
     e, _ = ens
     b = _batch(P, e)
     ts, td = _dens(P, e)
-    for prec in ("fp32k", "fp64"):
+    for prec in ("fp32k", "fp64", "df"):
         a = b.eval(ts, td, precision=prec, use_graph=False).cpu().numpy()
         g1 = b.eval(ts, td, precision=prec, use_graph=True).cpu().numpy()
         g2 = b.eval(ts, td, precision=prec, use_graph=True).cpu().numpy()
@@ -91,11 +91,12 @@ def test_batch_matches_single_instance_runs(P, ens):
     b = _batch(P, e)
     ts, td = _dens(P, e)
     geoms = [g for g, _, _ in e]
-    outs = {p: split_rows(b.eval(ts, td, precision=p).cpu().numpy(), geoms) for p in ("fp64", "fp32k")}
+    outs = {p: split_rows(b.eval(ts, td, precision=p).cpu().numpy(), geoms)
+            for p in ("fp64", "fp32k", "df")}
     b.close()
     for k, (g, s, d) in enumerate(e):
         one = P.StokesSum(g)
-        for p, tol in (("fp64", 1e-13), ("fp32k", 1e-6)):
+        for p, tol in (("fp64", 1e-13), ("fp32k", 1e-6), ("df", 1e-13)):
             ref = one.eval(dev(s), dev(d), precision=p).cpu().numpy()
             err = np.abs(outs[p][k] - ref).max(0) / np.abs(ref).max(0)
             assert np.all(err <= tol), (k, p, err)

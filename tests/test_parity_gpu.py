@@ -1,7 +1,8 @@
 """GPU parity: libstokes (through its C ABI) against the FP64 CPU oracle on the same inputs.
 
 Tolerances (max-norm relative error per output component, over wall targets and over
-vesicle targets separately): 1e-12 for the FP64 path, 1e-6 for the FP32 Kahan path.
+vesicle targets separately): 1e-12 for the FP64 path and for the double-float path, 1e-6 for
+the FP32 Kahan path.
 """
 import math
 
@@ -12,7 +13,7 @@ from paper_1510_05616_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32k": 1e-6}
+TOL = {"fp64": 1e-12, "fp32k": 1e-6, "df": 1e-12}
 EMPTY = np.zeros((0, 2))
 
 
@@ -89,19 +90,19 @@ def paper(oracle_mod):
     return g, slp, dlp, sel, oracle_mod.sum_nodes(g, slp, dlp, select=sel)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_small_channel_full(P, small, prec):
     g, slp, dlp, ref = small
     check(run(P, g, slp, dlp, prec), ref, g, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_mid_channel_full(P, mid, prec):
     g, slp, dlp, ref = mid
     check(run(P, g, slp, dlp, prec), ref, g, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_paper_scale_sampled(P, paper, prec):
     """N = 128,768 in the bench's launch configuration; oracle at sampled nodes."""
     g, slp, dlp, sel, ref = paper
@@ -126,7 +127,7 @@ def _ragged(seed=21, n_w=100, nvs=(36, 50, 18, 64, 8)):
     return g, slp, dlp
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 @pytest.mark.parametrize("period", [2 * math.pi, 0.0])
 @pytest.mark.parametrize("jump", [0.0, -0.5])
 def test_ragged_interleaved(P, oracle_mod, prec, period, jump):
@@ -136,7 +137,7 @@ def test_ragged_interleaved(P, oracle_mod, prec, period, jump):
     check(run(P, g, slp, dlp, prec, jump=jump), ref, g, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_walls_only_and_vesicles_only(P, oracle_mod, prec):
     g, slp, dlp = _ragged()
     walls = I.Geometry([c for c in g.curves if c.kind == I.KIND_DLP], g.period)
@@ -145,7 +146,7 @@ def test_walls_only_and_vesicles_only(P, oracle_mod, prec):
     check(run(P, ves, slp, EMPTY, prec), oracle_mod.sum_nodes(ves, slp, EMPTY), ves, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_single_tiny_vesicle(P, oracle_mod, prec):
     c = I.closed_curve(4, 0.3, 0.2, (0.1, 0.2), 0.5)
     g = I.Geometry([c], 1.0, 1.0)
@@ -153,14 +154,14 @@ def test_single_tiny_vesicle(P, oracle_mod, prec):
     check(run(P, g, f, EMPTY, prec), oracle_mod.sum_nodes(g, f, EMPTY), g, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 @pytest.mark.parametrize("splits", [1, 3, 1000])
 def test_split_count_does_not_change_result(P, small, prec, splits):
     g, slp, dlp, ref = small
     check(run(P, g, slp, dlp, prec, splits=splits), ref, g, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_free_targets(P, oracle_mod, prec):
     g, slp, dlp = _ragged()
     rng = np.random.default_rng(9)
@@ -177,7 +178,7 @@ def test_free_targets(P, oracle_mod, prec):
 def test_host_api_matches_device_api(P, small):
     g, slp, dlp, ref = small
     s = P.StokesSum(g)
-    for prec in ("fp64", "fp32k"):
+    for prec in ("fp64", "fp32k", "df"):
         out_h = np.zeros((g.n_nodes, 2))
         P.stokes_sum_eval_host(s.h, P.PRECISIONS[prec], slp, dlp, 0.0, out_h)
         out_d = s.eval(dev(P, slp), dev(P, dlp), precision=prec).cpu().numpy()
@@ -192,7 +193,7 @@ def test_deterministic_repeat(P, small):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_translation_by_period(P, small, prec):
     g, slp, dlp, ref = small
     check(run(P, g.translated((2 * math.pi, 0.0)), slp, dlp, prec), ref, g, prec)

@@ -14,7 +14,7 @@ from paper_1510_05616_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32k": 1e-6}
+TOL = {"fp64": 1e-12, "fp32k": 1e-6, "df": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +37,7 @@ def _targets(rng, n):
     return np.stack([rng.uniform(-1.0, 7.0, n), rng.uniform(-0.55, 0.55, n)], 1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
 def test_noalloc_matches_allocating_entry_point(P, prec):
     import torch
     g, slp, dlp = I.workload("small_n1280")
