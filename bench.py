@@ -342,10 +342,12 @@ def run_step(args):
     x0, s0, _ = sim.state()
     ev = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net)
     ev32 = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=P.STOKES_FP32_KAHAN)
+    evdf = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=P.STOKES_DOUBLE_FLOAT)
     sim.close()
     net.close()
     res["eval"] = ev
     res["eval_mixed_precision"] = ev32
+    res["eval_double_float"] = evdf
     z = ev["zero"]
     line = {"metric": "semi-implicit vesicle step, GMRES to 1e-10: mean iterations and ms per step",
             "value": z["step_ms"], "unit": "ms/step (zero guess)", "higher_is_better": False,
@@ -358,6 +360,8 @@ def run_step(args):
                                          for k, v in ev.items()},
             "mixed_precision": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
                                     "gmres_ms": v["gmres_ms"]} for k, v in ev32.items()},
+            "double_float": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
+                                 "gmres_ms": v["gmres_ms"]} for k, v in evdf.items()},
             "details": res}
     print(json.dumps(line))
     return 0
@@ -371,6 +375,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32k", choices=["fp32k", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--df-steps", type=int, default=3,
+                    help="timed double-float evaluations beside the FP32-Kahan leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
@@ -471,6 +477,30 @@ def main():
         d = np.abs(gpu_out - out64.cpu().numpy()).max(0) / np.abs(out64.cpu().numpy()).max(0)
         fp64["fp32k_rel_diff_vs_fp64"] = [float(v) for v in d]
 
+    # double-float path (FP64 accuracy on the FP32 pipes) on the same inputs
+    dfl = None
+    if args.precision == "fp32k" and args.df_steps > 0:
+        outdf = torch.empty_like(out)
+        P.stokes_sum_eval(s.h, P.STOKES_DOUBLE_FLOAT, ts, td, 0.0, outdf)
+        P.stokes_sync(s.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tdf = 0.0
+        for _ in range(args.df_steps):
+            flush.fill_(1.0)
+            e0.record(stream)
+            P.stokes_sum_eval(s.h, P.STOKES_DOUBLE_FLOAT, ts, td, 0.0, outdf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tdf += e0.elapsed_time(e1) / 1e3
+        P.stokes_sync(s.h)
+        dfl = {"value": pairs * args.df_steps / tdf / 1e9, "unit": "Gpair-evals/s",
+               "ms_per_step": 1e3 * tdf / args.df_steps}
+        df_out = outdf.cpu().numpy()
+        if fp64 is not None:
+            o64 = out64.cpu().numpy()
+            d = np.abs(df_out - o64).max(0) / np.abs(o64).max(0)
+            dfl["rel_diff_vs_fp64"] = [float(v) for v in d]
+
     # end to end through the host-buffer C entry point (pinned host memory)
     hs = torch.as_tensor(slp).pin_memory()
     hd = torch.as_tensor(dlp).pin_memory()
@@ -514,6 +544,7 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
         "fp64_path": fp64,
+        "double_float_path": dfl,
     }
     if not args.no_cpu_baseline and ws == 1:
         sel, ref, cpairs, dt, threads = cpu_sample_oracle(g, slp, dlp, args.cpu_budget)
@@ -522,6 +553,8 @@ def main():
                                 "sample": "%d random target nodes x all %d sources x 3 images"
                                           % (len(sel), g.n_nodes)}
         line["rel_err_vs_oracle"] = rel_err_by_kind(gpu_out, ref, g, sel)
+        if dfl is not None:
+            dfl["rel_err_vs_oracle"] = rel_err_by_kind(df_out, ref, g, sel)
     print(json.dumps(line))
     s.close()
     if ws > 1:

@@ -75,9 +75,9 @@ typedef enum {
                                is exact, error-free sums and FMA products, a table-driven
                                double-float logarithm; accuracy of the FP64 path (relative
                                error <= 1e-12) at a multiple of its speed on GPUs whose FP64
-                               rate is a small fraction of their FP32 rate.  Single-instance
-                               geometries (stokes_geom_set) only; FP64 self terms and
-                               reduction as above                                            */
+                               rate is a small fraction of their FP32 rate; every source tile
+                               is summed in double-float and the tile sums in FP64; FP64 self
+                               terms and cross-split reduction as above                      */
 } stokes_precision;
 
 typedef enum {
@@ -284,11 +284,13 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  * Eq. (tsteplinsys) with the arc-length correction Eq. (ALC):
  *   [I + dt kappa_B S d_ssss, -S d_s(x_s .); x_s . d_s, 0] [u; sigma] = [S f_b + u_resp; (L0-Lk)/(dt Lk)]
  * where S is the single layer of all vesicles with +-d images and Kress self terms.  With
- * precision STOKES_FP64 every GMRES matvec uses FP64 sums; with STOKES_FP32_KAHAN GMRES runs on
- * FP32-Kahan sums (to 1e-3, at most 40 iterations a sweep) inside iterative refinement with FP64
- * residuals while each refinement
- * cuts the residual 10x, then FP64 GMRES finishes from that iterate; either way the returned
- * relative residual meets tol in FP64.  Then x += dt u, area correction (App. B) and
+ * precision STOKES_FP64 every pair sum of the step (right-hand side, channel response, GMRES
+ * matvecs) is FP64; with STOKES_DOUBLE_FLOAT they are double-float sums (FP64-accurate, on the
+ * FP32 pipes); with STOKES_FP32_KAHAN the right-hand side and channel response are
+ * double-float, and GMRES runs on FP32-Kahan sums (to 1e-3, at most 40 iterations a sweep)
+ * inside iterative refinement with double-float residuals while each refinement cuts the
+ * residual 10x, then double-float GMRES finishes from that iterate.  In every mode the
+ * returned relative residual meets tol for an FP64-accurate operator.  Then x += dt u, area correction (App. B) and
  * reparameterization (App. C, Algorithm 2).  d/ds = |x_alpha|^-1 d/d alpha by Fourier
  * differentiation.  The unknown vector, guesses and solutions are laid out per vesicle as
  * [u_x (n), u_y (n), sigma (n)], vesicle after vesicle (3 n V doubles).

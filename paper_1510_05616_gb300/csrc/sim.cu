@@ -860,11 +860,13 @@ int set_stream_handles(stokes_sim *m) {
   return STOKES_OK;
 }
 
-// Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.
-int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out) {
+// Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.  The
+// two pair sums run in `prec` (STOKES_FP64 or the equally accurate STOKES_DOUBLE_FLOAT).
+int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out,
+                     int prec = STOKES_FP64) {
   const double cmu = 1.0 / (4.0 * kPiD * m->mu);
   // v = -S^near f at the wall nodes (vesicle sums at free targets)
-  ST(stokes_sum_eval_targets(m->ctx_v, STOKES_FP64, reinterpret_cast<const double *>(f), nullptr,
+  ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
                              m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
   side_rhs_kernel<<<m->K, 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w, f, m->period,
                                           cmu, p_drive, m->d_g);
@@ -883,7 +885,7 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, m->d_c, 1, &one,
                  m->d_tau, 1));
   // u_resp = D^near tau + sum_m c_m S(., y_m) at the vesicle nodes
-  ST(stokes_sum_eval_targets(m->ctx_w, STOKES_FP64, nullptr, m->d_tau, m->Nv,
+  ST(stokes_sum_eval_targets(m->ctx_w, prec, nullptr, m->d_tau, m->Nv,
                              reinterpret_cast<const double *>(m->d_x),
                              reinterpret_cast<double *>(u_out), m->s));
   proxy_eval_kernel<<<nb(m->Nv, 128), 128, 0, m->s>>>(m->Nv, m->d_x, m->M, m->d_proxy, m->d_c,
@@ -1395,8 +1397,12 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   }
   if (!(dt > 0.0) || !(tol > 0.0) || max_iter < 1)
     return fail(m, STOKES_ERR_ARG, "need dt > 0, tol > 0, max_iter >= 1");
-  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
+      precision != STOKES_DOUBLE_FLOAT)
     return fail(m, STOKES_ERR_ARG, "unknown precision");
+  // hp: the precision of every sum that must be FP64-accurate (right-hand side, channel
+  // response, residuals): FP64 itself, or double-float for the two faster modes
+  const int hp = precision == STOKES_FP64 ? STOKES_FP64 : STOKES_DOUBLE_FLOAT;
   SK(cudaSetDevice(m->device));
   const auto t0 = std::chrono::steady_clock::now();
   const int V = m->V, n = m->n;
@@ -1411,9 +1417,9 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
                                        m->d_fb, m->d_f);
   SK(cudaGetLastError());
   // steps 3-5: channel response of the explicit forces
-  if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures));
+  if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp));
   // right-hand side [S f_b + u_resp; ALC]
-  ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
+  ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
                      reinterpret_cast<double *>(m->d_tmp3), m->s));
   ves_rhs_kernel<<<V, n, 0, m->s>>>(n, m->d_tmp3, m->have_walls ? m->d_ures : nullptr, m->d_w,
                                     m->d_L0, dt, m->d_b, m->d_Lk);
@@ -1443,13 +1449,14 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   int iters = 0, refinements = 0;
   double rel = 0.0;
   int gst = STOKES_OK;
-  if (precision == STOKES_FP64) {
-    gst = gmres(m, dt, STOKES_FP64, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
+  if (precision != STOKES_FP32_KAHAN) {
+    gst = gmres(m, dt, hp, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
   } else {
-    // Mixed precision: corrections from GMRES with FP32-Kahan pair sums, residuals of the FP64
-    // operator (iterative refinement) while each refinement cuts the FP64 residual at least 10x;
-    // the stiff operator S (dt kB u_ssss) makes FP32 sums of high-mode densities cancel, so the
-    // refinement can stall -- FP64 GMRES then finishes from the refined iterate to tol.
+    // Mixed precision: corrections from GMRES with FP32-Kahan pair sums, residuals of the
+    // FP64-accurate (double-float) operator (iterative refinement) while each refinement cuts
+    // the residual at least 10x; the stiff operator S (dt kB u_ssss) makes FP32 sums of
+    // high-mode densities cancel, so the refinement can stall -- GMRES on the FP64-accurate
+    // operator then finishes from the refined iterate to tol.
     int st = STOKES_OK;
     const double bn = dnrm(m, len, m->d_b, &st);
     if (st) return fail(m, st, "cublasDnrm2 failed");
@@ -1457,7 +1464,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     double prev = 1e300;
     bool finish64 = false;
     for (;;) {
-      ST(step_matvec(m, dt, STOKES_FP64, m->d_xsol, m->d_wk));
+      ST(step_matvec(m, dt, hp, m->d_xsol, m->d_wk));
       SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
       BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
       const double rn = dnrm(m, len, m->d_rr, &st);
@@ -1483,7 +1490,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     }
     if (finish64) {
       int it64 = 0;
-      gst = gmres(m, dt, STOKES_FP64, m->d_b, m->d_xsol, tol, std::max(max_iter - iters, 1), &it64, &rel);
+      gst = gmres(m, dt, hp, m->d_b, m->d_xsol, tol, std::max(max_iter - iters, 1), &it64, &rel);
       iters += it64;
     }
   }

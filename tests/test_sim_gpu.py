@@ -130,11 +130,12 @@ def test_free_step_parity(P, S, period):
     assert np.abs(x - np.vstack(ox)).max() < 1e-10
 
 
-def test_channel_step_parity(P, S):
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_channel_step_parity(P, S, prec):
     walls, ves = _case(n_ves=2, n_v=16, n_w=64)
     dt, pd = 1e-3, 0.5
     h = make_sim(P, walls, ves)
-    st = P.vesicle_step_warmstart(h, dt, pd, tol=1e-12, max_iter=200)
+    st = P.vesicle_step_warmstart(h, dt, pd, tol=1e-12, max_iter=200, precision=P.PRECISIONS[prec])
     x, sg, sol = P.stokes_sim_get_state(h)
     P.stokes_sim_destroy(h)
     ox, osg, u, sig, ures = _oracle_step(S, [c.nodes for c in ves], dt, walls, pd)
@@ -203,3 +204,23 @@ def test_mixed_precision_step_meets_fp64_tolerance(P):
     # both meet the FP64 residual bound; the stiff system (condition ~1e5) lets two such
     # iterates differ by about cond x tol in the solution
     assert np.abs(sol32 - sol64).max() < 1e-4 * np.abs(sol64).max()
+
+
+def test_double_float_step_matches_fp64_step(P):
+    """Every sum of the step in double-float: the same iterations and, the operator agreeing
+    with FP64 to ~1e-13, the same solution up to that times the conditioning (~1e5)."""
+    walls, ves = _case(n_ves=4, n_v=32, n_w=96)
+    x0 = np.vstack([c.nodes for c in ves])
+    h = make_sim(P, walls, ves)
+    st64 = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300)
+    x64, _, sol64 = P.stokes_sim_get_state(h)
+    P.stokes_sim_set_state(h, x0, np.zeros(len(x0)))
+    stdf = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300,
+                                    precision=P.STOKES_DOUBLE_FLOAT)
+    xdf, _, soldf = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    assert stdf["residual"] <= 1e-11
+    assert abs(stdf["iterations"] - st64["iterations"]) <= 1
+    assert np.abs(soldf - sol64).max() < 1e-7 * np.abs(sol64).max()
+    # x^{k+1} = x^k + dt u (then the area correction and reparameterization, both Lipschitz ~1)
+    assert np.abs(xdf - x64).max() < 2 * 1e-3 * 1e-7 * np.abs(sol64).max()
