@@ -129,7 +129,7 @@ def aggregate_rate(units_per_rank, world_size, seconds_max):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_pair.cu", "stokes_internal.cuh"):
+    for f in ("k_pair.cu", "stokes_internal.cuh", "bulk_pipe.cuh"):
         with open(os.path.join(ROOT, "paper_1510_05616_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
