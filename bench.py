@@ -253,6 +253,8 @@ def run_batch(args):
     res = {}
     for prec_name in ("fp32k", "fp64"):
         prec = P.PRECISIONS[prec_name]
+        # the FP64 leg keeps its default shape: timing its candidates would take minutes
+        tuned = None if args.no_tune or prec_name != "fp32k" else P.stokes_autotune(b.h, prec, repeats=3)
         steps = args.steps if prec_name == "fp32k" else max(1, args.fp64_steps)
         for _ in range(max(1, args.warmup if prec_name == "fp32k" else 1)):
             P.stokes_batch_eval(b.h, prec, ts, td, 0.0, out, True)
@@ -262,7 +264,10 @@ def run_batch(args):
         res[prec_name] = {"graph_ms": statistics.median(g_ms), "direct_ms": statistics.median(d_ms),
                           "graph_gpairs": pairs / statistics.median(g_ms) / 1e6,
                           "items": P.stokes_batch_info(b.h, prec)[0],
-                          "blocks": P.stokes_batch_info(b.h, prec)[1]}
+                          "blocks": P.stokes_batch_info(b.h, prec)[1],
+                          "shape": dict(zip(("targets_per_thread", "items_per_slot"),
+                                            P.stokes_batch_info(b.h, prec)[2:])),
+                          "autotune": tuned}
     b.close()
     # plain form: one single-instance context per channel, evaluated back to back
     singles = [P.StokesSum(g) for g in geoms]
@@ -270,6 +275,21 @@ def run_batch(args):
     outs = [torch.empty((g.n_nodes, 2), dtype=torch.float64, device=dev) for g in geoms]
     for prec_name in ("fp32k",):
         prec = P.PRECISIONS[prec_name]
+        # per size class: a context whose class the tuner has not seen yet is tuned; the
+        # others took the recorded shape of their class when their geometry was set
+        n_tuned = 0
+        if not args.no_tune:
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            for h, g in zip(singles, geoms):
+                nw = int(g.kind_mask(I.KIND_DLP).sum())
+                if P.stokes_tune_lookup(sms, prec, 1, g.n_nodes, nw, g.n_nodes - nw) is None:
+                    P.stokes_autotune(h.h, prec, repeats=3)
+                    n_tuned += 1
+                else:
+                    sh = P.stokes_tune_lookup(sms, prec, 1, g.n_nodes, nw, g.n_nodes - nw)
+                    P.stokes_set_launch(h.h, prec, sh["source_splits"], sh["targets_per_thread"],
+                                        sh["kahan_group"])
+        res[prec_name]["plain_size_classes_tuned"] = n_tuned
         for h, (s_, d_), o in zip(singles, dens, outs):
             P.stokes_sum_eval(h.h, prec, s_, d_, 0.0, o)
         torch.cuda.synchronize()
@@ -387,6 +407,8 @@ def main():
     ap.add_argument("--step-workload", default="mid_n16k", choices=["mid_n16k", "small_n1280"])
     ap.add_argument("--train-runs", type=int, default=2)
     ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch-shape autotuner (wave-model default shapes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -424,6 +446,15 @@ def main():
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
+
+    # launch shape: the library's autotuner times its candidates on this geometry (untimed)
+    tuned = None if args.no_tune else P.stokes_autotune(s.h, prec, repeats=3)
+    launch = dict(zip(("source_splits", "targets_per_thread", "kahan_group"),
+                      P.stokes_get_launch(s.h, prec)))
+    launch["autotuned"] = tuned is not None
+    if tuned is not None:
+        launch["candidates"] = tuned["candidates"]
+        launch["default_shape_ms"] = tuned["initial_ms"]
 
     # warm-up
     for _ in range(max(args.warmup, 0)):
@@ -533,7 +564,7 @@ def main():
         "dtype": "f32" if args.precision == "fp32k" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESCS[args.workload], "N": g.n_nodes, "pairs_per_step": pairs,
                    "precision": args.precision, "l2": "flushed before each timed step (256 MB write)",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": "replicas" if ws > 1 else "single", "launch": launch},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "pair_f32k_kernel" if args.precision == "fp32k" else "pair_f64_kernel",

@@ -263,6 +263,52 @@ STOKES_API int stokes_get_launch(const stokes_ctx *ctx, int precision, int *sour
  * is 0), counting skipped and self pairs.  Written to *pairs. */
 STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *pairs);
 
+/*
+ * Launch-shape autotuner.  The paper evaluates these sums with a CPU FMM and has no
+ * counterpart; the direct GPU sum has the shape knobs above, whose best values depend on the
+ * problem size and the device, so the library times them.
+ *
+ * stokes_autotune: for the context's current geometry and `precision`, times each candidate
+ *   shape `repeats` times (1..50; 0 = 5) after one untimed call, with CUDA events on `stream`,
+ *   and applies the one with the smallest median time.  Candidates -- single instance:
+ *   targets_per_thread {1, 2, 4} x kahan_group {1, 2, 4} (FP32-Kahan; one shape otherwise) x
+ *   the three source-split counts the wave model ranks cheapest for that shape, plus the shape
+ *   the context had on entry; batched: targets_per_thread {1, 2, 4} (FP32-Kahan) x
+ *   items_per_slot {1, 2, 4, 8, 16}.  The timed calls evaluate unit densities held in device
+ *   buffers the tuner allocates and frees.  The choice is also recorded in a process-wide table
+ *   under the geometry's size class (below); every later stokes_geom_set / stokes_batch_set
+ *   whose geometry falls in a recorded class starts from the recorded shape instead of the
+ *   wave model's default.  Results depend on the shape only through rounding.  Synchronizes
+ *   `stream`; not for use while a stream is being captured.  Writes the outcome to *out (may
+ *   be NULL).  FP64 and double-float batched launches share one items_per_slot value.
+ * Size class: (SM count of the device, precision, instance count, and for each of the node
+ *   counts N, wall nodes and vesicle nodes, ceil(2 log2 count)), i.e. half-octave buckets.
+ * stokes_tune_lookup: 1 and *out filled when the table holds the class of the given counts,
+ *   0 when it does not, STOKES_ERR_ARG for bad arguments.  Host only.
+ * stokes_tune_save / stokes_tune_load: write the table to / merge it from a text file, one
+ *   class per line (STOKES_ERR_ARG on an I/O or format error; a failed load changes nothing).
+ * stokes_tune_clear: empty the table.
+ * The table is guarded by a mutex; the calls on a context are not thread-safe (as elsewhere).
+ */
+typedef struct {
+    int precision;
+    int source_splits;       /* single instance (0 for batched)                        */
+    int targets_per_thread;  /* FP32-Kahan: 1, 2 or 4; the fixed value otherwise        */
+    int kahan_group;         /* FP32-Kahan single instance: 1, 2 or 4; else 0           */
+    int items_per_slot;      /* batched: 1..16; else 0                                  */
+    int candidates;          /* shapes timed (0 for a table lookup)                     */
+    double best_ms;          /* median time of one evaluation with the chosen shape     */
+    double initial_ms;       /* the same for the shape in use on entry (0 for a lookup) */
+} stokes_tune_result;
+
+STOKES_API int stokes_autotune(stokes_ctx *ctx, int precision, int repeats,
+                               stokes_tune_result *out, void *stream);
+STOKES_API int stokes_tune_lookup(int num_sms, int precision, int n_inst, int n_nodes,
+                                  int n_wall_nodes, int n_ves_nodes, stokes_tune_result *out);
+STOKES_API int stokes_tune_save(const char *path);
+STOKES_API int stokes_tune_load(const char *path);
+STOKES_API int stokes_tune_clear(void);
+
 /* ===========================================================================================
  * Channel response and semi-implicit vesicle time stepping (built on the sums above).
  *

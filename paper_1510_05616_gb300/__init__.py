@@ -99,6 +99,11 @@ _SIGNATURES = {
     "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
     "stokes_sim_set_restart": [_vp, _c_int],
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
+    "stokes_autotune": [_vp, _c_int, _c_int, _vp, _vp],
+    "stokes_tune_lookup": [_c_int] * 6 + [_vp],
+    "stokes_tune_save": [ctypes.c_char_p],
+    "stokes_tune_load": [ctypes.c_char_p],
+    "stokes_tune_clear": [],
 }
 
 
@@ -322,6 +327,52 @@ def stokes_batch_info(h, precision):
     v = [_c_int() for _ in range(4)]
     _check(h, load().stokes_batch_info(h, int(precision), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("precision", _c_int), ("source_splits", _c_int),
+                ("targets_per_thread", _c_int), ("kahan_group", _c_int),
+                ("items_per_slot", _c_int), ("candidates", _c_int), ("best_ms", _c_double),
+                ("initial_ms", _c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def stokes_autotune(h, precision, repeats=5, stream=None):
+    """Time the candidate launch shapes, apply the fastest and record it for the size class."""
+    r = TuneResult()
+    _check(h, load().stokes_autotune(h, int(precision), int(repeats), _vp(ctypes.addressof(r)),
+                                     _stream(stream)))
+    return r.as_dict()
+
+
+def stokes_tune_lookup(num_sms, precision, n_inst, n_nodes, n_wall_nodes, n_ves_nodes):
+    """The recorded shape of a size class as a dict, or None."""
+    r = TuneResult()
+    code = load().stokes_tune_lookup(int(num_sms), int(precision), int(n_inst), int(n_nodes),
+                                     int(n_wall_nodes), int(n_ves_nodes), _vp(ctypes.addressof(r)))
+    if code < 0:
+        raise StokesError(code, "stokes_tune_lookup: bad argument")
+    return r.as_dict() if code == 1 else None
+
+
+def stokes_tune_save(path):
+    code = load().stokes_tune_save(os.fsencode(path))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_tune_save: cannot write %s" % path)
+    return code
+
+
+def stokes_tune_load(path):
+    code = load().stokes_tune_load(os.fsencode(path))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_tune_load: cannot read or parse %s" % path)
+    return code
+
+
+def stokes_tune_clear():
+    return load().stokes_tune_clear()
 
 
 # ---------------------------------------------------------------------------

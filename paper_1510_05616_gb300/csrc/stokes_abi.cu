@@ -15,6 +15,7 @@ cudaError_t launch_kress_table(int n, double *T, cudaStream_t s);
 cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
+void tune_apply_cached(stokes_ctx *c);  // tune.cu: shapes recorded for the geometry's size class
 }  // namespace stokes
 
 using namespace stokes;
@@ -120,11 +121,13 @@ int ensure_partial(stokes_ctx *c, size_t elems) {
   return STOKES_OK;
 }
 
-// Default source splits.  The pair kernel runs (target blocks x splits) equal-cost blocks in
-// waves of `slots` = resident blocks per SM x SMs; the time is ~ waves x (1 / splits), so the
-// split count minimising ceil(tb s / slots) / s wastes the least of the last wave.  At least
-// 4 tiles per split keep the per-block prologue and the partial traffic small.
-int default_splits(stokes_ctx *c, int precision) {
+// Wave model of the source splits.  The pair kernel runs (target blocks x splits) equal-cost
+// blocks in waves of `slots` = resident blocks per SM x SMs; the time is ~ waves x (1 / splits),
+// so a split count is costed as ceil(tb s / slots) / s plus a small per-split charge.  At least
+// 4 tiles per split keep the per-block prologue and the partial traffic small.  Returns
+// (cost, splits) for every split count that effective_splits leaves unchanged, in increasing
+// split order.
+std::vector<std::pair<double, int>> split_costs(stokes_ctx *c, int precision) {
   const bool f32 = precision == STOKES_FP32_KAHAN;
   const int per_block = f32 ? kThreadsF32 * c->tpt_f32
                             : precision == STOKES_DOUBLE_FLOAT ? kThreadsDF * kTptDF : kThreadsF64;
@@ -133,18 +136,25 @@ int default_splits(stokes_ctx *c, int precision) {
   const int n_tiles = f32 ? (c->wall_slots + c->ves_slots_f32) / kTileF32
                           : (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
   const int smax = std::max(1, std::min(n_tiles / 4, 256));
-  int best = 1;
-  double best_cost = 1e300;
+  std::vector<std::pair<double, int>> out;
   for (int sp = 1; sp <= smax; ++sp) {
     const int eff = effective_splits(c, precision, sp);
     if (eff != sp) continue;
     const double waves = double((tb * eff + slots - 1) / slots);
-    const double cost = waves / eff + 2e-4 * eff;
-    if (cost < best_cost - 1e-12) {
-      best_cost = cost;
-      best = eff;
-    }
+    out.emplace_back(waves / eff + 2e-4 * eff, eff);
   }
+  return out;
+}
+
+// Default source splits: the cheapest count of the wave model (the smallest on ties).
+int default_splits(stokes_ctx *c, int precision) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (const auto &cs : split_costs(c, precision))
+    if (cs.first < best_cost - 1e-12) {
+      best_cost = cs.first;
+      best = cs.second;
+    }
   return best;
 }
 
@@ -299,6 +309,21 @@ int stokes_num_nodes(const stokes_ctx *c) { return (c && c->have_geom) ? c->N : 
 }  // extern "C"
 
 namespace stokes {
+
+// The k cheapest split counts of the wave model, cheapest first (the autotuner's candidates).
+std::vector<int> ranked_splits(stokes_ctx *c, int precision, int k) {
+  auto cs = split_costs(c, precision);
+  std::stable_sort(cs.begin(), cs.end(),
+                   [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+                     return a.first < b.first;
+                   });
+  std::vector<int> out;
+  for (const auto &x : cs) {
+    if (int(out.size()) >= k) break;
+    out.push_back(x.second);
+  }
+  return out;
+}
 
 // Validate and upload a geometry of n_inst independent instances (instance k owns curves
 // [inst_curve_off[k], inst_curve_off[k+1])), and build the source-slot layout: the wall tiles
@@ -486,6 +511,7 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   c->splits_f32 = default_splits(c, STOKES_FP32_KAHAN);
   c->splits_f64 = default_splits(c, STOKES_FP64);
   c->splits_df = default_splits(c, STOKES_DOUBLE_FLOAT);
+  tune_apply_cached(c);
   int st = ensure_partial(c, size_t(std::max({c->splits_f32, c->splits_f64, c->splits_df})) * N);
   if (st) return st;
   st = read_status(c, s);
