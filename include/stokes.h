@@ -259,6 +259,22 @@ STOKES_API int stokes_set_launch(stokes_ctx *ctx, int precision, int source_spli
 STOKES_API int stokes_get_launch(const stokes_ctx *ctx, int precision, int *source_splits,
                                  int *targets_per_thread, int *kahan_group);
 
+/*
+ * Local frame of the FP32-Kahan stokeslet tiles (on by default).  The pair kernel normally
+ * forms each difference x - y from (hi, lo) float pairs (three float operations per
+ * coordinate).  With the local frame on, a target block whose targets all lie within 1/8
+ * of the geometry's extent (max norm) of the block's middle target evaluates its stokeslet
+ * (vesicle-source) tiles with coordinates relative to that target: each staged source and
+ * each of its images is translated once per block, exactly up to one final rounding, and a
+ * difference costs one float subtraction.  The rounding of a local coordinate is at most
+ * half an ulp of the block radius, so near pairs keep their accuracy; blocks that are not
+ * compact, and all stresslet (wall-source) tiles, keep the (hi, lo) form.  Node evaluations
+ * order their targets for compact blocks: per instance, the walls in node order, then the
+ * vesicles along a Morton curve of their centroids.  on = 0 turns the local frame off (every
+ * tile in the (hi, lo) form).  Results differ only by rounding.
+ */
+STOKES_API int stokes_set_local_frame(stokes_ctx *ctx, int on);
+
 /* Nominal pair-image evaluations of one stokes_sum_eval: 3 N_t N_s (1 N_t N_s when period
  * is 0), counting skipped and self pairs.  Written to *pairs. */
 STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *pairs);

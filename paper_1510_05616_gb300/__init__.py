@@ -99,6 +99,7 @@ _SIGNATURES = {
     "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
     "stokes_sim_set_restart": [_vp, _c_int],
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
+    "stokes_set_local_frame": [_vp, _c_int],
     "stokes_autotune": [_vp, _c_int, _c_int, _vp, _vp],
     "stokes_tune_lookup": [_c_int] * 6 + [_vp],
     "stokes_tune_save": [ctypes.c_char_p],
@@ -265,6 +266,10 @@ def stokes_num_nodes(h) -> int:
 def stokes_set_launch(h, precision, source_splits=0, targets_per_thread=0, kahan_group=0):
     return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits),
                                               int(targets_per_thread), int(kahan_group)))
+
+
+def stokes_set_local_frame(h, on: bool = True):
+    return _check(h, load().stokes_set_local_frame(h, int(bool(on))))
 
 
 def stokes_get_launch(h, precision):

@@ -36,6 +36,21 @@ namespace stokes {
 constexpr float kTiny32 = 1e-19f;
 constexpr double kTiny64 = 1e-150;
 
+// Knuth's error-free sum: s + e = a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (h + l) - o as one float, h, l the (hi, lo) split of a coordinate and o a float origin:
+// the difference h - o is taken exactly, so only the final rounding remains.
+__device__ __forceinline__ float local_coord(float h, float l, float o) {
+  float b, e;
+  two_sum(h, -o, b, e);
+  return __fadd_rn(b, __fadd_rn(e, l));
+}
+
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   const float y = __fsub_rn(v, c);
   const float t = __fadd_rn(s, y);
@@ -54,7 +69,8 @@ struct TgtF32 {
 };
 
 template <int NIMG>
-__device__ __forceinline__ void load_target_f32(const PairArgs &a, int i, TgtF32<NIMG> &t) {
+__device__ __forceinline__ void load_target_f32(const PairArgs &a, int k, TgtF32<NIMG> &t) {
+  const int i = a.tgt_perm ? a.tgt_perm[k] : k;
   const double2 p = a.tgt[i];
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
@@ -225,23 +241,20 @@ __device__ __forceinline__ SrcX2 load_src_x2(const float4 *P, const float4 *V, i
   return SrcX2{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
 }
 
-// Stokeslet source against two targets: as slp_source_f32, v0..v3 = (q1, q2, p1, p2).
-// With MASK0, the m = 0 image is dropped (per target) where sa / sb is set.
+// Stokeslet terms of one source against two targets, from the packed differences dx[m] (one
+// per image), dy, dyq = dy q2 and dy2 = dy^2 + tiny; v0..v3 = (q1, q2, p1, p2).  With MASK0,
+// the m = 0 image is dropped (per target) where sa / sb is set.
 template <int NIMG, bool MASK0>
-__device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const SrcX2 &src, bool sa,
-                                              bool sb, f2 &ax, f2 &ay) {
-  const f2 dy = add2(sub2(t.yh, src.yh), sub2(t.yl, src.yl));
-  const f2 dyq = mul2(dy, src.v1);
-  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+__device__ __forceinline__ void slp_images_x2(const f2 (&dxm)[NIMG], f2 dy, f2 dyq, f2 dy2,
+                                              f2 v0, f2 v2, f2 v3, bool sa, bool sb, f2 &ax,
+                                              f2 &ay) {
   if constexpr (NIMG == 3) {
     // Three images share one MUFU pair: with a, b, c the squared distances to the images
     // m = -1, 0, +1, the log terms sum to p log2(abc) and 1/a = bc/(abc), 1/b = ac/(abc),
     // 1/c = ab/(abc).  A masked m = 0 image enters the product as b = 1 and its r r^T / r^2
     // term is dropped.  (abc stays a normal float while no two images of one source lie
     // within ~1e-10 of a target, i.e. for any period above the curves' node spacing.)
-    const f2 dx0 = add2(sub2(t.xh[0], src.xh), sub2(t.xl[0], src.xl));
-    const f2 dx1 = add2(sub2(t.xh[1], src.xh), sub2(t.xl[1], src.xl));
-    const f2 dx2 = add2(sub2(t.xh[2], src.xh), sub2(t.xl[2], src.xl));
+    const f2 dx0 = dxm[0], dx1 = dxm[1], dx2 = dxm[2];
     const f2 a = fma2(dx0, dx0, dy2);
     f2 b = fma2(dx1, dx1, dy2);
     const f2 c = fma2(dx2, dx2, dy2);
@@ -262,27 +275,27 @@ __device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const Src
       f2_unpack(ib, i0, i1);
       ib = f2_pack(sa ? 0.0f : i0, sb ? 0.0f : i1);
     }
-    const f2 s0 = mul2(fma2(dx0, src.v0, dyq), ia);
-    const f2 s1 = mul2(fma2(dx1, src.v0, dyq), ib);
-    const f2 s2 = mul2(fma2(dx2, src.v0, dyq), ic);
-    ax = fma2(lg, src.v2, ax);
+    const f2 s0 = mul2(fma2(dx0, v0, dyq), ia);
+    const f2 s1 = mul2(fma2(dx1, v0, dyq), ib);
+    const f2 s2 = mul2(fma2(dx2, v0, dyq), ic);
+    ax = fma2(lg, v2, ax);
     ax = fma2(s0, dx0, ax);
     ax = fma2(s1, dx1, ax);
     ax = fma2(s2, dx2, ax);
-    ay = fma2(lg, src.v3, ay);
+    ay = fma2(lg, v3, ay);
     ay = fma2(add2(add2(s0, s1), s2), dy, ay);
   } else {
 #pragma unroll
     for (int k = 0; k < NIMG; ++k) {
       const f2 ax0 = ax, ay0 = ay;
-      const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+      const f2 dx = dxm[k];
       const f2 r2 = fma2(dx, dx, dy2);
       const f2 inv = rcp2(r2);
       const f2 lg = lg22(r2);
-      const f2 s = mul2(fma2(dx, src.v0, dyq), inv);
-      ax = fma2(lg, src.v2, ax);
+      const f2 s = mul2(fma2(dx, v0, dyq), inv);
+      ax = fma2(lg, v2, ax);
       ax = fma2(s, dx, ax);
-      ay = fma2(lg, src.v3, ay);
+      ay = fma2(lg, v3, ay);
       ay = fma2(s, dy, ay);
       if (MASK0 && k == NIMG / 2 && (sa || sb)) {
         float n0, n1, o0, o1;
@@ -295,6 +308,36 @@ __device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const Src
       }
     }
   }
+}
+
+// Stokeslet source against two targets from (hi, lo) coordinates: as slp_source_f32,
+// v0..v3 = (q1, q2, p1, p2).
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_source_x2(const TgtF32x2<NIMG> &t, const SrcX2 &src, bool sa,
+                                              bool sb, f2 &ax, f2 &ay) {
+  const f2 dy = add2(sub2(t.yh, src.yh), sub2(t.yl, src.yl));
+  const f2 dyq = mul2(dy, src.v1);
+  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+  f2 dxm[NIMG];
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) dxm[k] = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+  slp_images_x2<NIMG, MASK0>(dxm, dy, dyq, dy2, src.v0, src.v2, src.v3, sa, sb, ax, ay);
+}
+
+// Stokeslet source against two targets in a block-local frame: targets (tx, ty) and source
+// images sx[m], sy are single floats relative to the block's origin, so each difference is
+// one subtraction.
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_local_x2(f2 tx, f2 ty, const f2 (&sx)[NIMG], f2 sy, f2 v0,
+                                             f2 v1, f2 v2, f2 v3, bool sa, bool sb, f2 &ax,
+                                             f2 &ay) {
+  const f2 dy = sub2(ty, sy);
+  const f2 dyq = mul2(dy, v1);
+  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+  f2 dxm[NIMG];
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) dxm[k] = sub2(tx, sx[k]);
+  slp_images_x2<NIMG, MASK0>(dxm, dy, dyq, dy2, v0, v2, v3, sa, sb, ax, ay);
 }
 
 // Stresslet source against two targets: as dlp_source_f32, v0..v3 = (q1, q2, n1, n2).
@@ -322,16 +365,23 @@ __device__ __forceinline__ void dlp_source_x2(const TgtF32x2<NIMG> &t, const Src
 // sum, and each group sum enters the Kahan-compensated per-target accumulator.  Targets
 // are taken two at a time in packed arithmetic; an odd TPT leaves one scalar target.
 // Accumulators: packed pairs (sx2, cx2, sy2, cy2)[TPT / 2]; the scalar one in (sx, cx, sy, cy).
-template <int NIMG, int TPT, int KG, int KIND>  // KIND: 0 stresslet, 1 stokeslet, 2 stokeslet
-                                                // with the own-curve m = 0 skip
+// KIND: 0 stresslet, 1 stokeslet, 2 stokeslet with the own-curve m = 0 skip, 3 and 4 the
+// same two in the block-local frame (even TPT only): source images from L (written by
+// translate_tile_f32), targets from (lx, ly).
+template <int NIMG, int TPT, int KG, int KIND>
 __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], const float4 *P,
-                                             const float4 *V, int slot0, f2 (&acc)[TPT / 2 + 1][4],
-                                             float (&acc1)[4]) {
+                                             const float4 *V, const float4 *L, int slot0,
+                                             const f2 (&lx)[TPT / 2 + 1],
+                                             const f2 (&ly)[TPT / 2 + 1],
+                                             f2 (&acc)[TPT / 2 + 1][4], float (&acc1)[4]) {
   constexpr int NP = TPT / 2;
+  static_assert(KIND < 3 || (TPT & 1) == 0, "the local frame needs an even TPT");
   TgtF32x2<NIMG> tp[NP > 0 ? NP : 1];
+  if constexpr (KIND < 3) {
 #pragma unroll
-  for (int h = 0; h < NP; ++h) tp[h] = pack_targets<NIMG>(tg[2 * h], tg[2 * h + 1]);
-#pragma unroll(KIND == 2 ? 1 : 2)
+    for (int h = 0; h < NP; ++h) tp[h] = pack_targets<NIMG>(tg[2 * h], tg[2 * h + 1]);
+  }
+#pragma unroll((KIND == 2 || KIND == 4) ? 1 : 2)
   for (int j = 0; j < kTileF32; j += KG) {
     f2 gx[NP > 0 ? NP : 1], gy[NP > 0 ? NP : 1];
     float hx = -0.0f, hy = -0.0f;
@@ -339,8 +389,33 @@ __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], cons
     for (int h = 0; h < NP; ++h) gx[h] = gy[h] = f2_pack(-0.0f, -0.0f);
 #pragma unroll
     for (int u = 0; u < KG; ++u) {
-      const SrcX2 src = load_src_x2(P, V, j + u);
       const int slot = slot0 + j + u;
+      if constexpr (KIND >= 3) {
+        const ulonglong2 l0 = reinterpret_cast<const ulonglong2 *>(L)[2 * (j + u)];
+        const ulonglong2 l1 = reinterpret_cast<const ulonglong2 *>(L)[2 * (j + u) + 1];
+        const ulonglong2 w0 = reinterpret_cast<const ulonglong2 *>(V)[2 * (j + u)];
+        const ulonglong2 w1 = reinterpret_cast<const ulonglong2 *>(V)[2 * (j + u) + 1];
+        f2 sx[NIMG];
+        if constexpr (NIMG == 3) {
+          sx[0] = l0.x;
+          sx[1] = l0.y;
+          sx[2] = l1.x;
+        } else {
+          sx[0] = l0.y;
+        }
+#pragma unroll
+        for (int h = 0; h < NP; ++h) {
+          bool sa = false, sb = false;
+          if (KIND == 4) {
+            sa = slot >= tg[2 * h].skip.x && slot < tg[2 * h].skip.y;
+            sb = slot >= tg[2 * h + 1].skip.x && slot < tg[2 * h + 1].skip.y;
+          }
+          slp_local_x2<NIMG, KIND == 4>(lx[h], ly[h], sx, l1.y, w0.x, w0.y, w1.x, w1.y, sa, sb,
+                                         gx[h], gy[h]);
+        }
+        continue;
+      }
+      const SrcX2 src = load_src_x2(P, V, j + u);
 #pragma unroll
       for (int h = 0; h < NP; ++h) {
         if (KIND == 0) {
@@ -354,7 +429,7 @@ __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], cons
           slp_source_x2<NIMG, true>(tp[h], src, sa, sb, gx[h], gy[h]);
         }
       }
-      if (TPT & 1) {
+      if ((TPT & 1) && KIND < 3) {
         const TgtF32<NIMG> &t = tg[TPT - 1];
         const float4 a = P[2 * (j + u)], b = P[2 * (j + u) + 1];
         const float4 c = V[2 * (j + u)], d = V[2 * (j + u) + 1];
@@ -381,12 +456,40 @@ __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], cons
   }
 }
 
-// Shared memory of the FP32 kernels: kStages source tiles and their mbarriers.
+// Shared memory of the FP32 kernels: kStages source tiles and their mbarriers, and the
+// current stokeslet tile's positions in the block-local frame.
 struct SmemF32 {
   __align__(128) float4 pos[kStages][2 * kTileF32];
   __align__(128) float4 val[kStages][2 * kTileF32];
+  __align__(16) float4 loc[2 * kTileF32];
   __align__(8) uint64_t bar[kStages];
 };
+
+// Source k of a staged tile in the block-local frame with origin (ox, oy): the images
+// x + m d - ox for m = -1, 0, +1 (d = dh + dl) and y - oy, each rounded once, stored as
+// loc[2k] = (x_-1, x_-1, x_0, x_0), loc[2k+1] = (x_+1, x_+1, y, y) (with images off, every x is
+// x_0).  The origin is near the block's targets, so a source close to one of them gets small
+// local coordinates and small rounding errors.
+template <int NIMG>
+__device__ __forceinline__ void translate_source_f32(const float4 *P, int k, float ox, float oy,
+                                                     float dh, float dl, float4 *loc) {
+  const float4 h = P[2 * k], l = P[2 * k + 1];  // (x_hi, ., y_hi, .), (x_lo, ., y_lo, .)
+  float b, e;
+  two_sum(h.x, -ox, b, e);
+  const float el = __fadd_rn(e, l.x);
+  const float x0 = __fadd_rn(b, el);
+  float xm = x0, xp = x0;
+  if constexpr (NIMG == 3) {
+    float sm, em, sp, ep;
+    two_sum(b, -dh, sm, em);
+    two_sum(b, dh, sp, ep);
+    xm = __fadd_rn(sm, __fadd_rn(em, __fsub_rn(el, dl)));
+    xp = __fadd_rn(sp, __fadd_rn(ep, __fadd_rn(el, dl)));
+  }
+  const float y0 = local_coord(h.z, l.z, oy);
+  loc[2 * k] = make_float4(xm, xm, x0, x0);
+  loc[2 * k + 1] = make_float4(xp, xp, y0, y0);
+}
 
 __device__ __forceinline__ int item_tile(const ItemDesc &it, int vt) {
   return vt < it.nw ? it.wb + vt : it.vb + (vt - it.nw);
@@ -416,6 +519,34 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[h][c] = f2_pack(0.0f, 0.0f);
   }
+  // Block-local frame for the stokeslet tiles: origin at the item's middle target; taken when
+  // every target of the block lies within local_radius of it (max norm).
+  f2 lx[TPT / 2 + 1], ly[TPT / 2 + 1];
+  bool local = false;
+  float ox = 0.f, oy = 0.f, dh = 0.f, dl = 0.f;
+  if constexpr ((TPT & 1) == 0) {
+    if (a.local_radius > 0.f) {
+      const int k0 = it.tgt_begin + it.tgt_count / 2;
+      const int n0 = a.tgt_perm ? a.tgt_perm[k0] : k0;
+      const double2 o = a.tgt[n0];
+      ox = __double2float_rn(o.x);
+      oy = __double2float_rn(o.y);
+      float rmax = 0.f;
+#pragma unroll
+      for (int h = 0; h < TPT / 2; ++h) {
+        const TgtF32<NIMG> &u = tg[2 * h], &v = tg[2 * h + 1];
+        const float xa = local_coord(u.xh[NIMG / 2], u.xl[NIMG / 2], ox);
+        const float xb = local_coord(v.xh[NIMG / 2], v.xl[NIMG / 2], ox);
+        const float ya = local_coord(u.yh, u.yl, oy), yb = local_coord(v.yh, v.yl, oy);
+        lx[h] = f2_pack(xa, xb);
+        ly[h] = f2_pack(ya, yb);
+        rmax = fmaxf(rmax, fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fmaxf(fabsf(ya), fabsf(yb))));
+      }
+      local = !__syncthreads_or(!(rmax <= a.local_radius));
+      dh = __double2float_rn(it.period);
+      dl = __double2float_rn(it.period - double(dh));
+    }
+  }
   const float4 *gpos = static_cast<const float4 *>(a.src_pos);
   const float4 *gval = static_cast<const float4 *>(a.src_val);
   constexpr uint32_t kBytes = 2 * kTileF32 * sizeof(float4);
@@ -430,27 +561,45 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
     }
   }
 
+  static_assert(kThreadsF32 == kTileF32, "one thread translates one source of a tile");
   for (int r = 0; r < ntl; ++r) {
     const uint32_t gr = g + r;
     const int st = gr % kStages;
     const bool ok = mbar_wait_bounded(&sm.bar[st], (gr / kStages) & 1u);
+    const int vt = it.vt_begin + r;
+    if (local && vt >= it.nw) {  // uniform: stokeslet tile in the block-local frame
+      if (ok) translate_source_f32<NIMG>(sm.pos[st], threadIdx.x, ox, oy, dh, dl, sm.loc);
+      __syncthreads();
+    }
     if (ok) {
-      const int vt = it.vt_begin + r;
       const int tile = item_tile(it, vt);
       const int slot0 = tile * kTileF32;
       const float4 *P = sm.pos[st];
       const float4 *V = sm.val[st];
       if (vt < it.nw) {
-        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, slot0, acc, acc1);
+        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
       } else {
         bool mine = false;
 #pragma unroll
         for (int q = 0; q < TPT; ++q)
           mine |= (tg[q].skip.x < slot0 + kTileF32) && (tg[q].skip.y > slot0);
-        if (__any_sync(0xffffffffu, mine))
-          tile_sum_f32<NIMG, TPT, KG, 2>(tg, P, V, slot0, acc, acc1);
-        else
-          tile_sum_f32<NIMG, TPT, KG, 1>(tg, P, V, slot0, acc, acc1);
+        const bool any_mine = __any_sync(0xffffffffu, mine);
+        bool done = false;
+        if constexpr ((TPT & 1) == 0) {
+          if (local) {
+            if (any_mine)
+              tile_sum_f32<NIMG, TPT, KG, 4>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+            else
+              tile_sum_f32<NIMG, TPT, KG, 3>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+            done = true;
+          }
+        }
+        if (!done) {
+          if (any_mine)
+            tile_sum_f32<NIMG, TPT, KG, 2>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+          else
+            tile_sum_f32<NIMG, TPT, KG, 1>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+        }
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -496,16 +645,18 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
       }
     }
     const int loc = q * kThreadsF32 + int(threadIdx.x);
-    if (loc < it.tgt_count)
-      a.partial[it.part_off + it.tgt_begin + loc] =
+    if (loc < it.tgt_count) {
+      const int k = it.tgt_begin + loc;
+      a.partial[it.part_off + (a.tgt_perm ? a.tgt_perm[k] : k)] =
           make_double2(double(sx) - double(cx), double(sy) - double(cy));
+    }
   }
   return true;
 }
 
 // Single instance: blockIdx.x = target block, blockIdx.y = source split.
 template <int NIMG, int TPT, int KG>
-__global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
+__global__ void __launch_bounds__(kThreadsF32, TPT == 4 ? 4 : TPT == 2 ? 6 : 8) pair_f32k_kernel(PairArgs a) {
   __shared__ SmemF32 sm;
   init_barriers(sm.bar);
   ItemDesc it;
@@ -524,7 +675,7 @@ __global__ void __launch_bounds__(kThreadsF32) pair_f32k_kernel(PairArgs a) {
 
 // Batched instances: a persistent grid takes items from the table through a work counter.
 template <int NIMG, int TPT, int KG>
-__global__ void __launch_bounds__(kThreadsF32) pair_f32k_batch_kernel(PairArgs a) {
+__global__ void __launch_bounds__(kThreadsF32, TPT == 4 ? 4 : TPT == 2 ? 6 : 8) pair_f32k_batch_kernel(PairArgs a) {
   __shared__ SmemF32 sm;
   __shared__ int s_item;
   init_barriers(sm.bar);
@@ -768,6 +919,9 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
     a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
     const int eff = (a.n_tiles + a.tiles_per_split - 1) / a.tiles_per_split;
     if (eff != splits) return cudaErrorInvalidValue;  // callers pass effective_splits() values
+    // node evaluations (they pass the skip table) take the Morton target order
+    a.tgt_perm = skip ? c->d_tgt_perm : nullptr;
+    a.local_radius = c->local_frame ? c->local_radius : 0.f;
     const int tpt = c->tpt_f32;
     dim3 grid((n_targets + kThreadsF32 * tpt - 1) / (kThreadsF32 * tpt), eff);
     pick_f32(false, img, tpt, c->kgroup_f32)<<<grid, kThreadsF32, 0, s>>>(a);
@@ -805,6 +959,8 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
     a.src_val = c->d_src_val32;
     a.items = c->d_items32;
     a.n_items = c->n_items32;
+    a.tgt_perm = c->d_tgt_perm;
+    a.local_radius = c->local_frame ? c->local_radius : 0.f;
     pick_f32(true, img, c->tpt_f32, 4)<<<blocks, kThreadsF32, 0, s>>>(a);
   } else {
     a.tgt_skip = c->d_tgt_skip64;

@@ -63,6 +63,7 @@ void free_geometry(stokes_ctx *c) {
   dfree(c->d_node_dens);
   dfree(c->d_wall_nodes);
   dfree(c->d_ves_nodes);
+  dfree(c->d_tgt_perm);
   dfree(c->d_self);
   dfree(c->d_node_inst);
   dfree(c->d_inst);
@@ -308,6 +309,80 @@ int stokes_num_nodes(const stokes_ctx *c) { return (c && c->have_geom) ? c->N : 
 
 }  // extern "C"
 
+namespace {
+
+// Interleave the low 16 bits of x and y (x in the even bits).
+uint32_t morton2(uint32_t x, uint32_t y) {
+  auto spread = [](uint32_t v) {
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+  };
+  return spread(x) | (spread(y) << 1);
+}
+
+// Target order of the FP32 node evaluation: per instance, its wall nodes in node order, then
+// its vesicles along a Morton curve of their centroids (quantised to 2^16 steps over the
+// bounding box of the instance's nodes), each vesicle's nodes in node order.  Consecutive
+// target blocks then cover compact regions.  *radius = 1/8 of the smallest instance extent
+// (the block radius admitted to the pair kernel's local frame).
+std::vector<int> target_order(int n_inst, const int *inst_curve_off, const int32_t *off,
+                              const int32_t *kind, const std::vector<double2> &x,
+                              float *radius) {
+  std::vector<int> perm;
+  perm.reserve(x.size());
+  double min_ext = 0.0;
+  bool have_ext = false;
+  for (int k = 0; k < n_inst; ++k) {
+    const int c0 = inst_curve_off[k], c1 = inst_curve_off[k + 1];
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int i = off[c0]; i < off[c1]; ++i) {
+      if (!(isfinite(x[i].x) && isfinite(x[i].y))) continue;
+      x0 = std::min(x0, x[i].x);
+      x1 = std::max(x1, x[i].x);
+      y0 = std::min(y0, x[i].y);
+      y1 = std::max(y1, x[i].y);
+    }
+    const double ext = std::max(x1 - x0, y1 - y0);
+    if (ext > 0.0 && isfinite(ext)) {
+      min_ext = have_ext ? std::min(min_ext, ext) : ext;
+      have_ext = true;
+    }
+    std::vector<std::pair<uint32_t, int>> ves;
+    for (int cc = c0; cc < c1; ++cc) {
+      if (kind[cc] == STOKES_KIND_WALL) {
+        for (int i = off[cc]; i < off[cc + 1]; ++i) perm.push_back(i);
+        continue;
+      }
+      double cx = 0.0, cy = 0.0;
+      for (int i = off[cc]; i < off[cc + 1]; ++i) {
+        cx += x[i].x;
+        cy += x[i].y;
+      }
+      const double n = double(off[cc + 1] - off[cc]);
+      auto q = [](double v, double lo, double e) {
+        const double t = e > 0.0 ? (v - lo) / e : 0.0;
+        return (isfinite(t) && t > 0.0) ? uint32_t(std::min(t, 1.0) * 65535.0) : 0u;
+      };
+      const double e = std::max(x1 - x0, y1 - y0);
+      ves.emplace_back(morton2(q(cx / n, x0, e), q(cy / n, y0, e)), cc);
+    }
+    std::stable_sort(ves.begin(), ves.end(),
+                     [](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
+                       return a.first < b.first;
+                     });
+    for (const auto &v : ves)
+      for (int i = off[v.second]; i < off[v.second + 1]; ++i) perm.push_back(i);
+  }
+  *radius = have_ext ? float(min_ext / 8.0) : 0.f;
+  return perm;
+}
+
+}  // namespace
+
 namespace stokes {
 
 // The k cheapest split counts of the wave model, cheapest first (the autotuner's candidates).
@@ -492,6 +567,16 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   CK(upload(c->d_curves, curves, s));
   CK(upload(c->d_ves_curve_ids, ves_ids, s));
   if (n_inst > 1) CK(upload(c->d_node_inst, node_inst, s));
+  {
+    std::vector<double2> hx(N);
+    CK(cudaMemcpyAsync(hx.data(), c->d_x, sizeof(double2) * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float radius = 0.f;
+    const std::vector<int> perm =
+        target_order(n_inst, inst_curve_off, curve_offset, curve_kind, hx, &radius);
+    CK(upload(c->d_tgt_perm, perm, s));
+    c->local_radius = radius;
+  }
   CK(dalloc(c->d_self, n_ves));
   CK(dalloc(c->d_kress, kress_len));
   CK(dalloc(c->d_src_pos32, 2 * slot32.size()));
@@ -650,6 +735,12 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
   (precision == STOKES_FP32_KAHAN ? c->splits_f32
    : precision == STOKES_FP64    ? c->splits_f64
                                  : c->splits_df) = eff;
+  return STOKES_OK;
+}
+
+int stokes_set_local_frame(stokes_ctx *c, int on) {
+  if (!c) return STOKES_ERR_ARG;
+  c->local_frame = on != 0;
   return STOKES_OK;
 }
 

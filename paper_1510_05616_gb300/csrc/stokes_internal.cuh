@@ -62,6 +62,10 @@ struct PairArgs {
   int n_targets;
   const double2 *tgt;       // FP64 target points
   const int2 *tgt_skip;     // per target: source-slot range [x, y) skipped at image 0 (or NULL)
+  const int *tgt_perm;      // FP32 node evaluation: node of each kernel target (or NULL = same)
+  float local_radius;       // FP32: stokeslet tiles of a target block whose targets all lie
+                            //   within this distance (max norm) of its middle target are
+                            //   evaluated in that block's local frame; 0 disables
   double period;
   // single-instance grid launch: blockIdx.x = target block, blockIdx.y = split
   int n_tiles;
@@ -131,6 +135,8 @@ struct stokes_ctx {
   int splits_f32 = 0, splits_f64 = 0, splits_df = 0;
   int tpt_f32 = stokes::kTptF32;       // targets per thread of the FP32 pair kernel: 1, 2 or 4
   int kgroup_f32 = 4;          // sources summed in FP32 before each Kahan update: 1, 2 or 4
+  bool local_frame = true;     // FP32: evaluate stokeslet tiles of compact blocks in a local frame
+  float local_radius = 0.f;    // block radius admitted to the local frame (1/8 of the extent)
 
   // device geometry
   double2 *d_x = nullptr;        // [N] nodes
@@ -142,6 +148,8 @@ struct stokes_ctx {
   int *d_node_dens = nullptr;    // [N] row in the node kind's density array
   int *d_wall_nodes = nullptr;   // [n_wall_nodes] node indices of wall nodes
   int *d_ves_nodes = nullptr;    // [n_ves_nodes] node indices of vesicle nodes
+  int *d_tgt_perm = nullptr;     // [N] FP32 node-evaluation target order: per instance, walls in
+                                 //   node order, then vesicles by Morton code of their centroid
   double2 *d_self = nullptr;     // [n_ves_nodes] Kress self term, by vesicle density row
   stokes::CurveDev *d_curves = nullptr;  // [n_curves]
   int *d_ves_curve_ids = nullptr;        // [n_ves_curves]

@@ -252,3 +252,30 @@ def test_launch_knob_validation(P, small):
             P.stokes_set_launch(s.h, P.STOKES_FP32_KAHAN, *bad)
         assert e.value.code == P.STOKES_ERR_ARG
     s.close()
+
+
+@pytest.mark.parametrize("tpt", [2, 4])
+@pytest.mark.parametrize("workload", ["mid", "paper"])
+def test_local_frame_on_and_off(P, mid, paper, workload, tpt):
+    """The FP32 stokeslet tiles in the block-local frame (default) and in the (hi, lo) form
+    both meet the bound; the two differ (so the local frame is really taken) by rounding only."""
+    if workload == "mid":
+        g, slp, dlp, ref = mid
+        sel = None
+    else:
+        g, slp, dlp, sel, ref = paper
+    s = P.StokesSum(g)
+    P.stokes_set_launch(s.h, P.STOKES_FP32_KAHAN, 0, tpt, 4)
+    on = s.eval(dev(P, slp), dev(P, dlp), precision="fp32k").cpu().numpy()
+    P.stokes_set_local_frame(s.h, False)
+    off = s.eval(dev(P, slp), dev(P, dlp), precision="fp32k").cpu().numpy()
+    P.stokes_set_local_frame(s.h, True)
+    again = s.eval(dev(P, slp), dev(P, dlp), precision="fp32k").cpu().numpy()
+    s.close()
+    if sel is not None:
+        on, off, again = on[sel], off[sel], again[sel]
+    check(on, ref, g, "fp32k", select=sel)
+    check(off, ref, g, "fp32k", select=sel)
+    assert np.array_equal(on, again)
+    assert not np.array_equal(on, off)
+    assert np.abs(on - off).max() <= 1e-6 * np.abs(ref).max()
