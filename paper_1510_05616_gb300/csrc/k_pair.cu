@@ -340,7 +340,26 @@ __device__ __forceinline__ void slp_local_x2(f2 tx, f2 ty, const f2 (&sx)[NIMG],
   slp_images_x2<NIMG, MASK0>(dxm, dy, dyq, dy2, v0, v2, v3, sa, sb, ax, ay);
 }
 
-// Stresslet source against two targets: as dlp_source_f32, v0..v3 = (q1, q2, n1, n2).
+// Stresslet terms of one source against two targets from the packed differences dx[m],
+// dy, dyn = dy n2, dyq = dy q2 and dy2 = dy^2 + tiny; v0, v2 = q1, n1.
+template <int NIMG>
+__device__ __forceinline__ void dlp_images_x2(const f2 (&dxm)[NIMG], f2 dy, f2 dyn, f2 dyq, f2 dy2,
+                                              f2 v0, f2 v2, f2 &ax, f2 &ay) {
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const f2 dx = dxm[k];
+    const f2 r2 = fma2(dx, dx, dy2);
+    const f2 inv = rcp2(r2);
+    const f2 rn = fma2(dx, v2, dyn);
+    const f2 rq = fma2(dx, v0, dyq);
+    const f2 f = mul2(mul2(rn, rq), mul2(inv, inv));
+    ax = fma2(f, dx, ax);
+    ay = fma2(f, dy, ay);
+  }
+}
+
+// Stresslet source against two targets from (hi, lo) coordinates: as dlp_source_f32,
+// v0..v3 = (q1, q2, n1, n2).
 template <int NIMG>
 __device__ __forceinline__ void dlp_source_x2(const TgtF32x2<NIMG> &t, const SrcX2 &src, f2 &ax,
                                               f2 &ay) {
@@ -348,26 +367,33 @@ __device__ __forceinline__ void dlp_source_x2(const TgtF32x2<NIMG> &t, const Src
   const f2 dyn = mul2(dy, src.v3);
   const f2 dyq = mul2(dy, src.v1);
   const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+  f2 dxm[NIMG];
 #pragma unroll
-  for (int k = 0; k < NIMG; ++k) {
-    const f2 dx = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
-    const f2 r2 = fma2(dx, dx, dy2);
-    const f2 inv = rcp2(r2);
-    const f2 rn = fma2(dx, src.v2, dyn);
-    const f2 rq = fma2(dx, src.v0, dyq);
-    const f2 f = mul2(mul2(rn, rq), mul2(inv, inv));
-    ax = fma2(f, dx, ax);
-    ay = fma2(f, dy, ay);
-  }
+  for (int k = 0; k < NIMG; ++k) dxm[k] = add2(sub2(t.xh[k], src.xh), sub2(t.xl[k], src.xl));
+  dlp_images_x2<NIMG>(dxm, dy, dyn, dyq, dy2, src.v0, src.v2, ax, ay);
+}
+
+// Stresslet source against two targets in the block-local frame (see slp_local_x2).
+template <int NIMG>
+__device__ __forceinline__ void dlp_local_x2(f2 tx, f2 ty, const f2 (&sx)[NIMG], f2 sy, f2 v0,
+                                             f2 v1, f2 v2, f2 v3, f2 &ax, f2 &ay) {
+  const f2 dy = sub2(ty, sy);
+  const f2 dyn = mul2(dy, v3);
+  const f2 dyq = mul2(dy, v1);
+  const f2 dy2 = fma2(dy, dy, f2_pack(kTiny32, kTiny32));
+  f2 dxm[NIMG];
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) dxm[k] = sub2(tx, sx[k]);
+  dlp_images_x2<NIMG>(dxm, dy, dyn, dyq, dy2, v0, v2, ax, ay);
 }
 
 // Sum over one tile: KG consecutive sources (all images) are added in FP32 into a group
 // sum, and each group sum enters the Kahan-compensated per-target accumulator.  Targets
 // are taken two at a time in packed arithmetic; an odd TPT leaves one scalar target.
 // Accumulators: packed pairs (sx2, cx2, sy2, cy2)[TPT / 2]; the scalar one in (sx, cx, sy, cy).
-// KIND: 0 stresslet, 1 stokeslet, 2 stokeslet with the own-curve m = 0 skip, 3 and 4 the
-// same two in the block-local frame (even TPT only): source images from L (written by
-// translate_tile_f32), targets from (lx, ly).
+// KIND: 0 stresslet, 1 stokeslet, 2 stokeslet with the own-curve m = 0 skip; in the
+// block-local frame (even TPT only; source images from L, written by translate_source_f32,
+// targets from (lx, ly)): 3 stokeslet, 4 stokeslet with the skip, 5 stresslet.
 template <int NIMG, int TPT, int KG, int KIND>
 __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], const float4 *P,
                                              const float4 *V, const float4 *L, int slot0,
@@ -405,6 +431,10 @@ __device__ __forceinline__ void tile_sum_f32(const TgtF32<NIMG> (&tg)[TPT], cons
         }
 #pragma unroll
         for (int h = 0; h < NP; ++h) {
+          if (KIND == 5) {
+            dlp_local_x2<NIMG>(lx[h], ly[h], sx, l1.y, w0.x, w0.y, w1.x, w1.y, gx[h], gy[h]);
+            continue;
+          }
           bool sa = false, sb = false;
           if (KIND == 4) {
             sa = slot >= tg[2 * h].skip.x && slot < tg[2 * h].skip.y;
@@ -522,7 +552,7 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
   // Block-local frame for the stokeslet tiles: origin at the item's middle target; taken when
   // every target of the block lies within local_radius of it (max norm).
   f2 lx[TPT / 2 + 1], ly[TPT / 2 + 1];
-  bool local = false;
+  bool local = false, local_dlp = false;
   float ox = 0.f, oy = 0.f, dh = 0.f, dl = 0.f;
   if constexpr ((TPT & 1) == 0) {
     if (a.local_radius > 0.f) {
@@ -543,6 +573,11 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
         rmax = fmaxf(rmax, fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fmaxf(fabsf(ya), fabsf(yb))));
       }
       local = !__syncthreads_or(!(rmax <= a.local_radius));
+      // wall tiles too when every target is a vesicle node (they keep the gap from the walls)
+      bool ves = true;
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) ves = ves && tg[q].skip.x >= 0;
+      local_dlp = __syncthreads_and(local && ves);
       dh = __double2float_rn(it.period);
       dl = __double2float_rn(it.period - double(dh));
     }
@@ -567,7 +602,7 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
     const int st = gr % kStages;
     const bool ok = mbar_wait_bounded(&sm.bar[st], (gr / kStages) & 1u);
     const int vt = it.vt_begin + r;
-    if (local && vt >= it.nw) {  // uniform: stokeslet tile in the block-local frame
+    if (vt >= it.nw ? local : local_dlp) {  // uniform: tile in the block-local frame
       if (ok) translate_source_f32<NIMG>(sm.pos[st], threadIdx.x, ox, oy, dh, dl, sm.loc);
       __syncthreads();
     }
@@ -577,7 +612,14 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
       const float4 *P = sm.pos[st];
       const float4 *V = sm.val[st];
       if (vt < it.nw) {
-        tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+        bool done = false;
+        if constexpr ((TPT & 1) == 0) {
+          if (local_dlp) {
+            tile_sum_f32<NIMG, TPT, KG, 5>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
+            done = true;
+          }
+        }
+        if (!done) tile_sum_f32<NIMG, TPT, KG, 0>(tg, P, V, sm.loc, slot0, lx, ly, acc, acc1);
       } else {
         bool mine = false;
 #pragma unroll
