@@ -407,6 +407,9 @@ def main():
     ap.add_argument("--step-workload", default="mid_n16k", choices=["mid_n16k", "small_n1280"])
     ap.add_argument("--train-runs", type=int, default=2)
     ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--tune-file", default=None,
+                    help="shapes file of the autotuner: loaded when it exists (no tuning), "
+                         "else written after tuning")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the launch-shape autotuner (wave-model default shapes)")
     args = ap.parse_args()
@@ -434,6 +437,9 @@ def main():
 
     g, slp, dlp = I.workload(args.workload)
     dev = torch.device("cuda", local)
+    from_file = bool(args.tune_file) and os.path.exists(args.tune_file) and not args.no_tune
+    if from_file:
+        P.stokes_tune_load(args.tune_file)  # the context takes its class's shape at geometry set
     s = P.StokesSum(g, device=local)
     ts = torch.as_tensor(slp, device=dev)
     td = torch.as_tensor(dlp, device=dev)
@@ -448,10 +454,14 @@ def main():
             torch.distributed.barrier()
 
     # launch shape: the library's autotuner times its candidates on this geometry (untimed)
-    tuned = None if args.no_tune else P.stokes_autotune(s.h, prec, repeats=3)
+    tuned = None if (args.no_tune or from_file) else P.stokes_autotune(s.h, prec, repeats=3)
+    if tuned is not None and args.tune_file and rank == 0:
+        P.stokes_tune_save(args.tune_file)
     launch = dict(zip(("source_splits", "targets_per_thread", "kahan_group"),
                       P.stokes_get_launch(s.h, prec)))
-    launch["autotuned"] = tuned is not None
+    launch["autotuned"] = tuned is not None or from_file
+    if from_file:
+        launch["shapes_file"] = os.path.basename(args.tune_file)
     if tuned is not None:
         launch["candidates"] = tuned["candidates"]
         launch["default_shape_ms"] = tuned["initial_ms"]

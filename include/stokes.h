@@ -288,8 +288,8 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  *   shape `repeats` times (1..50; 0 = 5) after one untimed call, with CUDA events on `stream`,
  *   and applies the one with the smallest median time.  Candidates -- single instance:
  *   targets_per_thread {1, 2, 4} x kahan_group {1, 2, 4} (FP32-Kahan; one shape otherwise) x
- *   the three source-split counts the wave model ranks cheapest for that shape, plus the shape
- *   the context had on entry; batched: targets_per_thread {1, 2, 4} (FP32-Kahan) x
+ *   the three source-split counts the wave model ranks cheapest for that shape and two and four
+ *   times its cheapest, plus the shape the context had on entry; batched: targets_per_thread {1, 2, 4} (FP32-Kahan) x
  *   items_per_slot {1, 2, 4, 8, 16}.  The timed calls evaluate unit densities held in device
  *   buffers the tuner allocates and frees.  The choice is also recorded in a process-wide table
  *   under the geometry's size class (below); every later stokes_geom_set / stokes_batch_set

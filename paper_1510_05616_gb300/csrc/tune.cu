@@ -90,6 +90,21 @@ bool same_shape(const Shape &a, const Shape &b) {
   return a.splits == b.splits && a.tpt == b.tpt && a.kg == b.kg && a.ips == b.ips;
 }
 
+// Split counts to time for one shape: the wave model's three cheapest, and two and four
+// times its cheapest (finer work units balance uneven tiles better than the model, which
+// costs every tile the same, predicts), as effective counts without repeats.
+std::vector<int> split_candidates(stokes_ctx *c, int prec, int k) {
+  std::vector<int> sp = stokes::ranked_splits(c, prec, k);
+  if (!sp.empty()) {
+    const int best = sp[0];
+    for (int f : {2, 4}) {
+      const int e = stokes::effective_splits(c, prec, best * f);
+      if (std::find(sp.begin(), sp.end(), e) == sp.end()) sp.push_back(e);
+    }
+  }
+  return sp;
+}
+
 std::vector<Shape> candidates(stokes_ctx *c, int prec, const Shape &initial) {
   std::vector<Shape> out;
   const bool f32 = prec == STOKES_FP32_KAHAN;
@@ -101,13 +116,13 @@ std::vector<Shape> candidates(stokes_ctx *c, int prec, const Shape &initial) {
     const int saved = c->tpt_f32;
     for (int t : {1, 2, 4}) {
       c->tpt_f32 = t;  // the wave model sizes target blocks by targets per thread
-      const std::vector<int> sp = stokes::ranked_splits(c, prec, 3);
+      const std::vector<int> sp = split_candidates(c, prec, 3);
       for (int kg : {1, 2, 4})
         for (int s : sp) out.push_back(Shape{s, t, kg, 0});
     }
     c->tpt_f32 = saved;
   } else {
-    for (int s : stokes::ranked_splits(c, prec, 4)) out.push_back(Shape{s, initial.tpt, 0, 0});
+    for (int s : split_candidates(c, prec, 3)) out.push_back(Shape{s, initial.tpt, 0, 0});
   }
   bool have = false;
   for (const auto &s : out) have = have || same_shape(s, initial);
