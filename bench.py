@@ -322,7 +322,10 @@ def run_batch(args):
 def run_step(args):
     """Algorithm 1 on a channel (walls, channel response, GMRES to 1e-10): plain runs give the
     training states, the network is trained with the library's kernels, and a held-out channel
-    is stepped from the same state with the zero, previous-step and network guesses."""
+    is stepped from the same state with the zero, previous-step and network guesses, for each
+    precision of the Krylov matvecs (FP64; FP32-Kahan sweeps inside FP64-accurate refinement;
+    double-float).  The FP64 pair sum is left out at N = 128,768, where one of its matvecs
+    costs ~1.2 s."""
     import torch
     import paper_1510_05616_gb300 as P
     from paper_1510_05616_gb300 import build as B
@@ -330,20 +333,32 @@ def run_step(args):
     from paper_1510_05616_gb300 import warmstart as WS
     B.build()
     n_w, modes, nv, n_v, area = I.WORKLOADS[args.step_workload]
-    # bending modulus scaled to the vesicle size: with kappa_B = 1 the bending velocity
-    # kappa_B / (mu R^2) of R ~ 0.07 vesicles is ~200, and the explicit channel response moves a
-    # vesicle across its wall gap within one step of dt = 1e-3
-    dt, mu, kb = 1e-3, 1.0, 0.01
+    big = args.step_workload == "paper_n128k"
+    # bending modulus scaled with the vesicle area (0.01 at the 16k channel's vesicle size): the
+    # bending velocity kappa_B / (mu R^2) then stays ~2 and the explicit channel response does
+    # not move a vesicle across its wall gap within one step of dt = 1e-3
+    dt, mu = 1e-3, 1.0
+    kb = 0.01 * area / I.WORKLOADS["mid_n16k"][4]
     pd = 2 * mu * 2 * math.pi * 0.2
-    res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10}
+    names = {"fp64": P.STOKES_FP64, "fp32k": P.STOKES_FP32_KAHAN, "df": P.STOKES_DOUBLE_FLOAT}
+    precs = [p for p in args.step_precisions.split(",") if p] or (
+        ["fp32k", "df"] if big else ["fp64", "fp32k", "df"])
+    collect_prec = names[args.collect_precision or ("fp32k" if big else "fp64")]
+    res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10,
+           "precisions": precs, "collect_precision": args.collect_precision or
+           ("fp32k" if big else "fp64")}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
         g = I.channel(n_w, modes, nv, n_v, area, 1000 + r, mu=mu)
+        torch.cuda.synchronize()
         ts = time.perf_counter()
         sim = WS.Simulation(g, kappa_b=kb, restart=200)
+        torch.cuda.synchronize()
         res.setdefault("setup_s", time.perf_counter() - ts)
-        X, T, st = WS.collect(sim, args.train_steps, dt, pd)
+        res.setdefault("wall_solve", dict(zip(("refinements", "residual"),
+                                              P.stokes_sim_wall_stats(sim.h))))
+        X, T, st = WS.collect(sim, args.train_steps, dt, pd, precision=collect_prec)
         plain_its += [x["iterations"] for x in st]
         Xs.append(X)
         Ts.append(T)
@@ -360,29 +375,106 @@ def run_step(args):
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
     sim = WS.Simulation(g, kappa_b=kb, restart=200)
     x0, s0, _ = sim.state()
-    ev = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net)
-    ev32 = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=P.STOKES_FP32_KAHAN)
-    evdf = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=P.STOKES_DOUBLE_FLOAT)
+    evs = {p: WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=names[p])
+           for p in precs}
     sim.close()
     net.close()
-    res["eval"] = ev
-    res["eval_mixed_precision"] = ev32
-    res["eval_double_float"] = evdf
-    z = ev["zero"]
+    for p, ev in evs.items():
+        res["eval_" + p] = ev
+    head = evs[precs[0]]
+    z = head["zero"]
+
+    def summary(ev):
+        return {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
+                    "gmres_ms": v["gmres_ms"]} for k, v in ev.items()}
+
     line = {"metric": "semi-implicit vesicle step, GMRES to 1e-10: mean iterations and ms per step",
-            "value": z["step_ms"], "unit": "ms/step (zero guess)", "higher_is_better": False,
-            "n_gpus": 1, "steps": args.steps, "dtype": "f64", "data": "synthetic",
+            "value": z["step_ms"], "unit": "ms/step (zero guess, %s matvecs)" % precs[0],
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "dtype": "f64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_DESCS[args.step_workload], "vesicles": nv,
-                       "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w},
-            "guesses": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
-                            "gmres_ms": v["gmres_ms"]} for k, v in ev.items()},
-            "iterations_saved_vs_zero": {k: z["mean_iterations"] - v["mean_iterations"]
-                                         for k, v in ev.items()},
-            "mixed_precision": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
-                                    "gmres_ms": v["gmres_ms"]} for k, v in ev32.items()},
-            "double_float": {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
-                                 "gmres_ms": v["gmres_ms"]} for k, v in evdf.items()},
+                       "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w,
+                       "training_states": int(X.shape[0])},
+            "iterations_saved_vs_zero": {p: {k: ev["zero"]["mean_iterations"] - v["mean_iterations"]
+                                             for k, v in ev.items()} for p, ev in evs.items()},
+            "by_precision": {p: summary(ev) for p, ev in evs.items()},
             "details": res}
+    print(json.dumps(line))
+    return 0
+
+
+def run_poiseuille(args):
+    """Accuracy study of Sec. 5.1 on the GPU: the pressure-driven channel with wall data of the
+    exact Poiseuille flow u_e = (-p_drive/(2 mu d) y^2, 0), p_e = -p_drive x / d (+ const),
+    mu = 0.7, alpha = 0.2, d = 2 pi; errors at the probes (0.8, 0), (3.2, 0), (4.8, 0) as the
+    wall nodes N (K = 32, M = 128) and the side points K (M = 4K, N = 512) vary, for both sine
+    channels.  Velocity error: max over probes of |u - u_e| / max |u_e| on the walls; pressure
+    error: max over probes of |p - p_e - c| / p_drive with c the mean offset (the
+    representation fixes its own additive constant).  Also times the FP64 pressure and
+    traction sums at free points."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    B.build()
+    mu, d = 0.7, 2 * math.pi
+    pd = 2 * mu * d * 0.2
+    probes = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0]])
+    ue = lambda q: np.stack([-(pd / (2 * mu * d)) * q[:, 1] ** 2, 0 * q[:, 1]], 1)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+    def errors(shape, n_w, K, M):
+        lo, up = I.wall_curves(n_w, shape)
+        xw = np.vstack([lo.nodes, up.nodes])
+        h = P.stokes_sim_create(0)
+        P.stokes_sim_set_walls(h, n_w, xw, np.concatenate([lo.weights, up.weights]),
+                               np.vstack([lo.normals, up.normals]),
+                               np.concatenate([lo.curvature, up.curvature]), d, mu, K, M)
+        u = torch.zeros((len(probes), 2), dtype=torch.float64, device="cuda")
+        p = torch.zeros(len(probes), dtype=torch.float64, device="cuda")
+        P.stokes_sim_empty_channel(h, pd, dev(ue(xw)), dev(probes), u)
+        P.stokes_sim_empty_channel_pressure(h, pd, dev(ue(xw)), dev(probes), p)
+        P.stokes_sim_destroy(h)
+        u, p = u.cpu().numpy(), p.cpu().numpy()
+        eu = float(np.abs(u - ue(probes)).max() / np.abs(ue(xw)).max())
+        off = p + pd * probes[:, 0] / d
+        ep = float(np.abs(off - off.mean()).max() / pd)
+        return eu, ep
+
+    shapes = {"1+0.3 sin x": I.WALL_SHAPE_SMALL, "1+0.4 sin x+0.15 sin 3x": I.WALL_SHAPE_LARGE}
+    res = {"by_N": {}, "by_K": {}}
+    for name, shape in shapes.items():
+        res["by_N"][name] = {n: errors(shape, n, 32, 128) for n in (32, 48, 64, 96, 128, 192, 256, 512)}
+        res["by_K"][name] = {k: errors(shape, 512, k, 4 * k) for k in (4, 6, 8, 12, 16, 24, 32)}
+    # throughput of the FP64 field sums at the paper-scale geometry
+    g, slp, dlp = I.workload("paper_n128k")
+    s = P.StokesSum(g)
+    rng = np.random.default_rng(0)
+    T = 16384
+    pts = dev(np.stack([rng.uniform(0, d, T), rng.uniform(-0.5, 0.5, T)], 1))
+    nrm = dev(np.tile([[0.0, 1.0]], (T, 1)))
+    ts, td = dev(slp), dev(dlp)
+    pr = torch.zeros(T, dtype=torch.float64, device="cuda")
+    tr = torch.zeros((T, 2), dtype=torch.float64, device="cuda")
+    timing = {}
+    for name, fn in (("pressure", lambda: P.stokes_sum_eval_pressure(s.h, ts, td, pts, pr)),
+                     ("traction", lambda: P.stokes_sum_eval_traction(s.h, ts, td, pts, nrm, tr))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        timing[name] = {"ms": ms, "gpair_per_s": 3.0 * T * g.n_nodes / ms / 1e6}
+    s.close()
+    line = {"metric": "Poiseuille accuracy study (Sec. 5.1): relative errors at 3 probes",
+            "unit": "relative error", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"mu": mu, "alpha": 0.2, "period": d, "probes": probes.tolist(),
+                       "field_timing_targets": T, "field_timing_sources": g.n_nodes},
+            "velocity_pressure_errors": res, "field_sums": timing}
     print(json.dumps(line))
     return 0
 
@@ -402,9 +494,15 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
     ap.add_argument("--batch", action="store_true",
                     help="time the 64-channel batched ensemble instead (separate JSON line)")
+    ap.add_argument("--poiseuille", action="store_true",
+                    help="accuracy study of the pressure-driven channel (velocity and pressure)")
     ap.add_argument("--step", action="store_true",
                     help="time the semi-implicit vesicle step with the learned warm start instead")
-    ap.add_argument("--step-workload", default="mid_n16k", choices=["mid_n16k", "small_n1280"])
+    ap.add_argument("--step-workload", default="mid_n16k",
+                    choices=["paper_n128k", "mid_n16k", "small_n1280"])
+    ap.add_argument("--step-precisions", default="",
+                    help="comma list of fp64, fp32k, df (default: all three; fp32k,df at N=128,768)")
+    ap.add_argument("--collect-precision", default="", choices=["", "fp64", "fp32k", "df"])
     ap.add_argument("--train-runs", type=int, default=2)
     ap.add_argument("--train-steps", type=int, default=40)
     ap.add_argument("--tune-file", default=None,
@@ -419,6 +517,8 @@ def main():
         return run_batch(args)
     if args.step:
         return run_step(args)
+    if args.poiseuille:
+        return run_poiseuille(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -156,6 +156,31 @@ STOKES_API int stokes_sum_eval_targets(stokes_ctx *ctx, int precision, const dou
                                        const double *targets, double *out_velocity, void *stream);
 
 /*
+ * Pressure and traction at free points (FP64): the plain trapezoid rule over every source
+ * node and image, as stokes_sum_eval_targets, of
+ *   pressure  Q w f (vesicle sources, Eq. (Q)) + P w tau (wall sources, Eq. (P));
+ *   traction  K w f (Eq. (K)) + T w tau (Eq. (T)) at targets with unit normals n_x, taking
+ *             the dipole functions of Eq. (T) as d_x = (r . n_x)/r^2 (target) and
+ *             d_y = (r . n_y)/r^2 (source), the reading under which T is the traction
+ *             -p n_x + mu (grad u + grad u^T) n_x of the (D, P) pair.
+ * Targets must lie off the curves (the kernels are singular on them; no on-curve rule).
+ *   n_targets       >= 0 (0 is a no-op)
+ *   targets         DEVICE double[n_targets][2], 16-byte aligned
+ *   target_normals  DEVICE double[n_targets][2], 16-byte aligned (traction only)
+ *   out_pressure    DEVICE double[n_targets];  out_traction  DEVICE double[n_targets][2]
+ * Single-instance geometries only (STOKES_ERR_ARG on a batched context).  May grow the
+ * context's scratch buffer (device synchronisation).  Asynchronous on `stream`.
+ */
+STOKES_API int stokes_sum_eval_pressure(stokes_ctx *ctx, const double *slp_density,
+                                        const double *dlp_density, int n_targets,
+                                        const double *targets, double *out_pressure,
+                                        void *stream);
+STOKES_API int stokes_sum_eval_traction(stokes_ctx *ctx, const double *slp_density,
+                                        const double *dlp_density, int n_targets,
+                                        const double *targets, const double *target_normals,
+                                        double *out_traction, void *stream);
+
+/*
  * stokes_sum_eval with HOST buffers: copies the densities to the device, evaluates and
  * copies the velocities back, on the context's own stream; returns when `out_host` holds
  * the result (synchronous), with any device-side status folded in.
@@ -336,10 +361,27 @@ STOKES_API int stokes_tune_clear(void);
  * of the extended linear system [A B; C Q] (Eq. (BIEU), (BIED), (BIEgu), (BIEgT)) are
  * assembled in FP64 at stokes_sim_set_walls; A is LU-factored, S = Q - C A^-1 B is
  * pseudo-inverted (SVD, singular values below 1e-13 sigma_max dropped), and a solve is the
- * block elimination c = S^+ (g - C A^-1 v), tau = A^-1 v - A^-1 B c (Sec. 4.1, with LU in
- * place of the fast direct solver).  Side points: K Gauss-Legendre nodes across the inlet
- * x = 0 and their copies at x = d; proxies: M >= 2K points on a circle of radius R_p about
- * (d/2, 0).  Dense storage: (4 N_w)^2 doubles for A (N_w nodes per wall).
+ * block elimination c = S^+ (g - C A^-1 v), tau = A^-1 v - A^-1 B c (Sec. 4.1, with a dense
+ * direct solver in place of the paper's fast direct solver).  Side points: K Gauss-Legendre
+ * nodes across the inlet x = 0 and their copies at x = d; proxies: M >= 2K points on a circle
+ * of radius R_p about (d/2, 0).
+ *
+ * Wall solver (stokes_sim_set_wall_solver, read at the next stokes_sim_set_walls):
+ *   STOKES_WALLS_LU32_REFINE (default): A is kept in FP64; an FP32 copy is LU-factored
+ *     (partial pivoting) and inverted once (A32^-1); every solve A x = b starts from x = 0,
+ *     r = b and repeats x += A32^-1 r (FP32), r = b - A x (FP64) until ||r|| <= 1e-14 ||b||,
+ *     the residual stops shrinking, or 12 sweeps.  A = -I/2 + D is of the second kind and well
+ *     conditioned, so each sweep gains ~5 digits and the result is the FP64 solution.
+ *     Storage 12 (4 N_w)^2 bytes (16 during set-up); the FP32 factorization is far faster
+ *     than the FP64 one on this hardware, and a sweep streams the two matrices once.
+ *   STOKES_WALLS_LU64: FP64 LU (8 (4 N_w)^2 bytes), one triangular solve per solve.
+ * stokes_sim_wall_stats: refinement sweeps and relative residual ||b - A x|| / ||b|| of the
+ *   last wall solve (0 and 0 for STOKES_WALLS_LU64).
+ * Block refinement (stokes_sim_set_block_refinement, 0..8, default 2): the block solve is
+ *   followed by that many residual corrections on the whole extended system,
+ *   r = [v; g] - [A B; C Q][tau; c], [tau; c] += block solve of r, with A tau evaluated as the
+ *   walls' double-layer sum.  The truncated S^+ alone leaves ~1e-6 of the data in the
+ *   side-point rows (Poiseuille errors ~1e-6); two corrections bring it to round-off.
  *
  * Time step (Algorithm 1 steps 2-9): forces f_b = -kappa_B x_ssss, f = f_b + (sigma x_s)_s;
  * u_resp of f; GMRES (FP64, right preconditioned by each vesicle's self interaction) on
@@ -362,6 +404,11 @@ STOKES_API int stokes_tune_clear(void);
  * ===========================================================================================
  */
 typedef struct stokes_sim stokes_sim;
+
+typedef enum {
+    STOKES_WALLS_LU64 = 0,         /* FP64 LU of the wall operator                          */
+    STOKES_WALLS_LU32_REFINE = 1   /* FP32 LU + FP64 iterative refinement (default)         */
+} stokes_wall_solver;
 typedef struct stokes_mlp stokes_mlp;
 
 /* Initial iterate of the step's GMRES. */
@@ -394,6 +441,11 @@ STOKES_API int stokes_sim_set_walls(stokes_sim *sim, int n_per_wall, const doubl
  * [8, 256]; kappa_B, mu and period (0 = no images, else equal to the walls'). */
 STOKES_API int stokes_sim_set_vesicles(stokes_sim *sim, int V, int n, const double *x,
                                        double kappa_b, double mu, double period);
+/* Wall solver mode (stokes_wall_solver; read at the next set_walls) and the statistics of the
+ * last wall solve (see above). */
+STOKES_API int stokes_sim_set_wall_solver(stokes_sim *sim, int mode);
+STOKES_API int stokes_sim_wall_stats(const stokes_sim *sim, int *refinements, double *residual);
+STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
 /* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
 STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
                                            double *u_resp);
@@ -401,6 +453,12 @@ STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, dou
  * g_u = 0, g_T = p_drive n, at n_targets DEVICE points. */
 STOKES_API int stokes_sim_empty_channel(stokes_sim *sim, double p_drive, const double *v_walls,
                                         int n_targets, const double *targets, double *u_out);
+/* Pressure of the same flow, p = P^near tau + sum_m c_m . Q(., y_m) (Eq. (P), (Q)), at
+ * n_targets DEVICE points (p_out DEVICE double[n_targets]).  The representation fixes the
+ * pressure's additive constant; the exact Poiseuille pressure is matched up to a constant. */
+STOKES_API int stokes_sim_empty_channel_pressure(stokes_sim *sim, double p_drive,
+                                                 const double *v_walls, int n_targets,
+                                                 const double *targets, double *p_out);
 /* One time step.  guess_mode is a stokes_guess; model is required for STOKES_GUESS_MLP
  * (n >= 16) and guess (DEVICE, 3 n V, layout above) for STOKES_GUESS_USER.  GMRES always runs
  * to tol, so every guess only changes the iteration count, not the answer's tolerance. */

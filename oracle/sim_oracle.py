@@ -47,6 +47,49 @@ def stresslet(x, y, ny):
     return np.einsum("...i,...j->...ij", r, r) * (rn / (PI * rr * rr))[..., None, None]
 
 
+def slp_pressure(x, y):
+    """Q(x, y), Eq. (Q): pressure at x of the stokeslet at y, (1/(2 pi)) r / r^2 (row vector)."""
+    r = np.asarray(x, float) - np.asarray(y, float)
+    rr = (r * r).sum(-1)
+    return r / (2 * PI * rr[..., None])
+
+
+def dlp_pressure(x, y, ny, mu):
+    """P(x, y), Eq. (P): pressure at x of the double layer at y, (mu/pi)(-n_y/r^2 + 2 (r.n_y) r/r^4)."""
+    r = np.asarray(x, float) - np.asarray(y, float)
+    ny = np.broadcast_to(ny, r.shape)
+    rr = (r * r).sum(-1)
+    rn = (r * ny).sum(-1)
+    return (mu / PI) * (-ny / rr[..., None] + 2 * (rn / (rr * rr))[..., None] * r)
+
+
+def layer_fields(src, w, nrm, kind, slp, dlp, period, mu, pts, pts_normals=None):
+    """Pressure and (with target normals) traction at free points of the near-image layer
+    potentials: sum over images m = -1, 0, 1 and every source j of Q w f (vesicle sources,
+    Eq. (Q)) + P w tau (wall sources, Eq. (P)), and K w f + T w tau (Eq. (K), (T)); plain
+    trapezoid rule, nothing skipped (the targets lie off the curves).  src (N, 2), kind (N,)
+    0 = wall, 1 = vesicle; slp / dlp are the densities of the vesicle / wall nodes in node order."""
+    pts = np.atleast_2d(np.asarray(pts, float))
+    ves = kind == 1
+    dens = np.zeros_like(src)
+    dens[ves] = slp
+    dens[~ves] = dlp
+    q = w[:, None] * dens
+    p = np.zeros(len(pts))
+    t = np.zeros_like(pts) if pts_normals is not None else None
+    images = (-1, 0, 1) if period != 0.0 else (0,)
+    for m in images:
+        y = src + np.array([m * period, 0.0])
+        p += np.einsum("pji,ji->p", slp_pressure(pts[:, None], y[None, ves]), q[ves])
+        p += np.einsum("pji,ji->p", dlp_pressure(pts[:, None], y[None, ~ves], nrm[None, ~ves], mu), q[~ves])
+        if t is not None:
+            nx = pts_normals[:, None, :]
+            t += np.einsum("pjik,jk->pi", slp_traction(pts[:, None], y[None, ves], nx), q[ves])
+            t += np.einsum("pjik,jk->pi", dlp_traction(pts[:, None], y[None, ~ves], nx,
+                                                       nrm[None, ~ves], mu), q[~ves])
+    return p, t
+
+
 def slp_traction(x, y, nx):
     """K(x, y), Eq. (K): traction at x (normal n_x) of the stokeslet at y: -(1/pi) r r^T (r.n_x)/r^4."""
     r = np.asarray(x, float) - np.asarray(y, float)
@@ -153,6 +196,19 @@ class Walls:
         tau = Av - AB @ c
         return tau.reshape(-1, 2), c.reshape(-1, 2)
 
+    def solve_refined(self, v, g, sweeps=2, rcond=1e-13):
+        """The block solve followed by `sweeps` residual corrections on the whole extended
+        system: r = [v; g] - [A B; C Q][tau; c], (dtau, dc) = block solve of r.  The truncated
+        pseudo-inverse leaves a residual in the side-point rows; the corrections remove it."""
+        A, B, C, Q = self.A(), self.B(), self.C(), self.Q()
+        tau, c = (z.reshape(-1) for z in self.solve(v, g, rcond))
+        for _ in range(sweeps):
+            rv = v - A @ tau - B @ c
+            rg = g - C @ tau - Q @ c
+            dt, dc = self.solve(rv, rg, rcond)
+            tau, c = tau + dt.reshape(-1), c + dc.reshape(-1)
+        return tau.reshape(-1, 2), c.reshape(-1, 2)
+
     def solve_lstsq(self, v, g):
         """Minimum-norm least-squares solve of the whole rectangular system (SVD); used to pin
         the discretisation itself, independently of the block elimination."""
@@ -171,6 +227,17 @@ class Walls:
             u += np.einsum("pjik,jk->pi", stresslet(pts[:, None], y[None], self.n[None]) * self.w[None, :, None, None], tau)
         u += np.einsum("pmik,mk->pi", stokeslet(pts[:, None], self.proxy[None], self.mu), c)
         return u
+
+    def pressure(self, tau, c, pts):
+        """p = P^near tau + sum_m c_m . Q(., y_m) at free points (pressure of Eq. (urep))."""
+        pts = np.atleast_2d(pts)
+        p = np.zeros(len(pts))
+        for m in (-1, 0, 1):
+            y = self.x + np.array([m * self.d, 0.0])
+            P = dlp_pressure(pts[:, None], y[None], self.n[None], self.mu) * self.w[None, :, None]
+            p += np.einsum("pji,ji->p", P, tau)
+        p += np.einsum("pmi,mi->p", slp_pressure(pts[:, None], self.proxy[None]), c)
+        return p
 
     def traction(self, tau, c, pts, nrm):
         """Traction of (D^near tau + proxy stokeslets) at pts with normal nrm (Eq. (T), (K))."""
@@ -424,7 +491,7 @@ def step(ves_x, sigma, L0, A0, dt, kappa_b, mu, period, walls=None, p_drive=0.0,
     if walls is not None:
         wv = np.concatenate([curve_normals_weights(x)[1] for x in ves_x])
         v, g = vesicle_rhs(walls, xv, wv, f, p_drive)
-        tau, c = walls.solve(v, g)
+        tau, c = walls.solve_refined(v, g)
         u_resp = walls.velocity(tau, c, xv)
     else:
         u_resp = np.zeros_like(xv)

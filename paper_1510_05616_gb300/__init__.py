@@ -34,6 +34,8 @@ STOKES_GUESS_ZERO = 0
 STOKES_GUESS_PREVIOUS = 1
 STOKES_GUESS_MLP = 2
 STOKES_GUESS_USER = 3
+STOKES_WALLS_LU64 = 0
+STOKES_WALLS_LU32_REFINE = 1
 N_FEATURES = 64
 N_TARGETS = 48
 
@@ -78,6 +80,12 @@ _SIGNATURES = {
                              _c_double],
     "stokes_sim_set_vesicles": [_vp, _c_int, _c_int, _vp, _c_double, _c_double, _c_double],
     "stokes_sim_channel_response": [_vp, _vp, _c_double, _vp],
+    "stokes_sim_set_wall_solver": [_vp, _c_int],
+    "stokes_sim_set_block_refinement": [_vp, _c_int],
+    "stokes_sim_empty_channel_pressure": [_vp, _c_double, _vp, _c_int, _vp, _vp],
+    "stokes_sum_eval_pressure": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp],
+    "stokes_sum_eval_traction": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp],
+    "stokes_sim_wall_stats": [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double)],
     "stokes_sim_empty_channel": [_vp, _c_double, _vp, _c_int, _vp, _vp],
     "vesicle_step_warmstart": [_vp, _c_double, _c_double, _c_int, _vp, _vp, _c_double, _c_int,
                                _c_int, _vp],
@@ -439,6 +447,48 @@ def stokes_sim_set_vesicles(h, V, n, x, kappa_b, mu, period):
     a, p = _host(x, "x")
     return _sim_check(h, load().stokes_sim_set_vesicles(h, int(V), int(n), p, float(kappa_b),
                                                         float(mu), float(period)))
+
+
+def stokes_sim_empty_channel_pressure(h, p_drive, v_walls, targets, p_out):
+    return _sim_check(h, load().stokes_sim_empty_channel_pressure(
+        h, float(p_drive), _dptr(v_walls, "v_walls", (2,), True), int(targets.shape[0]),
+        _dptr(targets, "targets", (2,)), _dptr(p_out, "p_out")))
+
+
+def stokes_sum_eval_pressure(h, slp_density, dlp_density, targets, out_pressure, stream=None):
+    """Pressure of the layer potentials at free points (FP64), shape (T,)."""
+    code = load().stokes_sum_eval_pressure(
+        h, _dptr(slp_density, "slp_density", (2,), True), _dptr(dlp_density, "dlp_density", (2,), True),
+        int(targets.shape[0]), _dptr(targets, "targets", (2,)), _dptr(out_pressure, "out_pressure"),
+        _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sum_eval_traction(h, slp_density, dlp_density, targets, target_normals, out_traction,
+                             stream=None):
+    """Traction of the layer potentials at free points with normals (FP64), shape (T, 2)."""
+    code = load().stokes_sum_eval_traction(
+        h, _dptr(slp_density, "slp_density", (2,), True), _dptr(dlp_density, "dlp_density", (2,), True),
+        int(targets.shape[0]), _dptr(targets, "targets", (2,)),
+        _dptr(target_normals, "target_normals", (2,)), _dptr(out_traction, "out_traction", (2,)),
+        _stream(stream))
+    return _check(h, code)
+
+
+def stokes_sim_set_wall_solver(h, mode):
+    """STOKES_WALLS_LU32_REFINE (default) or STOKES_WALLS_LU64; read at the next set_walls."""
+    return _sim_check(h, load().stokes_sim_set_wall_solver(h, int(mode)))
+
+
+def stokes_sim_set_block_refinement(h, sweeps):
+    return _sim_check(h, load().stokes_sim_set_block_refinement(h, int(sweeps)))
+
+
+def stokes_sim_wall_stats(h):
+    """(refinement sweeps, relative residual) of the last wall solve."""
+    a, b = _c_int(), _c_double()
+    _sim_check(h, load().stokes_sim_wall_stats(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def stokes_sim_channel_response(h, f, p_drive, u_resp):

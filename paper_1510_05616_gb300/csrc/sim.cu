@@ -54,6 +54,18 @@ struct stokes_sim {
   double2 *d_proxy = nullptr;          // [M]
   double *d_LU = nullptr, *d_W = nullptr, *d_C = nullptr, *d_Spinv = nullptr;
   int *d_piv = nullptr, *d_info = nullptr;
+  // wall solver: STOKES_WALLS_LU64 factors A in FP64; STOKES_WALLS_LU32_REFINE inverts an FP32
+  // copy (LU, then the inverse, d_Ainv32) and refines every solve with FP64 residuals of the
+  // FP64 A (d_A)
+  int wall_solver = STOKES_WALLS_LU32_REFINE;
+  cusolverDnParams_t params = nullptr;
+  double *d_A = nullptr;
+  float *d_Ainv32 = nullptr;
+  double *d_wb = nullptr, *d_wr = nullptr;  // refinement right-hand sides and residuals
+  float *d_wr32 = nullptr, *d_wb32 = nullptr;  // FP32 residual and correction
+  size_t wall_ws_len = 0;                   // capacity of d_wb / d_wr / d_wr32 (elements)
+  int wall_refinements = 0;                 // last wall solve: refinement sweeps and
+  double wall_residual = 0.0;               //   relative residual ||b - A x|| / ||b||
   // vesicles
   bool have_ves = false;
   int V = 0, n = 0, Nv = 0;
@@ -65,6 +77,12 @@ struct stokes_sim {
   double2 *d_f = nullptr, *d_fb = nullptr, *d_ures = nullptr, *d_tmp2 = nullptr, *d_tmp3 = nullptr;
   double *d_vrhs = nullptr, *d_g = nullptr, *d_y = nullptr, *d_r = nullptr, *d_c = nullptr;
   double *d_tau = nullptr;
+  // refinement of the block solve on the whole extended system: B and Q kept, right-hand
+  // side copies, residuals and corrections
+  int block_refine = 2;
+  double *d_B = nullptr, *d_Q = nullptr;
+  double *d_rv = nullptr, *d_rg = nullptr, *d_resv = nullptr, *d_resg = nullptr;
+  double *d_dtau = nullptr, *d_dc = nullptr, *d_g2 = nullptr;
   // preconditioner (per vesicle 3n x 3n) and GMRES workspace
   double *d_G = nullptr, *d_Ds = nullptr, *d_D2 = nullptr, *d_D4 = nullptr, *d_T = nullptr;
   double *d_P = nullptr, *d_Pinv = nullptr;
@@ -344,6 +362,19 @@ __global__ void proxy_eval_kernel(int n_t, const double2 *xt, int M, const doubl
   }
   u[i].x += ux;
   u[i].y += uy;
+}
+
+// p_i += sum_m c_m . Q(x_i, y_m), Q = r / (2 pi r^2) (Eq. (Q); pressure of the proxy part).
+__global__ void proxy_pressure_kernel(int n_t, const double2 *xt, int M, const double2 *proxy,
+                                      const double *c, double *p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_t) return;
+  double acc = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double r1 = xt[i].x - proxy[m].x, r2 = xt[i].y - proxy[m].y;
+    acc += (r1 * c[2 * m] + r2 * c[2 * m + 1]) / (r1 * r1 + r2 * r2);
+  }
+  p[i] += acc / (2.0 * kPiD);
 }
 
 __global__ void axpby_kernel(long n, double a, const double *x, double b, double *y) {
@@ -860,8 +891,130 @@ int set_stream_handles(stokes_sim *m) {
   return STOKES_OK;
 }
 
+__global__ void d2f_kernel(size_t n, const double *a, float *b) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
+__global__ void add_f2d_kernel(size_t n, const float *a, double *b) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    b[i] += double(a[i]);
+}
+
+inline int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, size_t(152) * 32)); }
+
+__global__ void identity_f32_kernel(int64_t n, float *a) {
+  const size_t nn = size_t(n) * size_t(n);
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < nn; i += size_t(gridDim.x) * blockDim.x)
+    a[i] = (i % size_t(n + 1) == 0) ? 1.0f : 0.0f;
+}
+
+// X (nA x nrhs, column-major) <- A^-1 X.  FP64 LU: one getrs.  FP32 inverse + refinement:
+// starting from x = 0 and r = b, repeat  x += A32^-1 r (FP32 GEMV / GEMM of the FP32-rounded
+// residual; A32^-1 is the inverse of the FP32-rounded A, formed once from its LU),
+// r = b - A x (FP64 GEMV / GEMM with the FP64 A)  until ||r|| <= 1e-14 ||b||, the residual stops
+// shrinking (its FP64 rounding floor), or 12 sweeps.  A = -I/2 + D is a second-kind operator
+// with a small condition number, so each sweep gains about five digits; every sweep streams
+// the two dense matrices once instead of running latency-bound triangular solves.
+int wall_solve(stokes_sim *m, double *X, int nrhs) {
+  const int64_t nA = m->nA;
+  if (m->wall_solver == STOKES_WALLS_LU64) {
+    QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, nrhs, m->d_LU, m->nA, m->d_piv, X, m->nA,
+                        m->d_info));
+    m->wall_refinements = 0;
+    m->wall_residual = 0.0;
+    return STOKES_OK;
+  }
+  const size_t len = size_t(nA) * nrhs;
+  if (len > m->wall_ws_len) {
+    SK(dalloc(m->d_wb, len));
+    SK(dalloc(m->d_wr, len));
+    SK(dalloc(m->d_wr32, len));
+    SK(dalloc(m->d_wb32, len));
+    m->wall_ws_len = len;
+  }
+  SK(cudaMemcpyAsync(m->d_wb, X, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  SK(cudaMemcpyAsync(m->d_wr, X, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  SK(cudaMemsetAsync(X, 0, sizeof(double) * len, m->s));
+  double bn = 0.0;
+  BK(cublasDnrm2_64(m->blas, int64_t(len), m->d_wb, 1, &bn));
+  m->wall_refinements = 0;
+  m->wall_residual = 0.0;
+  if (!(bn > 0.0)) return STOKES_OK;
+  const double one = 1.0, mone = -1.0;
+  double prev = 1e300;
+  for (int it = 0; it < 12; ++it) {
+    d2f_kernel<<<grid_for(len), 256, 0, m->s>>>(len, m->d_wr, m->d_wr32);
+    const float fone = 1.0f, fzero = 0.0f;
+    float *corr = reinterpret_cast<float *>(m->d_wb32);
+    if (nrhs == 1)
+      BK(cublasSgemv_64(m->blas, CUBLAS_OP_N, nA, nA, &fone, m->d_Ainv32, nA, m->d_wr32, 1, &fzero,
+                        corr, 1));
+    else
+      BK(cublasSgemm_64(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, nA, nrhs, nA, &fone, m->d_Ainv32, nA,
+                        m->d_wr32, nA, &fzero, corr, nA));
+    add_f2d_kernel<<<grid_for(len), 256, 0, m->s>>>(len, corr, X);
+    SK(cudaGetLastError());
+    SK(cudaMemcpyAsync(m->d_wr, m->d_wb, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+    if (nrhs == 1)
+      BK(cublasDgemv_64(m->blas, CUBLAS_OP_N, nA, nA, &mone, m->d_A, nA, X, 1, &one, m->d_wr, 1));
+    else
+      BK(cublasDgemm_64(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, nA, nrhs, nA, &mone, m->d_A, nA, X, nA,
+                        &one, m->d_wr, nA));
+    double rn = 0.0;
+    BK(cublasDnrm2_64(m->blas, int64_t(len), m->d_wr, 1, &rn));
+    m->wall_refinements = it + 1;
+    m->wall_residual = rn / bn;
+    if (!(rn == rn)) return fail(m, STOKES_ERR_NONFINITE, "wall solve: non-finite residual");
+    if (rn <= 1e-14 * bn || rn > 0.5 * prev) break;
+    prev = rn;
+  }
+  return STOKES_OK;
+}
+
+// Block elimination of Sec. 4.1 for data (v, g): y = A^-1 v, c = S^+ (g - C y), tau = y - W c.
+int block_solve(stokes_sim *m, const double *v, const double *g, double *tau, double *c) {
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  SK(cudaMemcpyAsync(tau, v, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
+  ST(wall_solve(m, tau, 1));
+  SK(cudaMemcpyAsync(m->d_g2, g, sizeof(double) * 4 * m->K, cudaMemcpyDeviceToDevice, m->s));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, tau, 1, &one,
+                 m->d_g2, 1));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 2 * m->M, 4 * m->K, &one, m->d_Spinv, 2 * m->M, m->d_g2, 1,
+                 &zero, c, 1));
+  BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, c, 1, &one, tau, 1));
+  return STOKES_OK;
+}
+
+// The block solve for (d_rv, d_rg) into (d_tau, d_c), then block_refine residual corrections
+// on the whole extended system [A B; C Q]:  r = [v; g] - [A B; C Q][tau; c],
+// [tau; c] += block solve of r.  The truncated pseudo-inverse S^+ leaves a residual in the
+// side-point rows (~1e-6 of the data); the corrections remove it.  A tau is the walls'
+// double-layer sum with the interior jump -1/2 (the same operator as the assembled A), in
+// `prec` (FP64 or double-float).
+int refined_block_solve(stokes_sim *m, int prec) {
+  ST(block_solve(m, m->d_rv, m->d_rg, m->d_tau, m->d_c));
+  const double one = 1.0, mone = -1.0;
+  for (int k = 0; k < m->block_refine; ++k) {
+    ST(stokes_sum_eval(m->ctx_w, prec, nullptr, m->d_tau, -0.5, m->d_resv, m->s));
+    axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, 1.0, m->d_rv, -1.0, m->d_resv);
+    BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_B, m->nA, m->d_c, 1, &one,
+                   m->d_resv, 1));
+    SK(cudaMemcpyAsync(m->d_resg, m->d_rg, sizeof(double) * 4 * m->K, cudaMemcpyDeviceToDevice, m->s));
+    BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, m->d_tau, 1, &one,
+                   m->d_resg, 1));
+    BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, 2 * m->M, &mone, m->d_Q, 4 * m->K, m->d_c, 1, &one,
+                   m->d_resg, 1));
+    ST(block_solve(m, m->d_resv, m->d_resg, m->d_dtau, m->d_dc));
+    axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, 1.0, m->d_dtau, 1.0, m->d_tau);
+    axpby_kernel<<<nb(2 * m->M, 256), 256, 0, m->s>>>(2 * m->M, 1.0, m->d_dc, 1.0, m->d_c);
+    SK(cudaGetLastError());
+  }
+  return STOKES_OK;
+}
+
 // Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.  The
-// two pair sums run in `prec` (STOKES_FP64 or the equally accurate STOKES_DOUBLE_FLOAT).
+// pair sums run in `prec` (STOKES_FP64 or the equally accurate STOKES_DOUBLE_FLOAT).
 int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out,
                      int prec = STOKES_FP64) {
   const double cmu = 1.0 / (4.0 * kPiD * m->mu);
@@ -869,21 +1022,11 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
                              m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
   side_rhs_kernel<<<m->K, 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w, f, m->period,
-                                          cmu, p_drive, m->d_g);
+                                          cmu, p_drive, m->d_rg);
+  // v = -(S^near f) at the walls
+  axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, -1.0, m->d_vrhs, 0.0, m->d_rv);
   SK(cudaGetLastError());
-  // y = A^-1 (-v)
-  axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, -1.0, m->d_vrhs, 0.0, m->d_y);
-  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, 1, m->d_LU, m->nA, m->d_piv, m->d_y, m->nA,
-                      m->d_info));
-  // r = g - C y ; c = S^+ r ; tau = y - W c
-  const double one = 1.0, mone = -1.0, zero = 0.0;
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, m->d_y, 1, &one,
-                 m->d_g, 1));
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 2 * m->M, 4 * m->K, &one, m->d_Spinv, 2 * m->M, m->d_g, 1,
-                 &zero, m->d_c, 1));
-  SK(cudaMemcpyAsync(m->d_tau, m->d_y, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, m->d_c, 1, &one,
-                 m->d_tau, 1));
+  ST(refined_block_solve(m, prec));
   // u_resp = D^near tau + sum_m c_m S(., y_m) at the vesicle nodes
   ST(stokes_sum_eval_targets(m->ctx_w, prec, nullptr, m->d_tau, m->Nv,
                              reinterpret_cast<const double *>(m->d_x),
@@ -1054,6 +1197,13 @@ void free_walls(stokes_sim *m) {
   dfree(m->d_side);
   dfree(m->d_proxy);
   dfree(m->d_LU);
+  dfree(m->d_A);
+  dfree(m->d_Ainv32);
+  dfree(m->d_wb);
+  dfree(m->d_wr);
+  dfree(m->d_wr32);
+  dfree(m->d_wb32);
+  m->wall_ws_len = 0;
   dfree(m->d_W);
   dfree(m->d_C);
   dfree(m->d_Spinv);
@@ -1063,6 +1213,9 @@ void free_walls(stokes_sim *m) {
   dfree(m->d_y);
   dfree(m->d_c);
   dfree(m->d_tau);
+  for (double **p : {&m->d_B, &m->d_Q, &m->d_rv, &m->d_rg, &m->d_resv, &m->d_resg, &m->d_dtau,
+                     &m->d_dc, &m->d_g2})
+    dfree(*p);
   m->have_walls = false;
 }
 
@@ -1103,6 +1256,7 @@ int stokes_sim_create(int device, stokes_sim **out) {
       cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
       cublasCreate(&m->blas) != CUBLAS_STATUS_SUCCESS ||
       cusolverDnCreate(&m->sol) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnCreateParams(&m->params) != CUSOLVER_STATUS_SUCCESS ||
       cudaMalloc(reinterpret_cast<void **>(&m->d_info), sizeof(int)) != cudaSuccess) {
     delete m;
     return STOKES_ERR_CUDA;
@@ -1123,6 +1277,7 @@ int stokes_sim_destroy(stokes_sim *m) {
   free_vesicles(m);
   dfree(m->d_info);
   if (m->blas) cublasDestroy(m->blas);
+  if (m->params) cusolverDnDestroyParams(m->params);
   if (m->sol) cusolverDnDestroy(m->sol);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1196,26 +1351,70 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(cudaMemcpy(m->d_proxy, prox.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
   // assemble A, B, C, Q
   double *dQ = nullptr, *dS = nullptr, *dU = nullptr, *dVt = nullptr, *dsig = nullptr;
-  SK(dalloc(m->d_LU, size_t(nA) * nA));
+  const bool lu32 = m->wall_solver == STOKES_WALLS_LU32_REFINE;
+  double *dA = nullptr;
+  SK(dalloc(dA, size_t(nA) * nA));
+  (lu32 ? m->d_A : m->d_LU) = dA;
   SK(dalloc(m->d_W, size_t(nA) * 2 * M));
   SK(dalloc(m->d_C, size_t(4) * K * nA));
   SK(dalloc(dQ, size_t(4) * K * 2 * M));
-  SK(dalloc(m->d_piv, nA));
+  if (!lu32) SK(dalloc(m->d_piv, nA));
   const double cmu = 1.0 / (4.0 * kPiD * mu);
   const double2 *wx = m->d_wx, *wn = reinterpret_cast<const double2 *>(dn);
-  assemble_A_kernel<<<dim3(nb(Nt, 128), Nt), 128, 0, m->s>>>(Nt, wx, wn, dw, dk, period, m->d_LU);
+  assemble_A_kernel<<<dim3(nb(Nt, 128), Nt), 128, 0, m->s>>>(Nt, wx, wn, dw, dk, period, dA);
   assemble_B_kernel<<<dim3(nb(Nt, 128), M), 128, 0, m->s>>>(Nt, M, wx, m->d_proxy, cmu, m->d_W);
+  SK(dalloc(m->d_B, size_t(nA) * 2 * M));
+  SK(cudaMemcpyAsync(m->d_B, m->d_W, sizeof(double) * nA * 2 * M, cudaMemcpyDeviceToDevice, m->s));
   assemble_C_kernel<<<dim3(nb(Nt, 128), K), 128, 0, m->s>>>(Nt, K, wx, wn, dw, m->d_side, period, mu,
                                                            m->d_C);
   assemble_Q_kernel<<<dim3(nb(K, 64), M), 64, 0, m->s>>>(K, M, m->d_side, m->d_proxy, cmu, dQ);
+  SK(dalloc(m->d_Q, size_t(4) * K * 2 * M));
+  SK(cudaMemcpyAsync(m->d_Q, dQ, sizeof(double) * 4 * K * 2 * M, cudaMemcpyDeviceToDevice, m->s));
   SK(cudaGetLastError());
-  // LU of A; W = A^-1 B
-  int lwork = 0;
-  QK(cusolverDnDgetrf_bufferSize(m->sol, nA, nA, m->d_LU, nA, &lwork));
+  // LU of A (FP64, or FP32 with FP64 refinement); W = A^-1 B
   double *work = nullptr;
-  SK(dalloc(work, lwork));
-  QK(cusolverDnDgetrf(m->sol, nA, nA, m->d_LU, nA, work, m->d_piv, m->d_info));
-  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, nA, 2 * M, m->d_LU, nA, m->d_piv, m->d_W, nA, m->d_info));
+  float *lu32f = nullptr;
+  int64_t *piv64 = nullptr;
+  if (lu32) {
+    const size_t nn = size_t(nA) * nA;
+    SK(dalloc(lu32f, nn));
+    SK(dalloc(piv64, nA));
+    d2f_kernel<<<grid_for(nn), 256, 0, m->s>>>(nn, dA, lu32f);
+    SK(cudaGetLastError());
+    size_t wd = 0, wh = 0;
+    QK(cusolverDnXgetrf_bufferSize(m->sol, m->params, nA, nA, CUDA_R_32F, lu32f, nA, CUDA_R_32F,
+                                   &wd, &wh));
+    SK(dalloc(work, wd / sizeof(double) + 1));
+    std::vector<char> hwork(std::max<size_t>(wh, 1));
+    QK(cusolverDnXgetrf(m->sol, m->params, nA, nA, CUDA_R_32F, lu32f, nA, piv64, CUDA_R_32F,
+                        work, wd, hwork.data(), wh, m->d_info));
+  } else {
+    int lwork = 0;
+    QK(cusolverDnDgetrf_bufferSize(m->sol, nA, nA, m->d_LU, nA, &lwork));
+    SK(dalloc(work, lwork));
+    QK(cusolverDnDgetrf(m->sol, nA, nA, m->d_LU, nA, work, m->d_piv, m->d_info));
+  }
+  {
+    int finfo = 0;
+    SK(cudaMemcpyAsync(&finfo, m->d_info, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    SK(cudaStreamSynchronize(m->s));
+    if (finfo != 0) {
+      cudaFree(lu32f);
+      cudaFree(piv64);
+      return fail(m, STOKES_ERR_CUDA, "LU of the wall operator failed (info %d)", finfo);
+    }
+  }
+  if (lu32) {  // A32^-1 from the FP32 LU: solve A32 X = I, then drop the factors
+    SK(dalloc(m->d_Ainv32, size_t(nA) * nA));
+    identity_f32_kernel<<<grid_for(size_t(nA) * nA), 256, 0, m->s>>>(nA, m->d_Ainv32);
+    SK(cudaGetLastError());
+    QK(cusolverDnXgetrs(m->sol, m->params, CUBLAS_OP_N, nA, nA, CUDA_R_32F, lu32f, nA, piv64,
+                        CUDA_R_32F, m->d_Ainv32, nA, m->d_info));
+    SK(cudaStreamSynchronize(m->s));
+    cudaFree(lu32f);
+    cudaFree(piv64);
+  }
+  ST(wall_solve(m, m->d_W, 2 * M));
   // S = Q - C W  (4K x 2M); SVD of S^T (2M x 4K, needs rows >= cols)
   const double one = 1.0, mone = -1.0, zero = 0.0;
   BK(cublasDgemm(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, 4 * K, 2 * M, nA, &mone, m->d_C, 4 * K, m->d_W,
@@ -1250,6 +1449,13 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(dalloc(m->d_y, nA));
   SK(dalloc(m->d_c, 2 * M));
   SK(dalloc(m->d_tau, nA));
+  SK(dalloc(m->d_rv, nA));
+  SK(dalloc(m->d_resv, nA));
+  SK(dalloc(m->d_dtau, nA));
+  SK(dalloc(m->d_rg, 4 * K));
+  SK(dalloc(m->d_resg, 4 * K));
+  SK(dalloc(m->d_g2, 4 * K));
+  SK(dalloc(m->d_dc, 2 * M));
   if (info != 0) return fail(m, STOKES_ERR_CUDA, "SVD of the Schur complement did not converge (%d)", info);
   m->have_walls = true;
   return STOKES_OK;
@@ -1354,27 +1560,78 @@ int stokes_sim_channel_response(stokes_sim *m, const double *f, double p_drive, 
   return STOKES_OK;
 }
 
+int stokes_sim_set_wall_solver(stokes_sim *m, int mode) {
+  if (!m) return STOKES_ERR_ARG;
+  if (mode != STOKES_WALLS_LU64 && mode != STOKES_WALLS_LU32_REFINE)
+    return fail(m, STOKES_ERR_ARG, "unknown wall solver %d", mode);
+  m->wall_solver = mode;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_block_refinement(stokes_sim *m, int sweeps) {
+  if (!m) return STOKES_ERR_ARG;
+  if (sweeps < 0 || sweeps > 8) return fail(m, STOKES_ERR_ARG, "block refinement sweeps must be in [0, 8]");
+  m->block_refine = sweeps;
+  return STOKES_OK;
+}
+
+int stokes_sim_wall_stats(const stokes_sim *m, int *refinements, double *residual) {
+  if (!m || !refinements || !residual) return STOKES_ERR_ARG;
+  *refinements = m->wall_refinements;
+  *residual = m->wall_residual;
+  return STOKES_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Density tau (d_tau) and proxy weights c (d_c) of the pressure-driven channel with wall
+// velocity v_walls (device, NULL = no slip): the refined block solve of the empty-channel system.
+int empty_solve(stokes_sim *m, double p_drive, const double *v_walls) {
+  empty_rhs_kernel<<<nb(4 * m->K, 128), 128, 0, m->s>>>(m->K, p_drive, m->d_rg);
+  if (v_walls)
+    SK(cudaMemcpyAsync(m->d_rv, v_walls, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
+  else
+    SK(cudaMemsetAsync(m->d_rv, 0, sizeof(double) * m->nA, m->s));
+  return refined_block_solve(m, STOKES_FP64);
+}
+
+}  // namespace
+
+extern "C" {
+
 int stokes_sim_empty_channel(stokes_sim *m, double p_drive, const double *v_walls, int n_targets,
                              const double *targets, double *u_out) {
   if (!m) return STOKES_ERR_ARG;
   if (!m->have_walls) return fail(m, STOKES_ERR_NO_GEOM, "walls must be set");
   if (n_targets < 1 || !targets || !u_out) return fail(m, STOKES_ERR_ARG, "need targets and output");
   SK(cudaSetDevice(m->device));
-  empty_rhs_kernel<<<nb(4 * m->K, 128), 128, 0, m->s>>>(m->K, p_drive, m->d_g);
-  if (v_walls)
-    SK(cudaMemcpyAsync(m->d_y, v_walls, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
-  else
-    SK(cudaMemsetAsync(m->d_y, 0, sizeof(double) * m->nA, m->s));
-  QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, 1, m->d_LU, m->nA, m->d_piv, m->d_y, m->nA, m->d_info));
-  const double one = 1.0, mone = -1.0, zero = 0.0;
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 4 * m->K, m->nA, &mone, m->d_C, 4 * m->K, m->d_y, 1, &one, m->d_g, 1));
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, 2 * m->M, 4 * m->K, &one, m->d_Spinv, 2 * m->M, m->d_g, 1, &zero, m->d_c, 1));
-  SK(cudaMemcpyAsync(m->d_tau, m->d_y, sizeof(double) * m->nA, cudaMemcpyDeviceToDevice, m->s));
-  BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_W, m->nA, m->d_c, 1, &one, m->d_tau, 1));
+  ST(empty_solve(m, p_drive, v_walls));
   ST(stokes_sum_eval_targets(m->ctx_w, STOKES_FP64, nullptr, m->d_tau, n_targets, targets, u_out, m->s));
   proxy_eval_kernel<<<nb(n_targets, 128), 128, 0, m->s>>>(n_targets, reinterpret_cast<const double2 *>(targets), m->M,
                                                          m->d_proxy, m->d_c, 1.0 / (4.0 * kPiD * m->mu),
                                                          reinterpret_cast<double2 *>(u_out));
+  SK(cudaGetLastError());
+  SK(cudaStreamSynchronize(m->s));
+  return STOKES_OK;
+}
+
+int stokes_sim_empty_channel_pressure(stokes_sim *m, double p_drive, const double *v_walls,
+                                      int n_targets, const double *targets, double *p_out) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_walls) return fail(m, STOKES_ERR_NO_GEOM, "walls must be set");
+  if (n_targets < 1 || !targets || !p_out) return fail(m, STOKES_ERR_ARG, "need targets and output");
+  SK(cudaSetDevice(m->device));
+  ST(empty_solve(m, p_drive, v_walls));
+  const int st = stokes_sum_eval_pressure(m->ctx_w, nullptr, m->d_tau, n_targets, targets, p_out, m->s);
+  if (st) {
+    char b[256];
+    stokes_last_error(m->ctx_w, b, sizeof(b));
+    return fail(m, st, "walls: %s", b);
+  }
+  proxy_pressure_kernel<<<nb(n_targets, 128), 128, 0, m->s>>>(
+      n_targets, reinterpret_cast<const double2 *>(targets), m->M, m->d_proxy, m->d_c, p_out);
   SK(cudaGetLastError());
   SK(cudaStreamSynchronize(m->s));
   return STOKES_OK;

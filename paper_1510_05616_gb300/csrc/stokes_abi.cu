@@ -16,6 +16,9 @@ cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
 void tune_apply_cached(stokes_ctx *c);  // tune.cu: shapes recorded for the geometry's size class
+int field_splits(const stokes_ctx *c, int n_targets);  // k_field.cu
+cudaError_t launch_field(stokes_ctx *c, int n_targets, const double2 *tgt, const double2 *tnrm,
+                         int splits, double *out, cudaStream_t s);
 }  // namespace stokes
 
 using namespace stokes;
@@ -682,6 +685,52 @@ int stokes_sum_eval_targets(stokes_ctx *c, int precision, const double *slp, con
   CK(launch_finish_free(c, splits, n_targets, reinterpret_cast<double2 *>(out), s));
   MARK(3);
   return STOKES_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Pressure (tnrm == NULL) or traction of the layer potentials at free points, FP64.
+int field_eval(stokes_ctx *c, const double *slp, const double *dlp, int n_targets,
+               const double *targets, const double *tnrm, double *out, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  int st = check_density_args(c, STOKES_FP64, slp, dlp);
+  if (st) return st;
+  if (n_targets < 0) return fail(c, STOKES_ERR_ARG, "n_targets < 0");
+  if (n_targets == 0) return STOKES_OK;
+  if (!targets || !out || !aligned16(targets) || (tnrm && !aligned16(tnrm)) ||
+      (reinterpret_cast<uintptr_t>(out) & 7u))
+    return fail(c, STOKES_ERR_ARG, "targets (and normals) must be 16-byte aligned device pointers, "
+                                   "the output 8-byte aligned");
+  if (c->n_inst > 1)
+    return fail(c, STOKES_ERR_ARG, "free-point evaluation needs a single-instance geometry");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  const int splits = field_splits(c, n_targets);
+  st = ensure_partial(c, size_t(splits) * n_targets);
+  if (st) return st;
+  CK(launch_pack(c, STOKES_FP64, slp, dlp, s));
+  CK(launch_field(c, n_targets, reinterpret_cast<const double2 *>(targets),
+                  reinterpret_cast<const double2 *>(tnrm), splits, out, s));
+  return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stokes_sum_eval_pressure(stokes_ctx *c, const double *slp, const double *dlp, int n_targets,
+                             const double *targets, double *out_pressure, void *stream) {
+  return field_eval(c, slp, dlp, n_targets, targets, nullptr, out_pressure, stream);
+}
+
+int stokes_sum_eval_traction(stokes_ctx *c, const double *slp, const double *dlp, int n_targets,
+                             const double *targets, const double *target_normals,
+                             double *out_traction, void *stream) {
+  if (c && !target_normals && n_targets > 0)
+    return fail(c, STOKES_ERR_ARG, "target_normals is NULL");
+  return field_eval(c, slp, dlp, n_targets, targets, target_normals, out_traction, stream);
 }
 
 int stokes_sum_eval_host(stokes_ctx *c, int precision, const double *slp_h, const double *dlp_h,

@@ -68,16 +68,17 @@ class Simulation:
             pass
 
 
-def collect(sim: Simulation, steps, dt, p_drive, guess="previous", tol=1e-10):
+def collect(sim: Simulation, steps, dt, p_drive, guess="previous", tol=1e-10,
+            precision=STOKES_FP64):
     """Run plain steps; return device tensors (features, targets) of every vesicle state and
-    the per-step statistics."""
+    the per-step statistics.  Every precision solves to the same FP64 tolerance."""
     import torch
     V = sim.V
     X = torch.empty((steps * V, N_FEATURES), dtype=torch.float32, device="cuda")
     T = torch.empty((steps * V, N_TARGETS), dtype=torch.float32, device="cuda")
     stats = []
     for k in range(steps):
-        stats.append(sim.step(dt, p_drive, guess, tol=tol))
+        stats.append(sim.step(dt, p_drive, guess, tol=tol, precision=precision))
         sim.features(X[k * V:(k + 1) * V], T[k * V:(k + 1) * V])
     return X, T, stats
 

@@ -60,26 +60,34 @@ def _case(seed=3, n_w=96, n_ves=3, n_v=16):
 PTS = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0], [2.0, 0.5], [5.0, -0.4]])
 
 
-def test_poiseuille_on_gpu(P, S):
-    """The GPU block solve reproduces the exact Poiseuille flow at the paper's accuracy level,
-    and agrees with the oracle's block solve."""
+@pytest.mark.parametrize("sweeps", [2, 0])
+def test_poiseuille_on_gpu(P, S, sweeps):
+    """The GPU block solve reproduces the exact Poiseuille flow: to round-off with the default
+    two refinement sweeps, at the paper's accuracy level (the truncation of S^+) without them;
+    and it agrees with the oracle's solve of the same kind."""
     import torch
     lo, up = I.wall_curves(128, I.WALL_SHAPE_SMALL)
     pd = 2 * MU * D * 0.2
     ue = lambda p: np.stack([-(pd / (2 * MU * D)) * p[:, 1] ** 2, 0 * p[:, 1]], 1)
-    h = make_sim(P, (lo, up), K=32, M=128)
+    h = P.stokes_sim_create(0)
+    P.stokes_sim_set_block_refinement(h, sweeps)
     xw = np.vstack([lo.nodes, up.nodes])
+    P.stokes_sim_set_walls(h, lo.n, xw, np.concatenate([lo.weights, up.weights]),
+                           np.vstack([lo.normals, up.normals]),
+                           np.concatenate([lo.curvature, up.curvature]), D, MU, 32, 128)
     out = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
     P.stokes_sim_empty_channel(h, pd, dev(ue(xw)), dev(PTS), out)
     u = out.cpu().numpy()
     P.stokes_sim_destroy(h)
     scale = np.abs(ue(xw)).max()
-    assert np.abs(u - ue(PTS)).max() / scale < 5e-6
+    tol = 1e-12 if sweeps else 5e-6
+    assert np.abs(u - ue(PTS)).max() / scale < tol
     W = S.Walls(lo, up, D, MU, K=32, M=128)
     _, g = S.empty_channel_rhs(W, pd)
-    tau, c = W.solve(ue(xw).reshape(-1), g)
+    tau, c = (W.solve_refined(ue(xw).reshape(-1), g, sweeps=sweeps) if sweeps
+              else W.solve(ue(xw).reshape(-1), g))
     ref = W.velocity(tau, c, PTS)
-    assert np.abs(u - ref).max() / scale < 5e-6
+    assert np.abs(u - ref).max() / scale < tol
 
 
 def test_channel_response_parity(P, S):
@@ -96,11 +104,11 @@ def test_channel_response_parity(P, S):
     xv = np.vstack([c.nodes for c in ves])
     wv = np.concatenate([S.curve_normals_weights(c.nodes)[1] for c in ves])
     v, g = S.vesicle_rhs(W, xv, wv, f, 0.8)
-    tau, c = W.solve(v, g)
+    tau, c = W.solve_refined(v, g)
     ref = W.velocity(tau, c, xv)
-    # both sides truncate the pseudo-inverse of the Schur complement at 1e-13 sigma_max, so they
-    # differ at the level of that truncation (each is within 5e-6 of the exact Poiseuille flow)
-    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-5
+    # both sides refine the block solve to round-off, so the truncation of S^+ no longer
+    # separates them
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-9
 
 
 def _oracle_step(S, ves_x, dt, walls=None, p_drive=0.0, period=D, kappa_b=1.0, K=24, M=96):
@@ -224,3 +232,47 @@ def test_double_float_step_matches_fp64_step(P):
     assert np.abs(soldf - sol64).max() < 1e-7 * np.abs(sol64).max()
     # x^{k+1} = x^k + dt u (then the area correction and reparameterization, both Lipschitz ~1)
     assert np.abs(xdf - x64).max() < 2 * 1e-3 * 1e-7 * np.abs(sol64).max()
+
+
+def test_wall_solvers_agree(P, S):
+    """The FP32-LU + FP64-refinement wall solver (default) reaches the FP64 solution: every
+    solve ends with an FP64 residual below 1e-13 and the channel response equals the FP64-LU
+    solver's up to the truncation of the Schur complement's pseudo-inverse."""
+    import torch
+    walls, ves = _case(n_w=256)
+    rng = np.random.default_rng(8)
+    f = rng.normal(size=(sum(c.n for c in ves), 2))
+    xw = np.vstack([walls[0].nodes, walls[1].nodes])
+    outs = {}
+    for mode in (P.STOKES_WALLS_LU64, P.STOKES_WALLS_LU32_REFINE):
+        h = P.stokes_sim_create(0)
+        P.stokes_sim_set_wall_solver(h, mode)
+        lo, up = walls
+        P.stokes_sim_set_walls(h, lo.n, xw, np.concatenate([lo.weights, up.weights]),
+                               np.vstack([lo.normals, up.normals]),
+                               np.concatenate([lo.curvature, up.curvature]), D, MU, 24, 96)
+        refs, res = P.stokes_sim_wall_stats(h)  # the solve for W = A^-1 B
+        if mode == P.STOKES_WALLS_LU32_REFINE:
+            assert 1 <= refs <= 6 and res < 1e-13, (refs, res)
+        else:
+            assert (refs, res) == (0, 0.0)
+        P.stokes_sim_set_vesicles(h, len(ves), ves[0].n, np.vstack([c.nodes for c in ves]), 1.0,
+                                  MU, D)
+        out = torch.zeros_like(dev(f))
+        P.stokes_sim_channel_response(h, dev(f), 0.8, out)
+        refs, res = P.stokes_sim_wall_stats(h)
+        if mode == P.STOKES_WALLS_LU32_REFINE:
+            assert 1 <= refs <= 6 and res < 1e-13, (refs, res)
+        pts = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
+        P.stokes_sim_empty_channel(h, 0.8, None, dev(PTS), pts)
+        outs[mode] = (out.cpu().numpy(), pts.cpu().numpy())
+        P.stokes_sim_destroy(h)
+    # with the refined block solve both reach the discrete system's solution
+    for a, b in zip(outs[P.STOKES_WALLS_LU64], outs[P.STOKES_WALLS_LU32_REFINE]):
+        assert np.abs(a - b).max() / np.abs(a).max() < 1e-10
+    with pytest.raises(P.StokesError):
+        h = P.stokes_sim_create(0)
+        try:
+            P.stokes_sim_set_wall_solver(h, 7)
+        finally:
+            P.stokes_sim_destroy(h)

@@ -97,6 +97,23 @@ def test_poiseuille_block_solve_within_paper_accuracy(S):
     assert err < 5e-6
 
 
+def test_poiseuille_refined_block_solve_exact(S):
+    """Two residual corrections of the block solve on the whole extended system remove the
+    truncation's error: the exact flow to round-off, as the least-squares solve."""
+    for shape in (I.WALL_SHAPE_SMALL, I.WALL_SHAPE_LARGE):
+        lo, up = I.wall_curves(128, shape)
+        W = S.Walls(lo, up, D, MU, K=32, M=128)
+        pd = 2 * MU * D * 0.2
+        ue = _poiseuille(pd)
+        _, g = S.empty_channel_rhs(W, pd)
+        tau, c = W.solve_refined(ue(W.x).reshape(-1), g)
+        err = np.abs(W.velocity(tau, c, PTS) - ue(PTS)).max() / np.abs(ue(W.x)).max()
+        assert err < 1e-12
+        p = W.pressure(tau, c, PTS)
+        off = p + pd * PTS[:, 0] / D
+        assert np.abs(off - off.mean()).max() / pd < 1e-12
+
+
 def test_pressure_drive_direction(S):
     """With no vesicles and zero wall velocity, p_drive > 0 drives flow towards +x."""
     lo, up = I.wall_curves(96, I.WALL_SHAPE_SMALL)
