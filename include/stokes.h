@@ -446,6 +446,11 @@ STOKES_API int stokes_sim_set_vesicles(stokes_sim *sim, int V, int n, const doub
 STOKES_API int stokes_sim_set_wall_solver(stokes_sim *sim, int mode);
 STOKES_API int stokes_sim_wall_stats(const stokes_sim *sim, int *refinements, double *residual);
 STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
+/* Precision of the factorization of the block-diagonal self preconditioner: STOKES_FP32_KAHAN
+ * (default: FP32 batched LU and inverse of the FP64-assembled blocks, applied with FP64
+ * products and sums, so it is still one fixed linear operator and GMRES's FP64 tolerance is
+ * unaffected) or STOKES_FP64.  Only the iteration counts can differ. */
+STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
 /* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
 STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
                                            double *u_resp);

@@ -87,6 +87,11 @@ struct stokes_sim {
   double *d_G = nullptr, *d_Ds = nullptr, *d_D2 = nullptr, *d_D4 = nullptr, *d_T = nullptr;
   double *d_P = nullptr, *d_Pinv = nullptr;
   double **d_Pptr = nullptr, **d_Piptr = nullptr;
+  // FP32 factorization of the same blocks (default): P32 = fl32(P), Pinv32 = its inverse,
+  // applied with FP64 accumulation (a fixed FP64 linear operator)
+  int precond_fp32 = 1;
+  float *d_P32 = nullptr, *d_Pinv32 = nullptr;
+  float **d_Pptr32 = nullptr, **d_Piptr32 = nullptr;
   int *d_ppiv = nullptr, *d_pinfo = nullptr;
   int gm_m = 0;
   double *d_V = nullptr, *d_z = nullptr, *d_b = nullptr, *d_wk = nullptr, *d_h = nullptr;
@@ -860,6 +865,36 @@ __global__ void set_ptrs_kernel(int count, double *base, size_t stride, double *
   if (t < count) ptrs[t] = base + stride * t;
 }
 
+__global__ void set_ptrs32_kernel(int count, float *base, size_t stride, float **ptrs) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) ptrs[t] = base + stride * t;
+}
+
+__global__ void d2f_small_kernel(size_t n, const double *a, float *b) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
+// zout_v = Pinv32_v zin_v for every vesicle v (one block each, k = 3n rows, column-major k x k
+// blocks), products and sums in FP64: the FP32-stored inverse acts as a fixed FP64 operator.
+__global__ void precond32_apply_kernel(int k, const float *Pinv, const double *zin, double *zout) {
+  extern __shared__ double zs[];
+  const size_t off = size_t(blockIdx.x) * k;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) zs[j] = zin[off + j];
+  __syncthreads();
+  const float *B = Pinv + size_t(blockIdx.x) * k * k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int j = 0;
+    for (; j + 1 < k; j += 2) {
+      a0 = fma(double(B[i + size_t(j) * k]), zs[j], a0);
+      a1 = fma(double(B[i + size_t(j + 1) * k]), zs[j + 1], a1);
+    }
+    if (j < k) a0 = fma(double(B[i + size_t(j) * k]), zs[j], a0);
+    zout[off + i] = a0 + a1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
@@ -1052,6 +1087,12 @@ int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, doub
 
 int precond_apply(stokes_sim *m, const double *zin, double *zout) {
   const int k = 3 * m->n;
+  if (m->precond_fp32) {
+    precond32_apply_kernel<<<m->V, std::min(k, 1024), sizeof(double) * k, m->s>>>(k, m->d_Pinv32,
+                                                                                  zin, zout);
+    SK(cudaGetLastError());
+    return STOKES_OK;
+  }
   const double one = 1.0, zero = 0.0;
   BK(cublasDgemvStridedBatched(m->blas, CUBLAS_OP_N, k, k, &one, m->d_Pinv, k, size_t(k) * k, zin, 1,
                                k, &zero, zout, 1, k, m->V));
@@ -1088,6 +1129,13 @@ int precond_build(stokes_sim *m, double dt) {
   }
   pc_fill_kernel<<<dim3(nb(3 * n * n, 256), V), 256, 0, m->s>>>(n, m->d_Ds, m->d_xs, m->d_P);
   SK(cudaGetLastError());
+  if (m->precond_fp32) {
+    d2f_small_kernel<<<nb(long(kk) * V, 256), 256, 0, m->s>>>(kk * V, m->d_P, m->d_P32);
+    SK(cudaGetLastError());
+    BK(cublasSgetrfBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_pinfo, V));
+    BK(cublasSgetriBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_Piptr32, k, m->d_pinfo, V));
+    return STOKES_OK;
+  }
   BK(cublasDgetrfBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_pinfo, V));
   BK(cublasDgetriBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_Piptr, k, m->d_pinfo, V));
   return STOKES_OK;
@@ -1101,7 +1149,7 @@ double dnrm(stokes_sim *m, long len, const double *x, int *st) {
 
 // Right-preconditioned restarted GMRES (classical Gram-Schmidt, twice) on z; FP64.
 int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, double tol,
-          int max_iter, int *iters, double *relres) {
+          int max_iter, int *iters, double *relres, bool x_zero = false) {
   const long len = 3L * m->Nv;
   const int mr = m->gm_m;
   int st = STOKES_OK;
@@ -1117,10 +1165,13 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
       hcol2(mr + 1);
   const double one = 1.0, zero = 0.0, mone = -1.0;
   while (true) {
-    // r = b - A x
-    ST(step_matvec(m, dt, precision, x, m->d_wk));
+    // r = b - A x (r = b while x is the caller's zero iterate)
     SK(cudaMemcpyAsync(m->d_V, b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
-    BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_V, 1));
+    if (!x_zero) {
+      ST(step_matvec(m, dt, precision, x, m->d_wk));
+      BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_V, 1));
+    }
+    x_zero = false;
     const double beta = dnrm(m, len, m->d_V, &st);
     if (st) return fail(m, st, "cublasDnrm2 failed");
     *relres = beta / bn;
@@ -1236,6 +1287,10 @@ void free_vesicles(stokes_sim *m) {
   dfree(m->d_zprev);
   dfree(m->d_Pptr);
   dfree(m->d_Piptr);
+  dfree(m->d_P32);
+  dfree(m->d_Pinv32);
+  dfree(m->d_Pptr32);
+  dfree(m->d_Piptr32);
   dfree(m->d_ppiv);
   dfree(m->d_pinfo);
   m->have_ves = false;
@@ -1525,6 +1580,12 @@ int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double
   SK(dalloc(m->d_pinfo, V));
   set_ptrs_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_P, kk, m->d_Pptr);
   set_ptrs_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_Pinv, kk, m->d_Piptr);
+  SK(dalloc(m->d_P32, kk * V));
+  SK(dalloc(m->d_Pinv32, kk * V));
+  SK(dalloc(m->d_Pptr32, V));
+  SK(dalloc(m->d_Piptr32, V));
+  set_ptrs32_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_P32, kk, m->d_Pptr32);
+  set_ptrs32_kernel<<<nb(V, 128), 128, 0, m->s>>>(V, m->d_Pinv32, kk, m->d_Piptr32);
   m->gm_m = 80;
   const long len = 3L * Nv;
   SK(dalloc(m->d_V, size_t(len) * (m->gm_m + 1)));
@@ -1565,6 +1626,14 @@ int stokes_sim_set_wall_solver(stokes_sim *m, int mode) {
   if (mode != STOKES_WALLS_LU64 && mode != STOKES_WALLS_LU32_REFINE)
     return fail(m, STOKES_ERR_ARG, "unknown wall solver %d", mode);
   m->wall_solver = mode;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_precond_precision(stokes_sim *m, int precision) {
+  if (!m) return STOKES_ERR_ARG;
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fail(m, STOKES_ERR_ARG, "preconditioner precision must be STOKES_FP64 or STOKES_FP32_KAHAN");
+  m->precond_fp32 = precision == STOKES_FP32_KAHAN;
   return STOKES_OK;
 }
 
@@ -1707,7 +1776,8 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   double rel = 0.0;
   int gst = STOKES_OK;
   if (precision != STOKES_FP32_KAHAN) {
-    gst = gmres(m, dt, hp, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel);
+    gst = gmres(m, dt, hp, m->d_b, m->d_xsol, tol, max_iter, &iters, &rel,
+                guess_mode == STOKES_GUESS_ZERO);
   } else {
     // Mixed precision: corrections from GMRES with FP32-Kahan pair sums, residuals of the
     // FP64-accurate (double-float) operator (iterative refinement) while each refinement cuts
@@ -1720,10 +1790,14 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     const double one = 1.0, mone = -1.0;
     double prev = 1e300;
     bool finish64 = false;
+    bool zero_iterate = guess_mode == STOKES_GUESS_ZERO;  // A 0 = 0: no matvec needed
     for (;;) {
-      ST(step_matvec(m, dt, hp, m->d_xsol, m->d_wk));
       SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
-      BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
+      if (!zero_iterate) {
+        ST(step_matvec(m, dt, hp, m->d_xsol, m->d_wk));
+        BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
+      }
+      zero_iterate = false;
       const double rn = dnrm(m, len, m->d_rr, &st);
       if (st) return fail(m, st, "cublasDnrm2 failed");
       rel = bn > 0.0 ? rn / bn : 0.0;
@@ -1739,7 +1813,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
       int it_in = 0;
       double rel_in = 0.0;
       const int gs = gmres(m, dt, STOKES_FP32_KAHAN, m->d_rr, m->d_dd, tin,
-                           std::min(40, max_iter - iters), &it_in, &rel_in);
+                           std::min(40, max_iter - iters), &it_in, &rel_in, true);
       iters += it_in;
       ++refinements;
       if (gs && gs != STOKES_ERR_NOT_CONVERGED) return gs;

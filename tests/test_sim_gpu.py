@@ -276,3 +276,27 @@ def test_wall_solvers_agree(P, S):
             P.stokes_sim_set_wall_solver(h, 7)
         finally:
             P.stokes_sim_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+def test_fp32_preconditioner_keeps_the_solution(P, prec):
+    """The FP32-factored block preconditioner (default) is one fixed FP64 operator: the step
+    solves to the same FP64 tolerance as with the FP64 factorization, to the same solution."""
+    walls, ves = _case(n_ves=3, n_v=32, n_w=96)
+    out = {}
+    for pc in (P.STOKES_FP64, P.STOKES_FP32_KAHAN):
+        h = make_sim(P, walls, ves)
+        P.stokes_sim_set_precond_precision(h, pc)
+        st = P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300,
+                                      precision=P.PRECISIONS[prec])
+        x, sg, sol = P.stokes_sim_get_state(h)
+        P.stokes_sim_destroy(h)
+        assert st["residual"] <= 1e-11
+        out[pc] = (st["iterations"], sol)
+    (i64, s64), (i32, s32) = out[P.STOKES_FP64], out[P.STOKES_FP32_KAHAN]
+    assert abs(i32 - i64) <= 3
+    assert np.abs(s32 - s64).max() <= 1e-6 * np.abs(s64).max()
+    h = P.stokes_sim_create(0)
+    with pytest.raises(P.StokesError):
+        P.stokes_sim_set_precond_precision(h, P.STOKES_DOUBLE_FLOAT)
+    P.stokes_sim_destroy(h)
