@@ -377,11 +377,15 @@ STOKES_API int stokes_tune_clear(void);
  *   STOKES_WALLS_LU64: FP64 LU (8 (4 N_w)^2 bytes), one triangular solve per solve.
  * stokes_sim_wall_stats: refinement sweeps and relative residual ||b - A x|| / ||b|| of the
  *   last wall solve (0 and 0 for STOKES_WALLS_LU64).
- * Block refinement (stokes_sim_set_block_refinement, 0..8, default 2): the block solve is
+ * Block refinement (stokes_sim_set_block_refinement, 0..8, default 3): the block solve is
  *   followed by that many residual corrections on the whole extended system,
  *   r = [v; g] - [A B; C Q][tau; c], [tau; c] += block solve of r, with A tau evaluated as the
  *   walls' double-layer sum.  The truncated S^+ alone leaves ~1e-6 of the data in the
- *   side-point rows (Poiseuille errors ~1e-6); two corrections bring it to round-off.
+ *   side-point rows (Poiseuille errors ~1e-6).  With corrections the wall solves inside the
+ *   block solves are single FP32-inverse sweeps (~1e-5 each; the corrections make up for
+ *   them), and three corrections bring the result to round-off.  With 0 corrections every
+ *   wall solve is refined to FP64 accuracy on its own.  (The solve of W = A^-1 B at
+ *   stokes_sim_set_walls is always refined to FP64 accuracy.)
  *
  * Time step (Algorithm 1 steps 2-9): forces f_b = -kappa_B x_ssss, f = f_b + (sigma x_s)_s;
  * u_resp of f; GMRES (FP64, right preconditioned by each vesicle's self interaction) on

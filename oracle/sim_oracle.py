@@ -196,7 +196,7 @@ class Walls:
         tau = Av - AB @ c
         return tau.reshape(-1, 2), c.reshape(-1, 2)
 
-    def solve_refined(self, v, g, sweeps=2, rcond=1e-13):
+    def solve_refined(self, v, g, sweeps=3, rcond=1e-13):
         """The block solve followed by `sweeps` residual corrections on the whole extended
         system: r = [v; g] - [A B; C Q][tau; c], (dtau, dc) = block solve of r.  The truncated
         pseudo-inverse leaves a residual in the side-point rows; the corrections remove it."""

@@ -60,10 +60,10 @@ def _case(seed=3, n_w=96, n_ves=3, n_v=16):
 PTS = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0], [2.0, 0.5], [5.0, -0.4]])
 
 
-@pytest.mark.parametrize("sweeps", [2, 0])
+@pytest.mark.parametrize("sweeps", [3, 0])
 def test_poiseuille_on_gpu(P, S, sweeps):
     """The GPU block solve reproduces the exact Poiseuille flow: to round-off with the default
-    two refinement sweeps, at the paper's accuracy level (the truncation of S^+) without them;
+    three refinement sweeps, at the paper's accuracy level (the truncation of S^+) without them;
     and it agrees with the oracle's solve of the same kind."""
     import torch
     lo, up = I.wall_curves(128, I.WALL_SHAPE_SMALL)
@@ -261,8 +261,8 @@ def test_wall_solvers_agree(P, S):
         out = torch.zeros_like(dev(f))
         P.stokes_sim_channel_response(h, dev(f), 0.8, out)
         refs, res = P.stokes_sim_wall_stats(h)
-        if mode == P.STOKES_WALLS_LU32_REFINE:
-            assert 1 <= refs <= 6 and res < 1e-13, (refs, res)
+        if mode == P.STOKES_WALLS_LU32_REFINE:  # single inner sweeps under the block refinement
+            assert (refs, res) == (1, -1.0), (refs, res)
         pts = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
         P.stokes_sim_empty_channel(h, 0.8, None, dev(PTS), pts)
         outs[mode] = (out.cpu().numpy(), pts.cpu().numpy())
