@@ -26,7 +26,9 @@
 //    are reduced across splits in FP64 by the same finishing kernels as the other paths.
 //
 // Tiling and pipeline as the FP64 path: 64-source tiles in the FP64 slot layout, staged by
-// cp.async.bulk into a 3-stage mbarrier ring with bounded waits; 64 threads x 2 targets.
+// cp.async.bulk into a 3-stage mbarrier ring with bounded waits; 64 threads x 2 targets, the
+// two targets of a thread evaluated together by packed .f32x2 arithmetic (one instruction
+// for both; the MUFU approximation and the logarithm's bit work and tables per target).
 #include "stokes_internal.cuh"
 #include "bulk_pipe.cuh"
 
@@ -291,65 +293,207 @@ __device__ __forceinline__ void load_target_df(const PairArgs &a, double period,
   t.skip = a.tgt_skip ? a.tgt_skip[i] : make_int2(-1, -1);
 }
 
-// Stokeslet source (Eq. (S)): adds, over the images, -(1/2) q log r^2 + r (r . q) / r^2 with
-// q = w f / (4 pi mu); one logarithm of the product of the images' r^2.  pa, pb: position
-// record; va = q, vb = p = -q/2.  MASK0 drops the m = 0 image (r^2 enters the product as 1).
-template <int NIMG, bool MASK0>
-__device__ __forceinline__ void slp_source_df(const TgtDF<NIMG> &t, float4 pa, float4 pb,
-                                              float4 va, float4 vb, bool skip0, df &ax, df &ay,
-                                              const float4 *kt, const float2 *et) {
-  const df dy = diff3(t.yh, t.ym, t.yl, pa.w, pb.x, pb.y);
-  const df q1{va.x, va.y}, q2{va.z, va.w}, p1{vb.x, vb.y}, p2{vb.z, vb.w};
-  const df dyq = df_mul(dy, q2);
-  const df py = df_sq(dy);
-  df dx[NIMG], inv[NIMG], P{1.0f, 0.0f};
-#pragma unroll
-  for (int k = 0; k < NIMG; ++k) {
-    dx[k] = diff3(t.xh[k], t.xm[k], t.xl[k], pa.x, pa.y, pa.z);
-    df r2 = df_add_pos(df_sq(dx[k]), py);
-    if (MASK0 && k == NIMG / 2 && skip0) r2 = df{1.0f, 0.0f};
-    inv[k] = df_rcp(r2);
-    P = (k == 0) ? r2 : df_mul(P, r2);
-  }
-  const df L = df_log(P, kt, et);
-  df_mul_acc(ax, L, p1);
-  df_mul_acc(ay, L, p2);
-  df cs{0.0f, 0.0f};
-#pragma unroll
-  for (int k = 0; k < NIMG; ++k) {
-    df coef = df_mul(df_add(df_mul(dx[k], q1), dyq), inv[k]);
-    if (MASK0 && k == NIMG / 2 && skip0) coef = df{0.0f, 0.0f};
-    df_mul_acc(ax, coef, dx[k]);
-    cs = (k == 0) ? coef : df_add(cs, coef);
-  }
-  df_mul_acc(ay, cs, dy);
-  df_renorm(ax);
-  df_renorm(ay);
+// ---------------------------------------------------------------------------
+// packed double-float arithmetic: the two targets of a thread in the two halves of .f32x2
+// registers, one instruction for both (the MUFU approximation, the logarithm's bit work and
+// table lookups stay per target)
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;  // two floats, the first target in the low word
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ f2 bc(float a) { return pk(a, a); }
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// -a (sign bits flipped on the integer pipe)
+__device__ __forceinline__ f2 neg2(f2 a) { return a ^ 0x8000000080000000ull; }
+
+struct df2 {
+  f2 h, l;
+};
+
+__device__ __forceinline__ df2 two_sum2(f2 a, f2 b) {
+  const f2 s = add2(a, b);
+  const f2 bb = sub2(s, a);
+  return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+// Exact when |a| >= |b| (or a == 0), per half.
+__device__ __forceinline__ df2 fast_two_sum2(f2 a, f2 b) {
+  const f2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ df2 df_mul2(df2 a, df2 b) {
+  const f2 p = mul2(a.h, b.h);
+  f2 e = fma2(a.h, b.h, neg2(p));
+  e = fma2(a.h, b.l, e);
+  e = fma2(a.l, b.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ df2 df_add2(df2 a, df2 b) {
+  const df2 s = two_sum2(a.h, b.h);
+  return {s.h, add2(s.l, add2(a.l, b.l))};
+}
+__device__ __forceinline__ df2 df_sq2(df2 a) {
+  const f2 p = mul2(a.h, a.h);
+  f2 e = fma2(a.h, a.h, neg2(p));
+  e = fma2(add2(a.h, a.h), a.l, e);
+  return {p, e};
+}
+// 1/a for a > 0 per half, as df_rcp.
+__device__ __forceinline__ df2 df_rcp2(df2 a) {
+  float h0, h1;
+  upk(a.h, h0, h1);
+  const f2 y0 = pk(rcp_approx(fmaxf(h0, 1e-30f)), rcp_approx(fmaxf(h1, 1e-30f)));
+  f2 e = fma2(neg2(a.h), y0, bc(1.0f));
+  e = fma2(neg2(a.l), y0, e);
+  return {y0, mul2(y0, fma2(e, e, e))};
+}
+__device__ __forceinline__ void df_mul_acc2(df2 &acc, df2 a, df2 b) {
+  const f2 p = mul2(a.h, b.h);
+  f2 e = fma2(a.h, b.h, neg2(p));
+  e = fma2(a.h, b.l, e);
+  e = fma2(a.l, b.h, e);
+  const df2 s = two_sum2(acc.h, p);
+  acc.h = s.h;
+  acc.l = add2(acc.l, add2(s.l, e));
+}
+__device__ __forceinline__ void df_renorm2(df2 &a) { a = fast_two_sum2(a.h, a.l); }
+// r = t - s from three-part coordinates (as diff3), targets packed, source broadcast.
+__device__ __forceinline__ df2 diff3_2(f2 th, f2 tm, f2 tl, float sh, float sm, float sl) {
+  const f2 A = sub2(th, bc(sh));
+  const f2 B = sub2(tm, bc(sm));
+  const f2 C = sub2(tl, bc(sl));
+  const df2 s = fast_two_sum2(A, B);
+  return {s.h, add2(s.l, C)};
+}
+__device__ __forceinline__ df2 df_log2(df2 P, const float4 *kt, const float2 *et) {
+  float h0, h1, l0, l1;
+  upk(P.h, h0, h1);
+  upk(P.l, l0, l1);
+  const df a = df_log(df{h0, l0}, kt, et), b = df_log(df{h1, l1}, kt, et);
+  return {pk(a.h, b.h), pk(a.l, b.l)};
+}
+// per-half select: where the flag is set, take the replacement
+__device__ __forceinline__ f2 sel2(f2 v, bool s0, bool s1, float r) {
+  float a, b;
+  upk(v, a, b);
+  return pk(s0 ? r : a, s1 ? r : b);
 }
 
-// Stresslet source (Eq. (D)): adds, over the images, r (r . n)(r . q) / r^4, q = w tau / pi.
-// va = q, vb = n.  The coincident wall self pair has r = 0 exactly and adds 0.
+// Two targets, packed: (x - m d) in three parts per image, y in three parts.
 template <int NIMG>
-__device__ __forceinline__ void dlp_source_df(const TgtDF<NIMG> &t, float4 pa, float4 pb,
-                                              float4 va, float4 vb, df &ax, df &ay) {
-  const df dy = diff3(t.yh, t.ym, t.yl, pa.w, pb.x, pb.y);
-  const df q1{va.x, va.y}, q2{va.z, va.w}, n1{vb.x, vb.y}, n2{vb.z, vb.w};
-  const df dyn = df_mul(dy, n2), dyq = df_mul(dy, q2);
-  const df py = df_sq(dy);
-  df fs{0.0f, 0.0f};
+struct TgtDF2 {
+  f2 xh[NIMG], xm[NIMG], xl[NIMG];
+  f2 yh, ym, yl;
+};
+
+template <int NIMG>
+__device__ __forceinline__ TgtDF2<NIMG> pack_targets_df(const TgtDF<NIMG> &a, const TgtDF<NIMG> &b) {
+  TgtDF2<NIMG> t;
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
-    const df dx = diff3(t.xh[k], t.xm[k], t.xl[k], pa.x, pa.y, pa.z);
-    const df inv = df_rcp(df_add_pos(df_sq(dx), py));
-    const df rn = df_add(df_mul(dx, n1), dyn);
-    const df rq = df_add(df_mul(dx, q1), dyq);
-    const df f = df_mul(df_mul(rn, inv), df_mul(rq, inv));
-    df_mul_acc(ax, f, dx);
-    fs = (k == 0) ? f : df_add(fs, f);
+    t.xh[k] = pk(a.xh[k], b.xh[k]);
+    t.xm[k] = pk(a.xm[k], b.xm[k]);
+    t.xl[k] = pk(a.xl[k], b.xl[k]);
   }
-  df_mul_acc(ay, fs, dy);
-  df_renorm(ax);
-  df_renorm(ay);
+  t.yh = pk(a.yh, b.yh);
+  t.ym = pk(a.ym, b.ym);
+  t.yl = pk(a.yl, b.yl);
+  return t;
+}
+
+// Stokeslet source (Eq. (S)) against two targets: adds, over the images, -(1/2) q log r^2 +
+// r (r . q) / r^2 with q = w f / (4 pi mu); one logarithm of the product of the images' r^2
+// per target.  pa, pb: position record; va = q, vb = p = -q/2.  MASK0 drops the m = 0 image
+// of a target whose flag (s0, s1) is set (its r^2 enters the product as 1).
+template <int NIMG, bool MASK0>
+__device__ __forceinline__ void slp_source_df2(const TgtDF2<NIMG> &t, float4 pa, float4 pb,
+                                               float4 va, float4 vb, bool s0, bool s1, df2 &ax,
+                                               df2 &ay, const float4 *kt, const float2 *et) {
+  const df2 dy = diff3_2(t.yh, t.ym, t.yl, pa.w, pb.x, pb.y);
+  const df2 q1{bc(va.x), bc(va.y)}, q2{bc(va.z), bc(va.w)}, p1{bc(vb.x), bc(vb.y)},
+      p2{bc(vb.z), bc(vb.w)};
+  const df2 dyq = df_mul2(dy, q2);
+  const df2 py = df_sq2(dy);
+  df2 dx[NIMG], inv[NIMG], P;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    dx[k] = diff3_2(t.xh[k], t.xm[k], t.xl[k], pa.x, pa.y, pa.z);
+    const df2 sq = df_sq2(dx[k]);
+    const df2 sh = two_sum2(sq.h, py.h);
+    df2 r2{sh.h, add2(sh.l, add2(sq.l, py.l))};
+    if (MASK0 && k == NIMG / 2 && (s0 || s1)) r2 = {sel2(r2.h, s0, s1, 1.0f), sel2(r2.l, s0, s1, 0.0f)};
+    inv[k] = df_rcp2(r2);
+    P = (k == 0) ? r2 : df_mul2(P, r2);
+  }
+  const df2 L = df_log2(P, kt, et);
+  df_mul_acc2(ax, L, p1);
+  df_mul_acc2(ay, L, p2);
+  df2 cs;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    df2 coef = df_mul2(df_add2(df_mul2(dx[k], q1), dyq), inv[k]);
+    if (MASK0 && k == NIMG / 2 && (s0 || s1))
+      coef = {sel2(coef.h, s0, s1, 0.0f), sel2(coef.l, s0, s1, 0.0f)};
+    df_mul_acc2(ax, coef, dx[k]);
+    cs = (k == 0) ? coef : df_add2(cs, coef);
+  }
+  df_mul_acc2(ay, cs, dy);
+  df_renorm2(ax);
+  df_renorm2(ay);
+}
+
+// Stresslet source (Eq. (D)) against two targets: adds, over the images,
+// r (r . n)(r . q) / r^4, q = w tau / pi.  va = q, vb = n.  The coincident wall self pair has
+// r = 0 exactly and adds 0.
+template <int NIMG>
+__device__ __forceinline__ void dlp_source_df2(const TgtDF2<NIMG> &t, float4 pa, float4 pb,
+                                               float4 va, float4 vb, df2 &ax, df2 &ay) {
+  const df2 dy = diff3_2(t.yh, t.ym, t.yl, pa.w, pb.x, pb.y);
+  const df2 q1{bc(va.x), bc(va.y)}, q2{bc(va.z), bc(va.w)}, n1{bc(vb.x), bc(vb.y)},
+      n2{bc(vb.z), bc(vb.w)};
+  const df2 dyn = df_mul2(dy, n2), dyq = df_mul2(dy, q2);
+  const df2 py = df_sq2(dy);
+  df2 fs;
+#pragma unroll
+  for (int k = 0; k < NIMG; ++k) {
+    const df2 dx = diff3_2(t.xh[k], t.xm[k], t.xl[k], pa.x, pa.y, pa.z);
+    const df2 sq = df_sq2(dx);
+    const df2 sh = two_sum2(sq.h, py.h);
+    const df2 inv = df_rcp2({sh.h, add2(sh.l, add2(sq.l, py.l))});
+    const df2 rn = df_add2(df_mul2(dx, n1), dyn);
+    const df2 rq = df_add2(df_mul2(dx, q1), dyq);
+    const df2 f = df_mul2(df_mul2(rn, inv), df_mul2(rq, inv));
+    df_mul_acc2(ax, f, dx);
+    fs = (k == 0) ? f : df_add2(fs, f);
+  }
+  df_mul_acc2(ay, fs, dy);
+  df_renorm2(ax);
+  df_renorm2(ay);
 }
 
 struct SmemDF {
@@ -405,15 +549,14 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
       const int tile = item_tile_df(it, vt);
       const float4 *P = sm.pos[st];
       const float4 *V = sm.val[st];
-      df ax[kTptDF], ay[kTptDF];
-#pragma unroll
-      for (int q = 0; q < kTptDF; ++q) ax[q] = ay[q] = df{0.0f, 0.0f};
+      static_assert(kTptDF == 2, "the packed double-float kernel takes two targets per thread");
+      const TgtDF2<NIMG> tp = pack_targets_df<NIMG>(tg[0], tg[1]);
+      df2 ax2{0ull, 0ull}, ay2{0ull, 0ull};
       if (vt < it.nw) {
 #pragma unroll 1
         for (int j = 0; j < kTileF64; ++j) {
           const float4 pa = P[2 * j], pb = P[2 * j + 1], va = V[2 * j], vb = V[2 * j + 1];
-#pragma unroll
-          for (int q = 0; q < kTptDF; ++q) dlp_source_df<NIMG>(tg[q], pa, pb, va, vb, ax[q], ay[q]);
+          dlp_source_df2<NIMG>(tp, pa, pb, va, vb, ax2, ay2);
         }
       } else {
         const int slot0 = tile * kTileF64;
@@ -425,22 +568,23 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
 #pragma unroll 1
           for (int j = 0; j < kTileF64; ++j) {
             const float4 pa = P[2 * j], pb = P[2 * j + 1], va = V[2 * j], vb = V[2 * j + 1];
-#pragma unroll
-            for (int q = 0; q < kTptDF; ++q) {
-              const bool s0 = (slot0 + j >= tg[q].skip.x) && (slot0 + j < tg[q].skip.y);
-              slp_source_df<NIMG, true>(tg[q], pa, pb, va, vb, s0, ax[q], ay[q], sm.kt, sm.et);
-            }
+            const bool s0 = (slot0 + j >= tg[0].skip.x) && (slot0 + j < tg[0].skip.y);
+            const bool s1 = (slot0 + j >= tg[1].skip.x) && (slot0 + j < tg[1].skip.y);
+            slp_source_df2<NIMG, true>(tp, pa, pb, va, vb, s0, s1, ax2, ay2, sm.kt, sm.et);
           }
         } else {
 #pragma unroll 1
           for (int j = 0; j < kTileF64; ++j) {
             const float4 pa = P[2 * j], pb = P[2 * j + 1], va = V[2 * j], vb = V[2 * j + 1];
-#pragma unroll
-            for (int q = 0; q < kTptDF; ++q)
-              slp_source_df<NIMG, false>(tg[q], pa, pb, va, vb, false, ax[q], ay[q], sm.kt, sm.et);
+            slp_source_df2<NIMG, false>(tp, pa, pb, va, vb, false, false, ax2, ay2, sm.kt, sm.et);
           }
         }
       }
+      df ax[kTptDF], ay[kTptDF];
+      upk(ax2.h, ax[0].h, ax[1].h);
+      upk(ax2.l, ax[0].l, ax[1].l);
+      upk(ay2.h, ay[0].h, ay[1].h);
+      upk(ay2.l, ay[0].l, ay[1].l);
 #pragma unroll
       for (int q = 0; q < kTptDF; ++q) {
         ux[q] += double(ax[q].h) + double(ax[q].l);
