@@ -917,10 +917,12 @@ PairKernel f32_kernel() {
 template <bool BATCH, int NIMG, int TPT>
 PairKernel f32_by_kg(int kg) {
   if constexpr (BATCH) {
-    return f32_kernel<true, NIMG, TPT, 4>();  // the batched launch always groups by 4
+    return f32_kernel<true, NIMG, TPT, 8>();  // the batched launch always groups by 8
   } else {
-    return kg == 1 ? f32_kernel<false, NIMG, TPT, 1>()
-                   : kg == 2 ? f32_kernel<false, NIMG, TPT, 2>() : f32_kernel<false, NIMG, TPT, 4>();
+    return kg == 1   ? f32_kernel<false, NIMG, TPT, 1>()
+           : kg == 2 ? f32_kernel<false, NIMG, TPT, 2>()
+           : kg == 8 ? f32_kernel<false, NIMG, TPT, 8>()
+                     : f32_kernel<false, NIMG, TPT, 4>();
   }
 }
 
@@ -1003,7 +1005,7 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
     a.n_items = c->n_items32;
     a.tgt_perm = c->d_tgt_perm;
     a.local_radius = c->local_frame ? c->local_radius : 0.f;
-    pick_f32(true, img, c->tpt_f32, 4)<<<blocks, kThreadsF32, 0, s>>>(a);
+    pick_f32(true, img, c->tpt_f32, 8)<<<blocks, kThreadsF32, 0, s>>>(a);
   } else {
     a.tgt_skip = c->d_tgt_skip64;
     a.src_pos = c->d_src_pos64;
@@ -1035,7 +1037,7 @@ int pair_batch_blocks_per_sm(stokes_ctx *c, int precision) {
   if (precision == STOKES_DOUBLE_FLOAT) return pair_df_batch_blocks_per_sm(c);
   const bool img = c->period != 0.0;
   if (precision == STOKES_FP32_KAHAN)
-    return occupancy(pick_f32(true, img, c->tpt_f32, 4), kThreadsF32);
+    return occupancy(pick_f32(true, img, c->tpt_f32, 8), kThreadsF32);
   return occupancy(pick_f64(true, img), kThreadsF64);
 }
 

@@ -60,7 +60,7 @@ def test_autotune_fp32k_applies_records_and_keeps_parity(P, mid):
     initial = P.stokes_get_launch(a.h, P.STOKES_FP32_KAHAN)
     r = P.stokes_autotune(a.h, P.STOKES_FP32_KAHAN, repeats=3)
     assert r["candidates"] >= 9
-    assert r["targets_per_thread"] in (1, 2, 4) and r["kahan_group"] in (1, 2, 4)
+    assert r["targets_per_thread"] in (1, 2, 4) and r["kahan_group"] in (2, 4, 8)
     assert r["source_splits"] >= 1
     assert 0.0 < r["best_ms"] <= r["initial_ms"]
     assert P.stokes_get_launch(a.h, P.STOKES_FP32_KAHAN) == (
