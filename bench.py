@@ -682,7 +682,7 @@ def main():
                      "peak_basis": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peak_kind,
                      "flops_per_pair": FLOPS_PER_PAIR},
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,  # per step: self (side stream), pack, pair, 2 finish
         "clocks": clk,
         "fp64_path": fp64,
         "double_float_path": dfl,
