@@ -456,6 +456,9 @@ STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
  * products and sums, so it is still one fixed linear operator and GMRES's FP64 tolerance is
  * unaffected) or STOKES_FP64.  Only the iteration counts can differ. */
 STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
+/* Relative tolerance of each inner FP32-Kahan GMRES solve of a STOKES_FP32_KAHAN step
+ * (1e-8..0.5, default 1e-3); the outer FP64-accurate refinement still ends at `tol`. */
+STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
 /* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
 STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
                                            double *u_resp);

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "stokes_sim_set_wall_solver": [_vp, _c_int],
     "stokes_sim_set_block_refinement": [_vp, _c_int],
     "stokes_sim_set_precond_precision": [_vp, _c_int],
+    "stokes_sim_set_inner_tolerance": [_vp, _c_double],
     "stokes_sim_empty_channel_pressure": [_vp, _c_double, _vp, _c_int, _vp, _vp],
     "stokes_sum_eval_pressure": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sum_eval_traction": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp],
@@ -487,6 +488,10 @@ def stokes_sim_set_block_refinement(h, sweeps):
 
 def stokes_sim_set_precond_precision(h, precision):
     return _sim_check(h, load().stokes_sim_set_precond_precision(h, int(precision)))
+
+
+def stokes_sim_set_inner_tolerance(h, tol):
+    return _sim_check(h, load().stokes_sim_set_inner_tolerance(h, float(tol)))
 
 
 def stokes_sim_wall_stats(h):

@@ -80,6 +80,7 @@ struct stokes_sim {
   // refinement of the block solve on the whole extended system: B and Q kept, right-hand
   // side copies, residuals and corrections
   int block_refine = 3;
+  double inner_tol = 1e-3;  // mixed-precision step: relative tolerance of each FP32-Kahan solve
   double *d_B = nullptr, *d_Q = nullptr;
   double *d_rv = nullptr, *d_rg = nullptr, *d_resv = nullptr, *d_resg = nullptr;
   double *d_dtau = nullptr, *d_dc = nullptr, *d_g2 = nullptr;
@@ -1645,6 +1646,13 @@ int stokes_sim_set_precond_precision(stokes_sim *m, int precision) {
   return STOKES_OK;
 }
 
+int stokes_sim_set_inner_tolerance(stokes_sim *m, double tol) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!(tol >= 1e-8 && tol <= 0.5)) return fail(m, STOKES_ERR_ARG, "inner tolerance must be in [1e-8, 0.5]");
+  m->inner_tol = tol;
+  return STOKES_OK;
+}
+
 int stokes_sim_set_block_refinement(stokes_sim *m, int sweeps) {
   if (!m) return STOKES_ERR_ARG;
   if (sweeps < 0 || sweeps > 8) return fail(m, STOKES_ERR_ARG, "block refinement sweeps must be in [0, 8]");
@@ -1816,8 +1824,9 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
         break;
       }
       prev = rel;
-      // inner solve to 1e-3: about what the FP32-Kahan operator resolves on stiff densities
-      const double tin = std::max(1e-3, 0.5 * tol / rel);
+      // inner solve to inner_tol (default 1e-3: about what the FP32-Kahan operator resolves on
+      // stiff densities)
+      const double tin = std::max(m->inner_tol, 0.5 * tol / rel);
       SK(cudaMemsetAsync(m->d_dd, 0, sizeof(double) * len, m->s));
       int it_in = 0;
       double rel_in = 0.0;
