@@ -1807,18 +1807,24 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     const double one = 1.0, mone = -1.0;
     double prev = 1e300;
     bool finish64 = false;
-    bool zero_iterate = guess_mode == STOKES_GUESS_ZERO;  // A 0 = 0: no matvec needed
+    // A zero initial iterate needs no matvec (A 0 = 0).  A warm start's first residual only
+    // feeds an inner solve to ~1e-3, so it is taken with the FP32-Kahan operator; every later
+    // residual, and every convergence decision, uses the FP64-accurate one.
+    bool zero_iterate = guess_mode == STOKES_GUESS_ZERO;
+    bool rough = !zero_iterate;
     for (;;) {
       SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
       if (!zero_iterate) {
-        ST(step_matvec(m, dt, hp, m->d_xsol, m->d_wk));
+        ST(step_matvec(m, dt, rough ? STOKES_FP32_KAHAN : hp, m->d_xsol, m->d_wk));
         BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
       }
       zero_iterate = false;
       const double rn = dnrm(m, len, m->d_rr, &st);
       if (st) return fail(m, st, "cublasDnrm2 failed");
       rel = bn > 0.0 ? rn / bn : 0.0;
-      if (rel <= tol) break;
+      const bool was_rough = rough;
+      rough = false;
+      if (!was_rough && rel <= tol) break;
       if (rel > 0.1 * prev || refinements >= 8 || iters >= max_iter) {
         finish64 = true;
         break;

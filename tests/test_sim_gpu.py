@@ -214,6 +214,25 @@ def test_mixed_precision_step_meets_fp64_tolerance(P):
     assert np.abs(sol32 - sol64).max() < 1e-4 * np.abs(sol64).max()
 
 
+@pytest.mark.parametrize("guess", ["user_exact", "user_rough"])
+def test_mixed_precision_step_with_warm_start(P, guess):
+    """A warm-started FP32-Kahan step (whose first residual is taken with the FP32 operator)
+    still ends on an FP64-accurate residual below tol, at the FP64 step's solution."""
+    walls, ves = _case(n_ves=4, n_v=32, n_w=96)
+    x0 = np.vstack([c.nodes for c in ves])
+    h = make_sim(P, walls, ves)
+    P.vesicle_step_warmstart(h, 1e-3, 0.5, tol=1e-11, max_iter=300)
+    _, _, sol64 = P.stokes_sim_get_state(h)
+    g = sol64 if guess == "user_exact" else sol64 * (1.0 + 1e-3 * np.cos(np.arange(sol64.size)))
+    P.stokes_sim_set_state(h, x0, np.zeros(len(x0)))
+    st = P.vesicle_step_warmstart(h, 1e-3, 0.5, P.STOKES_GUESS_USER, guess=dev(g), tol=1e-11,
+                                  max_iter=300, precision=P.STOKES_FP32_KAHAN)
+    _, _, sol32 = P.stokes_sim_get_state(h)
+    P.stokes_sim_destroy(h)
+    assert st["residual"] <= 1e-11 and st["refinements"] >= 1
+    assert np.abs(sol32 - sol64).max() < 1e-4 * np.abs(sol64).max()
+
+
 def test_double_float_step_matches_fp64_step(P):
     """Every sum of the step in double-float: the same iterations and, the operator agreeing
     with FP64 to ~1e-13, the same solution up to that times the conditioning (~1e5)."""
