@@ -75,7 +75,7 @@ struct stokes_sim {
   double *d_w = nullptr, *d_spd = nullptr, *d_sigma = nullptr, *d_D = nullptr, *d_kress = nullptr;
   double *d_L0 = nullptr, *d_A0 = nullptr, *d_Lk = nullptr;
   double2 *d_f = nullptr, *d_fb = nullptr, *d_ures = nullptr, *d_tmp2 = nullptr, *d_tmp3 = nullptr;
-  double *d_vrhs = nullptr, *d_g = nullptr, *d_y = nullptr, *d_r = nullptr, *d_c = nullptr;
+  double *d_vrhs = nullptr, *d_c = nullptr;
   double *d_tau = nullptr;
   // refinement of the block solve on the whole extended system: B and Q kept, right-hand
   // side copies, residuals and corrections
@@ -1269,8 +1269,6 @@ void free_walls(stokes_sim *m) {
   dfree(m->d_Spinv);
   dfree(m->d_piv);
   dfree(m->d_vrhs);
-  dfree(m->d_g);
-  dfree(m->d_y);
   dfree(m->d_c);
   dfree(m->d_tau);
   for (double **p : {&m->d_B, &m->d_Q, &m->d_rv, &m->d_rg, &m->d_resv, &m->d_resg, &m->d_dtau,
@@ -1509,8 +1507,6 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(cudaStreamSynchronize(m->s));
   for (double *p : {dQ, dS, dU, dVt, dsig, work, work2, dw, dn, dk}) cudaFree(p);
   SK(dalloc(m->d_vrhs, nA));
-  SK(dalloc(m->d_g, 4 * K));
-  SK(dalloc(m->d_y, nA));
   SK(dalloc(m->d_c, 2 * M));
   SK(dalloc(m->d_tau, nA));
   SK(dalloc(m->d_rv, nA));

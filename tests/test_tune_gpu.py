@@ -138,3 +138,27 @@ def test_autotune_argument_errors(P, small):
         P.stokes_autotune(e.h, P.STOKES_FP32_KAHAN)
     assert ei.value.code == P.STOKES_ERR_NO_GEOM
     e.close()
+
+
+def test_autotuned_shape_at_paper_scale_keeps_parity(P, oracle_mod):
+    """N = 128,768 in the launch configuration the benchmark times: the autotuner's shape for
+    this geometry (tuned here as in the benchmark), checked against the FP64 oracle on sampled
+    nodes of both kinds."""
+    g, s, d = I.workload("paper_n128k")
+    rng = np.random.default_rng(5)
+    off = g.curve_offset
+    sel = np.unique(np.concatenate([rng.integers(0, off[2], 120), rng.integers(off[2], g.n_nodes, 200),
+                                    [0, off[1] - 1, off[2], g.n_nodes - 1]])).astype(np.int32)
+    ref = oracle_mod.sum_nodes(g, s, d, select=sel)
+    P.stokes_tune_clear()
+    a = P.StokesSum(g)
+    r = P.stokes_autotune(a.h, P.STOKES_FP32_KAHAN, repeats=3)
+    assert P.stokes_get_launch(a.h, P.STOKES_FP32_KAHAN) == (
+        r["source_splits"], r["targets_per_thread"], r["kahan_group"])
+    out = a.eval(dev(s), dev(d), precision="fp32k").cpu().numpy()[sel]
+    a.close()
+    P.stokes_tune_clear()
+    wall = g.kind_mask(I.KIND_DLP)[sel]
+    for m in (wall, ~wall):
+        e = np.abs(out[m] - ref[m]).max(0) / np.abs(ref[m]).max(0)
+        assert np.all(e <= TOL["fp32k"]), e
