@@ -479,6 +479,59 @@ def run_poiseuille(args):
     return 0
 
 
+def run_scaling(args):
+    """The FP32-Kahan node sum (autotuned shape) at N = 1,280 / 16,384 / 128,768 / 524,288:
+    throughput, pair-kernel fraction of the FP32 FMA peak and the error against the FP64
+    oracle on sampled nodes.  (The largest channel takes a couple of minutes to generate.)"""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    from oracle import oracle as O
+    B.build()
+    O.build()
+    peaks, _ = measured_peaks()
+    peak = SMS * LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    rows = {}
+    for name in ("small_n1280", "mid_n16k", "paper_n128k", "large_n512k"):
+        t0 = time.perf_counter()
+        g, slp, dlp = I.workload(name)
+        gen_s = time.perf_counter() - t0
+        s = P.StokesSum(g)
+        tuned = P.stokes_autotune(s.h, P.STOKES_FP32_KAHAN, repeats=3)
+        ts, td = torch.as_tensor(slp, device="cuda"), torch.as_tensor(dlp, device="cuda")
+        out = torch.empty((g.n_nodes, 2), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            P.stokes_sum_eval(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out)
+        P.stokes_sync(s.h)
+        P.stokes_set_profiling(s.h, True)
+        ms, pair_ms = [], []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.stokes_sum_eval(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            pair_ms.append(P.stokes_last_timing(s.h)[1])
+        P.stokes_set_profiling(s.h, False)
+        pairs = P.stokes_pair_count(s.h)
+        rng = np.random.default_rng(0)
+        k = min(g.n_nodes, 400)
+        sel = np.sort(rng.choice(g.n_nodes, k, replace=False)).astype(np.int32)
+        ref = O.sum_nodes(g, slp, dlp, select=sel)
+        err = rel_err_by_kind(out.cpu().numpy(), ref, g, sel)
+        s.close()
+        m, pm = statistics.median(ms), statistics.median(pair_ms)
+        rows[name] = {"N": g.n_nodes, "pairs": pairs, "ms": m, "gpair_per_s": pairs / m / 1e6,
+                      "pair_ms": pm, "frac_fp32_fma_peak": FLOPS_PER_PAIR * pairs / (pm / 1e3) / 1e12 / peak,
+                      "shape": {k2: tuned[k2] for k2 in ("source_splits", "targets_per_thread", "kahan_group")},
+                      "rel_err_vs_oracle": err, "oracle_sample": int(k), "generation_s": gen_s}
+    print(json.dumps({"metric": "FP32-Kahan node sum vs problem size", "unit": "Gpair-evals/s",
+                      "n_gpus": 1, "dtype": "f32", "data": "synthetic", "results": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +547,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS))
     ap.add_argument("--batch", action="store_true",
                     help="time the 64-channel batched ensemble instead (separate JSON line)")
+    ap.add_argument("--scaling", action="store_true",
+                    help="FP32-Kahan sum from N = 1,280 to N = 524,288 (throughput, roofline, error)")
     ap.add_argument("--poiseuille", action="store_true",
                     help="accuracy study of the pressure-driven channel (velocity and pressure)")
     ap.add_argument("--step", action="store_true",
@@ -519,6 +574,8 @@ def main():
         return run_step(args)
     if args.poiseuille:
         return run_poiseuille(args)
+    if args.scaling:
+        return run_scaling(args)
 
     import torch
     ws, rank, local = dist_env()

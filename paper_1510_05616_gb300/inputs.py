@@ -356,8 +356,11 @@ WORKLOADS = {
     "small_n1280": (512, WALL_SHAPE_SMALL, 4, 64, math.pi * 0.25**2),
     "mid_n16k": (4096, WALL_SHAPE_SMALL, 128, 64, 0.15 * CELL_AREA / 128),
     "paper_n128k": (16384, WALL_SHAPE_LARGE, 750, 128, 0.15 * CELL_AREA / 750),
+    # a 4x larger channel of the same shape and fill (scaling of the sum beyond the paper's size)
+    "large_n512k": (65536, WALL_SHAPE_LARGE, 3072, 128, 0.15 * CELL_AREA / 3072),
 }
-WORKLOAD_SEED = {"small_n1280": SEED_BASE + 0, "mid_n16k": SEED_BASE + 1, "paper_n128k": SEED_BASE + 2}
+WORKLOAD_SEED = {"small_n1280": SEED_BASE + 0, "mid_n16k": SEED_BASE + 1, "paper_n128k": SEED_BASE + 2,
+                 "large_n512k": SEED_BASE + 5}
 
 
 def channel(n_w, modes, n_ves, n_v, area, seed, period=TWO_PI, mu=1.0, gap_factor=5.0) -> Geometry:
