@@ -194,6 +194,12 @@ STOKES_API int stokes_sum_eval_host(stokes_ctx *ctx, int precision, const double
  * STOKES_ERR_NONFINITE or STOKES_ERR_TIMEOUT. */
 STOKES_API int stokes_sync(stokes_ctx *ctx, void *stream);
 
+/* Failure-handling check: launches one block on `stream` that waits, with the pair kernels'
+ * bounded wait, on a barrier nothing arrives at.  After the bound (~0.5 s) it records a
+ * timeout in the context's status word and exits; the next stokes_sync returns
+ * STOKES_ERR_TIMEOUT (and clears it), and the context stays usable.  For tests. */
+STOKES_API int stokes_check_wait_timeout(stokes_ctx *ctx, void *stream);
+
 /*
  * Phase timing with CUDA events recorded on the call's stream.  With profiling on (on != 0)
  * every stokes_sum_eval / stokes_sum_eval_targets records events around its three phases:

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "stokes_sum_eval_host": [_vp, _c_int, _vp, _vp, _c_double, _vp],
     "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sync": [_vp, _vp],
+    "stokes_check_wait_timeout": [_vp, _vp],
     "stokes_num_nodes": [_vp],
     "stokes_set_launch": [_vp, _c_int, _c_int, _c_int, _c_int],
     "stokes_get_launch": [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
@@ -267,6 +268,10 @@ def stokes_last_error(h) -> str:
 
 def stokes_sync(h, stream=None):
     return _check(h, load().stokes_sync(h, _stream(stream)))
+
+
+def stokes_check_wait_timeout(h, stream=None):
+    return _check(h, load().stokes_check_wait_timeout(h, _stream(stream)))
 
 
 def stokes_num_nodes(h) -> int:

@@ -10,6 +10,7 @@
 //    (Sec. 2.3, Eq. (JR)), plus the FP64 Kress self term of the single layer on each
 //    vesicle (Sec. 3.2).
 #include "stokes_internal.cuh"
+#include "bulk_pipe.cuh"
 
 namespace stokes {
 
@@ -398,6 +399,27 @@ namespace stokes {
 cudaError_t launch_finish_free_scratch(int splits, int n_targets, const double2 *partial,
                                        double2 *out, cudaStream_t s) {
   finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(n_targets, splits, partial, out);
+  return cudaGetLastError();
+}
+
+}  // namespace stokes
+
+namespace stokes {
+
+// Failure-handling check of the pipeline wait: one block waits on an mbarrier that nothing
+// arrives at, gives up after the wait's bound (~0.5 s) and records the timeout in the status
+// word, exactly as a pair kernel whose tile copy never lands would.
+__global__ void wait_timeout_check_kernel(unsigned *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0u)) atomicOr(status, kStatusTimeout);
+  }
+}
+
+cudaError_t launch_wait_timeout_check(stokes_ctx *c, cudaStream_t s) {
+  wait_timeout_check_kernel<<<1, 32, 0, s>>>(c->d_status);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ int effective_splits(stokes_ctx *c, int precision, int splits);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
 void tune_apply_cached(stokes_ctx *c);  // tune.cu: shapes recorded for the geometry's size class
 int field_splits(const stokes_ctx *c, int n_targets);  // k_field.cu
+cudaError_t launch_wait_timeout_check(stokes_ctx *c, cudaStream_t s);  // k_prep.cu
 cudaError_t launch_field(stokes_ctx *c, int n_targets, const double2 *tgt, const double2 *tnrm,
                          int splits, double *out, cudaStream_t s);
 }  // namespace stokes
@@ -719,6 +720,13 @@ int field_eval(stokes_ctx *c, const double *slp, const double *dlp, int n_target
 }  // namespace
 
 extern "C" {
+
+int stokes_check_wait_timeout(stokes_ctx *c, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(launch_wait_timeout_check(c, as_stream(stream)));
+  return STOKES_OK;
+}
 
 int stokes_sum_eval_pressure(stokes_ctx *c, const double *slp, const double *dlp, int n_targets,
                              const double *targets, double *out_pressure, void *stream) {
