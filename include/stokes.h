@@ -506,6 +506,10 @@ STOKES_API int stokes_mlp_last_error(const stokes_mlp *mlp, char *buf, size_t le
 STOKES_API int stokes_mlp_num_params(const stokes_mlp *mlp);
 STOKES_API int stokes_mlp_set_params(stokes_mlp *mlp, const float *theta);
 STOKES_API int stokes_mlp_get_params(stokes_mlp *mlp, float *theta);
+/* Adam state of the network (HOST float[n_params] first and second moments, step count), for
+ * checkpoints; stokes_mlp_set_params resets it to zero. */
+STOKES_API int stokes_mlp_get_adam(stokes_mlp *mlp, float *m, float *v, int *t);
+STOKES_API int stokes_mlp_set_adam(stokes_mlp *mlp, const float *m, const float *v, int t);
 STOKES_API int stokes_mlp_set_normalization(stokes_mlp *mlp, const float *norm);
 STOKES_API int stokes_mlp_get_normalization(stokes_mlp *mlp, float *norm);
 /* Column means / standard deviations of X (rows x n_in) and T (rows x n_out) as normalisation. */
@@ -524,6 +528,17 @@ STOKES_API int stokes_mlp_train_step(stokes_mlp *mlp, int rows, const float *X, 
 STOKES_API int stokes_sim_get_state(stokes_sim *sim, double *x, double *sigma, double *solution);
 STOKES_API int stokes_sim_set_state(stokes_sim *sim, const double *x, const double *sigma);
 /* Krylov subspace length of the step's restarted GMRES (default 80; storage 3 n V (m + 1)). */
+/* Checkpoint / resume of a time-stepping run (HOST buffers, any may be NULL): the initial
+ * perimeters L0[V] and areas A0[V] that the arc-length and area corrections hold, and the
+ * previous step's solution zprev[3 n V] and right-hand side bprev[3 n V] that the warm starts
+ * use.  With stokes_sim_get_state / stokes_sim_set_state (positions, tension) they make a run
+ * resumable: a new stokes_sim with the same walls and vesicle count, set_state, then
+ * set_history (in that order: set_state clears the history) continues bit-identically in FP64.
+ * set_history also makes zprev the current iterate of STOKES_GUESS_PREVIOUS. */
+STOKES_API int stokes_sim_get_history(stokes_sim *sim, double *L0, double *A0, double *zprev,
+                                      double *bprev);
+STOKES_API int stokes_sim_set_history(stokes_sim *sim, const double *L0, const double *A0,
+                                      const double *zprev, const double *bprev);
 STOKES_API int stokes_sim_set_restart(stokes_sim *sim, int restart);
 STOKES_API int stokes_sim_sizes(const stokes_sim *sim, int *n_vesicles, int *nodes_per_vesicle,
                                 int *wall_nodes);

@@ -109,6 +109,10 @@ _SIGNATURES = {
     "stokes_sim_set_state": [_vp, _vp, _vp],
     "stokes_sim_sizes": [_vp] + [ctypes.POINTER(_c_int)] * 3,
     "stokes_sim_set_restart": [_vp, _c_int],
+    "stokes_sim_get_history": [_vp, _vp, _vp, _vp, _vp],
+    "stokes_sim_set_history": [_vp, _vp, _vp, _vp, _vp],
+    "stokes_mlp_get_adam": [_vp, _vp, _vp, ctypes.POINTER(_c_int)],
+    "stokes_mlp_set_adam": [_vp, _vp, _vp, _c_int],
     "stokes_last_timing": [_vp, ctypes.POINTER(_c_double)],
     "stokes_set_local_frame": [_vp, _c_int],
     "stokes_autotune": [_vp, _c_int, _c_int, _vp, _vp],
@@ -630,6 +634,40 @@ def stokes_mlp_train_step(h, X, T, idx, lr):
                                                _fptr(idx, "idx"), int(idx.shape[0]), float(lr),
                                                _vp(loss.ctypes.data)))
     return float(loss[0])
+
+
+def stokes_sim_get_history(h):
+    """(L0 (V,), A0 (V,), zprev (3 n V,), bprev (3 n V,)) as NumPy arrays."""
+    import numpy as np
+    V, n, _ = stokes_sim_sizes(h)
+    L0, A0 = np.zeros(V), np.zeros(V)
+    zp, bp = np.zeros(3 * n * V), np.zeros(3 * n * V)
+    _sim_check(h, load().stokes_sim_get_history(h, _vp(L0.ctypes.data), _vp(A0.ctypes.data),
+                                                _vp(zp.ctypes.data), _vp(bp.ctypes.data)))
+    return L0, A0, zp, bp
+
+
+def stokes_sim_set_history(h, L0, A0, zprev, bprev):
+    keep = [_host(a, "history") for a in (L0, A0, zprev, bprev)]
+    return _sim_check(h, load().stokes_sim_set_history(h, *[p for _, p in keep]))
+
+
+def stokes_mlp_get_adam(h):
+    """(first moments, second moments, step count) of the network's Adam state."""
+    import numpy as np
+    n = stokes_mlp_num_params(h)
+    mm, vv, t = np.zeros(n, dtype=np.float32), np.zeros(n, dtype=np.float32), _c_int()
+    _mlp_check(h, load().stokes_mlp_get_adam(h, _vp(mm.ctypes.data), _vp(vv.ctypes.data),
+                                             ctypes.byref(t)))
+    return mm, vv, t.value
+
+
+def stokes_mlp_set_adam(h, m, v, t):
+    import numpy as np
+    mm = np.ascontiguousarray(m, dtype=np.float32)
+    vv = np.ascontiguousarray(v, dtype=np.float32)
+    return _mlp_check(h, load().stokes_mlp_set_adam(h, _vp(mm.ctypes.data), _vp(vv.ctypes.data),
+                                                    int(t)))
 
 
 def stokes_sim_set_restart(h, restart):

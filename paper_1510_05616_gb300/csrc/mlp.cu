@@ -381,6 +381,26 @@ int stokes_mlp_set_params(stokes_mlp *m, const float *theta_host) {
   return STOKES_OK;
 }
 
+int stokes_mlp_get_adam(stokes_mlp *m, float *m_host, float *v_host, int *t) {
+  if (!m || !m_host || !v_host || !t) return STOKES_ERR_ARG;
+  MK(cudaSetDevice(m->device));
+  MK(cudaStreamSynchronize(m->s));
+  MK(cudaMemcpy(m_host, m->d_m, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost));
+  MK(cudaMemcpy(v_host, m->d_v, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost));
+  *t = m->t_adam;
+  return STOKES_OK;
+}
+
+int stokes_mlp_set_adam(stokes_mlp *m, const float *m_host, const float *v_host, int t) {
+  if (!m || !m_host || !v_host || t < 0) return STOKES_ERR_ARG;
+  MK(cudaSetDevice(m->device));
+  MK(cudaStreamSynchronize(m->s));
+  MK(cudaMemcpy(m->d_m, m_host, sizeof(float) * m->n_params, cudaMemcpyHostToDevice));
+  MK(cudaMemcpy(m->d_v, v_host, sizeof(float) * m->n_params, cudaMemcpyHostToDevice));
+  m->t_adam = t;
+  return STOKES_OK;
+}
+
 int stokes_mlp_get_params(stokes_mlp *m, float *theta_host) {
   if (!m || !theta_host) return STOKES_ERR_ARG;
   MK(cudaSetDevice(m->device));

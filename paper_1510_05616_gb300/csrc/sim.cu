@@ -1908,6 +1908,37 @@ int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigm
   return STOKES_OK;
 }
 
+int stokes_sim_get_history(stokes_sim *m, double *L0_host, double *A0_host, double *zprev_host,
+                           double *bprev_host) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  SK(cudaSetDevice(m->device));
+  SK(cudaStreamSynchronize(m->s));
+  const size_t len = size_t(3) * m->Nv;
+  if (L0_host) SK(cudaMemcpy(L0_host, m->d_L0, sizeof(double) * m->V, cudaMemcpyDeviceToHost));
+  if (A0_host) SK(cudaMemcpy(A0_host, m->d_A0, sizeof(double) * m->V, cudaMemcpyDeviceToHost));
+  if (zprev_host) SK(cudaMemcpy(zprev_host, m->d_zprev, sizeof(double) * len, cudaMemcpyDeviceToHost));
+  if (bprev_host) SK(cudaMemcpy(bprev_host, m->d_bprev, sizeof(double) * len, cudaMemcpyDeviceToHost));
+  return STOKES_OK;
+}
+
+int stokes_sim_set_history(stokes_sim *m, const double *L0_host, const double *A0_host,
+                           const double *zprev_host, const double *bprev_host) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
+  SK(cudaSetDevice(m->device));
+  SK(cudaStreamSynchronize(m->s));
+  const size_t len = size_t(3) * m->Nv;
+  if (L0_host) SK(cudaMemcpy(m->d_L0, L0_host, sizeof(double) * m->V, cudaMemcpyHostToDevice));
+  if (A0_host) SK(cudaMemcpy(m->d_A0, A0_host, sizeof(double) * m->V, cudaMemcpyHostToDevice));
+  if (zprev_host) {
+    SK(cudaMemcpy(m->d_zprev, zprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+    SK(cudaMemcpy(m->d_xsol, zprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+  }
+  if (bprev_host) SK(cudaMemcpy(m->d_bprev, bprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+  return STOKES_OK;
+}
+
 int stokes_sim_set_restart(stokes_sim *m, int restart) {
   if (!m) return STOKES_ERR_ARG;
   if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");

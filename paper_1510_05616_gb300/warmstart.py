@@ -12,9 +12,12 @@ import numpy as np
 
 from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
                STOKES_GUESS_ZERO, stokes_mlp_create, stokes_mlp_destroy, stokes_sim_set_restart,
-               stokes_mlp_fit_normalization, stokes_mlp_num_params, stokes_mlp_set_params,
+               stokes_mlp_fit_normalization, stokes_mlp_get_adam, stokes_mlp_get_normalization,
+               stokes_mlp_get_params, stokes_mlp_num_params, stokes_mlp_set_adam,
+               stokes_mlp_set_normalization, stokes_mlp_set_params,
                stokes_mlp_train_step, stokes_sim_create, stokes_sim_destroy,
-               stokes_sim_get_state, stokes_sim_last_features, stokes_sim_set_state,
+               stokes_sim_get_history, stokes_sim_get_state, stokes_sim_last_features,
+               stokes_sim_set_history, stokes_sim_set_state,
                stokes_sim_set_vesicles, stokes_sim_set_walls, stokes_sim_sizes,
                vesicle_step_warmstart)
 
@@ -52,6 +55,24 @@ class Simulation:
 
     def set_state(self, x, sigma):
         stokes_sim_set_state(self.h, x, sigma)
+
+    def save(self, path, step=0):
+        """Checkpoint of the run (positions, tension, initial perimeters and areas, previous
+        solution and right-hand side, step index) to an .npz file."""
+        x, sigma, _ = stokes_sim_get_state(self.h)
+        L0, A0, zprev, bprev = stokes_sim_get_history(self.h)
+        np.savez(path, x=x, sigma=sigma, L0=L0, A0=A0, zprev=zprev, bprev=bprev,
+                 step=np.int64(step), V=np.int64(self.V), n=np.int64(self.n))
+
+    def restore(self, path):
+        """Continue a checkpointed run (same walls and vesicle count); returns its step index."""
+        with np.load(path) as z:
+            if int(z["V"]) != self.V or int(z["n"]) != self.n:
+                raise ValueError("checkpoint of %d x %d vesicles, simulation has %d x %d"
+                                 % (int(z["V"]), int(z["n"]), self.V, self.n))
+            stokes_sim_set_state(self.h, z["x"], z["sigma"])  # clears the history ...
+            stokes_sim_set_history(self.h, z["L0"], z["A0"], z["zprev"], z["bprev"])  # ... restored here
+            return int(z["step"])
 
     def features(self, feat, targ):
         stokes_sim_last_features(self.h, feat, targ)
@@ -98,14 +119,36 @@ class WarmStartNet:
         stokes_mlp_set_params(self.h, np.concatenate(theta).astype(np.float32))
         assert stokes_mlp_num_params(self.h) == sum(t.size for t in theta)
 
-    def fit(self, X, T, epochs=30, batch=256, lr=2e-3, seed=1, lr_decay=0.97):
-        """Adam on shuffled minibatches; returns the per-epoch mean losses."""
+    def save(self, path):
+        """Parameters, input/output normalisation and Adam state to an .npz file."""
+        theta = stokes_mlp_get_params(self.h)
+        norm = stokes_mlp_get_normalization(self.h)
+        m, v, t = stokes_mlp_get_adam(self.h)
+        np.savez(path, theta=theta, norm=norm, adam_m=m, adam_v=v, adam_t=np.int64(t),
+                 hidden=np.int64(self.hidden))
+
+    def load(self, path):
+        with np.load(path) as z:
+            if int(z["hidden"]) != self.hidden:
+                raise ValueError("checkpoint of a %d-wide network" % int(z["hidden"]))
+            stokes_mlp_set_params(self.h, z["theta"])  # resets Adam ...
+            stokes_mlp_set_normalization(self.h, z["norm"])
+            stokes_mlp_set_adam(self.h, z["adam_m"], z["adam_v"], int(z["adam_t"]))  # ... restored
+
+    def fit(self, X, T, epochs=30, batch=256, lr=2e-3, seed=1, lr_decay=0.97, start_epoch=0):
+        """Adam on shuffled minibatches; returns the per-epoch mean losses.  start_epoch > 0
+        resumes a checkpointed fit (same data and seed): the normalisation is kept and the
+        shuffles and learning rate continue where epoch start_epoch begins."""
         import torch
-        stokes_mlp_fit_normalization(self.h, X, T)
         rng = np.random.default_rng(seed)
         rows = X.shape[0]
+        if start_epoch == 0:
+            stokes_mlp_fit_normalization(self.h, X, T)
+        for _ in range(start_epoch):
+            rng.permutation(rows)
+        lr *= lr_decay ** start_epoch
         losses = []
-        for ep in range(epochs):
+        for ep in range(start_epoch, epochs):
             perm = torch.as_tensor(rng.permutation(rows).astype(np.int32), device="cuda")
             tot, cnt = 0.0, 0
             for b0 in range(0, rows - batch + 1, batch):
