@@ -382,8 +382,19 @@ STOKES_API int stokes_tune_clear(void);
  *     Storage 12 (4 N_w)^2 bytes (16 during set-up); the FP32 factorization is far faster
  *     than the FP64 one on this hardware, and a sweep streams the two matrices once.
  *   STOKES_WALLS_LU64: FP64 LU (8 (4 N_w)^2 bytes), one triangular solve per solve.
+ *   STOKES_WALLS_FDS: the fast direct solver of Sec. 4.  A = A_0 + A_{-1} + A_{+1}
+ *     (Eq. (formA)); A_0 (the cell's own walls) in HBS form by recursive skeletonisation
+ *     (interpolative decompositions against proxy circles, per-box inverses by
+ *     Eqs. (def_muhD)-(def_muG)); A_{-1}, A_{+1} = L R from dyadic sections toward each
+ *     neighbour (Sec. 4.2: proxy circles, the neighbour's near nodes for the touching
+ *     section); A^-1 by Sherman-Morrison-Woodbury (Eq. (woodbury1)).  O(N_w) storage and
+ *     set-up; a solve is two tree passes and three skinny products.  Accurate to about
+ *     1e-10 relative (the decompositions' tolerance, stokes_sim_set_fds_params); the block
+ *     refinement below takes the channel response to round-off.  The compression runs on
+ *     host threads (FP64), everything else on the device.
  * stokes_sim_wall_stats: refinement sweeps and relative residual ||b - A x|| / ||b|| of the
- *   last wall solve (0 and 0 for STOKES_WALLS_LU64).
+ *   last wall solve (0 and 0 for STOKES_WALLS_LU64; 0 and -1, not computed, for
+ *   STOKES_WALLS_FDS).
  * Block refinement (stokes_sim_set_block_refinement, 0..8, default 3): the block solve is
  *   followed by that many residual corrections on the whole extended system,
  *   r = [v; g] - [A B; C Q][tau; c], [tau; c] += block solve of r, with A tau evaluated as the
@@ -392,7 +403,8 @@ STOKES_API int stokes_tune_clear(void);
  *   block solves are single FP32-inverse sweeps (~1e-5 each; the corrections make up for
  *   them), and three corrections bring the result to round-off.  With 0 corrections every
  *   wall solve is refined to FP64 accuracy on its own.  (The solve of W = A^-1 B at
- *   stokes_sim_set_walls is always refined to FP64 accuracy.)
+ *   stokes_sim_set_walls is refined to FP64 accuracy by the LU solvers; the fast direct
+ *   solver gives it to its own ~1e-10.)
  *
  * Time step (Algorithm 1 steps 2-9): forces f_b = -kappa_B x_ssss, f = f_b + (sigma x_s)_s;
  * u_resp of f; GMRES (FP64, right preconditioned by each vesicle's self interaction) on
@@ -418,8 +430,23 @@ typedef struct stokes_sim stokes_sim;
 
 typedef enum {
     STOKES_WALLS_LU64 = 0,         /* FP64 LU of the wall operator                          */
-    STOKES_WALLS_LU32_REFINE = 1   /* FP32 LU + FP64 iterative refinement (default)         */
+    STOKES_WALLS_LU32_REFINE = 1,  /* FP32 LU + FP64 iterative refinement (default)         */
+    STOKES_WALLS_FDS = 2           /* HBS + low-rank neighbours + SMW (Sec. 4)              */
 } stokes_wall_solver;
+
+/* The fast direct solver after stokes_sim_set_walls (zeros, but walls_setup_ms, for the LU
+ * solvers). */
+typedef struct {
+    int levels;             /* HBS levels below the root (root: both walls; level 1: each wall) */
+    int max_rank;           /* largest skeleton of any HBS box                                 */
+    int root_size;          /* order of the dense root block                                   */
+    int neighbour_rank;     /* columns of L, both neighbours and both walls                    */
+    int sections;           /* neighbour sections, both neighbours and both walls              */
+    double host_ms;         /* compression and per-box inverses on host threads                */
+    double device_ms;       /* uploads, R, Z = A_0^-1 L and (I + R Z)^-1 on the device          */
+    double device_bytes;    /* device memory the solver holds                                  */
+    double walls_setup_ms;  /* the whole stokes_sim_set_walls call, any solver                 */
+} stokes_fds_info;
 typedef struct stokes_mlp stokes_mlp;
 
 /* Initial iterate of the step's GMRES. */
@@ -456,6 +483,18 @@ STOKES_API int stokes_sim_set_vesicles(stokes_sim *sim, int V, int n, const doub
  * last wall solve (see above). */
 STOKES_API int stokes_sim_set_wall_solver(stokes_sim *sim, int mode);
 STOKES_API int stokes_sim_wall_stats(const stokes_sim *sim, int *refinements, double *residual);
+/* X <- A^-1 X with the wall solver of the last set_walls (A = -I/2 + D^near, the wall
+ * operator; X a DEVICE array of 4 n_per_wall x nrhs doubles, column-major, unknowns
+ * (tau_1, tau_2) interleaved per node, lower wall then upper).  The LU32 solver refines to
+ * FP64 accuracy; the fast direct solver gives its own ~1e-10.  Synchronous.
+ * STOKES_ERR_NO_GEOM without walls, STOKES_ERR_ARG for a NULL X or nrhs < 1. */
+STOKES_API int stokes_sim_wall_solve(stokes_sim *sim, double *X, int nrhs);
+/* Fast direct solver parameters (read at the next set_walls): relative tolerance of every
+ * interpolative decomposition (1e-15..1e-3, default 1e-12), nodes per HBS leaf box (8..512,
+ * default 64), proxy points per HBS box (16..512, default 64).  STOKES_ERR_ARG outside. */
+STOKES_API int stokes_sim_set_fds_params(stokes_sim *sim, double tol, int leaf_nodes, int n_proxy);
+/* Statistics of the last stokes_sim_set_walls (see stokes_fds_info). */
+STOKES_API int stokes_sim_fds_info(const stokes_sim *sim, stokes_fds_info *info);
 STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
 /* Precision of the factorization of the block-diagonal self preconditioner: STOKES_FP32_KAHAN
  * (default: FP32 batched LU and inverse of the FP64-assembled blocks, applied with FP64

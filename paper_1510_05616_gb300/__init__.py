@@ -36,6 +36,7 @@ STOKES_GUESS_MLP = 2
 STOKES_GUESS_USER = 3
 STOKES_WALLS_LU64 = 0
 STOKES_WALLS_LU32_REFINE = 1
+STOKES_WALLS_FDS = 2
 N_FEATURES = 64
 N_TARGETS = 48
 
@@ -89,6 +90,9 @@ _SIGNATURES = {
     "stokes_sum_eval_pressure": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sum_eval_traction": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp],
     "stokes_sim_wall_stats": [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_double)],
+    "stokes_sim_set_fds_params": [_vp, _c_double, _c_int, _c_int],
+    "stokes_sim_wall_solve": [_vp, _vp, _c_int],
+    "stokes_sim_fds_info": [_vp, _vp],
     "stokes_sim_empty_channel": [_vp, _c_double, _vp, _c_int, _vp, _vp],
     "vesicle_step_warmstart": [_vp, _c_double, _c_double, _c_int, _vp, _vp, _c_double, _c_int,
                                _c_int, _vp],
@@ -487,8 +491,40 @@ def stokes_sum_eval_traction(h, slp_density, dlp_density, targets, target_normal
 
 
 def stokes_sim_set_wall_solver(h, mode):
-    """STOKES_WALLS_LU32_REFINE (default) or STOKES_WALLS_LU64; read at the next set_walls."""
+    """STOKES_WALLS_LU32_REFINE (default), STOKES_WALLS_LU64 or STOKES_WALLS_FDS (the fast
+    direct solver); read at the next set_walls."""
     return _sim_check(h, load().stokes_sim_set_wall_solver(h, int(mode)))
+
+
+class FdsInfo(ctypes.Structure):
+    _fields_ = [("levels", _c_int), ("max_rank", _c_int), ("root_size", _c_int),
+                ("neighbour_rank", _c_int), ("sections", _c_int), ("host_ms", _c_double),
+                ("device_ms", _c_double), ("device_bytes", _c_double),
+                ("walls_setup_ms", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def stokes_sim_wall_solve(h, X):
+    """X (device, (4 n_w,) or (nrhs, 4 n_w) rows = right-hand sides) <- A^-1 X in place."""
+    if X.dim() == 1:
+        nrhs = 1
+    else:
+        nrhs = int(X.shape[0])
+    return _sim_check(h, load().stokes_sim_wall_solve(h, _dptr(X, "X", None), nrhs))
+
+
+def stokes_sim_set_fds_params(h, tol=1e-12, leaf_nodes=64, n_proxy=64):
+    """Interpolative-decomposition tolerance, HBS leaf size and proxy count (next set_walls)."""
+    return _sim_check(h, load().stokes_sim_set_fds_params(h, float(tol), int(leaf_nodes), int(n_proxy)))
+
+
+def stokes_sim_fds_info(h):
+    """Statistics of the last set_walls (fast direct solver ranks and timings) as a dict."""
+    info = FdsInfo()
+    _sim_check(h, load().stokes_sim_fds_info(h, ctypes.byref(info)))
+    return info.as_dict()
 
 
 def stokes_sim_set_block_refinement(h, sweeps):

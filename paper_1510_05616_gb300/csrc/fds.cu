@@ -1,0 +1,993 @@
+// fds.cu -- fast direct solver for the fixed channel walls (Sec. 4).
+//
+// The wall operator A = -I/2 + D^near (Nystrom with the curvature diagonal; unknowns
+// (tau_1, tau_2) interleaved per node, lower wall then upper) is split as in Eq. (formA) into
+// the unit cell's self interaction A_0 and the neighbour interactions A_{-1}, A_{+1}:
+//
+//  * A_0 in HBS form (Sec. 4.3) by recursive skeletonisation: a binary tree of node ranges
+//    (root; the two walls; halves down to leaves of <= `leaf` nodes).  At every box, an
+//    interpolative decomposition of the box's unknowns against everything outside it gives
+//    its skeleton J and interpolation matrix P (one skeleton for rows and columns, U = V = P):
+//    the probe rows are the box's interactions, in both directions, with the active unknowns
+//    of the other boxes of its level inside a proxy circle (1.5 x the box radius), the fields
+//    of stokeslets and stresslets at the proxy points (any flow the far sources make inside the
+//    circle) and the box's own field at the proxy points (what the far targets see).  The box
+//    is then inverted by Eqs. (def_muhD)-(def_muG): D^ = (P^T D^-1 P)^-1, E = D^-1 P D^,
+//    F^* = D^ P^T D^-1, G = D^-1 - D^-1 P D^ P^T D^-1, where D is the leaf's diagonal block of
+//    A_0 or, for a parent, [D^_a, A_0(J_a, J_b); A_0(J_b, J_a), D^_b].  The root block is
+//    inverted densely; A_0^-1 v is then one upward pass (v^ = F^* v), the root solve and one
+//    downward pass (u = E u^ + G v).
+//  * A_{+1} and A_{-1} factored as L R (Sec. 4.2): each wall is cut dyadically toward the
+//    neighbour, down to a touching section of <= sec_max nodes.  A section away from the
+//    neighbour is skeletonised against stokeslets and stresslets at n_proxy_nb points on a
+//    circle 0.9 x its centre's distance to the shared cell boundary; the touching section
+//    against points on a circle 1.75 x its radius together with the neighbour nodes inside
+//    that circle.  L is block diagonal (the sections' P's) and R = A_m(J, :).
+//  * A^-1 by Sherman-Morrison-Woodbury, Eq. (woodbury1): Z = A_0^-1 L and
+//    K^-1 = (I + R Z)^-1 are formed once; a solve is y = A_0^-1 v, x = y - Z K^-1 R y.
+//
+// The compression and the small per-box inverses run on the host in FP64 (threads over the
+// boxes of one level); R, Z, K^-1 and every solve run on the device.
+#include <math.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "fds.cuh"
+#include "stokes.h"
+
+namespace stokes {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kHbsThreads = 256;
+constexpr int kHbsCols = 8;       // right-hand sides per CTA of a level pass
+constexpr int kChunk = 256;       // right-hand sides per pass through the tree
+
+// ---------------------------------------------------------------------------
+// host dense matrices (column-major, FP64)
+// ---------------------------------------------------------------------------
+struct HMat {
+  int r = 0, c = 0;
+  std::vector<double> a;
+  HMat() = default;
+  HMat(int r_, int c_) : r(r_), c(c_), a(size_t(r_) * c_, 0.0) {}
+  double &operator()(int i, int j) { return a[i + size_t(j) * r]; }
+  double operator()(int i, int j) const { return a[i + size_t(j) * r]; }
+  double *col(int j) { return a.data() + size_t(j) * r; }
+  const double *col(int j) const { return a.data() + size_t(j) * r; }
+};
+
+HMat mul(const HMat &A, const HMat &B) {  // A B
+  HMat C(A.r, B.c);
+  for (int j = 0; j < B.c; ++j) {
+    double *cj = C.col(j);
+    for (int k = 0; k < A.c; ++k) {
+      const double b = B(k, j);
+      if (b == 0.0) continue;
+      const double *ak = A.col(k);
+      for (int i = 0; i < A.r; ++i) cj[i] += ak[i] * b;
+    }
+  }
+  return C;
+}
+
+HMat mul_nt(const HMat &A, const HMat &B) {  // A B^T
+  HMat C(A.r, B.r);
+  for (int k = 0; k < A.c; ++k) {
+    const double *ak = A.col(k);
+    for (int j = 0; j < B.r; ++j) {
+      const double b = B(j, k);
+      if (b == 0.0) continue;
+      double *cj = C.col(j);
+      for (int i = 0; i < A.r; ++i) cj[i] += ak[i] * b;
+    }
+  }
+  return C;
+}
+
+// In-place inverse by LU with partial pivoting (P A = L U, then L U X = P).
+bool invert(HMat &A) {
+  const int n = A.r;
+  std::vector<int> piv(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = fabs(A(k, k));
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A(i, k)) > best) {
+        best = fabs(A(i, k));
+        p = i;
+      }
+    if (!(best > 0.0)) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(A(k, j), A(p, j));
+    const double inv = 1.0 / A(k, k);
+    double *ck = A.col(k);
+    for (int i = k + 1; i < n; ++i) ck[i] *= inv;
+    for (int j = k + 1; j < n; ++j) {
+      double *cj = A.col(j);
+      const double f = cj[k];
+      if (f == 0.0) continue;
+      for (int i = k + 1; i < n; ++i) cj[i] -= ck[i] * f;
+    }
+  }
+  HMat X(n, n);
+  for (int j = 0; j < n; ++j) X(j, j) = 1.0;
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k)
+      for (int j = 0; j < n; ++j) std::swap(X(k, j), X(piv[k], j));
+  for (int j = 0; j < n; ++j) {
+    double *x = X.col(j);
+    for (int k = 0; k < n; ++k) {  // unit lower triangle
+      const double xk = x[k];
+      if (xk == 0.0) continue;
+      const double *l = A.col(k);
+      for (int i = k + 1; i < n; ++i) x[i] -= l[i] * xk;
+    }
+    for (int k = n - 1; k >= 0; --k) {  // upper triangle
+      x[k] /= A(k, k);
+      const double xk = x[k];
+      const double *u = A.col(k);
+      for (int i = 0; i < k; ++i) x[i] -= u[i] * xk;
+    }
+  }
+  A = std::move(X);
+  return true;
+}
+
+// Column interpolative decomposition Z ~ Z(:, J) X (X is k x n with X(:, J) = I) by
+// Householder QR with column pivoting, stopped once the next pivot's remaining norm is at most
+// tol times the first's.  Z (m x n) is overwritten.
+void column_id(HMat &Z, double tol, std::vector<int> &J, HMat &X) {
+  const int m = Z.r, n = Z.c;
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<double> nrm(n), ref(n);
+  for (int q = 0; q < n; ++q) {
+    const double *z = Z.col(q);
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += z[i] * z[i];
+    nrm[q] = ref[q] = s;
+  }
+  const int kmax = std::min(m, n);
+  int k = 0;
+  double r00 = 0.0;
+  std::vector<double> v(m);
+  for (int j = 0; j < kmax; ++j) {
+    int p = j;
+    for (int q = j + 1; q < n; ++q)
+      if (nrm[q] > nrm[p]) p = q;
+    double s = 0.0;
+    {
+      const double *z = Z.col(p);
+      for (int i = j; i < m; ++i) s += z[i] * z[i];
+    }
+    const double rjj = sqrt(s);
+    if (j == 0) r00 = rjj;
+    if (!(rjj > tol * r00) || rjj == 0.0) break;
+    if (p != j) {
+      std::swap_ranges(Z.col(j), Z.col(j) + m, Z.col(p));
+      std::swap(perm[j], perm[p]);
+      std::swap(nrm[j], nrm[p]);
+      std::swap(ref[j], ref[p]);
+    }
+    double *zj = Z.col(j);
+    const double x0 = zj[j];
+    const double alpha = x0 >= 0.0 ? -rjj : rjj;
+    v[j] = x0 - alpha;
+    for (int i = j + 1; i < m; ++i) v[i] = zj[i];
+    const double vtv = 2.0 * (s - x0 * alpha);
+    const double beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    for (int q = j + 1; q < n; ++q) {
+      double *zq = Z.col(q);
+      double dot = 0.0;
+      for (int i = j; i < m; ++i) dot += v[i] * zq[i];
+      const double f = beta * dot;
+      for (int i = j; i < m; ++i) zq[i] -= f * v[i];
+      nrm[q] -= zq[j] * zq[j];
+      if (nrm[q] <= 1e-8 * ref[q]) {  // cancellation: recompute the remaining norm
+        double t = 0.0;
+        for (int i = j + 1; i < m; ++i) t += zq[i] * zq[i];
+        nrm[q] = ref[q] = t;
+      }
+    }
+    zj[j] = alpha;
+    k = j + 1;
+  }
+  if (k == 0) k = 1;  // a zero block keeps one unknown
+  J.assign(perm.begin(), perm.begin() + k);
+  X = HMat(k, n);
+  for (int c = 0; c < k; ++c) X(c, perm[c]) = 1.0;
+  std::vector<double> t(k);
+  for (int q = k; q < n; ++q) {  // R11^-1 R12 by back substitution
+    const double *zq = Z.col(q);
+    for (int i = k - 1; i >= 0; --i) {
+      double s = zq[i];
+      for (int c = i + 1; c < k; ++c) s -= Z(i, c) * t[c];
+      t[i] = Z(i, i) != 0.0 ? s / Z(i, i) : 0.0;
+    }
+    for (int c = 0; c < k; ++c) X(c, perm[q]) = t[c];
+  }
+}
+
+template <class F>
+void parallel_for(int n, F f) {
+  const int nt = std::max(1, std::min<int>(n, int(std::thread::hardware_concurrency())));
+  if (nt == 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&] {
+      for (int i = next++; i < n; i = next++) f(i);
+    });
+  for (auto &x : th) x.join();
+}
+
+// ---------------------------------------------------------------------------
+// the wall operator, entry by entry
+// ---------------------------------------------------------------------------
+struct WallGeom {
+  int nw = 0, Nt = 0;
+  double d = 0.0;
+  std::vector<double> x, y, nx, ny, w, kap;
+};
+
+// A_m(u_i, u_j) for unknowns u = 2 node + component: the stresslet of Eq. (D) times w_j
+// from node j shifted by m d; at m = 0 and i = j the curvature diagonal
+// -kappa_j/(2 pi) w_j t t^T minus the jump 1/2.
+__host__ __device__ inline double a_entry(int ui, int uj, int m, const double *x, const double *y,
+                                          const double *nx, const double *ny, const double *w,
+                                          const double *kap, double d) {
+  const int i = ui >> 1, ci = ui & 1, j = uj >> 1, cj = uj & 1;
+  if (m == 0 && i == j) {
+    const double tx = -ny[j], ty = nx[j];
+    const double c = -kap[j] / (2.0 * kPi) * w[j];
+    return c * (ci ? ty : tx) * (cj ? ty : tx) - (ci == cj ? 0.5 : 0.0);
+  }
+  const double r1 = x[i] - (x[j] + m * d), r2 = y[i] - y[j];
+  const double rr = r1 * r1 + r2 * r2;
+  const double rn = r1 * nx[j] + r2 * ny[j];
+  return (ci ? r2 : r1) * (cj ? r2 : r1) * rn / (kPi * rr * rr) * w[j];
+}
+
+inline double a_host(const WallGeom &g, int ui, int uj, int m) {
+  return a_entry(ui, uj, m, g.x.data(), g.y.data(), g.nx.data(), g.ny.data(), g.w.data(),
+                 g.kap.data(), g.d);
+}
+
+// Probe matrix of a group of unknowns `It` (one column each): rows A_m(It, near) (and, when
+// two_sided, A_m(near, It)^T), then for every proxy point on the circle (cx, cy, rad) the
+// stokeslet and the radial-normal stresslet it places on the unknown (two source components
+// each), then (when targets) the velocity the unknown's density makes at the proxy point.
+HMat probe_matrix(const WallGeom &g, const std::vector<int> &It, const std::vector<int> &near,
+                  int m, bool two_sided, double cx, double cy, double rad, int npx,
+                  bool targets) {
+  const int nn = int(near.size());
+  const int rows = nn * (two_sided ? 2 : 1) + 4 * npx + (targets ? 2 * npx : 0);
+  HMat Z(rows, int(It.size()));
+  for (int q = 0; q < int(It.size()); ++q) {
+    const int u = It[q], node = u >> 1, comp = u & 1;
+    double *z = Z.col(q);
+    int r = 0;
+    for (int p = 0; p < nn; ++p) z[r++] = a_host(g, u, near[p], m);
+    if (two_sided)
+      for (int p = 0; p < nn; ++p) z[r++] = a_host(g, near[p], u, m);
+    for (int p = 0; p < npx; ++p) {
+      const double c = cos(2.0 * kPi * p / npx), s = sin(2.0 * kPi * p / npx);
+      const double px = cx + rad * c, py = cy + rad * s;
+      const double r1 = g.x[node] - px, r2 = g.y[node] - py;
+      const double rr = r1 * r1 + r2 * r2;
+      const double rc = comp ? r2 : r1;
+      const double lg = -0.5 * log(rr);
+      z[r++] = ((comp == 0 ? lg : 0.0) + rc * r1 / rr) / (4.0 * kPi);
+      z[r++] = ((comp == 1 ? lg : 0.0) + rc * r2 / rr) / (4.0 * kPi);
+      const double rn = r1 * c + r2 * s;
+      z[r++] = rc * r1 * rn / (kPi * rr * rr);
+      z[r++] = rc * r2 * rn / (kPi * rr * rr);
+      if (targets) {
+        const double t1 = px - g.x[node], t2 = py - g.y[node];
+        const double tt = t1 * t1 + t2 * t2;
+        const double tn = t1 * g.nx[node] + t2 * g.ny[node];
+        const double f = (comp ? t2 : t1) * tn / (kPi * tt * tt) * g.w[node];
+        z[r++] = t1 * f;
+        z[r++] = t2 * f;
+      }
+    }
+  }
+  return Z;
+}
+
+struct Box {
+  int a = 0, b = 0;                  // node range
+  double x0 = 0, x1 = 0, y0 = 0, y1 = 0;  // bounding box of the nodes
+  std::vector<int> act, skel;        // active unknowns, skeleton (a subset of act)
+  HMat Dh, E, Ft, G;
+};
+
+// ---------------------------------------------------------------------------
+// device passes
+// ---------------------------------------------------------------------------
+struct HbsBox {
+  int n, k, in_off, out_off;  // active unknowns, skeleton, offsets in the level vectors
+  long long ft, e, g;         // offsets of F^* (k x n), E (n x k), G (n x n)
+};
+
+// mode 0 (upward):   y[out_off + r] = sum_j F^*[r + j k] x1[in_off + j],   r < k
+// mode 1 (downward): y[in_off + r]  = sum_j E[r + j n] x1[out_off + j]
+//                                   + sum_j G[r + j n] x2[in_off + j],     r < n
+// over the right-hand sides [blockIdx.y * kHbsCols, ...) of column-major x1, x2, y.
+__global__ void __launch_bounds__(kHbsThreads)
+    hbs_level_kernel(const HbsBox *boxes, const double *mats, int mode, int ncol, const double *x1,
+                     long long ld1, const double *x2, long long ld2, double *y, long long ldy) {
+  const HbsBox b = boxes[blockIdx.x];
+  const int c0 = blockIdx.y * kHbsCols;
+  const int nc = min(kHbsCols, ncol - c0);
+  const int rows = mode == 0 ? b.k : b.n;
+  for (int idx = threadIdx.x; idx < rows * nc; idx += blockDim.x) {
+    const int r = idx % rows;
+    const long long c = c0 + idx / rows;
+    double s = 0.0;
+    if (mode == 0) {
+      const double *M = mats + b.ft + r;
+      const double *x = x1 + c * ld1 + b.in_off;
+      for (int j = 0; j < b.n; ++j) s = fma(M[size_t(j) * b.k], x[j], s);
+      y[c * ldy + b.out_off + r] = s;
+    } else {
+      const double *M = mats + b.e + r;
+      const double *x = x1 + c * ld1 + b.out_off;
+      for (int j = 0; j < b.k; ++j) s = fma(M[size_t(j) * b.n], x[j], s);
+      const double *Gm = mats + b.g + r;
+      const double *z = x2 + c * ld2 + b.in_off;
+      for (int j = 0; j < b.n; ++j) s = fma(Gm[size_t(j) * b.n], z[j], s);
+      y[c * ldy + b.in_off + r] = s;
+    }
+  }
+}
+
+// R (l x nA, column-major): R[r, u] = A_{m_r}(J_r, u).
+__global__ void fill_rows_kernel(int l, int nA, const int *J, const int *mr, const double *x,
+                                 const double *y, const double *nx, const double *ny,
+                                 const double *w, const double *kap, double d, double *R) {
+  const size_t total = size_t(l) * nA;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    const int r = int(idx % l), u = int(idx / l);
+    R[idx] = a_entry(J[r], u, mr[r], x, y, nx, ny, w, kap, d);
+  }
+}
+
+// L (nA x l) block diagonal: section s puts its rows x cols block at (row0, col0).
+struct SecBlock {
+  int row0, rows, col0, cols;
+  long long off;
+};
+
+__global__ void scatter_blocks_kernel(const SecBlock *sec, const double *vals, int nA, double *L) {
+  const SecBlock s = sec[blockIdx.x];
+  for (int idx = threadIdx.x; idx < s.rows * s.cols; idx += blockDim.x) {
+    const int i = idx % s.rows, c = idx / s.rows;
+    L[size_t(s.col0 + c) * nA + s.row0 + i] = vals[s.off + idx];
+  }
+}
+
+__global__ void add_identity_kernel(int n, double *K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) K[size_t(i) * n + i] += 1.0;
+}
+
+__global__ void set_identity_kernel(int n, double *K) {
+  const size_t nn = size_t(n) * n;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < nn;
+       i += size_t(gridDim.x) * blockDim.x)
+    K[i] = (i % size_t(n + 1) == 0) ? 1.0 : 0.0;
+}
+
+int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, size_t(152) * 32)); }
+
+}  // namespace
+
+struct fds_solver {
+  int nA = 0, L = 0, l = 0;
+  // HBS: per level 1..L the box table and offsets, level vector lengths N[0..L]
+  std::vector<int> nboxes;             // [L + 1], nboxes[0] = 1 (root)
+  std::vector<HbsBox *> d_boxes;       // [L + 1]
+  std::vector<long long> N;            // [L + 1]
+  double *d_mats = nullptr;
+  // neighbour factors
+  double *d_Z = nullptr, *d_R = nullptr, *d_Kinv = nullptr;
+  // workspace of one pass (kChunk right-hand sides)
+  double *d_up = nullptr, *d_down = nullptr, *d_out = nullptr, *d_t = nullptr, *d_s = nullptr;
+  size_t up_len = 0;                   // sum of N[0..L-1]
+  fds_info info;
+};
+
+namespace {
+
+int cuda_fail(std::string &err, cudaError_t e, const char *what) {
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA;
+}
+
+#define FK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(err, e_, #call); \
+  } while (0)
+#define FB(call)                                                                 \
+  do {                                                                           \
+    cublasStatus_t e_ = (call);                                                  \
+    if (e_ != CUBLAS_STATUS_SUCCESS) {                                           \
+      err = std::string(#call) + ": cublas " + std::to_string(int(e_));          \
+      return STOKES_ERR_CUDA;                                                    \
+    }                                                                            \
+  } while (0)
+#define FQ(call)                                                                 \
+  do {                                                                           \
+    cusolverStatus_t e_ = (call);                                                \
+    if (e_ != CUSOLVER_STATUS_SUCCESS) {                                         \
+      err = std::string(#call) + ": cusolver " + std::to_string(int(e_));        \
+      return STOKES_ERR_CUDA;                                                    \
+    }                                                                            \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t n, size_t &bytes) {
+  bytes += sizeof(T) * n;
+  return cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * std::max<size_t>(n, 1));
+}
+
+void bounds(const WallGeom &g, Box &bx) {
+  bx.x0 = bx.y0 = 1e300;
+  bx.x1 = bx.y1 = -1e300;
+  for (int i = bx.a; i < bx.b; ++i) {
+    bx.x0 = std::min(bx.x0, g.x[i]);
+    bx.x1 = std::max(bx.x1, g.x[i]);
+    bx.y0 = std::min(bx.y0, g.y[i]);
+    bx.y1 = std::max(bx.y1, g.y[i]);
+  }
+}
+
+// A_0^-1 X for up to kChunk columns (X column-major with leading dimension nA).
+int hbs_pass(fds_solver *f, const double *X, double *out, int nc, cudaStream_t s,
+             std::string &err) {
+  const int L = f->L;
+  // upward: level L reads X, level l writes the level-(l-1) vector
+  std::vector<double *> up(L + 1), down(L + 1);
+  {
+    size_t o = 0;
+    for (int lev = 0; lev < L; ++lev) {
+      up[lev] = f->d_up + o * kChunk;
+      down[lev] = f->d_down + o * kChunk;
+      o += size_t(f->N[lev]);
+    }
+  }
+  for (int lev = L; lev >= 1; --lev) {
+    const double *x1 = lev == L ? X : up[lev];
+    const long long ld1 = f->N[lev];
+    hbs_level_kernel<<<dim3(f->nboxes[lev], (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
+        f->d_boxes[lev], f->d_mats, 0, nc, x1, ld1, nullptr, 0, up[lev - 1], f->N[lev - 1]);
+  }
+  // root: u^ = G_root v^
+  hbs_level_kernel<<<dim3(1, (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
+      f->d_boxes[0], f->d_mats, 0, nc, up[0], f->N[0], nullptr, 0, down[0], f->N[0]);
+  for (int lev = 1; lev <= L; ++lev) {
+    const double *v = lev == L ? X : up[lev];
+    double *y = lev == L ? out : down[lev];
+    hbs_level_kernel<<<dim3(f->nboxes[lev], (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
+        f->d_boxes[lev], f->d_mats, 1, nc, down[lev - 1], f->N[lev - 1], v, f->N[lev], y,
+        f->N[lev]);
+  }
+  FK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+// X <- A_0^-1 X, in passes of kChunk columns.
+int hbs_apply(fds_solver *f, double *X, int nrhs, cudaStream_t s, std::string &err) {
+  for (int c0 = 0; c0 < nrhs; c0 += kChunk) {
+    const int nc = std::min(kChunk, nrhs - c0);
+    double *Xc = X + size_t(c0) * f->nA;
+    int st = hbs_pass(f, Xc, f->d_out, nc, s, err);
+    if (st) return st;
+    FK(cudaMemcpyAsync(Xc, f->d_out, sizeof(double) * f->nA * nc, cudaMemcpyDeviceToDevice, s));
+  }
+  return STOKES_OK;
+}
+
+struct HostFactors {
+  int nA = 0, L = 0;
+  std::vector<int> nboxes;
+  std::vector<long long> N;
+  std::vector<double> mats;               // F^*, E, G per box, then G_root
+  std::vector<std::vector<HbsBox>> tabs;  // [L + 1], tabs[0] = the root
+  std::vector<int> Jall, mall;            // neighbour skeleton unknowns and their image m
+  std::vector<SecBlock> sb;               // L's blocks
+  std::vector<double> svals;
+  fds_info info;
+  WallGeom g;
+};
+
+// Host part of the build: the HBS tables and the neighbour sections, packed for the device.
+int host_factor(int n_w, const double *nodes, const double *weights, const double *normals,
+                const double *curvature, double period, const fds_params &p, HostFactors &hf,
+                std::string &err) {
+  if (n_w < 4 || !(period > 0.0) || p.leaf < 2 || p.n_proxy < 8 || p.n_proxy_nb < 8 ||
+      p.sec_max < 2 || !(p.tol > 0.0)) {
+    err = "fds: bad arguments";
+    return STOKES_ERR_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  WallGeom g;
+  g.nw = n_w;
+  g.Nt = 2 * n_w;
+  g.d = period;
+  const int Nt = g.Nt, nA = 2 * Nt;
+  g.x.resize(Nt);
+  g.y.resize(Nt);
+  g.nx.resize(Nt);
+  g.ny.resize(Nt);
+  g.w.assign(weights, weights + Nt);
+  g.kap.assign(curvature, curvature + Nt);
+  for (int i = 0; i < Nt; ++i) {
+    g.x[i] = nodes[2 * i];
+    g.y[i] = nodes[2 * i + 1];
+    g.nx[i] = normals[2 * i];
+    g.ny[i] = normals[2 * i + 1];
+  }
+  hf.nA = nA;
+  // ---- HBS tree: level 0 the root, level 1 the walls, then halves ----
+  std::vector<std::vector<Box>> lv(2);
+  lv[0].resize(1);
+  lv[0][0].a = 0;
+  lv[0][0].b = Nt;
+  lv[1].resize(2);
+  lv[1][0].a = 0;
+  lv[1][0].b = n_w;
+  lv[1][1].a = n_w;
+  lv[1][1].b = Nt;
+  while (lv.back()[0].b - lv.back()[0].a > p.leaf) {
+    std::vector<Box> nx;
+    for (const Box &bx : lv.back()) {
+      const int h = (bx.a + bx.b) / 2;
+      Box c0, c1;
+      c0.a = bx.a;
+      c0.b = h;
+      c1.a = h;
+      c1.b = bx.b;
+      nx.push_back(c0);
+      nx.push_back(c1);
+    }
+    lv.push_back(nx);
+  }
+  const int L = int(lv.size()) - 1;
+  hf.L = L;
+  for (auto &level : lv)
+    for (Box &bx : level) bounds(g, bx);
+  for (Box &bx : lv[L]) {
+    bx.act.resize(2 * (bx.b - bx.a));
+    std::iota(bx.act.begin(), bx.act.end(), 2 * bx.a);
+  }
+  std::atomic<int> failed(0);
+  for (int lev = L; lev >= 1; --lev) {
+    std::vector<Box> &B = lv[lev];
+    if (lev < L)
+      for (int i = 0; i < int(B.size()); ++i) {
+        const Box &c0 = lv[lev + 1][2 * i], &c1 = lv[lev + 1][2 * i + 1];
+        B[i].act = c0.skel;
+        B[i].act.insert(B[i].act.end(), c1.skel.begin(), c1.skel.end());
+      }
+    parallel_for(int(B.size()), [&](int i) {
+      Box &bx = B[i];
+      const double cx = 0.5 * (bx.x0 + bx.x1), cy = 0.5 * (bx.y0 + bx.y1);
+      const double rad = 1.5 * 0.5 * hypot(bx.x1 - bx.x0, bx.y1 - bx.y0);
+      std::vector<int> near;
+      for (int j = 0; j < int(B.size()); ++j) {
+        if (j == i) continue;
+        const Box &o = B[j];
+        const double dx = std::max({o.x0 - cx, 0.0, cx - o.x1});
+        const double dy = std::max({o.y0 - cy, 0.0, cy - o.y1});
+        if (dx * dx + dy * dy >= rad * rad) continue;
+        for (int u : o.act) {
+          const double ex = g.x[u >> 1] - cx, ey = g.y[u >> 1] - cy;
+          if (ex * ex + ey * ey < rad * rad) near.push_back(u);
+        }
+      }
+      HMat Z = probe_matrix(g, bx.act, near, 0, true, cx, cy, rad, p.n_proxy, true);
+      std::vector<int> J;
+      HMat X;
+      column_id(Z, p.tol, J, X);
+      bx.skel.resize(J.size());
+      for (size_t c = 0; c < J.size(); ++c) bx.skel[c] = bx.act[J[c]];
+      const int n = int(bx.act.size()), k = int(J.size());
+      HMat D(n, n);
+      if (lev == L) {
+        for (int jj = 0; jj < n; ++jj)
+          for (int ii = 0; ii < n; ++ii) D(ii, jj) = a_host(g, bx.act[ii], bx.act[jj], 0);
+      } else {
+        const Box &c0 = lv[lev + 1][2 * i], &c1 = lv[lev + 1][2 * i + 1];
+        const int ka = int(c0.skel.size());
+        for (int jj = 0; jj < n; ++jj)
+          for (int ii = 0; ii < n; ++ii) {
+            const bool ia = ii < ka, ja = jj < ka;
+            if (ia && ja)
+              D(ii, jj) = c0.Dh(ii, jj);
+            else if (!ia && !ja)
+              D(ii, jj) = c1.Dh(ii - ka, jj - ka);
+            else
+              D(ii, jj) = a_host(g, bx.act[ii], bx.act[jj], 0);
+          }
+      }
+      if (!invert(D)) {
+        failed = 1;
+        return;
+      }
+      const HMat DiP = mul_nt(D, X);   // D^-1 P      (n x k)
+      const HMat PtDi = mul(X, D);     // P^T D^-1    (k x n)
+      HMat Dh = mul_nt(PtDi, X);       // P^T D^-1 P  (k x k)
+      if (!invert(Dh)) {
+        failed = 1;
+        return;
+      }
+      bx.E = mul(DiP, Dh);
+      bx.Ft = mul(Dh, PtDi);
+      HMat EP = mul(bx.E, PtDi);
+      for (size_t q = 0; q < D.a.size(); ++q) D.a[q] -= EP.a[q];
+      bx.G = std::move(D);
+      bx.Dh = std::move(Dh);
+      (void)k;
+    });
+    if (failed) {
+      err = "fds: singular diagonal block in the HBS factorization";
+      return STOKES_ERR_CUDA;
+    }
+    // children's D^ are no longer needed
+    if (lev < L)
+      for (Box &c : lv[lev + 1]) c.Dh = HMat();
+  }
+  // root: [D^_a, A_0(J_a, J_b); A_0(J_b, J_a), D^_b]^-1
+  HMat Groot;
+  {
+    const Box &c0 = lv[1][0], &c1 = lv[1][1];
+    std::vector<int> act = c0.skel;
+    act.insert(act.end(), c1.skel.begin(), c1.skel.end());
+    const int n = int(act.size()), ka = int(c0.skel.size());
+    Groot = HMat(n, n);
+    for (int jj = 0; jj < n; ++jj)
+      for (int ii = 0; ii < n; ++ii) {
+        const bool ia = ii < ka, ja = jj < ka;
+        Groot(ii, jj) = (ia && ja)     ? c0.Dh(ii, jj)
+                        : (!ia && !ja) ? c1.Dh(ii - ka, jj - ka)
+                                       : a_host(g, act[ii], act[jj], 0);
+      }
+    if (!invert(Groot)) {
+      err = "fds: singular root block";
+      return STOKES_ERR_CUDA;
+    }
+    lv[0][0].act = act;
+  }
+  // ---- neighbour sections (Sec. 4.2) ----
+  struct Section {
+    int a, b, m;
+    std::vector<int> skel;
+    HMat P;  // rows x k (interpolation matrix)
+  };
+  std::vector<Section> secs;
+  for (int m : {-1, 1})
+    for (int w0 : {0, n_w}) {
+      int a = 0, b = n_w;
+      while (b - a > p.sec_max) {
+        const int h = (a + b) / 2;
+        if (m > 0) {
+          secs.push_back({w0 + a, w0 + h, m, {}, HMat()});
+          a = h;
+        } else {
+          secs.push_back({w0 + h, w0 + b, m, {}, HMat()});
+          b = h;
+        }
+      }
+      secs.push_back({w0 + a, w0 + b, m, {}, HMat()});
+    }
+  parallel_for(int(secs.size()), [&](int si) {
+    Section &sc = secs[si];
+    Box bx;
+    bx.a = sc.a;
+    bx.b = sc.b;
+    bounds(g, bx);
+    const double cx = 0.5 * (bx.x0 + bx.x1), cy = 0.5 * (bx.y0 + bx.y1);
+    const int la = sc.a % n_w, lb = sc.b - (sc.a - la);
+    const bool touch = (sc.m > 0 && lb == n_w) || (sc.m < 0 && la == 0);
+    double rad;
+    std::vector<int> near;
+    if (!touch) {
+      rad = 0.9 * fabs((sc.m > 0 ? g.d : 0.0) - cx);
+    } else {
+      rad = 1.75 * 0.5 * hypot(bx.x1 - bx.x0, bx.y1 - bx.y0);
+      for (int j = 0; j < Nt; ++j) {
+        const double ex = g.x[j] + sc.m * g.d - cx, ey = g.y[j] - cy;
+        if (ex * ex + ey * ey < rad * rad) {
+          near.push_back(2 * j);
+          near.push_back(2 * j + 1);
+        }
+      }
+    }
+    std::vector<int> It(2 * (sc.b - sc.a));
+    std::iota(It.begin(), It.end(), 2 * sc.a);
+    HMat Z = probe_matrix(g, It, near, sc.m, false, cx, cy, rad, p.n_proxy_nb, false);
+    std::vector<int> J;
+    HMat X;
+    column_id(Z, p.tol, J, X);
+    sc.skel.resize(J.size());
+    for (size_t c = 0; c < J.size(); ++c) sc.skel[c] = It[J[c]];
+    // P = X^T
+    sc.P = HMat(X.c, X.r);
+    for (int c = 0; c < X.r; ++c)
+      for (int r = 0; r < X.c; ++r) sc.P(r, c) = X(c, r);
+  });
+  const auto t1 = std::chrono::steady_clock::now();
+  hf.info.host_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  // ---- pack the HBS tables for the device ----
+  hf.nboxes.assign(L + 1, 0);
+  hf.N.assign(L + 1, 0);
+  hf.N[L] = nA;
+  
+  hf.tabs.assign(L + 1, {});
+  int max_rank = 0;
+  for (int lev = L; lev >= 1; --lev) {
+    int in_off = 0, out_off = 0;
+    for (const Box &bx : lv[lev]) {
+      HbsBox hb;
+      hb.n = int(bx.act.size());
+      hb.k = int(bx.skel.size());
+      hb.in_off = in_off;
+      hb.out_off = out_off;
+      hb.ft = (long long)hf.mats.size();
+      hf.mats.insert(hf.mats.end(), bx.Ft.a.begin(), bx.Ft.a.end());
+      hb.e = (long long)hf.mats.size();
+      hf.mats.insert(hf.mats.end(), bx.E.a.begin(), bx.E.a.end());
+      hb.g = (long long)hf.mats.size();
+      hf.mats.insert(hf.mats.end(), bx.G.a.begin(), bx.G.a.end());
+      hf.tabs[lev].push_back(hb);
+      in_off += hb.n;
+      out_off += hb.k;
+      max_rank = std::max(max_rank, hb.k);
+    }
+    hf.nboxes[lev] = int(lv[lev].size());
+    hf.N[lev - 1] = out_off;
+  }
+  {
+    HbsBox hb;
+    hb.n = hb.k = Groot.r;
+    hb.in_off = hb.out_off = 0;
+    hb.ft = (long long)hf.mats.size();
+    hb.e = hb.g = 0;
+    hf.mats.insert(hf.mats.end(), Groot.a.begin(), Groot.a.end());
+    hf.tabs[0].push_back(hb);
+    hf.nboxes[0] = 1;
+  }
+  hf.info.levels = L;
+  hf.info.max_rank = max_rank;
+  hf.info.root_size = Groot.r;
+  // neighbour factor layout
+  for (const Section &sc : secs) {
+    SecBlock b;
+    b.row0 = 2 * sc.a;
+    b.rows = 2 * (sc.b - sc.a);
+    b.col0 = int(hf.Jall.size());
+    b.cols = int(sc.skel.size());
+    b.off = (long long)hf.svals.size();
+    hf.svals.insert(hf.svals.end(), sc.P.a.begin(), sc.P.a.end());
+    hf.sb.push_back(b);
+    for (int u : sc.skel) {
+      hf.Jall.push_back(u);
+      hf.mall.push_back(sc.m);
+    }
+  }
+  hf.info.neighbour_rank = int(hf.Jall.size());
+  hf.info.sections = int(secs.size());
+  hf.g = std::move(g);
+  return STOKES_OK;
+}
+
+}  // namespace
+
+int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weights,
+              const double *normals, const double *curvature, double period, const fds_params &p,
+              cudaStream_t s, cublasHandle_t blas, cusolverDnHandle_t sol, std::string &err) {
+  *out = nullptr;
+  HostFactors hf;
+  {
+    const int st = host_factor(n_w, nodes, weights, normals, curvature, period, p, hf, err);
+    if (st) return st;
+  }
+  const WallGeom &g = hf.g;
+  const int L = hf.L, nA = hf.nA, Nt = g.Nt, l = int(hf.Jall.size());
+  fds_solver *f = new fds_solver();
+  f->nA = nA;
+  f->L = L;
+  f->l = l;
+  f->info = hf.info;
+  f->nboxes = hf.nboxes;
+  f->N = hf.N;
+  // ---- device side ----
+  size_t &bytes = f->info.device_bytes;
+  std::vector<void *> tmp;  // set-up scratch, freed on every exit
+  auto bail = [&](int st) {
+    for (void *q : tmp) cudaFree(q);
+    fds_destroy(f);
+    return st;
+  };
+#define FD(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return bail(cuda_fail(err, e_, #call)); \
+  } while (0)
+#define FDB(call)                                                      \
+  do {                                                                 \
+    cublasStatus_t e_ = (call);                                        \
+    if (e_ != CUBLAS_STATUS_SUCCESS) {                                 \
+      err = std::string(#call) + ": cublas " + std::to_string(int(e_)); \
+      return bail(STOKES_ERR_CUDA);                                    \
+    }                                                                  \
+  } while (0)
+#define FDQ(call)                                                        \
+  do {                                                                   \
+    cusolverStatus_t e_ = (call);                                        \
+    if (e_ != CUSOLVER_STATUS_SUCCESS) {                                 \
+      err = std::string(#call) + ": cusolver " + std::to_string(int(e_)); \
+      return bail(STOKES_ERR_CUDA);                                      \
+    }                                                                    \
+  } while (0)
+  const auto t2 = std::chrono::steady_clock::now();
+  FD(dalloc(f->d_mats, hf.mats.size(), bytes));
+  FD(cudaMemcpyAsync(f->d_mats, hf.mats.data(), sizeof(double) * hf.mats.size(), cudaMemcpyHostToDevice, s));
+  f->d_boxes.assign(L + 1, nullptr);
+  for (int lev = 0; lev <= L; ++lev) {
+    FD(dalloc(f->d_boxes[lev], hf.tabs[lev].size(), bytes));
+    FD(cudaMemcpyAsync(f->d_boxes[lev], hf.tabs[lev].data(), sizeof(HbsBox) * hf.tabs[lev].size(),
+                       cudaMemcpyHostToDevice, s));
+  }
+  f->up_len = 0;
+  for (int lev = 0; lev < L; ++lev) f->up_len += size_t(f->N[lev]);
+  FD(dalloc(f->d_up, f->up_len * kChunk, bytes));
+  FD(dalloc(f->d_down, f->up_len * kChunk, bytes));
+  FD(dalloc(f->d_out, size_t(nA) * kChunk, bytes));
+  FD(dalloc(f->d_t, size_t(l) * kChunk, bytes));
+  FD(dalloc(f->d_s, size_t(l) * kChunk, bytes));
+  // geometry, R = A_m(J, :)
+  double *dg = nullptr;
+  int *dJ = nullptr;
+  size_t scratch = 0;
+  FD(dalloc(dg, size_t(6) * Nt, scratch));
+  tmp.push_back(dg);
+  FD(dalloc(dJ, size_t(2) * l, scratch));
+  tmp.push_back(dJ);
+  const double *hs[6] = {g.x.data(), g.y.data(), g.nx.data(), g.ny.data(), g.w.data(), g.kap.data()};
+  for (int q = 0; q < 6; ++q)
+    FD(cudaMemcpyAsync(dg + size_t(q) * Nt, hs[q], sizeof(double) * Nt, cudaMemcpyHostToDevice, s));
+  FD(cudaMemcpyAsync(dJ, hf.Jall.data(), sizeof(int) * l, cudaMemcpyHostToDevice, s));
+  FD(cudaMemcpyAsync(dJ + l, hf.mall.data(), sizeof(int) * l, cudaMemcpyHostToDevice, s));
+  FD(dalloc(f->d_R, size_t(l) * nA, bytes));
+  fill_rows_kernel<<<grid_for(size_t(l) * nA), 256, 0, s>>>(
+      l, nA, dJ, dJ + l, dg, dg + Nt, dg + 2 * Nt, dg + 3 * Nt, dg + 4 * Nt, dg + 5 * Nt, g.d, f->d_R);
+  FD(cudaGetLastError());
+  // Z = A_0^-1 L
+  SecBlock *dsec = nullptr;
+  double *dvals = nullptr;
+  FD(dalloc(dsec, hf.sb.size(), scratch));
+  tmp.push_back(dsec);
+  FD(dalloc(dvals, hf.svals.size(), scratch));
+  tmp.push_back(dvals);
+  FD(cudaMemcpyAsync(dsec, hf.sb.data(), sizeof(SecBlock) * hf.sb.size(), cudaMemcpyHostToDevice, s));
+  FD(cudaMemcpyAsync(dvals, hf.svals.data(), sizeof(double) * hf.svals.size(), cudaMemcpyHostToDevice, s));
+  FD(dalloc(f->d_Z, size_t(nA) * l, bytes));
+  FD(cudaMemsetAsync(f->d_Z, 0, sizeof(double) * size_t(nA) * l, s));
+  scatter_blocks_kernel<<<int(hf.sb.size()), 256, 0, s>>>(dsec, dvals, nA, f->d_Z);
+  FD(cudaGetLastError());
+  {
+    int st = hbs_apply(f, f->d_Z, l, s, err);
+    if (st) return bail(st);
+  }
+  // K = I + R Z, then K^-1
+  double *dK = nullptr;
+  FD(dalloc(dK, size_t(l) * l, scratch));
+  tmp.push_back(dK);
+  const double one = 1.0, zero = 0.0;
+  cublasSetStream(blas, s);
+  cusolverDnSetStream(sol, s);
+  FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, nA, &one, f->d_R, l, f->d_Z, nA, &zero, dK, l));
+  add_identity_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, dK);
+  FD(cudaGetLastError());
+  int lwork = 0;
+  FDQ(cusolverDnDgetrf_bufferSize(sol, l, l, dK, l, &lwork));
+  double *work = nullptr;
+  int *piv = nullptr, *dinfo = nullptr;
+  FD(dalloc(work, size_t(std::max(lwork, 1)), scratch));
+  tmp.push_back(work);
+  FD(dalloc(piv, size_t(l) + 1, scratch));
+  tmp.push_back(piv);
+  FD(dalloc(dinfo, 2, scratch));
+  tmp.push_back(dinfo);
+  FD(dalloc(f->d_Kinv, size_t(l) * l, bytes));
+  set_identity_kernel<<<grid_for(size_t(l) * l), 256, 0, s>>>(l, f->d_Kinv);
+  FDQ(cusolverDnDgetrf(sol, l, l, dK, l, work, piv, dinfo));
+  FDQ(cusolverDnDgetrs(sol, CUBLAS_OP_N, l, l, dK, l, piv, f->d_Kinv, l, dinfo + 1));
+  int hinfo[2] = {0, 0};
+  FD(cudaMemcpyAsync(hinfo, dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+  FD(cudaStreamSynchronize(s));
+  if (hinfo[0] != 0 || hinfo[1] != 0) {
+    err = "fds: I + R A_0^-1 L is singular";
+    return bail(STOKES_ERR_CUDA);
+  }
+  for (void *q : tmp) cudaFree(q);
+#undef FD
+#undef FDB
+#undef FDQ
+  f->info.device_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t2).count();
+  *out = f;
+  return STOKES_OK;
+}
+
+int fds_solve(fds_solver *f, double *X, int nrhs, cudaStream_t s, cublasHandle_t blas,
+              std::string &err) {
+  if (!f || !X || nrhs < 0) {
+    err = "fds_solve: bad arguments";
+    return STOKES_ERR_ARG;
+  }
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  cublasSetStream(blas, s);
+  for (int c0 = 0; c0 < nrhs; c0 += kChunk) {
+    const int nc = std::min(kChunk, nrhs - c0);
+    double *Xc = X + size_t(c0) * f->nA;
+    int st = hbs_pass(f, Xc, f->d_out, nc, s, err);  // y = A_0^-1 v  (in d_out)
+    if (st) return st;
+    if (f->l > 0) {
+      if (nc == 1) {
+        FB(cublasDgemv(blas, CUBLAS_OP_N, f->l, f->nA, &one, f->d_R, f->l, f->d_out, 1, &zero,
+                       f->d_t, 1));
+        FB(cublasDgemv(blas, CUBLAS_OP_N, f->l, f->l, &one, f->d_Kinv, f->l, f->d_t, 1, &zero,
+                       f->d_s, 1));
+        FB(cublasDgemv(blas, CUBLAS_OP_N, f->nA, f->l, &mone, f->d_Z, f->nA, f->d_s, 1, &one,
+                       f->d_out, 1));
+      } else {
+        FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->nA, &one, f->d_R, f->l,
+                       f->d_out, f->nA, &zero, f->d_t, f->l));
+        FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->l, &one, f->d_Kinv, f->l,
+                       f->d_t, f->l, &zero, f->d_s, f->l));
+        FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->nA, nc, f->l, &mone, f->d_Z, f->nA,
+                       f->d_s, f->l, &one, f->d_out, f->nA));
+      }
+    }
+    FK(cudaMemcpyAsync(Xc, f->d_out, sizeof(double) * f->nA * nc, cudaMemcpyDeviceToDevice, s));
+  }
+  return STOKES_OK;
+}
+
+void fds_get_info(const fds_solver *f, fds_info *info) {
+  if (f && info) *info = f->info;
+}
+
+void fds_destroy(fds_solver *f) {
+  if (!f) return;
+  cudaFree(f->d_mats);
+  for (HbsBox *b : f->d_boxes) cudaFree(b);
+  cudaFree(f->d_Z);
+  cudaFree(f->d_R);
+  cudaFree(f->d_Kinv);
+  cudaFree(f->d_up);
+  cudaFree(f->d_down);
+  cudaFree(f->d_out);
+  cudaFree(f->d_t);
+  cudaFree(f->d_s);
+  delete f;
+}
+
+}  // namespace stokes

@@ -29,6 +29,7 @@
 #include <chrono>
 #include <vector>
 
+#include "fds.cuh"
 #include "stokes_internal.cuh"
 #include "stokes_mlp_internal.cuh"
 
@@ -66,6 +67,10 @@ struct stokes_sim {
   size_t wall_ws_len = 0;                   // capacity of d_wb / d_wr / d_wr32 (elements)
   int wall_refinements = 0;                 // last wall solve: refinement sweeps and
   double wall_residual = 0.0;               //   relative residual ||b - A x|| / ||b||
+  // STOKES_WALLS_FDS: the fast direct solver of Sec. 4 (HBS A_0^-1, neighbour L R, SMW)
+  stokes::fds_solver *fds = nullptr;
+  stokes::fds_params fds_p;
+  double walls_setup_ms = 0.0;              // last stokes_sim_set_walls, wall clock
   // vesicles
   bool have_ves = false;
   int V = 0, n = 0, Nv = 0;
@@ -954,6 +959,12 @@ __global__ void identity_f32_kernel(int64_t n, float *a) {
 // the two dense matrices once instead of running latency-bound triangular solves.
 int wall_solve(stokes_sim *m, double *X, int nrhs, int max_sweeps = 12) {
   const int64_t nA = m->nA;
+  if (m->wall_solver == STOKES_WALLS_FDS) {  // direct: HBS + SMW, no residual check
+    const int st = stokes::fds_solve(m->fds, X, nrhs, m->s, m->blas, m->err);
+    m->wall_refinements = 0;
+    m->wall_residual = -1.0;
+    return st;
+  }
   if (m->wall_solver == STOKES_WALLS_LU64) {
     QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, nrhs, m->d_LU, m->nA, m->d_piv, X, m->nA,
                         m->d_info));
@@ -1264,6 +1275,8 @@ void free_walls(stokes_sim *m) {
   dfree(m->d_wr32);
   dfree(m->d_wb32);
   m->wall_ws_len = 0;
+  stokes::fds_destroy(m->fds);
+  m->fds = nullptr;
   dfree(m->d_W);
   dfree(m->d_C);
   dfree(m->d_Spinv);
@@ -1365,6 +1378,7 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
     return fail(m, STOKES_ERR_ARG, "each wall's first node must lie on x = 0 (the inlet)");
   SK(cudaSetDevice(m->device));
   free_walls(m);
+  const auto t_setup = std::chrono::steady_clock::now();
   const int Nt = 2 * n_per_wall, nA = 2 * Nt;
   m->Nt = Nt;
   m->nA = nA;
@@ -1414,16 +1428,19 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   // assemble A, B, C, Q
   double *dQ = nullptr, *dS = nullptr, *dU = nullptr, *dVt = nullptr, *dsig = nullptr;
   const bool lu32 = m->wall_solver == STOKES_WALLS_LU32_REFINE;
+  const bool fds = m->wall_solver == STOKES_WALLS_FDS;
   double *dA = nullptr;
-  SK(dalloc(dA, size_t(nA) * nA));
-  (lu32 ? m->d_A : m->d_LU) = dA;
+  if (!fds) {
+    SK(dalloc(dA, size_t(nA) * nA));
+    (lu32 ? m->d_A : m->d_LU) = dA;
+  }
   SK(dalloc(m->d_W, size_t(nA) * 2 * M));
   SK(dalloc(m->d_C, size_t(4) * K * nA));
   SK(dalloc(dQ, size_t(4) * K * 2 * M));
-  if (!lu32) SK(dalloc(m->d_piv, nA));
+  if (!lu32 && !fds) SK(dalloc(m->d_piv, nA));
   const double cmu = 1.0 / (4.0 * kPiD * mu);
   const double2 *wx = m->d_wx, *wn = reinterpret_cast<const double2 *>(dn);
-  assemble_A_kernel<<<dim3(nb(Nt, 128), Nt), 128, 0, m->s>>>(Nt, wx, wn, dw, dk, period, dA);
+  if (!fds) assemble_A_kernel<<<dim3(nb(Nt, 128), Nt), 128, 0, m->s>>>(Nt, wx, wn, dw, dk, period, dA);
   assemble_B_kernel<<<dim3(nb(Nt, 128), M), 128, 0, m->s>>>(Nt, M, wx, m->d_proxy, cmu, m->d_W);
   SK(dalloc(m->d_B, size_t(nA) * 2 * M));
   SK(cudaMemcpyAsync(m->d_B, m->d_W, sizeof(double) * nA * 2 * M, cudaMemcpyDeviceToDevice, m->s));
@@ -1433,11 +1450,19 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(dalloc(m->d_Q, size_t(4) * K * 2 * M));
   SK(cudaMemcpyAsync(m->d_Q, dQ, sizeof(double) * 4 * K * 2 * M, cudaMemcpyDeviceToDevice, m->s));
   SK(cudaGetLastError());
-  // LU of A (FP64, or FP32 with FP64 refinement); W = A^-1 B
+  // LU of A (FP64, or FP32 with FP64 refinement) or the fast direct solver; W = A^-1 B
   double *work = nullptr;
   float *lu32f = nullptr;
   int64_t *piv64 = nullptr;
-  if (lu32) {
+  if (fds) {
+    SK(cudaStreamSynchronize(m->s));
+    const int st = stokes::fds_build(&m->fds, n_per_wall, nodes, weights, normals, curvature,
+                                     period, m->fds_p, m->s, m->blas, m->sol, m->err);
+    if (st) {
+      for (double *p : {dQ, dw, dn, dk}) cudaFree(p);
+      return st;
+    }
+  } else if (lu32) {
     const size_t nn = size_t(nA) * nA;
     SK(dalloc(lu32f, nn));
     SK(dalloc(piv64, nA));
@@ -1456,7 +1481,7 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
     SK(dalloc(work, lwork));
     QK(cusolverDnDgetrf(m->sol, nA, nA, m->d_LU, nA, work, m->d_piv, m->d_info));
   }
-  {
+  if (!fds) {
     int finfo = 0;
     SK(cudaMemcpyAsync(&finfo, m->d_info, sizeof(int), cudaMemcpyDeviceToHost, m->s));
     SK(cudaStreamSynchronize(m->s));
@@ -1518,6 +1543,9 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(dalloc(m->d_dc, 2 * M));
   if (info != 0) return fail(m, STOKES_ERR_CUDA, "SVD of the Schur complement did not converge (%d)", info);
   m->have_walls = true;
+  SK(cudaStreamSynchronize(m->s));
+  m->walls_setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_setup).count();
   return STOKES_OK;
 }
 
@@ -1628,9 +1656,49 @@ int stokes_sim_channel_response(stokes_sim *m, const double *f, double p_drive, 
 
 int stokes_sim_set_wall_solver(stokes_sim *m, int mode) {
   if (!m) return STOKES_ERR_ARG;
-  if (mode != STOKES_WALLS_LU64 && mode != STOKES_WALLS_LU32_REFINE)
+  if (mode != STOKES_WALLS_LU64 && mode != STOKES_WALLS_LU32_REFINE && mode != STOKES_WALLS_FDS)
     return fail(m, STOKES_ERR_ARG, "unknown wall solver %d", mode);
   m->wall_solver = mode;
+  return STOKES_OK;
+}
+
+int stokes_sim_wall_solve(stokes_sim *m, double *X, int nrhs) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!X || nrhs < 1) return fail(m, STOKES_ERR_ARG, "need a device X and nrhs >= 1");
+  if (!m->have_walls) return fail(m, STOKES_ERR_NO_GEOM, "no walls set");
+  SK(cudaSetDevice(m->device));
+  ST(wall_solve(m, X, nrhs));
+  SK(cudaStreamSynchronize(m->s));
+  return STOKES_OK;
+}
+
+int stokes_sim_set_fds_params(stokes_sim *m, double tol, int leaf_nodes, int n_proxy) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!(tol >= 1e-15 && tol <= 1e-3) || leaf_nodes < 8 || leaf_nodes > 512 || n_proxy < 16 ||
+      n_proxy > 512)
+    return fail(m, STOKES_ERR_ARG,
+                "need tol in [1e-15, 1e-3], leaf_nodes in [8, 512], n_proxy in [16, 512]");
+  m->fds_p.tol = tol;
+  m->fds_p.leaf = leaf_nodes;
+  m->fds_p.n_proxy = n_proxy;
+  return STOKES_OK;
+}
+
+int stokes_sim_fds_info(const stokes_sim *m, stokes_fds_info *out) {
+  if (!m || !out) return STOKES_ERR_ARG;
+  *out = stokes_fds_info{};
+  out->walls_setup_ms = m->walls_setup_ms;
+  if (!m->fds) return STOKES_OK;
+  stokes::fds_info f;
+  stokes::fds_get_info(m->fds, &f);
+  out->levels = f.levels;
+  out->max_rank = f.max_rank;
+  out->root_size = f.root_size;
+  out->neighbour_rank = f.neighbour_rank;
+  out->sections = f.sections;
+  out->host_ms = f.host_ms;
+  out->device_ms = f.device_ms;
+  out->device_bytes = double(f.device_bytes);
   return STOKES_OK;
 }
 

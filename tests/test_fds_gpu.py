@@ -1,0 +1,199 @@
+"""GPU fast direct solver for the walls (Sec. 4: HBS inverse of A_0, low-rank neighbour factors,
+Sherman-Morrison-Woodbury) against the oracle's dense wall operator and the dense solvers."""
+import math
+import warnings
+
+import numpy as np
+import pytest
+
+from paper_1510_05616_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+warnings.filterwarnings("ignore", category=RuntimeWarning)
+D = 2 * math.pi
+MU = 0.7
+PTS = np.array([[0.8, 0.0], [3.2, 0.0], [4.8, 0.0], [2.0, 0.5], [5.0, -0.4]])
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_05616_gb300 import build
+    build.build()
+    import paper_1510_05616_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def S():
+    from oracle import sim_oracle
+    return sim_oracle
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def walls_sim(P, walls, mode, K=24, M=96, refine=3, fds=None):
+    lo, up = walls
+    h = P.stokes_sim_create(0)
+    P.stokes_sim_set_wall_solver(h, mode)
+    P.stokes_sim_set_block_refinement(h, refine)
+    if fds is not None:
+        P.stokes_sim_set_fds_params(h, *fds)
+    P.stokes_sim_set_walls(h, lo.n, np.vstack([lo.nodes, up.nodes]),
+                           np.concatenate([lo.weights, up.weights]),
+                           np.vstack([lo.normals, up.normals]),
+                           np.concatenate([lo.curvature, up.curvature]), D, MU, K, M)
+    return h
+
+
+def rhs(n_unknowns, nrhs, seed):
+    """Smooth plus rough right-hand sides (rows = right-hand sides)."""
+    rng = np.random.default_rng(seed)
+    b = rng.normal(size=(nrhs, n_unknowns))
+    t = np.linspace(0, 2 * np.pi, n_unknowns, endpoint=False)
+    b[0] = np.cos(3 * t) + 0.5 * np.sin(7 * t)
+    return b
+
+
+@pytest.mark.parametrize("n_w,shape", [(96, I.WALL_SHAPE_SMALL), (512, I.WALL_SHAPE_LARGE),
+                                       (1000, I.WALL_SHAPE_LARGE)])
+def test_fds_solve_residual_against_oracle_operator(P, S, n_w, shape):
+    """x = FDS(b) solves the oracle's dense A x = b (Nystrom -I/2 + D^near with three images
+    and the curvature diagonal) to within 1e3 times the decompositions' tolerance (1e-12 per box,
+    compounded over the tree's levels), and equals the FP64-LU solution as closely; covers one-level trees, power-of-two walls and ragged (non-power-of-two) walls."""
+    lo, up = I.wall_curves(n_w, shape)
+    A = S.Walls(lo, up, D, MU).A()
+    b = rhs(A.shape[0], 3, n_w)
+    xs = {}
+    for mode in (P.STOKES_WALLS_FDS, P.STOKES_WALLS_LU64):
+        h = walls_sim(P, (lo, up), mode)
+        X = dev(b)
+        P.stokes_sim_wall_solve(h, X)
+        xs[mode] = X.cpu().numpy()
+        P.stokes_sim_destroy(h)
+    x = xs[P.STOKES_WALLS_FDS]
+    res = np.abs(x @ A.T - b).max(1) / np.abs(b).max(1)
+    assert res.max() < 1e-9, res
+    ref = xs[P.STOKES_WALLS_LU64]
+    assert np.abs(x - ref).max() / np.abs(ref).max() < 1e-9
+
+
+def test_fds_info_and_tolerance(P, S):
+    """The reported tree matches the wall size, ranks stay far below the box sizes, and a looser
+    tolerance gives smaller ranks and a proportionally larger (still bounded) residual.  (At this
+    size the solver's 256-column workspace outweighs the dense matrix; the footprint is checked
+    at the paper's channel.)"""
+    lo, up = I.wall_curves(512, I.WALL_SHAPE_LARGE)
+    A = S.Walls(lo, up, D, MU).A()
+    b = rhs(A.shape[0], 1, 5)
+    out = {}
+    for tol in (1e-12, 1e-7):
+        h = walls_sim(P, (lo, up), P.STOKES_WALLS_FDS, fds=(tol, 64, 64))
+        info = P.stokes_sim_fds_info(h)
+        X = dev(b)
+        P.stokes_sim_wall_solve(h, X)
+        refs, res = P.stokes_sim_wall_stats(h)
+        assert (refs, res) == (0, -1.0)
+        out[tol] = (info, np.abs(X.cpu().numpy() @ A.T - b).max() / np.abs(b).max())
+        P.stokes_sim_destroy(h)
+    info, r12 = out[1e-12]
+    # root = both walls, level 1 = the walls (512 nodes), then 256, 128, 64-node leaves
+    assert info["levels"] == 4
+    assert 10 < info["max_rank"] < 2 * 256
+    # each wall, each neighbour: sections of 256, 128, 64, 32, 32 nodes
+    assert info["sections"] == 20
+    assert 0 < info["neighbour_rank"] < 4 * 512
+    assert info["walls_setup_ms"] > 0 and info["host_ms"] > 0
+    info7, r7 = out[1e-7]
+    assert info7["max_rank"] < info["max_rank"]
+    assert info7["neighbour_rank"] < info["neighbour_rank"]
+    assert r12 < 1e-9 and 1e-12 < r7 < 1e-4, (r12, r7)
+
+
+def test_fds_param_validation(P):
+    h = P.stokes_sim_create(0)
+    try:
+        for args in ((0.0, 64, 64), (1e-12, 4, 64), (1e-12, 64, 8), (1e-2, 64, 64)):
+            with pytest.raises(P.StokesError):
+                P.stokes_sim_set_fds_params(h, *args)
+        with pytest.raises(P.StokesError):  # no walls yet
+            P.stokes_sim_wall_solve(h, dev(np.zeros(8)))
+    finally:
+        P.stokes_sim_destroy(h)
+
+
+def test_fds_channel_response_matches_oracle_and_lu(P, S):
+    """The channel response and the empty-channel flow with the fast direct solver equal the
+    dense FP32-LU solver's to round-off (both refine the block solve on the whole extended
+    system) and the oracle's refined solve."""
+    import torch
+    g = I.channel(512, I.WALL_SHAPE_LARGE, 6, 32, 0.01, 11)
+    walls = [c for c in g.curves if c.kind == I.KIND_DLP]
+    ves = [c for c in g.curves if c.kind == I.KIND_SLP]
+    rng = np.random.default_rng(12)
+    f = rng.normal(size=(sum(c.n for c in ves), 2))
+    xv = np.vstack([c.nodes for c in ves])
+    outs = {}
+    for mode in (P.STOKES_WALLS_FDS, P.STOKES_WALLS_LU32_REFINE):
+        h = walls_sim(P, walls, mode)
+        P.stokes_sim_set_vesicles(h, len(ves), ves[0].n, xv, 1.0, MU, D)
+        out = torch.zeros_like(dev(f))
+        P.stokes_sim_channel_response(h, dev(f), 0.8, out)
+        pts = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
+        P.stokes_sim_empty_channel(h, 0.8, None, dev(PTS), pts)
+        outs[mode] = (out.cpu().numpy(), pts.cpu().numpy())
+        P.stokes_sim_destroy(h)
+    for a, b in zip(outs[P.STOKES_WALLS_FDS], outs[P.STOKES_WALLS_LU32_REFINE]):
+        assert np.abs(a - b).max() / np.abs(b).max() < 1e-11
+    W = S.Walls(walls[0], walls[1], D, MU, K=24, M=96)
+    wv = np.concatenate([S.curve_normals_weights(c.nodes)[1] for c in ves])
+    v, gg = S.vesicle_rhs(W, xv, wv, f, 0.8)
+    tau, c = W.solve_refined(v, gg)
+    ref = W.velocity(tau, c, xv)
+    u = outs[P.STOKES_WALLS_FDS][0]
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("refine,tol", [(3, 1e-12), (0, 5e-6)])
+def test_fds_poiseuille(P, refine, tol):
+    """Exact Poiseuille flow from the empty channel: to round-off with the block refinement,
+    at the pseudo-inverse's truncation level without it."""
+    import torch
+    lo, up = I.wall_curves(256, I.WALL_SHAPE_SMALL)
+    pd = 2 * MU * D * 0.2
+    ue = lambda p: np.stack([-(pd / (2 * MU * D)) * p[:, 1] ** 2, 0 * p[:, 1]], 1)
+    xw = np.vstack([lo.nodes, up.nodes])
+    h = walls_sim(P, (lo, up), P.STOKES_WALLS_FDS, K=32, M=128, refine=refine)
+    out = torch.zeros((len(PTS), 2), dtype=torch.float64, device="cuda")
+    P.stokes_sim_empty_channel(h, pd, dev(ue(xw)), dev(PTS), out)
+    P.stokes_sim_destroy(h)
+    assert np.abs(out.cpu().numpy() - ue(PTS)).max() / np.abs(ue(xw)).max() < tol
+
+
+def test_fds_paper_channel(P):
+    """At the paper's channel (2 x 16,384 wall nodes, y = +-(1 + 0.4 sin x + 0.15 sin 3x)) the
+    solver builds in seconds with a small footprint, and its solutions satisfy A x = b with A
+    applied independently by the FP64 double-layer pair sum (-I/2 jump, curvature diagonal)."""
+    import torch
+    n_w = 16384
+    lo, up = I.wall_curves(n_w, I.WALL_SHAPE_LARGE)
+    h = walls_sim(P, (lo, up), P.STOKES_WALLS_FDS, K=32, M=128)
+    info = P.stokes_sim_fds_info(h)
+    b = rhs(4 * n_w, 2, 21)
+    X = dev(b)
+    P.stokes_sim_wall_solve(h, X)
+    P.stokes_sim_destroy(h)
+    assert info["levels"] == 9 and info["max_rank"] < 200, info
+    assert info["device_bytes"] < 4e9, info                 # dense FP64 A alone: 34 GB
+    geom = I.Geometry([lo, up], D, MU, {})
+    s = P.StokesSum(geom)
+    for k in range(2):
+        Ax = s.eval(None, X[k].view(-1, 2).contiguous(), precision="fp64", jump=-0.5)
+        r = (Ax.reshape(-1) - dev(b[k])).abs().max().item() / np.abs(b[k]).max()
+        assert r < 1e-9, (k, r)
+    s.close()
