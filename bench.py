@@ -479,6 +479,111 @@ def run_poiseuille(args):
     return 0
 
 
+def run_walls(args):
+    """Wall solvers at a channel's walls (default: the paper's, 2 x 16,384 nodes): the fast
+    direct solver of Sec. 4 (HBS inverse of A_0, low-rank neighbour factors, SMW) against the
+    dense FP32-LU inverse with FP64 refinement.  Set-up wall clock and device memory, median
+    time of one solve (one right-hand side) and of 256 right-hand sides, and the relative
+    residual max|A x - b| / max|b| with A applied by the FP64 double-layer pair sum.  The
+    one-right-hand-side solves of the fast solver run between cudaProfilerStart/Stop, so a
+    profiler started with --profile-from-start off sees only them."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    B.build()
+    mu, d = 0.7, 2 * math.pi
+    n_w = args.walls_nodes
+    lo, up = I.wall_curves(n_w, I.WALL_SHAPE_LARGE)
+    xw = np.vstack([lo.nodes, up.nodes])
+    rng = np.random.default_rng(0)
+    b = torch.as_tensor(rng.normal(size=(4, 4 * n_w)), device="cuda")
+    peaks, peak_kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    modes = {"fds": P.STOKES_WALLS_FDS, "lu32_refine": P.STOKES_WALLS_LU32_REFINE}
+    res = {}
+    sols = {}
+    # warm-up: a small channel with each solver (library loading, first cuBLAS/cuSOLVER calls)
+    wl, wu = I.wall_curves(256, I.WALL_SHAPE_LARGE)
+    for name in args.walls_solvers.split(","):
+        h = P.stokes_sim_create(0)
+        P.stokes_sim_set_wall_solver(h, modes[name])
+        P.stokes_sim_set_walls(h, 256, np.vstack([wl.nodes, wu.nodes]),
+                               np.concatenate([wl.weights, wu.weights]),
+                               np.vstack([wl.normals, wu.normals]),
+                               np.concatenate([wl.curvature, wu.curvature]), d, mu, 32, 128)
+        P.stokes_sim_destroy(h)
+    for name in args.walls_solvers.split(","):
+        h = P.stokes_sim_create(0)
+        P.stokes_sim_set_wall_solver(h, modes[name])
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        P.stokes_sim_set_walls(h, n_w, xw, np.concatenate([lo.weights, up.weights]),
+                               np.vstack([lo.normals, up.normals]),
+                               np.concatenate([lo.curvature, up.curvature]), d, mu, 32, 128)
+        setup = time.perf_counter() - t0
+        mem = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
+        info = P.stokes_sim_fds_info(h)
+        X = b[0].clone()
+        for _ in range(max(args.warmup, 3)):
+            X.copy_(b[0])
+            P.stokes_sim_wall_solve(h, X)
+        ts = []
+        if name == "fds":
+            torch.cuda.profiler.start()
+        for _ in range(max(args.steps, 5)):
+            X.copy_(b[0])
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            P.stokes_sim_wall_solve(h, X)  # synchronous
+            ts.append(time.perf_counter() - t)
+        if name == "fds":
+            torch.cuda.profiler.stop()
+        one_ms = 1e3 * statistics.median(ts)
+        Xs = b.clone()
+        P.stokes_sim_wall_solve(h, Xs)
+        Xm = torch.as_tensor(rng.normal(size=(256, 4 * n_w)), device="cuda")
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        P.stokes_sim_wall_solve(h, Xm)
+        many_ms = 1e3 * (time.perf_counter() - t)
+        del Xm
+        P.stokes_sim_destroy(h)
+        torch.cuda.empty_cache()
+        sols[name] = Xs
+        r = {"setup_s": setup, "device_gb": mem, "solve_ms": one_ms, "solve_256_ms": many_ms}
+        if name == "fds":
+            r["fds"] = {k: info[k] for k in ("levels", "max_rank", "root_size", "neighbour_rank",
+                                             "sections", "host_ms", "device_ms", "device_bytes",
+                                             "solve_bytes")}
+            gbs = info["solve_bytes"] / (one_ms * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                             "frac": gbs / hbm, "basis": "matrices read once per solve / "
+                             "wall-clock of the synchronous call, of %s copy peak" % peak_kind}
+        res[name] = r
+    # residuals through the FP64 double-layer pair sum (an independent application of A)
+    geom = I.Geometry([lo, up], d, mu, {})
+    s = P.StokesSum(geom)
+    for name, Xs in sols.items():
+        rr = []
+        for k in range(Xs.shape[0]):
+            Ax = s.eval(None, Xs[k].view(-1, 2).contiguous(), precision="fp64", jump=-0.5)
+            rr.append((Ax.reshape(-1) - b[k]).abs().max().item() / b[k].abs().max().item())
+        res[name]["residual_max"] = max(rr)
+    s.close()
+    if len(sols) == 2:
+        a, c = sols["fds"], sols["lu32_refine"]
+        res["fds_vs_lu32_max_rel"] = ((a - c).abs().max() / c.abs().max()).item()
+    line = {"metric": "channel wall solve: fast direct solver (Sec. 4) vs dense LU32 + FP64 refinement",
+            "unit": "ms / s / GB", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "walls y=+-(1+0.4 sin x+0.15 sin 3x), 2 x %d nodes, period 2pi, "
+                                   "mu 0.7, K=32, M=128" % n_w, "unknowns": 4 * n_w},
+            "solvers": res}
+    print(json.dumps(line))
+    return 0
+
+
 def run_scaling(args):
     """The FP32-Kahan node sum (autotuned shape) at N = 1,280 / 16,384 / 128,768 / 524,288:
     throughput, pair-kernel fraction of the FP32 FMA peak and the error against the FP64
@@ -549,6 +654,10 @@ def main():
                     help="time the 64-channel batched ensemble instead (separate JSON line)")
     ap.add_argument("--scaling", action="store_true",
                     help="FP32-Kahan sum from N = 1,280 to N = 524,288 (throughput, roofline, error)")
+    ap.add_argument("--walls", action="store_true",
+                    help="wall solvers: fast direct solver vs dense LU32 at a channel's walls")
+    ap.add_argument("--walls-nodes", type=int, default=16384)
+    ap.add_argument("--walls-solvers", default="fds,lu32_refine")
     ap.add_argument("--poiseuille", action="store_true",
                     help="accuracy study of the pressure-driven channel (velocity and pressure)")
     ap.add_argument("--step", action="store_true",
@@ -574,6 +683,8 @@ def main():
         return run_step(args)
     if args.poiseuille:
         return run_poiseuille(args)
+    if args.walls:
+        return run_walls(args)
     if args.scaling:
         return run_scaling(args)
 

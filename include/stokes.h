@@ -374,7 +374,7 @@ STOKES_API int stokes_tune_clear(void);
  * of radius R_p about (d/2, 0).
  *
  * Wall solver (stokes_sim_set_wall_solver, read at the next stokes_sim_set_walls):
- *   STOKES_WALLS_LU32_REFINE (default): A is kept in FP64; an FP32 copy is LU-factored
+ *   STOKES_WALLS_LU32_REFINE: A is kept in FP64; an FP32 copy is LU-factored
  *     (partial pivoting) and inverted once (A32^-1); every solve A x = b starts from x = 0,
  *     r = b and repeats x += A32^-1 r (FP32), r = b - A x (FP64) until ||r|| <= 1e-14 ||b||,
  *     the residual stops shrinking, or 12 sweeps.  A = -I/2 + D is of the second kind and well
@@ -382,7 +382,7 @@ STOKES_API int stokes_tune_clear(void);
  *     Storage 12 (4 N_w)^2 bytes (16 during set-up); the FP32 factorization is far faster
  *     than the FP64 one on this hardware, and a sweep streams the two matrices once.
  *   STOKES_WALLS_LU64: FP64 LU (8 (4 N_w)^2 bytes), one triangular solve per solve.
- *   STOKES_WALLS_FDS: the fast direct solver of Sec. 4.  A = A_0 + A_{-1} + A_{+1}
+ *   STOKES_WALLS_FDS (default): the fast direct solver of Sec. 4.  A = A_0 + A_{-1} + A_{+1}
  *     (Eq. (formA)); A_0 (the cell's own walls) in HBS form by recursive skeletonisation
  *     (interpolative decompositions against proxy circles, per-box inverses by
  *     Eqs. (def_muhD)-(def_muG)); A_{-1}, A_{+1} = L R from dyadic sections toward each
@@ -430,8 +430,8 @@ typedef struct stokes_sim stokes_sim;
 
 typedef enum {
     STOKES_WALLS_LU64 = 0,         /* FP64 LU of the wall operator                          */
-    STOKES_WALLS_LU32_REFINE = 1,  /* FP32 LU + FP64 iterative refinement (default)         */
-    STOKES_WALLS_FDS = 2           /* HBS + low-rank neighbours + SMW (Sec. 4)              */
+    STOKES_WALLS_LU32_REFINE = 1,  /* FP32 LU + FP64 iterative refinement                   */
+    STOKES_WALLS_FDS = 2           /* HBS + low-rank neighbours + SMW (Sec. 4), the default */
 } stokes_wall_solver;
 
 /* The fast direct solver after stokes_sim_set_walls (zeros, but walls_setup_ms, for the LU
@@ -445,6 +445,7 @@ typedef struct {
     double host_ms;         /* compression and per-box inverses on host threads                */
     double device_ms;       /* uploads, R, Z = A_0^-1 L and (I + R Z)^-1 on the device          */
     double device_bytes;    /* device memory the solver holds                                  */
+    double solve_bytes;     /* matrices a one-right-hand-side solve reads: HBS tables, R, Z, K^-1 */
     double walls_setup_ms;  /* the whole stokes_sim_set_walls call, any solver                 */
 } stokes_fds_info;
 typedef struct stokes_mlp stokes_mlp;

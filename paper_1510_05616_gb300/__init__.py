@@ -491,8 +491,8 @@ def stokes_sum_eval_traction(h, slp_density, dlp_density, targets, target_normal
 
 
 def stokes_sim_set_wall_solver(h, mode):
-    """STOKES_WALLS_LU32_REFINE (default), STOKES_WALLS_LU64 or STOKES_WALLS_FDS (the fast
-    direct solver); read at the next set_walls."""
+    """STOKES_WALLS_FDS (the fast direct solver, default), STOKES_WALLS_LU32_REFINE or
+    STOKES_WALLS_LU64; read at the next set_walls."""
     return _sim_check(h, load().stokes_sim_set_wall_solver(h, int(mode)))
 
 
@@ -500,7 +500,7 @@ class FdsInfo(ctypes.Structure):
     _fields_ = [("levels", _c_int), ("max_rank", _c_int), ("root_size", _c_int),
                 ("neighbour_rank", _c_int), ("sections", _c_int), ("host_ms", _c_double),
                 ("device_ms", _c_double), ("device_bytes", _c_double),
-                ("walls_setup_ms", _c_double)]
+                ("solve_bytes", _c_double), ("walls_setup_ms", _c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -47,6 +47,7 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kHbsThreads = 256;
 constexpr int kHbsCols = 8;       // right-hand sides per CTA of a level pass
+constexpr int kRowTile = 32;      // output rows per CTA of a level pass
 constexpr int kChunk = 256;       // right-hand sides per pass through the tree
 
 // ---------------------------------------------------------------------------
@@ -324,32 +325,72 @@ struct HbsBox {
 // mode 0 (upward):   y[out_off + r] = sum_j F^*[r + j k] x1[in_off + j],   r < k
 // mode 1 (downward): y[in_off + r]  = sum_j E[r + j n] x1[out_off + j]
 //                                   + sum_j G[r + j n] x2[in_off + j],     r < n
-// over the right-hand sides [blockIdx.y * kHbsCols, ...) of column-major x1, x2, y.
+// for the right-hand sides [blockIdx.z NC, ...) of column-major x1, x2, y.  E and G are stored
+// back to back, so both modes are one column-major product y = M v with v the box's inputs,
+// staged in shared memory.  A CTA takes the rows [blockIdx.y kRowTile, ...) of its box: each
+// row is split over kHbsThreads / kRowTile threads that sum strided shares of the columns (two
+// accumulators each, NC right-hand sides at once, so every matrix element is read once per
+// CTA), reduced in shared memory.  A warp reads kRowTile consecutive doubles of one column.
+// Dynamic shared memory: (NC max_cols + kHbsThreads NC) doubles.
+template <int NC>
 __global__ void __launch_bounds__(kHbsThreads)
     hbs_level_kernel(const HbsBox *boxes, const double *mats, int mode, int ncol, const double *x1,
                      long long ld1, const double *x2, long long ld2, double *y, long long ldy) {
+  extern __shared__ double sh[];
   const HbsBox b = boxes[blockIdx.x];
-  const int c0 = blockIdx.y * kHbsCols;
-  const int nc = min(kHbsCols, ncol - c0);
-  const int rows = mode == 0 ? b.k : b.n;
-  for (int idx = threadIdx.x; idx < rows * nc; idx += blockDim.x) {
-    const int r = idx % rows;
-    const long long c = c0 + idx / rows;
-    double s = 0.0;
-    if (mode == 0) {
-      const double *M = mats + b.ft + r;
-      const double *x = x1 + c * ld1 + b.in_off;
-      for (int j = 0; j < b.n; ++j) s = fma(M[size_t(j) * b.k], x[j], s);
-      y[c * ldy + b.out_off + r] = s;
-    } else {
-      const double *M = mats + b.e + r;
-      const double *x = x1 + c * ld1 + b.out_off;
-      for (int j = 0; j < b.k; ++j) s = fma(M[size_t(j) * b.n], x[j], s);
-      const double *Gm = mats + b.g + r;
-      const double *z = x2 + c * ld2 + b.in_off;
-      for (int j = 0; j < b.n; ++j) s = fma(Gm[size_t(j) * b.n], z[j], s);
-      y[c * ldy + b.in_off + r] = s;
+  const int R = mode == 0 ? b.k : b.n;
+  const int r0 = blockIdx.y * kRowTile;
+  if (r0 >= R) return;  // uniform over the CTA
+  const int c0 = blockIdx.z * NC;
+  const int nc = min(NC, ncol - c0);
+  const int C = mode == 0 ? b.n : b.k + b.n;
+  const int C1 = mode == 0 ? b.n : b.k;
+  const long long o1 = mode == 0 ? b.in_off : b.out_off;
+  const long long oy = mode == 0 ? b.out_off : b.in_off;
+  const double *M = mats + (mode == 0 ? b.ft : b.e);
+  double *v = sh;            // [NC][C]
+  double *part = sh + NC * C;  // [T][NC]
+  for (int idx = threadIdx.x; idx < NC * C; idx += blockDim.x) {
+    const int c = idx / C, j = idx - (idx / C) * C;
+    double val = 0.0;
+    if (c < nc)
+      val = j < C1 ? x1[(c0 + c) * ld1 + o1 + j] : x2[(c0 + c) * ld2 + b.in_off + (j - C1)];
+    v[idx] = val;
+  }
+  __syncthreads();
+  constexpr int split = kHbsThreads / kRowTile;
+  const int Rt = min(kRowTile, R - r0);
+  const int r = threadIdx.x % kRowTile, q = threadIdx.x / kRowTile;
+  double a0[NC], a1[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) a0[c] = a1[c] = 0.0;
+  if (r < Rt) {
+    const double *Mr = M + r0 + r;
+    int j = q;
+    for (; j + split < C; j += 2 * split) {
+      const double m0 = Mr[size_t(j) * R], m1 = Mr[size_t(j + split) * R];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        a0[c] = fma(m0, v[c * C + j], a0[c]);
+        a1[c] = fma(m1, v[c * C + j + split], a1[c]);
+      }
     }
+    if (j < C) {
+      const double m0 = Mr[size_t(j) * R];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a0[c] = fma(m0, v[c * C + j], a0[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) part[threadIdx.x * NC + c] = a0[c] + a1[c];
+  __syncthreads();
+  if (q == 0 && r < Rt) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a0[c] = part[r * NC + c];
+    for (int p = 1; p < split; ++p)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a0[c] += part[(p * kRowTile + r) * NC + c];
+    for (int c = 0; c < nc; ++c) y[(c0 + c) * ldy + oy + r0 + r] = a0[c];
   }
 }
 
@@ -407,6 +448,8 @@ struct fds_solver {
   // workspace of one pass (kChunk right-hand sides)
   double *d_up = nullptr, *d_down = nullptr, *d_out = nullptr, *d_t = nullptr, *d_s = nullptr;
   size_t up_len = 0;                   // sum of N[0..L-1]
+  int max_cols = 0;                    // widest level product (k + n, or n at the root)
+  std::vector<int> max_k, max_n;       // [L + 1] largest skeleton / active set per level
   fds_info info;
 };
 
@@ -456,11 +499,28 @@ void bounds(const WallGeom &g, Box &bx) {
   }
 }
 
+// One level pass: NC = 1 for a single right-hand side, else kHbsCols per CTA.
+void level(const fds_solver *f, int lev, int mode, int nc, const double *x1, long long ld1,
+           const double *x2, long long ld2, double *y, long long ldy, cudaStream_t s) {
+  const int nb = f->nboxes[lev];
+  const int rows = mode == 0 ? f->max_k[lev] : f->max_n[lev];
+  const int tiles = (rows + kRowTile - 1) / kRowTile;
+  if (nc == 1) {
+    const size_t sm = sizeof(double) * (size_t(f->max_cols) + kHbsThreads);
+    hbs_level_kernel<1><<<dim3(nb, tiles, 1), kHbsThreads, sm, s>>>(
+        f->d_boxes[lev], f->d_mats, mode, nc, x1, ld1, x2, ld2, y, ldy);
+  } else {
+    const size_t sm = sizeof(double) * kHbsCols * (size_t(f->max_cols) + kHbsThreads);
+    hbs_level_kernel<kHbsCols><<<dim3(nb, tiles, (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, sm,
+                                 s>>>(f->d_boxes[lev], f->d_mats, mode, nc, x1, ld1, x2, ld2, y,
+                                      ldy);
+  }
+}
+
 // A_0^-1 X for up to kChunk columns (X column-major with leading dimension nA).
 int hbs_pass(fds_solver *f, const double *X, double *out, int nc, cudaStream_t s,
              std::string &err) {
   const int L = f->L;
-  // upward: level L reads X, level l writes the level-(l-1) vector
   std::vector<double *> up(L + 1), down(L + 1);
   {
     size_t o = 0;
@@ -470,22 +530,15 @@ int hbs_pass(fds_solver *f, const double *X, double *out, int nc, cudaStream_t s
       o += size_t(f->N[lev]);
     }
   }
-  for (int lev = L; lev >= 1; --lev) {
-    const double *x1 = lev == L ? X : up[lev];
-    const long long ld1 = f->N[lev];
-    hbs_level_kernel<<<dim3(f->nboxes[lev], (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
-        f->d_boxes[lev], f->d_mats, 0, nc, x1, ld1, nullptr, 0, up[lev - 1], f->N[lev - 1]);
-  }
+  // upward: level L reads X, level l writes the level-(l-1) vector
+  for (int lev = L; lev >= 1; --lev)
+    level(f, lev, 0, nc, lev == L ? X : up[lev], f->N[lev], nullptr, 0, up[lev - 1], f->N[lev - 1], s);
   // root: u^ = G_root v^
-  hbs_level_kernel<<<dim3(1, (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
-      f->d_boxes[0], f->d_mats, 0, nc, up[0], f->N[0], nullptr, 0, down[0], f->N[0]);
-  for (int lev = 1; lev <= L; ++lev) {
-    const double *v = lev == L ? X : up[lev];
-    double *y = lev == L ? out : down[lev];
-    hbs_level_kernel<<<dim3(f->nboxes[lev], (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, 0, s>>>(
-        f->d_boxes[lev], f->d_mats, 1, nc, down[lev - 1], f->N[lev - 1], v, f->N[lev], y,
-        f->N[lev]);
-  }
+  level(f, 0, 0, nc, up[0], f->N[0], nullptr, 0, down[0], f->N[0], s);
+  // downward: u = E u^ + G v
+  for (int lev = 1; lev <= L; ++lev)
+    level(f, lev, 1, nc, down[lev - 1], f->N[lev - 1], lev == L ? X : up[lev], f->N[lev],
+          lev == L ? out : down[lev], f->N[lev], s);
   FK(cudaGetLastError());
   return STOKES_OK;
 }
@@ -511,6 +564,8 @@ struct HostFactors {
   std::vector<int> Jall, mall;            // neighbour skeleton unknowns and their image m
   std::vector<SecBlock> sb;               // L's blocks
   std::vector<double> svals;
+  int max_cols = 0;                       // widest level product
+  std::vector<int> max_k, max_n;          // [L + 1] per level
   fds_info info;
   WallGeom g;
 };
@@ -739,6 +794,8 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
   hf.N[L] = nA;
   
   hf.tabs.assign(L + 1, {});
+  hf.max_k.assign(L + 1, 0);
+  hf.max_n.assign(L + 1, 0);
   int max_rank = 0;
   for (int lev = L; lev >= 1; --lev) {
     int in_off = 0, out_off = 0;
@@ -758,6 +815,9 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
       in_off += hb.n;
       out_off += hb.k;
       max_rank = std::max(max_rank, hb.k);
+      hf.max_k[lev] = std::max(hf.max_k[lev], hb.k);
+      hf.max_n[lev] = std::max(hf.max_n[lev], hb.n);
+      hf.max_cols = std::max(hf.max_cols, hb.k + hb.n);  // [E | G] is n x (k + n)
     }
     hf.nboxes[lev] = int(lv[lev].size());
     hf.N[lev - 1] = out_off;
@@ -768,6 +828,8 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
     hb.in_off = hb.out_off = 0;
     hb.ft = (long long)hf.mats.size();
     hb.e = hb.g = 0;
+    hf.max_cols = std::max(hf.max_cols, hb.n);
+    hf.max_k[0] = hf.max_n[0] = hb.n;
     hf.mats.insert(hf.mats.end(), Groot.a.begin(), Groot.a.end());
     hf.tabs[0].push_back(hb);
     hf.nboxes[0] = 1;
@@ -816,6 +878,9 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
   f->info = hf.info;
   f->nboxes = hf.nboxes;
   f->N = hf.N;
+  f->max_cols = hf.max_cols;
+  f->max_k = hf.max_k;
+  f->max_n = hf.max_n;
   // ---- device side ----
   size_t &bytes = f->info.device_bytes;
   std::vector<void *> tmp;  // set-up scratch, freed on every exit
@@ -846,6 +911,17 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
     }                                                                    \
   } while (0)
   const auto t2 = std::chrono::steady_clock::now();
+  {
+    const int sm1 = int(sizeof(double) * (size_t(f->max_cols) + kHbsThreads));
+    const int sm8 = int(sizeof(double) * kHbsCols * (size_t(f->max_cols) + kHbsThreads));
+    if (sm8 > 227 * 1024) {
+      err = "fds: a level product is too wide for shared memory (lower leaf_nodes)";
+      return bail(STOKES_ERR_ARG);
+    }
+    FD(cudaFuncSetAttribute(hbs_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+    FD(cudaFuncSetAttribute(hbs_level_kernel<kHbsCols>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm8));
+  }
   FD(dalloc(f->d_mats, hf.mats.size(), bytes));
   FD(cudaMemcpyAsync(f->d_mats, hf.mats.data(), sizeof(double) * hf.mats.size(), cudaMemcpyHostToDevice, s));
   f->d_boxes.assign(L + 1, nullptr);
@@ -932,6 +1008,7 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
 #undef FDQ
   f->info.device_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t2).count();
+  f->info.solve_bytes = sizeof(double) * (hf.mats.size() + 2 * size_t(l) * nA + size_t(l) * l);
   *out = f;
   return STOKES_OK;
 }

@@ -27,6 +27,7 @@ struct fds_info {
   double host_ms = 0.0;    // compression and per-box inverses (host threads)
   double device_ms = 0.0;  // uploads, R, Z = A_0^-1 L, K^-1 (device)
   size_t device_bytes = 0; // device memory held by the solver
+  size_t solve_bytes = 0;  // matrices one single-right-hand-side solve reads (HBS tables, R, Z, K^-1)
 };
 
 // Builds the solver for the walls of one cell: n_w nodes per wall, host arrays in the wall

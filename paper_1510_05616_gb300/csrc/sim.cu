@@ -55,10 +55,10 @@ struct stokes_sim {
   double2 *d_proxy = nullptr;          // [M]
   double *d_LU = nullptr, *d_W = nullptr, *d_C = nullptr, *d_Spinv = nullptr;
   int *d_piv = nullptr, *d_info = nullptr;
-  // wall solver: STOKES_WALLS_LU64 factors A in FP64; STOKES_WALLS_LU32_REFINE inverts an FP32
-  // copy (LU, then the inverse, d_Ainv32) and refines every solve with FP64 residuals of the
-  // FP64 A (d_A)
-  int wall_solver = STOKES_WALLS_LU32_REFINE;
+  // wall solver: STOKES_WALLS_FDS (default) the fast direct solver of Sec. 4;
+  // STOKES_WALLS_LU64 factors A in FP64; STOKES_WALLS_LU32_REFINE inverts an FP32 copy (LU, then
+  // the inverse, d_Ainv32) and refines every solve with FP64 residuals of the FP64 A (d_A)
+  int wall_solver = STOKES_WALLS_FDS;
   cusolverDnParams_t params = nullptr;
   double *d_A = nullptr;
   float *d_Ainv32 = nullptr;
@@ -1699,6 +1699,7 @@ int stokes_sim_fds_info(const stokes_sim *m, stokes_fds_info *out) {
   out->host_ms = f.host_ms;
   out->device_ms = f.device_ms;
   out->device_bytes = double(f.device_bytes);
+  out->solve_bytes = double(f.solve_bytes);
   return STOKES_OK;
 }
 

@@ -17,7 +17,7 @@ from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUES
                stokes_mlp_set_normalization, stokes_mlp_set_params,
                stokes_mlp_train_step, stokes_sim_create, stokes_sim_destroy,
                stokes_sim_get_history, stokes_sim_get_state, stokes_sim_last_features,
-               stokes_sim_set_history, stokes_sim_set_state,
+               stokes_sim_set_history, stokes_sim_set_state, stokes_sim_set_wall_solver,
                stokes_sim_set_vesicles, stokes_sim_set_walls, stokes_sim_sizes,
                vesicle_step_warmstart)
 
@@ -27,11 +27,13 @@ GUESS_NAMES = {"zero": STOKES_GUESS_ZERO, "previous": STOKES_GUESS_PREVIOUS, "ml
 class Simulation:
     """A channel with vesicles (from an inputs.Geometry) on the GPU."""
 
-    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80):
+    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80, wall_solver=None):
         walls = [c for c in geom.curves if c.kind == 0]
         ves = [c for c in geom.curves if c.kind == 1]
         self.h = stokes_sim_create(device)
         self.mu, self.period = geom.mu, geom.period
+        if wall_solver is not None:  # else the library's default (the fast direct solver)
+            stokes_sim_set_wall_solver(self.h, wall_solver)
         if walls:
             lo, up = walls
             stokes_sim_set_walls(self.h, lo.n, np.vstack([lo.nodes, up.nodes]),
