@@ -584,6 +584,79 @@ def run_walls(args):
     return 0
 
 
+def run_fmm(args):
+    """The pair sum at the nodes by the fast multipole method (FP64 expansions, orders 20 and
+    28) against the direct GPU sums, from N = 1,280 to 524,288: evaluation time (median of
+    CUDA-event-timed calls after warm-up), the equivalent pair rate 3 N_t N_s / t, plan time,
+    and the FMM's error against the FP64-accurate double-float direct sum."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    B.build()
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    rows = {}
+    for name in args.fmm_workloads.split(","):
+        g, slp, dlp = I.workload(name)
+        s = P.StokesSum(g)
+        ts, td = dev(slp), dev(dlp)
+        N = g.n_nodes
+        pairs = 3.0 * N * N
+        out = torch.zeros((N, 2), dtype=torch.float64, device="cuda")
+        # the library's calls run on its own stream and end with a sync, so events on the
+        # current stream bracket them completely
+        r = {"N": N, "pairs": pairs}
+        ref = None
+        for prec in ("fp32k", "df") + (("fp64",) if N <= 20000 else ()):
+            ms = timed(lambda: s.eval(ts, td, precision=prec, out=out), 3 if N > 200000 else 5)
+            r["direct_" + prec] = {"ms": ms, "gpair_per_s": pairs / ms / 1e6}
+            if prec == "df":
+                ref = out.cpu().numpy().copy()
+        for order in (20, 28):
+            t0 = time.perf_counter()
+            f = P.stokes_fmm_create(s.h, order, args.fmm_leaf)
+            plan_ms = 1e3 * (time.perf_counter() - t0)
+
+            def call():
+                P.stokes_fmm_eval(f, ts, td, 0.0, out)
+                P.stokes_sync(s.h)
+            if order == 20:  # a profiler started with --profile-from-start off sees these calls
+                torch.cuda.profiler.start()
+            ms = timed(call, 5)
+            if order == 20:
+                torch.cuda.profiler.stop()
+            u = out.cpu().numpy()
+            err = float((np.abs(u - ref).max(0) / np.abs(ref).max(0)).max())
+            info = P.stokes_fmm_get_info(f)
+            P.stokes_fmm_destroy(f)
+            r["fmm_p%d" % order] = {"ms": ms, "equiv_gpair_per_s": pairs / ms / 1e6, "plan_ms": plan_ms,
+                                    "rel_err_vs_df": err, "levels": info["levels"],
+                                    "m2l_pairs": info["m2l_pairs"], "near_pairs": info["near_pairs"]}
+        s.close()
+        rows[name] = r
+    line = {"metric": "node evaluation of the layer-potential sum: FMM (FP64 expansions) vs direct",
+            "unit": "ms per evaluation", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workloads": {k: WORKLOAD_DESCS.get(k, k) for k in rows},
+                       "leaf_size": args.fmm_leaf, "direct_shapes": "default (not autotuned)"},
+            "results": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def run_scaling(args):
     """The FP32-Kahan node sum (autotuned shape) at N = 1,280 / 16,384 / 128,768 / 524,288:
     throughput, pair-kernel fraction of the FP32 FMA peak and the error against the FP64
@@ -654,6 +727,10 @@ def main():
                     help="time the 64-channel batched ensemble instead (separate JSON line)")
     ap.add_argument("--scaling", action="store_true",
                     help="FP32-Kahan sum from N = 1,280 to N = 524,288 (throughput, roofline, error)")
+    ap.add_argument("--fmm", action="store_true",
+                    help="fast multipole node evaluation vs the direct sums, N = 1,280 .. 524,288")
+    ap.add_argument("--fmm-workloads", default="small_n1280,mid_n16k,paper_n128k,large_n512k")
+    ap.add_argument("--fmm-leaf", type=int, default=32)
     ap.add_argument("--walls", action="store_true",
                     help="wall solvers: fast direct solver vs dense LU32 at a channel's walls")
     ap.add_argument("--walls-nodes", type=int, default=16384)
@@ -685,6 +762,8 @@ def main():
         return run_poiseuille(args)
     if args.walls:
         return run_walls(args)
+    if args.fmm:
+        return run_fmm(args)
     if args.scaling:
         return run_scaling(args)
 

@@ -200,6 +200,49 @@ STOKES_API int stokes_sync(stokes_ctx *ctx, void *stream);
  * STOKES_ERR_TIMEOUT (and clears it), and the context stays usable.  For tests. */
 STOKES_API int stokes_check_wait_timeout(stokes_ctx *ctx, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Fast multipole evaluation at the nodes (FP64).  The same discrete sum as stokes_sum_eval
+ * (pair sum over m in {-1, 0, +1} with the own curve skipped at m = 0, Kress self terms, wall
+ * curvature diagonal, jump), with the pair sum by the 2-D FMM in complex variables: the
+ * stokeslet and stresslet are written through the log potentials sum_j c_j log(z - w_j) of six
+ * charge sets (q1, q2, conj(w) q, 2 n.T, nu T, nu T conj(w)) and their first two derivatives,
+ * expanded to `order` terms (multipole to local conversions of Greengard and Rokhlin) on a
+ * forest quadtree of uniform depth over the nodes and their +-d images; the 3 x 3 neighbour
+ * leaves are summed directly.  The truncation error falls like ~0.5^order (about 1e-9
+ * relative at order 20).  This is the O(N) evaluation the paper's method relies on.
+ *
+ * stokes_fmm_create builds the plan (sorted image sources, cells, interaction and near lists)
+ * for `ctx`'s current single-instance geometry on the host (synchronous), with the depth
+ * chosen so that occupied leaves hold at most `leaf_size` sources on average; order in
+ * [4, 30], leaf_size in [4, 4096] (STOKES_ERR_ARG outside; STOKES_ERR_NO_GEOM without a
+ * geometry).  The plan stays valid until ctx's geometry is set again: stokes_fmm_eval then
+ * returns STOKES_ERR_NO_GEOM.  stokes_fmm_eval takes the arguments of stokes_sum_eval (device
+ * densities, out_velocity 2 N doubles, 16-byte aligned) and runs asynchronously on `stream`;
+ * it uses ctx's packing and finishing buffers, so one context runs one evaluation at a time.
+ * The caller owns the plan and destroys it before the context.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct stokes_fmm stokes_fmm;
+
+typedef struct {
+    int order;             /* expansion order p                                             */
+    int levels;            /* depth L of the forest below its roots                          */
+    int sources;           /* image sources (nodes x images)                                 */
+    int source_cells;      /* cells holding sources, all levels                              */
+    int target_cells;      /* cells holding targets, all levels                              */
+    double m2l_pairs;      /* multipole-to-local conversions per evaluation                   */
+    double near_pairs;     /* directly summed target-source pairs per evaluation              */
+    double plan_ms;        /* stokes_fmm_create, wall clock                                   */
+    double device_bytes;   /* device memory the plan holds                                    */
+} stokes_fmm_info;
+
+STOKES_API int stokes_fmm_create(stokes_ctx *ctx, int order, int leaf_size, stokes_fmm **out);
+STOKES_API int stokes_fmm_eval(stokes_fmm *fmm, const double *slp_density,
+                               const double *dlp_density, double jump, double *out_velocity,
+                               void *stream);
+STOKES_API int stokes_fmm_get_info(const stokes_fmm *fmm, stokes_fmm_info *info);
+STOKES_API int stokes_fmm_last_error(const stokes_fmm *fmm, char *buf, size_t len);
+STOKES_API int stokes_fmm_destroy(stokes_fmm *fmm);
+
 /*
  * Phase timing with CUDA events recorded on the call's stream.  With profiling on (on != 0)
  * every stokes_sum_eval / stokes_sum_eval_targets records events around its three phases:

@@ -64,6 +64,11 @@ _SIGNATURES = {
     "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sync": [_vp, _vp],
     "stokes_check_wait_timeout": [_vp, _vp],
+    "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
+    "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
+    "stokes_fmm_get_info": [_vp, _vp],
+    "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "stokes_fmm_destroy": [_vp],
     "stokes_num_nodes": [_vp],
     "stokes_set_launch": [_vp, _c_int, _c_int, _c_int, _c_int],
     "stokes_get_launch": [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
@@ -280,6 +285,56 @@ def stokes_sync(h, stream=None):
 
 def stokes_check_wait_timeout(h, stream=None):
     return _check(h, load().stokes_check_wait_timeout(h, _stream(stream)))
+
+
+class FmmInfo(ctypes.Structure):
+    _fields_ = [("order", _c_int), ("levels", _c_int), ("sources", _c_int),
+                ("source_cells", _c_int), ("target_cells", _c_int), ("m2l_pairs", _c_double),
+                ("near_pairs", _c_double), ("plan_ms", _c_double), ("device_bytes", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def stokes_fmm_create(h, order=24, leaf_size=32):
+    """FMM plan for the context's current geometry (see stokes.h)."""
+    f = _vp()
+    code = load().stokes_fmm_create(h, int(order), int(leaf_size), ctypes.byref(f))
+    if code != STOKES_OK:
+        raise StokesError(code, _err(h))
+    return f
+
+
+def _fmm_err(f) -> str:
+    buf = ctypes.create_string_buffer(512)
+    if f:
+        load().stokes_fmm_last_error(f, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def stokes_fmm_eval(f, slp_density, dlp_density, jump, out_velocity, stream=None):
+    code = load().stokes_fmm_eval(f, _dptr(slp_density, "slp_density", (2,), True),
+                                  _dptr(dlp_density, "dlp_density", (2,), True), float(jump),
+                                  _dptr(out_velocity, "out_velocity", (2,)), _stream(stream))
+    if code != STOKES_OK:
+        raise StokesError(code, _fmm_err(f))
+    return code
+
+
+def stokes_fmm_get_info(f):
+    info = FmmInfo()
+    code = load().stokes_fmm_get_info(f, ctypes.byref(info))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_fmm_get_info")
+    return info.as_dict()
+
+
+def stokes_fmm_last_error(f) -> str:
+    return _fmm_err(f)
+
+
+def stokes_fmm_destroy(f):
+    return load().stokes_fmm_destroy(f)
 
 
 def stokes_num_nodes(h) -> int:

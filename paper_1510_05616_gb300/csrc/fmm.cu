@@ -1,0 +1,1006 @@
+// fmm.cu -- fast multipole evaluation of the near-image layer-potential sum at the nodes (FP64).
+//
+// The same discrete sum as stokes_sum_eval (stokeslet sources on the vesicles, stresslet sources
+// on the walls, images m in {-1, 0, +1}, own curve skipped at m = 0, Kress self terms and the
+// wall curvature diagonal), with the pair sum in O(N) by the classical 2-D FMM in complex
+// variables.  With z = x1 + i x2, r = z - w, a stokeslet source of weight q = w f / (4 pi mu)
+// and a stresslet source of weight T = w tau / pi with normal nu (complex numbers throughout):
+//   stokeslet  -q log|r| + (r . q) r / |r|^2 = -q log|r| + q/2 + (1/2) r conj(q / r)
+//   stresslet  (r . n)(r . T) r / |r|^4 = (1/4) [nu T / r + 2 (n . T) / conj(r)
+//                                                + conj(nu T conj(r) / r^2)]
+// so every target needs, over the sources, the log potentials Phi_c(z) = sum_j c_j log(z - w_j)
+// of six charge sets -- q1, q2 (real parts of the values; q = q1 + i q2), conj(w) q, 2 n . T,
+// nu T, nu T conj(w) -- and their first and second derivatives:
+//   u = -(Re Phi_q1 + i Re Phi_q2) + Q/2 + (1/2) [z conj(Phi'_q1 + i Phi'_q2) - conj(Phi'_wq)]
+//     + (1/4) [Phi'_nuT + conj(Phi'_2nT) + conj(Phi''_nuTw - conj(z) Phi''_nuT)],
+// Q the sum of the stokeslet weights of the sources taken through the expansions.
+// Expansions (scaled by the cell side h): multipole a_0 log(z - c) + sum_k a_k h^k / (z - c)^k,
+// local sum_k b_k ((z - c)/h)^k, with the shift and conversion formulas of Greengard and
+// Rokhlin for the 2-D log kernel.  Tree: a forest of square roots of side S covering the
+// sources (the nodes and their +-d images) and the targets, uniform depth L, Morton keys;
+// interaction lists are the children of the parent's neighbours that are not neighbours; the
+// 3 x 3 neighbour leaves are summed directly (coincident pairs skipped).  Pairs of a vesicle
+// with itself at m = 0 are then removed by a direct pass over each vesicle's own nodes.
+//
+// The plan (sorted sources, cells, lists) is built on the host from the context's geometry and
+// reused by every evaluation until that geometry changes.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "stokes_internal.cuh"
+
+namespace stokes {
+namespace {
+
+constexpr double kPiF = 3.14159265358979323846;
+constexpr int kSets = 6;
+constexpr int kMaxOrder = 30;               // expansion order p <= kMaxOrder
+constexpr int kBin = 2 * kMaxOrder + 2;     // binomials C(n, k), n < kBin
+constexpr int kLeafThreads = 128;
+
+// Binomials in global memory (cached in L1): the threads of a warp read different entries, which
+// the constant cache would serialize.
+__device__ double c_binom[kBin][kBin];
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cinv(double2 a) {
+  const double d = 1.0 / (a.x * a.x + a.y * a.y);
+  return make_double2(a.x * d, -a.y * d);
+}
+// acc += a b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 cpow(double2 a, int n) {  // n >= 0, by squaring
+  double2 r = make_double2(1.0, 0.0);
+  while (n) {
+    if (n & 1) r = cmul(r, a);
+    a = cmul(a, a);
+    n >>= 1;
+  }
+  return r;
+}
+
+// The six charges of one (image) source at w: vesicle value (q1, q2, ., .), wall value
+// (T1, T2, n1, n2).
+__device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, double2 (&c)[kSets]) {
+  // w is taken relative to the forest's centre (as is z in the assembly): the terms
+  // z conj(Phi'_q) and conj(Phi'_wq) cancel to |q|-sized values, so small |z| keeps digits
+  if (!wall) {
+    const double2 q = make_double2(v.x, v.y);
+    c[0] = make_double2(v.x, 0.0);
+    c[1] = make_double2(v.y, 0.0);
+    c[2] = cmul(cconj(w), q);
+    c[3] = c[4] = c[5] = make_double2(0.0, 0.0);
+  } else {
+    const double2 T = make_double2(v.x, v.y), nu = make_double2(v.z, v.w);
+    const double2 nT = cmul(nu, T);
+    c[0] = c[1] = c[2] = make_double2(0.0, 0.0);
+    c[3] = make_double2(2.0 * (v.z * v.x + v.w * v.y), 0.0);
+    c[4] = nT;
+    c[5] = cmul(nT, cconj(w));
+  }
+}
+
+struct FmmDev {
+  int p, n_src, N;
+  int wall_slots;
+  const int2 *src_slot;       // [n_src] (slot, m), sorted by leaf
+  const double2 *src_pos;     // [n_src] image positions, sorted by leaf
+  const double4_32a *val;     // FP64 slot values (packed per call)
+  const double2 *scell_ctr;   // [source cells] centres
+  const int2 *scell_rng;      // leaves: source range; others: child cell range
+  const double2 *tcell_ctr;   // [target cells]
+  const int *tcell_parent;    // [target cells] parent target cell or -1
+  const int *il_off, *il_idx; // interaction lists (source cell indices)
+  const int *nl_off, *nl_idx; // near lists of target leaves (source leaf indices)
+  const int *tgt_node;        // [N] node of each sorted target
+  const int2 *tleaf_rng;      // [target leaves] range of sorted targets
+  const double2 *x;           // [N] node positions
+  double2 *M;                 // [source cells][kSets][p + 1]
+  double2 *Lc;                // [target cells][kSets][p + 1]
+  double2 *out;               // [N] pair sums (node order)
+  int n_roots_src, root_src0; // source cells of level 0: [root_src0, root_src0 + n_roots_src)
+  double2 o;                  // origin of the complex coordinates (the forest's centre)
+  const double2 *tpow;        // [49][p + 1] t^-n of the integer offsets |t_x|, |t_y| <= 3
+  const double2 *tlog;        // [49] log(-t) of the same offsets
+  const int *src_own;         // [n_src] vesicle curve of an m = 0 source, else -1
+  const int *node_curve;      // [N] vesicle curve of a node, else -1
+};
+
+// P2M: one CTA per source leaf; thread (set, k).  Sources are staged 32 at a time with their
+// charges and the powers u^k of their scaled offsets from the centre.
+constexpr int kP2mChunk = 32;
+__global__ void p2m_kernel(FmmDev f, int cell0, double h) {
+  const int cell = cell0 + blockIdx.x;
+  const int2 rg = f.scell_rng[cell];
+  const double2 ctr = f.scell_ctr[cell];
+  const int p = f.p, p1 = p + 1;
+  const int t = threadIdx.x;
+  const int set = t / p1, k = t - set * p1;
+  __shared__ double2 pw[kP2mChunk][kMaxOrder + 1];
+  __shared__ double2 sc[kP2mChunk][kSets];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j0 = rg.x; j0 < rg.y; j0 += kP2mChunk) {
+    const int nj = min(kP2mChunk, rg.y - j0);
+    __syncthreads();
+    if (t < nj) {
+      const int2 sm = f.src_slot[j0 + t];
+      const double2 w = f.src_pos[j0 + t];
+      const double2 u = make_double2((w.x - ctr.x) / h, (w.y - ctr.y) / h);
+      double2 c[kSets];
+      charges(sm.x < f.wall_slots, make_double2(w.x - f.o.x, w.y - f.o.y), f.val[sm.x], c);
+#pragma unroll
+      for (int s = 0; s < kSets; ++s) sc[t][s] = c[s];
+      double2 uk = make_double2(1.0, 0.0);
+      for (int n = 0; n <= p; ++n) {
+        pw[t][n] = uk;
+        uk = cmul(uk, u);
+      }
+    }
+    __syncthreads();
+    if (set < kSets)
+      for (int j = 0; j < nj; ++j) acc = cfma(sc[j][set], pw[j][k], acc);
+  }
+  if (set < kSets) f.M[(size_t(cell) * kSets + set) * p1 + k] = k == 0 ? acc : cscale(acc, -1.0 / k);
+}
+
+// M2M: one CTA per source cell of a level above the leaves; thread (set, q).  The children's
+// coefficients, the powers of their offsets and the binomials are staged in shared memory:
+// a'_q += -a_0 s^q / q + sum_{k <= q} a_k 2^-k s^(q-k) C(q - 1, k - 1), s = (c_child - c) / h.
+__global__ void m2m_kernel(FmmDev f, int cell0) {
+  const int cell = cell0 + blockIdx.x;
+  const int2 ch = f.scell_rng[cell];
+  const double2 ctr = f.scell_ctr[cell];
+  const int p = f.p, p1 = p + 1, np = kSets * p1;
+  const int t = threadIdx.x;
+  const int set = t / p1, q = t - set * p1;
+  const int nch = ch.y - ch.x;  // 1..4
+  __shared__ double2 sa[4][kSets * (kMaxOrder + 1)];
+  __shared__ double2 sp[4][kMaxOrder + 1];
+  __shared__ double bm[kMaxOrder * kMaxOrder];  // C(q - 1, k - 1) 2^-k, row q - 1, k = 1..p
+  for (int i = t; i < p * p; i += blockDim.x) {
+    const int qq = i / p, k = i - qq * p + 1;
+    bm[i] = c_binom[qq][k - 1] * ldexp(1.0, -k);
+  }
+  for (int i = t; i < nch * np; i += blockDim.x) {
+    const int c = i / np, r = i - c * np;
+    sa[c][r] = f.M[size_t(ch.x + c) * np + r];
+  }
+  for (int i = t; i < nch * p1; i += blockDim.x) {
+    const int c = i / p1, n = i - c * p1;
+    const double2 cc = f.scell_ctr[ch.x + c];
+    // the child centre sits a quarter of the parent side away along each axis
+    const double2 d = make_double2(cc.x - ctr.x, cc.y - ctr.y);
+    const double hp = 4.0 * fabs(d.x);
+    sp[c][n] = cpow(make_double2(d.x / hp, d.y / hp), n);
+  }
+  __syncthreads();
+  if (set >= kSets) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int c = 0; c < nch; ++c) {
+    const double2 *a = sa[c] + set * p1;
+    if (q == 0) {
+      acc = cadd(acc, a[0]);
+    } else {
+      double2 v = cscale(cmul(a[0], sp[c][q]), -1.0 / q);
+      const double *B = bm + (q - 1) * p;
+      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(sp[c][q - k], B[k - 1]), v);
+      acc = cadd(acc, v);
+    }
+  }
+  f.M[(size_t(cell) * kSets + set) * p1 + q] = acc;
+}
+
+// L2L from the parent and M2L from the interaction list: one CTA per target cell of one level;
+// thread (set, q).  Per source cell the weights w_k = a_k (-1)^k t^-k (w_0 = a_0) are formed once
+// in shared memory; then b_0 += a_0 log(-t h) + sum_k w_k and
+// b_q += t^-q (sum_k C(q + k - 1, k - 1) w_k - a_0 / q).  Below the roots t is an integer
+// offset with |t_x|, |t_y| <= 3, whose powers and log(-t) come from the plan's table.  Source
+// cells are staged kM2lBatch at a time.
+constexpr int kM2lBatch = 4;
+__global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
+  const int cell = cell0 + blockIdx.x;
+  const double2 ct = f.tcell_ctr[cell];
+  const int p = f.p, p1 = p + 1, np = kSets * p1;
+  const int t = threadIdx.x;
+  const int set = t / p1, q = t - set * p1;
+  __shared__ double2 sw[kM2lBatch][kSets * (kMaxOrder + 1)];
+  __shared__ double2 stq[kM2lBatch][kMaxOrder + 1];
+  __shared__ double2 slog[kM2lBatch];
+  __shared__ double bq[(kMaxOrder + 1) * kMaxOrder];  // C(q + k - 1, k - 1), row q, k = 1..p
+  for (int i = t; i < p1 * p; i += blockDim.x) {
+    const int qq = i / p, k = i - qq * p + 1;
+    bq[i] = c_binom[qq + k - 1][k - 1];
+  }
+  double2 acc = make_double2(0.0, 0.0);
+  const int par = f.tcell_parent[cell];
+  if (par >= 0) {  // L2L: stage the parent's locals and the powers of the offset
+    const double2 cp = f.tcell_ctr[par];
+    const double2 s = make_double2((ct.x - cp.x) / (2.0 * h), (ct.y - cp.y) / (2.0 * h));  // parent side 2h
+    for (int i = t; i < np; i += blockDim.x) sw[0][i] = f.Lc[size_t(par) * np + i];
+    if (t <= p) stq[0][t] = cpow(s, t);
+    __syncthreads();
+    if (set < kSets) {
+      const double2 *b = sw[0] + set * p1;
+      double2 v = make_double2(0.0, 0.0);
+      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(stq[0][k - q], c_binom[k][q]), v);
+      acc = cscale(v, ldexp(1.0, -q));
+    }
+  }
+  const int il0 = f.il_off[cell], ne = f.il_off[cell + 1] - il0;
+  for (int e0 = 0; e0 < ne; e0 += kM2lBatch) {
+    const int nb = min(kM2lBatch, ne - e0);
+    __syncthreads();
+    for (int i = t; i < nb * np; i += blockDim.x) {
+      const int el = i / np, r = i - el * np;
+      const int si = r / p1, qi = r - si * p1;
+      const int sc = f.il_idx[il0 + e0 + el];
+      const double2 cs = f.scell_ctr[sc];
+      const double ox = (cs.x - ct.x) / h, oy = (cs.y - ct.y) / h;
+      const int dx = __double2int_rn(ox), dy = __double2int_rn(oy);
+      const bool tab = abs(dx) <= 3 && abs(dy) <= 3;
+      const int ti = (dy + 3) * 7 + (dx + 3);
+      const double2 T = tab ? f.tpow[ti * p1 + qi] : cpow(cinv(make_double2(ox, oy)), qi);
+      const double2 a = f.M[size_t(sc) * np + r];
+      sw[el][r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
+      if (si == 0) {
+        stq[el][qi] = T;
+        if (qi == 0)
+          slog[el] = tab ? f.tlog[ti] : make_double2(0.5 * log(ox * ox + oy * oy), atan2(-oy, -ox));
+      }
+    }
+    __syncthreads();
+    if (set < kSets) {
+      const double *B = bq + q * p;
+      for (int el = 0; el < nb; ++el) {
+        const double2 *w = sw[el] + set * p1;
+        double vx = 0.0, vy = 0.0;
+        for (int k = 1; k <= p; ++k) {
+          vx = fma(B[k - 1], w[k].x, vx);
+          vy = fma(B[k - 1], w[k].y, vy);
+        }
+        if (q == 0)
+          acc = cadd(acc, cadd(cmul(w[0], make_double2(slog[el].x + log_h, slog[el].y)),
+                               make_double2(vx, vy)));
+        else
+          acc = cfma(make_double2(vx - w[0].x / q, vy - w[0].y / q), stq[el][q], acc);
+      }
+    }
+  }
+  if (set < kSets) f.Lc[(size_t(cell) * kSets + set) * p1 + q] = acc;
+}
+
+// L2P and the near field: one CTA per target leaf, one thread per target (strided).
+__global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0, int leaf0,
+                                                            double h) {
+  const int leaf = blockIdx.x;
+  const int cell = tcell0 + leaf;
+  const double2 ct = f.tcell_ctr[cell];
+  const int p = f.p, p1 = p + 1;
+  __shared__ double2 sb[kSets * (kMaxOrder + 1)];
+  __shared__ double2 qtot;
+  for (int i = threadIdx.x; i < kSets * p1; i += blockDim.x) sb[i] = f.Lc[size_t(cell) * kSets * p1 + i];
+  if (threadIdx.x == 0) {  // stokeslet weight of all sources: the roots' a_0 of q1 and q2
+    double2 s = make_double2(0.0, 0.0);
+    for (int r = 0; r < f.n_roots_src; ++r) {
+      const double2 *a = f.M + size_t(f.root_src0 + r) * kSets * p1;
+      s.x += a[0].x;
+      s.y += a[p1].x;
+    }
+    qtot = s;
+  }
+  __syncthreads();
+  const int2 trg = f.tleaf_rng[leaf];
+  const int nb0 = f.nl_off[leaf0 + leaf], nb1 = f.nl_off[leaf0 + leaf + 1];
+  for (int it = trg.x + threadIdx.x; it < trg.y; it += blockDim.x) {
+    const int node = f.tgt_node[it];
+    const double2 z = f.x[node];
+    const int tcur = f.node_curve[node];
+    const double2 u = make_double2((z.x - ct.x) / h, (z.y - ct.y) / h);
+    // Horner: value, first and second derivative (in u) of every set
+    double2 v[kSets], d1[kSets], d2[kSets];
+#pragma unroll
+    for (int s = 0; s < kSets; ++s) {
+      const double2 *b = sb + s * p1;
+      double2 a0 = b[p], a1 = make_double2(0.0, 0.0), a2 = make_double2(0.0, 0.0);
+      for (int k = p - 1; k >= 0; --k) {
+        a2 = cfma(a2, u, a1);
+        a1 = cfma(a1, u, a0);
+        a0 = cfma(a0, u, b[k]);
+      }
+      v[s] = a0;
+      d1[s] = cscale(a1, 1.0 / h);
+      d2[s] = cscale(a2, 2.0 / (h * h));
+    }
+    // near field, directly (coincident pairs skipped); the near stokeslet weight is kept to
+    // take it out of Q
+    double ux = 0.0, uy = 0.0, qn1 = 0.0, qn2 = 0.0;
+    for (int e = nb0; e < nb1; ++e) {
+      const int2 rg = f.scell_rng[f.nl_idx[e]];
+      for (int j = rg.x; j < rg.y; ++j) {
+        const int2 sm = f.src_slot[j];
+        const double2 w = f.src_pos[j];
+        const double4_32a vv = f.val[sm.x];
+        const bool wall = sm.x < f.wall_slots;
+        if (!wall) {
+          qn1 += vv.x;
+          qn2 += vv.y;
+        }
+        // a vesicle's own nodes at m = 0 are the Kress rule's: skipped (own_curve_kernel takes
+        // those that lie beyond the neighbour leaves out of the far field)
+        const int own = f.src_own[j];
+        if (own >= 0 && own == tcur) continue;
+        const double r1 = z.x - w.x, r2 = z.y - w.y;
+        const double rr = r1 * r1 + r2 * r2;
+        if (rr == 0.0) continue;
+        const double inv = 1.0 / rr;
+        if (!wall) {
+          const double lg = -0.5 * log(rr);
+          const double c = (r1 * vv.x + r2 * vv.y) * inv;
+          ux += lg * vv.x + c * r1;
+          uy += lg * vv.y + c * r2;
+        } else {
+          const double c = (r1 * vv.z + r2 * vv.w) * (r1 * vv.x + r2 * vv.y) * inv * inv;
+          ux += c * r1;
+          uy += c * r2;
+        }
+      }
+    }
+    // far field from the local expansion
+    const double2 dq = make_double2(d1[0].x - d1[1].y, d1[0].y + d1[1].x);  // Phi'_q1 + i Phi'_q2
+    const double2 zo = make_double2(z.x - f.o.x, z.y - f.o.y);
+    double2 s = make_double2(-v[0].x + 0.5 * (qtot.x - qn1), -v[1].x + 0.5 * (qtot.y - qn2));
+    s = cadd(s, cscale(cadd(cmul(zo, cconj(dq)), cscale(cconj(d1[2]), -1.0)), 0.5));
+    const double2 w5 = make_double2(d2[5].x, d2[5].y);
+    const double2 zc_d2 = cmul(cconj(zo), d2[4]);
+    double2 dl = cadd(d1[4], cconj(d1[3]));
+    dl = cadd(dl, cconj(make_double2(w5.x - zc_d2.x, w5.y - zc_d2.y)));
+    s = cadd(s, cscale(dl, 0.25));
+    f.out[node] = make_double2(s.x + ux, s.y + uy);
+  }
+}
+
+// Removes the pairs of every vesicle with itself at m = 0 that reached the far field (the Kress
+// rule carries them; the near field skips them): pairs whose leaves are not neighbours, found
+// with the plan's own binning.  One CTA per vesicle curve, one thread per target node.
+struct Binning {
+  double x0, y0, hmax;
+  int gmaxx, gmaxy, shift;  // level-L leaf = (integer coordinate at depth kLmax) >> shift
+};
+
+__device__ __forceinline__ int2 leaf_of(const Binning &bn, double2 q) {
+  const int gx = min(bn.gmaxx, max(0, int(floor((q.x - bn.x0) / bn.hmax))));
+  const int gy = min(bn.gmaxy, max(0, int(floor((q.y - bn.y0) / bn.hmax))));
+  return make_int2(gx >> bn.shift, gy >> bn.shift);
+}
+
+constexpr int kOwnMax = 256;  // nodes per vesicle (the step and Kress tables allow at most 256)
+__global__ void own_curve_kernel(const int *ves_curve_ids, const CurveDev *curves,
+                                 const double2 *x, const double *w, const int *node_dens,
+                                 const double *slp, double c_slp, Binning bn, double2 *out) {
+  const CurveDev cv = curves[ves_curve_ids[blockIdx.x]];
+  __shared__ int2 sl[kOwnMax];
+  const bool staged = cv.n <= kOwnMax;
+  if (staged)
+    for (int a = threadIdx.x; a < cv.n; a += blockDim.x) sl[a] = leaf_of(bn, x[cv.node_begin + a]);
+  __syncthreads();
+  for (int a = threadIdx.x; a < cv.n; a += blockDim.x) {
+    const int i = cv.node_begin + a;
+    const double2 z = x[i];
+    const int2 li = staged ? sl[a] : leaf_of(bn, z);
+    double ux = 0.0, uy = 0.0;
+    for (int b = 0; b < cv.n; ++b) {
+      if (b == a) continue;
+      const int j = cv.node_begin + b;
+      const int2 lj = staged ? sl[b] : leaf_of(bn, x[j]);
+      if (abs(lj.x - li.x) <= 1 && abs(lj.y - li.y) <= 1) continue;  // near: never added
+      const int row = node_dens[j];
+      const double c = w[j] * c_slp;
+      const double q1 = c * slp[2 * row], q2 = c * slp[2 * row + 1];
+      const double r1 = z.x - x[j].x, r2 = z.y - x[j].y;
+      const double rr = r1 * r1 + r2 * r2;
+      if (rr == 0.0) continue;
+      const double lg = -0.5 * log(rr);
+      const double cc = (r1 * q1 + r2 * q2) / rr;
+      ux += lg * q1 + cc * r1;
+      uy += lg * q2 + cc * r2;
+    }
+    out[i] = make_double2(out[i].x - ux, out[i].y - uy);
+  }
+}
+
+}  // namespace
+}  // namespace stokes
+
+// ---------------------------------------------------------------------------
+// host plan
+// ---------------------------------------------------------------------------
+struct stokes_fmm {
+  stokes_ctx *ctx = nullptr;
+  int p = 20, L = 0, nx = 1, ny = 1, N = 0, n_src = 0;
+  double x0 = 0.0, y0 = 0.0, S = 1.0;
+  std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
+  int n_tleaf = 0;
+  // device
+  int2 *d_src_slot = nullptr;
+  double2 *d_src_pos = nullptr, *d_sc_ctr = nullptr, *d_tc_ctr = nullptr;
+  int2 *d_sc_rng = nullptr, *d_tleaf_rng = nullptr;
+  int *d_tc_par = nullptr, *d_il_off = nullptr, *d_il_idx = nullptr, *d_nl_off = nullptr,
+      *d_nl_idx = nullptr, *d_tgt_node = nullptr;
+  double2 *d_M = nullptr, *d_Lc = nullptr;
+  double2 *d_tpow = nullptr, *d_tlog = nullptr;  // offset table of the conversions below the roots
+  int *d_src_own = nullptr, *d_node_curve = nullptr;
+  // the geometry the plan was made for
+  unsigned long long generation = 0;
+  std::string err;
+  stokes_fmm_info info{};
+};
+
+namespace stokes {
+
+// Geometry generation of every context: bumped whenever its geometry is freed (set again or
+// destroyed), so a plan knows when it no longer applies.
+namespace {
+std::mutex g_gen_mu;
+std::unordered_map<const stokes_ctx *, unsigned long long> g_gen;
+unsigned long long generation_of(const stokes_ctx *c) {
+  std::lock_guard<std::mutex> lk(g_gen_mu);
+  const auto it = g_gen.find(c);
+  return it == g_gen.end() ? 0ull : it->second;
+}
+}  // namespace
+
+void fmm_geometry_changed(const stokes_ctx *c) {
+  std::lock_guard<std::mutex> lk(g_gen_mu);
+  ++g_gen[c];
+}
+
+namespace {
+
+constexpr int kLmax = 20;  // depth of the integer coordinates the keys are cut from
+
+unsigned long long spread2(unsigned v) {  // bit b of v -> bit 2b
+  unsigned long long x = v & 0xFFFFFu;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+unsigned compact2(unsigned long long x) {  // inverse of spread2
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return unsigned(x);
+}
+
+// Key of the level-l cell (gx, gy) (global integer coordinates at level l): root index above
+// the 2l Morton bits of the coordinates within the root.
+unsigned long long encode(int gx, int gy, int l, int nx) {
+  const unsigned long long root = (unsigned long long)(gy >> l) * nx + (gx >> l);
+  const unsigned mask = (1u << l) - 1u;
+  return (root << (2 * l)) | spread2(unsigned(gx) & mask) | (spread2(unsigned(gy) & mask) << 1);
+}
+void decode(unsigned long long key, int l, int nx, int &gx, int &gy) {
+  const unsigned long long root = key >> (2 * l);
+  const unsigned long long m = key & ((1ull << (2 * l)) - 1ull);
+  gx = int((root % nx) << l) | int(compact2(m));
+  gy = int((root / nx) << l) | int(compact2(m >> 1));
+}
+
+int find_key(const std::vector<unsigned long long> &keys, int b, int e, unsigned long long k) {
+  const auto it = std::lower_bound(keys.begin() + b, keys.begin() + e, k);
+  return (it != keys.begin() + e && *it == k) ? int(it - keys.begin()) : -1;
+}
+
+template <class T>
+cudaError_t upload(T *&d, const std::vector<T> &h, size_t &bytes) {
+  bytes += sizeof(T) * std::max<size_t>(h.size(), 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&d), sizeof(T) * std::max<size_t>(h.size(), 1));
+  if (e != cudaSuccess || h.empty()) return e;
+  return cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+void free_plan(stokes_fmm *f) {
+  void *ps[] = {f->d_src_slot, f->d_src_pos, f->d_sc_ctr, f->d_tc_ctr, f->d_sc_rng,
+                f->d_tleaf_rng, f->d_tc_par, f->d_il_off, f->d_il_idx, f->d_nl_off,
+                f->d_nl_idx, f->d_tgt_node, f->d_M, f->d_Lc, f->d_tpow, f->d_tlog, f->d_src_own, f->d_node_curve};
+  for (void *q : ps) cudaFree(q);
+}
+
+// The plan on the host: node positions x, FP64 source slot positions and nodes (-1 = padding),
+// period d.
+struct PlanHost {
+  int L = 0, nx = 1, ny = 1, N = 0, ns = 0, n_tleaf = 0;
+  double x0 = 0.0, y0 = 0.0, S = 1.0;
+  std::vector<int> sc_off, tc_off, tc_par, il_off, il_idx, nl_off, nl_idx, tord;
+  std::vector<int2> src_sorted, sc_rng, tleaf_rng;
+  std::vector<int> src_own;  // vesicle curve of an m = 0 source (sorted order), else -1
+  std::vector<double2> pos_sorted, sc_ctr, tc_ctr;
+  long long near_pairs = 0;
+};
+
+void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
+               const std::vector<int> &snode, const std::vector<int> &node_curve, double d,
+               int leaf_target, PlanHost &ph) {
+  PlanHost *f = &ph;
+  const int N = int(x.size());
+  const int slots = int(spos.size());
+  // image sources
+  const int nimg = d != 0.0 ? 3 : 1;
+  std::vector<int2> src;  // (slot, m)
+  std::vector<double2> pos;
+  for (int m = (nimg == 3 ? -1 : 0); m <= (nimg == 3 ? 1 : 0); ++m)
+    for (int s = 0; s < slots; ++s)
+      if (snode[s] >= 0) {
+        src.push_back(make_int2(s, m));
+        pos.push_back(make_double2(spos[s].x + m * d, spos[s].y));
+      }
+  const int ns = int(src.size());
+  // forest of square roots over sources and targets
+  double xa = 1e300, xb = -1e300, ya = 1e300, yb = -1e300;
+  for (const double2 &q : pos) {
+    xa = std::min(xa, q.x); xb = std::max(xb, q.x); ya = std::min(ya, q.y); yb = std::max(yb, q.y);
+  }
+  for (const double2 &q : x) {
+    xa = std::min(xa, q.x); xb = std::max(xb, q.x); ya = std::min(ya, q.y); yb = std::max(yb, q.y);
+  }
+  const double W = xb - xa, H = yb - ya;
+  double S = std::max({H, W / 64.0, 1e-12 * (1.0 + fabs(xa) + fabs(ya))});
+  S *= 1.0 + 1e-9;
+  f->nx = std::max(1, int(ceil(W / S * (1.0 - 1e-12))));
+  f->ny = std::max(1, int(ceil(H / S * (1.0 - 1e-12))));
+  f->x0 = xa;
+  f->y0 = ya;
+  f->S = S;
+  const int gmaxx = (f->nx << kLmax) - 1, gmaxy = (f->ny << kLmax) - 1;
+  const double hmax = S / double(1 << kLmax);
+  auto gcoord = [&](double2 q, int &gx, int &gy) {
+    gx = std::min(gmaxx, std::max(0, int(floor((q.x - xa) / hmax))));
+    gy = std::min(gmaxy, std::max(0, int(floor((q.y - ya) / hmax))));
+  };
+  std::vector<unsigned long long> skey(ns), tkey(N);
+  for (int j = 0; j < ns; ++j) {
+    int gx, gy;
+    gcoord(pos[j], gx, gy);
+    skey[j] = encode(gx, gy, kLmax, f->nx);
+  }
+  for (int i = 0; i < N; ++i) {
+    int gx, gy;
+    gcoord(x[i], gx, gy);
+    tkey[i] = encode(gx, gy, kLmax, f->nx);
+  }
+  std::vector<int> sord(ns), tord(N);
+  for (int j = 0; j < ns; ++j) sord[j] = j;
+  for (int i = 0; i < N; ++i) tord[i] = i;
+  std::stable_sort(sord.begin(), sord.end(), [&](int a, int b) { return skey[a] < skey[b]; });
+  std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) { return tkey[a] < tkey[b]; });
+  // depth: the shallowest with at most leaf_target sources per occupied leaf
+  int L = 0;
+  for (; L < kLmax; ++L) {
+    const int sh = 2 * (kLmax - L);
+    int occ = 0;
+    for (int j = 0; j < ns; ++j)
+      if (j == 0 || (skey[sord[j]] >> sh) != (skey[sord[j - 1]] >> sh)) ++occ;
+    if (ns <= (long long)leaf_target * occ) break;
+  }
+  f->L = L;
+  const int sh = 2 * (kLmax - L);
+  // source leaves and cells of every level (level 0 first)
+  std::vector<std::vector<unsigned long long>> skeys(L + 1), tkeys(L + 1);
+  std::vector<int> leaf_begin;
+  for (int j = 0; j < ns; ++j) {
+    const unsigned long long k = skey[sord[j]] >> sh;
+    if (skeys[L].empty() || skeys[L].back() != k) {
+      skeys[L].push_back(k);
+      leaf_begin.push_back(j);
+    }
+  }
+  leaf_begin.push_back(ns);
+  for (int l = L - 1; l >= 0; --l)
+    for (unsigned long long k : skeys[l + 1])
+      if (skeys[l].empty() || skeys[l].back() != (k >> 2)) skeys[l].push_back(k >> 2);
+  std::vector<int> tleaf_begin;
+  for (int i = 0; i < N; ++i) {
+    const unsigned long long k = tkey[tord[i]] >> sh;
+    if (tkeys[L].empty() || tkeys[L].back() != k) {
+      tkeys[L].push_back(k);
+      tleaf_begin.push_back(i);
+    }
+  }
+  tleaf_begin.push_back(N);
+  for (int l = L - 1; l >= 0; --l)
+    for (unsigned long long k : tkeys[l + 1])
+      if (tkeys[l].empty() || tkeys[l].back() != (k >> 2)) tkeys[l].push_back(k >> 2);
+  // flatten
+  f->sc_off.assign(L + 2, 0);
+  f->tc_off.assign(L + 2, 0);
+  for (int l = 0; l <= L; ++l) {
+    f->sc_off[l + 1] = f->sc_off[l] + int(skeys[l].size());
+    f->tc_off[l + 1] = f->tc_off[l] + int(tkeys[l].size());
+  }
+  std::vector<unsigned long long> sk_all, tk_all;
+  for (int l = 0; l <= L; ++l) {
+    sk_all.insert(sk_all.end(), skeys[l].begin(), skeys[l].end());
+    tk_all.insert(tk_all.end(), tkeys[l].begin(), tkeys[l].end());
+  }
+  const int nsc = f->sc_off[L + 1], ntc = f->tc_off[L + 1];
+  auto centre = [&](unsigned long long k, int l) {
+    int gx, gy;
+    decode(k, l, f->nx, gx, gy);
+    const double h = S / double(1 << l);
+    return make_double2(xa + (gx + 0.5) * h, ya + (gy + 0.5) * h);
+  };
+  std::vector<double2> sc_ctr(nsc), tc_ctr(ntc);
+  std::vector<int2> sc_rng(nsc);
+  for (int l = 0; l <= L; ++l)
+    for (int i = f->sc_off[l]; i < f->sc_off[l + 1]; ++i) {
+      sc_ctr[i] = centre(sk_all[i], l);
+      if (l == L) {
+        const int li = i - f->sc_off[L];
+        sc_rng[i] = make_int2(leaf_begin[li], leaf_begin[li + 1]);
+      } else {
+        const auto b = std::lower_bound(sk_all.begin() + f->sc_off[l + 1], sk_all.begin() + f->sc_off[l + 2],
+                                        sk_all[i] << 2);
+        const auto e = std::upper_bound(sk_all.begin() + f->sc_off[l + 1], sk_all.begin() + f->sc_off[l + 2],
+                                        (sk_all[i] << 2) | 3ull);
+        sc_rng[i] = make_int2(int(b - sk_all.begin()), int(e - sk_all.begin()));
+      }
+    }
+  std::vector<int> tc_par(ntc, -1), il_off(ntc + 1, 0), il_idx;
+  for (int l = 0; l <= L; ++l) {
+    const int gnx = f->nx << l, gny = f->ny << l;
+    for (int i = f->tc_off[l]; i < f->tc_off[l + 1]; ++i) {
+      tc_ctr[i] = centre(tk_all[i], l);
+      if (l > 0) tc_par[i] = find_key(tk_all, f->tc_off[l - 1], f->tc_off[l], tk_all[i] >> 2);
+      int gx, gy;
+      decode(tk_all[i], l, f->nx, gx, gy);
+      if (l == 0) {
+        for (int sidx = f->sc_off[0]; sidx < f->sc_off[1]; ++sidx) {
+          int sx, sy;
+          decode(sk_all[sidx], 0, f->nx, sx, sy);
+          if (std::max(abs(sx - gx), abs(sy - gy)) >= 2) il_idx.push_back(sidx);
+        }
+      } else {
+        const int px = gx >> 1, py = gy >> 1;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx)
+            for (int ey = 0; ey < 2; ++ey)
+              for (int ex = 0; ex < 2; ++ex) {
+                const int cx = 2 * (px + dx) + ex, cy = 2 * (py + dy) + ey;
+                if (cx < 0 || cy < 0 || cx >= gnx || cy >= gny) continue;
+                if (std::max(abs(cx - gx), abs(cy - gy)) <= 1) continue;
+                const int sidx = find_key(sk_all, f->sc_off[l], f->sc_off[l + 1], encode(cx, cy, l, f->nx));
+                if (sidx >= 0) il_idx.push_back(sidx);
+              }
+      }
+      il_off[i + 1] = int(il_idx.size());
+    }
+  }
+  // near lists and target ranges of the target leaves
+  const int ntl = int(tkeys[L].size());
+  f->n_tleaf = ntl;
+  std::vector<int> nl_off(ntl + 1, 0), nl_idx;
+  std::vector<int2> tleaf_rng(ntl);
+  const int gnx = f->nx << L, gny = f->ny << L;
+  long long near_pairs = 0;
+  for (int t = 0; t < ntl; ++t) {
+    tleaf_rng[t] = make_int2(tleaf_begin[t], tleaf_begin[t + 1]);
+    int gx, gy;
+    decode(tkeys[L][t], L, f->nx, gx, gy);
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int cx = gx + dx, cy = gy + dy;
+        if (cx < 0 || cy < 0 || cx >= gnx || cy >= gny) continue;
+        const int sidx = find_key(sk_all, f->sc_off[L], f->sc_off[L + 1], encode(cx, cy, L, f->nx));
+        if (sidx >= 0) {
+          nl_idx.push_back(sidx);
+          near_pairs += (long long)(tleaf_begin[t + 1] - tleaf_begin[t]) * (sc_rng[sidx].y - sc_rng[sidx].x);
+        }
+      }
+    nl_off[t + 1] = int(nl_idx.size());
+  }
+  std::vector<int2> src_sorted(ns);
+  std::vector<double2> pos_sorted(ns);
+  for (int j = 0; j < ns; ++j) {
+    src_sorted[j] = src[sord[j]];
+    pos_sorted[j] = pos[sord[j]];
+  }
+  f->src_own.resize(ns);
+  for (int j = 0; j < ns; ++j) {
+    const int2 sm = src_sorted[j];
+    f->src_own[j] = sm.y == 0 ? node_curve[snode[sm.x]] : -1;
+  }
+  f->N = N;
+  f->ns = ns;
+  f->tord = tord;
+  f->near_pairs = near_pairs;
+  ph.sc_rng = sc_rng;
+  ph.sc_ctr = sc_ctr;
+  ph.tc_ctr = tc_ctr;
+  ph.tc_par = tc_par;
+  ph.il_off = il_off;
+  ph.il_idx = il_idx;
+  ph.nl_off = nl_off;
+  ph.nl_idx = nl_idx;
+  ph.tleaf_rng = tleaf_rng;
+  ph.src_sorted = src_sorted;
+  ph.pos_sorted = pos_sorted;
+}
+
+int build_plan(stokes_fmm *f, int leaf_target) {
+  stokes_ctx *c = f->ctx;
+  const int N = c->N;
+  const int slots = c->wall_slots_f64 + c->ves_slots_f64;
+  std::vector<double2> x(N), spos(slots);
+  std::vector<int> snode(slots);
+  if (cudaMemcpy(x.data(), c->d_x, sizeof(double2) * N, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(spos.data(), c->d_src_pos64, sizeof(double2) * slots, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(snode.data(), c->d_slot_node64, sizeof(int) * slots, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    f->err = "fmm: reading the geometry failed";
+    return STOKES_ERR_CUDA;
+  }
+  std::vector<int> node_curve(N, -1);
+  for (int cv = 0; cv < c->n_curves; ++cv)
+    if (c->kind[cv] == STOKES_KIND_VESICLE)
+      for (int i = c->off[cv]; i < c->off[cv + 1]; ++i) node_curve[i] = cv;
+  PlanHost ph;
+  plan_host(x, spos, snode, node_curve, c->period, leaf_target, ph);
+  f->L = ph.L;
+  f->nx = ph.nx;
+  f->ny = ph.ny;
+  f->x0 = ph.x0;
+  f->y0 = ph.y0;
+  f->S = ph.S;
+  f->sc_off = ph.sc_off;
+  f->tc_off = ph.tc_off;
+  f->n_tleaf = ph.n_tleaf;
+  f->N = N;
+  f->n_src = ph.ns;
+  const int L = ph.L, ns = ph.ns;
+  const int nsc = ph.sc_off[L + 1], ntc = ph.tc_off[L + 1];
+  const std::vector<int2> &src_sorted = ph.src_sorted, &sc_rng = ph.sc_rng, &tleaf_rng = ph.tleaf_rng;
+  const std::vector<double2> &pos_sorted = ph.pos_sorted, &sc_ctr = ph.sc_ctr, &tc_ctr = ph.tc_ctr;
+  const std::vector<int> &tc_par = ph.tc_par, &il_off = ph.il_off, &il_idx = ph.il_idx,
+                         &nl_off = ph.nl_off, &nl_idx = ph.nl_idx, &tord = ph.tord;
+  const long long near_pairs = ph.near_pairs;
+  (void)ns;
+  size_t bytes = 0;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  up(upload(f->d_src_slot, src_sorted, bytes));
+  up(upload(f->d_src_pos, pos_sorted, bytes));
+  up(upload(f->d_sc_ctr, sc_ctr, bytes));
+  up(upload(f->d_sc_rng, sc_rng, bytes));
+  up(upload(f->d_tc_ctr, tc_ctr, bytes));
+  up(upload(f->d_tc_par, tc_par, bytes));
+  up(upload(f->d_il_off, il_off, bytes));
+  up(upload(f->d_il_idx, il_idx, bytes));
+  up(upload(f->d_nl_off, nl_off, bytes));
+  up(upload(f->d_nl_idx, nl_idx, bytes));
+  up(upload(f->d_tgt_node, tord, bytes));
+  up(upload(f->d_tleaf_rng, tleaf_rng, bytes));
+  up(upload(f->d_src_own, ph.src_own, bytes));
+  up(upload(f->d_node_curve, node_curve, bytes));
+  {  // t^-n and log(-t) of the integer offsets t = (dx, dy), |dx|, |dy| <= 3
+    const int p1 = f->p + 1;
+    std::vector<double2> tpow(49 * p1), tlog(49);
+    for (int dy = -3; dy <= 3; ++dy)
+      for (int dx = -3; dx <= 3; ++dx) {
+        const int ti = (dy + 3) * 7 + (dx + 3);
+        const double r2 = double(dx * dx + dy * dy);
+        tlog[ti] = r2 > 0 ? make_double2(0.5 * log(r2), atan2(-double(dy), -double(dx))) : make_double2(0.0, 0.0);
+        const double ix = r2 > 0 ? dx / r2 : 0.0, iy = r2 > 0 ? -dy / r2 : 0.0;  // 1 / t
+        double px = 1.0, py = 0.0;
+        for (int n = 0; n < p1; ++n) {
+          tpow[ti * p1 + n] = make_double2(px, py);
+          const double nx = px * ix - py * iy, ny = px * iy + py * ix;
+          px = nx;
+          py = ny;
+        }
+      }
+    up(upload(f->d_tpow, tpow, bytes));
+    up(upload(f->d_tlog, tlog, bytes));
+  }
+  const size_t ne = size_t(kSets) * (f->p + 1);
+  up(cudaMalloc(reinterpret_cast<void **>(&f->d_M), sizeof(double2) * ne * std::max(nsc, 1)));
+  up(cudaMalloc(reinterpret_cast<void **>(&f->d_Lc), sizeof(double2) * ne * std::max(ntc, 1)));
+  bytes += sizeof(double2) * ne * (nsc + ntc);
+  if (e != cudaSuccess) {
+    f->err = std::string("fmm plan upload: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA;
+  }
+  f->info.levels = L;
+  f->info.sources = ns;
+  f->info.source_cells = nsc;
+  f->info.target_cells = ntc;
+  f->info.m2l_pairs = double(il_idx.size());
+  f->info.near_pairs = double(near_pairs);
+  f->info.device_bytes = double(bytes);
+  return STOKES_OK;
+}
+
+}  // namespace
+}  // namespace stokes
+
+using namespace stokes;
+
+namespace {
+
+int fmm_fail(stokes_fmm *f, int code, const std::string &msg) {
+  if (f) f->err = msg;
+  return code;
+}
+
+#define FMK(call)                                                                            \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fmm_fail(f, e_ == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,  \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out) {
+  if (!out) return STOKES_ERR_ARG;
+  *out = nullptr;
+  if (!c) return STOKES_ERR_ARG;
+  if (!c->have_geom) return STOKES_ERR_NO_GEOM;
+  if (c->n_inst != 1 || order < 4 || order > kMaxOrder || leaf_size < 4 || leaf_size > 4096)
+    return STOKES_ERR_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return STOKES_ERR_CUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  // binomial table (the same on every call)
+  static double hb[kBin][kBin];
+  for (int n = 0; n < kBin; ++n)
+    for (int k = 0; k < kBin; ++k) hb[n][k] = (k == 0 || k == n) ? 1.0 : (k > n ? 0.0 : hb[n - 1][k - 1] + hb[n - 1][k]);
+  if (cudaMemcpyToSymbol(c_binom, hb, sizeof(hb)) != cudaSuccess) return STOKES_ERR_CUDA;
+  stokes_fmm *f = new stokes_fmm();
+  f->ctx = c;
+  f->p = order;
+  const int st = build_plan(f, leaf_size);
+  if (st) {
+    c->err = f->err;
+    free_plan(f);
+    delete f;
+    return st;
+  }
+  f->generation = generation_of(c);
+  f->info.order = order;
+  f->info.plan_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = f;
+  return STOKES_OK;
+}
+
+int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double jump, double *out,
+                    void *stream) {
+  if (!f) return STOKES_ERR_ARG;
+  stokes_ctx *c = f->ctx;
+  if (!c->have_geom || generation_of(c) != f->generation || c->N != f->N)
+    return fmm_fail(f, STOKES_ERR_NO_GEOM, "the context's geometry changed since the plan was made");
+  if ((c->n_ves_nodes > 0 && !slp) || (c->n_wall_nodes > 0 && !dlp) || !out ||
+      (reinterpret_cast<uintptr_t>(out) & 15u) || !isfinite(jump))
+    return fmm_fail(f, STOKES_ERR_ARG, "need the densities of every kind present, a 16-byte aligned "
+                                       "output and a finite jump");
+  FMK(cudaSetDevice(c->device));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int N = c->N;
+  if (c->partial_cap < size_t(N)) {  // the finishing pass reads one split of partials
+    FMK(cudaDeviceSynchronize());
+    cudaFree(c->d_partial);
+    c->d_partial = nullptr;
+    c->partial_cap = 0;
+    FMK(cudaMalloc(reinterpret_cast<void **>(&c->d_partial), sizeof(double2) * N));
+    c->partial_cap = N;
+  }
+  if (c->n_ves_curves > 0) {
+    FMK(cudaEventRecord(c->ev_fork, s));
+    FMK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    FMK(launch_self(c, slp, c->side_stream));
+    FMK(cudaEventRecord(c->ev_join, c->side_stream));
+  }
+  FMK(launch_pack(c, STOKES_FP64, slp, dlp, s));
+  FmmDev d;
+  d.p = f->p;
+  d.n_src = f->n_src;
+  d.N = N;
+  d.wall_slots = c->wall_slots_f64;
+  d.src_slot = f->d_src_slot;
+  d.src_pos = f->d_src_pos;
+  d.val = c->d_src_val64;
+  d.scell_ctr = f->d_sc_ctr;
+  d.scell_rng = f->d_sc_rng;
+  d.tcell_ctr = f->d_tc_ctr;
+  d.tcell_parent = f->d_tc_par;
+  d.il_off = f->d_il_off;
+  d.il_idx = f->d_il_idx;
+  d.nl_off = f->d_nl_off;
+  d.nl_idx = f->d_nl_idx;
+  d.tgt_node = f->d_tgt_node;
+  d.tleaf_rng = f->d_tleaf_rng;
+  d.x = c->d_x;
+  d.M = f->d_M;
+  d.Lc = f->d_Lc;
+  d.out = c->d_partial;
+  d.root_src0 = f->sc_off[0];
+  d.n_roots_src = f->sc_off[1] - f->sc_off[0];
+  d.o = make_double2(f->x0 + 0.5 * f->nx * f->S, f->y0 + 0.5 * f->ny * f->S);
+  d.tpow = f->d_tpow;
+  d.tlog = f->d_tlog;
+  d.src_own = f->d_src_own;
+  d.node_curve = f->d_node_curve;
+  const int L = f->L;
+  const int nthr = std::max(kLeafThreads, (kSets * (f->p + 1) + 31) / 32 * 32);
+  auto hl = [&](int l) { return f->S / double(1 << l); };
+  const int nleaf_s = f->sc_off[L + 1] - f->sc_off[L];
+  if (nleaf_s > 0) p2m_kernel<<<nleaf_s, nthr, 0, s>>>(d, f->sc_off[L], hl(L));
+  for (int l = L - 1; l >= 0; --l) {
+    const int nc = f->sc_off[l + 1] - f->sc_off[l];
+    if (nc > 0) m2m_kernel<<<nc, nthr, 0, s>>>(d, f->sc_off[l]);
+  }
+  for (int l = 0; l <= L; ++l) {
+    const int nc = f->tc_off[l + 1] - f->tc_off[l];
+    if (nc > 0) m2l_kernel<<<nc, nthr, 0, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+  }
+  if (f->n_tleaf > 0) leaf_kernel<<<f->n_tleaf, kLeafThreads, 0, s>>>(d, f->tc_off[L], 0, hl(L));
+  if (c->n_ves_curves > 0) {
+    Binning bn;
+    bn.x0 = f->x0;
+    bn.y0 = f->y0;
+    bn.hmax = f->S / double(1 << kLmax);  // the plan's binning, bit for bit
+    bn.gmaxx = (f->nx << kLmax) - 1;
+    bn.gmaxy = (f->ny << kLmax) - 1;
+    bn.shift = kLmax - L;
+    own_curve_kernel<<<c->n_ves_curves, 128, 0, s>>>(c->d_ves_curve_ids, c->d_curves, c->d_x,
+                                                     c->d_w, c->d_node_dens, slp,
+                                                     1.0 / (4.0 * kPiF * c->mu), bn, c->d_partial);
+  }
+  FMK(cudaGetLastError());
+  if (c->n_ves_curves > 0) FMK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  FMK(launch_finish_nodes(c, 1, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
+  return STOKES_OK;
+}
+
+int stokes_fmm_get_info(const stokes_fmm *f, stokes_fmm_info *info) {
+  if (!f || !info) return STOKES_ERR_ARG;
+  *info = f->info;
+  return STOKES_OK;
+}
+
+int stokes_fmm_last_error(const stokes_fmm *f, char *buf, size_t len) {
+  if (!f || !buf || len == 0) return STOKES_ERR_ARG;
+  snprintf(buf, len, "%s", f->err.c_str());
+  return STOKES_OK;
+}
+
+int stokes_fmm_destroy(stokes_fmm *f) {
+  if (!f) return STOKES_OK;
+  cudaSetDevice(f->ctx->device);
+  cudaDeviceSynchronize();
+  free_plan(f);
+  delete f;
+  return STOKES_OK;
+}
+
+}  // extern "C"

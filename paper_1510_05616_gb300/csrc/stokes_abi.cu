@@ -16,6 +16,7 @@ cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
 int pair_blocks_per_sm(stokes_ctx *c, int precision);
 void tune_apply_cached(stokes_ctx *c);  // tune.cu: shapes recorded for the geometry's size class
+void fmm_geometry_changed(const stokes_ctx *c);  // fmm.cu: invalidates the context's FMM plans
 int field_splits(const stokes_ctx *c, int n_targets);  // k_field.cu
 cudaError_t launch_wait_timeout_check(stokes_ctx *c, cudaStream_t s);  // k_prep.cu
 cudaError_t launch_field(stokes_ctx *c, int n_targets, const double2 *tgt, const double2 *tnrm,
@@ -58,6 +59,7 @@ void dfree(T *&p) {
 }
 
 void free_geometry(stokes_ctx *c) {
+  fmm_geometry_changed(c);
   dfree(c->d_x);
   dfree(c->d_nrm);
   dfree(c->d_w);

@@ -1,0 +1,121 @@
+"""GPU fast multipole evaluation of the layer-potential sum at the nodes against the FP64 oracle
+and the direct GPU sums."""
+import numpy as np
+import pytest
+
+from paper_1510_05616_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_05616_gb300 import build
+    build.build()
+    import paper_1510_05616_gb300 as P
+    return P
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def rel(a, b):
+    """Per-component max-norm relative error."""
+    return float((np.abs(a - b).max(0) / np.abs(b).max(0)).max())
+
+
+def fmm_eval(P, s, slp, dlp, order, leaf=32, jump=0.0):
+    import torch
+    f = P.stokes_fmm_create(s.h, order, leaf)
+    try:
+        out = torch.zeros((s.N, 2), dtype=torch.float64, device="cuda")
+        P.stokes_fmm_eval(f, slp, dlp, jump, out)
+        P.stokes_sync(s.h)
+        return out.cpu().numpy(), P.stokes_fmm_get_info(f)
+    finally:
+        P.stokes_fmm_destroy(f)
+
+
+def test_fmm_matches_oracle_and_converges(P):
+    """On the small channel the FMM sum equals the FP64 oracle's discrete sum to the expansion
+    error, which falls with the order (about 0.45 per order): ~1e-7 at order 20, ~1e-10 at 28."""
+    from oracle import oracle as O
+    g, slp, dlp = I.workload("small_n1280")
+    ref = O.sum_nodes(g, slp, dlp)
+    s = P.StokesSum(g)
+    errs = {}
+    for order in (12, 20, 28):
+        u, info = fmm_eval(P, s, dev(slp), dev(dlp), order)
+        errs[order] = rel(u, ref)
+        assert info["order"] == order and info["levels"] >= 1
+        assert info["sources"] == 3 * g.n_nodes
+    s.close()
+    assert errs[12] > errs[20] > errs[28], errs
+    assert errs[20] < 1e-6 and errs[28] < 1e-9, errs
+
+
+@pytest.mark.parametrize("leaf", [8, 32, 200])
+def test_fmm_leaf_sizes_match_direct_fp64(P, leaf):
+    """Shallow and deep trees give the same sum as the FP64 direct GPU sum (16k channel)."""
+    g, slp, dlp = I.workload("mid_n16k")
+    s = P.StokesSum(g)
+    ref = s.eval(dev(slp), dev(dlp), precision="fp64").cpu().numpy()
+    u, info = fmm_eval(P, s, dev(slp), dev(dlp), 28, leaf)
+    s.close()
+    assert rel(u, ref) < 1e-9, (leaf, rel(u, ref), info)
+
+
+def test_fmm_jump_no_images_and_single_kinds(P):
+    """The jump term, a geometry without images (period 0) and walls-only / vesicles-only
+    geometries all match the direct FP64 sum."""
+    g, slp, dlp = I.workload("small_n1280")
+    cases = []
+    cases.append((g, slp, dlp, -0.5))
+    g0 = I.Geometry(g.curves, 0.0, g.mu, dict(g.meta))
+    cases.append((g0, slp, dlp, 0.0))
+    walls = [c for c in g.curves if c.kind == I.KIND_DLP]
+    ves = [c for c in g.curves if c.kind == I.KIND_SLP]
+    cases.append((I.Geometry(walls, g.period, g.mu, {}), None, dlp, -0.5))
+    cases.append((I.Geometry(ves, g.period, g.mu, {}), slp, None, 0.0))
+    for geo, sl, dl, jump in cases:
+        s = P.StokesSum(geo)
+        ts = dev(sl) if sl is not None else None
+        td = dev(dl) if dl is not None else None
+        ref = s.eval(ts, td, precision="fp64", jump=jump).cpu().numpy()
+        u, _ = fmm_eval(P, s, ts, td, 28, jump=jump)
+        s.close()
+        assert rel(u, ref) < 1e-9, (geo.period, jump, sl is None, dl is None, rel(u, ref))
+
+
+def test_fmm_plan_and_argument_errors(P):
+    import torch
+    g, slp, dlp = I.workload("small_n1280")
+    s = P.StokesSum(g)
+    for order, leaf in ((3, 32), (31, 32), (20, 2)):
+        with pytest.raises(P.StokesError):
+            P.stokes_fmm_create(s.h, order, leaf)
+    f = P.stokes_fmm_create(s.h, 20, 32)
+    out = torch.zeros((s.N, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.StokesError):  # the walls' density is missing
+        P.stokes_fmm_eval(f, dev(slp), None, 0.0, out)
+    s.set_geometry(g)                    # a new geometry: the plan no longer applies
+    with pytest.raises(P.StokesError) as e:
+        P.stokes_fmm_eval(f, dev(slp), dev(dlp), 0.0, out)
+    assert e.value.code == P.STOKES_ERR_NO_GEOM
+    P.stokes_fmm_destroy(f)
+    s.close()
+
+
+def test_fmm_paper_channel(P):
+    """At N = 128,768 the FMM sum (order 28) equals the FP64-accurate double-float direct sum."""
+    g, slp, dlp = I.workload("paper_n128k")
+    s = P.StokesSum(g)
+    ref = s.eval(dev(slp), dev(dlp), precision="df").cpu().numpy()
+    u, info = fmm_eval(P, s, dev(slp), dev(dlp), 28)
+    s.close()
+    assert rel(u, ref) < 1e-9, (rel(u, ref), info)
