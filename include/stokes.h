@@ -409,10 +409,10 @@ STOKES_API int stokes_tune_clear(void);
  * u_resp = D^near tau + sum_m c_m S(., y_m) (Eq. (urep)) to vesicle forces f and the pressure
  * drop p_drive per period (flow towards +x for p_drive > 0; g_T = p_drive (1, 0)).  The blocks
  * of the extended linear system [A B; C Q] (Eq. (BIEU), (BIED), (BIEgu), (BIEgT)) are
- * assembled in FP64 at stokes_sim_set_walls; A is LU-factored, S = Q - C A^-1 B is
- * pseudo-inverted (SVD, singular values below 1e-13 sigma_max dropped), and a solve is the
- * block elimination c = S^+ (g - C A^-1 v), tau = A^-1 v - A^-1 B c (Sec. 4.1, with a dense
- * direct solver in place of the paper's fast direct solver).  Side points: K Gauss-Legendre
+ * assembled in FP64 at stokes_sim_set_walls (A only for the dense wall solvers); A is
+ * factored by the wall solver below, S = Q - C A^-1 B is pseudo-inverted (SVD, singular values
+ * below 1e-13 sigma_max dropped), and a solve is the block elimination
+ * c = S^+ (g - C A^-1 v), tau = A^-1 v - A^-1 B c (Sec. 4.1).  Side points: K Gauss-Legendre
  * nodes across the inlet x = 0 and their copies at x = d; proxies: M >= 2K points on a circle
  * of radius R_p about (d/2, 0).
  *
@@ -443,8 +443,9 @@ STOKES_API int stokes_tune_clear(void);
  *   r = [v; g] - [A B; C Q][tau; c], [tau; c] += block solve of r, with A tau evaluated as the
  *   walls' double-layer sum.  The truncated S^+ alone leaves ~1e-6 of the data in the
  *   side-point rows (Poiseuille errors ~1e-6).  With corrections the wall solves inside the
- *   block solves are single FP32-inverse sweeps (~1e-5 each; the corrections make up for
- *   them), and three corrections bring the result to round-off.  With 0 corrections every
+ *   block solves are the fast direct solver's (~1e-10) or, with STOKES_WALLS_LU32_REFINE,
+ *   single FP32-inverse sweeps (~1e-5; the corrections make up for them), and three
+ *   corrections bring the result to round-off.  With 0 corrections every
  *   wall solve is refined to FP64 accuracy on its own.  (The solve of W = A^-1 B at
  *   stokes_sim_set_walls is refined to FP64 accuracy by the LU solvers; the fast direct
  *   solver gives it to its own ~1e-10.)

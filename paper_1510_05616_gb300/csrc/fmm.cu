@@ -870,11 +870,13 @@ int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out)
     return STOKES_ERR_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return STOKES_ERR_CUDA;
   const auto t0 = std::chrono::steady_clock::now();
-  // binomial table (the same on every call)
-  static double hb[kBin][kBin];
+  // binomial table (Pascal's triangle; the same on every call)
+  std::vector<double> hb(size_t(kBin) * kBin, 0.0);
   for (int n = 0; n < kBin; ++n)
-    for (int k = 0; k < kBin; ++k) hb[n][k] = (k == 0 || k == n) ? 1.0 : (k > n ? 0.0 : hb[n - 1][k - 1] + hb[n - 1][k]);
-  if (cudaMemcpyToSymbol(c_binom, hb, sizeof(hb)) != cudaSuccess) return STOKES_ERR_CUDA;
+    for (int k = 0; k <= n; ++k)
+      hb[n * kBin + k] = (k == 0 || k == n) ? 1.0 : hb[(n - 1) * kBin + k - 1] + hb[(n - 1) * kBin + k];
+  if (cudaMemcpyToSymbol(c_binom, hb.data(), sizeof(double) * hb.size()) != cudaSuccess)
+    return STOKES_ERR_CUDA;
   stokes_fmm *f = new stokes_fmm();
   f->ctx = c;
   f->p = order;
