@@ -168,6 +168,7 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
   const int t = threadIdx.x;
   const int set = t / p1, q = t - set * p1;
   const int nch = ch.y - ch.x;  // 1..4
+  const double inv_q = q > 0 ? 1.0 / q : 0.0;
   __shared__ double2 sa[4][kSets * (kMaxOrder + 1)];
   __shared__ double2 sp[4][kMaxOrder + 1];
   __shared__ double bm[kMaxOrder * kMaxOrder];  // C(q - 1, k - 1) 2^-k, row q - 1, k = 1..p
@@ -195,7 +196,7 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
     if (q == 0) {
       acc = cadd(acc, a[0]);
     } else {
-      double2 v = cscale(cmul(a[0], sp[c][q]), -1.0 / q);
+      double2 v = cscale(cmul(a[0], sp[c][q]), -inv_q);
       const double *B = bm + (q - 1) * p;
       for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(sp[c][q - k], B[k - 1]), v);
       acc = cadd(acc, v);
@@ -217,6 +218,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   const int p = f.p, p1 = p + 1, np = kSets * p1;
   const int t = threadIdx.x;
   const int set = t / p1, q = t - set * p1;
+  const double inv_h = 1.0 / h, inv_q = q > 0 ? 1.0 / q : 0.0;  // no divisions in the loops
   __shared__ double2 sw[kM2lBatch][kSets * (kMaxOrder + 1)];
   __shared__ double2 stq[kM2lBatch][kMaxOrder + 1];
   __shared__ double2 slog[kM2lBatch];
@@ -229,7 +231,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   const int par = f.tcell_parent[cell];
   if (par >= 0) {  // L2L: stage the parent's locals and the powers of the offset
     const double2 cp = f.tcell_ctr[par];
-    const double2 s = make_double2((ct.x - cp.x) / (2.0 * h), (ct.y - cp.y) / (2.0 * h));  // parent side 2h
+    const double2 s = make_double2((ct.x - cp.x) * (0.5 * inv_h), (ct.y - cp.y) * (0.5 * inv_h));  // parent side 2h
     for (int i = t; i < np; i += blockDim.x) sw[0][i] = f.Lc[size_t(par) * np + i];
     if (t <= p) stq[0][t] = cpow(s, t);
     __syncthreads();
@@ -249,17 +251,19 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       const int si = r / p1, qi = r - si * p1;
       const int sc = f.il_idx[il0 + e0 + el];
       const double2 cs = f.scell_ctr[sc];
-      const double ox = (cs.x - ct.x) / h, oy = (cs.y - ct.y) / h;
+      const double ox = (cs.x - ct.x) * inv_h, oy = (cs.y - ct.y) * inv_h;
       const int dx = __double2int_rn(ox), dy = __double2int_rn(oy);
       const bool tab = abs(dx) <= 3 && abs(dy) <= 3;
       const int ti = (dy + 3) * 7 + (dx + 3);
-      const double2 T = tab ? f.tpow[ti * p1 + qi] : cpow(cinv(make_double2(ox, oy)), qi);
+      // off the table (roots only) the offset is an integer pair as well: use it exactly
+      const double2 T = tab ? f.tpow[ti * p1 + qi] : cpow(cinv(make_double2(dx, dy)), qi);
       const double2 a = f.M[size_t(sc) * np + r];
       sw[el][r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
       if (si == 0) {
         stq[el][qi] = T;
         if (qi == 0)
-          slog[el] = tab ? f.tlog[ti] : make_double2(0.5 * log(ox * ox + oy * oy), atan2(-oy, -ox));
+          slog[el] = tab ? f.tlog[ti]
+                         : make_double2(0.5 * log(double(dx) * dx + double(dy) * dy), atan2(-double(dy), -double(dx)));
       }
     }
     __syncthreads();
@@ -276,7 +280,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
           acc = cadd(acc, cadd(cmul(w[0], make_double2(slog[el].x + log_h, slog[el].y)),
                                make_double2(vx, vy)));
         else
-          acc = cfma(make_double2(vx - w[0].x / q, vy - w[0].y / q), stq[el][q], acc);
+          acc = cfma(make_double2(fma(-w[0].x, inv_q, vx), fma(-w[0].y, inv_q, vy)), stq[el][q], acc);
       }
     }
   }
@@ -303,13 +307,14 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
     qtot = s;
   }
   __syncthreads();
+  const double inv_h = 1.0 / h;
   const int2 trg = f.tleaf_rng[leaf];
   const int nb0 = f.nl_off[leaf0 + leaf], nb1 = f.nl_off[leaf0 + leaf + 1];
   for (int it = trg.x + threadIdx.x; it < trg.y; it += blockDim.x) {
     const int node = f.tgt_node[it];
     const double2 z = f.x[node];
     const int tcur = f.node_curve[node];
-    const double2 u = make_double2((z.x - ct.x) / h, (z.y - ct.y) / h);
+    const double2 u = make_double2((z.x - ct.x) * inv_h, (z.y - ct.y) * inv_h);
     // Horner: value, first and second derivative (in u) of every set
     double2 v[kSets], d1[kSets], d2[kSets];
 #pragma unroll
@@ -322,8 +327,8 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
         a0 = cfma(a0, u, b[k]);
       }
       v[s] = a0;
-      d1[s] = cscale(a1, 1.0 / h);
-      d2[s] = cscale(a2, 2.0 / (h * h));
+      d1[s] = cscale(a1, inv_h);
+      d2[s] = cscale(a2, 2.0 * inv_h * inv_h);
     }
     // near field, directly (coincident pairs skipped); the near stokeslet weight is kept to
     // take it out of Q
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
         const double r1 = z.x - w.x, r2 = z.y - w.y;
         const double rr = r1 * r1 + r2 * r2;
         if (rr == 0.0) continue;
-        const double inv = 1.0 / rr;
+        const double inv = __drcp_rn(rr);
         if (!wall) {
           const double lg = -0.5 * log(rr);
           const double c = (r1 * vv.x + r2 * vv.y) * inv;
@@ -414,7 +419,7 @@ __global__ void own_curve_kernel(const int *ves_curve_ids, const CurveDev *curve
       const double rr = r1 * r1 + r2 * r2;
       if (rr == 0.0) continue;
       const double lg = -0.5 * log(rr);
-      const double cc = (r1 * q1 + r2 * q2) / rr;
+      const double cc = (r1 * q1 + r2 * q2) * __drcp_rn(rr);
       ux += lg * q1 + cc * r1;
       uy += lg * q2 + cc * r2;
     }
