@@ -59,6 +59,7 @@ struct stokes_sim {
   // STOKES_WALLS_LU64 factors A in FP64; STOKES_WALLS_LU32_REFINE inverts an FP32 copy (LU, then
   // the inverse, d_Ainv32) and refines every solve with FP64 residuals of the FP64 A (d_A)
   int wall_solver = STOKES_WALLS_FDS;
+  int walls_mode = STOKES_WALLS_FDS;  // the solver the current walls were factored for
   cusolverDnParams_t params = nullptr;
   double *d_A = nullptr;
   float *d_Ainv32 = nullptr;
@@ -959,13 +960,13 @@ __global__ void identity_f32_kernel(int64_t n, float *a) {
 // the two dense matrices once instead of running latency-bound triangular solves.
 int wall_solve(stokes_sim *m, double *X, int nrhs, int max_sweeps = 12) {
   const int64_t nA = m->nA;
-  if (m->wall_solver == STOKES_WALLS_FDS) {  // direct: HBS + SMW, no residual check
+  if (m->walls_mode == STOKES_WALLS_FDS) {  // direct: HBS + SMW, no residual check
     const int st = stokes::fds_solve(m->fds, X, nrhs, m->s, m->blas, m->err);
     m->wall_refinements = 0;
     m->wall_residual = -1.0;
     return st;
   }
-  if (m->wall_solver == STOKES_WALLS_LU64) {
+  if (m->walls_mode == STOKES_WALLS_LU64) {
     QK(cusolverDnDgetrs(m->sol, CUBLAS_OP_N, m->nA, nrhs, m->d_LU, m->nA, m->d_piv, X, m->nA,
                         m->d_info));
     m->wall_refinements = 0;
@@ -1427,8 +1428,9 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(cudaMemcpy(m->d_proxy, prox.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
   // assemble A, B, C, Q
   double *dQ = nullptr, *dS = nullptr, *dU = nullptr, *dVt = nullptr, *dsig = nullptr;
-  const bool lu32 = m->wall_solver == STOKES_WALLS_LU32_REFINE;
-  const bool fds = m->wall_solver == STOKES_WALLS_FDS;
+  m->walls_mode = m->wall_solver;  // later set_wall_solver calls wait for the next set_walls
+  const bool lu32 = m->walls_mode == STOKES_WALLS_LU32_REFINE;
+  const bool fds = m->walls_mode == STOKES_WALLS_FDS;
   double *dA = nullptr;
   if (!fds) {
     SK(dalloc(dA, size_t(nA) * nA));
