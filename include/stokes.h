@@ -243,6 +243,40 @@ STOKES_API int stokes_fmm_get_info(const stokes_fmm *fmm, stokes_fmm_info *info)
 STOKES_API int stokes_fmm_last_error(const stokes_fmm *fmm, char *buf, size_t len);
 STOKES_API int stokes_fmm_destroy(stokes_fmm *fmm);
 
+/* ---------------------------------------------------------------------------------------------
+ * Close evaluation of the vesicles' single layer at nearby nodes (FP64).  The plain n-point
+ * sum over a vesicle loses accuracy like exp(-2 pi delta / h) at a target delta away from a
+ * vesicle of node spacing h.  stokes_close_eval ADDS to out_velocity (the node result of
+ * stokes_sum_eval, 2 N doubles, 16-byte aligned DEVICE array), for every node x and every
+ * vesicle image m closer than factor h to x (own vesicle at m = 0 excluded: the Kress rule
+ * carries it), S_K[f](x) - S_1[f](x): S_1 the plain single-layer sum over that vesicle image,
+ * S_K the single layer of the trigonometric interpolants of the vesicle's nodes and density by
+ * the trapezoid rule on K n resampled points (error ~ exp(-2 pi K delta / h)).  The pairs are
+ * found on the host by stokes_close_create (synchronous) for ctx's current single-instance
+ * geometry: factor in (0, 50], upsample K >= 1 with K n <= 4096 for the largest vesicle
+ * (STOKES_ERR_ARG otherwise).  The plan stays valid until ctx's geometry is set again
+ * (stokes_close_eval then returns STOKES_ERR_NO_GEOM).  stokes_close_eval takes the DEVICE
+ * vesicle density of stokes_sum_eval and runs asynchronously on `stream`.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct stokes_close stokes_close;
+
+typedef struct {
+    int upsample;     /* K                                                        */
+    int pairs;        /* close (node, vesicle image) pairs                        */
+    int targets;      /* nodes with at least one close pair                       */
+    int vesicles;     /* vesicle curves resampled per evaluation                  */
+    double factor;    /* closeness threshold in node spacings                     */
+    double plan_ms;   /* stokes_close_create, wall clock                          */
+} stokes_close_info;
+
+STOKES_API int stokes_close_create(stokes_ctx *ctx, double factor, int upsample,
+                                   stokes_close **out);
+STOKES_API int stokes_close_eval(stokes_close *close, const double *slp_density,
+                                 double *out_velocity, void *stream);
+STOKES_API int stokes_close_get_info(const stokes_close *close, stokes_close_info *info);
+STOKES_API int stokes_close_last_error(const stokes_close *close, char *buf, size_t len);
+STOKES_API int stokes_close_destroy(stokes_close *close);
+
 /*
  * Phase timing with CUDA events recorded on the call's stream.  With profiling on (on != 0)
  * every stokes_sum_eval / stokes_sum_eval_targets records events around its three phases:

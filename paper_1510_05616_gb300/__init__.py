@@ -69,6 +69,11 @@ _SIGNATURES = {
     "stokes_fmm_get_info": [_vp, _vp],
     "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_fmm_destroy": [_vp],
+    "stokes_close_create": [_vp, _c_double, _c_int, ctypes.POINTER(_vp)],
+    "stokes_close_eval": [_vp, _vp, _vp, _vp],
+    "stokes_close_get_info": [_vp, _vp],
+    "stokes_close_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "stokes_close_destroy": [_vp],
     "stokes_num_nodes": [_vp],
     "stokes_set_launch": [_vp, _c_int, _c_int, _c_int, _c_int],
     "stokes_get_launch": [_vp, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
@@ -335,6 +340,51 @@ def stokes_fmm_last_error(f) -> str:
 
 def stokes_fmm_destroy(f):
     return load().stokes_fmm_destroy(f)
+
+
+class CloseInfo(ctypes.Structure):
+    _fields_ = [("upsample", _c_int), ("pairs", _c_int), ("targets", _c_int),
+                ("vesicles", _c_int), ("factor", _c_double), ("plan_ms", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def stokes_close_create(h, factor=5.0, upsample=16):
+    """Close-evaluation plan for the context's current geometry (see stokes.h)."""
+    f = _vp()
+    code = load().stokes_close_create(h, float(factor), int(upsample), ctypes.byref(f))
+    if code != STOKES_OK:
+        raise StokesError(code, _err(h))
+    return f
+
+
+def stokes_close_last_error(f) -> str:
+    buf = ctypes.create_string_buffer(512)
+    if f:
+        load().stokes_close_last_error(f, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def stokes_close_eval(f, slp_density, out_velocity, stream=None):
+    """Adds the close-evaluation correction to out_velocity (the node sum)."""
+    code = load().stokes_close_eval(f, _dptr(slp_density, "slp_density", (2,), True),
+                                    _dptr(out_velocity, "out_velocity", (2,)), _stream(stream))
+    if code != STOKES_OK:
+        raise StokesError(code, stokes_close_last_error(f))
+    return code
+
+
+def stokes_close_get_info(f):
+    info = CloseInfo()
+    code = load().stokes_close_get_info(f, ctypes.byref(info))
+    if code != STOKES_OK:
+        raise StokesError(code, "stokes_close_get_info")
+    return info.as_dict()
+
+
+def stokes_close_destroy(f):
+    return load().stokes_close_destroy(f)
 
 
 def stokes_num_nodes(h) -> int:

@@ -473,6 +473,9 @@ void fmm_geometry_changed(const stokes_ctx *c) {
   ++g_gen[c];
 }
 
+// The generation of a context's geometry (plans built for an older one no longer apply).
+unsigned long long geometry_generation(const stokes_ctx *c) { return generation_of(c); }
+
 namespace {
 
 constexpr int kLmax = 20;  // depth of the integer coordinates the keys are cut from
