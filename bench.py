@@ -12,6 +12,12 @@ node); value = pairs processed by all ranks / max-over-ranks time.
 
 ``--impl reference`` times the FP64 CPU oracle (the test oracle, a plain double loop) on the
 host cores, on bounded target samples of the same workload.
+
+Other measurements (one JSON line each): ``--batch`` (64-channel ensemble in one launch),
+``--scaling`` (the sum from N = 1,280 to 524,288), ``--step`` (semi-implicit vesicle step with
+the learned warm start), ``--poiseuille`` (the accuracy study of Sec. 5.1), ``--walls`` (the
+fast direct wall solver against the dense one), ``--fmm`` (fast multipole node evaluation
+against the direct sums).
 """
 from __future__ import annotations
 
