@@ -289,22 +289,28 @@ STOKES_API int stokes_last_timing(stokes_ctx *ctx, double *ms);
 
 /*
  * stokes_sum_eval_targets without any device allocation.  The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc where they evaluate -- code that
- * records a CUDA graph by stream capture, hosts that own all device memory through their own
- * pool, real-time loops that must not block on the allocator.  (stokes_sum_eval_targets may
- * grow the context's scratch buffer, with a device synchronisation, when it sees more
- * targets than before.)
+ * entry point exists for callers that cannot call cudaMalloc where they evaluate -- hosts
+ * that own all device memory through a pool of their own and forbid other allocations,
+ * plug-ins that run inside such a host on a fixed memory budget, real-time loops that must
+ * not block on the allocator.  (stokes_sum_eval_targets may grow the context's scratch
+ * buffer, with a device synchronisation, when it sees more targets than before.)
  *   Arguments, layout and results are those of stokes_sum_eval_targets; the context (created
- *   and given a geometry beforehand) supplies the geometry and its preallocated source buffers.
+ *   and given a single-instance geometry beforehand; a batched context gives STOKES_ERR_ARG)
+ *   supplies the geometry and its preallocated source buffers.
  *   The cross-split partial sums live in a fixed device array inside the library of
  *   262,144 x 16 B = 4 MiB, held by every device that loads the library until the process
  *   exits.  n_targets may be at most 262,144 (STOKES_ERR_ARG beyond, with a message); for
  *   large n_targets fewer source splits are used so that splits x n_targets fits.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *   make that first call before any stream capture.
+ *   The array's device address is looked up (cudaGetSymbolAddress) when a context is created
+ *   on the device, so contexts created after a cudaDeviceReset use the new address.  Should
+ *   that lookup have failed, the first call on the device looks it up instead; make that
+ *   first call before any stream capture.
  *   All calls, from every context on a device, share the one array: calls whose kernels can
  *   overlap on the GPU (different streams without ordering between them) race on it and
  *   must be serialised by the caller.  Nothing in the array needs clearing between calls.
+ *   Like every call on a context, it must not run concurrently with another call on the same
+ *   context from a second host thread.  With profiling on, the call records the same three
+ *   phase events as stokes_sum_eval_targets (stokes_last_timing reports them).
  */
 STOKES_API int stokes_sum_eval_targets_noalloc(stokes_ctx *ctx, int precision,
                                                const double *slp_density,

@@ -944,14 +944,15 @@ PairKernel pick_f64(bool batch, bool img) {
 }
 
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
-                        const int2 *skip, int splits, cudaStream_t s) {
-  if (precision == STOKES_DOUBLE_FLOAT) return launch_pair_df(c, n_targets, tgt, skip, splits, s);
+                        const int2 *skip, int splits, double2 *partial, cudaStream_t s) {
+  if (precision == STOKES_DOUBLE_FLOAT)
+    return launch_pair_df(c, n_targets, tgt, skip, splits, partial, s);
   PairArgs a{};
   a.n_targets = n_targets;
   a.tgt = tgt;
   a.tgt_skip = skip;
   a.period = c->period;
-  a.partial = c->d_partial;
+  a.partial = partial;
   a.status = c->d_status;
   a.logtab = c->d_logtab;
   const bool img = c->period != 0.0;
@@ -1054,17 +1055,3 @@ int effective_splits(stokes_ctx *c, int precision, int splits) {
 
 }  // namespace stokes
 
-namespace stokes {
-
-// Same launch as launch_pair, with the FP64 partials written to a caller-chosen buffer
-// (the no-allocation entry point passes the address of its static device array).
-cudaError_t launch_pair_scratch(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
-                                int splits, double2 *partial, cudaStream_t s) {
-  double2 *keep = c->d_partial;
-  c->d_partial = partial;
-  const cudaError_t e = launch_pair(c, precision, n_targets, tgt, nullptr, splits, s);
-  c->d_partial = keep;
-  return e;
-}
-
-}  // namespace stokes

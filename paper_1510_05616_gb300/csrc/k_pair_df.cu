@@ -701,8 +701,9 @@ static PairArgs df_args(stokes_ctx *c) {
 }
 
 cudaError_t launch_pair_df(stokes_ctx *c, int n_targets, const double2 *tgt, const int2 *skip,
-                           int splits, cudaStream_t s) {
+                           int splits, double2 *partial, cudaStream_t s) {
   PairArgs a = df_args(c);
+  a.partial = partial;
   a.n_targets = n_targets;
   a.tgt = tgt;
   a.tgt_skip = skip;

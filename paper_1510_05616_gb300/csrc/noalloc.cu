@@ -1,13 +1,12 @@
 // noalloc.cu -- free-point evaluation that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they evaluate: code recording a
-// CUDA graph by stream capture (allocation and the device-wide synchronisation that a
-// growing scratch buffer needs are not allowed while capturing), hosts that hand the GPU's
-// memory to a pool of their own and forbid other allocations, and real-time loops that
-// must not block on the allocator.  stokes_sum_eval_targets may grow the context's scratch
-// buffer (cudaMalloc after a device synchronisation) when it sees more targets than before.
-// The entry point below keeps its cross-split partial sums in a fixed, file-scope device
-// array instead, so a call never allocates.
+// Some callers cannot call cudaMalloc at the point where they evaluate: hosts that hand all
+// of the GPU's memory to a pool of their own and forbid other allocations, plug-ins that run
+// inside such a host with a fixed memory budget, and real-time loops that must not block on
+// the allocator.  stokes_sum_eval_targets may grow the context's scratch buffer (cudaMalloc
+// after a device synchronisation) when it sees more targets than before.  The entry point
+// below keeps its cross-split partial sums in a fixed, file-scope device array instead, so a
+// call never allocates.
 #include <stdio.h>
 
 #include <algorithm>
@@ -16,11 +15,10 @@
 #include "stokes_internal.cuh"
 
 namespace stokes {
-cudaError_t launch_pair_scratch(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
-                                int splits, double2 *partial, cudaStream_t s);
 cudaError_t launch_finish_free_scratch(int splits, int n_targets, const double2 *partial,
                                        double2 *out, cudaStream_t s);
 int effective_splits(stokes_ctx *c, int precision, int splits);
+void noalloc_setup_device(int device);
 }  // namespace stokes
 
 using namespace stokes;
@@ -36,17 +34,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double2 *g_partial_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_noalloc_partial on `device` (which must be current).  The name
-// g_noalloc_partial in host code is only a host-side stand-in, so the address is looked up
-// once per device with cudaGetSymbolAddress and cached.
+// Looks up the device address of g_noalloc_partial on `device` (which must be current) and
+// caches it.  The name g_noalloc_partial in host code is only a host-side stand-in, so host
+// code must pass this looked-up address to the kernels.
+cudaError_t lookup_locked(int device) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+  if (e != cudaSuccess) return e;
+  g_partial_ptr[device] = static_cast<double2 *>(p);
+  return cudaSuccess;
+}
+
+// The cached address for `device` (current), looked up now if no context creation has yet.
 cudaError_t scratch_for_device(int device, double2 **out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_partial_ptr[device]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    const cudaError_t e = lookup_locked(device);
     if (e != cudaSuccess) return e;
-    g_partial_ptr[device] = static_cast<double2 *>(p);
   }
   *out = g_partial_ptr[device];
   return cudaSuccess;
@@ -57,7 +62,30 @@ int set_err(stokes_ctx *c, int code, const char *msg) {
   return code;
 }
 
+// Profiling events of the three phases, as the allocating entry point records them.
+cudaError_t mark(stokes_ctx *c, int k, cudaStream_t s) {
+  if (!c->profiling) return cudaSuccess;
+  const cudaError_t e = cudaEventRecord(c->ev[k], s);
+  if (e == cudaSuccess && k == 3) c->timed = true;
+  return e;
+}
+
 }  // namespace
+
+namespace stokes {
+
+// Called by stokes_create with `device` current: (re)reads the array's device address, so a
+// context created after a cudaDeviceReset (which unloads the module and with it the array)
+// never sees an address from before the reset.  A failed lookup leaves the entry empty; the
+// entry point then retries and reports the error itself.
+void noalloc_setup_device(int device) {
+  if (device < 0 || device >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  g_partial_ptr[device] = nullptr;
+  (void)lookup_locked(device);
+}
+
+}  // namespace stokes
 
 extern "C" int stokes_sum_eval_targets_noalloc(stokes_ctx *c, int precision, const double *slp,
                                                const double *dlp, int n_targets,
@@ -65,6 +93,8 @@ extern "C" int stokes_sum_eval_targets_noalloc(stokes_ctx *c, int precision, con
                                                void *stream) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom) return set_err(c, STOKES_ERR_NO_GEOM, "no geometry set");
+  if (c->n_inst > 1)
+    return set_err(c, STOKES_ERR_ARG, "free-point evaluation needs a single-instance geometry");
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN &&
       precision != STOKES_DOUBLE_FLOAT)
     return set_err(c, STOKES_ERR_ARG, "unknown precision");
@@ -97,12 +127,16 @@ extern "C" int stokes_sum_eval_targets_noalloc(stokes_ctx *c, int precision, con
                                                   : c->splits_df;
   const int splits = effective_splits(c, precision, std::min(want, kNoAllocPartials / n_targets));
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  e = launch_pack(c, precision, slp, dlp, s);
+  e = mark(c, 0, s);
+  if (e == cudaSuccess) e = launch_pack(c, precision, slp, dlp, s);
+  if (e == cudaSuccess) e = mark(c, 1, s);
   if (e == cudaSuccess)
-    e = launch_pair_scratch(c, precision, n_targets, reinterpret_cast<const double2 *>(targets),
-                            splits, scratch, s);
+    e = launch_pair(c, precision, n_targets, reinterpret_cast<const double2 *>(targets), nullptr,
+                    splits, scratch, s);
+  if (e == cudaSuccess) e = mark(c, 2, s);
   if (e == cudaSuccess)
     e = launch_finish_free_scratch(splits, n_targets, scratch, reinterpret_cast<double2 *>(out), s);
+  if (e == cudaSuccess) e = mark(c, 3, s);
   if (e != cudaSuccess) return set_err(c, STOKES_ERR_CUDA, cudaGetErrorString(e));
   return STOKES_OK;
 }

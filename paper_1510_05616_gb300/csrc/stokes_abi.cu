@@ -19,6 +19,7 @@ void tune_apply_cached(stokes_ctx *c);  // tune.cu: shapes recorded for the geom
 void fmm_geometry_changed(const stokes_ctx *c);  // fmm.cu: invalidates the context's FMM plans
 int field_splits(const stokes_ctx *c, int n_targets);  // k_field.cu
 cudaError_t launch_wait_timeout_check(stokes_ctx *c, cudaStream_t s);  // k_prep.cu
+void noalloc_setup_device(int device);                                 // noalloc.cu
 cudaError_t launch_field(stokes_ctx *c, int n_targets, const double2 *tgt, const double2 *tnrm,
                          int splits, double *out, cudaStream_t s);
 }  // namespace stokes
@@ -246,7 +247,8 @@ int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp
   CK(launch_pack(c, precision, slp, dlp, s));
   MARK(1);
   CK(launch_pair(c, precision, c->N, c->d_x,
-                 precision == STOKES_FP32_KAHAN ? c->d_tgt_skip32 : c->d_tgt_skip64, splits, s));
+                 precision == STOKES_FP32_KAHAN ? c->d_tgt_skip32 : c->d_tgt_skip64, splits,
+                 c->d_partial, s));
   MARK(2);
   if (c->n_ves_curves > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   CK(launch_finish_nodes(c, splits, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
@@ -281,6 +283,7 @@ int stokes_create(int device, stokes_ctx **out) {
     delete c;
     return STOKES_ERR_CUDA;
   }
+  noalloc_setup_device(device);
   *out = c;
   return STOKES_OK;
 }
@@ -683,7 +686,7 @@ int stokes_sum_eval_targets(stokes_ctx *c, int precision, const double *slp, con
   CK(launch_pack(c, precision, slp, dlp, s));
   MARK(1);
   CK(launch_pair(c, precision, n_targets, reinterpret_cast<const double2 *>(targets), nullptr,
-                 splits, s));
+                 splits, c->d_partial, s));
   MARK(2);
   CK(launch_finish_free(c, splits, n_targets, reinterpret_cast<double2 *>(out), s));
   MARK(3);

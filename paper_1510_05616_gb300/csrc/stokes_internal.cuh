@@ -209,8 +209,9 @@ namespace stokes {
 cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s);
 cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const double *dlp,
                         cudaStream_t s);
+// FP64 partials of split k and target i go to partial[k * n_targets + i].
 cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const double2 *tgt,
-                        const int2 *skip, int splits, cudaStream_t s);
+                        const int2 *skip, int splits, double2 *partial, cudaStream_t s);
 cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s);
 cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
                                 double jump, double2 *out, cudaStream_t s);
@@ -226,7 +227,7 @@ cudaError_t launch_df_init(stokes::DFConst *d, cudaStream_t s);
 cudaError_t launch_geom_prep_df(stokes_ctx *c, cudaStream_t s);
 cudaError_t launch_pack_df(stokes_ctx *c, const double *slp, const double *dlp, cudaStream_t s);
 cudaError_t launch_pair_df(stokes_ctx *c, int n_targets, const double2 *tgt, const int2 *skip,
-                           int splits, cudaStream_t s);
+                           int splits, double2 *partial, cudaStream_t s);
 cudaError_t launch_pair_batch_df(stokes_ctx *c, int blocks, cudaStream_t s);
 int pair_df_blocks_per_sm(stokes_ctx *c);
 int pair_df_batch_blocks_per_sm(stokes_ctx *c);
