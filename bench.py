@@ -52,7 +52,13 @@ METRIC = "Stokes SLP+DLP Gpair-evals/s at Nâ‰ˆ128k: FP32-comp vs FP64, rel err â
 # tensor-vector product and the accumulation), counting every add, multiply, reciprocal and
 # log as one flop; used for the roofline's achieved rate.
 FLOPS_PER_PAIR = 20
-SMS, LANES = 152, 128
+LANES = 128  # FP32 FMA lanes per SM (Blackwell)
+
+
+def device_sms(device=0) -> int:
+    """Streaming multiprocessors of the CUDA device (read from the device, not assumed)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
 
 
 def dist_env():
@@ -675,7 +681,7 @@ def run_scaling(args):
     B.build()
     O.build()
     peaks, _ = measured_peaks()
-    peak = SMS * LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = device_sms() * LANES * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     rows = {}
     for name in ("small_n1280", "mid_n16k", "paper_n128k", "large_n512k"):
         t0 = time.perf_counter()
@@ -917,7 +923,8 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * LANES * 2 * sm_mhz * 1e6 / 1e12
+    sms = device_sms(torch.cuda.current_device())
+    peak_tflops = sms * LANES * 2 * sm_mhz * 1e6 / 1e12
     achieved = FLOPS_PER_PAIR * pairs / (pair_avg / 1e3) / 1e12
     traffic = profiled_traffic()
     line = {
@@ -932,7 +939,7 @@ def main():
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "pair_f32k_kernel" if args.precision == "fp32k" else "pair_f64_kernel",
                      "kernel_ms": pair_avg,
-                     "peak_basis": "FP32 FMA peak 152 SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % peak_kind,
+                     "peak_basis": "FP32 FMA peak %d SM x 128 lanes x 2 flop x sm_max_mhz (%s clocks)" % (sms, peak_kind),
                      "flops_per_pair": FLOPS_PER_PAIR},
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,  # per step: self (side stream), pack, pair, 2 finish

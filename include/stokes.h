@@ -200,6 +200,14 @@ STOKES_API int stokes_sync(stokes_ctx *ctx, void *stream);
  * STOKES_ERR_TIMEOUT (and clears it), and the context stays usable.  For tests. */
 STOKES_API int stokes_check_wait_timeout(stokes_ctx *ctx, void *stream);
 
+/* Self-check of the FP64 logarithm the FP64 pair kernel and the Kress self pass use
+ * (Eq. (S)'s log r and the log-split weights of Sec. 3.2 both go through it): out[i] =
+ * that kernel-side log of x[i] for i < n.  x, out: DEVICE double[n], caller-owned; x must be
+ * positive, finite and normal (the pair kernels pass r^2 >= 1e-150).  Asynchronous on
+ * `stream`.  STOKES_ERR_ARG for n < 0 or NULL pointers.  For tests. */
+STOKES_API int stokes_check_log64(stokes_ctx *ctx, const double *x, int n, double *out,
+                                  void *stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Fast multipole evaluation at the nodes (FP64).  The same discrete sum as stokes_sum_eval
  * (pair sum over m in {-1, 0, +1} with the own curve skipped at m = 0, Kress self terms, wall

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "stokes_sum_eval_targets_noalloc": [_vp, _c_int, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sync": [_vp, _vp],
     "stokes_check_wait_timeout": [_vp, _vp],
+    "stokes_check_log64": [_vp, _vp, _c_int, _vp, _vp],
     "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
@@ -290,6 +291,15 @@ def stokes_sync(h, stream=None):
 
 def stokes_check_wait_timeout(h, stream=None):
     return _check(h, load().stokes_check_wait_timeout(h, _stream(stream)))
+
+
+def stokes_check_log64(h, x, out, stream=None):
+    """out[i] = the FP64 pair kernels' logarithm of x[i] (device float64 tensors, same length)."""
+    n = int(x.numel())
+    if int(out.numel()) != n:
+        raise StokesError(STOKES_ERR_ARG, "x and out must have the same length")
+    return _check(h, load().stokes_check_log64(h, _dptr(x, "x"), n, _dptr(out, "out"),
+                                               _stream(stream)))
 
 
 class FmmInfo(ctypes.Structure):

@@ -218,9 +218,14 @@ void find_close_pairs(const std::vector<double2> &x, const std::vector<int> &cof
   }
   const int m0 = d != 0.0 ? -1 : 0, m1 = d != 0.0 ? 1 : 0;
   std::unordered_map<long long, std::vector<int2>> grid;
+  // cell (gx, gy) -> one 64-bit key: gx in the high word, gy's low 32 bits in the low word
+  // (shifted as unsigned: a left shift of a negative signed value is undefined)
+  auto cell_key = [](long long gx, long long gy) {
+    return (long long)((static_cast<unsigned long long>(gx) << 32) ^
+                       (static_cast<unsigned long long>(gy) & 0xffffffffull));
+  };
   auto key = [&](double px, double py) {
-    const long long gx = (long long)std::floor(px / G), gy = (long long)std::floor(py / G);
-    return (gx << 32) ^ (gy & 0xffffffffll);
+    return cell_key((long long)std::floor(px / G), (long long)std::floor(py / G));
   };
   if (V > 0)
     for (int v = 0; v < V; ++v)
@@ -233,7 +238,7 @@ void find_close_pairs(const std::vector<double2> &x, const std::vector<int> &cof
     const long long gx = (long long)std::floor(x[i].x / G), gy = (long long)std::floor(x[i].y / G);
     for (long long dy = -1; dy <= 1; ++dy)
       for (long long dx = -1; dx <= 1; ++dx) {
-        const auto it = grid.find(((gx + dx) << 32) ^ ((gy + dy) & 0xffffffffll));
+        const auto it = grid.find(cell_key(gx + dx, gy + dy));
         if (it != grid.end()) cand.insert(cand.end(), it->second.begin(), it->second.end());
       }
     std::sort(cand.begin(), cand.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });

@@ -432,7 +432,15 @@ __global__ void set_identity_kernel(int n, double *K) {
     K[i] = (i % size_t(n + 1) == 0) ? 1.0 : 0.0;
 }
 
-int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, size_t(152) * 32)); }
+// Blocks of a 256-thread grid-stride launch over n elements: one per 256 elements, at most
+// 32 per SM of the current device.
+int grid_for(size_t n) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  return int(std::max<size_t>(1, std::min<size_t>((n + 255) / 256, size_t(sms) * 32)));
+}
 
 }  // namespace
 

@@ -1,13 +1,17 @@
 // flog64.cuh -- table-driven FP64 natural logarithm for the FP64 pair and self kernels.
 //
-// Method (table lookup plus a short series, as in table-driven elementary functions):
+// Method: P. T. P. Tang, "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM Trans. Math. Software 16 (1990) 378-400 -- reduce x to a
+// breakpoint a_k near its mantissa, take log a_k from a table and the rest from a short
+// polynomial in u = (m - a_k)/a_k.  This build's own variant:
 // x = m 2^e with m in [1, 2); k = the top 7 bits of m's fraction; a_k = 1 + (k + 1/2) / 128, so
 // u = (m - a_k) / a_k satisfies |u| <= 1/256; then
 //   log x = e ln 2 + log a_k + log1p(u),   log1p(u) = u + u^2 (-1/2 + u/3 - u^2/4 + u^3/5 - u^4/6 + u^5/7),
-// whose truncation error |u|^8 / 8 < 1e-20.  The table holds (a_k, 1/a_k, log a_k), filled once per context
-// by a kernel that calls the CUDA log, and ln 2 split into a 32-bit head and a tail so
-// that e * head is exact.  Valid for positive, finite, normal x (the pair kernels pass
-// r^2 >= 1e-150).
+// the Taylor series of log1p cut after u^7, whose truncation error |u|^8 / 8 < 1e-20.  The
+// table holds (a_k, 1/a_k, log a_k), filled once per context by a kernel that calls the CUDA
+// log, and ln 2 split into a 32-bit head and a tail so that e * head is exact.  Valid for
+// positive, finite, normal x (the pair kernels pass r^2 >= 1e-150).  stokes_check_log64
+// evaluates it on caller-given points so that tests can compare it with CUDA's log.
 #pragma once
 #include <cuda_runtime.h>
 

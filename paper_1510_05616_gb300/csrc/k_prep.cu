@@ -319,6 +319,17 @@ cudaError_t launch_logtab_init(LogTab *t, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void check_log64_kernel(int n, const double *x, double *out, const LogTab *t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = flog64(x[i], t);
+}
+
+cudaError_t launch_check_log64(stokes_ctx *c, int n, const double *x, double *out,
+                               cudaStream_t s) {
+  check_log64_kernel<<<nblk(n, 256), 256, 0, s>>>(n, x, out, c->d_logtab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_kress_table(int n, double *T, cudaStream_t s) {
   kress_table_kernel<<<nblk(n, 128), 128, 0, s>>>(n, T);
   return cudaGetLastError();

@@ -943,7 +943,15 @@ __global__ void add_f2d_kernel(size_t n, const float *a, double *b) {
     b[i] += double(a[i]);
 }
 
-inline int grid_for(size_t n) { return int(std::min<size_t>((n + 255) / 256, size_t(152) * 32)); }
+// Blocks of a 256-thread grid-stride launch over n elements: one per 256 elements, at most
+// 32 per SM of the current device.
+inline int grid_for(size_t n) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  return int(std::max<size_t>(1, std::min<size_t>((n + 255) / 256, size_t(sms) * 32)));
+}
 
 __global__ void identity_f32_kernel(int64_t n, float *a) {
   const size_t nn = size_t(n) * size_t(n);

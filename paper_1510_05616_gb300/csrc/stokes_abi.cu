@@ -20,6 +20,8 @@ void fmm_geometry_changed(const stokes_ctx *c);  // fmm.cu: invalidates the cont
 int field_splits(const stokes_ctx *c, int n_targets);  // k_field.cu
 cudaError_t launch_wait_timeout_check(stokes_ctx *c, cudaStream_t s);  // k_prep.cu
 void noalloc_setup_device(int device);                                 // noalloc.cu
+cudaError_t launch_check_log64(stokes_ctx *c, int n, const double *x, double *out,
+                               cudaStream_t s);                        // k_prep.cu
 cudaError_t launch_field(stokes_ctx *c, int n_targets, const double2 *tgt, const double2 *tnrm,
                          int splits, double *out, cudaStream_t s);
 }  // namespace stokes
@@ -730,6 +732,16 @@ int stokes_check_wait_timeout(stokes_ctx *c, void *stream) {
   if (!c) return STOKES_ERR_ARG;
   CK(cudaSetDevice(c->device));
   CK(launch_wait_timeout_check(c, as_stream(stream)));
+  return STOKES_OK;
+}
+
+int stokes_check_log64(stokes_ctx *c, const double *x, int n, double *out, void *stream) {
+  if (!c) return STOKES_ERR_ARG;
+  if (n < 0) return fail(c, STOKES_ERR_ARG, "n < 0");
+  if (n == 0) return STOKES_OK;
+  if (!x || !out) return fail(c, STOKES_ERR_ARG, "x and out must be device pointers");
+  CK(cudaSetDevice(c->device));
+  CK(launch_check_log64(c, n, x, out, as_stream(stream)));
   return STOKES_OK;
 }
 

@@ -140,19 +140,27 @@ def test_free_step_parity(P, S, period):
 
 @pytest.mark.parametrize("prec", ["fp64", "df"])
 def test_channel_step_parity(P, S, prec):
+    """One step with walls: GPU GMRES to a 1e-13 residual against the oracle's dense direct
+    solve of the same system (both FP64-accurate), so what is left is round-off amplified by
+    the step system's conditioning, not the solver tolerance: 1e-9 relative on u and sigma."""
     walls, ves = _case(n_ves=2, n_v=16, n_w=64)
     dt, pd = 1e-3, 0.5
     h = make_sim(P, walls, ves)
-    st = P.vesicle_step_warmstart(h, dt, pd, tol=1e-12, max_iter=200, precision=P.PRECISIONS[prec])
+    st = P.vesicle_step_warmstart(h, dt, pd, tol=1e-13, max_iter=400, precision=P.PRECISIONS[prec])
     x, sg, sol = P.stokes_sim_get_state(h)
     P.stokes_sim_destroy(h)
+    assert st["residual"] <= 1e-13
     ox, osg, u, sig, ures = _oracle_step(S, [c.nodes for c in ves], dt, walls, pd)
     n = ves[0].n
     gu = np.concatenate([np.stack([sol[3 * n * v:3 * n * v + n], sol[3 * n * v + n:3 * n * v + 2 * n]], 1)
                          for v in range(len(ves))])
-    assert np.abs(gu - u).max() < 1e-6 * np.abs(u).max()
-    assert np.abs(sg - sig).max() < 1e-6 * np.abs(sig).max()
-    assert np.abs(x - np.vstack(ox)).max() < 1e-8
+    eu = np.abs(gu - u).max() / np.abs(u).max()
+    es = np.abs(sg - sig).max() / np.abs(sig).max()
+    ex = np.abs(x - np.vstack(ox)).max()
+    print("%s step with walls: u %.2e, sigma %.2e, x %.2e (GMRES %d its, residual %.1e)"
+          % (prec, eu, es, ex, st["iterations"], st["residual"]))
+    assert eu < 1e-9 and es < 1e-9
+    assert ex < 1e-11
 
 
 def test_warm_start_with_solution_converges_at_once(P):
