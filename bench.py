@@ -331,13 +331,28 @@ def run_batch(args):
     return 0
 
 
+def _mode_slice(nm_from, nm_to, history=False):
+    """Columns of the nm_from-mode features and targets that hold the nm_to-mode ones (the
+    modes k = -nm_to/2..nm_to/2-1 of shape, velocity change and solution change, and the
+    tension modes k = 0..nm_to/2-1, are a subset of the larger representation; with history
+    features the previous solution and its last change follow in the target layout)."""
+    lo = nm_from // 2 - nm_to // 2
+    shape = np.arange(2 * lo, 2 * lo + 2 * nm_to)
+    targ = np.concatenate([shape, 2 * nm_from + np.arange(nm_to)])
+    feat = [shape, 2 * nm_from + shape]
+    if history:
+        feat += [4 * nm_from + targ, 4 * nm_from + 3 * nm_from + targ]
+    return np.concatenate(feat), targ
+
+
 def run_step(args):
     """Algorithm 1 on a channel (walls, channel response, GMRES to 1e-10): plain runs give the
-    training states, the network is trained with the library's kernels, and a held-out channel
-    is stepped from the same state with the zero, previous-step and network guesses, for each
-    precision of the Krylov matvecs (FP64; FP32-Kahan sweeps inside FP64-accurate refinement;
-    double-float).  The FP64 pair sum is left out at N = 128,768, where one of its matvecs
-    costs ~1.2 s."""
+    training states, a network per feature size (warm-start modes) is trained with the
+    library's kernels, and a held-out channel is stepped from the same state with the zero,
+    previous-step and network guesses, for each precision of the Krylov matvecs (FP64;
+    FP32-Kahan sweeps inside FP64-accurate refinement -- whose FP64-accurate vesicle sums are
+    double-float direct sums, or the FMM with --residual-fmm; double-float).  The FP64 pair sum
+    is left out at N = 128,768, where one of its matvecs costs ~1.2 s."""
     import torch
     import paper_1510_05616_gb300 as P
     from paper_1510_05616_gb300 import build as B
@@ -356,16 +371,22 @@ def run_step(args):
     precs = [p for p in args.step_precisions.split(",") if p] or (
         ["fp32k", "df"] if big else ["fp64", "fp32k", "df"])
     collect_prec = names[args.collect_precision or ("fp32k" if big else "fp64")]
+    nets_modes = sorted({int(m) for m in args.step_modes.split(",") if m})
+    nm_max = max(nets_modes)
+    fmm = args.residual_fmm
+    hist = not args.no_warm_history
     res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10,
            "precisions": precs, "collect_precision": args.collect_precision or
-           ("fp32k" if big else "fp64")}
+           ("fp32k" if big else "fp64"), "warm_modes": nets_modes,
+           "residual_fmm_order": fmm, "history_features": hist}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
         g = I.channel(n_w, modes, nv, n_v, area, 1000 + r, mu=mu)
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        sim = WS.Simulation(g, kappa_b=kb, restart=200)
+        sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm,
+                            history=hist)
         torch.cuda.synchronize()
         res.setdefault("setup_s", time.perf_counter() - ts)
         res.setdefault("wall_solve", dict(zip(("refinements", "residual"),
@@ -377,28 +398,47 @@ def run_step(args):
         sim.close()
     X, T = torch.cat(Xs), torch.cat(Ts)
     res["collect_s"] = time.perf_counter() - t0
-    net = WS.WarmStartNet(hidden=256, seed=0)
-    t1 = time.perf_counter()
-    losses = net.fit(X, T, epochs=40, batch=256, lr=2e-3)
-    torch.cuda.synchronize()
-    res["train"] = {"samples": int(X.shape[0]), "epochs": 40, "batch": 256,
-                    "adam_steps": 40 * (int(X.shape[0]) // 256), "seconds": time.perf_counter() - t1,
-                    "loss_first": losses[0], "loss_last": losses[-1]}
+    nets, res["train"] = {}, {}
+    for nm in nets_modes:
+        fc, tc = (torch.as_tensor(c, device="cuda") for c in _mode_slice(nm_max, nm, hist))
+        Xm, Tm = X[:, fc].contiguous(), T[:, tc].contiguous()
+        net = WS.WarmStartNet(hidden=256, seed=0, modes=nm, history=hist)
+        t1 = time.perf_counter()
+        losses = net.fit(Xm, Tm, epochs=args.train_epochs, batch=256, lr=2e-3)
+        torch.cuda.synchronize()
+        res["train"][nm] = {"samples": int(Xm.shape[0]), "features": int(Xm.shape[1]),
+                            "targets": int(Tm.shape[1]), "epochs": args.train_epochs, "batch": 256,
+                            "adam_steps": args.train_epochs * (int(Xm.shape[0]) // 256),
+                            "seconds": time.perf_counter() - t1, "loss_first": losses[0],
+                            "loss_last": losses[-1]}
+        nets[nm] = net
+    del X, T, Xs, Ts
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
-    sim = WS.Simulation(g, kappa_b=kb, restart=200)
+    sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm, history=hist)
     x0, s0, _ = sim.state()
-    evs = {p: WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=net, precision=names[p])
-           for p in precs}
+    evs = {}
+    for p in precs:
+        ev = {}
+        for k, nm in enumerate(nets_modes):
+            P.stokes_sim_set_warm_modes(sim.h, nm)
+            gs = ("zero", "previous", "extrapolate", "mlp") if k == 0 else ("mlp",)
+            one = WS.evaluate(sim, x0, s0, args.steps, dt, pd, model=nets[nm], guesses=gs,
+                              precision=names[p])
+            one["mlp%d" % nm] = one.pop("mlp")
+            ev.update(one)
+        evs[p] = ev
     sim.close()
-    net.close()
+    for net in nets.values():
+        net.close()
     for p, ev in evs.items():
         res["eval_" + p] = ev
     head = evs[precs[0]]
     z = head["zero"]
 
     def summary(ev):
-        return {k: {"mean_iterations": v["mean_iterations"], "step_ms": v["step_ms"],
-                    "gmres_ms": v["gmres_ms"]} for k, v in ev.items()}
+        return {k: {kk: v[kk] for kk in ("mean_iterations", "step_ms", "gmres_ms",
+                                          "mean_refinements", "mean_accurate_residuals")}
+                for k, v in ev.items()}
 
     line = {"metric": "semi-implicit vesicle step, GMRES to 1e-10: mean iterations and ms per step",
             "value": z["step_ms"], "unit": "ms/step (zero guess, %s matvecs)" % precs[0],
@@ -406,7 +446,8 @@ def run_step(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESCS[args.step_workload], "vesicles": nv,
                        "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w,
-                       "training_states": int(X.shape[0])},
+                       "training_states": int(res["train"][nets_modes[0]]["samples"]),
+                       "warm_modes": nets_modes, "residual_fmm_order": fmm},
             "iterations_saved_vs_zero": {p: {k: ev["zero"]["mean_iterations"] - v["mean_iterations"]
                                              for k, v in ev.items()} for p, ev in evs.items()},
             "by_precision": {p: summary(ev) for p, ev in evs.items()},
@@ -758,6 +799,14 @@ def main():
     ap.add_argument("--collect-precision", default="", choices=["", "fp64", "fp32k", "df"])
     ap.add_argument("--train-runs", type=int, default=2)
     ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--step-modes", default="16",
+                    help="warm-start Fourier modes, one network each (e.g. 16,32)")
+    ap.add_argument("--no-warm-history", action="store_true",
+                    help="warm-start features without the previous solution and its last change")
+    ap.add_argument("--residual-fmm", type=int, default=0,
+                    help="FMM order of the FP64-accurate vesicle sums of FP32-Kahan steps "
+                         "(0: double-float direct sums)")
     ap.add_argument("--tune-file", default=None,
                     help="shapes file of the autotuner: loaded when it exists (no tuning), "
                          "else written after tuning")

@@ -222,9 +222,10 @@ STOKES_API int stokes_check_log64(stokes_ctx *ctx, const double *x, int n, doubl
  * stokes_fmm_create builds the plan (sorted image sources, cells, interaction and near lists)
  * for `ctx`'s current single-instance geometry on the host (synchronous), with the depth
  * chosen so that occupied leaves hold at most `leaf_size` sources on average; order in
- * [4, 30], leaf_size in [4, 4096] (STOKES_ERR_ARG outside; STOKES_ERR_NO_GEOM without a
- * geometry).  The plan stays valid until ctx's geometry is set again: stokes_fmm_eval then
- * returns STOKES_ERR_NO_GEOM.  stokes_fmm_eval takes the arguments of stokes_sum_eval (device
+ * [4, 40], leaf_size in [4, 4096] (STOKES_ERR_ARG outside; STOKES_ERR_NO_GEOM without a
+ * geometry).  The plan stays valid until ctx's geometry is set or updated again
+ * (stokes_geom_set, stokes_batch_set, stokes_geom_update): stokes_fmm_eval then returns
+ * STOKES_ERR_NO_GEOM.  stokes_fmm_eval takes the arguments of stokes_sum_eval (device
  * densities, out_velocity 2 N doubles, 16-byte aligned) and runs asynchronously on `stream`;
  * it uses ctx's packing and finishing buffers, so one context runs one evaluation at a time.
  * The caller owns the plan and destroys it before the context.
@@ -262,8 +263,8 @@ STOKES_API int stokes_fmm_destroy(stokes_fmm *fmm);
  * the trapezoid rule on K n resampled points (error ~ exp(-2 pi K delta / h)).  The pairs are
  * found on the host by stokes_close_create (synchronous) for ctx's current single-instance
  * geometry: factor in (0, 50], upsample K >= 1 with K n <= 4096 for the largest vesicle
- * (STOKES_ERR_ARG otherwise).  The plan stays valid until ctx's geometry is set again
- * (stokes_close_eval then returns STOKES_ERR_NO_GEOM).  stokes_close_eval takes the DEVICE
+ * (STOKES_ERR_ARG otherwise).  The plan stays valid until ctx's geometry is set or updated
+ * again (stokes_close_eval then returns STOKES_ERR_NO_GEOM).  stokes_close_eval takes the DEVICE
  * vesicle density of stokes_sum_eval and runs asynchronously on `stream`.
  * ------------------------------------------------------------------------------------------- */
 typedef struct stokes_close stokes_close;
@@ -546,9 +547,21 @@ typedef struct stokes_mlp stokes_mlp;
 typedef enum {
     STOKES_GUESS_ZERO = 0,      /* zero (the paper's plain method)                             */
     STOKES_GUESS_PREVIOUS = 1,  /* the previous step's solution                                */
-    STOKES_GUESS_MLP = 2,       /* previous solution + the network's predicted change           */
-    STOKES_GUESS_USER = 3       /* the caller's DEVICE vector `guess`                          */
+    STOKES_GUESS_MLP = 2,       /* base guess (stokes_sim_set_warm_base) + the network's
+                                   predicted change                                          */
+    STOKES_GUESS_USER = 3,      /* the caller's DEVICE vector `guess`                          */
+    STOKES_GUESS_EXTRAPOLATE = 4 /* 2 z_prev - z_prev2, linear extrapolation of the last two
+                                   solutions (the previous solution while only one exists)    */
 } stokes_guess;
+
+/* What the learned warm start's predicted change is added to (stokes_sim_set_warm_base). */
+typedef enum {
+    STOKES_WARM_BASE_PREVIOUS = 0,    /* z_prev (default): the network predicts z - z_prev     */
+    STOKES_WARM_BASE_EXTRAPOLATE = 1  /* 2 z_prev - z_prev2: the network predicts the second
+                                         difference z - 2 z_prev + z_prev2; until two solutions
+                                         exist the MLP guess is the previous solution and the
+                                         targets are first differences                        */
+} stokes_warm_base;
 
 typedef struct {
     int iterations;      /* GMRES iterations (matvecs inside the Krylov loop)            */
@@ -557,6 +570,9 @@ typedef struct {
     double gmres_ms;     /* Krylov solve                                                 */
     double total_ms;     /* whole step including the position update                    */
     int refinements;     /* FP32-Kahan refinement sweeps (STOKES_FP32_KAHAN steps), else 0 */
+    int accurate_residuals; /* FP64-accurate residuals of those sweeps (double-float or FMM) */
+    double fmm_plan_ms;  /* host time of this step's FMM plan (residual FMM on), else 0; it
+                            runs on a host thread beside the GPU's work                  */
 } stokes_step_stats;
 
 STOKES_API int stokes_sim_create(int device, stokes_sim **out);
@@ -597,6 +613,15 @@ STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
 /* Relative tolerance of each inner FP32-Kahan GMRES solve of a STOKES_FP32_KAHAN step
  * (1e-8..0.5, default 1e-3); the outer FP64-accurate refinement still ends at `tol`. */
 STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
+/* STOKES_FP32_KAHAN steps: take the FP64-accurate vesicle sums -- the right-hand side S f_b
+ * and every refinement residual -- from the fast multipole method (stokes_fmm_*, FP64
+ * expansions of `order`) instead of double-float direct sums, the paper's use of the FMM
+ * inside the step (Sec. 3.2).  order 0 turns it off (default); otherwise order in [4, 40] and
+ * leaf_size in [4, 4096].  The FMM's relative error (~0.48^order: ~1e-12 at order 36) must stay
+ * well below the step's tol, since it bounds how small a residual the refinement can certify.
+ * The plan is rebuilt each step (the geometry moves) by a host thread while the GPU computes
+ * the forces and the channel response.  Walls keep their double-float sums. */
+STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_size);
 /* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
 STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
                                            double *u_resp);
@@ -611,7 +636,8 @@ STOKES_API int stokes_sim_empty_channel_pressure(stokes_sim *sim, double p_drive
                                                  const double *v_walls, int n_targets,
                                                  const double *targets, double *p_out);
 /* One time step.  guess_mode is a stokes_guess; model is required for STOKES_GUESS_MLP
- * (n >= 16) and guess (DEVICE, 3 n V, layout above) for STOKES_GUESS_USER.  GMRES always runs
+ * (n >= the warm-start modes, dimensions as below) and guess (DEVICE, 3 n V, layout above) for
+ * STOKES_GUESS_USER.  GMRES always runs
  * to tol, so every guess only changes the iteration count, not the answer's tolerance. */
 STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive, int guess_mode,
                                       stokes_mlp *model, const double *guess, double tol,
@@ -619,16 +645,32 @@ STOKES_API int vesicle_step_warmstart(stokes_sim *sim, double dt, double p_drive
 /* Warm-start features and targets of the last step (DEVICE FP32; either may be NULL).  The
  * network predicts the change of the solution since the previous step (the learned guess is
  * z_prev + predicted change; z_prev = 0 and b_prev = 0 after stokes_sim_set_vesicles or
- * stokes_sim_set_state):
- * features (V x 64): per vesicle, in its principal-axes frame (centre c, angle theta of the
- *   second moments, length l = sqrt(A0 / pi)), the Fourier modes k = -8..7 (re, im) of the
- *   complex shape (x' + i y') / l, then of the change of the step's explicit velocity
+ * stokes_sim_set_state).  With nm the warm-start modes (stokes_sim_set_warm_modes, default 16):
+ * features (V x 4 nm): per vesicle, in its principal-axes frame (centre c, angle theta of the
+ *   second moments, length l = sqrt(A0 / pi)), the Fourier modes k = -nm/2..nm/2-1 (re, im)
+ *   of the complex shape (x' + i y') / l, then of the change of the step's explicit velocity
  *   (S f_b + u_resp) since the previous step, rotated to the frame, over U = kappa_B/(mu l^2);
- * targets (V x 48): modes k = -8..7 of the change of the solved velocity (frame, / U), then
- *   k = 0..7 of the change of the tension / (kappa_B / l^2). */
+ * targets (V x 3 nm): modes k = -nm/2..nm/2-1 of the change of the solved velocity (frame,
+ *   / U), then k = 0..nm/2-1 of the change of the tension / (kappa_B / l^2). */
 STOKES_API int stokes_sim_last_features(stokes_sim *sim, float *features, float *targets);
+/* Fourier modes nm of the warm-start features and targets: even, in [4, 64], at most the
+ * nodes per vesicle (STOKES_ERR_ARG otherwise).  Default 16 (features 64, targets 48); the
+ * paper-scale warm-start workload uses 32 (features 128, targets 96).  A network made for
+ * another nm is refused by STOKES_GUESS_MLP steps. */
+STOKES_API int stokes_sim_set_warm_modes(stokes_sim *sim, int modes);
+/* History features (on != 0; default off): the features also carry, after the 4 nm above, the
+ * previous solution z_prev and its change over the previous step (z_prev - z_prev2), both in
+ * this step's frame and in the target representation (3 nm each): 10 nm features in all.  The
+ * solution two steps back is reset with z_prev (set_vesicles, set_state) and made equal to it by
+ * stokes_sim_set_history, so the first step after either sees a zero previous change. */
+STOKES_API int stokes_sim_set_warm_history(stokes_sim *sim, int on);
+/* Base of the learned guess and of the targets (a stokes_warm_base; STOKES_ERR_ARG otherwise).
+ * Targets and network predictions are relative to this base, so a network must be trained and
+ * used with the same base. */
+STOKES_API int stokes_sim_set_warm_base(stokes_sim *sim, int base);
+STOKES_API int stokes_sim_get_warm_modes(const stokes_sim *sim, int *modes);
 
-/* Warm-start network: 64 -> H -> H -> 48 with SiLU, BF16 weights, FP32 accumulation, FP32
+/* Warm-start network: n_in -> H -> H -> n_out (4 nm -> H -> H -> 3 nm in the step) with SiLU, BF16 weights, FP32 accumulation, FP32
  * master parameters updated by Adam (flattened W1, b1, W2, b2, W3, b3; W row-major (out, in)),
  * input/output standardisation (mu_in, sd_in, mu_out, sd_out).  Host pointers for parameters
  * and normalisation; DEVICE FP32 pointers for data.  Synchronous. */
@@ -636,6 +678,9 @@ STOKES_API int stokes_mlp_create(int device, int n_in, int n_hidden, int n_out, 
 STOKES_API int stokes_mlp_destroy(stokes_mlp *mlp);
 STOKES_API int stokes_mlp_last_error(const stokes_mlp *mlp, char *buf, size_t len);
 STOKES_API int stokes_mlp_num_params(const stokes_mlp *mlp);
+/* The layer widths the network was created with (so callers can size the normalisation
+ * buffer: 2 (n_in + n_out) floats). */
+STOKES_API int stokes_mlp_get_dims(const stokes_mlp *mlp, int *n_in, int *n_hidden, int *n_out);
 STOKES_API int stokes_mlp_set_params(stokes_mlp *mlp, const float *theta);
 STOKES_API int stokes_mlp_get_params(stokes_mlp *mlp, float *theta);
 /* Adam state of the network (HOST float[n_params] first and second moments, step count), for

@@ -34,6 +34,9 @@ STOKES_GUESS_ZERO = 0
 STOKES_GUESS_PREVIOUS = 1
 STOKES_GUESS_MLP = 2
 STOKES_GUESS_USER = 3
+STOKES_GUESS_EXTRAPOLATE = 4
+STOKES_WARM_BASE_PREVIOUS = 0
+STOKES_WARM_BASE_EXTRAPOLATE = 1
 STOKES_WALLS_LU64 = 0
 STOKES_WALLS_LU32_REFINE = 1
 STOKES_WALLS_FDS = 2
@@ -97,6 +100,11 @@ _SIGNATURES = {
     "stokes_sim_set_block_refinement": [_vp, _c_int],
     "stokes_sim_set_precond_precision": [_vp, _c_int],
     "stokes_sim_set_inner_tolerance": [_vp, _c_double],
+    "stokes_sim_set_residual_fmm": [_vp, _c_int, _c_int],
+    "stokes_sim_set_warm_modes": [_vp, _c_int],
+    "stokes_sim_set_warm_history": [_vp, _c_int],
+    "stokes_sim_set_warm_base": [_vp, _c_int],
+    "stokes_sim_get_warm_modes": [_vp, ctypes.POINTER(_c_int)],
     "stokes_sim_empty_channel_pressure": [_vp, _c_double, _vp, _c_int, _vp, _vp],
     "stokes_sum_eval_pressure": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp],
     "stokes_sum_eval_traction": [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp],
@@ -112,6 +120,7 @@ _SIGNATURES = {
     "stokes_mlp_destroy": [_vp],
     "stokes_mlp_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_mlp_num_params": [_vp],
+    "stokes_mlp_get_dims": [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)],
     "stokes_mlp_set_params": [_vp, _vp],
     "stokes_mlp_get_params": [_vp, _vp],
     "stokes_mlp_set_normalization": [_vp, _vp],
@@ -523,7 +532,8 @@ def stokes_tune_clear():
 # ---------------------------------------------------------------------------
 class StepStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("residual", _c_double), ("setup_ms", _c_double),
-                ("gmres_ms", _c_double), ("total_ms", _c_double), ("refinements", _c_int)]
+                ("gmres_ms", _c_double), ("total_ms", _c_double), ("refinements", _c_int),
+                ("accurate_residuals", _c_int), ("fmm_plan_ms", _c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -654,6 +664,38 @@ def stokes_sim_set_inner_tolerance(h, tol):
     return _sim_check(h, load().stokes_sim_set_inner_tolerance(h, float(tol)))
 
 
+def stokes_sim_set_warm_modes(h, modes):
+    """Fourier modes nm of the warm-start features (4 nm) and targets (3 nm)."""
+    return _sim_check(h, load().stokes_sim_set_warm_modes(h, int(modes)))
+
+
+def stokes_sim_get_warm_modes(h) -> int:
+    v = _c_int()
+    _sim_check(h, load().stokes_sim_get_warm_modes(h, ctypes.byref(v)))
+    return int(v.value)
+
+
+def stokes_sim_set_warm_history(h, on=True):
+    """Features also carry the previous solution and its last change (10 nm features)."""
+    return _sim_check(h, load().stokes_sim_set_warm_history(h, int(bool(on))))
+
+
+def stokes_sim_set_warm_base(h, base):
+    """STOKES_WARM_BASE_PREVIOUS or STOKES_WARM_BASE_EXTRAPOLATE: what the learned change is
+    added to (and what the targets are relative to)."""
+    return _sim_check(h, load().stokes_sim_set_warm_base(h, int(base)))
+
+
+def feature_dims(modes: int, history: bool = False):
+    """(features, targets) per vesicle for `modes` warm-start modes (with history features)."""
+    return 4 * int(modes) + (6 * int(modes) if history else 0), 3 * int(modes)
+
+
+def stokes_sim_set_residual_fmm(h, order, leaf_size=32):
+    """FP32-Kahan steps: FP64-accurate vesicle sums by the FMM of `order` (0 = double-float)."""
+    return _sim_check(h, load().stokes_sim_set_residual_fmm(h, int(order), int(leaf_size)))
+
+
 def stokes_sim_wall_stats(h):
     """(refinement sweeps, relative residual) of the last wall solve."""
     a, b = _c_int(), _c_double()
@@ -735,6 +777,8 @@ def stokes_mlp_num_params(h):
 
 def stokes_mlp_set_params(h, theta):
     a, p = _host(theta, "theta", "float32")
+    if a.size != stokes_mlp_num_params(h):
+        raise StokesError(STOKES_ERR_ARG, "theta must hold %d floats" % stokes_mlp_num_params(h))
     return _mlp_check(h, load().stokes_mlp_set_params(h, p))
 
 
@@ -747,12 +791,27 @@ def stokes_mlp_get_params(h):
 
 def stokes_mlp_set_normalization(h, norm):
     a, p = _host(norm, "norm", "float32")
+    d_in, _, d_out = stokes_mlp_get_dims(h)
+    if a.size != 2 * (d_in + d_out):
+        raise StokesError(STOKES_ERR_ARG, "norm must hold 2 (n_in + n_out) = %d floats"
+                          % (2 * (d_in + d_out)))
     return _mlp_check(h, load().stokes_mlp_set_normalization(h, p))
 
 
-def stokes_mlp_get_normalization(h, n_in=N_FEATURES, n_out=N_TARGETS):
+def stokes_mlp_get_dims(h):
+    """(n_in, n_hidden, n_out) of the network."""
+    a, b, c = _c_int(), _c_int(), _c_int()
+    _mlp_check(h, load().stokes_mlp_get_dims(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def stokes_mlp_get_normalization(h, n_in=None, n_out=None):
+    """(mu_in, sd_in, mu_out, sd_out) concatenated; the sizes come from the network itself."""
     import numpy as np
-    out = np.zeros(2 * (n_in + n_out), dtype=np.float32)
+    d_in, _, d_out = stokes_mlp_get_dims(h)
+    if (n_in is not None and n_in != d_in) or (n_out is not None and n_out != d_out):
+        raise StokesError(STOKES_ERR_ARG, "the network maps %d -> %d" % (d_in, d_out))
+    out = np.zeros(2 * (d_in + d_out), dtype=np.float32)
     _mlp_check(h, load().stokes_mlp_get_normalization(h, _vp(out.ctypes.data)))
     return out
 
@@ -817,6 +876,8 @@ def stokes_mlp_set_adam(h, m, v, t):
     import numpy as np
     mm = np.ascontiguousarray(m, dtype=np.float32)
     vv = np.ascontiguousarray(v, dtype=np.float32)
+    if mm.size != stokes_mlp_num_params(h) or vv.size != mm.size:
+        raise StokesError(STOKES_ERR_ARG, "Adam moments must hold %d floats each" % stokes_mlp_num_params(h))
     return _mlp_check(h, load().stokes_mlp_set_adam(h, _vp(mm.ctypes.data), _vp(vv.ctypes.data),
                                                     int(t)))
 

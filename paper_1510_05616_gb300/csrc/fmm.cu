@@ -41,7 +41,7 @@ namespace {
 
 constexpr double kPiF = 3.14159265358979323846;
 constexpr int kSets = 6;
-constexpr int kMaxOrder = 30;               // expansion order p <= kMaxOrder
+constexpr int kMaxOrder = 40;               // expansion order p <= kMaxOrder
 constexpr int kBin = 2 * kMaxOrder + 2;     // binomials C(n, k), n < kBin
 constexpr int kLeafThreads = 128;
 
@@ -130,8 +130,10 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
   const int p = f.p, p1 = p + 1;
   const int t = threadIdx.x;
   const int set = t / p1, k = t - set * p1;
-  __shared__ double2 pw[kP2mChunk][kMaxOrder + 1];
-  __shared__ double2 sc[kP2mChunk][kSets];
+  // dynamic shared memory (p2m_smem): pw[kP2mChunk][p + 1], then sc[kP2mChunk][kSets]
+  extern __shared__ double2 dyn_p2m[];
+  double2 *pw = dyn_p2m;
+  double2(*sc)[kSets] = reinterpret_cast<double2(*)[kSets]>(dyn_p2m + kP2mChunk * p1);
   double2 acc = make_double2(0.0, 0.0);
   for (int j0 = rg.x; j0 < rg.y; j0 += kP2mChunk) {
     const int nj = min(kP2mChunk, rg.y - j0);
@@ -146,13 +148,13 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
       for (int s = 0; s < kSets; ++s) sc[t][s] = c[s];
       double2 uk = make_double2(1.0, 0.0);
       for (int n = 0; n <= p; ++n) {
-        pw[t][n] = uk;
+        pw[t * p1 + n] = uk;
         uk = cmul(uk, u);
       }
     }
     __syncthreads();
     if (set < kSets)
-      for (int j = 0; j < nj; ++j) acc = cfma(sc[j][set], pw[j][k], acc);
+      for (int j = 0; j < nj; ++j) acc = cfma(sc[j][set], pw[j * p1 + k], acc);
   }
   if (set < kSets) f.M[(size_t(cell) * kSets + set) * p1 + k] = k == 0 ? acc : cscale(acc, -1.0 / k);
 }
@@ -169,16 +171,18 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
   const int set = t / p1, q = t - set * p1;
   const int nch = ch.y - ch.x;  // 1..4
   const double inv_q = q > 0 ? 1.0 / q : 0.0;
-  __shared__ double2 sa[4][kSets * (kMaxOrder + 1)];
-  __shared__ double2 sp[4][kMaxOrder + 1];
-  __shared__ double bm[kMaxOrder * kMaxOrder];  // C(q - 1, k - 1) 2^-k, row q - 1, k = 1..p
+  // dynamic shared memory (m2m_smem): sa[4][np], sp[4][p + 1], then
+  // bm[p * p] = C(q - 1, k - 1) 2^-k, row q - 1, k = 1..p
+  extern __shared__ double2 dyn_m2m[];
+  double2 *sa = dyn_m2m, *sp = dyn_m2m + 4 * np;
+  double *bm = reinterpret_cast<double *>(sp + 4 * p1);
   for (int i = t; i < p * p; i += blockDim.x) {
     const int qq = i / p, k = i - qq * p + 1;
     bm[i] = c_binom[qq][k - 1] * ldexp(1.0, -k);
   }
   for (int i = t; i < nch * np; i += blockDim.x) {
     const int c = i / np, r = i - c * np;
-    sa[c][r] = f.M[size_t(ch.x + c) * np + r];
+    sa[c * np + r] = f.M[size_t(ch.x + c) * np + r];
   }
   for (int i = t; i < nch * p1; i += blockDim.x) {
     const int c = i / p1, n = i - c * p1;
@@ -186,19 +190,20 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
     // the child centre sits a quarter of the parent side away along each axis
     const double2 d = make_double2(cc.x - ctr.x, cc.y - ctr.y);
     const double hp = 4.0 * fabs(d.x);
-    sp[c][n] = cpow(make_double2(d.x / hp, d.y / hp), n);
+    sp[c * p1 + n] = cpow(make_double2(d.x / hp, d.y / hp), n);
   }
   __syncthreads();
   if (set >= kSets) return;
   double2 acc = make_double2(0.0, 0.0);
   for (int c = 0; c < nch; ++c) {
-    const double2 *a = sa[c] + set * p1;
+    const double2 *a = sa + c * np + set * p1;
+    const double2 *spc = sp + c * p1;
     if (q == 0) {
       acc = cadd(acc, a[0]);
     } else {
-      double2 v = cscale(cmul(a[0], sp[c][q]), -inv_q);
+      double2 v = cscale(cmul(a[0], spc[q]), -inv_q);
       const double *B = bm + (q - 1) * p;
-      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(sp[c][q - k], B[k - 1]), v);
+      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(spc[q - k], B[k - 1]), v);
       acc = cadd(acc, v);
     }
   }
@@ -219,10 +224,11 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   const int t = threadIdx.x;
   const int set = t / p1, q = t - set * p1;
   const double inv_h = 1.0 / h, inv_q = q > 0 ? 1.0 / q : 0.0;  // no divisions in the loops
-  __shared__ double2 sw[kM2lBatch][kSets * (kMaxOrder + 1)];
-  __shared__ double2 stq[kM2lBatch][kMaxOrder + 1];
-  __shared__ double2 slog[kM2lBatch];
-  __shared__ double bq[(kMaxOrder + 1) * kMaxOrder];  // C(q + k - 1, k - 1), row q, k = 1..p
+  // dynamic shared memory (m2l_smem): sw[kM2lBatch][np], stq[kM2lBatch][p + 1],
+  // slog[kM2lBatch], then bq[(p + 1) * p] = C(q + k - 1, k - 1), row q, k = 1..p
+  extern __shared__ double2 dyn_m2l[];
+  double2 *sw = dyn_m2l, *stq = sw + kM2lBatch * np, *slog = stq + kM2lBatch * p1;
+  double *bq = reinterpret_cast<double *>(slog + kM2lBatch);
   for (int i = t; i < p1 * p; i += blockDim.x) {
     const int qq = i / p, k = i - qq * p + 1;
     bq[i] = c_binom[qq + k - 1][k - 1];
@@ -232,13 +238,13 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   if (par >= 0) {  // L2L: stage the parent's locals and the powers of the offset
     const double2 cp = f.tcell_ctr[par];
     const double2 s = make_double2((ct.x - cp.x) * (0.5 * inv_h), (ct.y - cp.y) * (0.5 * inv_h));  // parent side 2h
-    for (int i = t; i < np; i += blockDim.x) sw[0][i] = f.Lc[size_t(par) * np + i];
-    if (t <= p) stq[0][t] = cpow(s, t);
+    for (int i = t; i < np; i += blockDim.x) sw[i] = f.Lc[size_t(par) * np + i];
+    if (t <= p) stq[t] = cpow(s, t);
     __syncthreads();
     if (set < kSets) {
-      const double2 *b = sw[0] + set * p1;
+      const double2 *b = sw + set * p1;
       double2 v = make_double2(0.0, 0.0);
-      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(stq[0][k - q], c_binom[k][q]), v);
+      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(stq[k - q], c_binom[k][q]), v);
       acc = cscale(v, ldexp(1.0, -q));
     }
   }
@@ -258,9 +264,9 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       // off the table (roots only) the offset is an integer pair as well: use it exactly
       const double2 T = tab ? f.tpow[ti * p1 + qi] : cpow(cinv(make_double2(dx, dy)), qi);
       const double2 a = f.M[size_t(sc) * np + r];
-      sw[el][r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
+      sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
       if (si == 0) {
-        stq[el][qi] = T;
+        stq[el * p1 + qi] = T;
         if (qi == 0)
           slog[el] = tab ? f.tlog[ti]
                          : make_double2(0.5 * log(double(dx) * dx + double(dy) * dy), atan2(-double(dy), -double(dx)));
@@ -270,7 +276,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
     if (set < kSets) {
       const double *B = bq + q * p;
       for (int el = 0; el < nb; ++el) {
-        const double2 *w = sw[el] + set * p1;
+        const double2 *w = sw + el * np + set * p1;
         double vx = 0.0, vy = 0.0;
         for (int k = 1; k <= p; ++k) {
           vx = fma(B[k - 1], w[k].x, vx);
@@ -280,7 +286,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
           acc = cadd(acc, cadd(cmul(w[0], make_double2(slog[el].x + log_h, slog[el].y)),
                                make_double2(vx, vy)));
         else
-          acc = cfma(make_double2(fma(-w[0].x, inv_q, vx), fma(-w[0].y, inv_q, vy)), stq[el][q], acc);
+          acc = cfma(make_double2(fma(-w[0].x, inv_q, vx), fma(-w[0].y, inv_q, vy)), stq[el * p1 + q], acc);
       }
     }
   }
@@ -964,14 +970,19 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const int nthr = std::max(kLeafThreads, (kSets * (f->p + 1) + 31) / 32 * 32);
   auto hl = [&](int l) { return f->S / double(1 << l); };
   const int nleaf_s = f->sc_off[L + 1] - f->sc_off[L];
-  if (nleaf_s > 0) p2m_kernel<<<nleaf_s, nthr, 0, s>>>(d, f->sc_off[L], hl(L));
+  const int p1 = f->p + 1, np = kSets * p1;
+  const size_t p2m_smem = sizeof(double2) * (kP2mChunk * p1 + kP2mChunk * kSets);
+  const size_t m2m_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(double) * f->p * f->p;
+  const size_t m2l_smem =
+      sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + sizeof(double) * p1 * f->p;
+  if (nleaf_s > 0) p2m_kernel<<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
   for (int l = L - 1; l >= 0; --l) {
     const int nc = f->sc_off[l + 1] - f->sc_off[l];
-    if (nc > 0) m2m_kernel<<<nc, nthr, 0, s>>>(d, f->sc_off[l]);
+    if (nc > 0) m2m_kernel<<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
   }
   for (int l = 0; l <= L; ++l) {
     const int nc = f->tc_off[l + 1] - f->tc_off[l];
-    if (nc > 0) m2l_kernel<<<nc, nthr, 0, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+    if (nc > 0) m2l_kernel<<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
   }
   if (f->n_tleaf > 0) leaf_kernel<<<f->n_tleaf, kLeafThreads, 0, s>>>(d, f->tc_off[L], 0, hl(L));
   if (c->n_ves_curves > 0) {

@@ -369,6 +369,14 @@ int stokes_mlp_last_error(const stokes_mlp *m, char *buf, size_t len) {
 
 int stokes_mlp_num_params(const stokes_mlp *m) { return m ? m->n_params : 0; }
 
+int stokes_mlp_get_dims(const stokes_mlp *m, int *n_in, int *n_hidden, int *n_out) {
+  if (!m || !n_in || !n_hidden || !n_out) return STOKES_ERR_ARG;
+  *n_in = m->n_in;
+  *n_hidden = m->H;
+  *n_out = m->n_out;
+  return STOKES_OK;
+}
+
 int stokes_mlp_set_params(stokes_mlp *m, const float *theta_host) {
   if (!m || !theta_host) return STOKES_ERR_ARG;
   MK(cudaSetDevice(m->device));

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <thread>
 #include <vector>
 
 #include "fds.cuh"
@@ -105,9 +106,19 @@ struct stokes_sim {
   double *d_xsol = nullptr;            // last solution [u_x, u_y, sigma] per vesicle
   double *d_rr = nullptr, *d_dd = nullptr;  // refinement residual and correction
   // warm-start features / targets of the last step
-  float *d_feat = nullptr, *d_targ = nullptr, *d_pred = nullptr;
+  float *d_feat = nullptr, *d_targ = nullptr, *d_pred = nullptr;  // sized for the most modes
+  int warm_modes = 16;                 // Fourier modes of the warm-start representation
+  bool warm_history = false;           // features also carry z_prev and z_prev - z_prev2
+  int warm_base = 0;                   // STOKES_WARM_BASE_*: what the network's change is added to
+  int hist_count = 0;                  // solutions in the history: z_prev valid at 1, z_prev2 at 2
+  double *d_zprev2 = nullptr;          // the solution two steps back
   double *d_frame = nullptr;           // per vesicle: cx, cy, theta, l, U, sigma scale
   double *d_bprev = nullptr, *d_zprev = nullptr;  // previous step's right-hand side and solution
+  // mixed-precision step: the FP64-accurate vesicle sums (right-hand side S f_b and the
+  // refinement residuals) by the FMM of order resid_fmm_order instead of double-float direct
+  // sums (0 = off); the plan is rebuilt every step on a host thread beside the GPU's work
+  int resid_fmm_order = 0, resid_fmm_leaf = 32;
+  stokes_fmm *fmm_v = nullptr;
 };
 
 namespace {
@@ -734,8 +745,19 @@ __global__ void pc_fill_kernel(int n, const double *Ds, const double2 *xs, doubl
 // ---------------------------------------------------------------------------
 // warm-start features, targets and guesses (per vesicle, principal-axes frame)
 // ---------------------------------------------------------------------------
-constexpr int kModes = 16;  // Fourier modes k = -8..7
-constexpr int kFeat = 64, kTarg = 48;
+// Fourier modes of the warm-start representation: nm modes k = -nm/2 .. nm/2 - 1 of the shape
+// and of the change of the explicit velocity (features: 4 nm reals), nm modes of the change of
+// u and the modes k = 0 .. nm/2 - 1 of the change of sigma (targets: 3 nm reals).  nm is even,
+// in [4, kMaxModes] and at most the nodes per vesicle (16 by default; 32 in the paper-scale
+// workload definition).
+constexpr int kDefaultModes = 16;
+constexpr int kMaxModes = 64;
+__host__ __device__ inline int targ_dim(int nm) { return 3 * nm; }
+// features: shape and velocity-change modes (4 nm), with history also the previous solution and
+// the previous step's change of it in the target representation (2 x 3 nm)
+__host__ __device__ inline int feat_dim(int nm, bool hist = false) {
+  return 4 * nm + (hist ? 2 * targ_dim(nm) : 0);
+}
 
 // Frame of one vesicle from its nodes in shared memory: centre, angle of the second moments'
 // major axis, length l = sqrt(A0 / pi), velocity scale U = kB / (mu l^2), tension scale kB / l^2.
@@ -778,9 +800,28 @@ __device__ void dft_mode(int n, int k, const double *re, const double *im, doubl
   out[1] = si / n;
 }
 
-__global__ void ves_features_kernel(int n, const double2 *x, const double *b, const double *bprev,
-                                    const double *A0, double kb, double mu, double *frame,
-                                    float *feat) {
+// Modes of a solution-like vector (u_x, u_y, sigma per node, staged as frame-rotated u / U in
+// (UR, UI) and sigma / (kappa_B / l^2) in SG) in the target representation, written to out.
+__device__ void solution_modes(int n, int nm, int a, const double *UR, const double *UI,
+                               const double *SG, const double *ZERO, float *out) {
+  for (int q = a; q < nm + nm / 2; q += n) {
+    double o[2];
+    if (q < nm) {
+      dft_mode(n, q - nm / 2, UR, UI, o);
+      out[2 * q] = float(o[0]);
+      out[2 * q + 1] = float(o[1]);
+    } else {
+      dft_mode(n, q - nm, SG, ZERO, o);
+      out[2 * nm + 2 * (q - nm)] = float(o[0]);
+      out[2 * nm + 2 * (q - nm) + 1] = float(o[1]);
+    }
+  }
+}
+
+__global__ void ves_features_kernel(int n, int nm, const double2 *x, const double *b,
+                                    const double *bprev, const double *zprev,
+                                    const double *zprev2, int two_back, const double *A0,
+                                    double kb, double mu, double *frame, float *feat) {
   __shared__ double X[kMaxN], Y[kMaxN], ZR[kMaxN], ZI[kMaxN], WR[kMaxN], WI[kMaxN];
   __shared__ double fr[6];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
@@ -798,68 +839,97 @@ __global__ void ves_features_kernel(int n, const double2 *x, const double *b, co
   WR[a] = (c * dbx + s * dby) / fr[4];
   WI[a] = (-s * dbx + c * dby) / fr[4];
   __syncthreads();
-  if (a < kModes) {
+  const bool hist = zprev != nullptr;
+  const int F = feat_dim(nm, hist);
+  float *fv = feat + size_t(v) * F;
+  for (int q = a; q < nm; q += n) {
     double o[2];
-    dft_mode(n, a - 8, ZR, ZI, o);
-    feat[size_t(v) * kFeat + 2 * a] = float(o[0]);
-    feat[size_t(v) * kFeat + 2 * a + 1] = float(o[1]);
-    dft_mode(n, a - 8, WR, WI, o);
-    feat[size_t(v) * kFeat + 32 + 2 * a] = float(o[0]);
-    feat[size_t(v) * kFeat + 32 + 2 * a + 1] = float(o[1]);
+    dft_mode(n, q - nm / 2, ZR, ZI, o);
+    fv[2 * q] = float(o[0]);
+    fv[2 * q + 1] = float(o[1]);
+    dft_mode(n, q - nm / 2, WR, WI, o);
+    fv[2 * nm + 2 * q] = float(o[0]);
+    fv[2 * nm + 2 * q + 1] = float(o[1]);
+  }
+  if (hist) {
+    // the previous solution, then its change over the previous step, in this step's frame
+    const double *z1 = zprev + size_t(3) * n * v, *z2 = zprev2 + size_t(3) * n * v;
+    for (int pass = 0; pass < 2; ++pass) {
+      __syncthreads();  // ZR..WI are reused as the staging arrays
+      // the previous change needs two solutions in the history; with fewer it is zero
+      const double g = pass ? double(two_back) : 0.0;
+      const double ux = z1[a] - g * z2[a] - (pass && !two_back ? z1[a] : 0.0);
+      const double uy = z1[n + a] - g * z2[n + a] - (pass && !two_back ? z1[n + a] : 0.0);
+      ZR[a] = (c * ux + s * uy) / fr[4];
+      ZI[a] = (-s * ux + c * uy) / fr[4];
+      WR[a] = (z1[2 * n + a] - g * z2[2 * n + a] - (pass && !two_back ? z1[2 * n + a] : 0.0)) / fr[5];
+      WI[a] = 0.0;
+      __syncthreads();
+      solution_modes(n, nm, a, ZR, ZI, WR, WI, fv + 4 * nm + pass * targ_dim(nm));
+    }
   }
   if (a < 6) frame[v * 6 + a] = fr[a];
 }
 
-__global__ void ves_targets_kernel(int n, const double *z, const double *zprev, const double *frame,
+// Base guess of the learned warm start at node component j of vesicle v: z_prev, plus the
+// previous change z_prev - z_prev2 when extrapolating (ext = 1).
+__device__ __forceinline__ double base_guess(const double *zp, const double *zp2, int ext,
+                                             size_t j) {
+  return ext ? 2.0 * zp[j] - zp2[j] : zp[j];
+}
+
+// Targets: modes of z - (base guess) in the vesicle's frame.
+__global__ void ves_targets_kernel(int n, int nm, const double *z, const double *zprev,
+                                   const double *zprev2, int ext, const double *frame,
                                    float *targ) {
   __shared__ double UR[kMaxN], UI[kMaxN], SG[kMaxN], ZERO[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x;
   const double *fr = frame + v * 6;
   const double c = cos(fr[2]), s = sin(fr[2]);
-  const double *zv = z + size_t(3) * n * v, *pv = zprev + size_t(3) * n * v;
-  const double dux = zv[a] - pv[a], duy = zv[n + a] - pv[n + a];
+  const size_t o = size_t(3) * n * v;
+  const double *zv = z + o;
+  const double dux = zv[a] - base_guess(zprev, zprev2, ext, o + a);
+  const double duy = zv[n + a] - base_guess(zprev, zprev2, ext, o + n + a);
   UR[a] = (c * dux + s * duy) / fr[4];
   UI[a] = (-s * dux + c * duy) / fr[4];
-  SG[a] = (zv[2 * n + a] - pv[2 * n + a]) / fr[5];
+  SG[a] = (zv[2 * n + a] - base_guess(zprev, zprev2, ext, o + 2 * n + a)) / fr[5];
   ZERO[a] = 0.0;
   __syncthreads();
-  double o[2];
-  if (a < kModes) {
-    dft_mode(n, a - 8, UR, UI, o);
-    targ[size_t(v) * kTarg + 2 * a] = float(o[0]);
-    targ[size_t(v) * kTarg + 2 * a + 1] = float(o[1]);
-  } else if (a < kModes + 8) {
-    dft_mode(n, a - kModes, SG, ZERO, o);
-    targ[size_t(v) * kTarg + 32 + 2 * (a - kModes)] = float(o[0]);
-    targ[size_t(v) * kTarg + 32 + 2 * (a - kModes) + 1] = float(o[1]);
-  }
+  solution_modes(n, nm, a, UR, UI, SG, ZERO, targ + size_t(v) * targ_dim(nm));
 }
 
 // Inverse of the targets' representation: z = z_prev + (predicted change at the nodes).
-__global__ void ves_guess_kernel(int n, const float *pred, const double *frame, const double *zprev,
-                                 double *z) {
+__global__ void ves_guess_kernel(int n, int nm, const float *pred, const double *frame,
+                                 const double *zprev, const double *zprev2, int ext, double *z) {
   const int v = blockIdx.x, a = threadIdx.x;
   const double *fr = frame + v * 6;
-  const float *p = pred + size_t(v) * kTarg;
+  const float *p = pred + size_t(v) * targ_dim(nm);
   const double al = 2.0 * kPiD * a / n;
   double ur = 0, ui = 0, sg = 0;
-  for (int q = 0; q < kModes; ++q) {
+  for (int q = 0; q < nm; ++q) {
     double sn, cs;
-    sincos((q - 8) * al, &sn, &cs);
+    sincos((q - nm / 2) * al, &sn, &cs);
     ur += p[2 * q] * cs - p[2 * q + 1] * sn;
     ui += p[2 * q] * sn + p[2 * q + 1] * cs;
   }
-  for (int q = 0; q < 8; ++q) {
+  const float *ps = p + 2 * nm;
+  for (int q = 0; q < nm / 2; ++q) {
     double sn, cs;
     sincos(q * al, &sn, &cs);
-    sg += (q == 0 ? 1.0 : 2.0) * (p[32 + 2 * q] * cs - p[32 + 2 * q + 1] * sn);
+    sg += (q == 0 ? 1.0 : 2.0) * (ps[2 * q] * cs - ps[2 * q + 1] * sn);
   }
   const double c = cos(fr[2]), s = sin(fr[2]);
-  double *zv = z + size_t(3) * n * v;
-  const double *pv = zprev + size_t(3) * n * v;
-  zv[a] = pv[a] + fr[4] * (c * ur - s * ui);
-  zv[n + a] = pv[n + a] + fr[4] * (s * ur + c * ui);
-  zv[2 * n + a] = pv[2 * n + a] + fr[5] * sg;
+  const size_t o = size_t(3) * n * v;
+  double *zv = z + o;
+  zv[a] = base_guess(zprev, zprev2, ext, o + a) + fr[4] * (c * ur - s * ui);
+  zv[n + a] = base_guess(zprev, zprev2, ext, o + n + a) + fr[4] * (s * ur + c * ui);
+  zv[2 * n + a] = base_guess(zprev, zprev2, ext, o + 2 * n + a) + fr[5] * sg;
+}
+
+// z = 2 z_prev - z_prev2 (linear extrapolation of the last two solutions).
+__global__ void extrapolate_kernel(long len, const double *zprev, const double *zprev2, double *z) {
+  for (long i = blockIdx.x * long(blockDim.x) + threadIdx.x; i < len; i += long(gridDim.x) * blockDim.x)
+    z[i] = 2.0 * zprev[i] - zprev2[i];
 }
 
 __global__ void extract_sigma_kernel(int n, const double *z, double *sigma) {
@@ -1114,6 +1184,60 @@ int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, doub
   return STOKES_OK;
 }
 
+// step_matvec with the vesicle sum by the step's FMM plan (FP64 expansions of order
+// resid_fmm_order: FP64-accurate to the expansion error).
+int step_matvec_fmm(stokes_sim *m, double dt, const double *zin, double *zout) {
+  ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
+                                             m->d_tmp2);
+  SK(cudaGetLastError());
+  const int st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
+                                 0.0, reinterpret_cast<double *>(m->d_tmp3), m->s);
+  if (st) {
+    char buf[256];
+    stokes_fmm_last_error(m->fmm_v, buf, sizeof(buf));
+    return fail(m, st, "FMM residual: %s", buf);
+  }
+  ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
+                                              zout);
+  SK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+// The FMM plan of the vesicles' current geometry, built by a host thread while the stream
+// runs the step's other work (the plan reads the geometry with synchronous copies, so the
+// geometry update must be complete when it starts).  The destructor joins the thread and
+// destroys a plan nobody took.
+struct FmmPlanJob {
+  std::thread th;
+  stokes_fmm *plan = nullptr;
+  int status = STOKES_OK;
+  double ms = 0.0;
+  void start(stokes_sim *m) {
+    th = std::thread([this, m] {
+      const auto t0 = std::chrono::steady_clock::now();
+      if (cudaSetDevice(m->device) != cudaSuccess) {
+        status = STOKES_ERR_CUDA;
+        return;
+      }
+      status = stokes_fmm_create(m->ctx_v, m->resid_fmm_order, m->resid_fmm_leaf, &plan);
+      ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    });
+  }
+  int join() {
+    if (th.joinable()) th.join();
+    return status;
+  }
+  stokes_fmm *take() {
+    stokes_fmm *p = plan;
+    plan = nullptr;
+    return p;
+  }
+  ~FmmPlanJob() {
+    join();
+    if (plan) stokes_fmm_destroy(plan);
+  }
+};
+
 int precond_apply(stokes_sim *m, const double *zin, double *zout) {
   const int k = 3 * m->n;
   if (m->precond_fp32) {
@@ -1300,6 +1424,8 @@ void free_walls(stokes_sim *m) {
 }
 
 void free_vesicles(stokes_sim *m) {
+  if (m->fmm_v) stokes_fmm_destroy(m->fmm_v);
+  m->fmm_v = nullptr;
   if (m->ctx_v) stokes_destroy(m->ctx_v);
   m->ctx_v = nullptr;
   double2 **p2[] = {&m->d_x, &m->d_nrm, &m->d_xs, &m->d_f, &m->d_fb, &m->d_ures, &m->d_tmp2, &m->d_tmp3};
@@ -1314,6 +1440,7 @@ void free_vesicles(stokes_sim *m) {
   dfree(m->d_frame);
   dfree(m->d_bprev);
   dfree(m->d_zprev);
+  dfree(m->d_zprev2);
   dfree(m->d_Pptr);
   dfree(m->d_Piptr);
   dfree(m->d_P32);
@@ -1640,16 +1767,19 @@ int stokes_sim_set_vesicles(stokes_sim *m, int V, int n, const double *x, double
   SK(dalloc(m->d_rr, len));
   SK(dalloc(m->d_dd, len));
   SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
-  SK(dalloc(m->d_feat, size_t(V) * kFeat));
-  SK(dalloc(m->d_targ, size_t(V) * kTarg));
-  SK(dalloc(m->d_pred, size_t(V) * kTarg));
+  SK(dalloc(m->d_feat, size_t(V) * feat_dim(kMaxModes, true)));
+  SK(dalloc(m->d_targ, size_t(V) * targ_dim(kMaxModes)));
+  SK(dalloc(m->d_pred, size_t(V) * targ_dim(kMaxModes)));
   SK(dalloc(m->d_frame, size_t(V) * 6));
   SK(dalloc(m->d_bprev, len));
   SK(dalloc(m->d_zprev, len));
+  SK(dalloc(m->d_zprev2, len));
   SK(cudaMemsetAsync(m->d_bprev, 0, sizeof(double) * len, m->s));
   SK(cudaMemsetAsync(m->d_zprev, 0, sizeof(double) * len, m->s));
+  SK(cudaMemsetAsync(m->d_zprev2, 0, sizeof(double) * len, m->s));
   SK(cudaStreamSynchronize(m->s));
   m->have_ves = true;
+  m->hist_count = 0;
   return STOKES_OK;
 }
 
@@ -1803,15 +1933,18 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
                            int precision, stokes_step_stats *out) {
   if (!m) return STOKES_ERR_ARG;
   if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
-  if (guess_mode < STOKES_GUESS_ZERO || guess_mode > STOKES_GUESS_USER)
+  if (guess_mode < STOKES_GUESS_ZERO || guess_mode > STOKES_GUESS_EXTRAPOLATE)
     return fail(m, STOKES_ERR_ARG, "unknown guess mode %d", guess_mode);
   if (guess_mode == STOKES_GUESS_USER && !guess) return fail(m, STOKES_ERR_ARG, "guess is NULL");
   if (guess_mode == STOKES_GUESS_MLP) {
     if (!model) return fail(m, STOKES_ERR_ARG, "model is NULL");
     int ni = 0, no = 0;
     mlp_dims(model, &ni, &no);
-    if (ni != kFeat || no != kTarg || m->n < kModes)
-      return fail(m, STOKES_ERR_ARG, "model must map %d features to %d targets (n >= %d)", kFeat, kTarg, kModes);
+    const int nm = m->warm_modes;
+    const int nf = feat_dim(nm, m->warm_history);
+    if (ni != nf || no != targ_dim(nm) || m->n < nm)
+      return fail(m, STOKES_ERR_ARG, "model must map %d features to %d targets (%d modes, n >= %d)",
+                  nf, targ_dim(nm), nm, nm);
   }
   if (!(dt > 0.0) || !(tol > 0.0) || max_iter < 1)
     return fail(m, STOKES_ERR_ARG, "need dt > 0, tol > 0, max_iter >= 1");
@@ -1821,15 +1954,27 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   // hp: the precision of every sum that must be FP64-accurate (right-hand side, channel
   // response, residuals): FP64 itself, or double-float for the two faster modes
   const int hp = precision == STOKES_FP64 ? STOKES_FP64 : STOKES_DOUBLE_FLOAT;
+  // mixed precision with FMM residuals: the vesicle sums of the right-hand side and of the
+  // refinement residuals go through this step's FMM plan
+  const bool use_fmm = precision == STOKES_FP32_KAHAN && m->resid_fmm_order > 0;
   SK(cudaSetDevice(m->device));
   const auto t0 = std::chrono::steady_clock::now();
   const int V = m->V, n = m->n;
   const long len = 3L * m->Nv;
+  if (m->fmm_v) {  // last step's plan: its geometry is gone
+    stokes_fmm_destroy(m->fmm_v);
+    m->fmm_v = nullptr;
+  }
   // geometry at x^k (weights/normals feed the sums)
   ves_geom_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D, m->d_spd, m->d_xs, m->d_nrm, m->d_w);
   SK(cudaGetLastError());
   ST(stokes_geom_update(m->ctx_v, reinterpret_cast<double *>(m->d_x), m->d_w,
                         reinterpret_cast<double *>(m->d_nrm), nullptr, m->s));
+  FmmPlanJob plan_job;
+  if (use_fmm) {
+    SK(cudaStreamSynchronize(m->s));  // the plan thread reads the updated geometry
+    plan_job.start(m);
+  }
   // step 2: forces
   ves_forces_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_sigma, m->d_D, m->d_spd, m->d_xs, m->kappa_b,
                                        m->d_fb, m->d_f);
@@ -1837,25 +1982,47 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   // steps 3-5: channel response of the explicit forces
   if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp));
   // right-hand side [S f_b + u_resp; ALC]
-  ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
-                     reinterpret_cast<double *>(m->d_tmp3), m->s));
+  double plan_ms = 0.0;
+  if (use_fmm) {
+    const int pst = plan_job.join();
+    if (pst) return fail(m, pst, "FMM plan of the vesicles failed (%s)", m->ctx_v->err.c_str());
+    m->fmm_v = plan_job.take();
+    plan_ms = plan_job.ms;
+    const int st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(m->d_fb), nullptr,
+                                   0.0, reinterpret_cast<double *>(m->d_tmp3), m->s);
+    if (st) return fail(m, st, "FMM right-hand side failed");
+  } else {
+    ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
+                       reinterpret_cast<double *>(m->d_tmp3), m->s));
+  }
   ves_rhs_kernel<<<V, n, 0, m->s>>>(n, m->d_tmp3, m->have_walls ? m->d_ures : nullptr, m->d_w,
                                     m->d_L0, dt, m->d_b, m->d_Lk);
   SK(cudaGetLastError());
   // warm-start features of this step (principal-axes frame)
-  if (n >= kModes) {
-    ves_features_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_b, m->d_bprev, m->d_A0, m->kappa_b,
-                                           m->mu, m->d_frame, m->d_feat);
+  if (n >= m->warm_modes) {
+    ves_features_kernel<<<V, n, 0, m->s>>>(
+        n, m->warm_modes, m->d_x, m->d_b, m->d_bprev, m->warm_history ? m->d_zprev : nullptr,
+        m->d_zprev2, m->hist_count >= 2, m->d_A0, m->kappa_b, m->mu, m->d_frame, m->d_feat);
     SK(cudaGetLastError());
   }
   // step 6: GMRES with the block-diagonal self preconditioner, from the chosen initial iterate
   ST(precond_build(m, dt));
   if (guess_mode == STOKES_GUESS_USER) {
     SK(cudaMemcpyAsync(m->d_xsol, guess, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  } else if (guess_mode == STOKES_GUESS_MLP && m->warm_base == STOKES_WARM_BASE_EXTRAPOLATE &&
+             m->hist_count < 2) {
+    // a network trained on changes relative to the extrapolation has nothing to add to until
+    // two solutions exist: the previous solution is the guess
+    SK(cudaMemcpyAsync(m->d_xsol, m->d_zprev, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
   } else if (guess_mode == STOKES_GUESS_MLP) {
     int st = mlp_infer(model, V, m->d_feat, m->d_pred, m->s);
     if (st) return fail(m, st, "warm-start network inference failed");
-    ves_guess_kernel<<<V, n, 0, m->s>>>(n, m->d_pred, m->d_frame, m->d_zprev, m->d_xsol);
+    ves_guess_kernel<<<V, n, 0, m->s>>>(n, m->warm_modes, m->d_pred, m->d_frame, m->d_zprev,
+                                        m->d_zprev2, m->warm_base == STOKES_WARM_BASE_EXTRAPOLATE,
+                                        m->d_xsol);
+    SK(cudaGetLastError());
+  } else if (guess_mode == STOKES_GUESS_EXTRAPOLATE && m->hist_count >= 2) {
+    extrapolate_kernel<<<grid_for(len), 256, 0, m->s>>>(len, m->d_zprev, m->d_zprev2, m->d_xsol);
     SK(cudaGetLastError());
   } else if (guess_mode == STOKES_GUESS_ZERO) {
     SK(cudaMemsetAsync(m->d_xsol, 0, sizeof(double) * len, m->s));
@@ -1864,7 +2031,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   }
   SK(cudaStreamSynchronize(m->s));
   const auto t1 = std::chrono::steady_clock::now();
-  int iters = 0, refinements = 0;
+  int iters = 0, refinements = 0, accurate = 0;
   double rel = 0.0;
   int gst = STOKES_OK;
   if (precision != STOKES_FP32_KAHAN) {
@@ -1890,7 +2057,12 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     for (;;) {
       SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
       if (!zero_iterate) {
-        ST(step_matvec(m, dt, rough ? STOKES_FP32_KAHAN : hp, m->d_xsol, m->d_wk));
+        if (!rough && use_fmm) {
+          ST(step_matvec_fmm(m, dt, m->d_xsol, m->d_wk));
+        } else {
+          ST(step_matvec(m, dt, rough ? STOKES_FP32_KAHAN : hp, m->d_xsol, m->d_wk));
+        }
+        if (!rough) ++accurate;
         BK(cublasDaxpy(m->blas, int(len), &mone, m->d_wk, 1, m->d_rr, 1));
       }
       zero_iterate = false;
@@ -1931,14 +2103,20 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     out->setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     out->gmres_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
     out->refinements = refinements;
+    out->accurate_residuals = accurate;
+    out->fmm_plan_ms = plan_ms;
   }
   if (gst) return gst;
-  if (n >= kModes) {
-    ves_targets_kernel<<<V, n, 0, m->s>>>(n, m->d_xsol, m->d_zprev, m->d_frame, m->d_targ);
+  if (n >= m->warm_modes) {
+    ves_targets_kernel<<<V, n, 0, m->s>>>(
+        n, m->warm_modes, m->d_xsol, m->d_zprev, m->d_zprev2,
+        m->warm_base == STOKES_WARM_BASE_EXTRAPOLATE && m->hist_count >= 2, m->d_frame, m->d_targ);
     SK(cudaGetLastError());
   }
   SK(cudaMemcpyAsync(m->d_bprev, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  SK(cudaMemcpyAsync(m->d_zprev2, m->d_zprev, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
   SK(cudaMemcpyAsync(m->d_zprev, m->d_xsol, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
+  m->hist_count = std::min(m->hist_count + 1, 2);
   // steps 7-9: x <- x + dt u, area correction, reparameterization; sigma <- sigma^{k+1}
   ves_advance_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_xsol, m->d_D, m->d_A0, dt);
   ves_reparam_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D);
@@ -1953,12 +2131,14 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
 int stokes_sim_last_features(stokes_sim *m, float *features, float *targets) {
   if (!m) return STOKES_ERR_ARG;
   if (!m->have_ves) return fail(m, STOKES_ERR_NO_GEOM, "vesicles must be set");
-  if (m->n < kModes) return fail(m, STOKES_ERR_ARG, "features need n >= %d nodes per vesicle", kModes);
+  const int nm = m->warm_modes;
+  if (m->n < nm) return fail(m, STOKES_ERR_ARG, "features need n >= %d nodes per vesicle", nm);
   SK(cudaSetDevice(m->device));
   if (features)
-    SK(cudaMemcpyAsync(features, m->d_feat, sizeof(float) * m->V * kFeat, cudaMemcpyDeviceToDevice, m->s));
+    SK(cudaMemcpyAsync(features, m->d_feat, sizeof(float) * m->V * feat_dim(nm, m->warm_history),
+                       cudaMemcpyDeviceToDevice, m->s));
   if (targets)
-    SK(cudaMemcpyAsync(targets, m->d_targ, sizeof(float) * m->V * kTarg, cudaMemcpyDeviceToDevice, m->s));
+    SK(cudaMemcpyAsync(targets, m->d_targ, sizeof(float) * m->V * targ_dim(nm), cudaMemcpyDeviceToDevice, m->s));
   SK(cudaStreamSynchronize(m->s));
   return STOKES_OK;
 }
@@ -1984,6 +2164,8 @@ int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigm
   // a new start: no previous step
   SK(cudaMemset(m->d_bprev, 0, sizeof(double) * 3 * m->Nv));
   SK(cudaMemset(m->d_zprev, 0, sizeof(double) * 3 * m->Nv));
+  SK(cudaMemset(m->d_zprev2, 0, sizeof(double) * 3 * m->Nv));
+  m->hist_count = 0;
   return STOKES_OK;
 }
 
@@ -2013,8 +2195,51 @@ int stokes_sim_set_history(stokes_sim *m, const double *L0_host, const double *A
   if (zprev_host) {
     SK(cudaMemcpy(m->d_zprev, zprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
     SK(cudaMemcpy(m->d_xsol, zprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+    // the solution two steps back is not part of the history: the previous change restarts at 0
+    SK(cudaMemcpy(m->d_zprev2, zprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+    m->hist_count = 1;
   }
   if (bprev_host) SK(cudaMemcpy(m->d_bprev, bprev_host, sizeof(double) * len, cudaMemcpyHostToDevice));
+  return STOKES_OK;
+}
+
+int stokes_sim_set_warm_modes(stokes_sim *m, int modes) {
+  if (!m) return STOKES_ERR_ARG;
+  if (modes < 4 || modes > kMaxModes || (modes & 1))
+    return fail(m, STOKES_ERR_ARG, "warm-start modes must be even and in [4, %d]", kMaxModes);
+  if (m->have_ves && m->n < modes)
+    return fail(m, STOKES_ERR_ARG, "%d modes need at least %d nodes per vesicle", modes, modes);
+  m->warm_modes = modes;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_warm_base(stokes_sim *m, int base) {
+  if (!m) return STOKES_ERR_ARG;
+  if (base != STOKES_WARM_BASE_PREVIOUS && base != STOKES_WARM_BASE_EXTRAPOLATE)
+    return fail(m, STOKES_ERR_ARG, "unknown warm-start base %d", base);
+  m->warm_base = base;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_warm_history(stokes_sim *m, int on) {
+  if (!m) return STOKES_ERR_ARG;
+  m->warm_history = on != 0;
+  return STOKES_OK;
+}
+
+int stokes_sim_get_warm_modes(const stokes_sim *m, int *modes) {
+  if (!m || !modes) return STOKES_ERR_ARG;
+  *modes = m->warm_modes;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_residual_fmm(stokes_sim *m, int order, int leaf_size) {
+  if (!m) return STOKES_ERR_ARG;
+  if (order != 0 && (order < 4 || order > 40))
+    return fail(m, STOKES_ERR_ARG, "FMM order must be 0 (off) or in [4, 40]");
+  if (leaf_size < 4 || leaf_size > 4096) return fail(m, STOKES_ERR_ARG, "leaf size must be in [4, 4096]");
+  m->resid_fmm_order = order;
+  m->resid_fmm_leaf = leaf_size;
   return STOKES_OK;
 }
 

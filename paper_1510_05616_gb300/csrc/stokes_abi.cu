@@ -644,6 +644,8 @@ int stokes_geom_update(stokes_ctx *c, const double *nodes, const double *weights
   CK(cudaSetDevice(c->device));
   cudaStream_t s = as_stream(stream);
   const int N = c->N;
+  // FMM and close-evaluation plans hold positions of the old geometry: they no longer apply
+  fmm_geometry_changed(c);
   CK(cudaMemcpyAsync(c->d_x, nodes, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(c->d_nrm, normals, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(c->d_w, weights, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));

@@ -10,8 +10,10 @@ import time
 
 import numpy as np
 
-from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
-               STOKES_GUESS_ZERO, stokes_mlp_create, stokes_mlp_destroy, stokes_sim_set_restart,
+from . import (STOKES_FP64, STOKES_GUESS_EXTRAPOLATE, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
+               STOKES_GUESS_ZERO, STOKES_WARM_BASE_EXTRAPOLATE, STOKES_WARM_BASE_PREVIOUS,
+               feature_dims, stokes_sim_set_warm_base, stokes_mlp_create, stokes_sim_set_residual_fmm,
+               stokes_sim_set_warm_history, stokes_sim_set_warm_modes, stokes_mlp_destroy, stokes_sim_set_restart,
                stokes_mlp_fit_normalization, stokes_mlp_get_adam, stokes_mlp_get_normalization,
                stokes_mlp_get_params, stokes_mlp_num_params, stokes_mlp_set_adam,
                stokes_mlp_set_normalization, stokes_mlp_set_params,
@@ -21,13 +23,16 @@ from . import (N_FEATURES, N_TARGETS, STOKES_FP64, STOKES_GUESS_MLP, STOKES_GUES
                stokes_sim_set_vesicles, stokes_sim_set_walls, stokes_sim_sizes,
                vesicle_step_warmstart)
 
-GUESS_NAMES = {"zero": STOKES_GUESS_ZERO, "previous": STOKES_GUESS_PREVIOUS, "mlp": STOKES_GUESS_MLP}
+GUESS_NAMES = {"zero": STOKES_GUESS_ZERO, "previous": STOKES_GUESS_PREVIOUS, "mlp": STOKES_GUESS_MLP,
+               "extrapolate": STOKES_GUESS_EXTRAPOLATE}
+BASES = {"previous": STOKES_WARM_BASE_PREVIOUS, "extrapolate": STOKES_WARM_BASE_EXTRAPOLATE}
 
 
 class Simulation:
     """A channel with vesicles (from an inputs.Geometry) on the GPU."""
 
-    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80, wall_solver=None):
+    def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80, wall_solver=None,
+                 modes=16, residual_fmm=0, history=False, base="previous"):
         walls = [c for c in geom.curves if c.kind == 0]
         ves = [c for c in geom.curves if c.kind == 1]
         self.h = stokes_sim_create(device)
@@ -46,6 +51,14 @@ class Simulation:
         self.V, self.n, _ = stokes_sim_sizes(self.h)
         if restart != 80:
             stokes_sim_set_restart(self.h, restart)
+        self.modes = int(modes)
+        self.history = bool(history)
+        self.base = base
+        stokes_sim_set_warm_modes(self.h, self.modes)
+        stokes_sim_set_warm_history(self.h, self.history)
+        stokes_sim_set_warm_base(self.h, BASES[base])
+        if residual_fmm:  # mixed-precision steps take their FP64-accurate vesicle sums by FMM
+            stokes_sim_set_residual_fmm(self.h, residual_fmm)
 
     def step(self, dt, p_drive, guess="zero", model=None, tol=1e-10, max_iter=500,
              precision=STOKES_FP64):
@@ -93,28 +106,40 @@ class Simulation:
 
 def collect(sim: Simulation, steps, dt, p_drive, guess="previous", tol=1e-10,
             precision=STOKES_FP64):
-    """Run plain steps; return device tensors (features, targets) of every vesicle state and
-    the per-step statistics.  Every precision solves to the same FP64 tolerance."""
+    """Run plain steps; return device tensors (features, targets) of the vesicle states and the
+    per-step statistics.  Every precision solves to the same FP64 tolerance.  The run's first
+    step has no previous solution (its "change" would be the whole solution, far outside what a
+    warm start ever predicts), and with the extrapolation base the second step's target is still
+    a first difference, so those states are left out: (steps - skip) V rows."""
     import torch
     V = sim.V
-    X = torch.empty((steps * V, N_FEATURES), dtype=torch.float32, device="cuda")
-    T = torch.empty((steps * V, N_TARGETS), dtype=torch.float32, device="cuda")
+    skip = 2 if sim.base == "extrapolate" else 1
+    nf, nt = feature_dims(sim.modes, sim.history)
+    X = torch.empty((max(steps - skip, 0) * V, nf), dtype=torch.float32, device="cuda")
+    T = torch.empty((max(steps - skip, 0) * V, nt), dtype=torch.float32, device="cuda")
     stats = []
     for k in range(steps):
-        stats.append(sim.step(dt, p_drive, guess, tol=tol, precision=precision))
-        sim.features(X[k * V:(k + 1) * V], T[k * V:(k + 1) * V])
+        stats.append(sim.step(dt, p_drive, "zero" if k == 0 else guess, tol=tol,
+                              precision=precision))
+        if k >= skip:
+            sim.features(X[(k - skip) * V:(k - skip + 1) * V], T[(k - skip) * V:(k - skip + 1) * V])
     return X, T, stats
 
 
 class WarmStartNet:
-    """The 64 -> H -> H -> 48 network; parameters initialised from a seeded NumPy draw."""
+    """The 4 nm -> H -> H -> 3 nm network (nm warm-start modes; 64 -> H -> H -> 48 at the default
+    16); parameters initialised from a seeded NumPy draw."""
 
-    def __init__(self, hidden=256, seed=0, device=0):
-        self.h = stokes_mlp_create(device, N_FEATURES, hidden, N_TARGETS)
+    def __init__(self, hidden=256, seed=0, device=0, modes=16, history=False):
+        # (a network is used with the feature set and base guess of the data it was fitted to)
+        nf, nt = feature_dims(modes, history)
+        self.h = stokes_mlp_create(device, nf, hidden, nt)
         self.hidden = hidden
+        self.modes = int(modes)
+        self.history = bool(history)
         rng = np.random.default_rng(seed)
         theta = []
-        for fan_in, fan_out in ((N_FEATURES, hidden), (hidden, hidden), (hidden, N_TARGETS)):
+        for fan_in, fan_out in ((nf, hidden), (hidden, hidden), (hidden, nt)):
             lim = np.sqrt(6.0 / (fan_in + fan_out))
             theta.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
             theta.append(np.zeros(fan_out))
@@ -124,7 +149,7 @@ class WarmStartNet:
     def save(self, path):
         """Parameters, input/output normalisation and Adam state to an .npz file."""
         theta = stokes_mlp_get_params(self.h)
-        norm = stokes_mlp_get_normalization(self.h)
+        norm = stokes_mlp_get_normalization(self.h, *feature_dims(self.modes, self.history))
         m, v, t = stokes_mlp_get_adam(self.h)
         np.savez(path, theta=theta, norm=norm, adam_m=m, adam_v=v, adam_t=np.int64(t),
                  hidden=np.int64(self.hidden))
@@ -180,16 +205,22 @@ def evaluate(sim: Simulation, x_start, sigma_start, steps, dt, p_drive, model=No
         if gname == "mlp" and model is None:
             continue
         sim.set_state(x_start, sigma_start)
-        its, tms, gms = [], [], []
+        its, tms, gms, refs, accs = [], [], [], [], []
         for k in range(steps):
-            # the first step of a "previous" run has no previous solution: start from zero
-            g = "zero" if (gname == "previous" and k == 0) else gname
+            # the first step of a run has no previous solution (nothing to extrapolate from):
+            # every warm start starts from zero there (the library itself falls back to the
+            # previous solution while an extrapolation lacks its second one)
+            g = "zero" if (gname in ("previous", "mlp", "extrapolate") and k == 0) else gname
             t0 = time.perf_counter()
             st = sim.step(dt, p_drive, g, model=model.h if model is not None else None, tol=tol,
                           precision=precision)
             tms.append(1e3 * (time.perf_counter() - t0))
             its.append(st["iterations"])
             gms.append(st["gmres_ms"])
+            refs.append(st["refinements"])
+            accs.append(st["accurate_residuals"])
         out[gname] = {"iterations": its, "mean_iterations": float(np.mean(its)),
-                      "step_ms": float(np.mean(tms)), "gmres_ms": float(np.mean(gms))}
+                      "step_ms": float(np.mean(tms)), "gmres_ms": float(np.mean(gms)),
+                      "mean_refinements": float(np.mean(refs)),
+                      "mean_accurate_residuals": float(np.mean(accs))}
     return out

@@ -96,7 +96,7 @@ def test_fmm_plan_and_argument_errors(P):
     import torch
     g, slp, dlp = I.workload("small_n1280")
     s = P.StokesSum(g)
-    for order, leaf in ((3, 32), (31, 32), (20, 2)):
+    for order, leaf in ((3, 32), (41, 32), (20, 2)):
         with pytest.raises(P.StokesError):
             P.stokes_fmm_create(s.h, order, leaf)
     f = P.stokes_fmm_create(s.h, 20, 32)
@@ -108,7 +108,30 @@ def test_fmm_plan_and_argument_errors(P):
         P.stokes_fmm_eval(f, dev(slp), dev(dlp), 0.0, out)
     assert e.value.code == P.STOKES_ERR_NO_GEOM
     P.stokes_fmm_destroy(f)
+    # moved nodes (stokes_geom_update) invalidate a plan as well: it holds the old positions
+    f = P.stokes_fmm_create(s.h, 20, 32)
+    x, w, n, k = (dev(a) for a in (g.nodes + [0.01, 0.0], g.weights, g.normals, g.curvature))
+    P.stokes_geom_update(s.h, x, w, n, k)
+    with pytest.raises(P.StokesError) as e:
+        P.stokes_fmm_eval(f, dev(slp), dev(dlp), 0.0, out)
+    assert e.value.code == P.STOKES_ERR_NO_GEOM
+    P.stokes_fmm_destroy(f)
     s.close()
+
+
+def test_fmm_high_order_converges(P):
+    """Orders above 30 (shared memory sized by the order) keep converging: at order 36 the FMM
+    meets the double-float direct sum to 1e-11 on the 16k channel."""
+    g, slp, dlp = I.workload("mid_n16k")
+    s = P.StokesSum(g)
+    ref = s.eval(dev(slp), dev(dlp), precision="df").cpu().numpy()
+    errs = {}
+    for order in (28, 36, 40):
+        u, _ = fmm_eval(P, s, dev(slp), dev(dlp), order)
+        errs[order] = float((np.abs(u - ref).max(0) / np.abs(ref).max(0)).max())
+    s.close()
+    print("FMM order -> error vs double-float:", errs)
+    assert errs[36] < errs[28] and errs[36] < 1e-11 and errs[40] < 1e-11, errs
 
 
 def test_fmm_paper_channel(P):

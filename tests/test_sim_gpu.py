@@ -163,6 +163,48 @@ def test_channel_step_parity(P, S, prec):
     assert ex < 1e-11
 
 
+def test_fmm_residual_step_matches_double_float_step(P):
+    """Mixed-precision steps on the 16k channel whose FP64-accurate vesicle sums (right-hand
+    side, refinement residuals) come from the FMM (order 36, plan rebuilt every step) agree
+    with the same steps on double-float direct sums: solutions to 1e-8, positions to 1e-10."""
+    from paper_1510_05616_gb300 import warmstart as WS
+    g = I.workload("mid_n16k")[0]
+    dt, pd, kb = 1e-3, 2 * 2 * PI * 0.2, 0.01
+    a = WS.Simulation(g, kappa_b=kb, restart=200)
+    b = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=36)
+    for k in range(2):
+        sa = a.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        sb = b.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        assert sa["residual"] <= 1e-10 and sb["residual"] <= 1e-10
+        assert sb["accurate_residuals"] >= 1 and sb["fmm_plan_ms"] > 0.0
+        assert sa["fmm_plan_ms"] == 0.0
+        xa, siga, za = a.state()
+        xb, sigb, zb = b.state()
+        ez = np.abs(za - zb).max() / np.abs(za).max()
+        ex = np.abs(xa - xb).max()
+        print("step %d: FMM vs double-float residuals: solution %.2e, positions %.2e; "
+              "its %d / %d, step %.1f / %.1f ms, plan %.1f ms"
+              % (k, ez, ex, sa["iterations"], sb["iterations"], sa["total_ms"], sb["total_ms"],
+                 sb["fmm_plan_ms"]))
+        assert ez <= 1e-8 and ex <= 1e-10
+    a.close()
+    b.close()
+
+
+def test_residual_fmm_and_warm_modes_arguments(P):
+    h = P.stokes_sim_create(0)
+    for bad in ((3, 32), (41, 32), (20, 2)):
+        with pytest.raises(P.StokesError):
+            P.stokes_sim_set_residual_fmm(h, *bad)
+    P.stokes_sim_set_residual_fmm(h, 0)
+    for bad in (2, 15, 66):
+        with pytest.raises(P.StokesError):
+            P.stokes_sim_set_warm_modes(h, bad)
+    P.stokes_sim_set_warm_modes(h, 32)
+    assert P.stokes_sim_get_warm_modes(h) == 32
+    P.stokes_sim_destroy(h)
+
+
 def test_warm_start_with_solution_converges_at_once(P):
     import torch
     walls, ves = _case(n_ves=3, n_v=16)
