@@ -637,6 +637,77 @@ def run_walls(args):
     return 0
 
 
+def run_close(args):
+    """Close evaluation (the near-pair correction of the vesicles' single layer, F2) on channels
+    packed with a gap of only `--close-gap` node spacings, so that close pairs exist: plan time
+    (host pair search), time per correction call (CUDA events, median after warm-up) against
+    the plain node sums it corrects, the close pairs found, and how much the correction moves
+    the FP64 node sum (max over nodes, relative to max |u|)."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    B.build()
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+    def timed(fn, reps=7):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    rows = {}
+    for name in args.close_workloads.split(","):
+        n_w, modes, nv, n_v, area = I.WORKLOADS[name]
+        t0 = time.perf_counter()
+        g = I.channel(n_w, modes, nv, n_v, area, I.WORKLOAD_SEED[name] + 500,
+                      gap_factor=args.close_gap)
+        slp, dlp = I.densities(g, I.WORKLOAD_SEED[name] + 500)
+        gen_s = time.perf_counter() - t0
+        s = P.StokesSum(g)
+        ts, td = dev(slp), dev(dlp)
+        N = g.n_nodes
+        out = torch.zeros((N, 2), dtype=torch.float64, device="cuda")
+        r = {"N": N, "vesicles": nv, "nodes_per_vesicle": n_v, "gap_spacings": args.close_gap,
+             "generation_s": gen_s}
+        for prec in ("fp32k", "df"):
+            r["plain_" + prec + "_ms"] = timed(lambda: s.eval(ts, td, precision=prec, out=out))
+        base = s.eval(ts, td, precision="df").clone()
+        for K in (8, 16):
+            t0 = time.perf_counter()
+            cl = P.stokes_close_create(s.h, args.close_factor, K)
+            plan_ms = 1e3 * (time.perf_counter() - t0)
+            info = P.stokes_close_get_info(cl)
+
+            def call():
+                P.stokes_close_eval(cl, ts, out)
+                P.stokes_sync(s.h)
+            out.copy_(base)
+            ms = timed(call)
+            out.copy_(base)
+            call()
+            moved = float((out - base).abs().max() / base.abs().max())
+            r["close_K%d" % K] = {"ms": ms, "plan_ms": plan_ms, "pairs": info["pairs"],
+                                  "targets": info["targets"], "vesicles": info["vesicles"],
+                                  "share_of_fp32k_sum": ms / r["plain_fp32k_ms"],
+                                  "share_of_df_sum": ms / r["plain_df_ms"],
+                                  "max_change_rel": moved}
+            P.stokes_close_destroy(cl)
+        s.close()
+        rows[name] = r
+    print(json.dumps({"metric": "close evaluation of the vesicles' single layer: time per call",
+                      "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+                      "data": "synthetic", "factor": args.close_factor, "results": rows}))
+    return 0
+
+
 def run_fmm(args):
     """The pair sum at the nodes by the fast multipole method (FP64 expansions, orders 20 and
     28) against the direct GPU sums, from N = 1,280 to 524,288: evaluation time (median of
@@ -802,6 +873,12 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=40)
     ap.add_argument("--step-modes", default="16",
                     help="warm-start Fourier modes, one network each (e.g. 16,32)")
+    ap.add_argument("--close", action="store_true",
+                    help="time the close-evaluation correction on densely packed channels")
+    ap.add_argument("--close-workloads", default="mid_n16k,paper_n128k")
+    ap.add_argument("--close-gap", type=float, default=1.5,
+                    help="vesicle gap in node spacings for --close (the other workloads use 5)")
+    ap.add_argument("--close-factor", type=float, default=5.0)
     ap.add_argument("--no-warm-history", action="store_true",
                     help="warm-start features without the previous solution and its last change")
     ap.add_argument("--residual-fmm", type=int, default=0,
@@ -823,6 +900,8 @@ def main():
         return run_poiseuille(args)
     if args.walls:
         return run_walls(args)
+    if args.close:
+        return run_close(args)
     if args.fmm:
         return run_fmm(args)
     if args.scaling:

@@ -61,7 +61,8 @@ typedef enum {
     STOKES_ERR_NONFINITE = -5,      /* non-finite density or geometry value             */
     STOKES_ERR_TIMEOUT = -6,        /* a device pipeline wait exceeded its bound        */
     STOKES_ERR_NOT_CONVERGED = -7,  /* iterative solve hit its iteration cap            */
-    STOKES_ERR_OOM = -8             /* device allocation failed                         */
+    STOKES_ERR_OOM = -8,            /* device allocation failed                         */
+    STOKES_ERR_BOUNDS = -9          /* debug build: a device bounds check failed        */
 } stokes_status;
 
 typedef enum {
@@ -191,7 +192,7 @@ STOKES_API int stokes_sum_eval_host(stokes_ctx *ctx, int precision, const double
                                     const double *dlp_density_host, double jump, double *out_host);
 
 /* Synchronize `stream` and return (then clear) the device status word: STOKES_OK,
- * STOKES_ERR_NONFINITE or STOKES_ERR_TIMEOUT. */
+ * STOKES_ERR_NONFINITE, STOKES_ERR_TIMEOUT or (debug build) STOKES_ERR_BOUNDS. */
 STOKES_API int stokes_sync(stokes_ctx *ctx, void *stream);
 
 /* Failure-handling check: launches one block on `stream` that waits, with the pair kernels'
@@ -207,6 +208,19 @@ STOKES_API int stokes_check_wait_timeout(stokes_ctx *ctx, void *stream);
  * `stream`.  STOKES_ERR_ARG for n < 0 or NULL pointers.  For tests. */
 STOKES_API int stokes_check_log64(stokes_ctx *ctx, const double *x, int n, double *out,
                                   void *stream);
+
+/* Debug build (libstokes_debug.so, compiled with -DSTOKES_DEBUG; no counterpart in the paper):
+ * the pair, pack and finishing kernels check every source-tile, target, density-row and
+ * partial-sum index against the buffer it addresses; a failed check records a bit in the
+ * context's status word and skips (or redirects to element 0) that access -- nothing traps --
+ * and the next stokes_sync returns STOKES_ERR_BOUNDS (-9).  The release build (libstokes.so)
+ * compiles the checks away.  stokes_debug_build returns 1 in the debug build, else 0.
+ * stokes_debug_tighten (debug build only; STOKES_ERR_ARG in the release build or for
+ * elements < 0) makes the checks treat the last `elements` elements of every partial-sum
+ * buffer as out of range while the buffers keep their size, so a test can see a check fire
+ * without any access leaving its allocation.  0 restores the real bounds.  For tests. */
+STOKES_API int stokes_debug_build(void);
+STOKES_API int stokes_debug_tighten(stokes_ctx *ctx, long long elements);
 
 /* ---------------------------------------------------------------------------------------------
  * Fast multipole evaluation at the nodes (FP64).  The same discrete sum as stokes_sum_eval
@@ -398,6 +412,25 @@ STOKES_API int stokes_get_launch(const stokes_ctx *ctx, int precision, int *sour
  * tile in the (hi, lo) form).  Results differ only by rounding.
  */
 STOKES_API int stokes_set_local_frame(stokes_ctx *ctx, int on);
+
+/*
+ * Graph replay of node sums (stokes_sum_eval on a single-instance geometry; no counterpart in
+ * the paper, a launch-overhead measure).  The five launches of a sum (density pack, the FP64
+ * self pass on a side stream, the pair kernel, the finishing pass) are captured once into a
+ * CUDA graph on the context's own stream and relaunched as one graph on the caller's stream
+ * while precision, jump and the density and output pointers repeat; a change of any of them,
+ * of the geometry, of the launch shape or of the partial buffer captures anew.  Results are
+ * bit-identical to the direct launches.  Modes: STOKES_GRAPH_OFF (direct launches),
+ * STOKES_GRAPH_SMALL (default: geometries of at most 65,536 nodes, where the launches' host
+ * overhead is a visible share of a sum), STOKES_GRAPH_ALWAYS.  Profiling (stokes_set_profiling)
+ * uses the direct launches.  STOKES_ERR_ARG for another mode.
+ */
+typedef enum {
+    STOKES_GRAPH_OFF = 0,
+    STOKES_GRAPH_SMALL = 1,
+    STOKES_GRAPH_ALWAYS = 2
+} stokes_graph_mode;
+STOKES_API int stokes_set_graph_mode(stokes_ctx *ctx, int mode);
 
 /* Nominal pair-image evaluations of one stokes_sum_eval: 3 N_t N_s (1 N_t N_s when period
  * is 0), counting skipped and self pairs.  Written to *pairs. */
@@ -622,6 +655,15 @@ STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
  * The plan is rebuilt each step (the geometry moves) by a host thread while the GPU computes
  * the forces and the channel response.  Walls keep their double-float sums. */
 STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_size);
+/* Close evaluation inside the step (the near-pair rule the paper applies to close vesicles,
+ * Sec. 3.2): with factor > 0, every vesicle-vesicle single-layer sum of a step (right-hand
+ * side, Krylov and residual matvecs in every precision, FMM sums) adds stokes_close_eval's
+ * correction for the (node, vesicle image) pairs closer than factor node spacings, found for
+ * the step's positions (stokes_close_create, on the host, once per step); upsample K as there
+ * (K n <= 4096).  The block preconditioner and the channel response (vesicle-to-wall sums)
+ * are unchanged.  factor 0 turns it off (default); STOKES_ERR_ARG for factor outside {0} and
+ * (0, 50] or K outside [1, 64]. */
+STOKES_API int stokes_sim_set_close_eval(stokes_sim *sim, double factor, int upsample);
 /* u_resp (DEVICE, V n x 2) of forces f (DEVICE, V n x 2) at the vesicle nodes. */
 STOKES_API int stokes_sim_channel_response(stokes_sim *sim, const double *f, double p_drive,
                                            double *u_resp);

@@ -363,6 +363,41 @@ def slp_operator(xs_list, period, mu):
     return S.reshape(2 * N, 2 * N)
 
 
+def close_correction(xs_list, period, mu, factor, K):
+    """Close evaluation of the single-layer operator (the near-pair reading of Sec. 3.2; see
+    close_oracle): the dense matrix C (rows and columns (node, comp), like slp_operator) to add to
+    it.  For every node x_i and every vesicle image m (own vesicle at m = 0 excluded) whose nodes
+    come closer to x_i than factor h (h its largest node spacing), the row block of x_i gets the
+    close oracle's single layer of the interpolated vesicle minus the plain n-point sum, column
+    by column (unit densities)."""
+    from oracle import close_oracle as C
+    nodes = np.vstack(xs_list)
+    ws = [curve_normals_weights(x)[1] for x in xs_list]
+    off = np.cumsum([0] + [x.shape[0] for x in xs_list])
+    N = nodes.shape[0]
+    out = np.zeros((2 * N, 2 * N))
+    shifts = (-1, 0, 1) if period else (0,)
+    owner = np.repeat(np.arange(len(xs_list)), np.diff(off))
+    for i in range(N):
+        for b, xb in enumerate(xs_list):
+            nb = xb.shape[0]
+            for m in shifts:
+                if b == owner[i] and m == 0:
+                    continue
+                xs = xb + np.array([m * period, 0.0])
+                h = np.sqrt((np.diff(np.vstack([xs, xs[:1]]), axis=0) ** 2).sum(1)).max()
+                if np.sqrt(((xs - nodes[i]) ** 2).sum(1)).min() >= factor * h:
+                    continue
+                plain = stokeslet(nodes[i][None], xs, mu) * ws[b][:, None, None]  # (nb, 2, 2)
+                for j in range(nb):
+                    for c in range(2):
+                        e = np.zeros((nb, 2))
+                        e[j, c] = 1.0
+                        fine = C.close_slp(xs, e, nodes[i:i + 1], mu, K=K)[0]
+                        out[2 * i:2 * i + 2, 2 * (off[b] + j) + c] += fine - plain[j][:, c]
+    return out
+
+
 def perimeter(x):
     s, _, _ = arclength_ops(x)
     return s.mean() * 2 * PI
@@ -445,12 +480,15 @@ def forces(x, sigma, kappa_b):
     return -kappa_b * xssss, Ds @ (sigma[:, None] * xs)
 
 
-def step_system(ves_x, dt, kappa_b, mu, period, L0):
+def step_system(ves_x, dt, kappa_b, mu, period, L0, close=None):
     """Dense matrix of Eq. (tsteplinsys) (unknowns: u of every node (node, comp), then sigma
-    of every node) and the arc-length-corrected constraint right-hand side."""
+    of every node) and the arc-length-corrected constraint right-hand side.  close =
+    (factor, K) adds the close-evaluation correction to the single-layer operator."""
     sizes = [x.shape[0] for x in ves_x]
     N = sum(sizes)
     Sop = slp_operator(ves_x, period, mu)
+    if close is not None:
+        Sop = Sop + close_correction(ves_x, period, mu, *close)
     D4 = np.zeros((2 * N, 2 * N))
     Tsig = np.zeros((2 * N, N))
     Xds = np.zeros((N, 2 * N))
@@ -474,7 +512,7 @@ def step_system(ves_x, dt, kappa_b, mu, period, L0):
 
 
 def step(ves_x, sigma, L0, A0, dt, kappa_b, mu, period, walls=None, p_drive=0.0,
-         reparam=True):
+         reparam=True, close=None):
     """One semi-implicit step of Algorithm 1: forces, channel response (explicit), the
     solve of Eq. (tsteplinsys) with Eq. (ALC), x <- x + dt u, area correction, reparam.
     Returns (new positions, new tensions, u, sigma_{k+1}, u_resp)."""
@@ -486,7 +524,7 @@ def step(ves_x, sigma, L0, A0, dt, kappa_b, mu, period, walls=None, p_drive=0.0,
         f.append(b + t)
     fb = np.vstack(fb)
     f = np.vstack(f)
-    M, Sop, rhs2 = step_system(ves_x, dt, kappa_b, mu, period, L0)
+    M, Sop, rhs2 = step_system(ves_x, dt, kappa_b, mu, period, L0, close)
     xv = np.vstack(ves_x)
     if walls is not None:
         wv = np.concatenate([curve_normals_weights(x)[1] for x in ves_x])

@@ -12,7 +12,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libstokes.so")
+# STOKES_LIBRARY=debug selects libstokes_debug.so (device bounds checks, -DSTOKES_DEBUG)
+LIB_PATH = os.path.join(HERE, "libstokes_debug.so" if os.environ.get("STOKES_LIBRARY") == "debug"
+                        else "libstokes.so")
 
 STOKES_OK = 0
 STOKES_ERR_ARG = -1
@@ -23,6 +25,7 @@ STOKES_ERR_NONFINITE = -5
 STOKES_ERR_TIMEOUT = -6
 STOKES_ERR_NOT_CONVERGED = -7
 STOKES_ERR_OOM = -8
+STOKES_ERR_BOUNDS = -9
 
 STOKES_FP64 = 0
 STOKES_FP32_KAHAN = 1
@@ -37,6 +40,9 @@ STOKES_GUESS_USER = 3
 STOKES_GUESS_EXTRAPOLATE = 4
 STOKES_WARM_BASE_PREVIOUS = 0
 STOKES_WARM_BASE_EXTRAPOLATE = 1
+STOKES_GRAPH_OFF = 0
+STOKES_GRAPH_SMALL = 1
+STOKES_GRAPH_ALWAYS = 2
 STOKES_WALLS_LU64 = 0
 STOKES_WALLS_LU32_REFINE = 1
 STOKES_WALLS_FDS = 2
@@ -68,6 +74,9 @@ _SIGNATURES = {
     "stokes_sync": [_vp, _vp],
     "stokes_check_wait_timeout": [_vp, _vp],
     "stokes_check_log64": [_vp, _vp, _c_int, _vp, _vp],
+    "stokes_set_graph_mode": [_vp, _c_int],
+    "stokes_debug_build": [],
+    "stokes_debug_tighten": [_vp, ctypes.c_longlong],
     "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
@@ -101,6 +110,7 @@ _SIGNATURES = {
     "stokes_sim_set_precond_precision": [_vp, _c_int],
     "stokes_sim_set_inner_tolerance": [_vp, _c_double],
     "stokes_sim_set_residual_fmm": [_vp, _c_int, _c_int],
+    "stokes_sim_set_close_eval": [_vp, _c_double, _c_int],
     "stokes_sim_set_warm_modes": [_vp, _c_int],
     "stokes_sim_set_warm_history": [_vp, _c_int],
     "stokes_sim_set_warm_base": [_vp, _c_int],
@@ -156,7 +166,7 @@ def load() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise StokesError(STOKES_ERR_CUDA, "libstokes.so is not built (%s)" % LIB_PATH)
+            raise StokesError(STOKES_ERR_CUDA, "%s is not built" % LIB_PATH)
         lib = ctypes.CDLL(LIB_PATH)
         for name, argt in _SIGNATURES.items():
             fn = getattr(lib, name)
@@ -413,6 +423,22 @@ def stokes_num_nodes(h) -> int:
 def stokes_set_launch(h, precision, source_splits=0, targets_per_thread=0, kahan_group=0):
     return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits),
                                               int(targets_per_thread), int(kahan_group)))
+
+
+def stokes_debug_build() -> bool:
+    """True when the loaded library is the debug build (device bounds checks)."""
+    return bool(load().stokes_debug_build())
+
+
+def stokes_debug_tighten(h, elements):
+    """Debug build: the bounds checks treat the last `elements` partial-sum elements as out
+    of range (the buffers keep their size)."""
+    return _check(h, load().stokes_debug_tighten(h, int(elements)))
+
+
+def stokes_set_graph_mode(h, mode=STOKES_GRAPH_SMALL):
+    """Node sums replayed from a captured CUDA graph: STOKES_GRAPH_OFF / _SMALL / _ALWAYS."""
+    return _check(h, load().stokes_set_graph_mode(h, int(mode)))
 
 
 def stokes_set_local_frame(h, on: bool = True):
@@ -689,6 +715,11 @@ def stokes_sim_set_warm_base(h, base):
 def feature_dims(modes: int, history: bool = False):
     """(features, targets) per vesicle for `modes` warm-start modes (with history features)."""
     return 4 * int(modes) + (6 * int(modes) if history else 0), 3 * int(modes)
+
+
+def stokes_sim_set_close_eval(h, factor, upsample=16):
+    """Steps add the close-evaluation correction of vesicle pairs closer than factor h (0: off)."""
+    return _sim_check(h, load().stokes_sim_set_close_eval(h, float(factor), int(upsample)))
 
 
 def stokes_sim_set_residual_fmm(h, order, leaf_size=32):

@@ -23,8 +23,11 @@
 //    circle 0.9 x its centre's distance to the shared cell boundary; the touching section
 //    against points on a circle 1.75 x its radius together with the neighbour nodes inside
 //    that circle.  L is block diagonal (the sections' P's) and R = A_m(J, :).
-//  * A^-1 by Sherman-Morrison-Woodbury, Eq. (woodbury1): Z = A_0^-1 L and
-//    K^-1 = (I + R Z)^-1 are formed once; a solve is y = A_0^-1 v, x = y - Z K^-1 R y.
+//  * A^-1 by Sherman-Morrison-Woodbury, Eq. (woodbury1): K^-1 = (I + R A_0^-1 L)^-1 is formed
+//    once (A_0^-1 L by the tree passes on L's l columns, then discarded); a solve is
+//    y = A_0^-1 v, x = A_0^-1 (v - L K^-1 R y) -- the same as y - A_0^-1 L K^-1 R y, with the
+//    second tree pass in place of a stored dense A_0^-1 L, so a solve reads the HBS tables twice,
+//    R once, K^-1 and L's section blocks, and nothing of size n x l besides R.
 //
 // The compression and the small per-box inverses run on the host in FP64 (threads over the
 // boxes of one level); R, Z, K^-1 and every solve run on the device.
@@ -432,6 +435,63 @@ __global__ void set_identity_kernel(int n, double *K) {
     K[i] = (i % size_t(n + 1) == 0) ? 1.0 : 0.0;
 }
 
+// y = M x for a column-major M (rows x cols, leading dimension rows), one right-hand side,
+// in two fixed-order passes: partial[ch][r] = sum over the columns of chunk ch of M[r, u] x[u]
+// (a CTA per (row tile, column chunk): a thread per row, the chunk of x staged in shared
+// memory, four columns in flight per thread; a warp reads 32 consecutive doubles of a column),
+// then y[r] = alpha sum_ch partial[ch][r] (+ y[r] when accumulate).  HBM-bound: M is read once.
+constexpr int kGemvRows = 256;     // rows per CTA (one per thread)
+constexpr int kGemvMaxChunk = 2048;  // columns per chunk (staged x: 16 KB)
+
+__global__ void __launch_bounds__(kGemvRows)
+    gemv_cm_partial_kernel(int rows, int cols, int chunk, const double *__restrict__ M,
+                           const double *__restrict__ x, double *__restrict__ partial) {
+  __shared__ double xs[kGemvMaxChunk];
+  const int u0 = blockIdx.y * chunk;
+  const int nu = min(chunk, cols - u0);
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) xs[j] = x[u0 + j];
+  __syncthreads();
+  const int r = blockIdx.x * kGemvRows + threadIdx.x;
+  if (r >= rows) return;
+  const double *Mr = M + size_t(u0) * rows + r;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int j = 0;
+  for (; j + 3 < nu; j += 4) {
+    const double m0 = __ldg(Mr + size_t(j) * rows), m1 = __ldg(Mr + size_t(j + 1) * rows);
+    const double m2 = __ldg(Mr + size_t(j + 2) * rows), m3 = __ldg(Mr + size_t(j + 3) * rows);
+    a0 = fma(m0, xs[j], a0);
+    a1 = fma(m1, xs[j + 1], a1);
+    a2 = fma(m2, xs[j + 2], a2);
+    a3 = fma(m3, xs[j + 3], a3);
+  }
+  for (; j < nu; ++j) a0 = fma(__ldg(Mr + size_t(j) * rows), xs[j], a0);
+  partial[size_t(blockIdx.y) * rows + r] = (a0 + a1) + (a2 + a3);
+}
+
+__global__ void gemv_reduce_kernel(int rows, int chunks, const double *partial, double alpha,
+                                   int accumulate, double *y) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double acc = 0.0;
+  for (int ch = 0; ch < chunks; ++ch) acc += partial[size_t(ch) * rows + r];
+  y[r] = accumulate ? fma(alpha, acc, y[r]) : alpha * acc;
+}
+
+// X[:, c] -= L S[:, c] for the nc columns of X (nA x nc, ld nA) and S (l x nc, ld l): L is
+// block diagonal, one CTA per section block (rows x cols at (row0, col0), values column-major).
+__global__ void sub_blocks_kernel(const SecBlock *sec, const double *vals, int nA, int l, int nc,
+                                  const double *S, double *X) {
+  const SecBlock b = sec[blockIdx.x];
+  for (int idx = threadIdx.x; idx < b.rows * nc; idx += blockDim.x) {
+    const int i = idx % b.rows, c = idx / b.rows;
+    const double *v = vals + b.off + i;
+    const double *sc = S + size_t(c) * l + b.col0;
+    double acc = 0.0;
+    for (int q = 0; q < b.cols; ++q) acc = fma(v[size_t(q) * b.rows], sc[q], acc);
+    X[size_t(c) * nA + b.row0 + i] -= acc;
+  }
+}
+
 // Blocks of a 256-thread grid-stride launch over n elements: one per 256 elements, at most
 // 32 per SM of the current device.
 int grid_for(size_t n) {
@@ -451,8 +511,14 @@ struct fds_solver {
   std::vector<HbsBox *> d_boxes;       // [L + 1]
   std::vector<long long> N;            // [L + 1]
   double *d_mats = nullptr;
-  // neighbour factors
-  double *d_Z = nullptr, *d_R = nullptr, *d_Kinv = nullptr;
+  // neighbour factors: R = A_m(J, :) (l x nA), K^-1 = (I + R A_0^-1 L)^-1, L's section blocks
+  double *d_R = nullptr, *d_Kinv = nullptr;
+  SecBlock *d_sec = nullptr;
+  double *d_svals = nullptr;
+  int n_sec = 0;
+  double *d_gpart = nullptr;           // partial sums of the one-right-hand-side products
+  int gemv_chunks_R = 1, gemv_chunks_K = 1;
+  int chunk_R = 1, chunk_K = 1;
   // workspace of one pass (kChunk right-hand sides)
   double *d_up = nullptr, *d_down = nullptr, *d_out = nullptr, *d_t = nullptr, *d_s = nullptr;
   size_t up_len = 0;                   // sum of N[0..L-1]
@@ -963,20 +1029,36 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
       l, nA, dJ, dJ + l, dg, dg + Nt, dg + 2 * Nt, dg + 3 * Nt, dg + 4 * Nt, dg + 5 * Nt, g.d, f->d_R);
   FD(cudaGetLastError());
   // Z = A_0^-1 L
-  SecBlock *dsec = nullptr;
-  double *dvals = nullptr;
-  FD(dalloc(dsec, hf.sb.size(), scratch));
-  tmp.push_back(dsec);
-  FD(dalloc(dvals, hf.svals.size(), scratch));
-  tmp.push_back(dvals);
-  FD(cudaMemcpyAsync(dsec, hf.sb.data(), sizeof(SecBlock) * hf.sb.size(), cudaMemcpyHostToDevice, s));
-  FD(cudaMemcpyAsync(dvals, hf.svals.data(), sizeof(double) * hf.svals.size(), cudaMemcpyHostToDevice, s));
-  FD(dalloc(f->d_Z, size_t(nA) * l, bytes));
-  FD(cudaMemsetAsync(f->d_Z, 0, sizeof(double) * size_t(nA) * l, s));
-  scatter_blocks_kernel<<<int(hf.sb.size()), 256, 0, s>>>(dsec, dvals, nA, f->d_Z);
+  f->n_sec = int(hf.sb.size());
+  FD(dalloc(f->d_sec, hf.sb.size(), bytes));
+  FD(dalloc(f->d_svals, hf.svals.size(), bytes));
+  FD(cudaMemcpyAsync(f->d_sec, hf.sb.data(), sizeof(SecBlock) * hf.sb.size(), cudaMemcpyHostToDevice, s));
+  FD(cudaMemcpyAsync(f->d_svals, hf.svals.data(), sizeof(double) * hf.svals.size(), cudaMemcpyHostToDevice, s));
+  // one-right-hand-side products: column chunks so that (row tiles x chunks) CTAs fill the
+  // SMs about four times over, at most kGemvMaxChunk columns each
+  {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int row_tiles = std::max(1, (l + kGemvRows - 1) / kGemvRows);
+    auto plan = [&](int cols, int &chunk, int &chunks) {
+      const int want = std::max(1, 4 * std::max(sms, 1) / row_tiles);
+      chunk = std::min(kGemvMaxChunk, std::max(64, (cols + want - 1) / want));
+      chunks = std::max(1, (cols + chunk - 1) / chunk);
+    };
+    plan(nA, f->chunk_R, f->gemv_chunks_R);
+    plan(l, f->chunk_K, f->gemv_chunks_K);
+    FD(dalloc(f->d_gpart, size_t(std::max(1, l)) * std::max(f->gemv_chunks_R, f->gemv_chunks_K), bytes));
+  }
+  // Z = A_0^-1 L (set-up only: K = I + R Z)
+  double *dZ = nullptr;
+  FD(dalloc(dZ, size_t(nA) * l, scratch));
+  tmp.push_back(dZ);
+  FD(cudaMemsetAsync(dZ, 0, sizeof(double) * size_t(nA) * l, s));
+  scatter_blocks_kernel<<<int(hf.sb.size()), 256, 0, s>>>(f->d_sec, f->d_svals, nA, dZ);
   FD(cudaGetLastError());
   {
-    int st = hbs_apply(f, f->d_Z, l, s, err);
+    int st = hbs_apply(f, dZ, l, s, err);
     if (st) return bail(st);
   }
   // K = I + R Z, then K^-1
@@ -986,7 +1068,7 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
   const double one = 1.0, zero = 0.0;
   cublasSetStream(blas, s);
   cusolverDnSetStream(sol, s);
-  FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, nA, &one, f->d_R, l, f->d_Z, nA, &zero, dK, l));
+  FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, nA, &one, f->d_R, l, dZ, nA, &zero, dK, l));
   add_identity_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, dK);
   FD(cudaGetLastError());
   int lwork = 0;
@@ -1016,8 +1098,22 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
 #undef FDQ
   f->info.device_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t2).count();
-  f->info.solve_bytes = sizeof(double) * (hf.mats.size() + 2 * size_t(l) * nA + size_t(l) * l);
+  // a solve reads the HBS tables twice, R, K^-1 and L's blocks once
+  f->info.solve_bytes = sizeof(double) * (2 * hf.mats.size() + size_t(l) * nA + size_t(l) * l +
+                                          hf.svals.size());
   *out = f;
+  return STOKES_OK;
+}
+
+// t (l) = alpha M x (+ t when accumulate) for the column-major l-row matrix M with `cols`
+// columns, by the library's own two-pass product.
+int gemv_rows(fds_solver *f, const double *M, int cols, int chunk, int chunks, const double *x,
+              double *t, cudaStream_t s, std::string &err) {
+  const int l = f->l;
+  dim3 grid((l + kGemvRows - 1) / kGemvRows, chunks);
+  gemv_cm_partial_kernel<<<grid, kGemvRows, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  gemv_reduce_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, chunks, f->d_gpart, 1.0, 0, t);
+  FK(cudaGetLastError());
   return STOKES_OK;
 }
 
@@ -1027,7 +1123,7 @@ int fds_solve(fds_solver *f, double *X, int nrhs, cudaStream_t s, cublasHandle_t
     err = "fds_solve: bad arguments";
     return STOKES_ERR_ARG;
   }
-  const double one = 1.0, mone = -1.0, zero = 0.0;
+  const double one = 1.0, zero = 0.0;
   cublasSetStream(blas, s);
   for (int c0 = 0; c0 < nrhs; c0 += kChunk) {
     const int nc = std::min(kChunk, nrhs - c0);
@@ -1035,21 +1131,21 @@ int fds_solve(fds_solver *f, double *X, int nrhs, cudaStream_t s, cublasHandle_t
     int st = hbs_pass(f, Xc, f->d_out, nc, s, err);  // y = A_0^-1 v  (in d_out)
     if (st) return st;
     if (f->l > 0) {
-      if (nc == 1) {
-        FB(cublasDgemv(blas, CUBLAS_OP_N, f->l, f->nA, &one, f->d_R, f->l, f->d_out, 1, &zero,
-                       f->d_t, 1));
-        FB(cublasDgemv(blas, CUBLAS_OP_N, f->l, f->l, &one, f->d_Kinv, f->l, f->d_t, 1, &zero,
-                       f->d_s, 1));
-        FB(cublasDgemv(blas, CUBLAS_OP_N, f->nA, f->l, &mone, f->d_Z, f->nA, f->d_s, 1, &one,
-                       f->d_out, 1));
-      } else {
+      if (nc == 1) {  // t = R y, s = K^-1 t: the library's own products
+        st = gemv_rows(f, f->d_R, f->nA, f->chunk_R, f->gemv_chunks_R, f->d_out, f->d_t, s, err);
+        if (!st) st = gemv_rows(f, f->d_Kinv, f->l, f->chunk_K, f->gemv_chunks_K, f->d_t, f->d_s, s, err);
+        if (st) return st;
+      } else {        // several right-hand sides (set-up work): library GEMMs
         FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->nA, &one, f->d_R, f->l,
                        f->d_out, f->nA, &zero, f->d_t, f->l));
         FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->l, &one, f->d_Kinv, f->l,
                        f->d_t, f->l, &zero, f->d_s, f->l));
-        FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->nA, nc, f->l, &mone, f->d_Z, f->nA,
-                       f->d_s, f->l, &one, f->d_out, f->nA));
       }
+      // v <- v - L s, then x = A_0^-1 v
+      sub_blocks_kernel<<<f->n_sec, 256, 0, s>>>(f->d_sec, f->d_svals, f->nA, f->l, nc, f->d_s, Xc);
+      FK(cudaGetLastError());
+      st = hbs_pass(f, Xc, f->d_out, nc, s, err);
+      if (st) return st;
     }
     FK(cudaMemcpyAsync(Xc, f->d_out, sizeof(double) * f->nA * nc, cudaMemcpyDeviceToDevice, s));
   }
@@ -1064,9 +1160,11 @@ void fds_destroy(fds_solver *f) {
   if (!f) return;
   cudaFree(f->d_mats);
   for (HbsBox *b : f->d_boxes) cudaFree(b);
-  cudaFree(f->d_Z);
   cudaFree(f->d_R);
   cudaFree(f->d_Kinv);
+  cudaFree(f->d_sec);
+  cudaFree(f->d_svals);
+  cudaFree(f->d_gpart);
   cudaFree(f->d_up);
   cudaFree(f->d_down);
   cudaFree(f->d_out);

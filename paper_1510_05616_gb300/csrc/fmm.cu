@@ -924,6 +924,7 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const int N = c->N;
   if (c->partial_cap < size_t(N)) {  // the finishing pass reads one split of partials
     FMK(cudaDeviceSynchronize());
+    invalidate_node_graph(c);
     cudaFree(c->d_partial);
     c->d_partial = nullptr;
     c->partial_cap = 0;

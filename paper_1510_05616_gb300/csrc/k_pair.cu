@@ -27,6 +27,8 @@
 // nodes (those are replaced by the Kress self rule); a wall target's own node at m = 0
 // gives r = 0 exactly and contributes 0 (r2 carries a tiny floor so 1/r^2 stays finite
 // while r . n = r . q = 0).
+#include <algorithm>
+
 #include "stokes_internal.cuh"
 #include "bulk_pipe.cuh"
 
@@ -68,9 +70,27 @@ struct TgtF32 {
   int2 skip;                 // own-curve source slots skipped at m = 0
 };
 
+// Target index of kernel target k (its node under the Morton order), bounds-checked in the
+// debug build (an out-of-range index is recorded and redirected to target 0).
+__device__ __forceinline__ int target_index(const PairArgs &a, int k) {
+  const int i = a.tgt_perm ? a.tgt_perm[k] : k;
+  return dcheck(i >= 0 && i < a.n_targets, a.status) ? i : 0;
+}
+
+// Source tile of a staged copy, bounds-checked in the debug build (out of range: recorded and
+// redirected to tile 0, so the copy still arrives on its barrier).
+__device__ __forceinline__ int checked_tile(const PairArgs &a, int tile) {
+  return dcheck(tile >= 0 && tile < a.src_tiles, a.status) ? tile : 0;
+}
+
+// partial[idx] = v, bounds-checked in the debug build (out of range: recorded, not written).
+__device__ __forceinline__ void store_partial(const PairArgs &a, long long idx, double2 v) {
+  if (dcheck(idx >= 0 && idx < a.partial_cap, a.status)) a.partial[idx] = v;
+}
+
 template <int NIMG>
 __device__ __forceinline__ void load_target_f32(const PairArgs &a, int k, TgtF32<NIMG> &t) {
-  const int i = a.tgt_perm ? a.tgt_perm[k] : k;
+  const int i = target_index(a, k);
   const double2 p = a.tgt[i];
 #pragma unroll
   for (int k = 0; k < NIMG; ++k) {
@@ -557,8 +577,7 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
   if constexpr ((TPT & 1) == 0) {
     if (a.local_radius > 0.f) {
       const int k0 = it.tgt_begin + it.tgt_count / 2;
-      const int n0 = a.tgt_perm ? a.tgt_perm[k0] : k0;
-      const double2 o = a.tgt[n0];
+      const double2 o = a.tgt[target_index(a, k0)];
       ox = __double2float_rn(o.x);
       oy = __double2float_rn(o.y);
       float rmax = 0.f;
@@ -589,7 +608,7 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
   if (threadIdx.x == 0) {
     for (int r = 0; r < kStages && r < ntl; ++r) {
       const int st = (g + r) % kStages;
-      const int tile = item_tile(it, it.vt_begin + r);
+      const int tile = checked_tile(a, item_tile(it, it.vt_begin + r));
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
@@ -655,7 +674,7 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
       return false;
     }
     if (threadIdx.x == 0 && r + kStages < ntl) {
-      const int tile = item_tile(it, it.vt_begin + r + kStages);
+      const int tile = checked_tile(a, item_tile(it, it.vt_begin + r + kStages));
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF32, kBytes, &sm.bar[st]);
@@ -689,8 +708,8 @@ __device__ __forceinline__ bool run_item_f32(const PairArgs &a, const ItemDesc &
     const int loc = q * kThreadsF32 + int(threadIdx.x);
     if (loc < it.tgt_count) {
       const int k = it.tgt_begin + loc;
-      a.partial[it.part_off + (a.tgt_perm ? a.tgt_perm[k] : k)] =
-          make_double2(double(sx) - double(cx), double(sy) - double(cy));
+      store_partial(a, it.part_off + target_index(a, k),
+                    make_double2(double(sx) - double(cx), double(sy) - double(cy)));
     }
   }
   return true;
@@ -798,7 +817,7 @@ __device__ __forceinline__ bool run_item_f64(const PairArgs &a, const ItemDesc &
                                              uint32_t &g) {
   const int ntl = it.vt_end - it.vt_begin;
   const int loc = threadIdx.x;
-  const int i = it.tgt_begin + min(loc, it.tgt_count - 1);
+  const int i = target_index(a, it.tgt_begin + min(loc, it.tgt_count - 1));
   TgtF64<NIMG> t;
   {
     const double2 p = a.tgt[i];
@@ -816,7 +835,7 @@ __device__ __forceinline__ bool run_item_f64(const PairArgs &a, const ItemDesc &
   if (threadIdx.x == 0) {
     for (int r = 0; r < kStages && r < ntl; ++r) {
       const int st = (g + r) % kStages;
-      const int tile = item_tile(it, it.vt_begin + r);
+      const int tile = checked_tile(a, item_tile(it, it.vt_begin + r));
       mbar_arrive_expect_tx(&sm.bar[st], kBp + kBv);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF64, kBp, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF64, kBv, &sm.bar[st]);
@@ -855,14 +874,14 @@ __device__ __forceinline__ bool run_item_f64(const PairArgs &a, const ItemDesc &
       return false;
     }
     if (threadIdx.x == 0 && r + kStages < ntl) {
-      const int tile = item_tile(it, it.vt_begin + r + kStages);
+      const int tile = checked_tile(a, item_tile(it, it.vt_begin + r + kStages));
       mbar_arrive_expect_tx(&sm.bar[st], kBp + kBv);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * kTileF64, kBp, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * kTileF64, kBv, &sm.bar[st]);
     }
   }
   g += ntl;
-  if (loc < it.tgt_count) a.partial[it.part_off + it.tgt_begin + loc] = make_double2(ux, uy);
+  if (loc < it.tgt_count) store_partial(a, it.part_off + it.tgt_begin + loc, make_double2(ux, uy));
   return true;
 }
 
@@ -953,12 +972,18 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
   a.tgt_skip = skip;
   a.period = c->period;
   a.partial = partial;
+  // the context's own buffer has its allocated size; a caller's buffer the splits x targets
+  // this launch writes
+  a.partial_cap = std::max(0LL, (partial == c->d_partial ? (long long)c->partial_cap
+                                                         : (long long)splits * n_targets) -
+                                    c->debug_tighten);
   a.status = c->d_status;
   a.logtab = c->d_logtab;
   const bool img = c->period != 0.0;
   if (precision == STOKES_FP32_KAHAN) {
     a.n_wall_tiles = c->wall_slots / kTileF32;
     a.n_tiles = a.n_wall_tiles + c->ves_slots_f32 / kTileF32;
+    a.src_tiles = a.n_tiles;
     a.src_pos = c->d_src_pos32;
     a.src_val = c->d_src_val32;
     a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
@@ -973,6 +998,7 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
   } else {
     a.n_wall_tiles = c->wall_slots_f64 / kTileF64;
     a.n_tiles = a.n_wall_tiles + c->ves_slots_f64 / kTileF64;
+    a.src_tiles = a.n_tiles;
     a.src_pos = c->d_src_pos64;
     a.src_val = c->d_src_val64;
     a.tiles_per_split = (a.n_tiles + splits - 1) / splits;
@@ -992,6 +1018,7 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
   a.n_targets = c->N;
   a.tgt = c->d_x;
   a.partial = c->d_partial;
+  a.partial_cap = std::max(0LL, (long long)c->partial_cap - c->debug_tighten);
   a.status = c->d_status;
   a.counter = c->d_counter;
   a.logtab = c->d_logtab;
@@ -1002,6 +1029,7 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
     a.tgt_skip = c->d_tgt_skip32;
     a.src_pos = c->d_src_pos32;
     a.src_val = c->d_src_val32;
+    a.src_tiles = (c->wall_slots + c->ves_slots_f32) / kTileF32;
     a.items = c->d_items32;
     a.n_items = c->n_items32;
     a.tgt_perm = c->d_tgt_perm;
@@ -1011,6 +1039,7 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
     a.tgt_skip = c->d_tgt_skip64;
     a.src_pos = c->d_src_pos64;
     a.src_val = c->d_src_val64;
+    a.src_tiles = (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
     a.items = c->d_items64;
     a.n_items = c->n_items64;
     pick_f64(true, img)<<<blocks, kThreadsF64, 0, s>>>(a);

@@ -29,6 +29,8 @@
 // cp.async.bulk into a 3-stage mbarrier ring with bounded waits; 64 threads x 2 targets, the
 // two targets of a thread evaluated together by packed .f32x2 arithmetic (one instruction
 // for both; the MUFU approximation and the logarithm's bit work and tables per target).
+#include <algorithm>
+
 #include "stokes_internal.cuh"
 #include "bulk_pipe.cuh"
 
@@ -200,13 +202,15 @@ __global__ void src_pos_df_kernel(int slots, const int *slot_node, const double2
 __global__ void pack_df_kernel(int slots, int wall_slots, const int *slot_node,
                                const int *node_dens, const double *w, const double2 *nrm,
                                const double *slp, const double *dlp, double c_slp,
-                               unsigned *status, float4 *val) {
+                               unsigned *status, float4 *val, int N, int n_slp_rows,
+                               int n_dlp_rows) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= slots) return;
   const int i = slot_node[s];
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-  if (i >= 0) {
-    const int row = node_dens[i];
+  // node and density row bounds-checked in the debug build (out of range: a dummy slot)
+  const int row = (i >= 0 && dcheck(i < N, status)) ? node_dens[i] : -1;
+  if (row >= 0 && dcheck(row < (s < wall_slots ? n_dlp_rows : n_slp_rows), status)) {
     if (s < wall_slots) {
       const double t1 = dlp[2 * row], t2 = dlp[2 * row + 1];
       if (!isfinite(t1) || !isfinite(t2)) atomicOr(status, kStatusNonfinite);
@@ -276,6 +280,7 @@ struct TgtDF {
 template <int NIMG>
 __device__ __forceinline__ void load_target_df(const PairArgs &a, double period, int i,
                                                TgtDF<NIMG> &t) {
+  if (!dcheck(i >= 0 && i < a.n_targets, a.status)) i = 0;
   const double2 p = a.tgt[i];
   const double g_h = a.dfc->g_h, g_m = a.dfc->g_m;
 #pragma unroll
@@ -509,8 +514,11 @@ __device__ __forceinline__ void load_tables_df(const DFConst *d, SmemDF &sm) {
   for (int k = threadIdx.x; k < 256; k += blockDim.x) sm.et[k] = d->et[k];
 }
 
-__device__ __forceinline__ int item_tile_df(const ItemDesc &it, int vt) {
-  return vt < it.nw ? it.wb + vt : it.vb + (vt - it.nw);
+// Source tile of a staged copy: the item's virtual tile vt, bounds-checked in the debug build
+// (out of range: recorded in the status word and redirected to tile 0).
+__device__ __forceinline__ int item_tile_df(const PairArgs &a, const ItemDesc &it, int vt) {
+  const int tile = vt < it.nw ? it.wb + vt : it.vb + (vt - it.nw);
+  return dcheck(tile >= 0 && tile < a.src_tiles, a.status) ? tile : 0;
 }
 
 // One work item (as run_item_f64): targets [tgt_begin, +tgt_count), two per thread, against
@@ -534,7 +542,7 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
   if (threadIdx.x == 0) {
     for (int r = 0; r < kStages && r < ntl; ++r) {
       const int st = (g + r) % kStages;
-      const int tile = item_tile_df(it, it.vt_begin + r);
+      const int tile = item_tile_df(a, it, it.vt_begin + r);
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF64, kBytes, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF64, kBytes, &sm.bar[st]);
@@ -546,7 +554,7 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
     const bool ok = mbar_wait_bounded(&sm.bar[st], (gr / kStages) & 1u);
     if (ok) {
       const int vt = it.vt_begin + r;
-      const int tile = item_tile_df(it, vt);
+      const int tile = item_tile_df(a, it, vt);
       const float4 *P = sm.pos[st];
       const float4 *V = sm.val[st];
       static_assert(kTptDF == 2, "the packed double-float kernel takes two targets per thread");
@@ -602,7 +610,7 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
       return false;
     }
     if (threadIdx.x == 0 && r + kStages < ntl) {
-      const int tile = item_tile_df(it, it.vt_begin + r + kStages);
+      const int tile = item_tile_df(a, it, it.vt_begin + r + kStages);
       mbar_arrive_expect_tx(&sm.bar[st], 2 * kBytes);
       bulk_g2s(sm.pos[st], gpos + size_t(tile) * 2 * kTileF64, kBytes, &sm.bar[st]);
       bulk_g2s(sm.val[st], gval + size_t(tile) * 2 * kTileF64, kBytes, &sm.bar[st]);
@@ -612,8 +620,9 @@ __device__ __forceinline__ bool run_item_df(const PairArgs &a, const ItemDesc &i
 #pragma unroll
   for (int q = 0; q < kTptDF; ++q) {
     const int loc = q * kThreadsDF + int(threadIdx.x);
-    if (loc < it.tgt_count)
-      a.partial[it.part_off + it.tgt_begin + loc] = make_double2(ux[q], uy[q]);
+    const long long idx = it.part_off + it.tgt_begin + loc;
+    if (loc < it.tgt_count && dcheck(idx >= 0 && idx < a.partial_cap, a.status))
+      a.partial[idx] = make_double2(ux[q], uy[q]);
   }
   return true;
 }
@@ -686,13 +695,16 @@ cudaError_t launch_pack_df(stokes_ctx *c, const double *slp, const double *dlp, 
   const int slots = c->wall_slots_f64 + c->ves_slots_f64;
   pack_df_kernel<<<nblk_df(slots, 256), 256, 0, s>>>(
       slots, c->wall_slots_f64, c->d_slot_node64, c->d_node_dens, c->d_w, c->d_nrm, slp, dlp,
-      1.0 / (4.0 * kPi * c->mu), c->d_status, c->d_src_val_df);
+      1.0 / (4.0 * kPi * c->mu), c->d_status, c->d_src_val_df, c->N, c->n_ves_nodes,
+      c->n_wall_nodes);
   return cudaGetLastError();
 }
 
 static PairArgs df_args(stokes_ctx *c) {
   PairArgs a{};
   a.partial = c->d_partial;
+  a.partial_cap = std::max(0LL, (long long)c->partial_cap - c->debug_tighten);
+  a.src_tiles = (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
   a.status = c->d_status;
   a.dfc = c->d_dfc;
   a.src_pos = c->d_src_pos_df;
@@ -704,6 +716,8 @@ cudaError_t launch_pair_df(stokes_ctx *c, int n_targets, const double2 *tgt, con
                            int splits, double2 *partial, cudaStream_t s) {
   PairArgs a = df_args(c);
   a.partial = partial;
+  if (partial != c->d_partial)  // a caller's buffer: the splits x targets this launch writes
+    a.partial_cap = std::max(0LL, (long long)splits * n_targets - c->debug_tighten);
   a.n_targets = n_targets;
   a.tgt = tgt;
   a.tgt_skip = skip;

@@ -9,6 +9,8 @@
 //    fixed order, plus the wall Nystrom diagonal -kappa/(2 pi) t t^T w tau and jump * tau
 //    (Sec. 2.3, Eq. (JR)), plus the FP64 Kress self term of the single layer on each
 //    vesicle (Sec. 3.2).
+#include <algorithm>
+
 #include "stokes_internal.cuh"
 #include "bulk_pipe.cuh"
 
@@ -85,17 +87,27 @@ struct PackArgs {
   const double *slp, *dlp;
   double c_slp;  // 1 / (4 pi mu)
   unsigned *status;
+  int N, n_slp_rows, n_dlp_rows;  // nodes and density rows (debug bounds checks)
 };
+
+// Node and density row of source slot s, bounds-checked in the debug build: false (and the
+// slot packed as a zero-weight dummy) when either is out of range.
+__device__ __forceinline__ bool slot_source(const PackArgs &a, int s, int &i, int &row) {
+  i = a.slot_node[s];
+  if (i < 0 || !dcheck(i < a.N, a.status)) return false;
+  row = a.node_dens[i];
+  const int rows = s < a.wall_slots ? a.n_dlp_rows : a.n_slp_rows;
+  return dcheck(row >= 0 && row < rows, a.status);
+}
 
 // FP32 source records, duplicated like the coordinates: val[2s] = (q1, q1, q2, q2) and
 // val[2s+1] = (p1, p1, p2, p2) for a stokeslet source, (n1, n1, n2, n2) for a stresslet source.
 __global__ void pack_f32_kernel(PackArgs a, float4 *val) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.slots) return;
-  const int i = a.slot_node[s];
+  int i = -1, row = 0;
   float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-  if (i >= 0) {
-    const int row = a.node_dens[i];
+  if (slot_source(a, s, i, row)) {
     const double w = a.w[i];
     if (s < a.wall_slots) {
       const double t1 = a.dlp[2 * row], t2 = a.dlp[2 * row + 1];
@@ -124,10 +136,9 @@ __global__ void pack_f32_kernel(PackArgs a, float4 *val) {
 __global__ void pack_f64_kernel(PackArgs a, double4_32a *val) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.slots) return;
-  const int i = a.slot_node[s];
+  int i = -1, row = 0;
   double4_32a r = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-  if (i >= 0) {
-    const int row = a.node_dens[i];
+  if (slot_source(a, s, i, row)) {
     const double w = a.w[i];
     if (s < a.wall_slots) {
       const double t1 = a.dlp[2 * row], t2 = a.dlp[2 * row + 1];
@@ -155,6 +166,8 @@ struct PartLoc {
   const InstDev *inst;
   int f64;
   int N, splits;
+  long long cap;          // elements of the partial buffer (debug bounds checks)
+  unsigned *status;
 };
 
 __device__ __forceinline__ void part_sum(const PartLoc &L, const double2 *partial, int i,
@@ -174,7 +187,9 @@ __device__ __forceinline__ void part_sum(const PartLoc &L, const double2 *partia
   ux = 0.0;
   uy = 0.0;
   for (int k = 0; k < cnt; ++k) {
-    const double2 p = partial[base + (long long)k * stride];
+    const long long idx = base + (long long)k * stride;
+    if (!dcheck(idx >= 0 && idx < L.cap, L.status)) continue;
+    const double2 p = partial[idx];
     ux += p.x;
     uy += p.y;
   }
@@ -268,12 +283,15 @@ __global__ void finish_vesicle_nodes_kernel(int n_ves, const int *ves_nodes, Par
   out[i] = make_double2(ux + v.x, uy + v.y);
 }
 
-__global__ void finish_free_kernel(int T, int splits, const double2 *partial, double2 *out) {
+__global__ void finish_free_kernel(int T, int splits, const double2 *partial, long long cap,
+                                   unsigned *status, double2 *out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
   double ux = 0.0, uy = 0.0;
   for (int k = 0; k < splits; ++k) {
-    const double2 p = partial[size_t(k) * T + t];
+    const long long idx = (long long)k * T + t;
+    if (!dcheck(idx < cap, status)) continue;
+    const double2 p = partial[idx];
     ux += p.x;
     uy += p.y;
   }
@@ -345,6 +363,9 @@ cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const d
   a.dlp = dlp;
   a.c_slp = 1.0 / (4.0 * kPi * c->mu);
   a.status = c->d_status;
+  a.N = c->N;
+  a.n_slp_rows = c->n_ves_nodes;
+  a.n_dlp_rows = c->n_wall_nodes;
   if (precision == STOKES_DOUBLE_FLOAT) return launch_pack_df(c, slp, dlp, s);
   if (precision == STOKES_FP32_KAHAN) {
     a.slots = c->wall_slots + c->ves_slots_f32;
@@ -386,19 +407,23 @@ static cudaError_t finish_nodes(stokes_ctx *c, const PartLoc &L, const double *d
 cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, const double *dlp,
                                 double jump, double2 *out, cudaStream_t s) {
   (void)slp;
-  const PartLoc L{nullptr, nullptr, 0, c->N, splits};
+  const PartLoc L{nullptr, nullptr, 0, c->N, splits,
+                  std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status};
   return finish_nodes(c, L, dlp, jump, out, s);
 }
 
 cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp, double jump,
                                 double2 *out, cudaStream_t s) {
-  const PartLoc L{c->d_node_inst, c->d_inst, precision != STOKES_FP32_KAHAN ? 1 : 0, c->N, 0};
+  const PartLoc L{c->d_node_inst, c->d_inst, precision != STOKES_FP32_KAHAN ? 1 : 0, c->N, 0,
+                  std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status};
   return finish_nodes(c, L, dlp, jump, out, s);
 }
 
 cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2 *out,
                                cudaStream_t s) {
-  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(n_targets, splits, c->d_partial, out);
+  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(
+      n_targets, splits, c->d_partial,
+      std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status, out);
   return cudaGetLastError();
 }
 
@@ -409,7 +434,9 @@ namespace stokes {
 // Same as launch_finish_free, reading the partials from a caller-chosen buffer.
 cudaError_t launch_finish_free_scratch(int splits, int n_targets, const double2 *partial,
                                        double2 *out, cudaStream_t s) {
-  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(n_targets, splits, partial, out);
+  // the caller's buffer holds exactly the splits x targets partials (no status word here)
+  finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(
+      n_targets, splits, partial, (long long)splits * n_targets, nullptr, out);
   return cudaGetLastError();
 }
 

@@ -119,6 +119,12 @@ struct stokes_sim {
   // sums (0 = off); the plan is rebuilt every step on a host thread beside the GPU's work
   int resid_fmm_order = 0, resid_fmm_leaf = 32;
   stokes_fmm *fmm_v = nullptr;
+  // close evaluation of the vesicle-vesicle single layer (stokes_sim_set_close_eval): every
+  // vesicle sum of the step adds the correction of the close (node, vesicle image) pairs found
+  // for the step's positions; factor 0 = off
+  double close_factor = 0.0;
+  int close_K = 16;
+  stokes_close *close_v = nullptr;
 };
 
 namespace {
@@ -1171,6 +1177,19 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   return STOKES_OK;
 }
 
+// With close evaluation on: out (the vesicle node sum of density f) += the close correction.
+int add_close(stokes_sim *m, const double2 *f, double2 *out) {
+  if (!m->close_v) return STOKES_OK;
+  const int st = stokes_close_eval(m->close_v, reinterpret_cast<const double *>(f),
+                                   reinterpret_cast<double *>(out), m->s);
+  if (st) {
+    char buf[256];
+    stokes_close_last_error(m->close_v, buf, sizeof(buf));
+    return fail(m, st, "close evaluation: %s", buf);
+  }
+  return STOKES_OK;
+}
+
 // z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).
 int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, double *zout) {
   ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
@@ -1178,6 +1197,7 @@ int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, doub
   SK(cudaGetLastError());
   ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
                      0.0, reinterpret_cast<double *>(m->d_tmp3), m->s));
+  ST(add_close(m, m->d_tmp2, m->d_tmp3));
   ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
                                               zout);
   SK(cudaGetLastError());
@@ -1197,6 +1217,7 @@ int step_matvec_fmm(stokes_sim *m, double dt, const double *zin, double *zout) {
     stokes_fmm_last_error(m->fmm_v, buf, sizeof(buf));
     return fail(m, st, "FMM residual: %s", buf);
   }
+  ST(add_close(m, m->d_tmp2, m->d_tmp3));
   ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
                                               zout);
   SK(cudaGetLastError());
@@ -1426,6 +1447,8 @@ void free_walls(stokes_sim *m) {
 void free_vesicles(stokes_sim *m) {
   if (m->fmm_v) stokes_fmm_destroy(m->fmm_v);
   m->fmm_v = nullptr;
+  if (m->close_v) stokes_close_destroy(m->close_v);
+  m->close_v = nullptr;
   if (m->ctx_v) stokes_destroy(m->ctx_v);
   m->ctx_v = nullptr;
   double2 **p2[] = {&m->d_x, &m->d_nrm, &m->d_xs, &m->d_f, &m->d_fb, &m->d_ures, &m->d_tmp2, &m->d_tmp3};
@@ -1970,10 +1993,17 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   SK(cudaGetLastError());
   ST(stokes_geom_update(m->ctx_v, reinterpret_cast<double *>(m->d_x), m->d_w,
                         reinterpret_cast<double *>(m->d_nrm), nullptr, m->s));
+  if (m->close_v) {  // last step's pairs: its geometry is gone
+    stokes_close_destroy(m->close_v);
+    m->close_v = nullptr;
+  }
   FmmPlanJob plan_job;
-  if (use_fmm) {
-    SK(cudaStreamSynchronize(m->s));  // the plan thread reads the updated geometry
-    plan_job.start(m);
+  if (use_fmm || m->close_factor > 0.0)
+    SK(cudaStreamSynchronize(m->s));  // the plans read the updated geometry
+  if (use_fmm) plan_job.start(m);
+  if (m->close_factor > 0.0) {
+    const int cst = stokes_close_create(m->ctx_v, m->close_factor, m->close_K, &m->close_v);
+    if (cst) return fail(m, cst, "close-evaluation pairs: %s", m->ctx_v->err.c_str());
   }
   // step 2: forces
   ves_forces_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_sigma, m->d_D, m->d_spd, m->d_xs, m->kappa_b,
@@ -1995,6 +2025,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
                        reinterpret_cast<double *>(m->d_tmp3), m->s));
   }
+  ST(add_close(m, m->d_fb, m->d_tmp3));
   ves_rhs_kernel<<<V, n, 0, m->s>>>(n, m->d_tmp3, m->have_walls ? m->d_ures : nullptr, m->d_w,
                                     m->d_L0, dt, m->d_b, m->d_Lk);
   SK(cudaGetLastError());
@@ -2230,6 +2261,15 @@ int stokes_sim_set_warm_history(stokes_sim *m, int on) {
 int stokes_sim_get_warm_modes(const stokes_sim *m, int *modes) {
   if (!m || !modes) return STOKES_ERR_ARG;
   *modes = m->warm_modes;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_close_eval(stokes_sim *m, double factor, int upsample) {
+  if (!m) return STOKES_ERR_ARG;
+  if (!(factor == 0.0 || (factor > 0.0 && factor <= 50.0)) || upsample < 1 || upsample > 64)
+    return fail(m, STOKES_ERR_ARG, "close evaluation: factor 0 (off) or in (0, 50], upsample in [1, 64]");
+  m->close_factor = factor;
+  m->close_K = upsample;
   return STOKES_OK;
 }
 

@@ -63,6 +63,7 @@ void dfree(T *&p) {
 
 void free_geometry(stokes_ctx *c) {
   fmm_geometry_changed(c);
+  invalidate_node_graph(c);
   dfree(c->d_x);
   dfree(c->d_nrm);
   dfree(c->d_w);
@@ -124,6 +125,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 int ensure_partial(stokes_ctx *c, size_t elems) {
   if (elems <= c->partial_cap) return STOKES_OK;
   CK(cudaDeviceSynchronize());
+  invalidate_node_graph(c);
   dfree(c->d_partial);
   c->partial_cap = 0;
   CK(dalloc(c->d_partial, elems));
@@ -134,9 +136,10 @@ int ensure_partial(stokes_ctx *c, size_t elems) {
 // Wave model of the source splits.  The pair kernel runs (target blocks x splits) equal-cost
 // blocks in waves of `slots` = resident blocks per SM x SMs; the time is ~ waves x (1 / splits),
 // so a split count is costed as ceil(tb s / slots) / s plus a small per-split charge.  At least
-// 4 tiles per split keep the per-block prologue and the partial traffic small.  Returns
-// (cost, splits) for every split count that effective_splits leaves unchanged, in increasing
-// split order.
+// 4 tiles per split keep the per-block prologue and the partial traffic small -- unless even
+// then the blocks would not fill one wave (small geometries), where splits down to one tile
+// each are allowed.  Returns (cost, splits) for every split count that effective_splits leaves
+// unchanged, in increasing split order.
 std::vector<std::pair<double, int>> split_costs(stokes_ctx *c, int precision) {
   const bool f32 = precision == STOKES_FP32_KAHAN;
   const int per_block = f32 ? kThreadsF32 * c->tpt_f32
@@ -145,7 +148,8 @@ std::vector<std::pair<double, int>> split_costs(stokes_ctx *c, int precision) {
   const long tb = (c->N + per_block - 1) / per_block;
   const int n_tiles = f32 ? (c->wall_slots + c->ves_slots_f32) / kTileF32
                           : (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
-  const int smax = std::max(1, std::min(n_tiles / 4, 256));
+  const int floor_tiles = tb * std::max(1, n_tiles / 4) < slots ? 1 : 4;
+  const int smax = std::max(1, std::min(n_tiles / floor_tiles, 256));
   std::vector<std::pair<double, int>> out;
   for (int sp = 1; sp <= smax; ++sp) {
     const int eff = effective_splits(c, precision, sp);
@@ -183,6 +187,8 @@ int read_status(stokes_ctx *c, cudaStream_t s) {
   if (st) {
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s));
     CK(cudaStreamSynchronize(s));
+    if (st & kStatusBounds)
+      return fail(c, STOKES_ERR_BOUNDS, "a device bounds check failed (debug build)");
     if (st & kStatusTimeout)
       return fail(c, STOKES_ERR_TIMEOUT, "a device pipeline wait exceeded its bound");
     return fail(c, STOKES_ERR_NONFINITE, "non-finite input value");
@@ -234,9 +240,8 @@ int run_batch(stokes_ctx *c, int precision, const double *slp, const double *dlp
   return STOKES_OK;
 }
 
-int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
-              double *out, cudaStream_t s) {
-  if (c->n_inst > 1) return run_batch(c, precision, slp, dlp, jump, out, s);
+int run_nodes_direct(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                     double jump, double *out, cudaStream_t s) {
   const int splits = splits_of(c, precision);
   MARK(0);
   // fork: the FP64 Kress self pass runs on the side stream beside the pair kernel
@@ -258,7 +263,63 @@ int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp
   return STOKES_OK;
 }
 
+// Node sums of geometries up to this size are replayed from a graph in STOKES_GRAPH_SMALL mode
+// (there the five launches' host overhead is a visible share of the sum).
+constexpr int kGraphSmallMaxN = 65536;
+
+bool use_node_graph(const stokes_ctx *c) {
+  if (c->profiling || c->graph_mode == STOKES_GRAPH_OFF) return false;
+  return c->graph_mode == STOKES_GRAPH_ALWAYS || c->N <= kGraphSmallMaxN;
+}
+
+// The node sum as one graph launch: captured on the context's own stream (joined by the side
+// stream of the self pass through the fork/join events) for these pointers, then relaunched on
+// the caller's stream while they repeat.  A capture that fails falls back to direct launches.
+int run_nodes_graph(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                    double jump, double *out, cudaStream_t s) {
+  if (!(c->node_graph && c->ng_precision == precision && c->ng_jump == jump &&
+        c->ng_slp == slp && c->ng_dlp == dlp && c->ng_out == out)) {
+    invalidate_node_graph(c);
+    cudaStream_t cs = c->own_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const int st = run_nodes_direct(c, precision, slp, dlp, jump, out, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e2 =
+        (st == STOKES_OK && e == cudaSuccess) ? cudaGraphInstantiate(&exec, graph, 0) : e;
+    if (graph) cudaGraphDestroy(graph);
+    if (st != STOKES_OK || e2 != cudaSuccess) {
+      cudaGetLastError();  // clear a capture error; the direct path reports its own
+      return run_nodes_direct(c, precision, slp, dlp, jump, out, s);
+    }
+    c->node_graph = exec;
+    c->ng_precision = precision;
+    c->ng_jump = jump;
+    c->ng_slp = slp;
+    c->ng_dlp = dlp;
+    c->ng_out = out;
+  }
+  CK(cudaGraphLaunch(c->node_graph, s));
+  return STOKES_OK;
+}
+
+int run_nodes(stokes_ctx *c, int precision, const double *slp, const double *dlp, double jump,
+              double *out, cudaStream_t s) {
+  if (c->n_inst > 1) return run_batch(c, precision, slp, dlp, jump, out, s);
+  if (use_node_graph(c)) return run_nodes_graph(c, precision, slp, dlp, jump, out, s);
+  return run_nodes_direct(c, precision, slp, dlp, jump, out, s);
+}
+
 }  // namespace
+
+namespace stokes {
+void invalidate_node_graph(stokes_ctx *c) {
+  if (c->node_graph) cudaGraphExecDestroy(c->node_graph);
+  c->node_graph = nullptr;
+  c->ng_precision = -1;
+}
+}  // namespace stokes
 
 extern "C" {
 
@@ -294,6 +355,7 @@ int stokes_destroy(stokes_ctx *c) {
   if (!c) return STOKES_OK;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  invalidate_node_graph(c);
   free_geometry(c);
   dfree(c->d_partial);
   dfree(c->d_status);
@@ -809,6 +871,7 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
   int eff = splits ? effective_splits(c, precision, splits) : default_splits(c, precision);
   int st = ensure_partial(c, size_t(eff) * c->N);
   if (st) return st;
+  invalidate_node_graph(c);
   (precision == STOKES_FP32_KAHAN ? c->splits_f32
    : precision == STOKES_FP64    ? c->splits_f64
                                  : c->splits_df) = eff;
@@ -818,6 +881,37 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
 int stokes_set_local_frame(stokes_ctx *c, int on) {
   if (!c) return STOKES_ERR_ARG;
   c->local_frame = on != 0;
+  invalidate_node_graph(c);
+  return STOKES_OK;
+}
+
+int stokes_debug_build(void) {
+#ifdef STOKES_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int stokes_debug_tighten(stokes_ctx *c, long long elements) {
+  if (!c) return STOKES_ERR_ARG;
+#ifdef STOKES_DEBUG
+  if (elements < 0) return fail(c, STOKES_ERR_ARG, "elements < 0");
+  c->debug_tighten = elements;
+  invalidate_node_graph(c);
+  return STOKES_OK;
+#else
+  (void)elements;
+  return fail(c, STOKES_ERR_ARG, "release build: no device bounds checks to tighten");
+#endif
+}
+
+int stokes_set_graph_mode(stokes_ctx *c, int mode) {
+  if (!c) return STOKES_ERR_ARG;
+  if (mode != STOKES_GRAPH_OFF && mode != STOKES_GRAPH_SMALL && mode != STOKES_GRAPH_ALWAYS)
+    return fail(c, STOKES_ERR_ARG, "unknown graph mode %d", mode);
+  c->graph_mode = mode;
+  invalidate_node_graph(c);
   return STOKES_OK;
 }
 

@@ -16,6 +16,20 @@ constexpr double kPi = 3.14159265358979323846;
 // Device status word bits (set by kernels, read by stokes_sync).
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusBounds = 4u;
+
+// Device bounds checks of the debug build (-DSTOKES_DEBUG, libstokes_debug.so): dcheck(ok,
+// status) records kStatusBounds in the context's status word when ok is false and returns ok,
+// so the caller skips (or redirects to a valid element) the access it guards -- nothing traps.
+// In the release build it is the constant true and the checks compile away.
+#ifdef STOKES_DEBUG
+__device__ __forceinline__ bool dcheck(bool ok, unsigned *status) {
+  if (!ok && status) atomicOr(status, kStatusBounds);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dcheck(bool, unsigned *) { return true; }
+#endif
 
 // Source tile (one pipeline stage) lengths.
 constexpr int kTileF32 = 128;   // FP32 path: 128 sources x 32 B
@@ -83,6 +97,8 @@ struct PairArgs {
                             //   p2|n2); FP64: double4_32a
   // outputs
   double2 *partial;
+  long long partial_cap;    // elements of partial (debug bounds checks)
+  int src_tiles;            // tiles the source buffers hold (debug bounds checks)
   unsigned *status;
   const LogTab *logtab;     // FP64 logarithm table (flog64)
   const DFConst *dfc;       // double-float path: coordinate grids and logarithm tables
@@ -170,6 +186,8 @@ struct stokes_ctx {
   // scratch
   double2 *d_partial = nullptr;
   size_t partial_cap = 0;        // in double2 elements
+  long long debug_tighten = 0;   // debug build: elements the bounds checks take off the
+                                 //   partial buffer's capacity (stokes_debug_tighten)
   unsigned *d_status = nullptr;
   // host-API staging
   double *d_h_slp = nullptr, *d_h_dlp = nullptr, *d_h_out = nullptr;
@@ -191,6 +209,15 @@ struct stokes_ctx {
   double graph_jump[3] = {0.0, 0.0, 0.0};
   double *d_b_slp = nullptr, *d_b_dlp = nullptr, *d_b_out = nullptr;  // graph staging
 
+  // single-instance node sums replayed from a CUDA graph (stokes_set_graph_mode): the graph
+  // is captured for one (precision, jump, density and output pointers) and relaunched while
+  // those repeat; anything that changes what it captured drops it (invalidate_node_graph)
+  int graph_mode = 1;                    // STOKES_GRAPH_OFF / _SMALL / _ALWAYS
+  cudaGraphExec_t node_graph = nullptr;
+  int ng_precision = -1;
+  double ng_jump = 0.0;
+  const void *ng_slp = nullptr, *ng_dlp = nullptr, *ng_out = nullptr;
+
   // phase timing (stokes_set_profiling)
   bool profiling = false;
   bool timed = false;
@@ -198,6 +225,10 @@ struct stokes_ctx {
 };
 
 namespace stokes {
+// Drops the captured node-sum graph (its kernels hold the pointers and launch shape of the
+// moment of capture).  Called whenever the partial buffer, the launch shape or the geometry
+// changes.
+void invalidate_node_graph(stokes_ctx *c);
 int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const double *periods,
                  int n_curves, const int32_t *curve_offset, const int32_t *curve_kind,
                  const double *nodes, const double *weights, const double *normals,

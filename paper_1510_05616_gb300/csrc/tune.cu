@@ -90,18 +90,27 @@ bool same_shape(const Shape &a, const Shape &b) {
   return a.splits == b.splits && a.tpt == b.tpt && a.kg == b.kg && a.ips == b.ips;
 }
 
-// Split counts to time for one shape: the wave model's three cheapest, and two and four
-// times its cheapest (finer work units balance uneven tiles better than the model, which
-// costs every tile the same, predicts), as effective counts without repeats.
+// Split counts to time for one shape: the wave model's three cheapest, two and four times its
+// cheapest (finer work units balance uneven tiles better than the model, which costs every tile
+// the same, predicts), and the counts whose blocks fill exactly one or two waves of the resident
+// slots (fewest, longest blocks for that many waves), as effective counts without repeats.
 std::vector<int> split_candidates(stokes_ctx *c, int prec, int k) {
   std::vector<int> sp = stokes::ranked_splits(c, prec, k);
+  auto add = [&](int want) {
+    const int e = stokes::effective_splits(c, prec, want);
+    if (std::find(sp.begin(), sp.end(), e) == sp.end()) sp.push_back(e);
+  };
   if (!sp.empty()) {
     const int best = sp[0];
-    for (int f : {2, 4}) {
-      const int e = stokes::effective_splits(c, prec, best * f);
-      if (std::find(sp.begin(), sp.end(), e) == sp.end()) sp.push_back(e);
-    }
+    for (int f : {2, 4}) add(best * f);
   }
+  const bool f32 = prec == STOKES_FP32_KAHAN;
+  const long per_block = f32 ? long(stokes::kThreadsF32) * c->tpt_f32
+                             : prec == STOKES_DOUBLE_FLOAT ? long(stokes::kThreadsDF) * stokes::kTptDF
+                                                           : long(stokes::kThreadsF64);
+  const long tb = (c->N + per_block - 1) / per_block;
+  const long slots = long(stokes::pair_blocks_per_sm(c, prec)) * std::max(c->num_sms, 1);
+  for (int waves : {1, 2}) add(int(std::max(1L, (waves * slots) / std::max(tb, 1L))));
   return sp;
 }
 

@@ -12,6 +12,7 @@ namespace stokes {  // unused on the CPU: stubs for the linker
 cudaError_t launch_pack(stokes_ctx *, int, const double *, const double *, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t launch_finish_nodes(stokes_ctx *, int, const double *, const double *, double, double2 *, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t launch_self(stokes_ctx *, const double *, cudaStream_t) { return cudaErrorNotSupported; }
+void invalidate_node_graph(stokes_ctx *) {}
 }
 
 static double binom(int n, int k) {

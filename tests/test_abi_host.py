@@ -36,6 +36,17 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_debug_library_exports_the_same_and_says_so(lib):
+    """libstokes_debug.so (device bounds checks) is the same ABI; only it reports a debug
+    build, and only it accepts stokes_debug_tighten."""
+    import ctypes
+    from paper_1510_05616_gb300 import build
+    dbg = ctypes.CDLL(build.LIB_DEBUG)
+    missing = [n for n in _declared() if not hasattr(dbg, n)]
+    assert not missing, missing
+    assert dbg.stokes_debug_build() == 1 and lib.stokes_debug_build() == 0
+
+
 def test_binding_names_match_abi():
     import paper_1510_05616_gb300 as P
     for n in _declared():

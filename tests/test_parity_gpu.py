@@ -279,3 +279,59 @@ def test_local_frame_on_and_off(P, mid, paper, workload, tpt):
     assert np.array_equal(on, again)
     assert not np.array_equal(on, off)
     assert np.abs(on - off).max() <= 1e-6 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# node sums replayed from a captured CUDA graph
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "fp32k", "df"])
+def test_graph_replay_equals_direct_launches(P, oracle_mod, small, prec):
+    """The graph-replayed node sum is bit-identical to the direct launches, is recaptured when the
+    pointers, the launch shape or the partial buffer change, and stays equal to the oracle."""
+    import torch
+    g, slp, dlp, ref = small
+    s = P.StokesSum(g)
+    pc = P.PRECISIONS[prec]
+    ts, td = dev(P, slp), dev(P, dlp)
+    out_d = torch.empty((g.n_nodes, 2), dtype=torch.float64, device="cuda")
+    P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_OFF)
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, out_d)
+    P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_ALWAYS)
+    outs = []
+    for k in range(3):  # capture, then two replays
+        o = torch.empty_like(out_d) if k != 2 else outs[0]
+        P.stokes_sum_eval(s.h, pc, ts, td, 0.0, o)
+        P.stokes_sync(s.h)
+        outs.append(o.clone())
+    for o in outs:
+        assert torch.equal(o, out_d)
+    # new densities in the same buffers: the replay reads them
+    ts.mul_(-2.0)
+    td.mul_(0.5)
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, outs[0])
+    P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_OFF)
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, out_d)
+    P.stokes_sync(s.h)
+    assert torch.equal(outs[0], out_d)
+    # a new launch shape and a grown partial buffer (free targets) drop the graph
+    P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_ALWAYS)
+    P.stokes_set_launch(s.h, pc, 3)
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, outs[1])
+    tg = dev(P, np.stack([np.linspace(0.1, 6.0, 50000), np.zeros(50000)], 1))
+    ft = torch.empty_like(tg)
+    P.stokes_sum_eval_targets(s.h, pc, ts, td, tg, ft)
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, outs[2])
+    P.stokes_sync(s.h)
+    s.close()
+    o1, o2 = outs[1].cpu().numpy(), outs[2].cpu().numpy()
+    assert np.array_equal(o1, o2)
+    check(o1, oracle_mod.sum_nodes(g, -2.0 * slp, 0.5 * dlp), g, prec)
+
+
+def test_graph_mode_argument(P, small):
+    g, slp, dlp, _ = small
+    s = P.StokesSum(g)
+    with pytest.raises(P.StokesError) as e:
+        P.stokes_set_graph_mode(s.h, 7)
+    assert e.value.code == P.STOKES_ERR_ARG
+    s.close()

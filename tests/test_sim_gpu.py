@@ -111,12 +111,13 @@ def test_channel_response_parity(P, S):
     assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-9
 
 
-def _oracle_step(S, ves_x, dt, walls=None, p_drive=0.0, period=D, kappa_b=1.0, K=24, M=96):
+def _oracle_step(S, ves_x, dt, walls=None, p_drive=0.0, period=D, kappa_b=1.0, K=24, M=96,
+                 close=None):
     L0 = [S.perimeter(x) for x in ves_x]
     A0 = [S.area(x) for x in ves_x]
     W = S.Walls(walls[0], walls[1], D, MU, K=K, M=M) if walls is not None else None
     sig = [np.zeros(x.shape[0]) for x in ves_x]
-    return S.step(ves_x, sig, L0, A0, dt, kappa_b, MU, period, W, p_drive)
+    return S.step(ves_x, sig, L0, A0, dt, kappa_b, MU, period, W, p_drive, close=close)
 
 
 @pytest.mark.parametrize("period", [D, 0.0])
@@ -161,6 +162,40 @@ def test_channel_step_parity(P, S, prec):
           % (prec, eu, es, ex, st["iterations"], st["residual"]))
     assert eu < 1e-9 and es < 1e-9
     assert ex < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+def test_step_with_close_evaluation_matches_oracle(P, S, prec):
+    """Two vesicles half a node spacing apart: with close evaluation on, one step (FP64 sums,
+    or FP32-Kahan sweeps inside FP64-accurate refinement) equals the oracle's step whose
+    single-layer operator carries the close oracle's correction; without it the step differs
+    from that by far more."""
+    from types import SimpleNamespace
+    n = 32
+    t = 2 * PI * np.arange(n) / n
+    A = np.stack([0.3 * np.cos(t), 0.15 * np.sin(t)], 1)
+    h = np.sqrt((np.diff(np.vstack([A, A[:1]]), axis=0) ** 2).sum(1)).max()
+    B = A @ np.array([[np.cos(0.3), np.sin(0.3)], [-np.sin(0.3), np.cos(0.3)]]) + [0.6 + 0.5 * h, 0.02]
+    ves = [SimpleNamespace(nodes=X, n=n) for X in (A, B)]
+    dt, factor, K = 1e-3, 5.0, 16
+    ox, osg, u, sig, _ = _oracle_step(S, [A, B], dt, period=0.0, close=(factor, K))
+    res = {}
+    for on in (True, False):
+        h_sim = make_sim(P, None, ves, period=0.0)
+        if on:
+            P.stokes_sim_set_close_eval(h_sim, factor, K)
+        st = P.vesicle_step_warmstart(h_sim, dt, 0.0, tol=1e-12, max_iter=300,
+                                      precision=P.PRECISIONS[prec])
+        x, sg, sol = P.stokes_sim_get_state(h_sim)
+        P.stokes_sim_destroy(h_sim)
+        gu = np.concatenate([np.stack([sol[3 * n * v:3 * n * v + n], sol[3 * n * v + n:3 * n * v + 2 * n]], 1)
+                             for v in range(2)])
+        res[on] = (np.abs(gu - u).max() / np.abs(u).max(), np.abs(sg - sig).max() / np.abs(sig).max(),
+                   np.abs(x - np.vstack(ox)).max(), st["residual"])
+    print("close step (%s): with %s, without %s" % (prec, res[True], res[False]))
+    assert res[True][3] <= 1e-12
+    assert res[True][0] < 1e-8 and res[True][1] < 1e-8 and res[True][2] < 1e-10
+    assert res[False][0] > 100 * res[True][0]
 
 
 def test_fmm_residual_step_matches_double_float_step(P):
