@@ -2081,10 +2081,13 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     double prev = 1e300;
     bool finish64 = false;
     // A zero initial iterate needs no matvec (A 0 = 0).  A warm start's first residual only
-    // feeds an inner solve to ~1e-3, so it is taken with the FP32-Kahan operator; every later
-    // residual, and every convergence decision, uses the FP64-accurate one.
+    // feeds an inner solve to ~1e-3, so with double-float residuals (~8x an FP32-Kahan sum) it
+    // is taken with the FP32-Kahan operator; with FMM residuals it is taken accurately like
+    // every later one (a very good guess -- say an extrapolation -- leaves a residual below
+    // what the FP32-Kahan operator resolves, and the refinement would stall on its noise).
+    // Every convergence decision uses the FP64-accurate operator.
     bool zero_iterate = guess_mode == STOKES_GUESS_ZERO;
-    bool rough = !zero_iterate;
+    bool rough = !zero_iterate && !use_fmm;
     for (;;) {
       SK(cudaMemcpyAsync(m->d_rr, m->d_b, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
       if (!zero_iterate) {
