@@ -806,15 +806,26 @@ def run_scaling(args):
         for _ in range(3):
             P.stokes_sum_eval(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out)
         P.stokes_sync(s.h)
-        P.stokes_set_profiling(s.h, True)
-        ms, pair_ms = [], []
-        for _ in range(5):
+        # the sum's device time: sums issued back to back by the library (small geometries
+        # replay a captured graph) ...
+        ms = [P.stokes_time_sums(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out,
+                                 reps=50 if g.n_nodes < 100000 else 5) for _ in range(5)]
+        # ... the same one call at a time through the Python binding (host overhead included) ...
+        call_ms = []
+        for _ in range(7):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             P.stokes_sum_eval(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out)
             e1.record()
             torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            call_ms.append(e0.elapsed_time(e1))
+        graphs = P.stokes_graph_stats(s.h)
+        # ... and the pair kernel alone (phase events; profiled calls launch directly)
+        P.stokes_set_profiling(s.h, True)
+        pair_ms = []
+        for _ in range(5):
+            P.stokes_sum_eval(s.h, P.STOKES_FP32_KAHAN, ts, td, 0.0, out)
+            P.stokes_sync(s.h)
             pair_ms.append(P.stokes_last_timing(s.h)[1])
         P.stokes_set_profiling(s.h, False)
         pairs = P.stokes_pair_count(s.h)
@@ -826,6 +837,8 @@ def run_scaling(args):
         s.close()
         m, pm = statistics.median(ms), statistics.median(pair_ms)
         rows[name] = {"N": g.n_nodes, "pairs": pairs, "ms": m, "gpair_per_s": pairs / m / 1e6,
+                      "python_call_ms": statistics.median(call_ms),
+                      "graph_captures_launches": graphs,
                       "pair_ms": pm, "frac_fp32_fma_peak": FLOPS_PER_PAIR * pairs / (pm / 1e3) / 1e12 / peak,
                       "shape": {k2: tuned[k2] for k2 in ("source_splits", "targets_per_thread", "kahan_group")},
                       "rel_err_vs_oracle": err, "oracle_sample": int(k), "generation_s": gen_s}

@@ -215,10 +215,11 @@ STOKES_API int stokes_check_log64(stokes_ctx *ctx, const double *x, int n, doubl
  * context's status word and skips (or redirects to element 0) that access -- nothing traps --
  * and the next stokes_sync returns STOKES_ERR_BOUNDS (-9).  The release build (libstokes.so)
  * compiles the checks away.  stokes_debug_build returns 1 in the debug build, else 0.
+ * The partial-sum checks bound every launch by the elements it writes or reads itself.
  * stokes_debug_tighten (debug build only; STOKES_ERR_ARG in the release build or for
- * elements < 0) makes the checks treat the last `elements` elements of every partial-sum
- * buffer as out of range while the buffers keep their size, so a test can see a check fire
- * without any access leaving its allocation.  0 restores the real bounds.  For tests. */
+ * elements < 0) makes those checks treat the last `elements` of them as out of range while
+ * the buffers keep their size, so a test can see a check fire without any access leaving its
+ * allocation.  0 restores the real bounds.  For tests. */
 STOKES_API int stokes_debug_build(void);
 STOKES_API int stokes_debug_tighten(stokes_ctx *ctx, long long elements);
 
@@ -431,6 +432,16 @@ typedef enum {
     STOKES_GRAPH_ALWAYS = 2
 } stokes_graph_mode;
 STOKES_API int stokes_set_graph_mode(stokes_ctx *ctx, int mode);
+/* Node-sum graphs captured and graph launches made by the context so far (host counters). */
+STOKES_API int stokes_graph_stats(const stokes_ctx *ctx, long long *captures, long long *launches);
+/* GPU time of a node sum: `reps` calls of stokes_sum_eval's work issued back to back from the
+ * library on `stream` between two CUDA events, so the time is the device's, not a caller's
+ * per-call overhead; *ms_per_sum = elapsed / reps.  Same arguments and results as
+ * stokes_sum_eval (out holds the last call's velocities); synchronizes `stream` and returns the
+ * device status like stokes_sync.  STOKES_ERR_ARG for reps < 1 or NULL ms_per_sum. */
+STOKES_API int stokes_time_sums(stokes_ctx *ctx, int precision, const double *slp_density,
+                                const double *dlp_density, double jump, double *out_velocity,
+                                int reps, void *stream, double *ms_per_sum);
 
 /* Nominal pair-image evaluations of one stokes_sum_eval: 3 N_t N_s (1 N_t N_s when period
  * is 0), counting skipped and self pairs.  Written to *pairs. */

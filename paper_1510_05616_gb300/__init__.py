@@ -76,6 +76,8 @@ _SIGNATURES = {
     "stokes_check_log64": [_vp, _vp, _c_int, _vp, _vp],
     "stokes_set_graph_mode": [_vp, _c_int],
     "stokes_debug_build": [],
+    "stokes_graph_stats": [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+    "stokes_time_sums": [_vp, _c_int, _vp, _vp, _c_double, _vp, _c_int, _vp, ctypes.POINTER(_c_double)],
     "stokes_debug_tighten": [_vp, ctypes.c_longlong],
     "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
@@ -423,6 +425,24 @@ def stokes_num_nodes(h) -> int:
 def stokes_set_launch(h, precision, source_splits=0, targets_per_thread=0, kahan_group=0):
     return _check(h, load().stokes_set_launch(h, int(precision), int(source_splits),
                                               int(targets_per_thread), int(kahan_group)))
+
+
+def stokes_graph_stats(h):
+    """(graphs captured, graph launches) of the context's node sums."""
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(h, load().stokes_graph_stats(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def stokes_time_sums(h, precision, slp_density, dlp_density, jump, out_velocity, reps=20,
+                     stream=None):
+    """Device time per node sum (ms) of `reps` sums issued back to back by the library."""
+    ms = _c_double()
+    _check(h, load().stokes_time_sums(h, int(precision), _dptr(slp_density, "slp_density", (2,), True),
+                                      _dptr(dlp_density, "dlp_density", (2,), True), float(jump),
+                                      _dptr(out_velocity, "out_velocity", (2,)), int(reps),
+                                      _stream(stream), ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def stokes_debug_build() -> bool:

@@ -437,13 +437,16 @@ __global__ void set_identity_kernel(int n, double *K) {
 
 // y = M x for a column-major M (rows x cols, leading dimension rows), one right-hand side,
 // in two fixed-order passes: partial[ch][r] = sum over the columns of chunk ch of M[r, u] x[u]
-// (a CTA per (row tile, column chunk): a thread per row, the chunk of x staged in shared
-// memory, four columns in flight per thread; a warp reads 32 consecutive doubles of a column),
-// then y[r] = alpha sum_ch partial[ch][r] (+ y[r] when accumulate).  HBM-bound: M is read once.
-constexpr int kGemvRows = 256;     // rows per CTA (one per thread)
-constexpr int kGemvMaxChunk = 2048;  // columns per chunk (staged x: 16 KB)
+// (a CTA per (tile of kGemvRows rows, column chunk), the chunk of x staged in shared memory;
+// with an even leading dimension a thread takes two adjacent rows as one 16-byte load, else
+// one row; eight columns in flight per thread), then y[r] = alpha sum_ch partial[ch][r]
+// (+ y[r] when accumulate).  HBM-bound: M is read once.
+constexpr int kGemvThreads = 128;
+constexpr int kGemvRows = 2 * kGemvThreads;  // rows per CTA
+constexpr int kGemvMaxChunk = 2048;          // columns per chunk (staged x: 16 KB)
 
-__global__ void __launch_bounds__(kGemvRows)
+template <bool PAIR>
+__global__ void __launch_bounds__(kGemvThreads)
     gemv_cm_partial_kernel(int rows, int cols, int chunk, const double *__restrict__ M,
                            const double *__restrict__ x, double *__restrict__ partial) {
   __shared__ double xs[kGemvMaxChunk];
@@ -451,21 +454,48 @@ __global__ void __launch_bounds__(kGemvRows)
   const int nu = min(chunk, cols - u0);
   for (int j = threadIdx.x; j < nu; j += blockDim.x) xs[j] = x[u0 + j];
   __syncthreads();
-  const int r = blockIdx.x * kGemvRows + threadIdx.x;
-  if (r >= rows) return;
-  const double *Mr = M + size_t(u0) * rows + r;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int j = 0;
-  for (; j + 3 < nu; j += 4) {
-    const double m0 = __ldg(Mr + size_t(j) * rows), m1 = __ldg(Mr + size_t(j + 1) * rows);
-    const double m2 = __ldg(Mr + size_t(j + 2) * rows), m3 = __ldg(Mr + size_t(j + 3) * rows);
-    a0 = fma(m0, xs[j], a0);
-    a1 = fma(m1, xs[j + 1], a1);
-    a2 = fma(m2, xs[j + 2], a2);
-    a3 = fma(m3, xs[j + 3], a3);
+  constexpr int RPT = PAIR ? 2 : 1;  // rows per thread
+  for (int pass = 0; pass < 2 / RPT; ++pass) {
+    const int r = blockIdx.x * kGemvRows + (PAIR ? 2 * threadIdx.x : pass * kGemvThreads + threadIdx.x);
+    if (r >= rows) continue;
+    double a[4][RPT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < RPT; ++h) a[q][h] = 0.0;
+    const double *Mr = M + size_t(u0) * rows + r;
+    int j = 0;
+    for (; j + 7 < nu; j += 8) {
+      double m[8][RPT];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if constexpr (PAIR) {
+          const double2 v = __ldg(reinterpret_cast<const double2 *>(Mr + size_t(j + q) * rows));
+          m[q][0] = v.x;
+          m[q][RPT - 1] = v.y;
+        } else {
+          m[q][0] = __ldg(Mr + size_t(j + q) * rows);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int h = 0; h < RPT; ++h) a[q & 3][h] = fma(m[q][h], xs[j + q], a[q & 3][h]);
+    }
+    for (; j < nu; ++j) {
+      if constexpr (PAIR) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(Mr + size_t(j) * rows));
+        a[0][0] = fma(v.x, xs[j], a[0][0]);
+        a[0][RPT - 1] = fma(v.y, xs[j], a[0][RPT - 1]);
+      } else {
+        a[0][0] = fma(__ldg(Mr + size_t(j) * rows), xs[j], a[0][0]);
+      }
+    }
+    double *pr = partial + size_t(blockIdx.y) * rows + r;
+#pragma unroll
+    for (int h = 0; h < RPT; ++h)
+      if (r + h < rows) pr[h] = (a[0][h] + a[1][h]) + (a[2][h] + a[3][h]);
   }
-  for (; j < nu; ++j) a0 = fma(__ldg(Mr + size_t(j) * rows), xs[j], a0);
-  partial[size_t(blockIdx.y) * rows + r] = (a0 + a1) + (a2 + a3);
 }
 
 __global__ void gemv_reduce_kernel(int rows, int chunks, const double *partial, double alpha,
@@ -477,18 +507,36 @@ __global__ void gemv_reduce_kernel(int rows, int chunks, const double *partial, 
   y[r] = accumulate ? fma(alpha, acc, y[r]) : alpha * acc;
 }
 
-// X[:, c] -= L S[:, c] for the nc columns of X (nA x nc, ld nA) and S (l x nc, ld l): L is
-// block diagonal, one CTA per section block (rows x cols at (row0, col0), values column-major).
-__global__ void sub_blocks_kernel(const SecBlock *sec, const double *vals, int nA, int l, int nc,
-                                  const double *S, double *X) {
+// X[:, c] -= L S[:, c] for the nc columns of X (nA x nc, ld nA) and S (l x nc, ld l) over the
+// given section blocks (rows x cols at (row0, col0), values column-major); the blocks of one
+// launch must cover disjoint rows.  CTA (section blockIdx.x, rows [blockIdx.y kSubRows, ...)):
+// a thread per row, the section's coefficients s staged in shared memory; a warp reads 32
+// consecutive rows of one column.
+constexpr int kSubRows = 256;
+constexpr int kSubMaxCols = 2048;
+__global__ void __launch_bounds__(kSubRows)
+    sub_blocks_kernel(const SecBlock *sec, const double *vals, int nA, int l, int nc,
+                      const double *S, double *X) {
+  __shared__ double ss[kSubMaxCols];
   const SecBlock b = sec[blockIdx.x];
-  for (int idx = threadIdx.x; idx < b.rows * nc; idx += blockDim.x) {
-    const int i = idx % b.rows, c = idx / b.rows;
-    const double *v = vals + b.off + i;
-    const double *sc = S + size_t(c) * l + b.col0;
-    double acc = 0.0;
-    for (int q = 0; q < b.cols; ++q) acc = fma(v[size_t(q) * b.rows], sc[q], acc);
-    X[size_t(c) * nA + b.row0 + i] -= acc;
+  const int r0 = blockIdx.y * kSubRows;
+  if (r0 >= b.rows) return;  // uniform over the CTA
+  const int i = r0 + threadIdx.x;
+  for (int c = 0; c < nc; ++c) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < b.cols; q += blockDim.x) ss[q] = S[size_t(c) * l + b.col0 + q];
+    __syncthreads();
+    if (i < b.rows) {
+      const double *v = vals + b.off + i;
+      double a0 = 0.0, a1 = 0.0;
+      int q = 0;
+      for (; q + 1 < b.cols; q += 2) {
+        a0 = fma(v[size_t(q) * b.rows], ss[q], a0);
+        a1 = fma(v[size_t(q + 1) * b.rows], ss[q + 1], a1);
+      }
+      if (q < b.cols) a0 = fma(v[size_t(q) * b.rows], ss[q], a0);
+      X[size_t(c) * nA + b.row0 + i] -= a0 + a1;
+    }
   }
 }
 
@@ -516,6 +564,9 @@ struct fds_solver {
   SecBlock *d_sec = nullptr;
   double *d_svals = nullptr;
   int n_sec = 0;
+  int n_sec_left = 0;                  // sections of the m = -1 neighbour (they come first);
+                                       //   each neighbour's sections partition both walls
+  int sub_row_chunks = 1;              // row chunks of the largest section (grid.y)
   double *d_gpart = nullptr;           // partial sums of the one-right-hand-side products
   int gemv_chunks_R = 1, gemv_chunks_K = 1;
   int chunk_R = 1, chunk_K = 1;
@@ -636,6 +687,7 @@ struct HostFactors {
   std::vector<double> mats;               // F^*, E, G per box, then G_root
   std::vector<std::vector<HbsBox>> tabs;  // [L + 1], tabs[0] = the root
   std::vector<int> Jall, mall;            // neighbour skeleton unknowns and their image m
+  std::vector<int> sec_m;                 // image m of every section block
   std::vector<SecBlock> sb;               // L's blocks
   std::vector<double> svals;
   int max_cols = 0;                       // widest level product
@@ -921,6 +973,7 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
     b.off = (long long)hf.svals.size();
     hf.svals.insert(hf.svals.end(), sc.P.a.begin(), sc.P.a.end());
     hf.sb.push_back(b);
+    hf.sec_m.push_back(sc.m);
     for (int u : sc.skel) {
       hf.Jall.push_back(u);
       hf.mall.push_back(sc.m);
@@ -1030,6 +1083,20 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
   FD(cudaGetLastError());
   // Z = A_0^-1 L
   f->n_sec = int(hf.sb.size());
+  f->n_sec_left = 0;
+  while (f->n_sec_left < f->n_sec && hf.sec_m[f->n_sec_left] < 0) ++f->n_sec_left;
+  for (const SecBlock &b : hf.sb) {
+    f->sub_row_chunks = std::max(f->sub_row_chunks, (b.rows + kSubRows - 1) / kSubRows);
+    if (b.cols > kSubMaxCols) {
+      err = "fds: a neighbour section's rank exceeds the staging buffer";
+      return bail(STOKES_ERR_ARG);
+    }
+  }
+  for (int q = f->n_sec_left; q < f->n_sec; ++q)
+    if (hf.sec_m[q] < 0) {
+      err = "fds: neighbour sections are not grouped by image";
+      return bail(STOKES_ERR_ARG);
+    }
   FD(dalloc(f->d_sec, hf.sb.size(), bytes));
   FD(dalloc(f->d_svals, hf.svals.size(), bytes));
   FD(cudaMemcpyAsync(f->d_sec, hf.sb.data(), sizeof(SecBlock) * hf.sb.size(), cudaMemcpyHostToDevice, s));
@@ -1042,7 +1109,7 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int row_tiles = std::max(1, (l + kGemvRows - 1) / kGemvRows);
     auto plan = [&](int cols, int &chunk, int &chunks) {
-      const int want = std::max(1, 4 * std::max(sms, 1) / row_tiles);
+      const int want = std::max(1, 8 * std::max(sms, 1) / row_tiles);
       chunk = std::min(kGemvMaxChunk, std::max(64, (cols + want - 1) / want));
       chunks = std::max(1, (cols + chunk - 1) / chunk);
     };
@@ -1111,7 +1178,10 @@ int gemv_rows(fds_solver *f, const double *M, int cols, int chunk, int chunks, c
               double *t, cudaStream_t s, std::string &err) {
   const int l = f->l;
   dim3 grid((l + kGemvRows - 1) / kGemvRows, chunks);
-  gemv_cm_partial_kernel<<<grid, kGemvRows, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  if (l % 2 == 0)  // column starts stay 16-byte aligned: two rows per load
+    gemv_cm_partial_kernel<true><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  else
+    gemv_cm_partial_kernel<false><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
   gemv_reduce_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, chunks, f->d_gpart, 1.0, 0, t);
   FK(cudaGetLastError());
   return STOKES_OK;
@@ -1141,8 +1211,15 @@ int fds_solve(fds_solver *f, double *X, int nrhs, cudaStream_t s, cublasHandle_t
         FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->l, &one, f->d_Kinv, f->l,
                        f->d_t, f->l, &zero, f->d_s, f->l));
       }
-      // v <- v - L s, then x = A_0^-1 v
-      sub_blocks_kernel<<<f->n_sec, 256, 0, s>>>(f->d_sec, f->d_svals, f->nA, f->l, nc, f->d_s, Xc);
+      // v <- v - L s, then x = A_0^-1 v.  The two neighbours' sections each cover both walls,
+      // so their row ranges overlap: one launch per neighbour (disjoint rows within each, and
+      // a fixed order of the two updates)
+      if (f->n_sec_left > 0)
+        sub_blocks_kernel<<<dim3(f->n_sec_left, f->sub_row_chunks), kSubRows, 0, s>>>(
+            f->d_sec, f->d_svals, f->nA, f->l, nc, f->d_s, Xc);
+      if (f->n_sec > f->n_sec_left)
+        sub_blocks_kernel<<<dim3(f->n_sec - f->n_sec_left, f->sub_row_chunks), kSubRows, 0, s>>>(
+            f->d_sec + f->n_sec_left, f->d_svals, f->nA, f->l, nc, f->d_s, Xc);
       FK(cudaGetLastError());
       st = hbs_pass(f, Xc, f->d_out, nc, s, err);
       if (st) return st;

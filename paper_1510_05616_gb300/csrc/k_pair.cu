@@ -974,9 +974,9 @@ cudaError_t launch_pair(stokes_ctx *c, int precision, int n_targets, const doubl
   a.partial = partial;
   // the context's own buffer has its allocated size; a caller's buffer the splits x targets
   // this launch writes
-  a.partial_cap = std::max(0LL, (partial == c->d_partial ? (long long)c->partial_cap
-                                                         : (long long)splits * n_targets) -
-                                    c->debug_tighten);
+  a.partial_cap = partial_check_cap(
+      c, partial == c->d_partial ? (long long)c->partial_cap : (long long)splits * n_targets,
+      (long long)splits * n_targets);
   a.status = c->d_status;
   a.logtab = c->d_logtab;
   const bool img = c->period != 0.0;
@@ -1018,7 +1018,8 @@ cudaError_t launch_pair_batch(stokes_ctx *c, int precision, int blocks, cudaStre
   a.n_targets = c->N;
   a.tgt = c->d_x;
   a.partial = c->d_partial;
-  a.partial_cap = std::max(0LL, (long long)c->partial_cap - c->debug_tighten);
+  a.partial_cap = partial_check_cap(c, (long long)c->partial_cap,
+                                    precision == STOKES_FP32_KAHAN ? c->batch_part32 : c->batch_part64);
   a.status = c->d_status;
   a.counter = c->d_counter;
   a.logtab = c->d_logtab;

@@ -703,7 +703,7 @@ cudaError_t launch_pack_df(stokes_ctx *c, const double *slp, const double *dlp, 
 static PairArgs df_args(stokes_ctx *c) {
   PairArgs a{};
   a.partial = c->d_partial;
-  a.partial_cap = std::max(0LL, (long long)c->partial_cap - c->debug_tighten);
+  a.partial_cap = partial_check_cap(c, (long long)c->partial_cap, c->batch_part64);
   a.src_tiles = (c->wall_slots_f64 + c->ves_slots_f64) / kTileF64;
   a.status = c->d_status;
   a.dfc = c->d_dfc;
@@ -716,8 +716,9 @@ cudaError_t launch_pair_df(stokes_ctx *c, int n_targets, const double2 *tgt, con
                            int splits, double2 *partial, cudaStream_t s) {
   PairArgs a = df_args(c);
   a.partial = partial;
-  if (partial != c->d_partial)  // a caller's buffer: the splits x targets this launch writes
-    a.partial_cap = std::max(0LL, (long long)splits * n_targets - c->debug_tighten);
+  a.partial_cap = partial_check_cap(
+      c, partial == c->d_partial ? (long long)c->partial_cap : (long long)splits * n_targets,
+      (long long)splits * n_targets);
   a.n_targets = n_targets;
   a.tgt = tgt;
   a.tgt_skip = skip;

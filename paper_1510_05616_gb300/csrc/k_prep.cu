@@ -270,6 +270,81 @@ __global__ void self_kress_kernel(const int *ves_curves, const CurveDev *curves,
   }
 }
 
+// The same Kress blocks stored (geometry only): thread p = k n + a of vesicle blockIdx.y writes
+// G11, G12, G22 of the block c_slp s_k [coef I + h M] (coef and M as in self_kress_kernel) to
+// G[off + p], G[off + n^2 + p], G[off + 2 n^2 + p].
+__global__ void self_matrix_kernel(const int *ves_curves, const CurveDev *curves,
+                                   const long long *g_off, const double *kress, const double2 *x,
+                                   const double2 *nrm, const double *w, double c_slp,
+                                   const LogTab *lt, double *G) {
+  const CurveDev cv = curves[ves_curves[blockIdx.y]];
+  const int n = cv.n;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n * n) return;
+  const int k = p / n, a = p - k * n;
+  const double h = 2.0 * kPi / n;
+  const double pin = kPi / n;
+  const double *T = kress + cv.kress_off;
+  const int i = cv.node_begin + a, j = cv.node_begin + k;
+  double coef, m11, m12, m22;
+  if (k == a) {
+    const double sp = w[i] / h;
+    const double2 nn = nrm[i];
+    const double tx = -nn.y, ty = nn.x;
+    coef = T[0] - pin * flog64(sp * sp, lt);
+    m11 = tx * tx;
+    m12 = tx * ty;
+    m22 = ty * ty;
+  } else {
+    const double2 xa = x[i], xk = x[j];
+    const double rx = xa.x - xk.x, ry = xa.y - xk.y;
+    const double rr = rx * rx + ry * ry;
+    const double inv = 1.0 / rr;
+    int dj = a - k;
+    if (dj < 0) dj += n;
+    coef = T[dj] - pin * flog64(rr, lt);
+    m11 = rx * rx * inv;
+    m12 = rx * ry * inv;
+    m22 = ry * ry * inv;
+  }
+  const double sc = c_slp * (w[j] / h);  // density scale of source node k: c_slp s_k
+  double *Gv = G + g_off[blockIdx.y];
+  const size_t nn2 = size_t(n) * n;
+  Gv[p] = sc * (coef + h * m11);
+  Gv[nn2 + p] = sc * (h * m12);
+  Gv[2 * nn2 + p] = sc * (coef + h * m22);
+}
+
+// u_self(a) = sum_k G_ak f_k from the stored blocks: one block per vesicle, the density staged
+// in shared memory, a thread per target node reading column-contiguous G (coalesced).
+__global__ void self_apply_kernel(const int *ves_curves, const CurveDev *curves,
+                                  const long long *g_off, const double *G, const double *slp,
+                                  double2 *self) {
+  extern __shared__ double sh[];
+  const CurveDev cv = curves[ves_curves[blockIdx.x]];
+  const int n = cv.n;
+  double *f1 = sh, *f2 = sh + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int row = cv.dens_begin + k;
+    f1[k] = slp[2 * row];
+    f2[k] = slp[2 * row + 1];
+  }
+  __syncthreads();
+  const double *G11 = G + g_off[blockIdx.x];
+  const size_t nn2 = size_t(n) * n;
+  const double *G12 = G11 + nn2, *G22 = G11 + 2 * nn2;
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    double vx = 0.0, vy = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const size_t e = size_t(k) * n + a;
+      const double g11 = G11[e], g12 = G12[e], g22 = G22[e];
+      vx = fma(g11, f1[k], fma(g12, f2[k], vx));
+      vy = fma(g12, f1[k], fma(g22, f2[k], vy));
+    }
+    self[cv.dens_begin + a] = make_double2(vx, vy);
+  }
+}
+
 // Vesicle nodes: FP64 fixed-order reduction of the split partials plus the self term.
 __global__ void finish_vesicle_nodes_kernel(int n_ves, const int *ves_nodes, PartLoc L,
                                             const double2 *partial, const int *node_dens,
@@ -303,6 +378,8 @@ __global__ void finish_free_kernel(int T, int splits, const double2 *partial, lo
 // ---------------------------------------------------------------------------
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
+cudaError_t launch_self_matrix(stokes_ctx *c, cudaStream_t s);
+
 cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s) {
   const int s32 = c->wall_slots + c->ves_slots_f32;
   const int s64 = c->wall_slots_f64 + c->ves_slots_f64;
@@ -311,7 +388,8 @@ cudaError_t launch_geom_prep(stokes_ctx *c, cudaStream_t s) {
                                                     c->d_status);
   src_pos32_kernel<<<nblk(s32, 256), 256, 0, s>>>(s32, c->d_slot_node32, c->d_x, c->d_src_pos32);
   src_pos64_kernel<<<nblk(s64, 256), 256, 0, s>>>(s64, c->d_slot_node64, c->d_x, c->d_src_pos64);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_self_matrix(c, s);
   if (e != cudaSuccess) return e;
   return launch_geom_prep_df(c, s);
 }
@@ -381,7 +459,22 @@ cudaError_t launch_pack(stokes_ctx *c, int precision, const double *slp, const d
   return cudaGetLastError();
 }
 
+cudaError_t launch_self_matrix(stokes_ctx *c, cudaStream_t s) {
+  if (!c->self_matrix || c->n_ves_curves == 0) return cudaSuccess;
+  const int nn = c->max_ves_n * c->max_ves_n;
+  self_matrix_kernel<<<dim3(nblk(nn, 256), c->n_ves_curves), 256, 0, s>>>(
+      c->d_ves_curve_ids, c->d_curves, c->d_selfG_off, c->d_kress, c->d_x, c->d_nrm, c->d_w,
+      1.0 / (4.0 * kPi * c->mu), c->d_logtab, c->d_selfG);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_self(stokes_ctx *c, const double *slp, cudaStream_t s) {
+  if (c->n_ves_curves > 0 && c->self_matrix) {
+    self_apply_kernel<<<c->n_ves_curves, std::min(256, (c->max_ves_n + 31) / 32 * 32),
+                        size_t(2) * c->max_ves_n * sizeof(double), s>>>(
+        c->d_ves_curve_ids, c->d_curves, c->d_selfG_off, c->d_selfG, slp, c->d_self);
+    return cudaGetLastError();
+  }
   if (c->n_ves_curves > 0) {
     const size_t smem = size_t(4) * c->max_ves_n * sizeof(double);
     self_kress_kernel<<<c->n_ves_curves, 128, smem, s>>>(c->d_ves_curve_ids, c->d_curves,
@@ -408,14 +501,17 @@ cudaError_t launch_finish_nodes(stokes_ctx *c, int splits, const double *slp, co
                                 double jump, double2 *out, cudaStream_t s) {
   (void)slp;
   const PartLoc L{nullptr, nullptr, 0, c->N, splits,
-                  std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status};
+                  partial_check_cap(c, (long long)c->partial_cap, (long long)splits * c->N),
+                  c->d_status};
   return finish_nodes(c, L, dlp, jump, out, s);
 }
 
 cudaError_t launch_finish_batch(stokes_ctx *c, int precision, const double *dlp, double jump,
                                 double2 *out, cudaStream_t s) {
   const PartLoc L{c->d_node_inst, c->d_inst, precision != STOKES_FP32_KAHAN ? 1 : 0, c->N, 0,
-                  std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status};
+                  partial_check_cap(c, (long long)c->partial_cap,
+                                    precision == STOKES_FP32_KAHAN ? c->batch_part32 : c->batch_part64),
+                  c->d_status};
   return finish_nodes(c, L, dlp, jump, out, s);
 }
 
@@ -423,7 +519,8 @@ cudaError_t launch_finish_free(stokes_ctx *c, int splits, int n_targets, double2
                                cudaStream_t s) {
   finish_free_kernel<<<nblk(n_targets, 256), 256, 0, s>>>(
       n_targets, splits, c->d_partial,
-      std::max(0LL, (long long)c->partial_cap - c->debug_tighten), c->d_status, out);
+      partial_check_cap(c, (long long)c->partial_cap, (long long)splits * n_targets), c->d_status,
+      out);
   return cudaGetLastError();
 }
 

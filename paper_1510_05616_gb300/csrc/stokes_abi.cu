@@ -75,6 +75,9 @@ void free_geometry(stokes_ctx *c) {
   dfree(c->d_ves_nodes);
   dfree(c->d_tgt_perm);
   dfree(c->d_self);
+  dfree(c->d_selfG);
+  dfree(c->d_selfG_off);
+  c->self_matrix = false;
   dfree(c->d_node_inst);
   dfree(c->d_inst);
   dfree(c->d_items32);
@@ -294,6 +297,7 @@ int run_nodes_graph(stokes_ctx *c, int precision, const double *slp, const doubl
       return run_nodes_direct(c, precision, slp, dlp, jump, out, s);
     }
     c->node_graph = exec;
+    ++c->graph_captures;
     c->ng_precision = precision;
     c->ng_jump = jump;
     c->ng_slp = slp;
@@ -301,6 +305,7 @@ int run_nodes_graph(stokes_ctx *c, int precision, const double *slp, const doubl
     c->ng_out = out;
   }
   CK(cudaGraphLaunch(c->node_graph, s));
+  ++c->graph_replays;
   return STOKES_OK;
 }
 
@@ -652,6 +657,20 @@ int set_geometry(stokes_ctx *c, int n_inst, const int *inst_curve_off, const dou
   }
   CK(dalloc(c->d_self, n_ves));
   CK(dalloc(c->d_kress, kress_len));
+  {  // stored Kress self blocks, when they fit
+    std::vector<long long> goff;
+    long long total = 0;
+    for (int cc : ves_ids) {
+      const long long n = curve_offset[cc + 1] - curve_offset[cc];
+      goff.push_back(total);
+      total += 3 * n * n;
+    }
+    c->self_matrix = !goff.empty() && total * long(sizeof(double)) <= kSelfMatrixMaxBytes;
+    if (c->self_matrix) {
+      CK(dalloc(c->d_selfG, size_t(total)));
+      CK(upload(c->d_selfG_off, goff, s));
+    }
+  }
   CK(dalloc(c->d_src_pos32, 2 * slot32.size()));
   CK(dalloc(c->d_src_val32, 2 * slot32.size()));
   CK(dalloc(c->d_src_pos64, slot64.size()));
@@ -885,6 +904,40 @@ int stokes_set_local_frame(stokes_ctx *c, int on) {
   return STOKES_OK;
 }
 
+int stokes_graph_stats(const stokes_ctx *c, long long *captures, long long *launches) {
+  if (!c || !captures || !launches) return STOKES_ERR_ARG;
+  *captures = c->graph_captures;
+  *launches = c->graph_replays;
+  return STOKES_OK;
+}
+
+int stokes_time_sums(stokes_ctx *c, int precision, const double *slp, const double *dlp,
+                     double jump, double *out, int reps, void *stream, double *ms_per_sum) {
+  if (!c || !ms_per_sum || reps < 1) return STOKES_ERR_ARG;
+  int st = check_density_args(c, precision, slp, dlp);
+  if (st) return st;
+  if (!out || !aligned16(out)) return fail(c, STOKES_ERR_ARG, "out_velocity must be a 16-byte aligned device pointer");
+  if (!isfinite(jump)) return fail(c, STOKES_ERR_ARG, "jump must be finite");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && e == cudaSuccess && st == STOKES_OK; ++r)
+    st = run_nodes(c, precision, slp, dlp, jump, out, s);
+  if (e == cudaSuccess && st == STOKES_OK) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess && st == STOKES_OK) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess && st == STOKES_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "stokes_time_sums");
+  *ms_per_sum = double(ms) / reps;
+  return read_status(c, s);
+}
+
 int stokes_debug_build(void) {
 #ifdef STOKES_DEBUG
   return 1;
@@ -1019,6 +1072,7 @@ int build_items(stokes_ctx *c, int precision, size_t *partial_elems) {
   dfree(dst);
   CK(upload(dst, items, c->own_stream));
   (f32 ? c->n_items32 : c->n_items64) = int(items.size());
+  (f32 ? c->batch_part32 : c->batch_part64) = off;
   *partial_elems = size_t(off);
   return STOKES_OK;
 }

@@ -45,6 +45,9 @@ constexpr int kThreadsDF = 64;  // double-float path: 64 threads x 2 targets, FP
 constexpr int kTptDF = 2;
 
 constexpr int kMaxVesicleNodes = 1024;  // Kress self pass stages one curve in shared memory
+// Largest stored Kress self matrix (all vesicles, 24 n^2 bytes each); beyond it the self term
+// is recomputed from the geometry on every sum.
+constexpr long long kSelfMatrixMaxBytes = 4LL << 30;
 
 // Per-curve description used by the finishing kernel.
 struct CurveDev {
@@ -167,6 +170,13 @@ struct stokes_ctx {
   int *d_tgt_perm = nullptr;     // [N] FP32 node-evaluation target order: per instance, walls in
                                  //   node order, then vesicles by Morton code of their centroid
   double2 *d_self = nullptr;     // [n_ves_nodes] Kress self term, by vesicle density row
+  // Kress self blocks assembled per geometry (when they fit kSelfMatrixMaxBytes): for vesicle
+  // v (in d_ves_curve_ids order) three n x n arrays (11, 12, 22) at d_selfG + d_selfG_off[v],
+  // element k n + a the 2 x 2 block that node k's density contributes at node a; each sum's
+  // self term is then a batched matvec instead of an FP64 pass over all the logs
+  double *d_selfG = nullptr;
+  long long *d_selfG_off = nullptr;
+  bool self_matrix = false;
   stokes::CurveDev *d_curves = nullptr;  // [n_curves]
   int *d_ves_curve_ids = nullptr;        // [n_ves_curves]
   double *d_kress = nullptr;             // concatenated Kress tables T_j per vesicle size
@@ -187,7 +197,8 @@ struct stokes_ctx {
   double2 *d_partial = nullptr;
   size_t partial_cap = 0;        // in double2 elements
   long long debug_tighten = 0;   // debug build: elements the bounds checks take off the
-                                 //   partial buffer's capacity (stokes_debug_tighten)
+                                 //   partial sums a launch writes or reads (stokes_debug_tighten)
+  long long batch_part32 = 0, batch_part64 = 0;  // partial sums of one batched evaluation
   unsigned *d_status = nullptr;
   // host-API staging
   double *d_h_slp = nullptr, *d_h_dlp = nullptr, *d_h_out = nullptr;
@@ -217,6 +228,7 @@ struct stokes_ctx {
   int ng_precision = -1;
   double ng_jump = 0.0;
   const void *ng_slp = nullptr, *ng_dlp = nullptr, *ng_out = nullptr;
+  long long graph_captures = 0, graph_replays = 0;  // node-sum graphs captured / launched
 
   // phase timing (stokes_set_profiling)
   bool profiling = false;
@@ -225,6 +237,13 @@ struct stokes_ctx {
 };
 
 namespace stokes {
+// Bound the debug build's checks put on a launch's partial-sum indices: the elements the
+// launch writes or reads (`needed`, within the allocation of `allocated`), less the elements
+// stokes_debug_tighten takes off.
+inline long long partial_check_cap(const stokes_ctx *c, long long allocated, long long needed) {
+  const long long cap = needed < allocated ? needed : allocated;
+  return cap > c->debug_tighten ? cap - c->debug_tighten : 0;
+}
 // Drops the captured node-sum graph (its kernels hold the pointers and launch shape of the
 // moment of capture).  Called whenever the partial buffer, the launch shape or the geometry
 // changes.

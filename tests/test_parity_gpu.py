@@ -297,14 +297,20 @@ def test_graph_replay_equals_direct_launches(P, oracle_mod, small, prec):
     P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_OFF)
     P.stokes_sum_eval(s.h, pc, ts, td, 0.0, out_d)
     P.stokes_set_graph_mode(s.h, P.STOKES_GRAPH_ALWAYS)
+    o = torch.empty_like(out_d)
     outs = []
-    for k in range(3):  # capture, then two replays
-        o = torch.empty_like(out_d) if k != 2 else outs[0]
+    for k in range(3):  # one capture, three launches of it
+        o.fill_(float("nan"))
         P.stokes_sum_eval(s.h, pc, ts, td, 0.0, o)
         P.stokes_sync(s.h)
         outs.append(o.clone())
-    for o in outs:
-        assert torch.equal(o, out_d)
+    for x in outs:
+        assert torch.equal(x, out_d)
+    assert P.stokes_graph_stats(s.h) == (1, 3)
+    outs[0] = torch.empty_like(out_d)  # a new output pointer: captured anew
+    P.stokes_sum_eval(s.h, pc, ts, td, 0.0, outs[0])
+    P.stokes_sync(s.h)
+    assert torch.equal(outs[0], out_d) and P.stokes_graph_stats(s.h) == (2, 4)
     # new densities in the same buffers: the replay reads them
     ts.mul_(-2.0)
     td.mul_(0.5)
