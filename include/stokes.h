@@ -388,7 +388,7 @@ STOKES_API int stokes_batch_info(const stokes_ctx *ctx, int precision, int *n_it
  *                       FP64 in fixed order; 0 = the occupancy/wave model's default
  *   targets_per_thread  FP32 path only: 1, 2 or 4 (0 keeps the current value)
  *   kahan_group         FP32 path only: sources (all images) summed in FP32 before each Kahan
- *                       update, 1, 2, 4 or 8 (0 keeps the current value; the batched launch
+ *                       update, 1, 2, 4, 8 or 16 (0 keeps the current value; the batched launch
  *                       uses 8)
  * Results depend on these only through FP32/FP64 rounding.  May grow the context's scratch
  * buffer (device synchronisation).
@@ -455,7 +455,7 @@ STOKES_API int stokes_pair_count(const stokes_ctx *ctx, int n_targets, double *p
  * stokes_autotune: for the context's current geometry and `precision`, times each candidate
  *   shape `repeats` times (1..50; 0 = 5) after one untimed call, with CUDA events on `stream`,
  *   and applies the one with the smallest median time.  Candidates -- single instance:
- *   targets_per_thread {1, 2, 4} x kahan_group {2, 4, 8} (FP32-Kahan; one shape otherwise) x
+ *   targets_per_thread {1, 2, 4} x kahan_group {2, 4, 8, 16} (FP32-Kahan; one shape otherwise) x
  *   the three source-split counts the wave model ranks cheapest for that shape and two and four
  *   times its cheapest, plus the shape the context had on entry; batched: targets_per_thread {1, 2, 4} (FP32-Kahan) x
  *   items_per_slot {1, 2, 4, 8, 16}.  The timed calls evaluate unit densities held in device
@@ -478,7 +478,7 @@ typedef struct {
     int precision;
     int source_splits;       /* single instance (0 for batched)                        */
     int targets_per_thread;  /* FP32-Kahan: 1, 2 or 4; the fixed value otherwise        */
-    int kahan_group;         /* FP32-Kahan single instance: 1, 2, 4 or 8; else 0        */
+    int kahan_group;         /* FP32-Kahan single instance: 1, 2, 4, 8 or 16; else 0    */
     int items_per_slot;      /* batched: 1..16; else 0                                  */
     int candidates;          /* shapes timed (0 for a table lookup)                     */
     double best_ms;          /* median time of one evaluation with the chosen shape     */

@@ -498,13 +498,89 @@ __global__ void __launch_bounds__(kGemvThreads)
   }
 }
 
-__global__ void gemv_reduce_kernel(int rows, int chunks, const double *partial, double alpha,
-                                   int accumulate, double *y) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
+// The same partial products for an even leading dimension of at most kColsMaxRows rows, with
+// every CTA streaming whole columns: CTA ch reads columns [ch chunk, ...) contiguously (all
+// rows), a thread owning the row pairs t, t + kColsThreads, ... (P of them, 16-byte loads), U
+// columns in flight.  Long contiguous runs keep the DRAM pages open; the tile kernel above reads
+// 2 KB pieces of columns 8 l bytes apart instead.
+constexpr int kColsThreads = 256;
+constexpr int kColsMaxRows = 2 * kColsThreads * 8;  // 4096 (P = 8)
+template <int P, int U>
+__global__ void __launch_bounds__(kColsThreads)
+    gemv_cols_partial_kernel(int rows, int cols, int chunk, const double *__restrict__ M,
+                             const double *__restrict__ x, double *__restrict__ partial) {
+  __shared__ double xs[kGemvMaxChunk];
+  const int u0 = blockIdx.x * chunk;
+  const int nu = min(chunk, cols - u0);
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) xs[j] = x[u0 + j];
+  __syncthreads();
+  const int pairs = rows / 2;
+  double2 acc[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) acc[k] = make_double2(0.0, 0.0);
+  const double2 *col = reinterpret_cast<const double2 *>(M + size_t(u0) * rows);
+  const size_t ld2 = size_t(pairs);
+  int j = 0;
+  for (; j + U - 1 < nu; j += U) {
+    double2 v[U][P];
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int rp = threadIdx.x + k * kColsThreads;
+        v[q][k] = rp < pairs ? __ldg(col + size_t(j + q) * ld2 + rp) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const double xq = xs[j + q];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        acc[k].x = fma(v[q][k].x, xq, acc[k].x);
+        acc[k].y = fma(v[q][k].y, xq, acc[k].y);
+      }
+    }
+  }
+  for (; j < nu; ++j) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int rp = threadIdx.x + k * kColsThreads;
+      if (rp < pairs) {
+        const double2 v = __ldg(col + size_t(j) * ld2 + rp);
+        acc[k].x = fma(v.x, xs[j], acc[k].x);
+        acc[k].y = fma(v.y, xs[j], acc[k].y);
+      }
+    }
+  }
+  double *pr = partial + size_t(blockIdx.x) * rows;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int rp = threadIdx.x + k * kColsThreads;
+    if (rp < pairs) {
+      pr[2 * rp] = acc[k].x;
+      pr[2 * rp + 1] = acc[k].y;
+    }
+  }
+}
+
+// y[r] = alpha sum_ch partial[ch][r] (+ y[r]): a CTA per 32 rows, lane g of 8 summing the
+// chunks g, g + 8, ..., then the 8 lane sums added in lane order (fixed order throughout).
+constexpr int kRedRows = 32, kRedLanes = 8;
+__global__ void __launch_bounds__(kRedRows * kRedLanes)
+    gemv_reduce_kernel(int rows, int chunks, const double *partial, double alpha, int accumulate,
+                       double *y) {
+  __shared__ double part[kRedLanes][kRedRows];
+  const int rl = threadIdx.x % kRedRows, g = threadIdx.x / kRedRows;
+  const int r = blockIdx.x * kRedRows + rl;
   double acc = 0.0;
-  for (int ch = 0; ch < chunks; ++ch) acc += partial[size_t(ch) * rows + r];
-  y[r] = accumulate ? fma(alpha, acc, y[r]) : alpha * acc;
+  if (r < rows)
+    for (int ch = g; ch < chunks; ch += kRedLanes) acc += partial[size_t(ch) * rows + r];
+  part[g][rl] = acc;
+  __syncthreads();
+  if (g == 0 && r < rows) {
+    double t = part[0][rl];
+    for (int q = 1; q < kRedLanes; ++q) t += part[q][rl];
+    y[r] = accumulate ? fma(alpha, t, y[r]) : alpha * t;
+  }
 }
 
 // X[:, c] -= L S[:, c] for the nc columns of X (nA x nc, ld nA) and S (l x nc, ld l) over the
@@ -1107,9 +1183,21 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int row_tiles = std::max(1, (l + kGemvRows - 1) / kGemvRows);
+    // the whole-column kernel runs one CTA per chunk, as many as are resident at once (one
+    // wave); the tile kernel (odd or tall R) one per (row tile, chunk)
+    const bool cols_kernel = l % 2 == 0 && l <= kColsMaxRows;
+    int resident = 4;
+    if (cols_kernel) {
+      int nb = 0;
+      const void *fn = l <= 2 * kColsThreads * 4
+                           ? reinterpret_cast<const void *>(gemv_cols_partial_kernel<4, 4>)
+                           : reinterpret_cast<const void *>(gemv_cols_partial_kernel<8, 2>);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kColsThreads, 0) == cudaSuccess && nb > 0)
+        resident = nb;
+    }
+    const int row_tiles = cols_kernel ? 1 : std::max(1, (l + kGemvRows - 1) / kGemvRows);
     auto plan = [&](int cols, int &chunk, int &chunks) {
-      const int want = std::max(1, 8 * std::max(sms, 1) / row_tiles);
+      const int want = std::max(1, resident * std::max(sms, 1) / row_tiles);
       chunk = std::min(kGemvMaxChunk, std::max(64, (cols + want - 1) / want));
       chunks = std::max(1, (cols + chunk - 1) / chunk);
     };
@@ -1177,12 +1265,19 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
 int gemv_rows(fds_solver *f, const double *M, int cols, int chunk, int chunks, const double *x,
               double *t, cudaStream_t s, std::string &err) {
   const int l = f->l;
-  dim3 grid((l + kGemvRows - 1) / kGemvRows, chunks);
-  if (l % 2 == 0)  // column starts stay 16-byte aligned: two rows per load
-    gemv_cm_partial_kernel<true><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
-  else
-    gemv_cm_partial_kernel<false><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
-  gemv_reduce_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, chunks, f->d_gpart, 1.0, 0, t);
+  if (l % 2 == 0 && l <= 2 * kColsThreads * 4) {  // whole columns per CTA, 16-byte loads
+    gemv_cols_partial_kernel<4, 4><<<chunks, kColsThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  } else if (l % 2 == 0 && l <= kColsMaxRows) {
+    gemv_cols_partial_kernel<8, 2><<<chunks, kColsThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  } else {
+    dim3 grid((l + kGemvRows - 1) / kGemvRows, chunks);
+    if (l % 2 == 0)  // column starts stay 16-byte aligned: two rows per load
+      gemv_cm_partial_kernel<true><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+    else
+      gemv_cm_partial_kernel<false><<<grid, kGemvThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  }
+  gemv_reduce_kernel<<<(l + kRedRows - 1) / kRedRows, kRedRows * kRedLanes, 0, s>>>(
+      l, chunks, f->d_gpart, 1.0, 0, t);
   FK(cudaGetLastError());
   return STOKES_OK;
 }

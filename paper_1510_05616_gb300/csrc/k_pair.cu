@@ -941,6 +941,7 @@ PairKernel f32_by_kg(int kg) {
     return kg == 1   ? f32_kernel<false, NIMG, TPT, 1>()
            : kg == 2 ? f32_kernel<false, NIMG, TPT, 2>()
            : kg == 8 ? f32_kernel<false, NIMG, TPT, 8>()
+           : kg == 16 ? f32_kernel<false, NIMG, TPT, 16>()
                      : f32_kernel<false, NIMG, TPT, 4>();
   }
 }

@@ -880,8 +880,8 @@ int stokes_set_launch(stokes_ctx *c, int precision, int splits, int targets_per_
       targets_per_thread != 4)
     return fail(c, STOKES_ERR_ARG, "targets_per_thread must be 0, 1, 2 or 4");
   if (kahan_group != 0 && kahan_group != 1 && kahan_group != 2 && kahan_group != 4 &&
-      kahan_group != 8)
-    return fail(c, STOKES_ERR_ARG, "kahan_group must be 0, 1, 2, 4 or 8");
+      kahan_group != 8 && kahan_group != 16)
+    return fail(c, STOKES_ERR_ARG, "kahan_group must be 0, 1, 2, 4, 8 or 16");
   CK(cudaSetDevice(c->device));
   if (precision == STOKES_FP32_KAHAN) {
     if (targets_per_thread) c->tpt_f32 = targets_per_thread;

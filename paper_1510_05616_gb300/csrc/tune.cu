@@ -53,7 +53,7 @@ bool valid_prec(int p) {
 bool valid_shape(int prec, const Shape &s) {
   const bool tpt_ok = prec == STOKES_FP32_KAHAN ? (s.tpt == 1 || s.tpt == 2 || s.tpt == 4)
                                                 : s.tpt >= 1;
-  const bool kg_ok = s.kg == 0 || s.kg == 1 || s.kg == 2 || s.kg == 4 || s.kg == 8;
+  const bool kg_ok = s.kg == 0 || s.kg == 1 || s.kg == 2 || s.kg == 4 || s.kg == 8 || s.kg == 16;
   return tpt_ok && kg_ok && s.splits >= 0 && s.ips >= 0 && s.ips <= 64;
 }
 
@@ -126,7 +126,7 @@ std::vector<Shape> candidates(stokes_ctx *c, int prec, const Shape &initial) {
     for (int t : {1, 2, 4}) {
       c->tpt_f32 = t;  // the wave model sizes target blocks by targets per thread
       const std::vector<int> sp = split_candidates(c, prec, 3);
-      for (int kg : {2, 4, 8})
+      for (int kg : {2, 4, 8, 16})
         for (int s : sp) out.push_back(Shape{s, t, kg, 0});
     }
     c->tpt_f32 = saved;

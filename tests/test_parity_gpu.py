@@ -230,7 +230,7 @@ def test_errors_are_reported(P, small):
 
 
 @pytest.mark.parametrize("tpt", [1, 2, 4])
-@pytest.mark.parametrize("kg", [1, 2, 4, 8])
+@pytest.mark.parametrize("kg", [1, 2, 4, 8, 16])
 def test_fp32_launch_shapes(P, oracle_mod, tpt, kg):
     """Every compiled FP32 kernel shape (targets per thread x Kahan group) meets the bound,
     on the ragged interleaved geometry (partial target blocks, padded tiles)."""
