@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "fds.cuh"
+#include "bulk_pipe.cuh"
 #include "stokes.h"
 
 namespace stokes {
@@ -560,6 +561,96 @@ __global__ void __launch_bounds__(kColsThreads)
       pr[2 * rp + 1] = acc[k].y;
     }
   }
+}
+
+// The same partial products with every CTA's run of whole columns streamed into shared
+// memory by 1-D bulk async copies (cp.async.bulk, completion on an mbarrier) through a ring of
+// kBulkStages stages of `cpt` columns each, instead of per-thread global loads: the copy engine
+// keeps the HBM stream going without the L1 request throttling the load-based kernels hit.
+// A thread owns the row pairs t, t + kColsThreads, ... (P of them) and reads them from the
+// staged columns as 16-byte shared loads.  Needs an even leading dimension (16-byte aligned
+// column starts and copy sizes).  Dynamic shared memory: kBulkStages stages of cpt x rows
+// doubles, the chunk of x, then the barriers.  A stage wait that runs out (~0.5 s) makes the
+// CTA wait for its copies still in flight and write NaN partials, so the solve fails loudly.
+constexpr int kBulkStages = 3;
+constexpr int kBulkStageBytes = 32768;  // at most, per stage
+template <int P>
+__global__ void __launch_bounds__(kColsThreads)
+    gemv_bulk_partial_kernel(int rows, int cols, int chunk, int cpt, const double *__restrict__ M,
+                             const double *__restrict__ x, double *__restrict__ partial) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const size_t stage_elems = size_t(cpt) * rows;
+  double *stage0 = reinterpret_cast<double *>(smem_raw);
+  double *xs = stage0 + kBulkStages * stage_elems;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(xs + ((chunk + 1) & ~1));
+  const int u0 = blockIdx.x * chunk;
+  const int nu = min(chunk, cols - u0);
+  const int ntile = (nu + cpt - 1) / cpt;
+  const int pairs = rows / 2;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kBulkStages; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) xs[j] = x[u0 + j];
+  __syncthreads();
+  auto issue = [&](int t) {  // thread 0: columns [t cpt, ...) of the chunk into stage t mod S
+    const int st = t % kBulkStages;
+    const int nc = min(cpt, nu - t * cpt);
+    const uint32_t bytes = uint32_t(nc) * uint32_t(rows) * 8u;
+    mbar_arrive_expect_tx(&bar[st], bytes);
+    bulk_g2s(stage0 + st * stage_elems, M + (size_t(u0) + size_t(t) * cpt) * rows, bytes, &bar[st]);
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < kBulkStages && t < ntile; ++t) issue(t);
+  double2 acc[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) acc[k] = make_double2(0.0, 0.0);
+  bool failed = false;
+  for (int t = 0; t < ntile; ++t) {
+    const int st = t % kBulkStages;
+    const bool ok = mbar_wait_bounded(&bar[st], (t / kBulkStages) & 1u);
+    if (__syncthreads_or(!ok)) {  // uniform: record, drain the copies in flight, leave
+      if (threadIdx.x == 0)
+        for (int q = t; q < ntile && q < t + kBulkStages; ++q)
+          mbar_wait_bounded(&bar[q % kBulkStages], (q / kBulkStages) & 1u);
+      failed = true;
+      break;
+    }
+    const double2 *S = reinterpret_cast<const double2 *>(stage0 + st * stage_elems);
+    const int nc = min(cpt, nu - t * cpt);
+    for (int q = 0; q < nc; ++q) {
+      const double xq = xs[t * cpt + q];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int rp = threadIdx.x + k * kColsThreads;
+        if (rp < pairs) {
+          const double2 v = S[size_t(q) * pairs + rp];
+          acc[k].x = fma(v.x, xq, acc[k].x);
+          acc[k].y = fma(v.y, xq, acc[k].y);
+        }
+      }
+    }
+    __syncthreads();  // stage st is consumed
+    if (threadIdx.x == 0 && t + kBulkStages < ntile) issue(t + kBulkStages);
+  }
+  double *pr = partial + size_t(blockIdx.x) * rows;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int rp = threadIdx.x + k * kColsThreads;
+    if (rp < pairs) {
+      pr[2 * rp] = failed ? nan : acc[k].x;
+      pr[2 * rp + 1] = failed ? nan : acc[k].y;
+    }
+  }
+}
+
+// Columns per stage of the bulk-copy product (stages of at most kBulkStageBytes) and its
+// dynamic shared memory for a chunk of `chunk` columns.
+int bulk_cols_per_stage(int rows) { return std::max(1, kBulkStageBytes / (rows * 8)); }
+size_t bulk_smem_bytes(int rows, int chunk) {
+  return sizeof(double) * (size_t(kBulkStages) * bulk_cols_per_stage(rows) * rows + ((chunk + 1) & ~1)) +
+         sizeof(uint64_t) * kBulkStages;
 }
 
 // y[r] = alpha sum_ch partial[ch][r] (+ y[r]): a CTA per 32 rows, lane g of 8 summing the
@@ -1190,15 +1281,17 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
     if (cols_kernel) {
       int nb = 0;
       const void *fn = l <= 2 * kColsThreads * 4
-                           ? reinterpret_cast<const void *>(gemv_cols_partial_kernel<4, 4>)
-                           : reinterpret_cast<const void *>(gemv_cols_partial_kernel<8, 2>);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kColsThreads, 0) == cudaSuccess && nb > 0)
+                           ? reinterpret_cast<const void *>(gemv_bulk_partial_kernel<4>)
+                           : reinterpret_cast<const void *>(gemv_bulk_partial_kernel<8>);
+      const size_t smem = bulk_smem_bytes(l, kGemvMaxChunk);
+      FD(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kColsThreads, smem) == cudaSuccess && nb > 0)
         resident = nb;
     }
     const int row_tiles = cols_kernel ? 1 : std::max(1, (l + kGemvRows - 1) / kGemvRows);
     auto plan = [&](int cols, int &chunk, int &chunks) {
       const int want = std::max(1, resident * std::max(sms, 1) / row_tiles);
-      chunk = std::min(kGemvMaxChunk, std::max(64, (cols + want - 1) / want));
+      chunk = std::min(kGemvMaxChunk, std::max(8, (cols + want - 1) / want));
       chunks = std::max(1, (cols + chunk - 1) / chunk);
     };
     plan(nA, f->chunk_R, f->gemv_chunks_R);
@@ -1265,10 +1358,13 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
 int gemv_rows(fds_solver *f, const double *M, int cols, int chunk, int chunks, const double *x,
               double *t, cudaStream_t s, std::string &err) {
   const int l = f->l;
-  if (l % 2 == 0 && l <= 2 * kColsThreads * 4) {  // whole columns per CTA, 16-byte loads
-    gemv_cols_partial_kernel<4, 4><<<chunks, kColsThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
-  } else if (l % 2 == 0 && l <= kColsMaxRows) {
-    gemv_cols_partial_kernel<8, 2><<<chunks, kColsThreads, 0, s>>>(l, cols, chunk, M, x, f->d_gpart);
+  if (l % 2 == 0 && l <= kColsMaxRows) {  // whole columns per CTA, staged by bulk copies
+    const int cpt = bulk_cols_per_stage(l);
+    const size_t smem = bulk_smem_bytes(l, chunk);
+    if (l <= 2 * kColsThreads * 4)
+      gemv_bulk_partial_kernel<4><<<chunks, kColsThreads, smem, s>>>(l, cols, chunk, cpt, M, x, f->d_gpart);
+    else
+      gemv_bulk_partial_kernel<8><<<chunks, kColsThreads, smem, s>>>(l, cols, chunk, cpt, M, x, f->d_gpart);
   } else {
     dim3 grid((l + kGemvRows - 1) / kGemvRows, chunks);
     if (l % 2 == 0)  // column starts stay 16-byte aligned: two rows per load
