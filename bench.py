@@ -553,7 +553,10 @@ def run_walls(args):
     b = torch.as_tensor(rng.normal(size=(4, 4 * n_w)), device="cuda")
     peaks, peak_kind = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    modes = {"fds": P.STOKES_WALLS_FDS, "lu32_refine": P.STOKES_WALLS_LU32_REFINE}
+    # fds_plain: the fast direct solver without the column recompression of its neighbour
+    # factors (R = A_m(J, :) stored dense)
+    modes = {"fds": P.STOKES_WALLS_FDS, "fds_plain": P.STOKES_WALLS_FDS,
+             "lu32_refine": P.STOKES_WALLS_LU32_REFINE}
     res = {}
     sols = {}
     # warm-up: a small channel with each solver (library loading, first cuBLAS/cuSOLVER calls)
@@ -561,6 +564,7 @@ def run_walls(args):
     for name in args.walls_solvers.split(","):
         h = P.stokes_sim_create(0)
         P.stokes_sim_set_wall_solver(h, modes[name])
+        P.stokes_sim_set_fds_recompress(h, name != "fds_plain")
         P.stokes_sim_set_walls(h, 256, np.vstack([wl.nodes, wu.nodes]),
                                np.concatenate([wl.weights, wu.weights]),
                                np.vstack([wl.normals, wu.normals]),
@@ -569,6 +573,7 @@ def run_walls(args):
     for name in args.walls_solvers.split(","):
         h = P.stokes_sim_create(0)
         P.stokes_sim_set_wall_solver(h, modes[name])
+        P.stokes_sim_set_fds_recompress(h, name != "fds_plain")
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
         t0 = time.perf_counter()
@@ -606,10 +611,10 @@ def run_walls(args):
         torch.cuda.empty_cache()
         sols[name] = Xs
         r = {"setup_s": setup, "device_gb": mem, "solve_ms": one_ms, "solve_256_ms": many_ms}
-        if name == "fds":
+        if name in ("fds", "fds_plain"):
             r["fds"] = {k: info[k] for k in ("levels", "max_rank", "root_size", "neighbour_rank",
-                                             "sections", "host_ms", "device_ms", "device_bytes",
-                                             "solve_bytes")}
+                                             "neighbour_col_rank", "sections", "host_ms",
+                                             "device_ms", "device_bytes", "solve_bytes")}
             gbs = info["solve_bytes"] / (one_ms * 1e-3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                              "frac": gbs / hbm, "basis": "matrices read once per solve / "
@@ -625,9 +630,10 @@ def run_walls(args):
             rr.append((Ax.reshape(-1) - b[k]).abs().max().item() / b[k].abs().max().item())
         res[name]["residual_max"] = max(rr)
     s.close()
-    if len(sols) == 2:
-        a, c = sols["fds"], sols["lu32_refine"]
-        res["fds_vs_lu32_max_rel"] = ((a - c).abs().max() / c.abs().max()).item()
+    for other in ("lu32_refine", "fds_plain"):
+        if "fds" in sols and other in sols:
+            a, c = sols["fds"], sols[other]
+            res["fds_vs_%s_max_rel" % other] = ((a - c).abs().max() / c.abs().max()).item()
     line = {"metric": "channel wall solve: fast direct solver (Sec. 4) vs dense LU32 + FP64 refinement",
             "unit": "ms / s / GB", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
             "config": {"workload": "walls y=+-(1+0.4 sin x+0.15 sin 3x), 2 x %d nodes, period 2pi, "

@@ -523,8 +523,9 @@ STOKES_API int stokes_tune_clear(void);
  *     (interpolative decompositions against proxy circles, per-box inverses by
  *     Eqs. (def_muhD)-(def_muG)); A_{-1}, A_{+1} = L R from dyadic sections toward each
  *     neighbour (Sec. 4.2: proxy circles, the neighbour's near nodes for the touching
- *     section); A^-1 by Sherman-Morrison-Woodbury (Eq. (woodbury1)).  O(N_w) storage and
- *     set-up; a solve is two tree passes and three skinny products.  Accurate to about
+ *     section), recompressed by column skeletons (stokes_sim_set_fds_recompress); A^-1 by
+ *     Sherman-Morrison-Woodbury (Eq. (woodbury1)).  O(N_w) storage and set-up; a solve is
+ *     two tree passes and three small products.  Accurate to about
  *     1e-10 relative (the decompositions' tolerance, stokes_sim_set_fds_params); the block
  *     refinement below takes the channel response to round-off.  The compression runs on
  *     host threads (FP64), everything else on the device.
@@ -580,10 +581,14 @@ typedef struct {
     int neighbour_rank;     /* columns of L, both neighbours and both walls                    */
     int sections;           /* neighbour sections, both neighbours and both walls              */
     double host_ms;         /* compression and per-box inverses on host threads                */
-    double device_ms;       /* uploads, R, Z = A_0^-1 L and (I + R Z)^-1 on the device          */
+    double device_ms;       /* uploads, the neighbour factors, A_0^-1 L (set-up only) and the
+                               Woodbury matrix on the device                                  */
     double device_bytes;    /* device memory the solver holds                                  */
-    double solve_bytes;     /* matrices a one-right-hand-side solve reads: HBS tables, R, Z, K^-1 */
+    double solve_bytes;     /* matrices a one-right-hand-side solve reads: the HBS tables
+                               twice, L's and C's blocks, K^-1 S (recompressed) or R and K^-1 */
     double walls_setup_ms;  /* the whole stokes_sim_set_walls call, any solver                 */
+    int neighbour_col_rank; /* rows of C, the column skeletons of the recompressed neighbour
+                               factors (0 without the recompression)                          */
 } stokes_fds_info;
 typedef struct stokes_mlp stokes_mlp;
 
@@ -646,6 +651,19 @@ STOKES_API int stokes_sim_wall_solve(stokes_sim *sim, double *X, int nrhs);
  * interpolative decomposition (1e-15..1e-3, default 1e-12), nodes per HBS leaf box (8..512,
  * default 64), proxy points per HBS box (16..512, default 64).  STOKES_ERR_ARG outside. */
 STOKES_API int stokes_sim_set_fds_params(stokes_sim *sim, double tol, int leaf_nodes, int n_proxy);
+/* Recompression of the fast direct solver's neighbour factors (read at the next set_walls;
+ * on = 1 by default, 0 off).  The remark closing Sec. 4.2 notes that L R does not have optimal
+ * rank and may be recompressed by further low-rank factorisations.  On, R = A_m(J, :) is
+ * factored once more by skeletonising A_m's columns: each wall cut dyadically toward the end
+ * whose sources the shift m d carries next to the cell, each section's columns interpolated
+ * from a column skeleton J_c (an interpolative decomposition against the velocity its
+ * densities make on a proxy circle, and for the touching section at the cell's nodes inside
+ * it), so that A_m ~ L A_m(J, J_c) C with C block diagonal.  The solver then stores
+ * K^-1 A_m(J, J_c) (l x l_c) in place of R (l x 4 N_w) and K^-1, and a one-right-hand-side
+ * solve reads the HBS tables twice plus O(N_w) more instead of the 8 l 4 N_w bytes of R.
+ * Either way the solution is accurate to about the decompositions' tolerance.
+ * STOKES_ERR_ARG for on outside {0, 1}. */
+STOKES_API int stokes_sim_set_fds_recompress(stokes_sim *sim, int on);
 /* Statistics of the last stokes_sim_set_walls (see stokes_fds_info). */
 STOKES_API int stokes_sim_fds_info(const stokes_sim *sim, stokes_fds_info *info);
 STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);

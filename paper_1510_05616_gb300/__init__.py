@@ -124,6 +124,7 @@ _SIGNATURES = {
     "stokes_sim_set_fds_params": [_vp, _c_double, _c_int, _c_int],
     "stokes_sim_wall_solve": [_vp, _vp, _c_int],
     "stokes_sim_fds_info": [_vp, _vp],
+    "stokes_sim_set_fds_recompress": [_vp, _c_int],
     "stokes_sim_empty_channel": [_vp, _c_double, _vp, _c_int, _vp, _vp],
     "vesicle_step_warmstart": [_vp, _c_double, _c_double, _c_int, _vp, _vp, _c_double, _c_int,
                                _c_int, _vp],
@@ -671,7 +672,8 @@ class FdsInfo(ctypes.Structure):
     _fields_ = [("levels", _c_int), ("max_rank", _c_int), ("root_size", _c_int),
                 ("neighbour_rank", _c_int), ("sections", _c_int), ("host_ms", _c_double),
                 ("device_ms", _c_double), ("device_bytes", _c_double),
-                ("solve_bytes", _c_double), ("walls_setup_ms", _c_double)]
+                ("solve_bytes", _c_double), ("walls_setup_ms", _c_double),
+                ("neighbour_col_rank", _c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -689,6 +691,11 @@ def stokes_sim_wall_solve(h, X):
 def stokes_sim_set_fds_params(h, tol=1e-12, leaf_nodes=64, n_proxy=64):
     """Interpolative-decomposition tolerance, HBS leaf size and proxy count (next set_walls)."""
     return _sim_check(h, load().stokes_sim_set_fds_params(h, float(tol), int(leaf_nodes), int(n_proxy)))
+
+
+def stokes_sim_set_fds_recompress(h, on=True):
+    """Column recompression of the neighbour factors (Sec. 4.2 remark), read at the next set_walls."""
+    return _sim_check(h, load().stokes_sim_set_fds_recompress(h, int(on)))
 
 
 def stokes_sim_fds_info(h):

@@ -23,14 +23,23 @@
 //    circle 0.9 x its centre's distance to the shared cell boundary; the touching section
 //    against points on a circle 1.75 x its radius together with the neighbour nodes inside
 //    that circle.  L is block diagonal (the sections' P's) and R = A_m(J, :).
+//  * Recompression (the remark closing Sec. 4.2, on by default): R = A_m(J, :) is itself low
+//    rank block by block, so its columns are skeletonised the same way -- each wall cut
+//    dyadically toward the end whose sources the shift m d carries next to the cell, a
+//    section's columns interpolated from a column skeleton J_c against the velocity its
+//    densities make on a proxy circle and, for the touching section, at the cell's own nodes
+//    inside that circle -- giving A_m ~ L S C with S = A_m(J, J_c) (l x l_c) and C block
+//    diagonal (the sections' interpolation matrices).
 //  * A^-1 by Sherman-Morrison-Woodbury, Eq. (woodbury1): K^-1 = (I + R A_0^-1 L)^-1 is formed
 //    once (A_0^-1 L by the tree passes on L's l columns, then discarded); a solve is
 //    y = A_0^-1 v, x = A_0^-1 (v - L K^-1 R y) -- the same as y - A_0^-1 L K^-1 R y, with the
-//    second tree pass in place of a stored dense A_0^-1 L, so a solve reads the HBS tables twice,
-//    R once, K^-1 and L's section blocks, and nothing of size n x l besides R.
+//    second tree pass in place of a stored dense A_0^-1 L.  With the recompression
+//    K^-1 R y = (K^-1 S)(C y), K^-1 S stored (l x l_c), so a solve reads the HBS tables twice
+//    and, once each, C's and L's section blocks and K^-1 S: nothing of size n x l.  Without it,
+//    R (l x n) and K^-1 are read.
 //
 // The compression and the small per-box inverses run on the host in FP64 (threads over the
-// boxes of one level); R, Z, K^-1 and every solve run on the device.
+// boxes of one level); the neighbour factors, K^-1 and every solve run on the device.
 #include <math.h>
 
 #include <algorithm>
@@ -311,6 +320,33 @@ HMat probe_matrix(const WallGeom &g, const std::vector<int> &It, const std::vect
   return Z;
 }
 
+// Probe matrix of a group of source unknowns `It` of A_m (one column each), for its column
+// skeleton: rows A_m(near, It) for the target unknowns `near`, then for every proxy point on
+// the circle (cx, cy, rad) the velocity the unknown's density makes there.  The circle is
+// drawn around the sources before the shift m d (the kernel depends on differences only), so
+// the near targets are those within it once moved by -m d.
+HMat probe_cols(const WallGeom &g, const std::vector<int> &It, const std::vector<int> &near,
+                int m, double cx, double cy, double rad, int npx) {
+  const int nn = int(near.size());
+  HMat Z(nn + 2 * npx, int(It.size()));
+  for (int q = 0; q < int(It.size()); ++q) {
+    const int u = It[q], node = u >> 1, comp = u & 1;
+    double *z = Z.col(q);
+    int r = 0;
+    for (int p = 0; p < nn; ++p) z[r++] = a_host(g, near[p], u, m);
+    for (int p = 0; p < npx; ++p) {
+      const double px = cx + rad * cos(2.0 * kPi * p / npx), py = cy + rad * sin(2.0 * kPi * p / npx);
+      const double t1 = px - g.x[node], t2 = py - g.y[node];
+      const double tt = t1 * t1 + t2 * t2;
+      const double tn = t1 * g.nx[node] + t2 * g.ny[node];
+      const double f = (comp ? t2 : t1) * tn / (kPi * tt * tt) * g.w[node];
+      z[r++] = t1 * f;
+      z[r++] = t2 * f;
+    }
+  }
+  return Z;
+}
+
 struct Box {
   int a = 0, b = 0;                  // node range
   double x0 = 0, x1 = 0, y0 = 0, y1 = 0;  // bounding box of the nodes
@@ -415,6 +451,20 @@ struct SecBlock {
   int row0, rows, col0, cols;
   long long off;
 };
+
+// S (l x lc, column-major): S[r, c] = A_m(J_r, J_c) where the row and column skeletons belong
+// to the same neighbour m, else 0 (the two neighbours' factors are separate blocks).
+__global__ void fill_core_kernel(int l, int lc, const int *J, const int *mr, const int *Jc,
+                                 const int *mc, const double *x, const double *y,
+                                 const double *nx, const double *ny, const double *w,
+                                 const double *kap, double d, double *S) {
+  const size_t total = size_t(l) * lc;
+  for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total;
+       idx += size_t(gridDim.x) * blockDim.x) {
+    const int r = int(idx % l), c = int(idx / l);
+    S[idx] = mr[r] == mc[c] ? a_entry(J[r], Jc[c], mr[r], x, y, nx, ny, w, kap, d) : 0.0;
+  }
+}
 
 __global__ void scatter_blocks_kernel(const SecBlock *sec, const double *vals, int nA, double *L) {
   const SecBlock s = sec[blockIdx.x];
@@ -707,6 +757,37 @@ __global__ void __launch_bounds__(kSubRows)
   }
 }
 
+// c = C y, one right-hand side, for the column sections' blocks (rows x cols, column-major,
+// block b covering c[col0, col0 + cols) and y[row0, row0 + rows)): c[r] = sum_q
+// P_b[q, r - col0] y[row0 + q], with cmap[r] = b.  A CTA per output; column r - col0 of P_b
+// is contiguous and read as 16-byte pairs (rows, row0 and every block offset are even), two
+// accumulators a thread, then a fixed-order reduction (shuffles, then the warps in order).
+constexpr int kDotThreads = 256;
+__global__ void __launch_bounds__(kDotThreads)
+    sec_dot_kernel(const SecBlock *sec, const int *cmap, const double *vals, const double *y,
+                   double *c) {
+  __shared__ double red[kDotThreads / 32];
+  const int r = blockIdx.x;
+  const SecBlock b = sec[cmap[r]];
+  const double2 *pv = reinterpret_cast<const double2 *>(vals + b.off + size_t(r - b.col0) * b.rows);
+  const double2 *yv = reinterpret_cast<const double2 *>(y + b.row0);
+  double a0 = 0.0, a1 = 0.0;
+  for (int q = threadIdx.x; q < b.rows / 2; q += kDotThreads) {
+    const double2 p2 = pv[q], y2 = yv[q];
+    a0 = fma(p2.x, y2.x, a0);
+    a1 = fma(p2.y, y2.y, a1);
+  }
+  double a = a0 + a1;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kDotThreads / 32; ++q) t += red[q];
+    c[r] = t;
+  }
+}
+
 // Blocks of a 256-thread grid-stride launch over n elements: one per 256 elements, at most
 // 32 per SM of the current device.
 int grid_for(size_t n) {
@@ -726,10 +807,17 @@ struct fds_solver {
   std::vector<HbsBox *> d_boxes;       // [L + 1]
   std::vector<long long> N;            // [L + 1]
   double *d_mats = nullptr;
-  // neighbour factors: R = A_m(J, :) (l x nA), K^-1 = (I + R A_0^-1 L)^-1, L's section blocks
-  double *d_R = nullptr, *d_Kinv = nullptr;
+  // neighbour factors: R = A_m(J, :) (l x nA), K^-1 = (I + R A_0^-1 L)^-1, L's section blocks;
+  // recompressed: M = K^-1 S (l x lc) and C's blocks (host copy of their table for the
+  // several-right-hand-side products) in place of R and K^-1
+  double *d_R = nullptr, *d_Kinv = nullptr, *d_M = nullptr;
   SecBlock *d_sec = nullptr;
   double *d_svals = nullptr;
+  int lc = 0;                          // rows of C (0: not recompressed)
+  SecBlock *d_csec = nullptr;
+  int *d_cmap = nullptr;               // [lc] block of every row of C
+  double *d_cvals = nullptr;
+  std::vector<SecBlock> h_csec;
   int n_sec = 0;
   int n_sec_left = 0;                  // sections of the m = -1 neighbour (they come first);
                                        //   each neighbour's sections partition both walls
@@ -857,6 +945,9 @@ struct HostFactors {
   std::vector<int> sec_m;                 // image m of every section block
   std::vector<SecBlock> sb;               // L's blocks
   std::vector<double> svals;
+  std::vector<int> Jc, mc;                // column skeleton unknowns and their image m
+  std::vector<SecBlock> csb;              // C's blocks (each stored transposed: rows x cols)
+  std::vector<double> cvals;
   int max_cols = 0;                       // widest level product
   std::vector<int> max_k, max_n;          // [L + 1] per level
   fds_info info;
@@ -1027,58 +1118,80 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
     std::vector<int> skel;
     HMat P;  // rows x k (interpolation matrix)
   };
-  std::vector<Section> secs;
-  for (int m : {-1, 1})
-    for (int w0 : {0, n_w}) {
-      int a = 0, b = n_w;
-      while (b - a > p.sec_max) {
-        const int h = (a + b) / 2;
-        if (m > 0) {
-          secs.push_back({w0 + a, w0 + h, m, {}, HMat()});
-          a = h;
-        } else {
-          secs.push_back({w0 + h, w0 + b, m, {}, HMat()});
-          b = h;
+  // Each wall of each neighbour m, cut dyadically toward the end that meets the shared cell
+  // boundary: for A_m's rows the targets next to the neighbour (the right end for m = +1),
+  // for its columns the sources that the shift m d carries next to the cell (the left end).
+  auto cut = [&](bool cols) {
+    std::vector<Section> out;
+    for (int m : {-1, 1})
+      for (int w0 : {0, n_w}) {
+        const bool to_right = (m > 0) != cols;
+        int a = 0, b = n_w;
+        while (b - a > p.sec_max) {
+          const int h = (a + b) / 2;
+          if (to_right) {
+            out.push_back({w0 + a, w0 + h, m, {}, HMat()});
+            a = h;
+          } else {
+            out.push_back({w0 + h, w0 + b, m, {}, HMat()});
+            b = h;
+          }
+        }
+        out.push_back({w0 + a, w0 + b, m, {}, HMat()});
+      }
+    return out;
+  };
+  // The skeleton of a section: against a proxy circle 0.9 x its centre's distance to that
+  // boundary or, for the touching section, 1.75 x its radius together with the nodes on the
+  // other side within that circle (the neighbour's sources for rows, the cell's targets for
+  // columns).
+  auto skeletonise = [&](std::vector<Section> &secs, bool cols) {
+    parallel_for(int(secs.size()), [&](int si) {
+      Section &sc = secs[si];
+      Box bx;
+      bx.a = sc.a;
+      bx.b = sc.b;
+      bounds(g, bx);
+      const double cx = 0.5 * (bx.x0 + bx.x1), cy = 0.5 * (bx.y0 + bx.y1);
+      const int la = sc.a % n_w, lb = sc.b - (sc.a - la);
+      const bool to_right = (sc.m > 0) != cols;
+      const bool touch = to_right ? lb == n_w : la == 0;
+      const double shift = (cols ? -sc.m : sc.m) * g.d;
+      double rad;
+      std::vector<int> near;
+      if (!touch) {
+        rad = 0.9 * fabs((to_right ? g.d : 0.0) - cx);
+      } else {
+        rad = 1.75 * 0.5 * hypot(bx.x1 - bx.x0, bx.y1 - bx.y0);
+        for (int j = 0; j < Nt; ++j) {
+          const double ex = g.x[j] + shift - cx, ey = g.y[j] - cy;
+          if (ex * ex + ey * ey < rad * rad) {
+            near.push_back(2 * j);
+            near.push_back(2 * j + 1);
+          }
         }
       }
-      secs.push_back({w0 + a, w0 + b, m, {}, HMat()});
-    }
-  parallel_for(int(secs.size()), [&](int si) {
-    Section &sc = secs[si];
-    Box bx;
-    bx.a = sc.a;
-    bx.b = sc.b;
-    bounds(g, bx);
-    const double cx = 0.5 * (bx.x0 + bx.x1), cy = 0.5 * (bx.y0 + bx.y1);
-    const int la = sc.a % n_w, lb = sc.b - (sc.a - la);
-    const bool touch = (sc.m > 0 && lb == n_w) || (sc.m < 0 && la == 0);
-    double rad;
-    std::vector<int> near;
-    if (!touch) {
-      rad = 0.9 * fabs((sc.m > 0 ? g.d : 0.0) - cx);
-    } else {
-      rad = 1.75 * 0.5 * hypot(bx.x1 - bx.x0, bx.y1 - bx.y0);
-      for (int j = 0; j < Nt; ++j) {
-        const double ex = g.x[j] + sc.m * g.d - cx, ey = g.y[j] - cy;
-        if (ex * ex + ey * ey < rad * rad) {
-          near.push_back(2 * j);
-          near.push_back(2 * j + 1);
-        }
-      }
-    }
-    std::vector<int> It(2 * (sc.b - sc.a));
-    std::iota(It.begin(), It.end(), 2 * sc.a);
-    HMat Z = probe_matrix(g, It, near, sc.m, false, cx, cy, rad, p.n_proxy_nb, false);
-    std::vector<int> J;
-    HMat X;
-    column_id(Z, p.tol, J, X);
-    sc.skel.resize(J.size());
-    for (size_t c = 0; c < J.size(); ++c) sc.skel[c] = It[J[c]];
-    // P = X^T
-    sc.P = HMat(X.c, X.r);
-    for (int c = 0; c < X.r; ++c)
-      for (int r = 0; r < X.c; ++r) sc.P(r, c) = X(c, r);
-  });
+      std::vector<int> It(2 * (sc.b - sc.a));
+      std::iota(It.begin(), It.end(), 2 * sc.a);
+      HMat Z = cols ? probe_cols(g, It, near, sc.m, cx, cy, rad, p.n_proxy_nb)
+                    : probe_matrix(g, It, near, sc.m, false, cx, cy, rad, p.n_proxy_nb, false);
+      std::vector<int> J;
+      HMat X;
+      column_id(Z, p.tol, J, X);
+      sc.skel.resize(J.size());
+      for (size_t c = 0; c < J.size(); ++c) sc.skel[c] = It[J[c]];
+      // P = X^T
+      sc.P = HMat(X.c, X.r);
+      for (int c = 0; c < X.r; ++c)
+        for (int r = 0; r < X.c; ++r) sc.P(r, c) = X(c, r);
+    });
+  };
+  std::vector<Section> secs = cut(false), csecs;
+  skeletonise(secs, false);
+  if (p.recompress) {
+    csecs = cut(true);
+    skeletonise(csecs, true);
+  }
   const auto t1 = std::chrono::steady_clock::now();
   hf.info.host_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   // ---- pack the HBS tables for the device ----
@@ -1148,6 +1261,21 @@ int host_factor(int n_w, const double *nodes, const double *weights, const doubl
   }
   hf.info.neighbour_rank = int(hf.Jall.size());
   hf.info.sections = int(secs.size());
+  for (const Section &sc : csecs) {
+    SecBlock b;
+    b.row0 = 2 * sc.a;
+    b.rows = 2 * (sc.b - sc.a);
+    b.col0 = int(hf.Jc.size());
+    b.cols = int(sc.skel.size());
+    b.off = (long long)hf.cvals.size();
+    hf.cvals.insert(hf.cvals.end(), sc.P.a.begin(), sc.P.a.end());
+    hf.csb.push_back(b);
+    for (int u : sc.skel) {
+      hf.Jc.push_back(u);
+      hf.mc.push_back(sc.m);
+    }
+  }
+  hf.info.neighbour_col_rank = int(hf.Jc.size());
   hf.g = std::move(g);
   return STOKES_OK;
 }
@@ -1229,26 +1357,57 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
   FD(dalloc(f->d_up, f->up_len * kChunk, bytes));
   FD(dalloc(f->d_down, f->up_len * kChunk, bytes));
   FD(dalloc(f->d_out, size_t(nA) * kChunk, bytes));
-  FD(dalloc(f->d_t, size_t(l) * kChunk, bytes));
+  const int lc = int(hf.Jc.size());
+  f->lc = lc;
+  FD(dalloc(f->d_t, size_t(std::max(l, lc)) * kChunk, bytes));
   FD(dalloc(f->d_s, size_t(l) * kChunk, bytes));
-  // geometry, R = A_m(J, :)
+  // geometry and skeleton lists
   double *dg = nullptr;
   int *dJ = nullptr;
   size_t scratch = 0;
   FD(dalloc(dg, size_t(6) * Nt, scratch));
   tmp.push_back(dg);
-  FD(dalloc(dJ, size_t(2) * l, scratch));
+  FD(dalloc(dJ, size_t(2) * (l + lc), scratch));
   tmp.push_back(dJ);
   const double *hs[6] = {g.x.data(), g.y.data(), g.nx.data(), g.ny.data(), g.w.data(), g.kap.data()};
   for (int q = 0; q < 6; ++q)
     FD(cudaMemcpyAsync(dg + size_t(q) * Nt, hs[q], sizeof(double) * Nt, cudaMemcpyHostToDevice, s));
   FD(cudaMemcpyAsync(dJ, hf.Jall.data(), sizeof(int) * l, cudaMemcpyHostToDevice, s));
   FD(cudaMemcpyAsync(dJ + l, hf.mall.data(), sizeof(int) * l, cudaMemcpyHostToDevice, s));
-  FD(dalloc(f->d_R, size_t(l) * nA, bytes));
-  fill_rows_kernel<<<grid_for(size_t(l) * nA), 256, 0, s>>>(
-      l, nA, dJ, dJ + l, dg, dg + Nt, dg + 2 * Nt, dg + 3 * Nt, dg + 4 * Nt, dg + 5 * Nt, g.d, f->d_R);
+  if (lc > 0) {
+    FD(cudaMemcpyAsync(dJ + 2 * l, hf.Jc.data(), sizeof(int) * lc, cudaMemcpyHostToDevice, s));
+    FD(cudaMemcpyAsync(dJ + 2 * l + lc, hf.mc.data(), sizeof(int) * lc, cudaMemcpyHostToDevice, s));
+  }
+  // the row factor: R = A_m(J, :) (l x nA), or S = A_m(J, J_c) (l x lc) and C's blocks
+  double *dRS = nullptr;  // R (kept) or S (set-up only)
+  if (lc == 0) {
+    FD(dalloc(f->d_R, size_t(l) * nA, bytes));
+    dRS = f->d_R;
+    fill_rows_kernel<<<grid_for(size_t(l) * nA), 256, 0, s>>>(
+        l, nA, dJ, dJ + l, dg, dg + Nt, dg + 2 * Nt, dg + 3 * Nt, dg + 4 * Nt, dg + 5 * Nt, g.d, f->d_R);
+  } else {
+    FD(dalloc(dRS, size_t(l) * lc, scratch));
+    tmp.push_back(dRS);
+    fill_core_kernel<<<grid_for(size_t(l) * lc), 256, 0, s>>>(
+        l, lc, dJ, dJ + l, dJ + 2 * l, dJ + 2 * l + lc, dg, dg + Nt, dg + 2 * Nt, dg + 3 * Nt,
+        dg + 4 * Nt, dg + 5 * Nt, g.d, dRS);
+    for (const SecBlock &b : hf.csb)
+      if (b.rows % 2 || b.row0 % 2 || b.off % 2) {
+        err = "fds: a column section is not made of whole nodes";
+        return bail(STOKES_ERR_ARG);
+      }
+    std::vector<int> cmap(lc);
+    for (int q = 0; q < int(hf.csb.size()); ++q)
+      for (int c = 0; c < hf.csb[q].cols; ++c) cmap[hf.csb[q].col0 + c] = q;
+    f->h_csec = hf.csb;
+    FD(dalloc(f->d_csec, hf.csb.size(), bytes));
+    FD(dalloc(f->d_cmap, size_t(lc), bytes));
+    FD(dalloc(f->d_cvals, hf.cvals.size(), bytes));
+    FD(cudaMemcpyAsync(f->d_csec, hf.csb.data(), sizeof(SecBlock) * hf.csb.size(), cudaMemcpyHostToDevice, s));
+    FD(cudaMemcpyAsync(f->d_cmap, cmap.data(), sizeof(int) * lc, cudaMemcpyHostToDevice, s));
+    FD(cudaMemcpyAsync(f->d_cvals, hf.cvals.data(), sizeof(double) * hf.cvals.size(), cudaMemcpyHostToDevice, s));
+  }
   FD(cudaGetLastError());
-  // Z = A_0^-1 L
   f->n_sec = int(hf.sb.size());
   f->n_sec_left = 0;
   while (f->n_sec_left < f->n_sec && hf.sec_m[f->n_sec_left] < 0) ++f->n_sec_left;
@@ -1295,7 +1454,7 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
       chunks = std::max(1, (cols + chunk - 1) / chunk);
     };
     plan(nA, f->chunk_R, f->gemv_chunks_R);
-    plan(l, f->chunk_K, f->gemv_chunks_K);
+    plan(lc > 0 ? lc : l, f->chunk_K, f->gemv_chunks_K);
     FD(dalloc(f->d_gpart, size_t(std::max(1, l)) * std::max(f->gemv_chunks_R, f->gemv_chunks_K), bytes));
   }
   // Z = A_0^-1 L (set-up only: K = I + R Z)
@@ -1309,14 +1468,24 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
     int st = hbs_apply(f, dZ, l, s, err);
     if (st) return bail(st);
   }
-  // K = I + R Z, then K^-1
+  // K = I + R Z (recompressed: R Z = S (C Z)), then K^-1 (or M = K^-1 S)
   double *dK = nullptr;
   FD(dalloc(dK, size_t(l) * l, scratch));
   tmp.push_back(dK);
   const double one = 1.0, zero = 0.0;
   cublasSetStream(blas, s);
   cusolverDnSetStream(sol, s);
-  FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, nA, &one, f->d_R, l, dZ, nA, &zero, dK, l));
+  if (lc == 0) {
+    FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, nA, &one, f->d_R, l, dZ, nA, &zero, dK, l));
+  } else {
+    double *dW = nullptr;  // C Z (lc x l)
+    FD(dalloc(dW, size_t(lc) * l, scratch));
+    tmp.push_back(dW);
+    for (const SecBlock &b : hf.csb)
+      FDB(cublasDgemm(blas, CUBLAS_OP_T, CUBLAS_OP_N, b.cols, l, b.rows, &one, f->d_cvals + b.off,
+                      b.rows, dZ + b.row0, nA, &zero, dW + b.col0, lc));
+    FDB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, l, l, lc, &one, dRS, l, dW, lc, &zero, dK, l));
+  }
   add_identity_kernel<<<(l + 255) / 256, 256, 0, s>>>(l, dK);
   FD(cudaGetLastError());
   int lwork = 0;
@@ -1329,10 +1498,16 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
   tmp.push_back(piv);
   FD(dalloc(dinfo, 2, scratch));
   tmp.push_back(dinfo);
-  FD(dalloc(f->d_Kinv, size_t(l) * l, bytes));
-  set_identity_kernel<<<grid_for(size_t(l) * l), 256, 0, s>>>(l, f->d_Kinv);
   FDQ(cusolverDnDgetrf(sol, l, l, dK, l, work, piv, dinfo));
-  FDQ(cusolverDnDgetrs(sol, CUBLAS_OP_N, l, l, dK, l, piv, f->d_Kinv, l, dinfo + 1));
+  if (lc == 0) {
+    FD(dalloc(f->d_Kinv, size_t(l) * l, bytes));
+    set_identity_kernel<<<grid_for(size_t(l) * l), 256, 0, s>>>(l, f->d_Kinv);
+    FDQ(cusolverDnDgetrs(sol, CUBLAS_OP_N, l, l, dK, l, piv, f->d_Kinv, l, dinfo + 1));
+  } else {
+    FD(dalloc(f->d_M, size_t(l) * lc, bytes));
+    FD(cudaMemcpyAsync(f->d_M, dRS, sizeof(double) * size_t(l) * lc, cudaMemcpyDeviceToDevice, s));
+    FDQ(cusolverDnDgetrs(sol, CUBLAS_OP_N, l, lc, dK, l, piv, f->d_M, l, dinfo + 1));
+  }
   int hinfo[2] = {0, 0};
   FD(cudaMemcpyAsync(hinfo, dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
   FD(cudaStreamSynchronize(s));
@@ -1346,9 +1521,11 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
 #undef FDQ
   f->info.device_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t2).count();
-  // a solve reads the HBS tables twice, R, K^-1 and L's blocks once
-  f->info.solve_bytes = sizeof(double) * (2 * hf.mats.size() + size_t(l) * nA + size_t(l) * l +
-                                          hf.svals.size());
+  // a solve reads the HBS tables twice and L's blocks once, and either R and K^-1 or C's
+  // blocks and M = K^-1 S once
+  f->info.solve_bytes =
+      sizeof(double) * (2 * hf.mats.size() + hf.svals.size() +
+                        (lc == 0 ? size_t(l) * nA + size_t(l) * l : size_t(l) * lc + hf.cvals.size()));
   *out = f;
   return STOKES_OK;
 }
@@ -1392,11 +1569,22 @@ int fds_solve(fds_solver *f, double *X, int nrhs, cudaStream_t s, cublasHandle_t
     int st = hbs_pass(f, Xc, f->d_out, nc, s, err);  // y = A_0^-1 v  (in d_out)
     if (st) return st;
     if (f->l > 0) {
-      if (nc == 1) {  // t = R y, s = K^-1 t: the library's own products
+      if (nc == 1 && f->lc > 0) {  // t = C y, s = M t: the library's own products
+        sec_dot_kernel<<<f->lc, kDotThreads, 0, s>>>(f->d_csec, f->d_cmap, f->d_cvals, f->d_out, f->d_t);
+        FK(cudaGetLastError());
+        st = gemv_rows(f, f->d_M, f->lc, f->chunk_K, f->gemv_chunks_K, f->d_t, f->d_s, s, err);
+        if (st) return st;
+      } else if (nc == 1) {        // t = R y, s = K^-1 t
         st = gemv_rows(f, f->d_R, f->nA, f->chunk_R, f->gemv_chunks_R, f->d_out, f->d_t, s, err);
         if (!st) st = gemv_rows(f, f->d_Kinv, f->l, f->chunk_K, f->gemv_chunks_K, f->d_t, f->d_s, s, err);
         if (st) return st;
-      } else {        // several right-hand sides (set-up work): library GEMMs
+      } else if (f->lc > 0) {      // several right-hand sides: library GEMMs per C block, then M
+        for (const SecBlock &b : f->h_csec)
+          FB(cublasDgemm(blas, CUBLAS_OP_T, CUBLAS_OP_N, b.cols, nc, b.rows, &one, f->d_cvals + b.off,
+                         b.rows, f->d_out + b.row0, f->nA, &zero, f->d_t + b.col0, f->lc));
+        FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->lc, &one, f->d_M, f->l,
+                       f->d_t, f->lc, &zero, f->d_s, f->l));
+      } else {
         FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->nA, &one, f->d_R, f->l,
                        f->d_out, f->nA, &zero, f->d_t, f->l));
         FB(cublasDgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, f->l, nc, f->l, &one, f->d_Kinv, f->l,
@@ -1430,6 +1618,10 @@ void fds_destroy(fds_solver *f) {
   for (HbsBox *b : f->d_boxes) cudaFree(b);
   cudaFree(f->d_R);
   cudaFree(f->d_Kinv);
+  cudaFree(f->d_M);
+  cudaFree(f->d_csec);
+  cudaFree(f->d_cmap);
+  cudaFree(f->d_cvals);
   cudaFree(f->d_sec);
   cudaFree(f->d_svals);
   cudaFree(f->d_gpart);

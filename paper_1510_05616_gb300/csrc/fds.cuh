@@ -16,6 +16,7 @@ struct fds_params {
   int n_proxy = 64;    // proxy points per HBS box
   int n_proxy_nb = 80; // proxy points per neighbour section (Sec. 4.2)
   int sec_max = 45;    // nodes of the smallest (touching) neighbour section, n_max of Sec. 4.2
+  bool recompress = true;  // also skeletonise A_m's columns: R = A_m(J, J_c) C (Sec. 4.2 remark)
 };
 
 struct fds_info {
@@ -24,10 +25,11 @@ struct fds_info {
   int root_size = 0;       // order of the dense root block
   int neighbour_rank = 0;  // columns of L (both neighbours, both walls)
   int sections = 0;        // neighbour sections (both neighbours, both walls)
+  int neighbour_col_rank = 0;  // rows of C (column skeletons; 0 without the recompression)
   double host_ms = 0.0;    // compression and per-box inverses (host threads)
-  double device_ms = 0.0;  // uploads, R, Z = A_0^-1 L, K^-1 (device)
+  double device_ms = 0.0;  // uploads, the neighbour factors, K^-1 (device)
   size_t device_bytes = 0; // device memory held by the solver
-  size_t solve_bytes = 0;  // matrices one single-right-hand-side solve reads (HBS tables, R, Z, K^-1)
+  size_t solve_bytes = 0;  // matrices one single-right-hand-side solve reads
 };
 
 // Builds the solver for the walls of one cell: n_w nodes per wall, host arrays in the wall

@@ -1847,6 +1847,13 @@ int stokes_sim_set_fds_params(stokes_sim *m, double tol, int leaf_nodes, int n_p
   return STOKES_OK;
 }
 
+int stokes_sim_set_fds_recompress(stokes_sim *m, int on) {
+  if (!m) return STOKES_ERR_ARG;
+  if (on != 0 && on != 1) return fail(m, STOKES_ERR_ARG, "recompress must be 0 or 1");
+  m->fds_p.recompress = on == 1;
+  return STOKES_OK;
+}
+
 int stokes_sim_fds_info(const stokes_sim *m, stokes_fds_info *out) {
   if (!m || !out) return STOKES_ERR_ARG;
   *out = stokes_fds_info{};
@@ -1863,6 +1870,7 @@ int stokes_sim_fds_info(const stokes_sim *m, stokes_fds_info *out) {
   out->device_ms = f.device_ms;
   out->device_bytes = double(f.device_bytes);
   out->solve_bytes = double(f.solve_bytes);
+  out->neighbour_col_rank = f.neighbour_col_rank;
   return STOKES_OK;
 }
 

@@ -1,9 +1,11 @@
 // Host-logic check of the fast direct wall solver (tests/test_host_logic.py): runs the host
 // factorization of csrc/fds.cu (HBS tables, neighbour sections) on a wall geometry read from a
 // file, emulates the device solve on the CPU with the packed tables (upward pass, root, downward
-// pass; R = A_m(J, :), Z = A_0^-1 L, (I + R Z)^-1, Sherman-Morrison-Woodbury) and writes the
-// solutions of the given right-hand sides for the test to check against the oracle's dense
-// operator.  Usage: fds_host_check <case.bin> <out.bin>
+// pass; R = A_m(J, :) or, recompressed, R = A_m(J, J_c) C from the column sections;
+// Z = A_0^-1 L, (I + R Z)^-1, Sherman-Morrison-Woodbury) and writes the solutions of the given
+// right-hand sides for the test to check against the oracle's dense operator; prints the
+// recompressed R's largest deviation from A_m(J, :) relative to its largest entry.
+// Usage: fds_host_check <case.bin> <out.bin> [recompress 0|1, default 1]
 //   case.bin: int32 n_w, int32 nrhs; float64 period; nodes (2 N), weights (N), normals (2 N),
 //             curvature (N) with N = 2 n_w; right-hand sides (nrhs x 4 n_w).
 #include <cstdio>
@@ -62,6 +64,7 @@ int main(int argc, char **argv) {
     return 2;
   fclose(fp);
   fds_params p;
+  p.recompress = argc < 4 || argv[3][0] != '0';
   HostFactors hf;
   std::string err;
   if (host_factor(nw, nodes.data(), w.data(), nrm.data(), kap.data(), d, p, hf, err) != STOKES_OK) {
@@ -76,6 +79,25 @@ int main(int argc, char **argv) {
       for (int i = 0; i < sb.rows; ++i) Lm(sb.row0 + i, sb.col0 + c) = hf.svals[sb.off + i + size_t(c) * sb.rows];
   for (int u = 0; u < nA; ++u)
     for (int r = 0; r < l; ++r) R(r, u) = a_host(g, hf.Jall[r], u, hf.mall[r]);
+  const int lc = int(hf.Jc.size());
+  double r_dev = 0.0;
+  if (lc > 0) {  // R <- S C
+    HMat S(l, lc), C(lc, nA);
+    for (int c = 0; c < lc; ++c)
+      for (int r = 0; r < l; ++r)
+        S(r, c) = hf.mall[r] == hf.mc[c] ? a_host(g, hf.Jall[r], hf.Jc[c], hf.mall[r]) : 0.0;
+    for (const SecBlock &sb : hf.csb)
+      for (int c = 0; c < sb.cols; ++c)
+        for (int i = 0; i < sb.rows; ++i) C(sb.col0 + c, sb.row0 + i) = hf.cvals[sb.off + i + size_t(c) * sb.rows];
+    HMat SC = mul(S, C);
+    double big = 0.0, dev = 0.0;
+    for (size_t q = 0; q < R.a.size(); ++q) {
+      big = std::max(big, fabs(R.a[q]));
+      dev = std::max(dev, fabs(R.a[q] - SC.a[q]));
+    }
+    r_dev = dev / big;
+    R = SC;
+  }
   HMat Z = Lm;
   for (int c = 0; c < l; ++c) {
     std::vector<double> col(Z.col(c), Z.col(c) + nA);
@@ -109,7 +131,8 @@ int main(int argc, char **argv) {
     fwrite(x.data(), 8, nA, fo);
   }
   fclose(fo);
-  printf("levels %d max_rank %d root %d neighbour_rank %d sections %d\n", hf.info.levels,
-         hf.info.max_rank, hf.info.root_size, hf.info.neighbour_rank, hf.info.sections);
+  printf("levels %d max_rank %d root %d neighbour_rank %d sections %d col_rank %d r_dev %.3e\n",
+         hf.info.levels, hf.info.max_rank, hf.info.root_size, hf.info.neighbour_rank,
+         hf.info.sections, hf.info.neighbour_col_rank, r_dev);
   return 0;
 }

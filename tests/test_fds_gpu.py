@@ -37,11 +37,12 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
-def walls_sim(P, walls, mode, K=24, M=96, refine=3, fds=None):
+def walls_sim(P, walls, mode, K=24, M=96, refine=3, fds=None, recompress=True):
     lo, up = walls
     h = P.stokes_sim_create(0)
     P.stokes_sim_set_wall_solver(h, mode)
     P.stokes_sim_set_block_refinement(h, refine)
+    P.stokes_sim_set_fds_recompress(h, recompress)
     if fds is not None:
         P.stokes_sim_set_fds_params(h, *fds)
     P.stokes_sim_set_walls(h, lo.n, np.vstack([lo.nodes, up.nodes]),
@@ -83,6 +84,40 @@ def test_fds_solve_residual_against_oracle_operator(P, S, n_w, shape):
     assert np.abs(x - ref).max() / np.abs(ref).max() < 1e-9
 
 
+@pytest.mark.parametrize("n_w,shape", [(96, I.WALL_SHAPE_SMALL), (1000, I.WALL_SHAPE_LARGE)])
+def test_fds_recompression(P, S, n_w, shape):
+    """The column recompression of the neighbour factors (the remark closing Sec. 4.2) keeps the
+    solve at the decompositions' accuracy, one right-hand side (the library's section and
+    matrix-vector kernels) and several (library GEMMs) alike, agrees with the plain factors'
+    solution, and shrinks what a solve reads: K^-1 S (l x l_c) and C's blocks in place of
+    R (l x 4 n_w) and K^-1."""
+    lo, up = I.wall_curves(n_w, shape)
+    A = S.Walls(lo, up, D, MU).A()
+    b = rhs(A.shape[0], 3, n_w + 1)
+    out = {}
+    for rc in (True, False):
+        h = walls_sim(P, (lo, up), P.STOKES_WALLS_FDS, recompress=rc)
+        info = P.stokes_sim_fds_info(h)
+        X1 = dev(b[0])
+        P.stokes_sim_wall_solve(h, X1)
+        X = dev(b)
+        P.stokes_sim_wall_solve(h, X)
+        out[rc] = (info, X1.cpu().numpy(), X.cpu().numpy())
+        P.stokes_sim_destroy(h)
+    for rc, (info, x1, x) in out.items():
+        res = np.abs(x @ A.T - b).max(1) / np.abs(b).max(1)
+        assert res.max() < 1e-9, (rc, res)
+        assert np.abs(x1 - x[0]).max() / np.abs(x[0]).max() < 1e-12, rc
+    on, off = out[True][0], out[False][0]
+    assert off["neighbour_col_rank"] == 0
+    assert 0 < on["neighbour_col_rank"] < 2 * on["neighbour_rank"]
+    assert on["neighbour_rank"] == off["neighbour_rank"]
+    n_a = 4 * n_w
+    assert off["solve_bytes"] - on["solve_bytes"] > 0.5 * 8 * on["neighbour_rank"] * n_a, (on, off)
+    xa, xb = out[True][2], out[False][2]
+    assert np.abs(xa - xb).max() / np.abs(xb).max() < 1e-9
+
+
 def test_fds_info_and_tolerance(P, S):
     """The reported tree matches the wall size, ranks stay far below the box sizes, and a looser
     tolerance gives smaller ranks and a proportionally larger (still bounded) residual.  (At this
@@ -121,6 +156,8 @@ def test_fds_param_validation(P):
         for args in ((0.0, 64, 64), (1e-12, 4, 64), (1e-12, 64, 8), (1e-2, 64, 64)):
             with pytest.raises(P.StokesError):
                 P.stokes_sim_set_fds_params(h, *args)
+        with pytest.raises(P.StokesError):
+            P.stokes_sim_set_fds_recompress(h, 2)
         with pytest.raises(P.StokesError):  # no walls yet
             P.stokes_sim_wall_solve(h, dev(np.zeros(8)))
     finally:
@@ -190,6 +227,9 @@ def test_fds_paper_channel(P):
     P.stokes_sim_destroy(h)
     assert info["levels"] == 9 and info["max_rank"] < 200, info
     assert info["device_bytes"] < 4e9, info                 # dense FP64 A alone: 34 GB
+    # recompressed: a solve reads the HBS tables twice and O(N_w) more, not R's 8 l 4 n_w bytes
+    assert info["neighbour_col_rank"] > 0
+    assert info["solve_bytes"] < 8 * info["neighbour_rank"] * 4 * n_w, info
     geom = I.Geometry([lo, up], D, MU, {})
     s = P.StokesSum(geom)
     for k in range(2):

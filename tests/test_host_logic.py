@@ -105,10 +105,12 @@ def test_fmm_plan_and_passes(bins, tmp_path, order, leaf, tol):
 # ---------------------------------------------------------------------------
 # fast direct solver: host factorization
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("recompress", [0, 1])
 @pytest.mark.parametrize("n_w,shape", [(96, I.WALL_SHAPE_SMALL), (512, I.WALL_SHAPE_LARGE)])
-def test_fds_host_factorization_solves_the_oracle_operator(bins, tmp_path, n_w, shape):
+def test_fds_host_factorization_solves_the_oracle_operator(bins, tmp_path, n_w, shape, recompress):
     """The HBS tables and neighbour sections, applied as the device would, solve the oracle's
-    dense wall operator to ~1e-10."""
+    dense wall operator to ~1e-10; with the column recompression (the remark closing Sec. 4.2)
+    A_m(J, J_c) C reproduces R = A_m(J, :) to near the decompositions' 1e-12 tolerance."""
     from oracle import sim_oracle as S
     lo, up = I.wall_curves(n_w, shape)
     d, mu = 2 * PI, 0.7
@@ -124,8 +126,15 @@ def test_fds_host_factorization_solves_the_oracle_operator(bins, tmp_path, n_w, 
         np.vstack([lo.normals, up.normals]).tofile(f)
         np.concatenate([lo.curvature, up.curvature]).tofile(f)
         b.tofile(f)
-    txt = run(bins["fds_host_check"], case, out)
+    txt = run(bins["fds_host_check"], case, out, recompress)
     assert "levels" in txt
+    f = txt.split()
+    col_rank, r_dev = int(f[f.index("col_rank") + 1]), float(f[f.index("r_dev") + 1])
+    rank = int(f[f.index("neighbour_rank") + 1])
+    if recompress:
+        assert 0 < col_rank < 2 * rank and r_dev < 1e-11, txt
+    else:
+        assert col_rank == 0, txt
     x = np.fromfile(out).reshape(3, -1)
     res = np.abs(x @ A.T - b).max(1) / np.abs(b).max(1)
     assert res.max() < 1e-9, res
