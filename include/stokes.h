@@ -263,6 +263,13 @@ STOKES_API int stokes_fmm_create(stokes_ctx *ctx, int order, int leaf_size, stok
 STOKES_API int stokes_fmm_eval(stokes_fmm *fmm, const double *slp_density,
                                const double *dlp_density, double jump, double *out_velocity,
                                void *stream);
+/* Order of the following evaluations of this plan: 4 <= order <= the plan's order, or 0 for
+ * the plan's order (the default).  The expansions are truncated at that order (the plan's
+ * tree, lists and buffers are unchanged), so one plan serves a cheaper, less accurate
+ * evaluation beside its full-order one; the error falls by ~0.45 per order.  Takes effect
+ * at the next stokes_fmm_eval (evaluations already queued keep their order).
+ * STOKES_ERR_ARG outside that range. */
+STOKES_API int stokes_fmm_set_eval_order(stokes_fmm *fmm, int order);
 STOKES_API int stokes_fmm_get_info(const stokes_fmm *fmm, stokes_fmm_info *info);
 STOKES_API int stokes_fmm_last_error(const stokes_fmm *fmm, char *buf, size_t len);
 STOKES_API int stokes_fmm_destroy(stokes_fmm *fmm);
@@ -684,6 +691,16 @@ STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
  * The plan is rebuilt each step (the geometry moves) by a host thread while the GPU computes
  * the forces and the channel response.  Walls keep their double-float sums. */
 STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_size);
+/* STOKES_FP32_KAHAN steps: run the Krylov sweeps' vesicle sums (the operator of every inner
+ * GMRES iteration, the paper's FMM-accelerated matvec) on the step's FMM plan evaluated at
+ * `order` (stokes_fmm_set_eval_order) instead of the FP32-Kahan direct sum.  order 0 turns it
+ * off (default); otherwise order in [4, 40].  Order 14 matches the FP32-Kahan sum's ~5e-7
+ * relative error and order 20 gives ~5e-9; the sweeps only need to resolve the inner
+ * tolerance, and every convergence decision still uses the FP64-accurate residuals, so the
+ * step's result and tolerance are unchanged.  The plan (leaf size as set by
+ * stokes_sim_set_residual_fmm) is made at the larger of the two orders, once per step.
+ * STOKES_ERR_ARG outside the range. */
+STOKES_API int stokes_sim_set_sweep_fmm(stokes_sim *sim, int order);
 /* Close evaluation inside the step (the near-pair rule the paper applies to close vesicles,
  * Sec. 3.2): with factor > 0, every vesicle-vesicle single-layer sum of a step (right-hand
  * side, Krylov and residual matvecs in every precision, FMM sums) adds stokes_close_eval's

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
+    "stokes_fmm_set_eval_order": [_vp, _c_int],
     "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_fmm_destroy": [_vp],
     "stokes_close_create": [_vp, _c_double, _c_int, ctypes.POINTER(_vp)],
@@ -112,6 +113,7 @@ _SIGNATURES = {
     "stokes_sim_set_precond_precision": [_vp, _c_int],
     "stokes_sim_set_inner_tolerance": [_vp, _c_double],
     "stokes_sim_set_residual_fmm": [_vp, _c_int, _c_int],
+    "stokes_sim_set_sweep_fmm": [_vp, _c_int],
     "stokes_sim_set_close_eval": [_vp, _c_double, _c_int],
     "stokes_sim_set_warm_modes": [_vp, _c_int],
     "stokes_sim_set_warm_history": [_vp, _c_int],
@@ -353,6 +355,14 @@ def stokes_fmm_eval(f, slp_density, dlp_density, jump, out_velocity, stream=None
     code = load().stokes_fmm_eval(f, _dptr(slp_density, "slp_density", (2,), True),
                                   _dptr(dlp_density, "dlp_density", (2,), True), float(jump),
                                   _dptr(out_velocity, "out_velocity", (2,)), _stream(stream))
+    if code != STOKES_OK:
+        raise StokesError(code, _fmm_err(f))
+    return code
+
+
+def stokes_fmm_set_eval_order(f, order):
+    """Truncate the following evaluations of plan f at `order` (0: the plan's order)."""
+    code = load().stokes_fmm_set_eval_order(f, int(order))
     if code != STOKES_OK:
         raise StokesError(code, _fmm_err(f))
     return code
@@ -752,6 +762,11 @@ def stokes_sim_set_close_eval(h, factor, upsample=16):
 def stokes_sim_set_residual_fmm(h, order, leaf_size=32):
     """FP32-Kahan steps: FP64-accurate vesicle sums by the FMM of `order` (0 = double-float)."""
     return _sim_check(h, load().stokes_sim_set_residual_fmm(h, int(order), int(leaf_size)))
+
+
+def stokes_sim_set_sweep_fmm(h, order):
+    """FP32-Kahan steps: the Krylov sweeps' vesicle sums by the step's FMM plan at `order` (0 = direct)."""
+    return _sim_check(h, load().stokes_sim_set_sweep_fmm(h, int(order)))
 
 
 def stokes_sim_wall_stats(h):

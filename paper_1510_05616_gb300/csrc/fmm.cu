@@ -95,7 +95,8 @@ __device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, dou
 }
 
 struct FmmDev {
-  int p, n_src, N;
+  int p, n_src, N;            // p: the evaluation's expansion order
+  int tp1;                    // row length of tpow: the plan's order + 1
   int wall_slots;
   const int2 *src_slot;       // [n_src] (slot, m), sorted by leaf
   const double2 *src_pos;     // [n_src] image positions, sorted by leaf
@@ -114,7 +115,7 @@ struct FmmDev {
   double2 *out;               // [N] pair sums (node order)
   int n_roots_src, root_src0; // source cells of level 0: [root_src0, root_src0 + n_roots_src)
   double2 o;                  // origin of the complex coordinates (the forest's centre)
-  const double2 *tpow;        // [49][p + 1] t^-n of the integer offsets |t_x|, |t_y| <= 3
+  const double2 *tpow;        // [49][tp1] t^-n of the integer offsets |t_x|, |t_y| <= 3
   const double2 *tlog;        // [49] log(-t) of the same offsets
   const int *src_own;         // [n_src] vesicle curve of an m = 0 source, else -1
   const int *node_curve;      // [N] vesicle curve of a node, else -1
@@ -262,7 +263,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       const bool tab = abs(dx) <= 3 && abs(dy) <= 3;
       const int ti = (dy + 3) * 7 + (dx + 3);
       // off the table (roots only) the offset is an integer pair as well: use it exactly
-      const double2 T = tab ? f.tpow[ti * p1 + qi] : cpow(cinv(make_double2(dx, dy)), qi);
+      const double2 T = tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi);
       const double2 a = f.M[size_t(sc) * np + r];
       sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
       if (si == 0) {
@@ -442,6 +443,7 @@ __global__ void own_curve_kernel(const int *ves_curve_ids, const CurveDev *curve
 struct stokes_fmm {
   stokes_ctx *ctx = nullptr;
   int p = 20, L = 0, nx = 1, ny = 1, N = 0, n_src = 0;
+  int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -939,7 +941,9 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   }
   FMK(launch_pack(c, STOKES_FP64, slp, dlp, s));
   FmmDev d;
-  d.p = f->p;
+  const int pe = f->eval_p > 0 ? f->eval_p : f->p;  // every buffer is sized for f->p >= pe
+  d.p = pe;
+  d.tp1 = f->p + 1;
   d.n_src = f->n_src;
   d.N = N;
   d.wall_slots = c->wall_slots_f64;
@@ -968,14 +972,14 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.src_own = f->d_src_own;
   d.node_curve = f->d_node_curve;
   const int L = f->L;
-  const int nthr = std::max(kLeafThreads, (kSets * (f->p + 1) + 31) / 32 * 32);
+  const int nthr = std::max(kLeafThreads, (kSets * (pe + 1) + 31) / 32 * 32);
   auto hl = [&](int l) { return f->S / double(1 << l); };
   const int nleaf_s = f->sc_off[L + 1] - f->sc_off[L];
-  const int p1 = f->p + 1, np = kSets * p1;
+  const int p1 = pe + 1, np = kSets * p1;
   const size_t p2m_smem = sizeof(double2) * (kP2mChunk * p1 + kP2mChunk * kSets);
-  const size_t m2m_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(double) * f->p * f->p;
+  const size_t m2m_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(double) * pe * pe;
   const size_t m2l_smem =
-      sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + sizeof(double) * p1 * f->p;
+      sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + sizeof(double) * p1 * pe;
   if (nleaf_s > 0) p2m_kernel<<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
   for (int l = L - 1; l >= 0; --l) {
     const int nc = f->sc_off[l + 1] - f->sc_off[l];
@@ -1001,6 +1005,14 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   FMK(cudaGetLastError());
   if (c->n_ves_curves > 0) FMK(cudaStreamWaitEvent(s, c->ev_join, 0));
   FMK(launch_finish_nodes(c, 1, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
+  return STOKES_OK;
+}
+
+int stokes_fmm_set_eval_order(stokes_fmm *f, int order) {
+  if (!f) return STOKES_ERR_ARG;
+  if (order != 0 && (order < 4 || order > f->p))
+    return fmm_fail(f, STOKES_ERR_ARG, "the evaluation order must be 0 or in [4, the plan's order]");
+  f->eval_p = order == f->p ? 0 : order;
   return STOKES_OK;
 }
 

@@ -118,6 +118,10 @@ struct stokes_sim {
   // refinement residuals) by the FMM of order resid_fmm_order instead of double-float direct
   // sums (0 = off); the plan is rebuilt every step on a host thread beside the GPU's work
   int resid_fmm_order = 0, resid_fmm_leaf = 32;
+  // mixed-precision step: the Krylov sweeps' vesicle sums by the same plan evaluated at order
+  // sweep_fmm_order instead of the FP32-Kahan direct sum (0 = off); the plan is made at the
+  // larger of the two orders
+  int sweep_fmm_order = 0;
   stokes_fmm *fmm_v = nullptr;
   // close evaluation of the vesicle-vesicle single layer (stokes_sim_set_close_eval): every
   // vesicle sum of the step adds the correction of the close (node, vesicle image) pairs found
@@ -1190,13 +1194,31 @@ int add_close(stokes_sim *m, const double2 *f, double2 *out) {
   return STOKES_OK;
 }
 
-// z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).
+int fmm_sum(stokes_sim *m, int order, const double2 *dens, double2 *out, const char *what) {
+  int st = stokes_fmm_set_eval_order(m->fmm_v, order);
+  if (!st)
+    st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(dens), nullptr, 0.0,
+                         reinterpret_cast<double *>(out), m->s);
+  if (st) {
+    char buf[256];
+    stokes_fmm_last_error(m->fmm_v, buf, sizeof(buf));
+    return fail(m, st, "%s: %s", what, buf);
+  }
+  return STOKES_OK;
+}
+
+// z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).  FP32-Kahan
+// sums are the sweeps' operator: with sweep_fmm_order set they come from the step's FMM plan
+// at that order instead.
 int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, double *zout) {
   ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
                                              m->d_tmp2);
   SK(cudaGetLastError());
-  ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
-                     0.0, reinterpret_cast<double *>(m->d_tmp3), m->s));
+  if (precision == STOKES_FP32_KAHAN && m->sweep_fmm_order > 0 && m->fmm_v)
+    ST(fmm_sum(m, m->sweep_fmm_order, m->d_tmp2, m->d_tmp3, "FMM sweep"));
+  else
+    ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
+                       0.0, reinterpret_cast<double *>(m->d_tmp3), m->s));
   ST(add_close(m, m->d_tmp2, m->d_tmp3));
   ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
                                               zout);
@@ -1210,13 +1232,7 @@ int step_matvec_fmm(stokes_sim *m, double dt, const double *zin, double *zout) {
   ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
                                              m->d_tmp2);
   SK(cudaGetLastError());
-  const int st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
-                                 0.0, reinterpret_cast<double *>(m->d_tmp3), m->s);
-  if (st) {
-    char buf[256];
-    stokes_fmm_last_error(m->fmm_v, buf, sizeof(buf));
-    return fail(m, st, "FMM residual: %s", buf);
-  }
+  ST(fmm_sum(m, m->resid_fmm_order, m->d_tmp2, m->d_tmp3, "FMM residual"));
   ST(add_close(m, m->d_tmp2, m->d_tmp3));
   ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
                                               zout);
@@ -1240,7 +1256,8 @@ struct FmmPlanJob {
         status = STOKES_ERR_CUDA;
         return;
       }
-      status = stokes_fmm_create(m->ctx_v, m->resid_fmm_order, m->resid_fmm_leaf, &plan);
+      status = stokes_fmm_create(m->ctx_v, std::max(m->resid_fmm_order, m->sweep_fmm_order),
+                                 m->resid_fmm_leaf, &plan);
       ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });
   }
@@ -1988,6 +2005,8 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   // mixed precision with FMM residuals: the vesicle sums of the right-hand side and of the
   // refinement residuals go through this step's FMM plan
   const bool use_fmm = precision == STOKES_FP32_KAHAN && m->resid_fmm_order > 0;
+  // a plan for this step: FMM residuals and/or FMM sweeps
+  const bool use_plan = precision == STOKES_FP32_KAHAN && (use_fmm || m->sweep_fmm_order > 0);
   SK(cudaSetDevice(m->device));
   const auto t0 = std::chrono::steady_clock::now();
   const int V = m->V, n = m->n;
@@ -2006,9 +2025,9 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     m->close_v = nullptr;
   }
   FmmPlanJob plan_job;
-  if (use_fmm || m->close_factor > 0.0)
+  if (use_plan || m->close_factor > 0.0)
     SK(cudaStreamSynchronize(m->s));  // the plans read the updated geometry
-  if (use_fmm) plan_job.start(m);
+  if (use_plan) plan_job.start(m);
   if (m->close_factor > 0.0) {
     const int cst = stokes_close_create(m->ctx_v, m->close_factor, m->close_K, &m->close_v);
     if (cst) return fail(m, cst, "close-evaluation pairs: %s", m->ctx_v->err.c_str());
@@ -2021,14 +2040,14 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp));
   // right-hand side [S f_b + u_resp; ALC]
   double plan_ms = 0.0;
-  if (use_fmm) {
+  if (use_plan) {
     const int pst = plan_job.join();
     if (pst) return fail(m, pst, "FMM plan of the vesicles failed (%s)", m->ctx_v->err.c_str());
     m->fmm_v = plan_job.take();
     plan_ms = plan_job.ms;
-    const int st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(m->d_fb), nullptr,
-                                   0.0, reinterpret_cast<double *>(m->d_tmp3), m->s);
-    if (st) return fail(m, st, "FMM right-hand side failed");
+  }
+  if (use_fmm) {
+    ST(fmm_sum(m, m->resid_fmm_order, m->d_fb, m->d_tmp3, "FMM right-hand side"));
   } else {
     ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
                        reinterpret_cast<double *>(m->d_tmp3), m->s));
@@ -2291,6 +2310,14 @@ int stokes_sim_set_residual_fmm(stokes_sim *m, int order, int leaf_size) {
   if (leaf_size < 4 || leaf_size > 4096) return fail(m, STOKES_ERR_ARG, "leaf size must be in [4, 4096]");
   m->resid_fmm_order = order;
   m->resid_fmm_leaf = leaf_size;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_sweep_fmm(stokes_sim *m, int order) {
+  if (!m) return STOKES_ERR_ARG;
+  if (order != 0 && (order < 4 || order > 40))
+    return fail(m, STOKES_ERR_ARG, "FMM order must be 0 (off) or in [4, 40]");
+  m->sweep_fmm_order = order;
   return STOKES_OK;
 }
 

@@ -119,6 +119,38 @@ def test_fmm_plan_and_argument_errors(P):
     s.close()
 
 
+def test_fmm_eval_order_truncates_the_plan(P):
+    """A plan evaluated below its order (stokes_fmm_set_eval_order) computes what a plan made
+    at that order computes -- the tree and lists do not depend on the order -- to the last bit,
+    and 0 or the plan's own order restores the full evaluation; orders outside [4, plan] are
+    refused."""
+    import torch
+    g, slp, dlp = I.workload("mid_n16k")
+    s = P.StokesSum(g)
+    ts, td = dev(slp), dev(dlp)
+    u14, _ = fmm_eval(P, s, ts, td, 14)
+    u36, _ = fmm_eval(P, s, ts, td, 36)
+    f = P.stokes_fmm_create(s.h, 36, 32)
+    out = torch.zeros((s.N, 2), dtype=torch.float64, device="cuda")
+    try:
+        for bad in (3, 37, -1):
+            with pytest.raises(P.StokesError):
+                P.stokes_fmm_set_eval_order(f, bad)
+        P.stokes_fmm_set_eval_order(f, 14)
+        P.stokes_fmm_eval(f, ts, td, 0.0, out)
+        P.stokes_sync(s.h)
+        assert np.array_equal(out.cpu().numpy(), u14)
+        for full in (0, 36):
+            P.stokes_fmm_set_eval_order(f, full)
+            P.stokes_fmm_eval(f, ts, td, 0.0, out)
+            P.stokes_sync(s.h)
+            assert np.array_equal(out.cpu().numpy(), u36)
+        assert P.stokes_fmm_get_info(f)["order"] == 36
+    finally:
+        P.stokes_fmm_destroy(f)
+        s.close()
+
+
 def test_fmm_high_order_converges(P):
     """Orders above 30 (shared memory sized by the order) keep converging: at order 36 the FMM
     meets the double-float direct sum to 1e-11 on the 16k channel."""

@@ -228,12 +228,45 @@ def test_fmm_residual_step_matches_double_float_step(P):
     b.close()
 
 
+@pytest.mark.parametrize("resid", [36, 0])
+def test_fmm_sweep_step_matches_direct_sweep_step(P, resid):
+    """Mixed-precision steps on the 16k channel whose Krylov sweeps take their vesicle sums from
+    the step's FMM plan (order 20; with FMM residuals at order 36 or double-float residuals)
+    end on the same FP64-accurate residual bound at the same solution as the steps with
+    FP32-Kahan direct sweeps: solutions to 1e-8, positions to 1e-10."""
+    from paper_1510_05616_gb300 import warmstart as WS
+    g = I.workload("mid_n16k")[0]
+    dt, pd, kb = 1e-3, 2 * 2 * PI * 0.2, 0.01
+    a = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=resid)
+    b = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=resid, sweep_fmm=20)
+    for k in range(2):
+        sa = a.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        sb = b.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        assert sa["residual"] <= 1e-10 and sb["residual"] <= 1e-10
+        assert sb["fmm_plan_ms"] > 0.0
+        xa, siga, za = a.state()
+        xb, sigb, zb = b.state()
+        ez = np.abs(za - zb).max() / np.abs(za).max()
+        ex = np.abs(xa - xb).max()
+        print("step %d (residuals %s): FMM vs direct sweeps: solution %.2e, positions %.2e; "
+              "its %d / %d, step %.1f / %.1f ms"
+              % (k, resid or "df", ez, ex, sa["iterations"], sb["iterations"], sa["total_ms"],
+                 sb["total_ms"]))
+        assert ez <= 1e-8 and ex <= 1e-10
+    a.close()
+    b.close()
+
+
 def test_residual_fmm_and_warm_modes_arguments(P):
     h = P.stokes_sim_create(0)
     for bad in ((3, 32), (41, 32), (20, 2)):
         with pytest.raises(P.StokesError):
             P.stokes_sim_set_residual_fmm(h, *bad)
     P.stokes_sim_set_residual_fmm(h, 0)
+    for bad in (3, 41, -2):
+        with pytest.raises(P.StokesError):
+            P.stokes_sim_set_sweep_fmm(h, bad)
+    P.stokes_sim_set_sweep_fmm(h, 0)
     for bad in (2, 15, 66):
         with pytest.raises(P.StokesError):
             P.stokes_sim_set_warm_modes(h, bad)
