@@ -83,6 +83,7 @@ _SIGNATURES = {
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
     "stokes_fmm_set_eval_order": [_vp, _c_int],
+    "stokes_fmm_set_near_precision": [_vp, _c_int],
     "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_fmm_destroy": [_vp],
     "stokes_close_create": [_vp, _c_double, _c_int, ctypes.POINTER(_vp)],
@@ -363,6 +364,14 @@ def stokes_fmm_eval(f, slp_density, dlp_density, jump, out_velocity, stream=None
 def stokes_fmm_set_eval_order(f, order):
     """Truncate the following evaluations of plan f at `order` (0: the plan's order)."""
     code = load().stokes_fmm_set_eval_order(f, int(order))
+    if code != STOKES_OK:
+        raise StokesError(code, _fmm_err(f))
+    return code
+
+
+def stokes_fmm_set_near_precision(f, precision):
+    """Arithmetic of the directly summed pairs: STOKES_FP64 or STOKES_FP32_KAHAN."""
+    code = load().stokes_fmm_set_near_precision(f, int(precision))
     if code != STOKES_OK:
         raise StokesError(code, _fmm_err(f))
     return code

@@ -367,19 +367,23 @@ struct HbsBox {
 //                                   + sum_j G[r + j n] x2[in_off + j],     r < n
 // for the right-hand sides [blockIdx.z NC, ...) of column-major x1, x2, y.  E and G are stored
 // back to back, so both modes are one column-major product y = M v with v the box's inputs,
-// staged in shared memory.  A CTA takes the rows [blockIdx.y kRowTile, ...) of its box: each
-// row is split over kHbsThreads / kRowTile threads that sum strided shares of the columns (two
-// accumulators each, NC right-hand sides at once, so every matrix element is read once per
-// CTA), reduced in shared memory.  A warp reads kRowTile consecutive doubles of one column.
+// staged in shared memory.  A CTA takes the rows [blockIdx.y RT, ...) of its box: each row is
+// split over kHbsThreads / RT threads that sum strided shares of the columns (two accumulators
+// each, NC right-hand sides at once, so every matrix element is read once per CTA), reduced in
+// shared memory.  A warp reads RT consecutive doubles of 32 / RT columns.  RT = kRowTile (32)
+// for levels with many boxes; the small row tile (8 rows, 32 threads per row) serves the top
+// levels, where a few boxes would leave most SMs idle and each thread would walk a long chain
+// of columns: four times the CTAs and a quarter of the chain.
 // Dynamic shared memory: (NC max_cols + kHbsThreads NC) doubles.
-template <int NC>
+constexpr int kRowTileSmall = 8;
+template <int NC, int RT = kRowTile>
 __global__ void __launch_bounds__(kHbsThreads)
     hbs_level_kernel(const HbsBox *boxes, const double *mats, int mode, int ncol, const double *x1,
                      long long ld1, const double *x2, long long ld2, double *y, long long ldy) {
   extern __shared__ double sh[];
   const HbsBox b = boxes[blockIdx.x];
   const int R = mode == 0 ? b.k : b.n;
-  const int r0 = blockIdx.y * kRowTile;
+  const int r0 = blockIdx.y * RT;
   if (r0 >= R) return;  // uniform over the CTA
   const int c0 = blockIdx.z * NC;
   const int nc = min(NC, ncol - c0);
@@ -398,9 +402,9 @@ __global__ void __launch_bounds__(kHbsThreads)
     v[idx] = val;
   }
   __syncthreads();
-  constexpr int split = kHbsThreads / kRowTile;
-  const int Rt = min(kRowTile, R - r0);
-  const int r = threadIdx.x % kRowTile, q = threadIdx.x / kRowTile;
+  constexpr int split = kHbsThreads / RT;
+  const int Rt = min(RT, R - r0);
+  const int r = threadIdx.x % RT, q = threadIdx.x / RT;
   double a0[NC], a1[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) a0[c] = a1[c] = 0.0;
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(kHbsThreads)
     for (int c = 0; c < NC; ++c) a0[c] = part[r * NC + c];
     for (int p = 1; p < split; ++p)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) a0[c] += part[(p * kRowTile + r) * NC + c];
+      for (int c = 0; c < NC; ++c) a0[c] += part[(p * RT + r) * NC + c];
     for (int c = 0; c < nc; ++c) y[(c0 + c) * ldy + oy + r0 + r] = a0[c];
   }
 }
@@ -822,6 +826,7 @@ struct fds_solver {
   int n_sec_left = 0;                  // sections of the m = -1 neighbour (they come first);
                                        //   each neighbour's sections partition both walls
   int sub_row_chunks = 1;              // row chunks of the largest section (grid.y)
+  int sms = 1;                         // SMs of the device the solver was built on
   double *d_gpart = nullptr;           // partial sums of the one-right-hand-side products
   int gemv_chunks_R = 1, gemv_chunks_K = 1;
   int chunk_R = 1, chunk_K = 1;
@@ -887,8 +892,14 @@ void level(const fds_solver *f, int lev, int mode, int nc, const double *x1, lon
   const int tiles = (rows + kRowTile - 1) / kRowTile;
   if (nc == 1) {
     const size_t sm = sizeof(double) * (size_t(f->max_cols) + kHbsThreads);
-    hbs_level_kernel<1><<<dim3(nb, tiles, 1), kHbsThreads, sm, s>>>(
-        f->d_boxes[lev], f->d_mats, mode, nc, x1, ld1, x2, ld2, y, ldy);
+    if (nb * tiles < f->sms) {  // a top level: small row tiles
+      const int st = (rows + kRowTileSmall - 1) / kRowTileSmall;
+      hbs_level_kernel<1, kRowTileSmall><<<dim3(nb, st, 1), kHbsThreads, sm, s>>>(
+          f->d_boxes[lev], f->d_mats, mode, nc, x1, ld1, x2, ld2, y, ldy);
+    } else {
+      hbs_level_kernel<1><<<dim3(nb, tiles, 1), kHbsThreads, sm, s>>>(
+          f->d_boxes[lev], f->d_mats, mode, nc, x1, ld1, x2, ld2, y, ldy);
+    }
   } else {
     const size_t sm = sizeof(double) * kHbsCols * (size_t(f->max_cols) + kHbsThreads);
     hbs_level_kernel<kHbsCols><<<dim3(nb, tiles, (nc + kHbsCols - 1) / kHbsCols), kHbsThreads, sm,
@@ -1341,6 +1352,11 @@ int fds_build(fds_solver **out, int n_w, const double *nodes, const double *weig
       return bail(STOKES_ERR_ARG);
     }
     FD(cudaFuncSetAttribute(hbs_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+    FD(cudaFuncSetAttribute(hbs_level_kernel<1, kRowTileSmall>,
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+    int dev = 0;
+    FD(cudaGetDevice(&dev));
+    FD(cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, dev));
     FD(cudaFuncSetAttribute(hbs_level_kernel<kHbsCols>,
                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm8));
   }

@@ -96,6 +96,7 @@ __device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, dou
 
 struct FmmDev {
   int p, n_src, N;            // p: the evaluation's expansion order
+  int near32;                 // near-field pairs in FP32 arithmetic (accumulated in FP64)
   int tp1;                    // row length of tpow: the plan's order + 1
   int wall_slots;
   const int2 *src_slot;       // [n_src] (slot, m), sorted by leaf
@@ -340,6 +341,40 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
     // near field, directly (coincident pairs skipped); the near stokeslet weight is kept to
     // take it out of Q
     double ux = 0.0, uy = 0.0, qn1 = 0.0, qn2 = 0.0;
+    if (f.near32) {  // the same pairs in FP32 arithmetic: differences rounded once from FP64
+      for (int e = nb0; e < nb1; ++e) {
+        const int2 rg = f.scell_rng[f.nl_idx[e]];
+        for (int j = rg.x; j < rg.y; ++j) {
+          const int2 sm = f.src_slot[j];
+          const double2 w = f.src_pos[j];
+          const double4_32a vv = f.val[sm.x];
+          const bool wall = sm.x < f.wall_slots;
+          if (!wall) {
+            qn1 += vv.x;
+            qn2 += vv.y;
+          }
+          const int own = f.src_own[j];
+          if (own >= 0 && own == tcur) continue;
+          const double d1 = z.x - w.x, d2 = z.y - w.y;
+          if (d1 == 0.0 && d2 == 0.0) continue;
+          const float r1 = float(d1), r2 = float(d2);
+          const float rr = fmaf(r1, r1, r2 * r2);
+          const float inv = __frcp_rn(rr);
+          if (!wall) {
+            const float q1 = float(vv.x), q2 = float(vv.y);
+            const float lg = -0.5f * __logf(rr);
+            const float c = fmaf(r1, q1, r2 * q2) * inv;
+            ux += double(fmaf(lg, q1, c * r1));
+            uy += double(fmaf(lg, q2, c * r2));
+          } else {
+            const float c = fmaf(r1, float(vv.z), r2 * float(vv.w)) *
+                            fmaf(r1, float(vv.x), r2 * float(vv.y)) * inv * inv;
+            ux += double(c * r1);
+            uy += double(c * r2);
+          }
+        }
+      }
+    } else {
     for (int e = nb0; e < nb1; ++e) {
       const int2 rg = f.scell_rng[f.nl_idx[e]];
       for (int j = rg.x; j < rg.y; ++j) {
@@ -371,6 +406,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
         }
       }
     }
+    }
     // far field from the local expansion
     const double2 dq = make_double2(d1[0].x - d1[1].y, d1[0].y + d1[1].x);  // Phi'_q1 + i Phi'_q2
     const double2 zo = make_double2(z.x - f.o.x, z.y - f.o.y);
@@ -400,6 +436,7 @@ __device__ __forceinline__ int2 leaf_of(const Binning &bn, double2 q) {
 }
 
 constexpr int kOwnMax = 256;  // nodes per vesicle (the step and Kress tables allow at most 256)
+template <bool F32>
 __global__ void own_curve_kernel(const int *ves_curve_ids, const CurveDev *curves,
                                  const double2 *x, const double *w, const int *node_dens,
                                  const double *slp, double c_slp, Binning bn, double2 *out) {
@@ -423,6 +460,16 @@ __global__ void own_curve_kernel(const int *ves_curve_ids, const CurveDev *curve
       const double c = w[j] * c_slp;
       const double q1 = c * slp[2 * row], q2 = c * slp[2 * row + 1];
       const double r1 = z.x - x[j].x, r2 = z.y - x[j].y;
+      if constexpr (F32) {  // as the FP32 near field
+        if (r1 == 0.0 && r2 == 0.0) continue;
+        const float f1 = float(r1), f2 = float(r2), g1 = float(q1), g2 = float(q2);
+        const float rr = fmaf(f1, f1, f2 * f2);
+        const float lg = -0.5f * __logf(rr);
+        const float cc = fmaf(f1, g1, f2 * g2) * __frcp_rn(rr);
+        ux += double(fmaf(lg, g1, cc * f1));
+        uy += double(fmaf(lg, g2, cc * f2));
+        continue;
+      }
       const double rr = r1 * r1 + r2 * r2;
       if (rr == 0.0) continue;
       const double lg = -0.5 * log(rr);
@@ -444,6 +491,7 @@ struct stokes_fmm {
   stokes_ctx *ctx = nullptr;
   int p = 20, L = 0, nx = 1, ny = 1, N = 0, n_src = 0;
   int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
+  bool near32 = false;  // direct pairs (near field, own-curve removal) in FP32 arithmetic
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -944,6 +992,7 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const int pe = f->eval_p > 0 ? f->eval_p : f->p;  // every buffer is sized for f->p >= pe
   d.p = pe;
   d.tp1 = f->p + 1;
+  d.near32 = f->near32 ? 1 : 0;
   d.n_src = f->n_src;
   d.N = N;
   d.wall_slots = c->wall_slots_f64;
@@ -998,9 +1047,14 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     bn.gmaxx = (f->nx << kLmax) - 1;
     bn.gmaxy = (f->ny << kLmax) - 1;
     bn.shift = kLmax - L;
-    own_curve_kernel<<<c->n_ves_curves, 128, 0, s>>>(c->d_ves_curve_ids, c->d_curves, c->d_x,
-                                                     c->d_w, c->d_node_dens, slp,
-                                                     1.0 / (4.0 * kPiF * c->mu), bn, c->d_partial);
+    if (f->near32)
+      own_curve_kernel<true><<<c->n_ves_curves, 128, 0, s>>>(c->d_ves_curve_ids, c->d_curves, c->d_x,
+                                                             c->d_w, c->d_node_dens, slp,
+                                                             1.0 / (4.0 * kPiF * c->mu), bn, c->d_partial);
+    else
+      own_curve_kernel<false><<<c->n_ves_curves, 128, 0, s>>>(c->d_ves_curve_ids, c->d_curves, c->d_x,
+                                                              c->d_w, c->d_node_dens, slp,
+                                                              1.0 / (4.0 * kPiF * c->mu), bn, c->d_partial);
   }
   FMK(cudaGetLastError());
   if (c->n_ves_curves > 0) FMK(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -1013,6 +1067,14 @@ int stokes_fmm_set_eval_order(stokes_fmm *f, int order) {
   if (order != 0 && (order < 4 || order > f->p))
     return fmm_fail(f, STOKES_ERR_ARG, "the evaluation order must be 0 or in [4, the plan's order]");
   f->eval_p = order == f->p ? 0 : order;
+  return STOKES_OK;
+}
+
+int stokes_fmm_set_near_precision(stokes_fmm *f, int precision) {
+  if (!f) return STOKES_ERR_ARG;
+  if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
+    return fmm_fail(f, STOKES_ERR_ARG, "near-field precision must be STOKES_FP64 or STOKES_FP32_KAHAN");
+  f->near32 = precision == STOKES_FP32_KAHAN;
   return STOKES_OK;
 }
 

@@ -123,6 +123,10 @@ struct stokes_sim {
   // larger of the two orders
   int sweep_fmm_order = 0;
   stokes_fmm *fmm_v = nullptr;
+  // with FMM residuals, the block refinement's wall double-layer sums (channel response) come
+  // from an FMM plan of the fixed walls, made at the first such step after stokes_sim_set_walls
+  stokes_fmm *fmm_w = nullptr;
+  int fmm_w_order = 0;
   // close evaluation of the vesicle-vesicle single layer (stokes_sim_set_close_eval): every
   // vesicle sum of the step adds the correction of the close (node, vesicle image) pairs found
   // for the step's positions; factor 0 = off
@@ -418,18 +422,30 @@ __global__ void axpby_kernel(long n, double a, const double *x, double b, double
 // ---------------------------------------------------------------------------
 // per-vesicle spectral kernels (one block per vesicle, blockDim = n)
 // ---------------------------------------------------------------------------
+// Fourier differentiation on n equispaced points (n even) is circulant: D[a][k] = d[(a - k) mod
+// n] with d[0] = 0, d[q] = (-1)^q cot(q pi / n) / 2; every entry is computed from q in [0, n).
 __global__ void fourier_diff_kernel(int n, double *D) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * n) return;
-  const int a = t / n, k = t % n, q = a - k;
+  const int a = t / n, k = t % n, q = a >= k ? a - k : a - k + n;
   D[t] = (q == 0) ? 0.0 : 0.5 * ((q & 1) ? -1.0 : 1.0) / tan(q * kPiD / n);
 }
 
-// out = D in over one vesicle's n values held in shared memory (row-major D).
-__device__ __forceinline__ double drow(const double *D, const double *in, int n, int a) {
+// The per-vesicle kernels (blockDim = n, thread a) keep dd[j] = d[j mod n], j < 2n, in shared
+// memory, taken from D's column 0, and read row a of D as dd[a + n - k]: broadcast-free,
+// conflict-free shared loads instead of a strided walk through D's rows.  Needs a
+// __syncthreads() before the first drow.
+__device__ __forceinline__ void load_diff(const double *D, double *dd, int n, int a) {
+  const double d = D[size_t(a) * n];
+  dd[a] = d;
+  dd[a + n] = d;
+}
+
+// out = D in over one vesicle's n values held in shared memory (D as dd above).
+__device__ __forceinline__ double drow(const double *dd, const double *in, int n, int a) {
   double s = 0.0;
-  const double *row = D + size_t(a) * n;
-  for (int k = 0; k < n; ++k) s += row[k] * in[k];
+  const double *row = dd + a + n;
+  for (int k = 0; k < n; ++k) s += row[-k] * in[k];
   return s;
 }
 
@@ -438,10 +454,12 @@ __global__ void ves_geom_kernel(int n, const double2 *x, const double *D, double
                                 double2 *xs, double2 *nrm, double *w) {
   __shared__ double X[kMaxN], Y[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   X[a] = x[i].x;
   Y[a] = x[i].y;
   __syncthreads();
-  const double xa = drow(D, X, n, a), ya = drow(D, Y, n, a);
+  const double xa = drow(dd, X, n, a), ya = drow(dd, Y, n, a);
   const double s = sqrt(xa * xa + ya * ya);
   spd[i] = s;
   xs[i] = make_double2(xa / s, ya / s);
@@ -455,12 +473,14 @@ __global__ void ves_forces_kernel(int n, const double2 *x, const double *sigma, 
                                   double2 *f) {
   __shared__ double X[kMaxN], Y[kMaxN], TX[kMaxN], TY[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   const double s = spd[i];
   X[a] = x[i].x;
   Y[a] = x[i].y;
   __syncthreads();
   for (int r = 0; r < 4; ++r) {  // d/ds four times
-    const double dx = drow(D, X, n, a) / s, dy = drow(D, Y, n, a) / s;
+    const double dx = drow(dd, X, n, a) / s, dy = drow(dd, Y, n, a) / s;
     __syncthreads();
     X[a] = dx;
     Y[a] = dy;
@@ -470,7 +490,7 @@ __global__ void ves_forces_kernel(int n, const double2 *x, const double *sigma, 
   TX[a] = sigma[i] * xs[i].x;
   TY[a] = sigma[i] * xs[i].y;
   __syncthreads();
-  const double sx = drow(D, TX, n, a) / s, sy = drow(D, TY, n, a) / s;
+  const double sx = drow(dd, TX, n, a) / s, sy = drow(dd, TY, n, a) / s;
   fb[i] = make_double2(bx, by);
   f[i] = make_double2(bx + sx, by + sy);
 }
@@ -480,6 +500,8 @@ __global__ void ves_mv_pre_kernel(int n, const double *z, const double *D, const
                                   const double2 *xs, double dtkb, double2 *g) {
   __shared__ double X[kMaxN], Y[kMaxN], TX[kMaxN], TY[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   const double *zv = z + size_t(3) * n * v;
   const double s = spd[i];
   X[a] = zv[a];
@@ -487,9 +509,9 @@ __global__ void ves_mv_pre_kernel(int n, const double *z, const double *D, const
   TX[a] = zv[2 * n + a] * xs[i].x;
   TY[a] = zv[2 * n + a] * xs[i].y;
   __syncthreads();
-  const double sx = drow(D, TX, n, a) / s, sy = drow(D, TY, n, a) / s;
+  const double sx = drow(dd, TX, n, a) / s, sy = drow(dd, TY, n, a) / s;
   for (int r = 0; r < 4; ++r) {
-    const double dx = drow(D, X, n, a) / s, dy = drow(D, Y, n, a) / s;
+    const double dx = drow(dd, X, n, a) / s, dy = drow(dd, Y, n, a) / s;
     __syncthreads();
     X[a] = dx;
     Y[a] = dy;
@@ -503,13 +525,15 @@ __global__ void ves_mv_post_kernel(int n, const double *z, const double2 *Sg, co
                                    const double *spd, const double2 *xs, double *out) {
   __shared__ double X[kMaxN], Y[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   const double *zv = z + size_t(3) * n * v;
   double *ov = out + size_t(3) * n * v;
   X[a] = zv[a];
   Y[a] = zv[n + a];
   __syncthreads();
   const double s = spd[i];
-  const double ux = drow(D, X, n, a) / s, uy = drow(D, Y, n, a) / s;
+  const double ux = drow(dd, X, n, a) / s, uy = drow(dd, Y, n, a) / s;
   ov[a] = X[a] + Sg[i].x;
   ov[n + a] = Y[a] + Sg[i].y;
   ov[2 * n + a] = xs[i].x * ux + xs[i].y * uy;
@@ -541,11 +565,13 @@ __global__ void ves_LA_kernel(int n, const double2 *x, const double *D, const do
                               double *A) {
   __shared__ double X[kMaxN], Y[kMaxN], P[kMaxN], W[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   X[a] = x[i].x;
   Y[a] = x[i].y;
   W[a] = w[i];
   __syncthreads();
-  P[a] = X[a] * drow(D, Y, n, a);
+  P[a] = X[a] * drow(dd, Y, n, a);
   __syncthreads();
   if (a == 0) {
     double l = 0.0, s = 0.0;
@@ -564,14 +590,16 @@ __global__ void ves_advance_kernel(int n, double2 *x, const double *z, const dou
   __shared__ double X[kMaxN], Y[kMaxN], XA[kMaxN], YA[kMaxN], P[4][kMaxN];
   __shared__ double cc;
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   const double *zv = z + size_t(3) * n * v;
   X[a] = x[i].x + dt * zv[a];
   Y[a] = x[i].y + dt * zv[n + a];
   __syncthreads();
-  XA[a] = drow(D, X, n, a);
-  YA[a] = drow(D, Y, n, a);
+  XA[a] = drow(dd, X, n, a);
+  YA[a] = drow(dd, Y, n, a);
   __syncthreads();
-  const double xaa = drow(D, XA, n, a);
+  const double xaa = drow(dd, XA, n, a);
   P[0][a] = X[a] * YA[a];
   P[1][a] = X[a] * xaa;
   P[2][a] = YA[a] * YA[a];
@@ -604,11 +632,13 @@ __global__ void ves_reparam_kernel(int n, double2 *x, const double *D) {
   __shared__ double X[kMaxN], Y[kMaxN], S[kMaxN], Cr[kMaxN], Ci[kMaxN], SJ[kMaxN + 1];
   __shared__ double Xr[kMaxN], Xi[kMaxN], Yr[kMaxN], Yi[kMaxN], AS[kMaxN];
   const int v = blockIdx.x, a = threadIdx.x, i = v * n + a;
+  __shared__ double dd[2 * kMaxN];
+  load_diff(D, dd, n, a);
   const double h = 2.0 * kPiD / n;
   X[a] = x[i].x;
   Y[a] = x[i].y;
   __syncthreads();
-  const double xa = drow(D, X, n, a), ya = drow(D, Y, n, a);
+  const double xa = drow(dd, X, n, a), ya = drow(dd, Y, n, a);
   S[a] = sqrt(xa * xa + ya * ya);
   __syncthreads();
   // Fourier coefficients (frequency index a; a > n/2 means a - n) of speed and position
@@ -684,9 +714,9 @@ __global__ void ves_reparam_kernel(int n, double2 *x, const double *D) {
 // unknown order [u_x, u_y, sigma])
 // ---------------------------------------------------------------------------
 // Kress self single-layer blocks G_ij (n x n column-major each) and D_s = diag(1/s) D.
+template <typename T>
 __global__ void pc_parts_kernel(int n, const double2 *x, const double2 *xs, const double *spd,
-                                const double *kress, const double *D, double cmu, double *G,
-                                double *Ds) {
+                                const double *kress, const double *D, double cmu, T *G, T *Ds) {
   const int v = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * n) return;
@@ -712,44 +742,46 @@ __global__ void pc_parts_kernel(int n, const double2 *x, const double2 *xs, cons
   }
   const double sk = cmu * spd[ik];
   const size_t nn = size_t(n) * n, base = size_t(v) * 4 * nn + t;
-  G[base + 0 * nn] = (coef + h * m11) * sk;  // G_11
-  G[base + 1 * nn] = (h * m12) * sk;         // G_12
-  G[base + 2 * nn] = (h * m12) * sk;         // G_21
-  G[base + 3 * nn] = (coef + h * m22) * sk;  // G_22
-  Ds[size_t(v) * nn + t] = D[size_t(a) * n + k] / spd[ia];
+  G[base + 0 * nn] = T((coef + h * m11) * sk);  // G_11
+  G[base + 1 * nn] = T((h * m12) * sk);         // G_12
+  G[base + 2 * nn] = T((h * m12) * sk);         // G_21
+  G[base + 3 * nn] = T((coef + h * m22) * sk);  // G_22
+  Ds[size_t(v) * nn + t] = T(D[size_t(a) * n + k] / spd[ia]);
 }
 
 // T_c = D_s diag(x_s,c)  (c = 0, 1), stored as two n x n blocks per vesicle.
-__global__ void pc_T_kernel(int n, const double *Ds, const double2 *xs, double *T) {
+template <typename F>
+__global__ void pc_T_kernel(int n, const F *Ds, const double2 *xs, F *T) {
   const int v = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * n) return;
   const int k = t / n;
   const size_t nn = size_t(n) * n;
   const double d = Ds[size_t(v) * nn + t];
-  T[size_t(v) * 2 * nn + t] = d * xs[v * n + k].x;
-  T[size_t(v) * 2 * nn + nn + t] = d * xs[v * n + k].y;
+  T[size_t(v) * 2 * nn + t] = F(d * xs[v * n + k].x);
+  T[size_t(v) * 2 * nn + nn + t] = F(d * xs[v * n + k].y);
 }
 
 // Fill the constraint rows [diag(x_s,1) D_s, diag(x_s,2) D_s, 0] and add the identity of the
 // u block.
-__global__ void pc_fill_kernel(int n, const double *Ds, const double2 *xs, double *P) {
+template <typename F>
+__global__ void pc_fill_kernel(int n, const F *Ds, const double2 *xs, F *P) {
   const int v = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = 3 * n;
   if (t >= m * n) return;
   const int row = 2 * n + t % n, col = t / n;  // constraint rows, all 3n columns
   const size_t mm = size_t(m) * m;
-  double *Pv = P + size_t(v) * mm;
+  F *Pv = P + size_t(v) * mm;
   const int a = row - 2 * n;
   double val = 0.0;
   if (col < 2 * n) {
     const int c = col / n, k = col % n;
     const double xsc = c == 0 ? xs[v * n + a].x : xs[v * n + a].y;
-    val = xsc * Ds[size_t(v) * n * n + size_t(k) * n + a];
+    val = xsc * double(Ds[size_t(v) * n * n + size_t(k) * n + a]);
   }
-  Pv[row + size_t(col) * m] = val;
-  if (t < 2 * n) Pv[t + size_t(t) * m] += 1.0;
+  Pv[row + size_t(col) * m] = F(val);
+  if (t < 2 * n) Pv[t + size_t(t) * m] += F(1.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -957,11 +989,6 @@ __global__ void set_ptrs32_kernel(int count, float *base, size_t stride, float *
   if (t < count) ptrs[t] = base + stride * t;
 }
 
-__global__ void d2f_small_kernel(size_t n, const double *a, float *b) {
-  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    b[i] = __double2float_rn(a[i]);
-}
-
 // zout_v = Pinv32_v zin_v for every vesicle v (one block each, k = 3n rows, column-major k x k
 // blocks), products and sums in FP64: the FP32-stored inverse acts as a fixed FP64 operator.
 __global__ void precond32_apply_kernel(int k, const float *Pinv, const double *zin, double *zout) {
@@ -971,14 +998,18 @@ __global__ void precond32_apply_kernel(int k, const float *Pinv, const double *z
   __syncthreads();
   const float *B = Pinv + size_t(blockIdx.x) * k * k;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double a0 = 0.0, a1 = 0.0;
+    // eight coalesced column loads in flight per thread (HBM-bound: the block is read once)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int j = 0;
-    for (; j + 1 < k; j += 2) {
-      a0 = fma(double(B[i + size_t(j) * k]), zs[j], a0);
-      a1 = fma(double(B[i + size_t(j + 1) * k]), zs[j + 1], a1);
+    for (; j + 7 < k; j += 8) {
+      float b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = B[i + size_t(j + u) * k];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u & 3] = fma(double(b[u]), zs[j + u], acc[u & 3]);
     }
-    if (j < k) a0 = fma(double(B[i + size_t(j) * k]), zs[j], a0);
-    zout[off + i] = a0 + a1;
+    for (; j < k; ++j) acc[0] = fma(double(B[i + size_t(j) * k]), zs[j], acc[0]);
+    zout[off + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
 }
 
@@ -1136,11 +1167,37 @@ int block_solve(stokes_sim *m, const double *v, const double *g, double *tau, do
 // shrinks both by about five digits, so three reach round-off.  A tau is the walls'
 // double-layer sum with the interior jump -1/2 (the same operator as the assembled A), in
 // `prec` (FP64 or double-float).
-int refined_block_solve(stokes_sim *m, int prec) {
+// The walls' FMM plan at `order` (kept across steps: the walls do not move).
+int wall_fmm(stokes_sim *m, int order) {
+  if (m->fmm_w && m->fmm_w_order == order) return STOKES_OK;
+  if (m->fmm_w) stokes_fmm_destroy(m->fmm_w);
+  m->fmm_w = nullptr;
+  m->fmm_w_order = 0;
+  SK(cudaStreamSynchronize(m->s));
+  const int st = stokes_fmm_create(m->ctx_w, order, m->resid_fmm_leaf, &m->fmm_w);
+  if (st) return fail(m, st, "FMM plan of the walls failed (%s)", m->ctx_w->err.c_str());
+  m->fmm_w_order = order;
+  return STOKES_OK;
+}
+
+// Block solve of the extended system, then block_refine residual corrections on the whole
+// system; the wall double-layer sums of the residuals in `prec`, or by the walls' FMM plan of
+// order fmm_order (> 0).
+int refined_block_solve(stokes_sim *m, int prec, int fmm_order = 0) {
   ST(block_solve(m, m->d_rv, m->d_rg, m->d_tau, m->d_c));
   const double one = 1.0, mone = -1.0;
+  if (fmm_order > 0 && m->block_refine > 0) ST(wall_fmm(m, fmm_order));
   for (int k = 0; k < m->block_refine; ++k) {
-    ST(stokes_sum_eval(m->ctx_w, prec, nullptr, m->d_tau, -0.5, m->d_resv, m->s));
+    if (fmm_order > 0) {
+      const int st = stokes_fmm_eval(m->fmm_w, nullptr, m->d_tau, -0.5, m->d_resv, m->s);
+      if (st) {
+        char buf[256];
+        stokes_fmm_last_error(m->fmm_w, buf, sizeof(buf));
+        return fail(m, st, "FMM wall sum: %s", buf);
+      }
+    } else {
+      ST(stokes_sum_eval(m->ctx_w, prec, nullptr, m->d_tau, -0.5, m->d_resv, m->s));
+    }
     axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, 1.0, m->d_rv, -1.0, m->d_resv);
     BK(cublasDgemv(m->blas, CUBLAS_OP_N, m->nA, 2 * m->M, &mone, m->d_B, m->nA, m->d_c, 1, &one,
                    m->d_resv, 1));
@@ -1160,7 +1217,7 @@ int refined_block_solve(stokes_sim *m, int prec) {
 // Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.  The
 // pair sums run in `prec` (STOKES_FP64 or the equally accurate STOKES_DOUBLE_FLOAT).
 int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out,
-                     int prec = STOKES_FP64) {
+                     int prec = STOKES_FP64, int fmm_order = 0) {
   const double cmu = 1.0 / (4.0 * kPiD * m->mu);
   // v = -S^near f at the wall nodes (vesicle sums at free targets)
   ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
@@ -1170,7 +1227,7 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   // v = -(S^near f) at the walls
   axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, -1.0, m->d_vrhs, 0.0, m->d_rv);
   SK(cudaGetLastError());
-  ST(refined_block_solve(m, prec));
+  ST(refined_block_solve(m, prec, fmm_order));
   // u_resp = D^near tau + sum_m c_m S(., y_m) at the vesicle nodes
   ST(stokes_sum_eval_targets(m->ctx_w, prec, nullptr, m->d_tau, m->Nv,
                              reinterpret_cast<const double *>(m->d_x),
@@ -1194,8 +1251,12 @@ int add_close(stokes_sim *m, const double2 *f, double2 *out) {
   return STOKES_OK;
 }
 
-int fmm_sum(stokes_sim *m, int order, const double2 *dens, double2 *out, const char *what) {
+// The vesicle sum of `dens` by the step's FMM plan at `order`, its direct pairs in FP64 or (for
+// the sweeps, whose expansions are no more accurate) in FP32.
+int fmm_sum(stokes_sim *m, int order, bool near32, const double2 *dens, double2 *out,
+            const char *what) {
   int st = stokes_fmm_set_eval_order(m->fmm_v, order);
+  if (!st) st = stokes_fmm_set_near_precision(m->fmm_v, near32 ? STOKES_FP32_KAHAN : STOKES_FP64);
   if (!st)
     st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(dens), nullptr, 0.0,
                          reinterpret_cast<double *>(out), m->s);
@@ -1207,6 +1268,10 @@ int fmm_sum(stokes_sim *m, int order, const double2 *dens, double2 *out, const c
   return STOKES_OK;
 }
 
+// Sweep evaluations up to this order (truncation error ~1e-7 and above) take their direct pairs
+// in FP32.
+constexpr int kSweepNear32MaxOrder = 16;
+
 // z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).  FP32-Kahan
 // sums are the sweeps' operator: with sweep_fmm_order set they come from the step's FMM plan
 // at that order instead.
@@ -1215,7 +1280,8 @@ int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, doub
                                              m->d_tmp2);
   SK(cudaGetLastError());
   if (precision == STOKES_FP32_KAHAN && m->sweep_fmm_order > 0 && m->fmm_v)
-    ST(fmm_sum(m, m->sweep_fmm_order, m->d_tmp2, m->d_tmp3, "FMM sweep"));
+    ST(fmm_sum(m, m->sweep_fmm_order, m->sweep_fmm_order <= kSweepNear32MaxOrder, m->d_tmp2,
+               m->d_tmp3, "FMM sweep"));
   else
     ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,
                        0.0, reinterpret_cast<double *>(m->d_tmp3), m->s));
@@ -1232,7 +1298,7 @@ int step_matvec_fmm(stokes_sim *m, double dt, const double *zin, double *zout) {
   ves_mv_pre_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_D, m->d_spd, m->d_xs, dt * m->kappa_b,
                                              m->d_tmp2);
   SK(cudaGetLastError());
-  ST(fmm_sum(m, m->resid_fmm_order, m->d_tmp2, m->d_tmp3, "FMM residual"));
+  ST(fmm_sum(m, m->resid_fmm_order, false, m->d_tmp2, m->d_tmp3, "FMM residual"));
   ST(add_close(m, m->d_tmp2, m->d_tmp3));
   ves_mv_post_kernel<<<m->V, m->n, 0, m->s>>>(m->n, zin, m->d_tmp3, m->d_D, m->d_spd, m->d_xs,
                                               zout);
@@ -1290,43 +1356,59 @@ int precond_apply(stokes_sim *m, const double *zin, double *zout) {
   return STOKES_OK;
 }
 
-int precond_build(stokes_sim *m, double dt) {
+// The preconditioner's 3n x 3n blocks [I + dt kB G D4, -(G_1 T_1 + G_2 T_2); x_s . D_s, 0] per
+// vesicle.  With an FP32 factorization (the default) they are assembled in FP32 as well
+// (SGEMMs; the FP64 buffers hold the FP32 factors), since only the factors' inverse is used and
+// it is a fixed operator either way; with FP64 factors, in FP64.
+template <typename F>
+int precond_assemble(stokes_sim *m, double dt, F *G, F *Ds, F *D2, F *D4, F *T, F *P) {
   const int n = m->n, V = m->V, k = 3 * n;
   const size_t nn = size_t(n) * n, kk = size_t(k) * k;
   const double cmu = 1.0 / (4.0 * kPiD * m->mu);
   dim3 g2(nb(n * n, 256), V);
-  pc_parts_kernel<<<g2, 256, 0, m->s>>>(n, m->d_x, m->d_xs, m->d_spd, m->d_kress, m->d_D, cmu,
-                                        m->d_G, m->d_Ds);
+  pc_parts_kernel<F><<<g2, 256, 0, m->s>>>(n, m->d_x, m->d_xs, m->d_spd, m->d_kress, m->d_D, cmu, G, Ds);
   SK(cudaGetLastError());
-  const double one = 1.0, zero = 0.0, mone = -1.0, dtkb = dt * m->kappa_b;
+  const F one = F(1), zero = F(0), mone = F(-1), dtkb = F(dt * m->kappa_b);
+  auto gemm = [&](const F *alpha, const F *A, int lda, long long sa, const F *B, int ldb,
+                  long long sb, const F *beta, F *C, int ldc, long long sc) {
+    if constexpr (sizeof(F) == 8)
+      return cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, alpha, A, lda, sa,
+                                       B, ldb, sb, beta, C, ldc, sc, V);
+    else
+      return cublasSgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, alpha, A, lda, sa,
+                                       B, ldb, sb, beta, C, ldc, sc, V);
+  };
   // D2 = Ds Ds, D4 = D2 D2
-  BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, m->d_Ds, n, nn,
-                               m->d_Ds, n, nn, &zero, m->d_D2, n, nn, V));
-  BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, m->d_D2, n, nn,
-                               m->d_D2, n, nn, &zero, m->d_D4, n, nn, V));
-  pc_T_kernel<<<g2, 256, 0, m->s>>>(n, m->d_Ds, m->d_xs, m->d_T);
+  BK(gemm(&one, Ds, n, nn, Ds, n, nn, &zero, D2, n, nn));
+  BK(gemm(&one, D2, n, nn, D2, n, nn, &zero, D4, n, nn));
+  pc_T_kernel<F><<<g2, 256, 0, m->s>>>(n, Ds, m->d_xs, T);
   SK(cudaGetLastError());
   // u block: dt kB G_ij D4 ; sigma column block: -(G_i1 T_1 + G_i2 T_2)
   for (int i = 0; i < 2; ++i) {
     for (int j = 0; j < 2; ++j) {
-      BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &dtkb,
-                                   m->d_G + (2 * i + j) * nn, n, 4 * nn, m->d_D4, n, nn, &zero,
-                                   m->d_P + i * n + size_t(j) * n * k, k, kk, V));
-      BK(cublasDgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &mone,
-                                   m->d_G + (2 * i + j) * nn, n, 4 * nn, m->d_T + j * nn, n, 2 * nn,
-                                   j == 0 ? &zero : &one, m->d_P + i * n + size_t(2 * n) * k, k, kk,
-                                   V));
+      BK(gemm(&dtkb, G + (2 * i + j) * nn, n, 4 * nn, D4, n, nn, &zero,
+              P + i * n + size_t(j) * n * k, k, kk));
+      BK(gemm(&mone, G + (2 * i + j) * nn, n, 4 * nn, T + j * nn, n, 2 * nn,
+              j == 0 ? &zero : &one, P + i * n + size_t(2 * n) * k, k, kk));
     }
   }
-  pc_fill_kernel<<<dim3(nb(3 * n * n, 256), V), 256, 0, m->s>>>(n, m->d_Ds, m->d_xs, m->d_P);
+  pc_fill_kernel<F><<<dim3(nb(3 * n * n, 256), V), 256, 0, m->s>>>(n, Ds, m->d_xs, P);
   SK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+int precond_build(stokes_sim *m, double dt) {
+  const int n = m->n, V = m->V, k = 3 * n;
   if (m->precond_fp32) {
-    d2f_small_kernel<<<nb(long(kk) * V, 256), 256, 0, m->s>>>(kk * V, m->d_P, m->d_P32);
-    SK(cudaGetLastError());
+    // FP32 views of the FP64 assembly buffers (each has room for twice its FP32 contents)
+    ST(precond_assemble<float>(m, dt, reinterpret_cast<float *>(m->d_G), reinterpret_cast<float *>(m->d_Ds),
+                               reinterpret_cast<float *>(m->d_D2), reinterpret_cast<float *>(m->d_D4),
+                               reinterpret_cast<float *>(m->d_T), m->d_P32));
     BK(cublasSgetrfBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_pinfo, V));
     BK(cublasSgetriBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_Piptr32, k, m->d_pinfo, V));
     return STOKES_OK;
   }
+  ST(precond_assemble<double>(m, dt, m->d_G, m->d_Ds, m->d_D2, m->d_D4, m->d_T, m->d_P));
   BK(cublasDgetrfBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_pinfo, V));
   BK(cublasDgetriBatched(m->blas, k, m->d_Pptr, k, m->d_ppiv, m->d_Piptr, k, m->d_pinfo, V));
   return STOKES_OK;
@@ -1433,6 +1515,9 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
 }
 
 void free_walls(stokes_sim *m) {
+  if (m->fmm_w) stokes_fmm_destroy(m->fmm_w);  // before its context
+  m->fmm_w = nullptr;
+  m->fmm_w_order = 0;
   if (m->ctx_w) stokes_destroy(m->ctx_w);
   m->ctx_w = nullptr;
   dfree(m->d_wx);
@@ -2037,7 +2122,8 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
                                        m->d_fb, m->d_f);
   SK(cudaGetLastError());
   // steps 3-5: channel response of the explicit forces
-  if (m->have_walls) ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp));
+  if (m->have_walls)
+    ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp, use_fmm ? m->resid_fmm_order : 0));
   // right-hand side [S f_b + u_resp; ALC]
   double plan_ms = 0.0;
   if (use_plan) {
@@ -2047,7 +2133,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     plan_ms = plan_job.ms;
   }
   if (use_fmm) {
-    ST(fmm_sum(m, m->resid_fmm_order, m->d_fb, m->d_tmp3, "FMM right-hand side"));
+    ST(fmm_sum(m, m->resid_fmm_order, false, m->d_fb, m->d_tmp3, "FMM right-hand side"));
   } else {
     ST(stokes_sum_eval(m->ctx_v, hp, reinterpret_cast<const double *>(m->d_fb), nullptr, 0.0,
                        reinterpret_cast<double *>(m->d_tmp3), m->s));
