@@ -270,13 +270,14 @@ STOKES_API int stokes_fmm_eval(stokes_fmm *fmm, const double *slp_density,
  * at the next stokes_fmm_eval (evaluations already queued keep their order).
  * STOKES_ERR_ARG outside that range. */
 STOKES_API int stokes_fmm_set_eval_order(stokes_fmm *fmm, int order);
-/* Arithmetic of the directly summed pairs of the following evaluations (the near field of each
- * target leaf and the removal of a vesicle's own far-field pairs): STOKES_FP64 (default) or
- * STOKES_FP32_KAHAN -- each pair's terms in FP32 from coordinate differences taken in FP64 and
- * rounded once (relative error ~1e-7 per pair), accumulated in FP64.  Meant for evaluations
- * whose truncation error is of that size anyway (orders up to ~16).  STOKES_ERR_ARG for any
- * other precision. */
-STOKES_API int stokes_fmm_set_near_precision(stokes_fmm *fmm, int precision);
+/* Arithmetic of the following evaluations: STOKES_FP64 (default) or STOKES_FP32_KAHAN -- the
+ * expansions (P2M, M2M, M2L, L2L, L2P) in FP32 complex arithmetic, and each directly summed
+ * pair (near field, removal of a vesicle's own far-field pairs) in FP32 from coordinate
+ * differences taken in FP64 and rounded once, accumulated in FP64; coordinates, offsets and
+ * the final assembly of the velocity stay FP64.  FP32 rounding adds ~1e-6 relative, so it is
+ * meant for orders up to ~16, whose truncation error is of that size anyway.  STOKES_ERR_ARG
+ * for any other precision. */
+STOKES_API int stokes_fmm_set_precision(stokes_fmm *fmm, int precision);
 STOKES_API int stokes_fmm_get_info(const stokes_fmm *fmm, stokes_fmm_info *info);
 STOKES_API int stokes_fmm_last_error(const stokes_fmm *fmm, char *buf, size_t len);
 STOKES_API int stokes_fmm_destroy(stokes_fmm *fmm);
@@ -706,8 +707,8 @@ STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_
  * off (default); otherwise order in [4, 40].  Order 14 matches the FP32-Kahan sum's ~5e-7
  * relative error and order 20 gives ~5e-9; the sweeps only need to resolve the inner
  * tolerance, and every convergence decision still uses the FP64-accurate residuals, so the
- * step's result and tolerance are unchanged.  Up to order 16 the sweeps' directly summed pairs
- * run in FP32 (stokes_fmm_set_near_precision), above it in FP64.  The plan (leaf size as set by
+ * step's result and tolerance are unchanged.  Up to order 16 the sweep evaluations run in FP32
+ * (stokes_fmm_set_precision), above it in FP64.  The plan (leaf size as set by
  * stokes_sim_set_residual_fmm) is made at the larger of the two orders, once per step.
  * STOKES_ERR_ARG outside the range. */
 STOKES_API int stokes_sim_set_sweep_fmm(stokes_sim *sim, int order);

@@ -83,7 +83,7 @@ _SIGNATURES = {
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
     "stokes_fmm_set_eval_order": [_vp, _c_int],
-    "stokes_fmm_set_near_precision": [_vp, _c_int],
+    "stokes_fmm_set_precision": [_vp, _c_int],
     "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
     "stokes_fmm_destroy": [_vp],
     "stokes_close_create": [_vp, _c_double, _c_int, ctypes.POINTER(_vp)],
@@ -369,9 +369,10 @@ def stokes_fmm_set_eval_order(f, order):
     return code
 
 
-def stokes_fmm_set_near_precision(f, precision):
-    """Arithmetic of the directly summed pairs: STOKES_FP64 or STOKES_FP32_KAHAN."""
-    code = load().stokes_fmm_set_near_precision(f, int(precision))
+def stokes_fmm_set_precision(f, precision):
+    """Arithmetic of the following evaluations: STOKES_FP64 or STOKES_FP32_KAHAN (FP32 expansions
+    and direct pairs)."""
+    code = load().stokes_fmm_set_precision(f, int(precision))
     if code != STOKES_OK:
         raise StokesError(code, _fmm_err(f))
     return code

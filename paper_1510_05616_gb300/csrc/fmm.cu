@@ -73,6 +73,28 @@ __device__ __forceinline__ double2 cpow(double2 a, int n) {  // n >= 0, by squar
   return r;
 }
 
+// The same operations on FP32 complex numbers (the evaluations at low orders run their
+// expansions in FP32), and the complex type of each real type.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+template <typename R> struct CxOf;
+template <> struct CxOf<double> { using type = double2; };
+template <> struct CxOf<float> { using type = float2; };
+template <typename R> using cx = typename CxOf<R>::type;
+template <typename R> __device__ __forceinline__ cx<R> mkc(double x, double y) {
+  return cx<R>{R(x), R(y)};
+}
+template <typename R> __device__ __forceinline__ cx<R> tocx(double2 a) { return mkc<R>(a.x, a.y); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+
 // The six charges of one (image) source at w: vesicle value (q1, q2, ., .), wall value
 // (T1, T2, n1, n2).
 __device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, double2 (&c)[kSets]) {
@@ -111,8 +133,8 @@ struct FmmDev {
   const int *tgt_node;        // [N] node of each sorted target
   const int2 *tleaf_rng;      // [target leaves] range of sorted targets
   const double2 *x;           // [N] node positions
-  double2 *M;                 // [source cells][kSets][p + 1]
-  double2 *Lc;                // [target cells][kSets][p + 1]
+  double2 *M;                 // [source cells][kSets][p + 1], FP64 or (FP32 evaluations) float2
+  double2 *Lc;                // [target cells][kSets][p + 1], likewise
   double2 *out;               // [N] pair sums (node order)
   int n_roots_src, root_src0; // source cells of level 0: [root_src0, root_src0 + n_roots_src)
   double2 o;                  // origin of the complex coordinates (the forest's centre)
@@ -125,7 +147,9 @@ struct FmmDev {
 // P2M: one CTA per source leaf; thread (set, k).  Sources are staged 32 at a time with their
 // charges and the powers u^k of their scaled offsets from the centre.
 constexpr int kP2mChunk = 32;
+template <typename R>
 __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
+  using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
   const int2 rg = f.scell_rng[cell];
   const double2 ctr = f.scell_ctr[cell];
@@ -134,21 +158,22 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
   const int set = t / p1, k = t - set * p1;
   // dynamic shared memory (p2m_smem): pw[kP2mChunk][p + 1], then sc[kP2mChunk][kSets]
   extern __shared__ double2 dyn_p2m[];
-  double2 *pw = dyn_p2m;
-  double2(*sc)[kSets] = reinterpret_cast<double2(*)[kSets]>(dyn_p2m + kP2mChunk * p1);
-  double2 acc = make_double2(0.0, 0.0);
+  C *pw = reinterpret_cast<C *>(dyn_p2m);
+  C(*sc)[kSets] = reinterpret_cast<C(*)[kSets]>(pw + kP2mChunk * p1);
+  C *M = reinterpret_cast<C *>(f.M);
+  C acc = mkc<R>(0.0, 0.0);
   for (int j0 = rg.x; j0 < rg.y; j0 += kP2mChunk) {
     const int nj = min(kP2mChunk, rg.y - j0);
     __syncthreads();
     if (t < nj) {
       const int2 sm = f.src_slot[j0 + t];
       const double2 w = f.src_pos[j0 + t];
-      const double2 u = make_double2((w.x - ctr.x) / h, (w.y - ctr.y) / h);
+      const C u = mkc<R>((w.x - ctr.x) / h, (w.y - ctr.y) / h);
       double2 c[kSets];
       charges(sm.x < f.wall_slots, make_double2(w.x - f.o.x, w.y - f.o.y), f.val[sm.x], c);
 #pragma unroll
-      for (int s = 0; s < kSets; ++s) sc[t][s] = c[s];
-      double2 uk = make_double2(1.0, 0.0);
+      for (int s = 0; s < kSets; ++s) sc[t][s] = tocx<R>(c[s]);
+      C uk = mkc<R>(1.0, 0.0);
       for (int n = 0; n <= p; ++n) {
         pw[t * p1 + n] = uk;
         uk = cmul(uk, u);
@@ -158,13 +183,15 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
     if (set < kSets)
       for (int j = 0; j < nj; ++j) acc = cfma(sc[j][set], pw[j * p1 + k], acc);
   }
-  if (set < kSets) f.M[(size_t(cell) * kSets + set) * p1 + k] = k == 0 ? acc : cscale(acc, -1.0 / k);
+  if (set < kSets) M[(size_t(cell) * kSets + set) * p1 + k] = k == 0 ? acc : cscale(acc, R(-1.0 / k));
 }
 
 // M2M: one CTA per source cell of a level above the leaves; thread (set, q).  The children's
 // coefficients, the powers of their offsets and the binomials are staged in shared memory:
 // a'_q += -a_0 s^q / q + sum_{k <= q} a_k 2^-k s^(q-k) C(q - 1, k - 1), s = (c_child - c) / h.
+template <typename R>
 __global__ void m2m_kernel(FmmDev f, int cell0) {
+  using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
   const int2 ch = f.scell_rng[cell];
   const double2 ctr = f.scell_ctr[cell];
@@ -172,19 +199,21 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
   const int t = threadIdx.x;
   const int set = t / p1, q = t - set * p1;
   const int nch = ch.y - ch.x;  // 1..4
-  const double inv_q = q > 0 ? 1.0 / q : 0.0;
+  const R inv_q = q > 0 ? R(1.0 / q) : R(0);
+  C *M = reinterpret_cast<C *>(f.M);
   // dynamic shared memory (m2m_smem): sa[4][np], sp[4][p + 1], then
-  // bm[p * p] = C(q - 1, k - 1) 2^-k, row q - 1, k = 1..p
+  // bm[p * p] = C(q - 1, k - 1) 2^-k at (k - 1) p + q - 1, k = 1..p (consecutive q, consecutive
+  // words)
   extern __shared__ double2 dyn_m2m[];
-  double2 *sa = dyn_m2m, *sp = dyn_m2m + 4 * np;
-  double *bm = reinterpret_cast<double *>(sp + 4 * p1);
+  C *sa = reinterpret_cast<C *>(dyn_m2m), *sp = sa + 4 * np;
+  R *bm = reinterpret_cast<R *>(sp + 4 * p1);
   for (int i = t; i < p * p; i += blockDim.x) {
-    const int qq = i / p, k = i - qq * p + 1;
-    bm[i] = c_binom[qq][k - 1] * ldexp(1.0, -k);
+    const int k1 = i / p, qq = i - k1 * p;  // k1 = k - 1, qq = q - 1
+    bm[i] = R(c_binom[qq][k1] * ldexp(1.0, -(k1 + 1)));
   }
   for (int i = t; i < nch * np; i += blockDim.x) {
     const int c = i / np, r = i - c * np;
-    sa[c * np + r] = f.M[size_t(ch.x + c) * np + r];
+    sa[c * np + r] = M[size_t(ch.x + c) * np + r];
   }
   for (int i = t; i < nch * p1; i += blockDim.x) {
     const int c = i / p1, n = i - c * p1;
@@ -192,24 +221,24 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
     // the child centre sits a quarter of the parent side away along each axis
     const double2 d = make_double2(cc.x - ctr.x, cc.y - ctr.y);
     const double hp = 4.0 * fabs(d.x);
-    sp[c * p1 + n] = cpow(make_double2(d.x / hp, d.y / hp), n);
+    sp[c * p1 + n] = tocx<R>(cpow(make_double2(d.x / hp, d.y / hp), n));
   }
   __syncthreads();
   if (set >= kSets) return;
-  double2 acc = make_double2(0.0, 0.0);
+  C acc = mkc<R>(0.0, 0.0);
   for (int c = 0; c < nch; ++c) {
-    const double2 *a = sa + c * np + set * p1;
-    const double2 *spc = sp + c * p1;
+    const C *a = sa + c * np + set * p1;
+    const C *spc = sp + c * p1;
     if (q == 0) {
       acc = cadd(acc, a[0]);
     } else {
-      double2 v = cscale(cmul(a[0], spc[q]), -inv_q);
-      const double *B = bm + (q - 1) * p;
-      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(spc[q - k], B[k - 1]), v);
+      C v = cscale(cmul(a[0], spc[q]), -inv_q);
+      const R *B = bm + (q - 1);
+      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(spc[q - k], B[(k - 1) * p]), v);
       acc = cadd(acc, v);
     }
   }
-  f.M[(size_t(cell) * kSets + set) * p1 + q] = acc;
+  M[(size_t(cell) * kSets + set) * p1 + q] = acc;
 }
 
 // L2L from the parent and M2L from the interaction list: one CTA per target cell of one level;
@@ -219,35 +248,41 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
 // offset with |t_x|, |t_y| <= 3, whose powers and log(-t) come from the plan's table.  Source
 // cells are staged kM2lBatch at a time.
 constexpr int kM2lBatch = 4;
+template <typename R>
 __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
+  using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
   const double2 ct = f.tcell_ctr[cell];
   const int p = f.p, p1 = p + 1, np = kSets * p1;
   const int t = threadIdx.x;
   const int set = t / p1, q = t - set * p1;
-  const double inv_h = 1.0 / h, inv_q = q > 0 ? 1.0 / q : 0.0;  // no divisions in the loops
+  const double inv_h = 1.0 / h;
+  const R inv_q = q > 0 ? R(1.0 / q) : R(0);  // no divisions in the loops
+  const C *M = reinterpret_cast<const C *>(f.M);
+  C *Lc = reinterpret_cast<C *>(f.Lc);
   // dynamic shared memory (m2l_smem): sw[kM2lBatch][np], stq[kM2lBatch][p + 1],
-  // slog[kM2lBatch], then bq[(p + 1) * p] = C(q + k - 1, k - 1), row q, k = 1..p
+  // slog[kM2lBatch], then bq[p * (p + 1)] = C(q + k - 1, k - 1) at (k - 1) (p + 1) + q, k = 1..p
+  // (consecutive q -- the threads of one set -- read consecutive words: no bank conflicts)
   extern __shared__ double2 dyn_m2l[];
-  double2 *sw = dyn_m2l, *stq = sw + kM2lBatch * np, *slog = stq + kM2lBatch * p1;
-  double *bq = reinterpret_cast<double *>(slog + kM2lBatch);
+  C *sw = reinterpret_cast<C *>(dyn_m2l), *stq = sw + kM2lBatch * np, *slog = stq + kM2lBatch * p1;
+  R *bq = reinterpret_cast<R *>(slog + kM2lBatch);
   for (int i = t; i < p1 * p; i += blockDim.x) {
-    const int qq = i / p, k = i - qq * p + 1;
-    bq[i] = c_binom[qq + k - 1][k - 1];
+    const int k1 = i / p1, qq = i - k1 * p1;  // k1 = k - 1
+    bq[i] = R(c_binom[qq + k1][k1]);
   }
-  double2 acc = make_double2(0.0, 0.0);
+  C acc = mkc<R>(0.0, 0.0);
   const int par = f.tcell_parent[cell];
   if (par >= 0) {  // L2L: stage the parent's locals and the powers of the offset
     const double2 cp = f.tcell_ctr[par];
     const double2 s = make_double2((ct.x - cp.x) * (0.5 * inv_h), (ct.y - cp.y) * (0.5 * inv_h));  // parent side 2h
-    for (int i = t; i < np; i += blockDim.x) sw[i] = f.Lc[size_t(par) * np + i];
-    if (t <= p) stq[t] = cpow(s, t);
+    for (int i = t; i < np; i += blockDim.x) sw[i] = Lc[size_t(par) * np + i];
+    if (t <= p) stq[t] = tocx<R>(cpow(s, t));
     __syncthreads();
     if (set < kSets) {
-      const double2 *b = sw + set * p1;
-      double2 v = make_double2(0.0, 0.0);
-      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(stq[k - q], c_binom[k][q]), v);
-      acc = cscale(v, ldexp(1.0, -q));
+      const C *b = sw + set * p1;
+      C v = mkc<R>(0.0, 0.0);
+      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(stq[k - q], R(c_binom[k][q])), v);
+      acc = cscale(v, R(ldexp(1.0, -q)));
     }
   }
   const int il0 = f.il_off[cell], ne = f.il_off[cell + 1] - il0;
@@ -264,53 +299,59 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       const bool tab = abs(dx) <= 3 && abs(dy) <= 3;
       const int ti = (dy + 3) * 7 + (dx + 3);
       // off the table (roots only) the offset is an integer pair as well: use it exactly
-      const double2 T = tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi);
-      const double2 a = f.M[size_t(sc) * np + r];
-      sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), (qi & 1) ? -1.0 : 1.0);
+      const C T = tocx<R>(tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi));
+      const C a = M[size_t(sc) * np + r];
+      sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
       if (si == 0) {
         stq[el * p1 + qi] = T;
         if (qi == 0)
-          slog[el] = tab ? f.tlog[ti]
-                         : make_double2(0.5 * log(double(dx) * dx + double(dy) * dy), atan2(-double(dy), -double(dx)));
+          slog[el] = tocx<R>(tab ? f.tlog[ti]
+                                 : make_double2(0.5 * log(double(dx) * dx + double(dy) * dy),
+                                                atan2(-double(dy), -double(dx))));
       }
     }
     __syncthreads();
     if (set < kSets) {
-      const double *B = bq + q * p;
+      const R *B = bq + q;
       for (int el = 0; el < nb; ++el) {
-        const double2 *w = sw + el * np + set * p1;
-        double vx = 0.0, vy = 0.0;
+        const C *w = sw + el * np + set * p1;
+        R vx = R(0), vy = R(0);
         for (int k = 1; k <= p; ++k) {
-          vx = fma(B[k - 1], w[k].x, vx);
-          vy = fma(B[k - 1], w[k].y, vy);
+          const R bk = B[(k - 1) * p1];
+          vx = fma(bk, w[k].x, vx);
+          vy = fma(bk, w[k].y, vy);
         }
         if (q == 0)
-          acc = cadd(acc, cadd(cmul(w[0], make_double2(slog[el].x + log_h, slog[el].y)),
-                               make_double2(vx, vy)));
+          acc = cadd(acc, cadd(cmul(w[0], mkc<R>(double(slog[el].x) + log_h, slog[el].y)),
+                               C{vx, vy}));
         else
-          acc = cfma(make_double2(fma(-w[0].x, inv_q, vx), fma(-w[0].y, inv_q, vy)), stq[el * p1 + q], acc);
+          acc = cfma(C{fma(-w[0].x, inv_q, vx), fma(-w[0].y, inv_q, vy)}, stq[el * p1 + q], acc);
       }
     }
   }
-  if (set < kSets) f.Lc[(size_t(cell) * kSets + set) * p1 + q] = acc;
+  if (set < kSets) Lc[(size_t(cell) * kSets + set) * p1 + q] = acc;
 }
 
 // L2P and the near field: one CTA per target leaf, one thread per target (strided).
+template <typename R>
 __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0, int leaf0,
                                                             double h) {
+  using C = cx<R>;
   const int leaf = blockIdx.x;
   const int cell = tcell0 + leaf;
   const double2 ct = f.tcell_ctr[cell];
   const int p = f.p, p1 = p + 1;
-  __shared__ double2 sb[kSets * (kMaxOrder + 1)];
+  const C *M = reinterpret_cast<const C *>(f.M);
+  const C *Lc = reinterpret_cast<const C *>(f.Lc);
+  __shared__ C sb[kSets * (kMaxOrder + 1)];
   __shared__ double2 qtot;
-  for (int i = threadIdx.x; i < kSets * p1; i += blockDim.x) sb[i] = f.Lc[size_t(cell) * kSets * p1 + i];
+  for (int i = threadIdx.x; i < kSets * p1; i += blockDim.x) sb[i] = Lc[size_t(cell) * kSets * p1 + i];
   if (threadIdx.x == 0) {  // stokeslet weight of all sources: the roots' a_0 of q1 and q2
     double2 s = make_double2(0.0, 0.0);
     for (int r = 0; r < f.n_roots_src; ++r) {
-      const double2 *a = f.M + size_t(f.root_src0 + r) * kSets * p1;
-      s.x += a[0].x;
-      s.y += a[p1].x;
+      const C *a = M + size_t(f.root_src0 + r) * kSets * p1;
+      s.x += double(a[0].x);
+      s.y += double(a[p1].x);
     }
     qtot = s;
   }
@@ -322,21 +363,21 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
     const int node = f.tgt_node[it];
     const double2 z = f.x[node];
     const int tcur = f.node_curve[node];
-    const double2 u = make_double2((z.x - ct.x) * inv_h, (z.y - ct.y) * inv_h);
+    const C u = mkc<R>((z.x - ct.x) * inv_h, (z.y - ct.y) * inv_h);
     // Horner: value, first and second derivative (in u) of every set
     double2 v[kSets], d1[kSets], d2[kSets];
 #pragma unroll
     for (int s = 0; s < kSets; ++s) {
-      const double2 *b = sb + s * p1;
-      double2 a0 = b[p], a1 = make_double2(0.0, 0.0), a2 = make_double2(0.0, 0.0);
+      const C *b = sb + s * p1;
+      C a0 = b[p], a1 = mkc<R>(0.0, 0.0), a2 = mkc<R>(0.0, 0.0);
       for (int k = p - 1; k >= 0; --k) {
         a2 = cfma(a2, u, a1);
         a1 = cfma(a1, u, a0);
         a0 = cfma(a0, u, b[k]);
       }
-      v[s] = a0;
-      d1[s] = cscale(a1, inv_h);
-      d2[s] = cscale(a2, 2.0 * inv_h * inv_h);
+      v[s] = to_d2(a0);
+      d1[s] = cscale(to_d2(a1), inv_h);
+      d2[s] = cscale(to_d2(a2), 2.0 * inv_h * inv_h);
     }
     // near field, directly (coincident pairs skipped); the near stokeslet weight is kept to
     // take it out of Q
@@ -492,6 +533,7 @@ struct stokes_fmm {
   int p = 20, L = 0, nx = 1, ny = 1, N = 0, n_src = 0;
   int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
   bool near32 = false;  // direct pairs (near field, own-curve removal) in FP32 arithmetic
+  bool fp32 = false;    // expansions (P2M, M2M, M2L, L2L, L2P) in FP32 arithmetic
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -1025,20 +1067,27 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   auto hl = [&](int l) { return f->S / double(1 << l); };
   const int nleaf_s = f->sc_off[L + 1] - f->sc_off[L];
   const int p1 = pe + 1, np = kSets * p1;
-  const size_t p2m_smem = sizeof(double2) * (kP2mChunk * p1 + kP2mChunk * kSets);
-  const size_t m2m_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(double) * pe * pe;
-  const size_t m2l_smem =
-      sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + sizeof(double) * p1 * pe;
-  if (nleaf_s > 0) p2m_kernel<<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
-  for (int l = L - 1; l >= 0; --l) {
-    const int nc = f->sc_off[l + 1] - f->sc_off[l];
-    if (nc > 0) m2m_kernel<<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
-  }
-  for (int l = 0; l <= L; ++l) {
-    const int nc = f->tc_off[l + 1] - f->tc_off[l];
-    if (nc > 0) m2l_kernel<<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
-  }
-  if (f->n_tleaf > 0) leaf_kernel<<<f->n_tleaf, kLeafThreads, 0, s>>>(d, f->tc_off[L], 0, hl(L));
+  const size_t cb = f->fp32 ? sizeof(float2) : sizeof(double2), rb = cb / 2;  // complex, real
+  const size_t p2m_smem = cb * (kP2mChunk * p1 + kP2mChunk * kSets);
+  const size_t m2m_smem = cb * (4 * np + 4 * p1) + rb * pe * pe;
+  const size_t m2l_smem = cb * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + rb * p1 * pe;
+  auto passes = [&](auto real) {
+    using R = decltype(real);
+    if (nleaf_s > 0) p2m_kernel<R><<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
+    for (int l = L - 1; l >= 0; --l) {
+      const int nc = f->sc_off[l + 1] - f->sc_off[l];
+      if (nc > 0) m2m_kernel<R><<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
+    }
+    for (int l = 0; l <= L; ++l) {
+      const int nc = f->tc_off[l + 1] - f->tc_off[l];
+      if (nc > 0) m2l_kernel<R><<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+    }
+    if (f->n_tleaf > 0) leaf_kernel<R><<<f->n_tleaf, kLeafThreads, 0, s>>>(d, f->tc_off[L], 0, hl(L));
+  };
+  if (f->fp32)
+    passes(0.0f);
+  else
+    passes(0.0);
   if (c->n_ves_curves > 0) {
     Binning bn;
     bn.x0 = f->x0;
@@ -1070,11 +1119,11 @@ int stokes_fmm_set_eval_order(stokes_fmm *f, int order) {
   return STOKES_OK;
 }
 
-int stokes_fmm_set_near_precision(stokes_fmm *f, int precision) {
+int stokes_fmm_set_precision(stokes_fmm *f, int precision) {
   if (!f) return STOKES_ERR_ARG;
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
-    return fmm_fail(f, STOKES_ERR_ARG, "near-field precision must be STOKES_FP64 or STOKES_FP32_KAHAN");
-  f->near32 = precision == STOKES_FP32_KAHAN;
+    return fmm_fail(f, STOKES_ERR_ARG, "evaluation precision must be STOKES_FP64 or STOKES_FP32_KAHAN");
+  f->near32 = f->fp32 = precision == STOKES_FP32_KAHAN;
   return STOKES_OK;
 }
 

@@ -1251,12 +1251,12 @@ int add_close(stokes_sim *m, const double2 *f, double2 *out) {
   return STOKES_OK;
 }
 
-// The vesicle sum of `dens` by the step's FMM plan at `order`, its direct pairs in FP64 or (for
-// the sweeps, whose expansions are no more accurate) in FP32.
-int fmm_sum(stokes_sim *m, int order, bool near32, const double2 *dens, double2 *out,
+// The vesicle sum of `dens` by the step's FMM plan at `order`, in FP64 or (for the low-order
+// sweeps, whose truncation error is ~1e-7 and above) in FP32.
+int fmm_sum(stokes_sim *m, int order, bool fp32, const double2 *dens, double2 *out,
             const char *what) {
   int st = stokes_fmm_set_eval_order(m->fmm_v, order);
-  if (!st) st = stokes_fmm_set_near_precision(m->fmm_v, near32 ? STOKES_FP32_KAHAN : STOKES_FP64);
+  if (!st) st = stokes_fmm_set_precision(m->fmm_v, fp32 ? STOKES_FP32_KAHAN : STOKES_FP64);
   if (!st)
     st = stokes_fmm_eval(m->fmm_v, reinterpret_cast<const double *>(dens), nullptr, 0.0,
                          reinterpret_cast<double *>(out), m->s);
@@ -1268,9 +1268,8 @@ int fmm_sum(stokes_sim *m, int order, bool near32, const double2 *dens, double2 
   return STOKES_OK;
 }
 
-// Sweep evaluations up to this order (truncation error ~1e-7 and above) take their direct pairs
-// in FP32.
-constexpr int kSweepNear32MaxOrder = 16;
+// Sweep evaluations up to this order (truncation error ~1e-7 and above) run in FP32.
+constexpr int kSweepFp32MaxOrder = 16;
 
 // z_out = A z_in (the operator of Eq. (tsteplinsys) at the current positions).  FP32-Kahan
 // sums are the sweeps' operator: with sweep_fmm_order set they come from the step's FMM plan
@@ -1280,7 +1279,7 @@ int step_matvec(stokes_sim *m, double dt, int precision, const double *zin, doub
                                              m->d_tmp2);
   SK(cudaGetLastError());
   if (precision == STOKES_FP32_KAHAN && m->sweep_fmm_order > 0 && m->fmm_v)
-    ST(fmm_sum(m, m->sweep_fmm_order, m->sweep_fmm_order <= kSweepNear32MaxOrder, m->d_tmp2,
+    ST(fmm_sum(m, m->sweep_fmm_order, m->sweep_fmm_order <= kSweepFp32MaxOrder, m->d_tmp2,
                m->d_tmp3, "FMM sweep"));
   else
     ST(stokes_sum_eval(m->ctx_v, precision, reinterpret_cast<const double *>(m->d_tmp2), nullptr,

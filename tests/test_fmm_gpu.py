@@ -151,35 +151,39 @@ def test_fmm_eval_order_truncates_the_plan(P):
         s.close()
 
 
-def test_fmm_fp32_near_field(P):
-    """FP32 arithmetic for the directly summed pairs (stokes_fmm_set_near_precision) moves an
-    order-14 evaluation by about the FP32 rounding of those pairs (~1e-7), far below its
-    truncation error (~2e-5 here): its error against the double-float direct sum stays within
-    10 % of the FP64-pair evaluation's, and switching back gives the FP64-pair result bit for
-    bit.  Other precisions are refused."""
+def test_fmm_fp32_evaluation(P):
+    """FP32 arithmetic for the expansions and the directly summed pairs
+    (stokes_fmm_set_precision) moves an order-14 evaluation by about FP32 rounding (~1e-6),
+    below its truncation error (~2e-5 here): its error against the double-float direct sum stays
+    within 10 % of the FP64 evaluation's (and at order 10 within 10 % as well), and switching
+    back gives the FP64 result bit for bit.  Other precisions are refused."""
     import torch
     g, slp, dlp = I.workload("mid_n16k")
     s = P.StokesSum(g)
     ts, td = dev(slp), dev(dlp)
     ref = s.eval(ts, td, precision="df").cpu().numpy()
-    f = P.stokes_fmm_create(s.h, 14, 32)
     out = torch.zeros((s.N, 2), dtype=torch.float64, device="cuda")
-    res = {}
-    try:
-        with pytest.raises(P.StokesError):
-            P.stokes_fmm_set_near_precision(f, P.STOKES_DOUBLE_FLOAT)
-        for prec in (P.STOKES_FP64, P.STOKES_FP32_KAHAN, P.STOKES_FP64):
-            P.stokes_fmm_set_near_precision(f, prec)
-            P.stokes_fmm_eval(f, ts, td, 0.0, out)
-            P.stokes_sync(s.h)
-            res.setdefault(prec, []).append(out.cpu().numpy())
-    finally:
-        P.stokes_fmm_destroy(f)
-        s.close()
-    e64, e32 = rel(res[P.STOKES_FP64][0], ref), rel(res[P.STOKES_FP32_KAHAN][0], ref)
-    print("order 14: FP64 pairs %.2e, FP32 pairs %.2e" % (e64, e32))
-    assert e64 < 1e-4 and abs(e32 - e64) <= 0.1 * e64 + 1e-6
-    assert np.array_equal(res[P.STOKES_FP64][0], res[P.STOKES_FP64][1])
+    errs = {}
+    for order in (10, 14):
+        f = P.stokes_fmm_create(s.h, order, 32)
+        res = {}
+        try:
+            with pytest.raises(P.StokesError):
+                P.stokes_fmm_set_precision(f, P.STOKES_DOUBLE_FLOAT)
+            for prec in (P.STOKES_FP64, P.STOKES_FP32_KAHAN, P.STOKES_FP64):
+                P.stokes_fmm_set_precision(f, prec)
+                P.stokes_fmm_eval(f, ts, td, 0.0, out)
+                P.stokes_sync(s.h)
+                res.setdefault(prec, []).append(out.cpu().numpy())
+        finally:
+            P.stokes_fmm_destroy(f)
+        e64, e32 = rel(res[P.STOKES_FP64][0], ref), rel(res[P.STOKES_FP32_KAHAN][0], ref)
+        errs[order] = (e64, e32)
+        assert np.array_equal(res[P.STOKES_FP64][0], res[P.STOKES_FP64][1])
+    s.close()
+    print("FMM FP64 / FP32 evaluation errors:", errs)
+    for order, (e64, e32) in errs.items():
+        assert e64 < 1e-3 and abs(e32 - e64) <= 0.1 * e64 + 2e-6, (order, e64, e32)
 
 
 def test_fmm_high_order_converges(P):
