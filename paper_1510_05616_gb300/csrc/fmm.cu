@@ -34,6 +34,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "df.cuh"
 #include "stokes_internal.cuh"
 
 namespace stokes {
@@ -248,7 +249,11 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
 // offset with |t_x|, |t_y| <= 3, whose powers and log(-t) come from the plan's table.  Source
 // cells are staged kM2lBatch at a time.
 constexpr int kM2lBatch = 4;
-template <typename R>
+// DF (FP64 evaluations): the binomial sums sum_k C(q + k - 1, k - 1) w_k -- the bulk of the
+// conversion work -- run in double-float arithmetic on the FP32 pipes (FP64 is the narrow
+// pipe on this chip) from FP64 weights split exactly into float pairs (~48-bit products and
+// sums, renormalised every 8 terms); the staging and the complex update stay FP64.
+template <typename R, bool DF = false>
 __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
@@ -263,12 +268,21 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   // dynamic shared memory (m2l_smem): sw[kM2lBatch][np], stq[kM2lBatch][p + 1],
   // slog[kM2lBatch], then bq[p * (p + 1)] = C(q + k - 1, k - 1) at (k - 1) (p + 1) + q, k = 1..p
   // (consecutive q -- the threads of one set -- read consecutive words: no bank conflicts)
+  // (with DF: then swf[kM2lBatch][np] the split weights (x.h, x.l, y.h, y.l), and bq holds the
+  // split binomials as float2 instead)
   extern __shared__ double2 dyn_m2l[];
   C *sw = reinterpret_cast<C *>(dyn_m2l), *stq = sw + kM2lBatch * np, *slog = stq + kM2lBatch * p1;
-  R *bq = reinterpret_cast<R *>(slog + kM2lBatch);
+  float4 *swf = reinterpret_cast<float4 *>(slog + kM2lBatch);
+  R *bq = reinterpret_cast<R *>(DF ? reinterpret_cast<C *>(swf + kM2lBatch * np) : slog + kM2lBatch);
+  float2 *bqf = reinterpret_cast<float2 *>(bq);
   for (int i = t; i < p1 * p; i += blockDim.x) {
     const int k1 = i / p1, qq = i - k1 * p1;  // k1 = k - 1
-    bq[i] = R(c_binom[qq + k1][k1]);
+    if constexpr (DF) {
+      const df b = split_df(c_binom[qq + k1][k1]);
+      bqf[i] = make_float2(b.h, b.l);
+    } else {
+      bq[i] = R(c_binom[qq + k1][k1]);
+    }
   }
   C acc = mkc<R>(0.0, 0.0);
   const int par = f.tcell_parent[cell];
@@ -301,7 +315,12 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       // off the table (roots only) the offset is an integer pair as well: use it exactly
       const C T = tocx<R>(tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi));
       const C a = M[size_t(sc) * np + r];
-      sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
+      const C wv = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
+      sw[el * np + r] = wv;
+      if constexpr (DF) {
+        const df wx = split_df(double(wv.x)), wy = split_df(double(wv.y));
+        swf[el * np + r] = make_float4(wx.h, wx.l, wy.h, wy.l);
+      }
       if (si == 0) {
         stq[el * p1 + qi] = T;
         if (qi == 0)
@@ -316,10 +335,28 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       for (int el = 0; el < nb; ++el) {
         const C *w = sw + el * np + set * p1;
         R vx = R(0), vy = R(0);
-        for (int k = 1; k <= p; ++k) {
-          const R bk = B[(k - 1) * p1];
-          vx = fma(bk, w[k].x, vx);
-          vy = fma(bk, w[k].y, vy);
+        if constexpr (DF) {
+          const float4 *wf = swf + el * np + set * p1;
+          const float2 *Bf = bqf + q;
+          df ax = {0.0f, 0.0f}, ay = {0.0f, 0.0f};
+          for (int k = 1; k <= p; ++k) {
+            const float2 b = Bf[(k - 1) * p1];
+            const float4 wk = wf[k];
+            df_mul_acc(ax, {b.x, b.y}, {wk.x, wk.y});
+            df_mul_acc(ay, {b.x, b.y}, {wk.z, wk.w});
+            if ((k & 7) == 0) {
+              df_renorm(ax);
+              df_renorm(ay);
+            }
+          }
+          vx = R(double(ax.h) + double(ax.l));
+          vy = R(double(ay.h) + double(ay.l));
+        } else {
+          for (int k = 1; k <= p; ++k) {
+            const R bk = B[(k - 1) * p1];
+            vx = fma(bk, w[k].x, vx);
+            vy = fma(bk, w[k].y, vy);
+          }
         }
         if (q == 0)
           acc = cadd(acc, cadd(cmul(w[0], mkc<R>(double(slog[el].x) + log_h, slog[el].y)),
@@ -534,6 +571,7 @@ struct stokes_fmm {
   int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
   bool near32 = false;  // direct pairs (near field, own-curve removal) in FP32 arithmetic
   bool fp32 = false;    // expansions (P2M, M2M, M2L, L2L, L2P) in FP32 arithmetic
+  bool m2l_df = true;   // FP64 evaluations: M2L binomial sums in double-float (FP32 pipes)
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -1071,6 +1109,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const size_t p2m_smem = cb * (kP2mChunk * p1 + kP2mChunk * kSets);
   const size_t m2m_smem = cb * (4 * np + 4 * p1) + rb * pe * pe;
   const size_t m2l_smem = cb * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + rb * p1 * pe;
+  const size_t m2l_df_smem = sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) +
+                             sizeof(float4) * kM2lBatch * np + sizeof(float2) * p1 * pe;
   auto passes = [&](auto real) {
     using R = decltype(real);
     if (nleaf_s > 0) p2m_kernel<R><<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
@@ -1080,7 +1120,11 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     }
     for (int l = 0; l <= L; ++l) {
       const int nc = f->tc_off[l + 1] - f->tc_off[l];
-      if (nc > 0) m2l_kernel<R><<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+      if (nc == 0) continue;
+      if (sizeof(R) == 8 && f->m2l_df)
+        m2l_kernel<double, true><<<nc, nthr, m2l_df_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+      else
+        m2l_kernel<R><<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
     }
     if (f->n_tleaf > 0) leaf_kernel<R><<<f->n_tleaf, kLeafThreads, 0, s>>>(d, f->tc_off[L], 0, hl(L));
   };

@@ -31,32 +31,16 @@
 // for both; the MUFU approximation and the logarithm's bit work and tables per target).
 #include <algorithm>
 
+#include "df.cuh"
 #include "stokes_internal.cuh"
 #include "bulk_pipe.cuh"
 
 namespace stokes {
 
 // ---------------------------------------------------------------------------
-// double-float primitives (the _rn intrinsics keep the compiler from contracting or
-// reassociating the error-free transformations)
+// double-float primitives beyond df.cuh's (the _rn intrinsics keep the compiler from
+// contracting or reassociating the error-free transformations)
 // ---------------------------------------------------------------------------
-struct df {
-  float h, l;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-
-// Exact when |a| >= |b| (or a == 0).
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
 // (a.h + a.l)(b.h + b.l) without the l*l term; unnormalised result.
 __device__ __forceinline__ df df_mul(df a, df b) {
   const float p = __fmul_rn(a.h, b.h);
@@ -92,27 +76,6 @@ __device__ __forceinline__ df df_rcp(df a) {
   float e = __fmaf_rn(-a.h, y0, 1.0f);
   e = __fmaf_rn(-a.l, y0, e);
   return {y0, __fmul_rn(y0, __fmaf_rn(e, e, e))};
-}
-
-// acc += a * b, acc a double-float accumulator.
-__device__ __forceinline__ void df_mul_acc(df &acc, df a, df b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  const df s = two_sum(acc.h, p);
-  acc.h = s.h;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
-}
-
-// Renormalise an accumulator so |l| <= ulp(h)/2: without it the low word collects every
-// rounding error of a long sum, grows like sqrt(n) ulp(h), and its own rounding then costs
-// ~2^-24 of that per addition.
-__device__ __forceinline__ void df_renorm(df &a) { a = fast_two_sum(a.h, a.l); }
-
-__device__ __forceinline__ df split_df(double v) {
-  const float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - double(h))};
 }
 
 // v = h + m + l on the grids g_h, g_m (powers of two): h and m are exact floats while

@@ -90,6 +90,7 @@ struct stokes_sim {
   double inner_tol = 1e-3;  // mixed-precision step: relative tolerance of each FP32-Kahan solve
   double *d_B = nullptr, *d_Q = nullptr;
   double *d_rv = nullptr, *d_rg = nullptr, *d_resv = nullptr, *d_resg = nullptr;
+  double *d_side_part = nullptr;       // [K][kSideChunks][4] partial side-point sums
   double *d_dtau = nullptr, *d_dc = nullptr, *d_g2 = nullptr;
   // preconditioner (per vesicle 3n x 3n) and GMRES workspace
   double *d_G = nullptr, *d_Ds = nullptr, *d_D2 = nullptr, *d_D4 = nullptr, *d_T = nullptr;
@@ -344,14 +345,18 @@ __global__ void transpose_kernel(int rows, int cols, const double *in, double *o
 
 // Data g of the response to vesicle forces (Eq. (vesgu), (vesgT)) at the side points; one
 // block per side point, fixed-order tree reduction over the vesicle nodes.
+// Side-point data: CTA (k, c) sums the vesicle nodes j = c 256 + t, + kSideChunks 256, ...
+// (thread t) for side pair k into part[k][c][4]; side_rhs_finish_kernel adds the chunks in
+// order.  kSideChunks CTAs per side pair spread the 2K x N_v pairs over the SMs.
+constexpr int kSideChunks = 32;
 __global__ void side_rhs_kernel(int K, int Nv, const double2 *side, const double2 *xv,
                                 const double *wv, const double2 *f, double d, double cmu,
-                                double p_drive, double *g) {
+                                double *part) {
   __shared__ double red[4][256];
-  const int k = blockIdx.x;
+  const int k = blockIdx.x, c = blockIdx.y;
   const double2 L = side[k], R = side[K + k];
   double acc[4] = {0, 0, 0, 0};
-  for (int j = threadIdx.x; j < Nv; j += blockDim.x) {
+  for (int j = c * blockDim.x + threadIdx.x; j < Nv; j += kSideChunks * blockDim.x) {
     const double qx = wv[j] * f[j].x, qy = wv[j] * f[j].y;
     double a[4], b[4];
     k_stokeslet(R.x - (xv[j].x - d), R.y - xv[j].y, cmu, a);
@@ -372,12 +377,20 @@ __global__ void side_rhs_kernel(int K, int Nv, const double2 *side, const double
       for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    g[2 * k] = red[0][0];
-    g[2 * k + 1] = red[1][0];
-    g[2 * K + 2 * k] = red[2][0] + p_drive;  // + p_drive n, n = (1, 0)
-    g[2 * K + 2 * k + 1] = red[3][0];
-  }
+  if (threadIdx.x < 4) part[(size_t(k) * kSideChunks + c) * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void side_rhs_finish_kernel(int K, const double *part, double p_drive, double *g) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double a[4] = {0, 0, 0, 0};
+  for (int c = 0; c < kSideChunks; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] += part[(size_t(k) * kSideChunks + c) * 4 + q];
+  g[2 * k] = a[0];
+  g[2 * k + 1] = a[1];
+  g[2 * K + 2 * k] = a[2] + p_drive;  // + p_drive n, n = (1, 0)
+  g[2 * K + 2 * k + 1] = a[3];
 }
 
 __global__ void empty_rhs_kernel(int K, double p_drive, double *g) {
@@ -1222,8 +1235,9 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   // v = -S^near f at the wall nodes (vesicle sums at free targets)
   ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
                              m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
-  side_rhs_kernel<<<m->K, 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w, f, m->period,
-                                          cmu, p_drive, m->d_rg);
+  side_rhs_kernel<<<dim3(m->K, kSideChunks), 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w,
+                                                            f, m->period, cmu, m->d_side_part);
+  side_rhs_finish_kernel<<<nb(m->K, 128), 128, 0, m->s>>>(m->K, m->d_side_part, p_drive, m->d_rg);
   // v = -(S^near f) at the walls
   axpby_kernel<<<nb(m->nA, 256), 256, 0, m->s>>>(m->nA, -1.0, m->d_vrhs, 0.0, m->d_rv);
   SK(cudaGetLastError());
@@ -1539,7 +1553,7 @@ void free_walls(stokes_sim *m) {
   dfree(m->d_vrhs);
   dfree(m->d_c);
   dfree(m->d_tau);
-  for (double **p : {&m->d_B, &m->d_Q, &m->d_rv, &m->d_rg, &m->d_resv, &m->d_resg, &m->d_dtau,
+  for (double **p : {&m->d_B, &m->d_Q, &m->d_rv, &m->d_rg, &m->d_side_part, &m->d_resv, &m->d_resg, &m->d_dtau,
                      &m->d_dc, &m->d_g2})
     dfree(*p);
   m->have_walls = false;
@@ -1799,6 +1813,7 @@ int stokes_sim_set_walls(stokes_sim *m, int n_per_wall, const double *nodes, con
   SK(dalloc(m->d_resv, nA));
   SK(dalloc(m->d_dtau, nA));
   SK(dalloc(m->d_rg, 4 * K));
+  SK(dalloc(m->d_side_part, size_t(4) * kSideChunks * K));
   SK(dalloc(m->d_resg, 4 * K));
   SK(dalloc(m->d_g2, 4 * K));
   SK(dalloc(m->d_dc, 2 * M));
