@@ -16,7 +16,10 @@
 // Q the sum of the stokeslet weights of the sources taken through the expansions.
 // Expansions (scaled by the cell side h): multipole a_0 log(z - c) + sum_k a_k h^k / (z - c)^k,
 // local sum_k b_k ((z - c)/h)^k, with the shift and conversion formulas of Greengard and
-// Rokhlin for the 2-D log kernel.  Tree: a forest of square roots of side S covering the
+// Rokhlin for the 2-D log kernel.  The conj(w)-weighted sets are taken relative to each
+// expansion's own centre c (conj(w - c) q, nu T conj(w - c)), re-centred exactly at every shift
+// and conversion, and the assembly uses z - c of the target leaf: the terms z conj(Phi'_q) and
+// conj(Phi'_wq) then no longer cancel from |z| |q| down to |q| (see recentred()).  Tree: a forest of square roots of side S covering the
 // sources (the nodes and their +-d images) and the targets, uniform depth L, Morton keys;
 // interaction lists are the children of the parent's neighbours that are not neighbours; the
 // 3 x 3 neighbour leaves are summed directly (coincident pairs skipped).  Pairs of a vesicle
@@ -96,11 +99,35 @@ template <typename R> __device__ __forceinline__ cx<R> tocx(double2 a) { return 
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
 
+// Coefficient r of the expansion stored at E + base (kSets sets of p1 coefficients) with the
+// sets 2 and 5 moved to a new centre.  Those two sets carry conj(w - c) q and nu T conj(w - c):
+// each expansion keeps them relative to its own centre c, which spares the assembly the
+// cancellation between z conj(Phi'_q) and conj(Phi'_wq) (terms of size |z| |q| whose
+// difference is |q|-sized), and moving the centre by dc = c_old - c_new adds conj(dc) times the
+// q (= q1 + i q2) or nu T expansion, coefficient by coefficient (the expansions are linear in
+// the charges).
+template <typename C>
+__device__ __forceinline__ C recentred(const C *E, size_t base, int r, int p1, double2 dc) {
+  const int si = r / p1, qi = r - si * p1;
+  C a = E[base + r];
+  if (si == 2 || si == 5) {
+    const C cdc = C{decltype(a.x)(dc.x), decltype(a.x)(-dc.y)};
+    C b;
+    if (si == 2) {
+      const C a0 = E[base + qi], a1 = E[base + p1 + qi];
+      b = C{a0.x - a1.y, a0.y + a1.x};  // a0 + i a1
+    } else {
+      b = E[base + 4 * p1 + qi];
+    }
+    a = cfma(cdc, b, a);
+  }
+  return a;
+}
+
 // The six charges of one (image) source at w: vesicle value (q1, q2, ., .), wall value
 // (T1, T2, n1, n2).
 __device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, double2 (&c)[kSets]) {
-  // w is taken relative to the forest's centre (as is z in the assembly): the terms
-  // z conj(Phi'_q) and conj(Phi'_wq) cancel to |q|-sized values, so small |z| keeps digits
+  // w is taken relative to the expansion's centre (the source leaf's); see recentred()
   if (!wall) {
     const double2 q = make_double2(v.x, v.y);
     c[0] = make_double2(v.x, 0.0);
@@ -138,7 +165,6 @@ struct FmmDev {
   double2 *Lc;                // [target cells][kSets][p + 1], likewise
   double2 *out;               // [N] pair sums (node order)
   int n_roots_src, root_src0; // source cells of level 0: [root_src0, root_src0 + n_roots_src)
-  double2 o;                  // origin of the complex coordinates (the forest's centre)
   const double2 *tpow;        // [49][tp1] t^-n of the integer offsets |t_x|, |t_y| <= 3
   const double2 *tlog;        // [49] log(-t) of the same offsets
   const int *src_own;         // [n_src] vesicle curve of an m = 0 source, else -1
@@ -171,7 +197,7 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
       const double2 w = f.src_pos[j0 + t];
       const C u = mkc<R>((w.x - ctr.x) / h, (w.y - ctr.y) / h);
       double2 c[kSets];
-      charges(sm.x < f.wall_slots, make_double2(w.x - f.o.x, w.y - f.o.y), f.val[sm.x], c);
+      charges(sm.x < f.wall_slots, make_double2(w.x - ctr.x, w.y - ctr.y), f.val[sm.x], c);
 #pragma unroll
       for (int s = 0; s < kSets; ++s) sc[t][s] = tocx<R>(c[s]);
       C uk = mkc<R>(1.0, 0.0);
@@ -214,7 +240,8 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
   }
   for (int i = t; i < nch * np; i += blockDim.x) {
     const int c = i / np, r = i - c * np;
-    sa[c * np + r] = M[size_t(ch.x + c) * np + r];
+    const double2 cc = f.scell_ctr[ch.x + c];
+    sa[c * np + r] = recentred(M, size_t(ch.x + c) * np, r, p1, make_double2(cc.x - ctr.x, cc.y - ctr.y));
   }
   for (int i = t; i < nch * p1; i += blockDim.x) {
     const int c = i / p1, n = i - c * p1;
@@ -289,7 +316,8 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   if (par >= 0) {  // L2L: stage the parent's locals and the powers of the offset
     const double2 cp = f.tcell_ctr[par];
     const double2 s = make_double2((ct.x - cp.x) * (0.5 * inv_h), (ct.y - cp.y) * (0.5 * inv_h));  // parent side 2h
-    for (int i = t; i < np; i += blockDim.x) sw[i] = Lc[size_t(par) * np + i];
+    for (int i = t; i < np; i += blockDim.x)
+      sw[i] = recentred(Lc, size_t(par) * np, i, p1, make_double2(cp.x - ct.x, cp.y - ct.y));
     if (t <= p) stq[t] = tocx<R>(cpow(s, t));
     __syncthreads();
     if (set < kSets) {
@@ -314,7 +342,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       const int ti = (dy + 3) * 7 + (dx + 3);
       // off the table (roots only) the offset is an integer pair as well: use it exactly
       const C T = tocx<R>(tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi));
-      const C a = M[size_t(sc) * np + r];
+      const C a = recentred(M, size_t(sc) * np, r, p1, make_double2(cs.x - ct.x, cs.y - ct.y));
       const C wv = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
       sw[el * np + r] = wv;
       if constexpr (DF) {
@@ -487,7 +515,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
     }
     // far field from the local expansion
     const double2 dq = make_double2(d1[0].x - d1[1].y, d1[0].y + d1[1].x);  // Phi'_q1 + i Phi'_q2
-    const double2 zo = make_double2(z.x - f.o.x, z.y - f.o.y);
+    const double2 zo = make_double2(z.x - ct.x, z.y - ct.y);  // sets 2 and 5 are centred at ct
     double2 s = make_double2(-v[0].x + 0.5 * (qtot.x - qn1), -v[1].x + 0.5 * (qtot.y - qn2));
     s = cadd(s, cscale(cadd(cmul(zo, cconj(dq)), cscale(cconj(d1[2]), -1.0)), 0.5));
     const double2 w5 = make_double2(d2[5].x, d2[5].y);
@@ -1095,7 +1123,6 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.out = c->d_partial;
   d.root_src0 = f->sc_off[0];
   d.n_roots_src = f->sc_off[1] - f->sc_off[0];
-  d.o = make_double2(f->x0 + 0.5 * f->nx * f->S, f->y0 + 0.5 * f->ny * f->S);
   d.tpow = f->d_tpow;
   d.tlog = f->d_tlog;
   d.src_own = f->d_src_own;

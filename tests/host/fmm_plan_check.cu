@@ -1,7 +1,9 @@
 // Host-logic check of the FMM (tests/test_host_logic.py): builds the plan of csrc/fmm.cu from a
 // geometry file, checks its invariants, emulates every pass on the CPU with the plan's arrays
-// (the same expansions and conversions) and writes the far + near sum for the test to compare
-// with a direct sum.  Usage: fmm_plan_check <case.bin> <order> <leaf> <out.bin>
+// (the same expansions and conversions, the conj(w)-weighted charge sets kept relative to each
+// expansion's centre and re-centred at every shift and conversion) and writes the far + near
+// sum for the test to compare with a direct sum.
+// Usage: fmm_plan_check <case.bin> <order> <leaf> <out.bin>
 #include "../../paper_1510_05616_gb300/csrc/fmm.cu"
 #include <complex>
 #include <cstdio>
@@ -92,10 +94,10 @@ int main(int argc, char **argv) {
   printf("invariant violations: %d\n", bad);
   // ---- emulated passes
   const int p1 = p + 1;
-  const cd O(ph.x0 + 0.5 * ph.nx * ph.S, ph.y0 + 0.5 * ph.ny * ph.S);
-  auto charges_h = [&](int j, cd (&c)[kSets]) {
+  // charges of source j with the conj(w)-weighted sets 2 and 5 relative to the centre ctr
+  auto charges_h = [&](int j, cd ctr, cd (&c)[kSets]) {
     const int s = ph.src_sorted[j].x;
-    const cd w = cd(ph.pos_sorted[j].x, ph.pos_sorted[j].y) - O;
+    const cd w = cd(ph.pos_sorted[j].x, ph.pos_sorted[j].y) - ctr;
     const double *v = &sval[4 * s];
     for (auto &q : c) q = 0;
     if (s >= wall_slots) {
@@ -107,12 +109,22 @@ int main(int argc, char **argv) {
     }
   };
   auto hl = [&](int l) { return ph.S / double(1 << l); };
+  // the kSets x p1 coefficients at e, sets 2 and 5 moved from their centre by dc = old - new:
+  // they gain conj(dc) times the q = q1 + i q2 (set 2) or nu T (set 5) coefficients
+  auto recentre = [&](const cd *e, cd dc, std::vector<cd> &out) {
+    out.assign(e, e + kSets * p1);
+    for (int k = 0; k <= p; ++k) {
+      out[2 * p1 + k] += std::conj(dc) * (e[k] + cd(0, 1) * e[p1 + k]);
+      out[5 * p1 + k] += std::conj(dc) * e[4 * p1 + k];
+    }
+  };
+  std::vector<cd> rc;
   std::vector<cd> M(size_t(nsc) * kSets * p1, 0.0), Lc(size_t(ntc) * kSets * p1, 0.0);
   for (int i = ph.sc_off[L]; i < nsc; ++i) {
     const cd ctr(ph.sc_ctr[i].x, ph.sc_ctr[i].y);
     for (int j = ph.sc_rng[i].x; j < ph.sc_rng[i].y; ++j) {
       cd c[kSets];
-      charges_h(j, c);
+      charges_h(j, ctr, c);
       const cd u = (cd(ph.pos_sorted[j].x, ph.pos_sorted[j].y) - ctr) / hl(L);
       for (int s = 0; s < kSets; ++s) {
         M[(size_t(i) * kSets + s) * p1] += c[s];
@@ -125,9 +137,11 @@ int main(int argc, char **argv) {
     for (int i = ph.sc_off[l]; i < ph.sc_off[l + 1]; ++i) {
       const cd c0(ph.sc_ctr[i].x, ph.sc_ctr[i].y);
       for (int ch = ph.sc_rng[i].x; ch < ph.sc_rng[i].y; ++ch) {
-        const cd s = (cd(ph.sc_ctr[ch].x, ph.sc_ctr[ch].y) - c0) / hl(l);
+        const cd cc(ph.sc_ctr[ch].x, ph.sc_ctr[ch].y);
+        const cd s = (cc - c0) / hl(l);
+        recentre(&M[size_t(ch) * kSets * p1], cc - c0, rc);
         for (int st = 0; st < kSets; ++st) {
-          const cd *a = &M[(size_t(ch) * kSets + st) * p1];
+          const cd *a = &rc[size_t(st) * p1];
           cd *b = &M[(size_t(i) * kSets + st) * p1];
           b[0] += a[0];
           for (int q = 1; q <= p; ++q) {
@@ -146,8 +160,10 @@ int main(int argc, char **argv) {
         cd *b = &Lc[(size_t(i) * kSets + st) * p1];
         if (ph.tc_par[i] >= 0) {
           const int pr = ph.tc_par[i];
-          const cd s = (ct - cd(ph.tc_ctr[pr].x, ph.tc_ctr[pr].y)) / (2 * h);
-          const cd *pb = &Lc[(size_t(pr) * kSets + st) * p1];
+          const cd cp(ph.tc_ctr[pr].x, ph.tc_ctr[pr].y);
+          const cd s = (ct - cp) / (2 * h);
+          recentre(&Lc[size_t(pr) * kSets * p1], cp - ct, rc);
+          const cd *pb = &rc[size_t(st) * p1];
           for (int q = 0; q <= p; ++q) {
             cd acc = 0;
             for (int k = q; k <= p; ++k) acc += pb[k] * binom(k, q) * std::pow(s, k - q);
@@ -156,8 +172,10 @@ int main(int argc, char **argv) {
         }
         for (int e = ph.il_off[i]; e < ph.il_off[i + 1]; ++e) {
           const int sc = ph.il_idx[e];
-          const cd t = (cd(ph.sc_ctr[sc].x, ph.sc_ctr[sc].y) - ct) / h;
-          const cd *a = &M[(size_t(sc) * kSets + st) * p1];
+          const cd cs(ph.sc_ctr[sc].x, ph.sc_ctr[sc].y);
+          const cd t = (cs - ct) / h;
+          recentre(&M[size_t(sc) * kSets * p1], cs - ct, rc);
+          const cd *a = &rc[size_t(st) * p1];
           b[0] += a[0] * (std::log(-t) + std::log(h));
           for (int k = 1; k <= p; ++k) b[0] += a[k] * (k & 1 ? -1.0 : 1.0) / std::pow(t, k);
           for (int q = 1; q <= p; ++q) {
@@ -208,7 +226,7 @@ int main(int argc, char **argv) {
           }
         }
       const cd dq = d1[0] + cd(0, 1) * d1[1];
-      const cd zo = z - O;
+      const cd zo = z - ct;  // sets 2 and 5 are centred at the leaf's centre
       cd s = cd(-v[0].real(), -v[1].real()) + 0.5 * (qtot - qn) + 0.5 * (zo * std::conj(dq) - std::conj(d1[2]));
       s += 0.25 * (d1[4] + std::conj(d1[3]) + std::conj(d2[5] - std::conj(zo) * d2[4]));
       uf[node] = s + near;
