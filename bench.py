@@ -743,10 +743,15 @@ def run_fmm(args):
         return statistics.median(ts)
 
     rows = {}
+    orders = [("fp64", int(o)) for o in args.fmm_orders.split(",") if o] + \
+             [("fp32", int(o)) for o in args.fmm_fp32_orders.split(",") if o]
     for name in args.fmm_workloads.split(","):
         g, slp, dlp = I.workload(name)
+        if args.fmm_vesicles_only:  # the step's vesicle sums: vesicle curves only
+            ves = [c for c in g.curves if c.kind == I.KIND_SLP]  # slp rows are the vesicle nodes
+            g, dlp = I.Geometry(ves, g.period, g.mu, dict(g.meta)), None
         s = P.StokesSum(g)
-        ts, td = dev(slp), dev(dlp)
+        ts, td = dev(slp), (dev(dlp) if dlp is not None else None)
         N = g.n_nodes
         pairs = 3.0 * N * N
         out = torch.zeros((N, 2), dtype=torch.float64, device="cuda")
@@ -759,24 +764,27 @@ def run_fmm(args):
             r["direct_" + prec] = {"ms": ms, "gpair_per_s": pairs / ms / 1e6}
             if prec == "df":
                 ref = out.cpu().numpy().copy()
-        for order in (20, 28):
+        for arith, order in orders:
             t0 = time.perf_counter()
             f = P.stokes_fmm_create(s.h, order, args.fmm_leaf)
             plan_ms = 1e3 * (time.perf_counter() - t0)
+            P.stokes_fmm_set_precision(f, P.STOKES_FP32_KAHAN if arith == "fp32" else P.STOKES_FP64)
 
             def call():
                 P.stokes_fmm_eval(f, ts, td, 0.0, out)
                 P.stokes_sync(s.h)
-            if order == 20:  # a profiler started with --profile-from-start off sees these calls
+            first = (arith, order) == orders[0]
+            if first:  # a profiler started with --profile-from-start off sees these calls
                 torch.cuda.profiler.start()
             ms = timed(call, 5)
-            if order == 20:
+            if first:
                 torch.cuda.profiler.stop()
             u = out.cpu().numpy()
             err = float((np.abs(u - ref).max(0) / np.abs(ref).max(0)).max())
             info = P.stokes_fmm_get_info(f)
             P.stokes_fmm_destroy(f)
-            r["fmm_p%d" % order] = {"ms": ms, "equiv_gpair_per_s": pairs / ms / 1e6, "plan_ms": plan_ms,
+            r["fmm_p%d" % order + ("_fp32" if arith == "fp32" else "")] = {
+                                    "ms": ms, "equiv_gpair_per_s": pairs / ms / 1e6, "plan_ms": plan_ms,
                                     "rel_err_vs_df": err, "levels": info["levels"],
                                     "m2l_pairs": info["m2l_pairs"], "near_pairs": info["near_pairs"]}
         s.close()
@@ -784,6 +792,7 @@ def run_fmm(args):
     line = {"metric": "node evaluation of the layer-potential sum: FMM (FP64 expansions) vs direct",
             "unit": "ms per evaluation", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
             "config": {"workloads": {k: WORKLOAD_DESCS.get(k, k) for k in rows},
+                       "vesicles_only": bool(args.fmm_vesicles_only),
                        "leaf_size": args.fmm_leaf, "direct_shapes": "default (not autotuned)"},
             "results": rows}
     print(json.dumps(line))
@@ -877,6 +886,10 @@ def main():
                     help="fast multipole node evaluation vs the direct sums, N = 1,280 .. 524,288")
     ap.add_argument("--fmm-workloads", default="small_n1280,mid_n16k,paper_n128k,large_n512k")
     ap.add_argument("--fmm-leaf", type=int, default=32)
+    ap.add_argument("--fmm-orders", default="20,28", help="--fmm: FP64 evaluation orders")
+    ap.add_argument("--fmm-fp32-orders", default="", help="--fmm: FP32 evaluation orders")
+    ap.add_argument("--fmm-vesicles-only", action="store_true",
+                    help="--fmm: the vesicle curves of each workload only (the step's vesicle sums)")
     ap.add_argument("--walls", action="store_true",
                     help="wall solvers: fast direct solver vs dense LU32 at a channel's walls")
     ap.add_argument("--walls-nodes", type=int, default=16384)
