@@ -375,11 +375,13 @@ def run_step(args):
     nm_max = max(nets_modes)
     fmm = args.residual_fmm
     sweep = args.sweep_fmm
+    refresh = args.precond_refresh
     hist = not args.no_warm_history
     res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10,
            "precisions": precs, "collect_precision": args.collect_precision or
            ("fp32k" if big else "fp64"), "warm_modes": nets_modes,
-           "residual_fmm_order": fmm, "sweep_fmm_order": sweep, "history_features": hist}
+           "residual_fmm_order": fmm, "sweep_fmm_order": sweep, "precond_refresh": refresh,
+           "history_features": hist}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
@@ -387,7 +389,7 @@ def run_step(args):
         torch.cuda.synchronize()
         ts = time.perf_counter()
         sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm,
-                            history=hist, sweep_fmm=sweep)
+                            history=hist, sweep_fmm=sweep, precond_refresh=refresh)
         torch.cuda.synchronize()
         res.setdefault("setup_s", time.perf_counter() - ts)
         res.setdefault("wall_solve", dict(zip(("refinements", "residual"),
@@ -416,7 +418,7 @@ def run_step(args):
     del X, T, Xs, Ts
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
     sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm, history=hist,
-                        sweep_fmm=sweep)
+                        sweep_fmm=sweep, precond_refresh=refresh)
     x0, s0, _ = sim.state()
     evs = {}
     for p in precs:
@@ -450,7 +452,7 @@ def run_step(args):
                        "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w,
                        "training_states": int(res["train"][nets_modes[0]]["samples"]),
                        "warm_modes": nets_modes, "residual_fmm_order": fmm,
-                       "sweep_fmm_order": sweep},
+                       "sweep_fmm_order": sweep, "precond_refresh": refresh},
             "iterations_saved_vs_zero": {p: {k: ev["zero"]["mean_iterations"] - v["mean_iterations"]
                                              for k, v in ev.items()} for p, ev in evs.items()},
             "by_precision": {p: summary(ev) for p, ev in evs.items()},
@@ -916,6 +918,9 @@ def main():
     ap.add_argument("--close-factor", type=float, default=5.0)
     ap.add_argument("--no-warm-history", action="store_true",
                     help="warm-start features without the previous solution and its last change")
+    ap.add_argument("--precond-refresh", action="store_true",
+                    help="--step: refresh the preconditioner inverse by Newton-Schulz from the "
+                         "previous step's instead of factorising every step")
     ap.add_argument("--sweep-fmm", type=int, default=0,
                     help="--step, fp32k: the Krylov sweeps' vesicle sums by the step's FMM plan at "
                          "this order (0: FP32-Kahan direct sums)")

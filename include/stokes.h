@@ -637,6 +637,8 @@ typedef struct {
     int accurate_residuals; /* FP64-accurate residuals of those sweeps (double-float or FMM) */
     double fmm_plan_ms;  /* host time of this step's FMM plan (residual FMM on), else 0; it
                             runs on a host thread beside the GPU's work                  */
+    int precond_refresh; /* Newton-Schulz products of the preconditioner refresh
+                            (stokes_sim_set_precond_refresh); 0: the blocks were factorised */
 } stokes_step_stats;
 
 STOKES_API int stokes_sim_create(int device, stokes_sim **out);
@@ -687,6 +689,18 @@ STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
  * products and sums, so it is still one fixed linear operator and GMRES's FP64 tolerance is
  * unaffected) or STOKES_FP64.  Only the iteration counts can differ. */
 STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
+/* Refresh of the FP32 preconditioner inverse (on = 1; default 0 = factorise every step): the
+ * blocks move little in one step, so the previous step's inverse X is kept when
+ * ||I - P X||_F <= 1e-3 on every block, or updated by up to three Newton-Schulz iterations
+ * X <- X (2I - P X) (a batched SGEMM each, plus one for the check; the error squaring) while
+ * it starts at most 0.5 and is seen to square (the result within ~1e-2 at worst); otherwise the
+ * blocks are factorised as usual.  The refreshed inverse is
+ * a fixed operator within the step, so GMRES's tolerance is unaffected; iteration counts can
+ * differ slightly.  The first step, a new dt, stokes_sim_set_state and a precision change
+ * factorise.  Steps then depend on the previous steps' preconditioners, so a resumed run
+ * (stokes_sim_set_state) matches an uninterrupted one to the step tolerance, not bit for bit.
+ * STOKES_ERR_ARG for on outside {0, 1}. */
+STOKES_API int stokes_sim_set_precond_refresh(stokes_sim *sim, int on);
 /* Relative tolerance of each inner FP32-Kahan GMRES solve of a STOKES_FP32_KAHAN step
  * (1e-8..0.5, default 1e-3); the outer FP64-accurate refinement still ends at `tol`. */
 STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);

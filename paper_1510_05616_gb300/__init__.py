@@ -112,6 +112,7 @@ _SIGNATURES = {
     "stokes_sim_set_wall_solver": [_vp, _c_int],
     "stokes_sim_set_block_refinement": [_vp, _c_int],
     "stokes_sim_set_precond_precision": [_vp, _c_int],
+    "stokes_sim_set_precond_refresh": [_vp, _c_int],
     "stokes_sim_set_inner_tolerance": [_vp, _c_double],
     "stokes_sim_set_residual_fmm": [_vp, _c_int, _c_int],
     "stokes_sim_set_sweep_fmm": [_vp, _c_int],
@@ -600,7 +601,8 @@ def stokes_tune_clear():
 class StepStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("residual", _c_double), ("setup_ms", _c_double),
                 ("gmres_ms", _c_double), ("total_ms", _c_double), ("refinements", _c_int),
-                ("accurate_residuals", _c_int), ("fmm_plan_ms", _c_double)]
+                ("accurate_residuals", _c_int), ("fmm_plan_ms", _c_double),
+                ("precond_refresh", _c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -727,6 +729,11 @@ def stokes_sim_fds_info(h):
 
 def stokes_sim_set_block_refinement(h, sweeps):
     return _sim_check(h, load().stokes_sim_set_block_refinement(h, int(sweeps)))
+
+
+def stokes_sim_set_precond_refresh(h, on=True):
+    """Newton-Schulz refresh of the FP32 preconditioner inverse from the previous step's."""
+    return _sim_check(h, load().stokes_sim_set_precond_refresh(h, int(on)))
 
 
 def stokes_sim_set_precond_precision(h, precision):

@@ -101,6 +101,15 @@ struct stokes_sim {
   int precond_fp32 = 1;
   float *d_P32 = nullptr, *d_Pinv32 = nullptr;
   float **d_Pptr32 = nullptr, **d_Piptr32 = nullptr;
+  // Newton-Schulz refresh of the FP32 inverse from the previous step's (opt-in): workspace, the
+  // largest per-vesicle ||I - P X||_F (device), whether d_Pinv32 holds an inverse for the
+  // current dt, the dt it was made for, and the last step's refresh count (0: LU)
+  bool precond_refresh = false;
+  float *d_T32 = nullptr, *d_X32 = nullptr;
+  unsigned *d_enorm = nullptr;
+  bool pinv_valid = false;
+  double pinv_dt = 0.0;
+  int last_refresh = 0;
   int *d_ppiv = nullptr, *d_pinfo = nullptr;
   int gm_m = 0;
   double *d_V = nullptr, *d_z = nullptr, *d_b = nullptr, *d_wk = nullptr, *d_h = nullptr;
@@ -1026,6 +1035,29 @@ __global__ void precond32_apply_kernel(int k, const float *Pinv, const double *z
   }
 }
 
+// Newton-Schulz step of the preconditioner inverse: T = P X (per vesicle, k x k) is replaced in
+// place by W = 2I - T = I + E with E = I - T, and the largest per-vesicle ||E||_F goes to *enorm
+// (the bits of a non-negative float order as unsigned integers).  A CTA per vesicle.
+__global__ void ns_prepare_kernel(int k, float *T, unsigned *enorm) {
+  __shared__ float red[256];
+  const size_t kk = size_t(k) * k;
+  float *Tv = T + size_t(blockIdx.x) * kk;
+  float acc = 0.0f;
+  for (size_t i = threadIdx.x; i < kk; i += blockDim.x) {
+    const float d = (i % size_t(k + 1)) == 0 ? 1.0f : 0.0f;
+    const float e = d - Tv[i];
+    acc = fmaf(e, e, acc);
+    Tv[i] = d + e;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(enorm, __float_as_uint(sqrtf(red[0])));
+}
+
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
@@ -1410,6 +1442,51 @@ int precond_assemble(stokes_sim *m, double dt, F *G, F *Ds, F *D2, F *D4, F *T, 
   return STOKES_OK;
 }
 
+// Newton-Schulz refresh of X = d_Pinv32 toward P^-1 (P = d_P32): X <- X (2I - P X), whose
+// error E = I - P X squares at every update.  The previous step's inverse is kept as it stands
+// when its ||E||_F (largest over the vesicles) is at most kNsDone, else updated at most three
+// times while the error starts at most kNsLimit[0] and is seen to shrink like a square
+// (kNsLimit[it] before update it), so the result is within kNsLimit[2]^2 ~ 1e-2 at worst: a fixed
+// operator as close to P^-1 as the preconditioner needs.  Otherwise *done stays false and the
+// caller factorises.  m->last_refresh counts the products P X evaluated.  (Measured at the paper
+// channel: a start of 1 with four updates refreshes from a few steps earlier in a fresh run but
+// costs one more update on every later step.)
+constexpr float kNsDone = 1e-3f;
+constexpr int kNsUpdates = 3;
+constexpr float kNsLimit[kNsUpdates] = {0.5f, 0.3f, 0.1f};
+int precond_refresh_ns(stokes_sim *m, bool *done) {
+  const int V = m->V, k = 3 * m->n;
+  const long long kk = (long long)k * k;
+  const float one = 1.0f, zero = 0.0f;
+  *done = false;
+  for (int it = 0; it < kNsUpdates; ++it) {
+    BK(cublasSgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, m->d_P32, k, kk,
+                                 m->d_Pinv32, k, kk, &zero, m->d_T32, k, kk, V));
+    SK(cudaMemsetAsync(m->d_enorm, 0, sizeof(unsigned), m->s));
+    ns_prepare_kernel<<<V, 256, 0, m->s>>>(k, m->d_T32, m->d_enorm);
+    SK(cudaGetLastError());
+    unsigned hb = 0;
+    SK(cudaMemcpyAsync(&hb, m->d_enorm, sizeof(unsigned), cudaMemcpyDeviceToHost, m->s));
+    SK(cudaStreamSynchronize(m->s));
+    float en;
+    memcpy(&en, &hb, sizeof(en));
+    m->last_refresh = it + 1;
+    if (en <= kNsDone) {  // accurate as it stands
+      *done = true;
+      return STOKES_OK;
+    }
+    if (!(en <= kNsLimit[it])) {  // too far, or not squaring
+      *done = false;
+      return STOKES_OK;
+    }
+    BK(cublasSgemmStridedBatched(m->blas, CUBLAS_OP_N, CUBLAS_OP_N, k, k, k, &one, m->d_Pinv32, k, kk,
+                                 m->d_T32, k, kk, &zero, m->d_X32, k, kk, V));
+    SK(cudaMemcpyAsync(m->d_Pinv32, m->d_X32, sizeof(float) * size_t(kk) * V, cudaMemcpyDeviceToDevice, m->s));
+    *done = true;
+  }
+  return STOKES_OK;
+}
+
 int precond_build(stokes_sim *m, double dt) {
   const int n = m->n, V = m->V, k = 3 * n;
   if (m->precond_fp32) {
@@ -1417,8 +1494,21 @@ int precond_build(stokes_sim *m, double dt) {
     ST(precond_assemble<float>(m, dt, reinterpret_cast<float *>(m->d_G), reinterpret_cast<float *>(m->d_Ds),
                                reinterpret_cast<float *>(m->d_D2), reinterpret_cast<float *>(m->d_D4),
                                reinterpret_cast<float *>(m->d_T), m->d_P32));
+    m->last_refresh = 0;
+    if (m->precond_refresh && m->pinv_valid && m->pinv_dt == dt) {
+      if (!m->d_T32) {
+        SK(dalloc(m->d_T32, size_t(k) * k * V));
+        SK(dalloc(m->d_X32, size_t(k) * k * V));
+        SK(dalloc(m->d_enorm, 1));
+      }
+      bool done = false;
+      ST(precond_refresh_ns(m, &done));
+      if (done) return STOKES_OK;
+    }
     BK(cublasSgetrfBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_pinfo, V));
     BK(cublasSgetriBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_Piptr32, k, m->d_pinfo, V));
+    m->pinv_valid = true;
+    m->pinv_dt = dt;
     return STOKES_OK;
   }
   ST(precond_assemble<double>(m, dt, m->d_G, m->d_Ds, m->d_D2, m->d_D4, m->d_T, m->d_P));
@@ -1585,6 +1675,10 @@ void free_vesicles(stokes_sim *m) {
   dfree(m->d_Pinv32);
   dfree(m->d_Pptr32);
   dfree(m->d_Piptr32);
+  dfree(m->d_T32);
+  dfree(m->d_X32);
+  dfree(m->d_enorm);
+  m->pinv_valid = false;
   dfree(m->d_ppiv);
   dfree(m->d_pinfo);
   m->have_ves = false;
@@ -1995,6 +2089,14 @@ int stokes_sim_set_precond_precision(stokes_sim *m, int precision) {
   if (precision != STOKES_FP64 && precision != STOKES_FP32_KAHAN)
     return fail(m, STOKES_ERR_ARG, "preconditioner precision must be STOKES_FP64 or STOKES_FP32_KAHAN");
   m->precond_fp32 = precision == STOKES_FP32_KAHAN;
+  m->pinv_valid = false;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_precond_refresh(stokes_sim *m, int on) {
+  if (!m) return STOKES_ERR_ARG;
+  if (on != 0 && on != 1) return fail(m, STOKES_ERR_ARG, "refresh must be 0 or 1");
+  m->precond_refresh = on == 1;
   return STOKES_OK;
 }
 
@@ -2266,6 +2368,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     out->refinements = refinements;
     out->accurate_residuals = accurate;
     out->fmm_plan_ms = plan_ms;
+    out->precond_refresh = m->last_refresh;
   }
   if (gst) return gst;
   if (n >= m->warm_modes) {
@@ -2322,7 +2425,8 @@ int stokes_sim_set_state(stokes_sim *m, const double *x_host, const double *sigm
   SK(cudaSetDevice(m->device));
   if (x_host) SK(cudaMemcpy(m->d_x, x_host, sizeof(double2) * m->Nv, cudaMemcpyHostToDevice));
   if (sigma_host) SK(cudaMemcpy(m->d_sigma, sigma_host, sizeof(double) * m->Nv, cudaMemcpyHostToDevice));
-  // a new start: no previous step
+  // a new start: no previous step (nor its preconditioner)
+  m->pinv_valid = false;
   SK(cudaMemset(m->d_bprev, 0, sizeof(double) * 3 * m->Nv));
   SK(cudaMemset(m->d_zprev, 0, sizeof(double) * 3 * m->Nv));
   SK(cudaMemset(m->d_zprev2, 0, sizeof(double) * 3 * m->Nv));

@@ -257,6 +257,39 @@ def test_fmm_sweep_step_matches_direct_sweep_step(P, resid):
     b.close()
 
 
+def test_precond_refresh_step_matches_factorised_step(P):
+    """Mixed-precision steps on the 16k channel whose preconditioner inverse is refreshed from the
+    previous step's by Newton-Schulz (stokes_sim_set_precond_refresh) end on the same
+    FP64-accurate residual bound at the same solution as the steps that factorise every block:
+    solutions to 1e-8, positions to 1e-10; the first step factorises, later ones refresh."""
+    from paper_1510_05616_gb300 import warmstart as WS
+    g = I.workload("mid_n16k")[0]
+    dt, pd, kb = 1e-3, 2 * 2 * PI * 0.2, 0.01
+    a = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=36)
+    b = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=36, precond_refresh=True)
+    refreshed = []
+    for k in range(4):
+        sa = a.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        sb = b.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
+        assert sa["residual"] <= 1e-10 and sb["residual"] <= 1e-10
+        assert sa["precond_refresh"] == 0
+        refreshed.append(sb["precond_refresh"])
+        xa, siga, za = a.state()
+        xb, sigb, zb = b.state()
+        ez = np.abs(za - zb).max() / np.abs(za).max()
+        ex = np.abs(xa - xb).max()
+        print("step %d: refresh products %d; solution %.2e, positions %.2e; its %d / %d"
+              % (k, sb["precond_refresh"], ez, ex, sa["iterations"], sb["iterations"]))
+        assert ez <= 1e-8 and ex <= 1e-10
+    assert refreshed[0] == 0 and all(r > 0 for r in refreshed[1:]), refreshed
+    h = P.stokes_sim_create(0)
+    with pytest.raises(P.StokesError):
+        P.stokes_sim_set_precond_refresh(h, 2)
+    P.stokes_sim_destroy(h)
+    a.close()
+    b.close()
+
+
 def test_residual_fmm_and_warm_modes_arguments(P):
     h = P.stokes_sim_create(0)
     for bad in ((3, 32), (41, 32), (20, 2)):
