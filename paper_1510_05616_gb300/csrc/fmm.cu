@@ -169,6 +169,8 @@ struct FmmDev {
   const double2 *tlog;        // [49] log(-t) of the same offsets
   const int *src_own;         // [n_src] vesicle curve of an m = 0 source, else -1
   const int *node_curve;      // [N] vesicle curve of a node, else -1
+  const float4 *m2m_df;       // M2M shift weights per child quadrant (double-float), plan order
+  int mp;                     // the plan's order (row stride of m2m_df: mp + 1, block: mp rows)
 };
 
 // P2M: one CTA per source leaf; thread (set, k).  Sources are staged 32 at a time with their
@@ -216,7 +218,10 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
 // M2M: one CTA per source cell of a level above the leaves; thread (set, q).  The children's
 // coefficients, the powers of their offsets and the binomials are staged in shared memory:
 // a'_q += -a_0 s^q / q + sum_{k <= q} a_k 2^-k s^(q-k) C(q - 1, k - 1), s = (c_child - c) / h.
-template <typename R>
+// DF (FP64 evaluations): the shift sums sum_k a_k s^(q-k) C(q - 1, k - 1) 2^-k in double-float
+// on the FP32 pipes, the weights from the plan's table of the four child quadrants, the
+// children's coefficients split exactly into float pairs; the a_0 term stays FP64.
+template <typename R, bool DF = false>
 __global__ void m2m_kernel(FmmDev f, int cell0) {
   using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
@@ -231,17 +236,33 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
   // dynamic shared memory (m2m_smem): sa[4][np], sp[4][p + 1], then
   // bm[p * p] = C(q - 1, k - 1) 2^-k at (k - 1) p + q - 1, k = 1..p (consecutive q, consecutive
   // words)
+  // (with DF: saf[4][np] the children's coefficients split (re.h, re.l, im.h, im.l) in place
+  // of bm, and the quadrant of every child)
   extern __shared__ double2 dyn_m2m[];
   C *sa = reinterpret_cast<C *>(dyn_m2m), *sp = sa + 4 * np;
   R *bm = reinterpret_cast<R *>(sp + 4 * p1);
-  for (int i = t; i < p * p; i += blockDim.x) {
-    const int k1 = i / p, qq = i - k1 * p;  // k1 = k - 1, qq = q - 1
-    bm[i] = R(c_binom[qq][k1] * ldexp(1.0, -(k1 + 1)));
+  float4 *saf = reinterpret_cast<float4 *>(sp + 4 * p1);
+  __shared__ int quad[4];
+  if constexpr (DF) {
+    if (t < nch) {
+      const double2 cc = f.scell_ctr[ch.x + t];
+      quad[t] = (cc.x > ctr.x ? 1 : 0) + (cc.y > ctr.y ? 2 : 0);
+    }
+  } else {
+    for (int i = t; i < p * p; i += blockDim.x) {
+      const int k1 = i / p, qq = i - k1 * p;  // k1 = k - 1, qq = q - 1
+      bm[i] = R(c_binom[qq][k1] * ldexp(1.0, -(k1 + 1)));
+    }
   }
   for (int i = t; i < nch * np; i += blockDim.x) {
     const int c = i / np, r = i - c * np;
     const double2 cc = f.scell_ctr[ch.x + c];
-    sa[c * np + r] = recentred(M, size_t(ch.x + c) * np, r, p1, make_double2(cc.x - ctr.x, cc.y - ctr.y));
+    const C a = recentred(M, size_t(ch.x + c) * np, r, p1, make_double2(cc.x - ctr.x, cc.y - ctr.y));
+    sa[c * np + r] = a;
+    if constexpr (DF) {
+      const df ar = split_df(double(a.x)), ai = split_df(double(a.y));
+      saf[c * np + r] = make_float4(ar.h, ar.l, ai.h, ai.l);
+    }
   }
   for (int i = t; i < nch * p1; i += blockDim.x) {
     const int c = i / p1, n = i - c * p1;
@@ -261,8 +282,26 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
       acc = cadd(acc, a[0]);
     } else {
       C v = cscale(cmul(a[0], spc[q]), -inv_q);
-      const R *B = bm + (q - 1);
-      for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(spc[q - k], B[(k - 1) * p]), v);
+      if constexpr (DF) {
+        const float4 *af = saf + c * np + set * p1;
+        const float4 *T = f.m2m_df + size_t(quad[c]) * f.mp * (f.mp + 1) + q;
+        df vr = {0.0f, 0.0f}, vi = {0.0f, 0.0f};
+        for (int k = 1; k <= q; ++k) {
+          const float4 w = T[(k - 1) * (f.mp + 1)], ak = af[k];
+          df_mul_acc(vr, {ak.x, ak.y}, {w.x, w.y});   // re: a.re w.re - a.im w.im
+          df_mul_acc(vr, {-ak.z, -ak.w}, {w.z, w.w});
+          df_mul_acc(vi, {ak.x, ak.y}, {w.z, w.w});   // im: a.re w.im + a.im w.re
+          df_mul_acc(vi, {ak.z, ak.w}, {w.x, w.y});
+          if ((k & 7) == 0) {
+            df_renorm(vr);
+            df_renorm(vi);
+          }
+        }
+        v = cadd(v, C{R(double(vr.h) + double(vr.l)), R(double(vi.h) + double(vi.l))});
+      } else {
+        const R *B = bm + (q - 1);
+        for (int k = 1; k <= q; ++k) v = cfma(a[k], cscale(spc[q - k], B[(k - 1) * p]), v);
+      }
       acc = cadd(acc, v);
     }
   }
@@ -599,7 +638,7 @@ struct stokes_fmm {
   int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
   bool near32 = false;  // direct pairs (near field, own-curve removal) in FP32 arithmetic
   bool fp32 = false;    // expansions (P2M, M2M, M2L, L2L, L2P) in FP32 arithmetic
-  bool m2l_df = true;   // FP64 evaluations: M2L binomial sums in double-float (FP32 pipes)
+  bool m2l_df = true;   // FP64 evaluations: M2L and M2M sums in double-float (FP32 pipes)
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -611,6 +650,7 @@ struct stokes_fmm {
       *d_nl_idx = nullptr, *d_tgt_node = nullptr;
   double2 *d_M = nullptr, *d_Lc = nullptr;
   double2 *d_tpow = nullptr, *d_tlog = nullptr;  // offset table of the conversions below the roots
+  float4 *d_m2m_df = nullptr;  // M2M shift weights per child quadrant, double-float (see m2m_kernel)
   int *d_src_own = nullptr, *d_node_curve = nullptr;
   // the geometry the plan was made for
   unsigned long long generation = 0;
@@ -693,7 +733,8 @@ cudaError_t upload(T *&d, const std::vector<T> &h, size_t &bytes) {
 void free_plan(stokes_fmm *f) {
   void *ps[] = {f->d_src_slot, f->d_src_pos, f->d_sc_ctr, f->d_tc_ctr, f->d_sc_rng,
                 f->d_tleaf_rng, f->d_tc_par, f->d_il_off, f->d_il_idx, f->d_nl_off,
-                f->d_nl_idx, f->d_tgt_node, f->d_M, f->d_Lc, f->d_tpow, f->d_tlog, f->d_src_own, f->d_node_curve};
+                f->d_nl_idx, f->d_tgt_node, f->d_M, f->d_Lc, f->d_tpow, f->d_tlog, f->d_src_own, f->d_node_curve,
+                f->d_m2m_df};
   for (void *q : ps) cudaFree(q);
 }
 
@@ -991,6 +1032,38 @@ int build_plan(stokes_fmm *f, int leaf_target) {
     up(upload(f->d_tpow, tpow, bytes));
     up(upload(f->d_tlog, tlog, bytes));
   }
+  {  // M2M weights s^(q-k) C(q - 1, k - 1) 2^-k for the child offsets s = (+-1 +- i)/4 (quadrant
+     // c = [s_x > 0] + 2 [s_y > 0]), 1 <= k <= q <= p, at (c p + k - 1) (p + 1) + q, split into
+     // float pairs (re.h, re.l, im.h, im.l)
+    const int p = f->p, p1 = p + 1;
+    std::vector<double> bn(size_t(p1) * p1, 0.0);  // C(n, k), Pascal's triangle (exact)
+    for (int n = 0; n <= p; ++n)
+      for (int k = 0; k <= n; ++k)
+        bn[n * p1 + k] = (k == 0 || k == n) ? 1.0 : bn[(n - 1) * p1 + k - 1] + bn[(n - 1) * p1 + k];
+    std::vector<float4> tab(size_t(4) * p * p1, make_float4(0.f, 0.f, 0.f, 0.f));
+    auto split = [](double v, float &h, float &l) {
+      h = float(v);
+      l = float(v - double(h));
+    };
+    for (int c = 0; c < 4; ++c) {
+      const double sx = (c & 1) ? 0.25 : -0.25, sy = (c & 2) ? 0.25 : -0.25;
+      std::vector<double> pr(p1), pi(p1);  // s^n
+      pr[0] = 1.0;
+      pi[0] = 0.0;
+      for (int n = 1; n <= p; ++n) {
+        pr[n] = pr[n - 1] * sx - pi[n - 1] * sy;
+        pi[n] = pr[n - 1] * sy + pi[n - 1] * sx;
+      }
+      for (int q = 1; q <= p; ++q)
+        for (int k = 1; k <= q; ++k) {
+          const double w = bn[(q - 1) * p1 + (k - 1)] * ldexp(1.0, -k);
+          float4 &t = tab[(size_t(c) * p + (k - 1)) * p1 + q];
+          split(pr[q - k] * w, t.x, t.y);
+          split(pi[q - k] * w, t.z, t.w);
+        }
+    }
+    up(upload(f->d_m2m_df, tab, bytes));
+  }
   const size_t ne = size_t(kSets) * (f->p + 1);
   up(cudaMalloc(reinterpret_cast<void **>(&f->d_M), sizeof(double2) * ne * std::max(nsc, 1)));
   up(cudaMalloc(reinterpret_cast<void **>(&f->d_Lc), sizeof(double2) * ne * std::max(ntc, 1)));
@@ -1101,6 +1174,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.p = pe;
   d.tp1 = f->p + 1;
   d.near32 = f->near32 ? 1 : 0;
+  d.m2m_df = f->d_m2m_df;
+  d.mp = f->p;
   d.n_src = f->n_src;
   d.N = N;
   d.wall_slots = c->wall_slots_f64;
@@ -1135,6 +1210,7 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const size_t cb = f->fp32 ? sizeof(float2) : sizeof(double2), rb = cb / 2;  // complex, real
   const size_t p2m_smem = cb * (kP2mChunk * p1 + kP2mChunk * kSets);
   const size_t m2m_smem = cb * (4 * np + 4 * p1) + rb * pe * pe;
+  const size_t m2m_df_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(float4) * 4 * np;
   const size_t m2l_smem = cb * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + rb * p1 * pe;
   const size_t m2l_df_smem = sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) +
                              sizeof(float4) * kM2lBatch * np + sizeof(float2) * p1 * pe;
@@ -1143,7 +1219,11 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     if (nleaf_s > 0) p2m_kernel<R><<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
     for (int l = L - 1; l >= 0; --l) {
       const int nc = f->sc_off[l + 1] - f->sc_off[l];
-      if (nc > 0) m2m_kernel<R><<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
+      if (nc == 0) continue;
+      if (sizeof(R) == 8 && f->m2l_df)
+        m2m_kernel<double, true><<<nc, nthr, m2m_df_smem, s>>>(d, f->sc_off[l]);
+      else
+        m2m_kernel<R><<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
     }
     for (int l = 0; l <= L; ++l) {
       const int nc = f->tc_off[l + 1] - f->tc_off[l];
