@@ -99,6 +99,34 @@ template <typename R> __device__ __forceinline__ cx<R> tocx(double2 a) { return 
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
 
+// A complex number in double-float: (re.h, re.l, im.h, im.l).
+__device__ __forceinline__ float4 split_c(double2 a) {
+  const df r = split_df(a.x), i = split_df(a.y);
+  return make_float4(r.h, r.l, i.h, i.l);
+}
+struct dfc {
+  df re, im;
+};
+__device__ __forceinline__ dfc dfc_of(float4 a) { return {{a.x, a.y}, {a.z, a.w}}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+// acc += a b (complex, double-float)
+__device__ __forceinline__ void dfc_mul_acc(dfc &acc, dfc a, dfc b) {
+  df_mul_acc(acc.re, a.re, b.re);
+  df_mul_acc(acc.re, df_neg(a.im), b.im);
+  df_mul_acc(acc.im, a.re, b.im);
+  df_mul_acc(acc.im, a.im, b.re);
+}
+// x + y (double-float): TwoSum of the high parts, the low parts added to its error.
+__device__ __forceinline__ df df_sum(df x, df y) {
+  const df s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ void dfc_renorm(dfc &a) {
+  df_renorm(a.re);
+  df_renorm(a.im);
+}
+__device__ __forceinline__ float4 dfc_pack(dfc a) { return make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
+
 // Coefficient r of the expansion stored at E + base (kSets sets of p1 coefficients) with the
 // sets 2 and 5 moved to a new centre.  Those two sets carry conj(w - c) q and nu T conj(w - c):
 // each expansion keeps them relative to its own centre c, which spares the assembly the
@@ -170,6 +198,9 @@ struct FmmDev {
   const int *src_own;         // [n_src] vesicle curve of an m = 0 source, else -1
   const int *node_curve;      // [N] vesicle curve of a node, else -1
   const float4 *m2m_df;       // M2M shift weights per child quadrant (double-float), plan order
+  float4 *Mf;                 // FP64 evaluations: M split into float pairs (re.h, re.l, im.h,
+                              // im.l), written beside M by P2M and M2M, read by m2l_df_kernel
+  const float4 *tpow_df;      // [49][tp1] tpow split likewise
   int mp;                     // the plan's order (row stride of m2m_df: mp + 1, block: mp rows)
 };
 
@@ -212,15 +243,22 @@ __global__ void p2m_kernel(FmmDev f, int cell0, double h) {
     if (set < kSets)
       for (int j = 0; j < nj; ++j) acc = cfma(sc[j][set], pw[j * p1 + k], acc);
   }
-  if (set < kSets) M[(size_t(cell) * kSets + set) * p1 + k] = k == 0 ? acc : cscale(acc, R(-1.0 / k));
+  if (set < kSets) {
+    const C v = k == 0 ? acc : cscale(acc, R(-1.0 / k));
+    const size_t idx = (size_t(cell) * kSets + set) * p1 + k;
+    M[idx] = v;
+    if constexpr (sizeof(R) == 8)
+      if (f.Mf) f.Mf[idx] = split_c(to_d2(v));
+  }
 }
 
 // M2M: one CTA per source cell of a level above the leaves; thread (set, q).  The children's
 // coefficients, the powers of their offsets and the binomials are staged in shared memory:
 // a'_q += -a_0 s^q / q + sum_{k <= q} a_k 2^-k s^(q-k) C(q - 1, k - 1), s = (c_child - c) / h.
-// DF (FP64 evaluations): the shift sums sum_k a_k s^(q-k) C(q - 1, k - 1) 2^-k in double-float
-// on the FP32 pipes, the weights from the plan's table of the four child quadrants, the
-// children's coefficients split exactly into float pairs; the a_0 term stays FP64.
+// DF (the FP64 evaluations): the shift sums sum_k a_k s^(q-k) C(q - 1, k - 1) 2^-k in
+// double-float on the FP32 pipes, the weights from the plan's table of the four child
+// quadrants, the children's coefficients split exactly into float pairs; the a_0 term stays
+// FP64.  Without DF: the FP32 evaluations.
 template <typename R, bool DF = false>
 __global__ void m2m_kernel(FmmDev f, int cell0) {
   using C = cx<R>;
@@ -305,7 +343,10 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
       acc = cadd(acc, v);
     }
   }
-  M[(size_t(cell) * kSets + set) * p1 + q] = acc;
+  const size_t idx = (size_t(cell) * kSets + set) * p1 + q;
+  M[idx] = acc;
+  if constexpr (sizeof(R) == 8)
+    if (f.Mf) f.Mf[idx] = split_c(to_d2(acc));
 }
 
 // L2L from the parent and M2L from the interaction list: one CTA per target cell of one level;
@@ -313,13 +354,9 @@ __global__ void m2m_kernel(FmmDev f, int cell0) {
 // in shared memory; then b_0 += a_0 log(-t h) + sum_k w_k and
 // b_q += t^-q (sum_k C(q + k - 1, k - 1) w_k - a_0 / q).  Below the roots t is an integer
 // offset with |t_x|, |t_y| <= 3, whose powers and log(-t) come from the plan's table.  Source
-// cells are staged kM2lBatch at a time.
+// cells are staged kM2lBatch at a time.  FP32 evaluations; the FP64 ones use m2l_df_kernel.
 constexpr int kM2lBatch = 4;
-// DF (FP64 evaluations): the binomial sums sum_k C(q + k - 1, k - 1) w_k -- the bulk of the
-// conversion work -- run in double-float arithmetic on the FP32 pipes (FP64 is the narrow
-// pipe on this chip) from FP64 weights split exactly into float pairs (~48-bit products and
-// sums, renormalised every 8 terms); the staging and the complex update stay FP64.
-template <typename R, bool DF = false>
+template <typename R>
 __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   using C = cx<R>;
   const int cell = cell0 + blockIdx.x;
@@ -334,21 +371,12 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
   // dynamic shared memory (m2l_smem): sw[kM2lBatch][np], stq[kM2lBatch][p + 1],
   // slog[kM2lBatch], then bq[p * (p + 1)] = C(q + k - 1, k - 1) at (k - 1) (p + 1) + q, k = 1..p
   // (consecutive q -- the threads of one set -- read consecutive words: no bank conflicts)
-  // (with DF: then swf[kM2lBatch][np] the split weights (x.h, x.l, y.h, y.l), and bq holds the
-  // split binomials as float2 instead)
   extern __shared__ double2 dyn_m2l[];
   C *sw = reinterpret_cast<C *>(dyn_m2l), *stq = sw + kM2lBatch * np, *slog = stq + kM2lBatch * p1;
-  float4 *swf = reinterpret_cast<float4 *>(slog + kM2lBatch);
-  R *bq = reinterpret_cast<R *>(DF ? reinterpret_cast<C *>(swf + kM2lBatch * np) : slog + kM2lBatch);
-  float2 *bqf = reinterpret_cast<float2 *>(bq);
+  R *bq = reinterpret_cast<R *>(slog + kM2lBatch);
   for (int i = t; i < p1 * p; i += blockDim.x) {
     const int k1 = i / p1, qq = i - k1 * p1;  // k1 = k - 1
-    if constexpr (DF) {
-      const df b = split_df(c_binom[qq + k1][k1]);
-      bqf[i] = make_float2(b.h, b.l);
-    } else {
-      bq[i] = R(c_binom[qq + k1][k1]);
-    }
+    bq[i] = R(c_binom[qq + k1][k1]);
   }
   C acc = mkc<R>(0.0, 0.0);
   const int par = f.tcell_parent[cell];
@@ -382,12 +410,7 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       // off the table (roots only) the offset is an integer pair as well: use it exactly
       const C T = tocx<R>(tab ? f.tpow[ti * f.tp1 + qi] : cpow(cinv(make_double2(dx, dy)), qi));
       const C a = recentred(M, size_t(sc) * np, r, p1, make_double2(cs.x - ct.x, cs.y - ct.y));
-      const C wv = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
-      sw[el * np + r] = wv;
-      if constexpr (DF) {
-        const df wx = split_df(double(wv.x)), wy = split_df(double(wv.y));
-        swf[el * np + r] = make_float4(wx.h, wx.l, wy.h, wy.l);
-      }
+      sw[el * np + r] = qi == 0 ? a : cscale(cmul(a, T), R((qi & 1) ? -1.0 : 1.0));
       if (si == 0) {
         stq[el * p1 + qi] = T;
         if (qi == 0)
@@ -402,28 +425,10 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
       for (int el = 0; el < nb; ++el) {
         const C *w = sw + el * np + set * p1;
         R vx = R(0), vy = R(0);
-        if constexpr (DF) {
-          const float4 *wf = swf + el * np + set * p1;
-          const float2 *Bf = bqf + q;
-          df ax = {0.0f, 0.0f}, ay = {0.0f, 0.0f};
-          for (int k = 1; k <= p; ++k) {
-            const float2 b = Bf[(k - 1) * p1];
-            const float4 wk = wf[k];
-            df_mul_acc(ax, {b.x, b.y}, {wk.x, wk.y});
-            df_mul_acc(ay, {b.x, b.y}, {wk.z, wk.w});
-            if ((k & 7) == 0) {
-              df_renorm(ax);
-              df_renorm(ay);
-            }
-          }
-          vx = R(double(ax.h) + double(ax.l));
-          vy = R(double(ay.h) + double(ay.l));
-        } else {
-          for (int k = 1; k <= p; ++k) {
-            const R bk = B[(k - 1) * p1];
-            vx = fma(bk, w[k].x, vx);
-            vy = fma(bk, w[k].y, vy);
-          }
+        for (int k = 1; k <= p; ++k) {
+          const R bk = B[(k - 1) * p1];
+          vx = fma(bk, w[k].x, vx);
+          vy = fma(bk, w[k].y, vy);
         }
         if (q == 0)
           acc = cadd(acc, cadd(cmul(w[0], mkc<R>(double(slog[el].x) + log_h, slog[el].y)),
@@ -434,6 +439,134 @@ __global__ void m2l_kernel(FmmDev f, int cell0, double h, double log_h) {
     }
   }
   if (set < kSets) Lc[(size_t(cell) * kSets + set) * p1 + q] = acc;
+}
+
+// M2L of FP64 evaluations with every per-interaction operation in double-float on the FP32
+// pipes: the weights w_k = a_k (-1)^k t^-k from the double-float copy of the multipoles (Mf) and
+// offset powers (tpow_df), the re-centring of sets 2 and 5, the binomial sums and the
+// accumulation of b_q += t^-q (sum_k C(q + k - 1, k - 1) w_k - a_0 / q) (b_0: a_0 log(-t h) +
+// sum_k w_k).  FP64 is left for the L2L from the parent (once per target cell), the per-source
+// offsets (one thread each) and the final write.  Same thread layout and batching as m2l_kernel.
+__global__ void m2l_df_kernel(FmmDev f, int cell0, double h, double log_h) {
+  const int cell = cell0 + blockIdx.x;
+  const double2 ct = f.tcell_ctr[cell];
+  const int p = f.p, p1 = p + 1, np = kSets * p1;
+  const int t = threadIdx.x;
+  const int set = t / p1, q = t - set * p1;
+  const double inv_h = 1.0 / h;
+  const double2 *Lc64 = f.Lc;
+  // dynamic shared memory: swf[kM2lBatch][np], stqf[kM2lBatch][p + 1], bqf[p][p + 1] (float2),
+  // then the L2L staging sw[np], sp[p + 1] (double2)
+  extern __shared__ double2 dyn_m2l_df[];
+  float4 *swf = reinterpret_cast<float4 *>(dyn_m2l_df), *stqf = swf + kM2lBatch * np;
+  float2 *bqf = reinterpret_cast<float2 *>(stqf + kM2lBatch * p1);
+  double2 *sw = reinterpret_cast<double2 *>(bqf + p * p1 + (p * p1) % 2), *sp = sw + np;
+  __shared__ float4 slogf[kM2lBatch], dcf[kM2lBatch];
+  __shared__ int sidx[kM2lBatch], tidx[kM2lBatch];
+  for (int i = t; i < p1 * p; i += blockDim.x) {
+    const int k1 = i / p1, qq = i - k1 * p1;  // k1 = k - 1
+    const df b = split_df(c_binom[qq + k1][k1]);
+    bqf[i] = make_float2(b.h, b.l);
+  }
+  double2 acc64 = make_double2(0.0, 0.0);
+  const int par = f.tcell_parent[cell];
+  if (par >= 0) {  // L2L in FP64 (once per target cell)
+    const double2 cp = f.tcell_ctr[par];
+    const double2 s = make_double2((ct.x - cp.x) * (0.5 * inv_h), (ct.y - cp.y) * (0.5 * inv_h));
+    for (int i = t; i < np; i += blockDim.x)
+      sw[i] = recentred(Lc64, size_t(par) * np, i, p1, make_double2(cp.x - ct.x, cp.y - ct.y));
+    if (t <= p) sp[t] = cpow(s, t);
+    __syncthreads();
+    if (set < kSets) {
+      const double2 *b = sw + set * p1;
+      double2 v = make_double2(0.0, 0.0);
+      for (int k = q; k <= p; ++k) v = cfma(b[k], cscale(sp[k - q], c_binom[k][q]), v);
+      acc64 = cscale(v, ldexp(1.0, -q));
+    }
+  }
+  const df inv_q = split_df(q > 0 ? 1.0 / q : 0.0);
+  dfc acc = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+  const int il0 = f.il_off[cell], ne = f.il_off[cell + 1] - il0;
+  for (int e0 = 0; e0 < ne; e0 += kM2lBatch) {
+    const int nb = min(kM2lBatch, ne - e0);
+    __syncthreads();
+    if (t < nb) {  // per source cell: the offset, its table row, conj(dc) and log(-t h)
+      const int sc = f.il_idx[il0 + e0 + t];
+      const double2 cs = f.scell_ctr[sc];
+      const double ox = (cs.x - ct.x) * inv_h, oy = (cs.y - ct.y) * inv_h;
+      const int dx = __double2int_rn(ox), dy = __double2int_rn(oy);
+      const bool tab = abs(dx) <= 3 && abs(dy) <= 3;
+      sidx[t] = sc;
+      tidx[t] = tab ? (dy + 3) * 7 + (dx + 3) : -1 - ((dy + 64) * 256 + (dx + 64));
+      dcf[t] = split_c(make_double2(cs.x - ct.x, -(cs.y - ct.y)));  // conj(c_s - c_t)
+      const double2 lg = tab ? f.tlog[(dy + 3) * 7 + (dx + 3)]
+                             : make_double2(0.5 * log(double(dx) * dx + double(dy) * dy),
+                                            atan2(-double(dy), -double(dx)));
+      slogf[t] = split_c(make_double2(lg.x + log_h, lg.y));
+    }
+    __syncthreads();
+    for (int i = t; i < nb * np; i += blockDim.x) {
+      const int el = i / np, r = i - el * np;
+      const int si = r / p1, qi = r - si * p1;
+      const size_t base = size_t(sidx[el]) * np;
+      dfc a = dfc_of(f.Mf[base + r]);
+      if (si == 2 || si == 5) {  // re-centre to c_t (see recentred())
+        dfc b;
+        if (si == 2) {
+          const dfc a0 = dfc_of(f.Mf[base + qi]), a1 = dfc_of(f.Mf[base + p1 + qi]);
+          b = {df_sum(a0.re, df_neg(a1.im)), df_sum(a0.im, a1.re)};  // a0 + i a1
+        } else {
+          b = dfc_of(f.Mf[base + 4 * p1 + qi]);
+        }
+        dfc_mul_acc(a, dfc_of(dcf[el]), b);
+      }
+      const int ti = tidx[el];
+      dfc T;
+      if (ti >= 0) {
+        T = dfc_of(f.tpow_df[ti * f.tp1 + qi]);
+      } else {  // off the table (roots only): the integer offset, powers in FP64
+        const int code = -1 - ti, dy = code / 256 - 64, dx = code % 256 - 64;
+        T = dfc_of(split_c(cpow(cinv(make_double2(dx, dy)), qi)));
+      }
+      dfc w = a;
+      if (qi > 0) {
+        w = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+        dfc_mul_acc(w, a, T);
+        if (qi & 1) w = {df_neg(w.re), df_neg(w.im)};
+      }
+      swf[el * np + r] = dfc_pack(w);
+      if (si == 0) stqf[el * p1 + qi] = dfc_pack(T);
+    }
+    __syncthreads();
+    if (set < kSets) {
+      const float2 *Bf = bqf + q;
+      for (int el = 0; el < nb; ++el) {
+        const float4 *wf = swf + el * np + set * p1;
+        dfc v = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+        for (int k = 1; k <= p; ++k) {
+          const float2 b = Bf[(k - 1) * p1];
+          const float4 wk = wf[k];
+          df_mul_acc(v.re, {b.x, b.y}, {wk.x, wk.y});
+          df_mul_acc(v.im, {b.x, b.y}, {wk.z, wk.w});
+          if ((k & 7) == 0) dfc_renorm(v);
+        }
+        const dfc w0 = dfc_of(wf[0]);
+        if (q == 0) {  // b_0 += a_0 log(-t h) + sum_k w_k
+          dfc_mul_acc(acc, w0, dfc_of(slogf[el]));
+          acc = {df_sum(acc.re, v.re), df_sum(acc.im, v.im)};
+        } else {       // b_q += t^-q (sum - a_0 / q)
+          df_mul_acc(v.re, df_neg(w0.re), inv_q);
+          df_mul_acc(v.im, df_neg(w0.im), inv_q);
+          dfc_mul_acc(acc, v, dfc_of(stqf[el * p1 + q]));
+        }
+        dfc_renorm(acc);
+      }
+    }
+  }
+  if (set < kSets)
+    f.Lc[(size_t(cell) * kSets + set) * p1 + q] =
+        make_double2(acc64.x + (double(acc.re.h) + double(acc.re.l)),
+                     acc64.y + (double(acc.im.h) + double(acc.im.l)));
 }
 
 // L2P and the near field: one CTA per target leaf, one thread per target (strided).
@@ -638,7 +771,6 @@ struct stokes_fmm {
   int eval_p = 0;  // order of the evaluations (0: p); expansions truncated below the plan's
   bool near32 = false;  // direct pairs (near field, own-curve removal) in FP32 arithmetic
   bool fp32 = false;    // expansions (P2M, M2M, M2L, L2L, L2P) in FP32 arithmetic
-  bool m2l_df = true;   // FP64 evaluations: M2L and M2M sums in double-float (FP32 pipes)
   double x0 = 0.0, y0 = 0.0, S = 1.0;
   std::vector<int> sc_off, tc_off;  // [L + 2] first source / target cell of each level
   int n_tleaf = 0;
@@ -651,6 +783,7 @@ struct stokes_fmm {
   double2 *d_M = nullptr, *d_Lc = nullptr;
   double2 *d_tpow = nullptr, *d_tlog = nullptr;  // offset table of the conversions below the roots
   float4 *d_m2m_df = nullptr;  // M2M shift weights per child quadrant, double-float (see m2m_kernel)
+  float4 *d_tpow_df = nullptr, *d_Mf = nullptr;  // double-float copies for m2l_df_kernel
   int *d_src_own = nullptr, *d_node_curve = nullptr;
   // the geometry the plan was made for
   unsigned long long generation = 0;
@@ -734,7 +867,7 @@ void free_plan(stokes_fmm *f) {
   void *ps[] = {f->d_src_slot, f->d_src_pos, f->d_sc_ctr, f->d_tc_ctr, f->d_sc_rng,
                 f->d_tleaf_rng, f->d_tc_par, f->d_il_off, f->d_il_idx, f->d_nl_off,
                 f->d_nl_idx, f->d_tgt_node, f->d_M, f->d_Lc, f->d_tpow, f->d_tlog, f->d_src_own, f->d_node_curve,
-                f->d_m2m_df};
+                f->d_m2m_df, f->d_tpow_df, f->d_Mf};
   for (void *q : ps) cudaFree(q);
 }
 
@@ -1031,6 +1164,12 @@ int build_plan(stokes_fmm *f, int leaf_target) {
       }
     up(upload(f->d_tpow, tpow, bytes));
     up(upload(f->d_tlog, tlog, bytes));
+    std::vector<float4> tpow_df(tpow.size());
+    for (size_t i = 0; i < tpow.size(); ++i) {
+      const float rh = float(tpow[i].x), ih = float(tpow[i].y);
+      tpow_df[i] = make_float4(rh, float(tpow[i].x - double(rh)), ih, float(tpow[i].y - double(ih)));
+    }
+    up(upload(f->d_tpow_df, tpow_df, bytes));
   }
   {  // M2M weights s^(q-k) C(q - 1, k - 1) 2^-k for the child offsets s = (+-1 +- i)/4 (quadrant
      // c = [s_x > 0] + 2 [s_y > 0]), 1 <= k <= q <= p, at (c p + k - 1) (p + 1) + q, split into
@@ -1066,8 +1205,9 @@ int build_plan(stokes_fmm *f, int leaf_target) {
   }
   const size_t ne = size_t(kSets) * (f->p + 1);
   up(cudaMalloc(reinterpret_cast<void **>(&f->d_M), sizeof(double2) * ne * std::max(nsc, 1)));
+  up(cudaMalloc(reinterpret_cast<void **>(&f->d_Mf), sizeof(float4) * ne * std::max(nsc, 1)));
   up(cudaMalloc(reinterpret_cast<void **>(&f->d_Lc), sizeof(double2) * ne * std::max(ntc, 1)));
-  bytes += sizeof(double2) * ne * (nsc + ntc);
+  bytes += sizeof(double2) * ne * (nsc + ntc) + sizeof(float4) * ne * nsc;
   if (e != cudaSuccess) {
     f->err = std::string("fmm plan upload: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA;
@@ -1176,6 +1316,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.near32 = f->near32 ? 1 : 0;
   d.m2m_df = f->d_m2m_df;
   d.mp = f->p;
+  d.Mf = f->fp32 ? nullptr : f->d_Mf;
+  d.tpow_df = f->d_tpow_df;
   d.n_src = f->n_src;
   d.N = N;
   d.wall_slots = c->wall_slots_f64;
@@ -1212,15 +1354,16 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   const size_t m2m_smem = cb * (4 * np + 4 * p1) + rb * pe * pe;
   const size_t m2m_df_smem = sizeof(double2) * (4 * np + 4 * p1) + sizeof(float4) * 4 * np;
   const size_t m2l_smem = cb * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) + rb * p1 * pe;
-  const size_t m2l_df_smem = sizeof(double2) * (kM2lBatch * np + kM2lBatch * p1 + kM2lBatch) +
-                             sizeof(float4) * kM2lBatch * np + sizeof(float2) * p1 * pe;
+  const size_t m2l_df_smem = sizeof(float4) * (kM2lBatch * np + kM2lBatch * p1) +
+                             sizeof(float2) * (size_t(p1) * pe + (size_t(p1) * pe) % 2) +
+                             sizeof(double2) * (np + p1);
   auto passes = [&](auto real) {
     using R = decltype(real);
     if (nleaf_s > 0) p2m_kernel<R><<<nleaf_s, nthr, p2m_smem, s>>>(d, f->sc_off[L], hl(L));
     for (int l = L - 1; l >= 0; --l) {
       const int nc = f->sc_off[l + 1] - f->sc_off[l];
       if (nc == 0) continue;
-      if (sizeof(R) == 8 && f->m2l_df)
+      if constexpr (sizeof(R) == 8)  // FP64 evaluations: shift sums in double-float
         m2m_kernel<double, true><<<nc, nthr, m2m_df_smem, s>>>(d, f->sc_off[l]);
       else
         m2m_kernel<R><<<nc, nthr, m2m_smem, s>>>(d, f->sc_off[l]);
@@ -1228,8 +1371,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     for (int l = 0; l <= L; ++l) {
       const int nc = f->tc_off[l + 1] - f->tc_off[l];
       if (nc == 0) continue;
-      if (sizeof(R) == 8 && f->m2l_df)
-        m2l_kernel<double, true><<<nc, nthr, m2l_df_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
+      if constexpr (sizeof(R) == 8)  // FP64 evaluations: conversions in double-float
+        m2l_df_kernel<<<nc, nthr, m2l_df_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
       else
         m2l_kernel<R><<<nc, nthr, m2l_smem, s>>>(d, f->tc_off[l], hl(l), log(hl(l)));
     }
