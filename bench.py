@@ -345,6 +345,41 @@ def _mode_slice(nm_from, nm_to, history=False):
     return np.concatenate(feat), targ
 
 
+def run_step_one(args):
+    """One mixed-precision zero-guess step of the held-out channel of --step (seed 2000), after
+    --warmup warm steps, between cudaProfilerStart/Stop -- for a launch list of one step with
+    `ncu --profile-from-start off`.  Settings as --step: --residual-fmm, --sweep-fmm,
+    --precond-refresh."""
+    import torch
+    import paper_1510_05616_gb300 as P
+    from paper_1510_05616_gb300 import build as B
+    from paper_1510_05616_gb300 import inputs as I
+    from paper_1510_05616_gb300 import warmstart as WS
+    B.build()
+    n_w, modes, nv, n_v, area = I.WORKLOADS[args.step_workload]
+    kb = 0.01 * area / I.WORKLOADS["mid_n16k"][4]  # as run_step
+    pd = 2 * 1.0 * 2 * math.pi * 0.2
+    g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=1.0)
+    sim = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=args.residual_fmm,
+                        sweep_fmm=args.sweep_fmm, precond_refresh=args.precond_refresh)
+    for _ in range(args.warmup):
+        sim.step(1e-3, pd, "zero", precision=P.STOKES_FP32_KAHAN)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    st = sim.step(1e-3, pd, "zero", precision=P.STOKES_FP32_KAHAN)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    sim.close()
+    print(json.dumps({"metric": "one semi-implicit step (zero guess), profiled", "unit": "ms",
+                      "value": st["total_ms"], "warm_steps": args.warmup,
+                      "config": {"workload": WORKLOAD_DESCS[args.step_workload],
+                                 "residual_fmm_order": args.residual_fmm,
+                                 "sweep_fmm_order": args.sweep_fmm,
+                                 "precond_refresh": bool(args.precond_refresh)},
+                      "stats": st}))
+    return 0
+
+
 def run_step(args):
     """Algorithm 1 on a channel (walls, channel response, GMRES to 1e-10): plain runs give the
     training states, a network per feature size (warm-start modes) is trained with the
@@ -918,6 +953,9 @@ def main():
     ap.add_argument("--close-factor", type=float, default=5.0)
     ap.add_argument("--no-warm-history", action="store_true",
                     help="warm-start features without the previous solution and its last change")
+    ap.add_argument("--step-one", action="store_true",
+                    help="one zero-guess step of the --step held-out channel after --warmup steps, "
+                         "between cudaProfilerStart/Stop")
     ap.add_argument("--precond-refresh", action="store_true",
                     help="--step: refresh the preconditioner inverse by Newton-Schulz from the "
                          "previous step's instead of factorising every step")
@@ -937,6 +975,8 @@ def main():
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.step_one:
+        return run_step_one(args)
     if args.step:
         return run_step(args)
     if args.poiseuille:
