@@ -685,9 +685,10 @@ STOKES_API int stokes_sim_set_fds_recompress(stokes_sim *sim, int on);
 STOKES_API int stokes_sim_fds_info(const stokes_sim *sim, stokes_fds_info *info);
 STOKES_API int stokes_sim_set_block_refinement(stokes_sim *sim, int sweeps);
 /* Precision of the factorization of the block-diagonal self preconditioner: STOKES_FP32_KAHAN
- * (default: FP32 batched LU and inverse of the FP64-assembled blocks, applied with FP64
- * products and sums, so it is still one fixed linear operator and GMRES's FP64 tolerance is
- * unaffected) or STOKES_FP64.  Only the iteration counts can differ. */
+ * (default: the blocks assembled in FP32, FP32 batched LU and inverse, applied with exact
+ * products of the FP32 entries and double-float sums (~1e-14 relative), so it is still one
+ * fixed linear operator and GMRES's FP64 tolerance is unaffected) or STOKES_FP64.  Only the
+ * iteration counts can differ. */
 STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
 /* Refresh of the FP32 preconditioner inverse (on = 1; default 0 = factorise every step): the
  * blocks move little in one step, so the previous step's inverse X is kept when

@@ -30,6 +30,7 @@
 #include <thread>
 #include <vector>
 
+#include "df.cuh"
 #include "fds.cuh"
 #include "stokes_internal.cuh"
 #include "stokes_mlp_internal.cuh"
@@ -56,6 +57,7 @@ struct stokes_sim {
   double2 *d_proxy = nullptr;          // [M]
   double *d_LU = nullptr, *d_W = nullptr, *d_C = nullptr, *d_Spinv = nullptr;
   int *d_piv = nullptr, *d_info = nullptr;
+  double *d_nrm_part = nullptr;        // [kNrmBlocks] partial sums of squares (dnrm)
   // wall solver: STOKES_WALLS_FDS (default) the fast direct solver of Sec. 4;
   // STOKES_WALLS_LU64 factors A in FP64; STOKES_WALLS_LU32_REFINE inverts an FP32 copy (LU, then
   // the inverse, d_Ainv32) and refines every solve with FP64 residuals of the FP64 A (d_A)
@@ -1013,26 +1015,69 @@ __global__ void set_ptrs32_kernel(int count, float *base, size_t stride, float *
 
 // zout_v = Pinv32_v zin_v for every vesicle v (one block each, k = 3n rows, column-major k x k
 // blocks), products and sums in FP64: the FP32-stored inverse acts as a fixed FP64 operator.
+// zout = Pinv zin per vesicle (k x k FP32 blocks, column-major; a CTA per vesicle).  Each
+// product b z_j with the FP32 entry b and the FP64 z_j = z_h + z_l split into floats is formed
+// as b z_h exactly (FMA) plus b z_l and added into a double-float accumulator, on the FP32
+// pipes (~1e-14 relative, the FP64 operator to that accuracy); eight coalesced column loads
+// are in flight per thread (the block is read once from HBM).
 __global__ void precond32_apply_kernel(int k, const float *Pinv, const double *zin, double *zout) {
-  extern __shared__ double zs[];
+  extern __shared__ float2 zs2[];  // z split: (h, l)
   const size_t off = size_t(blockIdx.x) * k;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) zs[j] = zin[off + j];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const df z = split_df(zin[off + j]);
+    zs2[j] = make_float2(z.h, z.l);
+  }
   __syncthreads();
   const float *B = Pinv + size_t(blockIdx.x) * k * k;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    // eight coalesced column loads in flight per thread (HBM-bound: the block is read once)
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    df acc[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     int j = 0;
     for (; j + 7 < k; j += 8) {
       float b[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) b[u] = B[i + size_t(j + u) * k];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u & 3] = fma(double(b[u]), zs[j + u], acc[u & 3]);
+      for (int u = 0; u < 8; ++u) {
+        const float2 z = zs2[j + u];
+        df_mul_acc(acc[u & 1], {b[u], 0.0f}, {z.x, z.y});
+      }
+      df_renorm(acc[0]);
+      df_renorm(acc[1]);
     }
-    for (; j < k; ++j) acc[0] = fma(double(B[i + size_t(j) * k]), zs[j], acc[0]);
-    zout[off + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    for (; j < k; ++j) {
+      const float2 z = zs2[j];
+      df_mul_acc(acc[0], {B[i + size_t(j) * k], 0.0f}, {z.x, z.y});
+    }
+    zout[off + i] = (double(acc[0].h) + double(acc[0].l)) + (double(acc[1].h) + double(acc[1].l));
   }
+}
+
+// Sum of squares of x (len), in fixed order: block b sums the elements b * 256 + t, + grid
+// stride, reduced in shared memory; nrm_finish_kernel adds the kNrmBlocks partials in order.
+constexpr int kNrmBlocks = 256;
+__global__ void nrm_partial_kernel(long len, const double *x, double *part) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (long i = long(blockIdx.x) * 256 + threadIdx.x; i < len; i += long(kNrmBlocks) * 256)
+    a = fma(x[i], x[i], a);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void nrm_finish_kernel(double *part) {
+  __shared__ double red[kNrmBlocks];
+  red[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int st = kNrmBlocks / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[0] = red[0];
 }
 
 // Newton-Schulz step of the preconditioner inverse: T = P X (per vesicle, k x k) is replaced in
@@ -1390,7 +1435,7 @@ struct FmmPlanJob {
 int precond_apply(stokes_sim *m, const double *zin, double *zout) {
   const int k = 3 * m->n;
   if (m->precond_fp32) {
-    precond32_apply_kernel<<<m->V, std::min(k, 1024), sizeof(double) * k, m->s>>>(k, m->d_Pinv32,
+    precond32_apply_kernel<<<m->V, std::min(k, 1024), sizeof(float2) * k, m->s>>>(k, m->d_Pinv32,
                                                                                   zin, zout);
     SK(cudaGetLastError());
     return STOKES_OK;
@@ -1517,10 +1562,17 @@ int precond_build(stokes_sim *m, double dt) {
   return STOKES_OK;
 }
 
+// ||x||_2 (len doubles, device), synchronous: two fixed-order reduction kernels and one 8-byte
+// read back.  (The sums of squares of the step's O(1) unknowns are far from FP64's range ends.)
 double dnrm(stokes_sim *m, long len, const double *x, int *st) {
   double r = 0.0;
-  if (cublasDnrm2(m->blas, int(len), x, 1, &r) != CUBLAS_STATUS_SUCCESS) *st = STOKES_ERR_CUDA;
-  return r;
+  nrm_partial_kernel<<<kNrmBlocks, 256, 0, m->s>>>(len, x, m->d_nrm_part);
+  nrm_finish_kernel<<<1, kNrmBlocks, 0, m->s>>>(m->d_nrm_part);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&r, m->d_nrm_part, sizeof(double), cudaMemcpyDeviceToHost, m->s) != cudaSuccess ||
+      cudaStreamSynchronize(m->s) != cudaSuccess)
+    *st = STOKES_ERR_CUDA;
+  return sqrt(r);
 }
 
 // Right-preconditioned restarted GMRES (classical Gram-Schmidt, twice) on z; FP64.
@@ -1530,7 +1582,7 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
   const int mr = m->gm_m;
   int st = STOKES_OK;
   const double bn = dnrm(m, len, b, &st);
-  if (st) return fail(m, st, "cublasDnrm2 failed");
+  if (st) return fail(m, st, "norm reduction failed");
   *iters = 0;
   *relres = 0.0;
   if (bn == 0.0) {
@@ -1549,7 +1601,7 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
     }
     x_zero = false;
     const double beta = dnrm(m, len, m->d_V, &st);
-    if (st) return fail(m, st, "cublasDnrm2 failed");
+    if (st) return fail(m, st, "norm reduction failed");
     *relres = beta / bn;
     if (*relres <= tol) return STOKES_OK;
     if (*iters >= max_iter) return fail(m, STOKES_ERR_NOT_CONVERGED, "GMRES: %d iterations, relative residual %.3e", *iters, *relres);
@@ -1574,7 +1626,7 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
                      vn, 1));
       SK(cudaMemcpyAsync(hcol2.data(), m->d_h, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, m->s));
       const double hn = dnrm(m, len, vn, &st);  // synchronises the stream
-      if (st) return fail(m, st, "cublasDnrm2 failed");
+      if (st) return fail(m, st, "norm reduction failed");
       for (int q = 0; q <= j; ++q) hcol[q] += hcol2[q];
       hcol[j + 1] = hn;
       if (hn > 0.0) {
@@ -1700,7 +1752,8 @@ int stokes_sim_create(int device, stokes_sim **out) {
       cublasCreate(&m->blas) != CUBLAS_STATUS_SUCCESS ||
       cusolverDnCreate(&m->sol) != CUSOLVER_STATUS_SUCCESS ||
       cusolverDnCreateParams(&m->params) != CUSOLVER_STATUS_SUCCESS ||
-      cudaMalloc(reinterpret_cast<void **>(&m->d_info), sizeof(int)) != cudaSuccess) {
+      cudaMalloc(reinterpret_cast<void **>(&m->d_info), sizeof(int)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void **>(&m->d_nrm_part), sizeof(double) * kNrmBlocks) != cudaSuccess) {
     delete m;
     return STOKES_ERR_CUDA;
   }
@@ -1719,6 +1772,7 @@ int stokes_sim_destroy(stokes_sim *m) {
   free_walls(m);
   free_vesicles(m);
   dfree(m->d_info);
+  dfree(m->d_nrm_part);
   if (m->blas) cublasDestroy(m->blas);
   if (m->params) cusolverDnDestroyParams(m->params);
   if (m->sol) cusolverDnDestroy(m->sol);
@@ -2305,7 +2359,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     // operator then finishes from the refined iterate to tol.
     int st = STOKES_OK;
     const double bn = dnrm(m, len, m->d_b, &st);
-    if (st) return fail(m, st, "cublasDnrm2 failed");
+    if (st) return fail(m, st, "norm reduction failed");
     const double one = 1.0, mone = -1.0;
     double prev = 1e300;
     bool finish64 = false;
@@ -2330,7 +2384,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
       }
       zero_iterate = false;
       const double rn = dnrm(m, len, m->d_rr, &st);
-      if (st) return fail(m, st, "cublasDnrm2 failed");
+      if (st) return fail(m, st, "norm reduction failed");
       rel = bn > 0.0 ? rn / bn : 0.0;
       const bool was_rough = rough;
       rough = false;
