@@ -411,12 +411,13 @@ def run_step(args):
     fmm = args.residual_fmm
     sweep = args.sweep_fmm
     refresh = args.precond_refresh
+    base = args.warm_base
     hist = not args.no_warm_history
     res = {"workload": args.step_workload, "dt": dt, "p_drive": pd, "kappa_b": kb, "tol": 1e-10,
            "precisions": precs, "collect_precision": args.collect_precision or
            ("fp32k" if big else "fp64"), "warm_modes": nets_modes,
            "residual_fmm_order": fmm, "sweep_fmm_order": sweep, "precond_refresh": refresh,
-           "history_features": hist}
+           "warm_base": base, "history_features": hist}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
@@ -424,7 +425,7 @@ def run_step(args):
         torch.cuda.synchronize()
         ts = time.perf_counter()
         sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm,
-                            history=hist, sweep_fmm=sweep, precond_refresh=refresh)
+                            history=hist, sweep_fmm=sweep, precond_refresh=refresh, base=base)
         torch.cuda.synchronize()
         res.setdefault("setup_s", time.perf_counter() - ts)
         res.setdefault("wall_solve", dict(zip(("refinements", "residual"),
@@ -453,7 +454,7 @@ def run_step(args):
     del X, T, Xs, Ts
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
     sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm, history=hist,
-                        sweep_fmm=sweep, precond_refresh=refresh)
+                        sweep_fmm=sweep, precond_refresh=refresh, base=base)
     x0, s0, _ = sim.state()
     evs = {}
     for p in precs:
@@ -487,7 +488,7 @@ def run_step(args):
                        "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w,
                        "training_states": int(res["train"][nets_modes[0]]["samples"]),
                        "warm_modes": nets_modes, "residual_fmm_order": fmm,
-                       "sweep_fmm_order": sweep, "precond_refresh": refresh},
+                       "sweep_fmm_order": sweep, "precond_refresh": refresh, "warm_base": base},
             "iterations_saved_vs_zero": {p: {k: ev["zero"]["mean_iterations"] - v["mean_iterations"]
                                              for k, v in ev.items()} for p, ev in evs.items()},
             "by_precision": {p: summary(ev) for p, ev in evs.items()},
@@ -953,6 +954,8 @@ def main():
     ap.add_argument("--close-factor", type=float, default=5.0)
     ap.add_argument("--no-warm-history", action="store_true",
                     help="warm-start features without the previous solution and its last change")
+    ap.add_argument("--warm-base", default="previous", choices=["previous", "extrapolate"],
+                    help="--step: what the network's predicted change is added to (and trained on)")
     ap.add_argument("--step-one", action="store_true",
                     help="one zero-guess step of the --step held-out channel after --warmup steps, "
                          "between cudaProfilerStart/Stop")
