@@ -260,9 +260,23 @@ typedef struct {
 } stokes_fmm_info;
 
 STOKES_API int stokes_fmm_create(stokes_ctx *ctx, int order, int leaf_size, stokes_fmm **out);
+/* A plan that also evaluates at n_targets free points (DEVICE array, 2 n_targets doubles,
+ * (x, y) pairs, read once at creation; 1 <= n_targets <= 2^26): stokes_fmm_eval_targets then
+ * gives the velocity there -- the near-image pair sum of stokes_sum_eval_targets, no self
+ * terms -- to the plan's accuracy; stokes_fmm_eval still gives the node sum.  The points are
+ * part of the plan (its target tree), so a new set needs a new plan.  STOKES_ERR_NONFINITE for
+ * a non-finite point; otherwise as stokes_fmm_create. */
+STOKES_API int stokes_fmm_create_targets(stokes_ctx *ctx, int order, int leaf_size, int n_targets,
+                                         const double *targets, stokes_fmm **out);
 STOKES_API int stokes_fmm_eval(stokes_fmm *fmm, const double *slp_density,
                                const double *dlp_density, double jump, double *out_velocity,
                                void *stream);
+/* The velocity at the plan's free targets (out_velocity: 2 n_targets doubles, DEVICE, 16-byte
+ * aligned), densities as stokes_fmm_eval; the node targets are not evaluated.  Asynchronous on
+ * `stream`.  STOKES_ERR_ARG for a plan without free targets. */
+STOKES_API int stokes_fmm_eval_targets(stokes_fmm *fmm, const double *slp_density,
+                                       const double *dlp_density, double *out_velocity,
+                                       void *stream);
 /* Order of the following evaluations of this plan: 4 <= order <= the plan's order, or 0 for
  * the plan's order (the default).  The expansions are truncated at that order (the plan's
  * tree, lists and buffers are unchanged), so one plan serves a cheaper, less accurate

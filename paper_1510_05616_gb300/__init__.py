@@ -82,6 +82,8 @@ _SIGNATURES = {
     "stokes_fmm_create": [_vp, _c_int, _c_int, ctypes.POINTER(_vp)],
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
+    "stokes_fmm_create_targets": [_vp, _c_int, _c_int, _c_int, _vp, _vp],
+    "stokes_fmm_eval_targets": [_vp, _vp, _vp, _vp, _vp],
     "stokes_fmm_set_eval_order": [_vp, _c_int],
     "stokes_fmm_set_precision": [_vp, _c_int],
     "stokes_fmm_last_error": [_vp, ctypes.c_char_p, ctypes.c_size_t],
@@ -351,6 +353,26 @@ def _fmm_err(f) -> str:
     if f:
         load().stokes_fmm_last_error(f, buf, 512)
     return buf.value.decode(errors="replace")
+
+
+def stokes_fmm_create_targets(h, targets, order=24, leaf_size=32):
+    """FMM plan of context h that also evaluates at the free points `targets` (device, (T, 2))."""
+    f = _vp()
+    code = load().stokes_fmm_create_targets(h, int(order), int(leaf_size), int(targets.shape[0]),
+                                            _dptr(targets, "targets", (2,)), ctypes.byref(f))
+    if code != STOKES_OK:
+        raise StokesError(code, _err(h))
+    return f
+
+
+def stokes_fmm_eval_targets(f, slp_density, dlp_density, out_velocity, stream=None):
+    """Velocity at the plan's free targets into out_velocity (device, (T, 2))."""
+    code = load().stokes_fmm_eval_targets(f, _dptr(slp_density, "slp_density", (2,), True),
+                                          _dptr(dlp_density, "dlp_density", (2,), True),
+                                          _dptr(out_velocity, "out_velocity", (2,)), _stream(stream))
+    if code != STOKES_OK:
+        raise StokesError(code, _fmm_err(f))
+    return code
 
 
 def stokes_fmm_eval(f, slp_density, dlp_density, jump, out_velocity, stream=None):

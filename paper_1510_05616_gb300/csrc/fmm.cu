@@ -173,7 +173,9 @@ __device__ __forceinline__ void charges(bool wall, double2 w, double4_32a v, dou
 }
 
 struct FmmDev {
-  int p, n_src, N;            // p: the evaluation's expansion order
+  int p, n_src, N;            // p: the evaluation's expansion order; N: the context's nodes
+  int want_nodes;             // 0: only the extra targets are wanted (node targets skipped)
+  double2 *out_extra;         // [targets N ..] free-target velocities, or NULL (not wanted)
   int near32;                 // near-field pairs in FP32 arithmetic (accumulated in FP64)
   int tp1;                    // row length of tpow: the plan's order + 1
   int wall_slots;
@@ -188,7 +190,7 @@ struct FmmDev {
   const int *nl_off, *nl_idx; // near lists of target leaves (source leaf indices)
   const int *tgt_node;        // [N] node of each sorted target
   const int2 *tleaf_rng;      // [target leaves] range of sorted targets
-  const double2 *x;           // [N] node positions
+  const double2 *x;           // [N + extra] target positions: the nodes, then the free targets
   double2 *M;                 // [source cells][kSets][p + 1], FP64 or (FP32 evaluations) float2
   double2 *Lc;                // [target cells][kSets][p + 1], likewise
   double2 *out;               // [N] pair sums (node order)
@@ -598,6 +600,9 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
   const int nb0 = f.nl_off[leaf0 + leaf], nb1 = f.nl_off[leaf0 + leaf + 1];
   for (int it = trg.x + threadIdx.x; it < trg.y; it += blockDim.x) {
     const int node = f.tgt_node[it];
+    // targets past the nodes are the plan's free targets: no own curve (node_curve -1), and
+    // their velocity is the pair sum itself (no self terms), written to out_extra
+    if (node < f.N ? !f.want_nodes : !f.out_extra) continue;
     const double2 z = f.x[node];
     const int tcur = f.node_curve[node];
     const C u = mkc<R>((z.x - ct.x) * inv_h, (z.y - ct.y) * inv_h);
@@ -695,7 +700,10 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_kernel(FmmDev f, int tcell0
     double2 dl = cadd(d1[4], cconj(d1[3]));
     dl = cadd(dl, cconj(make_double2(w5.x - zc_d2.x, w5.y - zc_d2.y)));
     s = cadd(s, cscale(dl, 0.25));
-    f.out[node] = make_double2(s.x + ux, s.y + uy);
+    if (node < f.N)
+      f.out[node] = make_double2(s.x + ux, s.y + uy);
+    else
+      f.out_extra[node - f.N] = make_double2(s.x + ux, s.y + uy);
   }
 }
 
@@ -785,6 +793,8 @@ struct stokes_fmm {
   float4 *d_m2m_df = nullptr;  // M2M shift weights per child quadrant, double-float (see m2m_kernel)
   float4 *d_tpow_df = nullptr, *d_Mf = nullptr;  // double-float copies for m2l_df_kernel
   int *d_src_own = nullptr, *d_node_curve = nullptr;
+  int n_extra = 0;                // free targets after the nodes
+  double2 *d_tx = nullptr;        // [N + n_extra] target positions
   // the geometry the plan was made for
   unsigned long long generation = 0;
   std::string err;
@@ -867,6 +877,7 @@ void free_plan(stokes_fmm *f) {
   void *ps[] = {f->d_src_slot, f->d_src_pos, f->d_sc_ctr, f->d_tc_ctr, f->d_sc_rng,
                 f->d_tleaf_rng, f->d_tc_par, f->d_il_off, f->d_il_idx, f->d_nl_off,
                 f->d_nl_idx, f->d_tgt_node, f->d_M, f->d_Lc, f->d_tpow, f->d_tlog, f->d_src_own, f->d_node_curve,
+                f->d_tx,
                 f->d_m2m_df, f->d_tpow_df, f->d_Mf};
   for (void *q : ps) cudaFree(q);
 }
@@ -1091,19 +1102,26 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   ph.pos_sorted = pos_sorted;
 }
 
-int build_plan(stokes_fmm *f, int leaf_target) {
+int build_plan(stokes_fmm *f, int leaf_target, int n_extra, const double2 *extra) {
   stokes_ctx *c = f->ctx;
   const int N = c->N;
   const int slots = c->wall_slots_f64 + c->ves_slots_f64;
-  std::vector<double2> x(N), spos(slots);
+  std::vector<double2> x(size_t(N) + n_extra), spos(slots);
   std::vector<int> snode(slots);
-  if (cudaMemcpy(x.data(), c->d_x, sizeof(double2) * N, cudaMemcpyDeviceToHost) != cudaSuccess ||
+  if ((n_extra > 0 && cudaMemcpy(x.data() + N, extra, sizeof(double2) * n_extra,
+                                 cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      cudaMemcpy(x.data(), c->d_x, sizeof(double2) * N, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(spos.data(), c->d_src_pos64, sizeof(double2) * slots, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(snode.data(), c->d_slot_node64, sizeof(int) * slots, cudaMemcpyDeviceToHost) != cudaSuccess) {
     f->err = "fmm: reading the geometry failed";
     return STOKES_ERR_CUDA;
   }
-  std::vector<int> node_curve(N, -1);
+  for (int i = 0; i < n_extra; ++i)
+    if (!isfinite(x[N + i].x) || !isfinite(x[N + i].y)) {
+      f->err = "fmm: a free target is not finite";
+      return STOKES_ERR_NONFINITE;
+    }
+  std::vector<int> node_curve(size_t(N) + n_extra, -1);
   for (int cv = 0; cv < c->n_curves; ++cv)
     if (c->kind[cv] == STOKES_KIND_VESICLE)
       for (int i = c->off[cv]; i < c->off[cv + 1]; ++i) node_curve[i] = cv;
@@ -1145,6 +1163,8 @@ int build_plan(stokes_fmm *f, int leaf_target) {
   up(upload(f->d_tleaf_rng, tleaf_rng, bytes));
   up(upload(f->d_src_own, ph.src_own, bytes));
   up(upload(f->d_node_curve, node_curve, bytes));
+  up(upload(f->d_tx, x, bytes));
+  f->n_extra = n_extra;
   {  // t^-n and log(-t) of the integer offsets t = (dx, dy), |dx|, |dy| <= 3
     const int p1 = f->p + 1;
     std::vector<double2> tpow(49 * p1), tlog(49);
@@ -1246,12 +1266,14 @@ int fmm_fail(stokes_fmm *f, int code, const std::string &msg) {
 
 extern "C" {
 
-int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out) {
+static int fmm_create(stokes_ctx *c, int order, int leaf_size, int n_extra, const double *extra,
+                      stokes_fmm **out) {
   if (!out) return STOKES_ERR_ARG;
   *out = nullptr;
   if (!c) return STOKES_ERR_ARG;
   if (!c->have_geom) return STOKES_ERR_NO_GEOM;
-  if (c->n_inst != 1 || order < 4 || order > kMaxOrder || leaf_size < 4 || leaf_size > 4096)
+  if (c->n_inst != 1 || order < 4 || order > kMaxOrder || leaf_size < 4 || leaf_size > 4096 ||
+      n_extra < 0 || (n_extra > 0 && !extra) || n_extra > (1 << 26))
     return STOKES_ERR_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return STOKES_ERR_CUDA;
   const auto t0 = std::chrono::steady_clock::now();
@@ -1265,7 +1287,7 @@ int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out)
   stokes_fmm *f = new stokes_fmm();
   f->ctx = c;
   f->p = order;
-  const int st = build_plan(f, leaf_size);
+  const int st = build_plan(f, leaf_size, n_extra, reinterpret_cast<const double2 *>(extra));
   if (st) {
     c->err = f->err;
     free_plan(f);
@@ -1280,16 +1302,34 @@ int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out)
   return STOKES_OK;
 }
 
-int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double jump, double *out,
-                    void *stream) {
+int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out) {
+  return fmm_create(c, order, leaf_size, 0, nullptr, out);
+}
+
+int stokes_fmm_create_targets(stokes_ctx *c, int order, int leaf_size, int n_targets,
+                              const double *targets, stokes_fmm **out) {
+  if (n_targets < 1) {
+    if (out) *out = nullptr;
+    return STOKES_ERR_ARG;
+  }
+  return fmm_create(c, order, leaf_size, n_targets, targets, out);
+}
+
+// An evaluation: the node sum into out (with the self terms, the curvature diagonal and the
+// jump) when out is given, the free targets' velocities into out_targets when given.
+static int fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double jump, double *out,
+                    double *out_targets, void *stream) {
   if (!f) return STOKES_ERR_ARG;
   stokes_ctx *c = f->ctx;
   if (!c->have_geom || generation_of(c) != f->generation || c->N != f->N)
     return fmm_fail(f, STOKES_ERR_NO_GEOM, "the context's geometry changed since the plan was made");
-  if ((c->n_ves_nodes > 0 && !slp) || (c->n_wall_nodes > 0 && !dlp) || !out ||
-      (reinterpret_cast<uintptr_t>(out) & 15u) || !isfinite(jump))
-    return fmm_fail(f, STOKES_ERR_ARG, "need the densities of every kind present, a 16-byte aligned "
-                                       "output and a finite jump");
+  if ((c->n_ves_nodes > 0 && !slp) || (c->n_wall_nodes > 0 && !dlp) || (!out && !out_targets) ||
+      (reinterpret_cast<uintptr_t>(out) & 15u) || (reinterpret_cast<uintptr_t>(out_targets) & 15u) ||
+      !isfinite(jump))
+    return fmm_fail(f, STOKES_ERR_ARG, "need the densities of every kind present, 16-byte aligned "
+                                       "outputs and a finite jump");
+  if (out_targets && f->n_extra == 0)
+    return fmm_fail(f, STOKES_ERR_ARG, "the plan was made without free targets");
   FMK(cudaSetDevice(c->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int N = c->N;
@@ -1302,7 +1342,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     FMK(cudaMalloc(reinterpret_cast<void **>(&c->d_partial), sizeof(double2) * N));
     c->partial_cap = N;
   }
-  if (c->n_ves_curves > 0) {
+  const bool self = out && c->n_ves_curves > 0;  // the Kress self terms of the node sum
+  if (self) {
     FMK(cudaEventRecord(c->ev_fork, s));
     FMK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
     FMK(launch_self(c, slp, c->side_stream));
@@ -1320,6 +1361,8 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.tpow_df = f->d_tpow_df;
   d.n_src = f->n_src;
   d.N = N;
+  d.want_nodes = out ? 1 : 0;
+  d.out_extra = reinterpret_cast<double2 *>(out_targets);
   d.wall_slots = c->wall_slots_f64;
   d.src_slot = f->d_src_slot;
   d.src_pos = f->d_src_pos;
@@ -1334,7 +1377,7 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
   d.nl_idx = f->d_nl_idx;
   d.tgt_node = f->d_tgt_node;
   d.tleaf_rng = f->d_tleaf_rng;
-  d.x = c->d_x;
+  d.x = f->d_tx;
   d.M = f->d_M;
   d.Lc = f->d_Lc;
   d.out = c->d_partial;
@@ -1382,7 +1425,7 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
     passes(0.0f);
   else
     passes(0.0);
-  if (c->n_ves_curves > 0) {
+  if (out && c->n_ves_curves > 0) {
     Binning bn;
     bn.x0 = f->x0;
     bn.y0 = f->y0;
@@ -1400,10 +1443,23 @@ int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
                                                               1.0 / (4.0 * kPiF * c->mu), bn, c->d_partial);
   }
   FMK(cudaGetLastError());
-  if (c->n_ves_curves > 0) FMK(cudaStreamWaitEvent(s, c->ev_join, 0));
-  FMK(launch_finish_nodes(c, 1, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
+  if (self) FMK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  if (out) FMK(launch_finish_nodes(c, 1, slp, dlp, jump, reinterpret_cast<double2 *>(out), s));
   return STOKES_OK;
 }
+
+int stokes_fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double jump, double *out,
+                    void *stream) {
+  if (!out) return fmm_fail(f, STOKES_ERR_ARG, "need an output");
+  return fmm_eval(f, slp, dlp, jump, out, nullptr, stream);
+}
+
+int stokes_fmm_eval_targets(stokes_fmm *f, const double *slp, const double *dlp, double *out_targets,
+                            void *stream) {
+  if (!out_targets) return fmm_fail(f, STOKES_ERR_ARG, "need an output");
+  return fmm_eval(f, slp, dlp, 0.0, nullptr, out_targets, stream);
+}
+
 
 int stokes_fmm_set_eval_order(stokes_fmm *f, int order) {
   if (!f) return STOKES_ERR_ARG;

@@ -139,6 +139,10 @@ struct stokes_sim {
   // from an FMM plan of the fixed walls, made at the first such step after stokes_sim_set_walls
   stokes_fmm *fmm_w = nullptr;
   int fmm_w_order = 0;
+  // ... and the channel response's two vesicle-wall sums from per-step plans with the other
+  // kind's nodes as free targets: vesicle sources at the wall nodes, wall sources at the
+  // vesicle nodes
+  stokes_fmm *fmm_vw = nullptr, *fmm_wv = nullptr;
   // close evaluation of the vesicle-vesicle single layer (stokes_sim_set_close_eval): every
   // vesicle sum of the step adds the correction of the close (node, vesicle image) pairs found
   // for the step's positions; factor 0 = off
@@ -1306,12 +1310,28 @@ int refined_block_solve(stokes_sim *m, int prec, int fmm_order = 0) {
 
 // Channel response to vesicle forces f (device, Nv x 2): u_resp at the vesicle nodes.  The
 // pair sums run in `prec` (STOKES_FP64 or the equally accurate STOKES_DOUBLE_FLOAT).
+// The free-target evaluation of a response plan (fmm_vw, fmm_wv), as fmm_sum.
+int fmm_targets(stokes_sim *m, stokes_fmm *f, const double *slp, const double *dlp, double *out,
+                const char *what) {
+  const int st = stokes_fmm_eval_targets(f, slp, dlp, out, m->s);
+  if (st) {
+    char buf[256];
+    stokes_fmm_last_error(f, buf, sizeof(buf));
+    return fail(m, st, "%s: %s", what, buf);
+  }
+  return STOKES_OK;
+}
+
 int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u_out,
                      int prec = STOKES_FP64, int fmm_order = 0) {
   const double cmu = 1.0 / (4.0 * kPiD * m->mu);
   // v = -S^near f at the wall nodes (vesicle sums at free targets)
-  ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
-                             m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
+  if (fmm_order > 0 && m->fmm_vw)
+    ST(fmm_targets(m, m->fmm_vw, reinterpret_cast<const double *>(f), nullptr, m->d_vrhs,
+                   "FMM vesicle-to-wall sum"));
+  else
+    ST(stokes_sum_eval_targets(m->ctx_v, prec, reinterpret_cast<const double *>(f), nullptr,
+                               m->Nt, reinterpret_cast<const double *>(m->d_wx), m->d_vrhs, m->s));
   side_rhs_kernel<<<dim3(m->K, kSideChunks), 256, 0, m->s>>>(m->K, m->Nv, m->d_side, m->d_x, m->d_w,
                                                             f, m->period, cmu, m->d_side_part);
   side_rhs_finish_kernel<<<nb(m->K, 128), 128, 0, m->s>>>(m->K, m->d_side_part, p_drive, m->d_rg);
@@ -1320,9 +1340,13 @@ int channel_response(stokes_sim *m, const double2 *f, double p_drive, double2 *u
   SK(cudaGetLastError());
   ST(refined_block_solve(m, prec, fmm_order));
   // u_resp = D^near tau + sum_m c_m S(., y_m) at the vesicle nodes
-  ST(stokes_sum_eval_targets(m->ctx_w, prec, nullptr, m->d_tau, m->Nv,
-                             reinterpret_cast<const double *>(m->d_x),
-                             reinterpret_cast<double *>(u_out), m->s));
+  if (fmm_order > 0 && m->fmm_wv)
+    ST(fmm_targets(m, m->fmm_wv, nullptr, m->d_tau, reinterpret_cast<double *>(u_out),
+                   "FMM wall-to-vesicle sum"));
+  else
+    ST(stokes_sum_eval_targets(m->ctx_w, prec, nullptr, m->d_tau, m->Nv,
+                               reinterpret_cast<const double *>(m->d_x),
+                               reinterpret_cast<double *>(u_out), m->s));
   proxy_eval_kernel<<<nb(m->Nv, 128), 128, 0, m->s>>>(m->Nv, m->d_x, m->M, m->d_proxy, m->d_c,
                                                       cmu, u_out);
   SK(cudaGetLastError());
@@ -1405,15 +1429,18 @@ struct FmmPlanJob {
   stokes_fmm *plan = nullptr;
   int status = STOKES_OK;
   double ms = 0.0;
-  void start(stokes_sim *m) {
-    th = std::thread([this, m] {
+  // A plan of ctx at `order`, with n_extra free targets (device points) when n_extra > 0.
+  void start(stokes_sim *m, stokes_ctx *ctx, int order, int n_extra = 0,
+             const double *extra = nullptr) {
+    th = std::thread([this, m, ctx, order, n_extra, extra] {
       const auto t0 = std::chrono::steady_clock::now();
       if (cudaSetDevice(m->device) != cudaSuccess) {
         status = STOKES_ERR_CUDA;
         return;
       }
-      status = stokes_fmm_create(m->ctx_v, std::max(m->resid_fmm_order, m->sweep_fmm_order),
-                                 m->resid_fmm_leaf, &plan);
+      status = n_extra > 0
+                   ? stokes_fmm_create_targets(ctx, order, m->resid_fmm_leaf, n_extra, extra, &plan)
+                   : stokes_fmm_create(ctx, order, m->resid_fmm_leaf, &plan);
       ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });
   }
@@ -1670,8 +1697,11 @@ int gmres(stokes_sim *m, double dt, int precision, const double *b, double *x, d
 }
 
 void free_walls(stokes_sim *m) {
-  if (m->fmm_w) stokes_fmm_destroy(m->fmm_w);  // before its context
-  m->fmm_w = nullptr;
+  for (stokes_fmm **pl : {&m->fmm_w, &m->fmm_vw, &m->fmm_wv})  // before their contexts
+    if (*pl) {
+      stokes_fmm_destroy(*pl);
+      *pl = nullptr;
+    }
   m->fmm_w_order = 0;
   if (m->ctx_w) stokes_destroy(m->ctx_w);
   m->ctx_w = nullptr;
@@ -1702,8 +1732,11 @@ void free_walls(stokes_sim *m) {
 }
 
 void free_vesicles(stokes_sim *m) {
-  if (m->fmm_v) stokes_fmm_destroy(m->fmm_v);
-  m->fmm_v = nullptr;
+  for (stokes_fmm **pl : {&m->fmm_v, &m->fmm_vw, &m->fmm_wv})
+    if (*pl) {
+      stokes_fmm_destroy(*pl);
+      *pl = nullptr;
+    }
   if (m->close_v) stokes_close_destroy(m->close_v);
   m->close_v = nullptr;
   if (m->ctx_v) stokes_destroy(m->ctx_v);
@@ -2266,10 +2299,13 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   const auto t0 = std::chrono::steady_clock::now();
   const int V = m->V, n = m->n;
   const long len = 3L * m->Nv;
-  if (m->fmm_v) {  // last step's plan: its geometry is gone
-    stokes_fmm_destroy(m->fmm_v);
-    m->fmm_v = nullptr;
-  }
+  for (stokes_fmm **pl : {&m->fmm_v, &m->fmm_vw, &m->fmm_wv})  // last step's plans: the
+    if (*pl) {                                                  // geometry they hold is gone
+      stokes_fmm_destroy(*pl);
+      *pl = nullptr;
+    }
+  // with FMM residuals and walls, the channel response's vesicle-wall sums by FMM as well
+  const bool resp_fmm = use_fmm && m->have_walls;
   // geometry at x^k (weights/normals feed the sums)
   ves_geom_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_D, m->d_spd, m->d_xs, m->d_nrm, m->d_w);
   SK(cudaGetLastError());
@@ -2279,10 +2315,15 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     stokes_close_destroy(m->close_v);
     m->close_v = nullptr;
   }
-  FmmPlanJob plan_job;
+  FmmPlanJob plan_job, plan_vw, plan_wv;
   if (use_plan || m->close_factor > 0.0)
     SK(cudaStreamSynchronize(m->s));  // the plans read the updated geometry
-  if (use_plan) plan_job.start(m);
+  if (use_plan)
+    plan_job.start(m, m->ctx_v, std::max(m->resid_fmm_order, m->sweep_fmm_order));
+  if (resp_fmm) {
+    plan_vw.start(m, m->ctx_v, m->resid_fmm_order, m->Nt, reinterpret_cast<const double *>(m->d_wx));
+    plan_wv.start(m, m->ctx_w, m->resid_fmm_order, m->Nv, reinterpret_cast<const double *>(m->d_x));
+  }
   if (m->close_factor > 0.0) {
     const int cst = stokes_close_create(m->ctx_v, m->close_factor, m->close_K, &m->close_v);
     if (cst) return fail(m, cst, "close-evaluation pairs: %s", m->ctx_v->err.c_str());
@@ -2291,7 +2332,18 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   ves_forces_kernel<<<V, n, 0, m->s>>>(n, m->d_x, m->d_sigma, m->d_D, m->d_spd, m->d_xs, m->kappa_b,
                                        m->d_fb, m->d_f);
   SK(cudaGetLastError());
+  // the block-diagonal self preconditioner of step 6 (geometry and dt only): built here, while
+  // host threads build this step's FMM plans
+  ST(precond_build(m, dt));
   // steps 3-5: channel response of the explicit forces
+  if (resp_fmm) {
+    int pst = plan_vw.join();
+    if (!pst) pst = plan_wv.join();
+    if (pst) return fail(m, pst, "FMM plans of the channel response failed (%s / %s)",
+                         m->ctx_v->err.c_str(), m->ctx_w->err.c_str());
+    m->fmm_vw = plan_vw.take();
+    m->fmm_wv = plan_wv.take();
+  }
   if (m->have_walls)
     ST(channel_response(m, m->d_f, p_drive, m->d_ures, hp, use_fmm ? m->resid_fmm_order : 0));
   // right-hand side [S f_b + u_resp; ALC]
@@ -2320,7 +2372,6 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     SK(cudaGetLastError());
   }
   // step 6: GMRES with the block-diagonal self preconditioner, from the chosen initial iterate
-  ST(precond_build(m, dt));
   if (guess_mode == STOKES_GUESS_USER) {
     SK(cudaMemcpyAsync(m->d_xsol, guess, sizeof(double) * len, cudaMemcpyDeviceToDevice, m->s));
   } else if (guess_mode == STOKES_GUESS_MLP && m->warm_base == STOKES_WARM_BASE_EXTRAPOLATE &&

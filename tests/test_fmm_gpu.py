@@ -186,6 +186,46 @@ def test_fmm_fp32_evaluation(P):
         assert e64 < 1e-3 and abs(e32 - e64) <= 0.1 * e64 + 2e-6, (order, e64, e32)
 
 
+@pytest.mark.parametrize("kind", ["vesicles", "walls"])
+def test_fmm_free_targets_match_direct_free_point_sum(P, kind):
+    """A plan with free targets (stokes_fmm_create_targets) gives, at those points, the direct
+    free-point sum of stokes_sum_eval_targets (double-float) to the expansion error: the
+    vesicles' single layer at the walls' nodes, and the walls' double layer at the vesicles'
+    nodes -- the two sums of the channel response.  The same plan's node evaluation still meets
+    the direct node sum to the expansion error (the free targets widen the forest, so its tree
+    -- and the truncation error -- differs from the nodes-only plan's)."""
+    import torch
+    g, slp, dlp = I.workload("mid_n16k")
+    ves = [c for c in g.curves if c.kind == I.KIND_SLP]
+    walls = [c for c in g.curves if c.kind == I.KIND_DLP]
+    if kind == "vesicles":
+        gs, other, ds, dd = I.Geometry(ves, g.period, g.mu, {}), walls, dev(slp), None
+    else:
+        gs, other, ds, dd = I.Geometry(walls, g.period, g.mu, {}), ves, None, dev(dlp)
+    tg = dev(np.vstack([c.nodes for c in other]))
+    s = P.StokesSum(gs)
+    ref = s.eval_targets(ds, dd, tg, precision="df").cpu().numpy()
+    node_ref = s.eval(ds, dd, precision="df").cpu().numpy()
+    f = P.stokes_fmm_create_targets(s.h, tg, 28, 32)
+    try:
+        out = torch.zeros_like(tg)
+        P.stokes_fmm_eval_targets(f, ds, dd, out)
+        nodes = torch.zeros((s.N, 2), dtype=torch.float64, device="cuda")
+        P.stokes_fmm_eval(f, ds, dd, 0.0, nodes)
+        P.stokes_sync(s.h)
+        err = rel(out.cpu().numpy(), ref)
+        assert err < 1e-9, err
+        assert rel(nodes.cpu().numpy(), node_ref) < 1e-9
+    finally:
+        P.stokes_fmm_destroy(f)
+    f0 = P.stokes_fmm_create(s.h, 20, 32)
+    with pytest.raises(P.StokesError):  # no free targets in this plan
+        P.stokes_fmm_eval_targets(f0, ds, dd, torch.zeros_like(tg))
+    P.stokes_fmm_destroy(f0)
+    s.close()
+    print("free targets (%s sources): %.2e" % (kind, err))
+
+
 def test_fmm_high_order_converges(P):
     """Orders above 30 (shared memory sized by the order) keep converging: at order 36 the FMM
     meets the double-float direct sum to 1e-11 on the 16k channel."""
