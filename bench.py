@@ -361,7 +361,8 @@ def run_step_one(args):
     pd = 2 * 1.0 * 2 * math.pi * 0.2
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=1.0)
     sim = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=args.residual_fmm,
-                        sweep_fmm=args.sweep_fmm, precond_refresh=args.precond_refresh)
+                        sweep_fmm=args.sweep_fmm, precond_refresh=args.precond_refresh,
+                        precond_tensor=args.precond_tensor)
     for _ in range(args.warmup):
         sim.step(1e-3, pd, "zero", precision=P.STOKES_FP32_KAHAN)
     torch.cuda.synchronize()
@@ -375,7 +376,8 @@ def run_step_one(args):
                       "config": {"workload": WORKLOAD_DESCS[args.step_workload],
                                  "residual_fmm_order": args.residual_fmm,
                                  "sweep_fmm_order": args.sweep_fmm,
-                                 "precond_refresh": bool(args.precond_refresh)},
+                                 "precond_refresh": bool(args.precond_refresh),
+                                 "precond_tensor": bool(args.precond_tensor)},
                       "stats": st}))
     return 0
 
@@ -417,7 +419,7 @@ def run_step(args):
            "precisions": precs, "collect_precision": args.collect_precision or
            ("fp32k" if big else "fp64"), "warm_modes": nets_modes,
            "residual_fmm_order": fmm, "sweep_fmm_order": sweep, "precond_refresh": refresh,
-           "warm_base": base, "history_features": hist}
+           "precond_tensor": bool(args.precond_tensor), "warm_base": base, "history_features": hist}
     t0 = time.perf_counter()
     Xs, Ts, plain_its = [], [], []
     for r in range(args.train_runs):
@@ -425,7 +427,8 @@ def run_step(args):
         torch.cuda.synchronize()
         ts = time.perf_counter()
         sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm,
-                            history=hist, sweep_fmm=sweep, precond_refresh=refresh, base=base)
+                            history=hist, sweep_fmm=sweep, precond_refresh=refresh, base=base,
+                            precond_tensor=args.precond_tensor)
         torch.cuda.synchronize()
         res.setdefault("setup_s", time.perf_counter() - ts)
         res.setdefault("wall_solve", dict(zip(("refinements", "residual"),
@@ -454,7 +457,8 @@ def run_step(args):
     del X, T, Xs, Ts
     g = I.channel(n_w, modes, nv, n_v, area, 2000, mu=mu)
     sim = WS.Simulation(g, kappa_b=kb, restart=200, modes=nm_max, residual_fmm=fmm, history=hist,
-                        sweep_fmm=sweep, precond_refresh=refresh, base=base)
+                        sweep_fmm=sweep, precond_refresh=refresh, base=base,
+                        precond_tensor=args.precond_tensor)
     x0, s0, _ = sim.state()
     evs = {}
     for p in precs:
@@ -488,7 +492,8 @@ def run_step(args):
                        "nodes_per_vesicle": n_v, "wall_nodes": 2 * n_w,
                        "training_states": int(res["train"][nets_modes[0]]["samples"]),
                        "warm_modes": nets_modes, "residual_fmm_order": fmm,
-                       "sweep_fmm_order": sweep, "precond_refresh": refresh, "warm_base": base},
+                       "sweep_fmm_order": sweep, "precond_refresh": refresh,
+                       "precond_tensor": bool(args.precond_tensor), "warm_base": base},
             "iterations_saved_vs_zero": {p: {k: ev["zero"]["mean_iterations"] - v["mean_iterations"]
                                              for k, v in ev.items()} for p, ev in evs.items()},
             "by_precision": {p: summary(ev) for p, ev in evs.items()},
@@ -962,6 +967,9 @@ def main():
     ap.add_argument("--precond-refresh", action="store_true",
                     help="--step: refresh the preconditioner inverse by Newton-Schulz from the "
                          "previous step's instead of factorising every step")
+    ap.add_argument("--precond-tensor", action="store_true",
+                    help="--step: the FP32 preconditioner's GEMMs by cuBLAS's BF16x9 FP32 emulation "
+                         "on the tensor cores")
     ap.add_argument("--sweep-fmm", type=int, default=0,
                     help="--step, fp32k: the Krylov sweeps' vesicle sums by the step's FMM plan at "
                          "this order (0: FP32-Kahan direct sums)")

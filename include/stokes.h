@@ -716,6 +716,14 @@ STOKES_API int stokes_sim_set_precond_precision(stokes_sim *sim, int precision);
  * (stokes_sim_set_state) matches an uninterrupted one to the step tolerance, not bit for bit.
  * STOKES_ERR_ARG for on outside {0, 1}. */
 STOKES_API int stokes_sim_set_precond_refresh(stokes_sim *sim, int on);
+/* FP32 preconditioner (the default STOKES_FP32_KAHAN precision of stokes_sim_set_precond_precision):
+ * on = 1 runs its batched GEMMs -- the assembly products and the Newton-Schulz refresh -- through
+ * cuBLAS's BF16x9 emulation of FP32 on the tensor cores (each FP32 operand split into three
+ * BF16 parts, products accumulated in FP32), wherever cuBLAS can emulate them; the LU
+ * factorisation and inversion keep the default math mode.  0 (default): plain SGEMMs.  The
+ * preconditioner is a fixed operator inside the FP64-accurate refinement, so the setting moves
+ * the iteration count, not what a step converges to.  STOKES_ERR_ARG for another value. */
+STOKES_API int stokes_sim_set_precond_tensor(stokes_sim *sim, int on);
 /* Relative tolerance of each inner FP32-Kahan GMRES solve of a STOKES_FP32_KAHAN step
  * (1e-8..0.5, default 1e-3); the outer FP64-accurate refinement still ends at `tol`. */
 STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
@@ -728,7 +736,10 @@ STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
  * The plan is rebuilt each step (the geometry moves) by a host thread while the GPU computes
  * the forces and the channel response.  The wall double-layer sums of the channel response's
  * block refinement then come from an FMM plan of the walls at the same order, made once after
- * stokes_sim_set_walls; the two vesicle-wall sums stay double-float. */
+ * stokes_sim_set_walls.  The channel response's vesicle-to-wall and wall-to-vesicle sums come
+ * from two plans built each step on host threads while the block preconditioner is built: one
+ * of the vesicles with the wall nodes as free targets, one of the walls with the vesicle nodes
+ * as free targets (stokes_fmm_create_targets). */
 STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_size);
 /* STOKES_FP32_KAHAN steps: run the Krylov sweeps' vesicle sums (the operator of every inner
  * GMRES iteration, the paper's FMM-accelerated matvec) on the step's FMM plan evaluated at

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "stokes_sim_set_block_refinement": [_vp, _c_int],
     "stokes_sim_set_precond_precision": [_vp, _c_int],
     "stokes_sim_set_precond_refresh": [_vp, _c_int],
+    "stokes_sim_set_precond_tensor": [_vp, _c_int],
     "stokes_sim_set_inner_tolerance": [_vp, _c_double],
     "stokes_sim_set_residual_fmm": [_vp, _c_int, _c_int],
     "stokes_sim_set_sweep_fmm": [_vp, _c_int],
@@ -756,6 +757,11 @@ def stokes_sim_set_block_refinement(h, sweeps):
 def stokes_sim_set_precond_refresh(h, on=True):
     """Newton-Schulz refresh of the FP32 preconditioner inverse from the previous step's."""
     return _sim_check(h, load().stokes_sim_set_precond_refresh(h, int(on)))
+
+
+def stokes_sim_set_precond_tensor(h, on=True):
+    """FP32 preconditioner GEMMs (assembly, refresh) by cuBLAS's BF16x9 FP32 emulation."""
+    return _sim_check(h, load().stokes_sim_set_precond_tensor(h, int(on)))
 
 
 def stokes_sim_set_precond_precision(h, precision):

@@ -107,6 +107,8 @@ struct stokes_sim {
   // largest per-vesicle ||I - P X||_F (device), whether d_Pinv32 holds an inverse for the
   // current dt, the dt it was made for, and the last step's refresh count (0: LU)
   bool precond_refresh = false;
+  // the FP32 assembly and refresh GEMMs by cuBLAS's BF16x9 FP32 emulation (opt-in)
+  bool precond_tensor = false;
   float *d_T32 = nullptr, *d_X32 = nullptr;
   unsigned *d_enorm = nullptr;
   bool pinv_valid = false;
@@ -1559,9 +1561,30 @@ int precond_refresh_ns(stokes_sim *m, bool *done) {
   return STOKES_OK;
 }
 
+// While alive, the handle's FP32 GEMMs run as cuBLAS's BF16x9 emulation on the tensor cores
+// (each FP32 operand split into three BF16 parts, the products accumulated in FP32: FP32-class
+// accuracy) wherever cuBLAS can emulate them; the default math mode is restored after.
+struct Bf16x9Scope {
+  cublasHandle_t h;
+  bool on;
+  cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+  Bf16x9Scope(cublasHandle_t h_, bool on_) : h(h_), on(on_) {
+    if (!on) return;
+    st = cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH);
+    if (st == CUBLAS_STATUS_SUCCESS) st = cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
+  }
+  ~Bf16x9Scope() {
+    if (!on) return;
+    cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_DEFAULT);
+    cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
+  }
+};
+
 int precond_build(stokes_sim *m, double dt) {
   const int n = m->n, V = m->V, k = 3 * n;
   if (m->precond_fp32) {
+    Bf16x9Scope emu(m->blas, m->precond_tensor);
+    BK(emu.st);
     // FP32 views of the FP64 assembly buffers (each has room for twice its FP32 contents)
     ST(precond_assemble<float>(m, dt, reinterpret_cast<float *>(m->d_G), reinterpret_cast<float *>(m->d_Ds),
                                reinterpret_cast<float *>(m->d_D2), reinterpret_cast<float *>(m->d_D4),
@@ -1576,6 +1599,11 @@ int precond_build(stokes_sim *m, double dt) {
       bool done = false;
       ST(precond_refresh_ns(m, &done));
       if (done) return STOKES_OK;
+    }
+    if (emu.on) {  // the factorisation in the default math mode
+      BK(cublasSetEmulationStrategy(m->blas, CUBLAS_EMULATION_STRATEGY_DEFAULT));
+      BK(cublasSetMathMode(m->blas, CUBLAS_DEFAULT_MATH));
+      emu.on = false;
     }
     BK(cublasSgetrfBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_pinfo, V));
     BK(cublasSgetriBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_Piptr32, k, m->d_pinfo, V));
@@ -2184,6 +2212,13 @@ int stokes_sim_set_precond_refresh(stokes_sim *m, int on) {
   if (!m) return STOKES_ERR_ARG;
   if (on != 0 && on != 1) return fail(m, STOKES_ERR_ARG, "refresh must be 0 or 1");
   m->precond_refresh = on == 1;
+  return STOKES_OK;
+}
+
+int stokes_sim_set_precond_tensor(stokes_sim *m, int on) {
+  if (!m) return STOKES_ERR_ARG;
+  if (on != 0 && on != 1) return fail(m, STOKES_ERR_ARG, "tensor must be 0 or 1");
+  m->precond_tensor = on == 1;
   return STOKES_OK;
 }
 

@@ -13,7 +13,7 @@ import numpy as np
 from . import (STOKES_FP64, STOKES_GUESS_EXTRAPOLATE, STOKES_GUESS_MLP, STOKES_GUESS_PREVIOUS,
                STOKES_GUESS_ZERO, STOKES_WARM_BASE_EXTRAPOLATE, STOKES_WARM_BASE_PREVIOUS,
                feature_dims, stokes_sim_set_warm_base, stokes_mlp_create, stokes_sim_set_residual_fmm,
-               stokes_sim_set_sweep_fmm, stokes_sim_set_precond_refresh,
+               stokes_sim_set_sweep_fmm, stokes_sim_set_precond_refresh, stokes_sim_set_precond_tensor,
                stokes_sim_set_warm_history, stokes_sim_set_warm_modes, stokes_mlp_destroy, stokes_sim_set_restart,
                stokes_mlp_fit_normalization, stokes_mlp_get_adam, stokes_mlp_get_normalization,
                stokes_mlp_get_params, stokes_mlp_num_params, stokes_mlp_set_adam,
@@ -34,7 +34,7 @@ class Simulation:
 
     def __init__(self, geom, kappa_b=1.0, K=32, M=128, device=0, restart=80, wall_solver=None,
                  modes=16, residual_fmm=0, history=False, base="previous", sweep_fmm=0,
-                 precond_refresh=False):
+                 precond_refresh=False, precond_tensor=False):
         walls = [c for c in geom.curves if c.kind == 0]
         ves = [c for c in geom.curves if c.kind == 1]
         self.h = stokes_sim_create(device)
@@ -65,6 +65,8 @@ class Simulation:
             stokes_sim_set_sweep_fmm(self.h, sweep_fmm)
         if precond_refresh:  # Newton-Schulz refresh of the preconditioner inverse
             stokes_sim_set_precond_refresh(self.h, True)
+        if precond_tensor:  # ... and its GEMMs by BF16x9 FP32 emulation on the tensor cores
+            stokes_sim_set_precond_tensor(self.h, True)
 
     def step(self, dt, p_drive, guess="zero", model=None, tol=1e-10, max_iter=500,
              precision=STOKES_FP64):
