@@ -268,6 +268,13 @@ STOKES_API int stokes_fmm_create(stokes_ctx *ctx, int order, int leaf_size, stok
  * a non-finite point; otherwise as stokes_fmm_create. */
 STOKES_API int stokes_fmm_create_targets(stokes_ctx *ctx, int order, int leaf_size, int n_targets,
                                          const double *targets, stokes_fmm **out);
+/* As stokes_fmm_create_targets, but the plan's target tree holds the free points alone: no
+ * cell, conversion or near list is made for the nodes, so an evaluation costs what the free
+ * targets need.  Only stokes_fmm_eval_targets evaluates it; stokes_fmm_eval returns
+ * STOKES_ERR_ARG. */
+STOKES_API int stokes_fmm_create_targets_only(stokes_ctx *ctx, int order, int leaf_size,
+                                              int n_targets, const double *targets,
+                                              stokes_fmm **out);
 STOKES_API int stokes_fmm_eval(stokes_fmm *fmm, const double *slp_density,
                                const double *dlp_density, double jump, double *out_velocity,
                                void *stream);
@@ -738,8 +745,8 @@ STOKES_API int stokes_sim_set_inner_tolerance(stokes_sim *sim, double tol);
  * block refinement then come from an FMM plan of the walls at the same order, made once after
  * stokes_sim_set_walls.  The channel response's vesicle-to-wall and wall-to-vesicle sums come
  * from two plans built each step on host threads while the block preconditioner is built: one
- * of the vesicles with the wall nodes as free targets, one of the walls with the vesicle nodes
- * as free targets (stokes_fmm_create_targets). */
+ * of the vesicles with the wall nodes as its only targets, one of the walls with the vesicle
+ * nodes as its only targets (stokes_fmm_create_targets_only). */
 STOKES_API int stokes_sim_set_residual_fmm(stokes_sim *sim, int order, int leaf_size);
 /* STOKES_FP32_KAHAN steps: run the Krylov sweeps' vesicle sums (the operator of every inner
  * GMRES iteration, the paper's FMM-accelerated matvec) on the step's FMM plan evaluated at

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "stokes_fmm_eval": [_vp, _vp, _vp, _c_double, _vp, _vp],
     "stokes_fmm_get_info": [_vp, _vp],
     "stokes_fmm_create_targets": [_vp, _c_int, _c_int, _c_int, _vp, _vp],
+    "stokes_fmm_create_targets_only": [_vp, _c_int, _c_int, _c_int, _vp, _vp],
     "stokes_fmm_eval_targets": [_vp, _vp, _vp, _vp, _vp],
     "stokes_fmm_set_eval_order": [_vp, _c_int],
     "stokes_fmm_set_precision": [_vp, _c_int],
@@ -361,6 +362,17 @@ def stokes_fmm_create_targets(h, targets, order=24, leaf_size=32):
     f = _vp()
     code = load().stokes_fmm_create_targets(h, int(order), int(leaf_size), int(targets.shape[0]),
                                             _dptr(targets, "targets", (2,)), ctypes.byref(f))
+    if code != STOKES_OK:
+        raise StokesError(code, _err(h))
+    return f
+
+
+def stokes_fmm_create_targets_only(h, targets, order=24, leaf_size=32):
+    """FMM plan of context h whose only targets are the free points `targets` (device, (T, 2))."""
+    f = _vp()
+    code = load().stokes_fmm_create_targets_only(h, int(order), int(leaf_size),
+                                                 int(targets.shape[0]),
+                                                 _dptr(targets, "targets", (2,)), ctypes.byref(f))
     if code != STOKES_OK:
         raise StokesError(code, _err(h))
     return f

@@ -794,6 +794,7 @@ struct stokes_fmm {
   float4 *d_tpow_df = nullptr, *d_Mf = nullptr;  // double-float copies for m2l_df_kernel
   int *d_src_own = nullptr, *d_node_curve = nullptr;
   int n_extra = 0;                // free targets after the nodes
+  bool node_targets = true;       // the nodes are targets too (else only the free targets)
   double2 *d_tx = nullptr;        // [N + n_extra] target positions
   // the geometry the plan was made for
   unsigned long long generation = 0;
@@ -894,6 +895,33 @@ struct PlanHost {
   long long near_pairs = 0;
 };
 
+// The indices 0..n-1 ordered by key[i], equal keys in index order (the order of a stable
+// sort): least-significant-digit radix sort of (key, index) pairs, 11 bits per pass, over the
+// bits the keys use.
+std::vector<int> order_by_key(const std::vector<unsigned long long> &key) {
+  const int n = int(key.size());
+  constexpr int kBits = 11, kBuckets = 1 << kBits;
+  std::vector<unsigned long long> ka(key), kb(n);
+  std::vector<int> ia(n), ib(n);
+  for (int i = 0; i < n; ++i) ia[i] = i;
+  unsigned long long used = 0;
+  for (unsigned long long k : key) used |= k;
+  std::vector<int> cnt(kBuckets + 1);
+  for (int shift = 0; shift < 64 && (used >> shift) != 0; shift += kBits) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int i = 0; i < n; ++i) ++cnt[((ka[i] >> shift) & (kBuckets - 1)) + 1];
+    for (int b = 0; b < kBuckets; ++b) cnt[b + 1] += cnt[b];
+    for (int i = 0; i < n; ++i) {
+      const int at = cnt[(ka[i] >> shift) & (kBuckets - 1)]++;
+      kb[at] = ka[i];
+      ib[at] = ia[i];
+    }
+    ka.swap(kb);
+    ia.swap(ib);
+  }
+  return ia;
+}
+
 void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
                const std::vector<int> &snode, const std::vector<int> &node_curve, double d,
                int leaf_target, PlanHost &ph) {
@@ -904,6 +932,9 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   const int nimg = d != 0.0 ? 3 : 1;
   std::vector<int2> src;  // (slot, m)
   std::vector<double2> pos;
+  const size_t live = size_t(std::count_if(snode.begin(), snode.end(), [](int v) { return v >= 0; }));
+  src.reserve(live * nimg);
+  pos.reserve(live * nimg);
   for (int m = (nimg == 3 ? -1 : 0); m <= (nimg == 3 ? 1 : 0); ++m)
     for (int s = 0; s < slots; ++s)
       if (snode[s] >= 0) {
@@ -944,11 +975,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
     gcoord(x[i], gx, gy);
     tkey[i] = encode(gx, gy, kLmax, f->nx);
   }
-  std::vector<int> sord(ns), tord(N);
-  for (int j = 0; j < ns; ++j) sord[j] = j;
-  for (int i = 0; i < N; ++i) tord[i] = i;
-  std::stable_sort(sord.begin(), sord.end(), [&](int a, int b) { return skey[a] < skey[b]; });
-  std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) { return tkey[a] < tkey[b]; });
+  const std::vector<int> sord = order_by_key(skey), tord = order_by_key(tkey);
   // depth: the shallowest with at most leaf_target sources per occupied leaf
   int L = 0;
   for (; L < kLmax; ++L) {
@@ -1102,7 +1129,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   ph.pos_sorted = pos_sorted;
 }
 
-int build_plan(stokes_fmm *f, int leaf_target, int n_extra, const double2 *extra) {
+int build_plan(stokes_fmm *f, int leaf_target, int n_extra, const double2 *extra, bool nodes) {
   stokes_ctx *c = f->ctx;
   const int N = c->N;
   const int slots = c->wall_slots_f64 + c->ves_slots_f64;
@@ -1126,7 +1153,13 @@ int build_plan(stokes_fmm *f, int leaf_target, int n_extra, const double2 *extra
     if (c->kind[cv] == STOKES_KIND_VESICLE)
       for (int i = c->off[cv]; i < c->off[cv + 1]; ++i) node_curve[i] = cv;
   PlanHost ph;
-  plan_host(x, spos, snode, node_curve, c->period, leaf_target, ph);
+  if (nodes) {
+    plan_host(x, spos, snode, node_curve, c->period, leaf_target, ph);
+  } else {  // a forest over the sources and the free targets only; targets keep their index N + i
+    const std::vector<double2> xt(x.begin() + N, x.end());
+    plan_host(xt, spos, snode, node_curve, c->period, leaf_target, ph);
+    for (int &t : ph.tord) t += N;
+  }
   f->L = ph.L;
   f->nx = ph.nx;
   f->ny = ph.ny;
@@ -1165,6 +1198,7 @@ int build_plan(stokes_fmm *f, int leaf_target, int n_extra, const double2 *extra
   up(upload(f->d_node_curve, node_curve, bytes));
   up(upload(f->d_tx, x, bytes));
   f->n_extra = n_extra;
+  f->node_targets = nodes;
   {  // t^-n and log(-t) of the integer offsets t = (dx, dy), |dx|, |dy| <= 3
     const int p1 = f->p + 1;
     std::vector<double2> tpow(49 * p1), tlog(49);
@@ -1267,7 +1301,7 @@ int fmm_fail(stokes_fmm *f, int code, const std::string &msg) {
 extern "C" {
 
 static int fmm_create(stokes_ctx *c, int order, int leaf_size, int n_extra, const double *extra,
-                      stokes_fmm **out) {
+                      bool nodes, stokes_fmm **out) {
   if (!out) return STOKES_ERR_ARG;
   *out = nullptr;
   if (!c) return STOKES_ERR_ARG;
@@ -1287,7 +1321,7 @@ static int fmm_create(stokes_ctx *c, int order, int leaf_size, int n_extra, cons
   stokes_fmm *f = new stokes_fmm();
   f->ctx = c;
   f->p = order;
-  const int st = build_plan(f, leaf_size, n_extra, reinterpret_cast<const double2 *>(extra));
+  const int st = build_plan(f, leaf_size, n_extra, reinterpret_cast<const double2 *>(extra), nodes);
   if (st) {
     c->err = f->err;
     free_plan(f);
@@ -1303,7 +1337,7 @@ static int fmm_create(stokes_ctx *c, int order, int leaf_size, int n_extra, cons
 }
 
 int stokes_fmm_create(stokes_ctx *c, int order, int leaf_size, stokes_fmm **out) {
-  return fmm_create(c, order, leaf_size, 0, nullptr, out);
+  return fmm_create(c, order, leaf_size, 0, nullptr, true, out);
 }
 
 int stokes_fmm_create_targets(stokes_ctx *c, int order, int leaf_size, int n_targets,
@@ -1312,7 +1346,16 @@ int stokes_fmm_create_targets(stokes_ctx *c, int order, int leaf_size, int n_tar
     if (out) *out = nullptr;
     return STOKES_ERR_ARG;
   }
-  return fmm_create(c, order, leaf_size, n_targets, targets, out);
+  return fmm_create(c, order, leaf_size, n_targets, targets, true, out);
+}
+
+int stokes_fmm_create_targets_only(stokes_ctx *c, int order, int leaf_size, int n_targets,
+                                   const double *targets, stokes_fmm **out) {
+  if (n_targets < 1) {
+    if (out) *out = nullptr;
+    return STOKES_ERR_ARG;
+  }
+  return fmm_create(c, order, leaf_size, n_targets, targets, false, out);
 }
 
 // An evaluation: the node sum into out (with the self terms, the curvature diagonal and the
@@ -1330,6 +1373,8 @@ static int fmm_eval(stokes_fmm *f, const double *slp, const double *dlp, double 
                                        "outputs and a finite jump");
   if (out_targets && f->n_extra == 0)
     return fmm_fail(f, STOKES_ERR_ARG, "the plan was made without free targets");
+  if (out && !f->node_targets)
+    return fmm_fail(f, STOKES_ERR_ARG, "the plan was made for its free targets only");
   FMK(cudaSetDevice(c->device));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int N = c->N;

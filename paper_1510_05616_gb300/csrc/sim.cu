@@ -142,8 +142,8 @@ struct stokes_sim {
   stokes_fmm *fmm_w = nullptr;
   int fmm_w_order = 0;
   // ... and the channel response's two vesicle-wall sums from per-step plans with the other
-  // kind's nodes as free targets: vesicle sources at the wall nodes, wall sources at the
-  // vesicle nodes
+  // kind's nodes as their only targets: vesicle sources at the wall nodes, wall sources at
+  // the vesicle nodes
   stokes_fmm *fmm_vw = nullptr, *fmm_wv = nullptr;
   // close evaluation of the vesicle-vesicle single layer (stokes_sim_set_close_eval): every
   // vesicle sum of the step adds the correction of the close (node, vesicle image) pairs found
@@ -1431,7 +1431,8 @@ struct FmmPlanJob {
   stokes_fmm *plan = nullptr;
   int status = STOKES_OK;
   double ms = 0.0;
-  // A plan of ctx at `order`, with n_extra free targets (device points) when n_extra > 0.
+  // A plan of ctx at `order`; when n_extra > 0, one whose only targets are n_extra free
+  // points (device).
   void start(stokes_sim *m, stokes_ctx *ctx, int order, int n_extra = 0,
              const double *extra = nullptr) {
     th = std::thread([this, m, ctx, order, n_extra, extra] {
@@ -1441,7 +1442,7 @@ struct FmmPlanJob {
         return;
       }
       status = n_extra > 0
-                   ? stokes_fmm_create_targets(ctx, order, m->resid_fmm_leaf, n_extra, extra, &plan)
+                   ? stokes_fmm_create_targets_only(ctx, order, m->resid_fmm_leaf, n_extra, extra, &plan)
                    : stokes_fmm_create(ctx, order, m->resid_fmm_leaf, &plan);
       ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     });

@@ -193,7 +193,9 @@ def test_fmm_free_targets_match_direct_free_point_sum(P, kind):
     vesicles' single layer at the walls' nodes, and the walls' double layer at the vesicles'
     nodes -- the two sums of the channel response.  The same plan's node evaluation still meets
     the direct node sum to the expansion error (the free targets widen the forest, so its tree
-    -- and the truncation error -- differs from the nodes-only plan's)."""
+    -- and the truncation error -- differs from the nodes-only plan's).  A targets-only plan
+    (stokes_fmm_create_targets_only) gives the free-point sum to the same bound and refuses a
+    node evaluation."""
     import torch
     g, slp, dlp = I.workload("mid_n16k")
     ves = [c for c in g.curves if c.kind == I.KIND_SLP]
@@ -216,14 +218,31 @@ def test_fmm_free_targets_match_direct_free_point_sum(P, kind):
         err = rel(out.cpu().numpy(), ref)
         assert err < 1e-9, err
         assert rel(nodes.cpu().numpy(), node_ref) < 1e-9
+        cells_all = P.stokes_fmm_get_info(f)["target_cells"]
     finally:
         P.stokes_fmm_destroy(f)
+    # a plan whose target tree holds the free points alone: the same sums, fewer target cells
+    ft = P.stokes_fmm_create_targets_only(s.h, tg, 28, 32)
+    try:
+        out2 = torch.zeros_like(tg)
+        P.stokes_fmm_eval_targets(ft, ds, dd, out2)
+        P.stokes_sync(s.h)
+        err2 = rel(out2.cpu().numpy(), ref)
+        assert err2 < 1e-9, err2
+        cells = P.stokes_fmm_get_info(ft)["target_cells"]
+        with pytest.raises(P.StokesError):  # the nodes are not targets of this plan
+            P.stokes_fmm_eval(ft, ds, dd, 0.0, torch.zeros((s.N, 2), dtype=torch.float64,
+                                                           device="cuda"))
+    finally:
+        P.stokes_fmm_destroy(ft)
     f0 = P.stokes_fmm_create(s.h, 20, 32)
+    assert cells < cells_all, (cells, cells_all)
     with pytest.raises(P.StokesError):  # no free targets in this plan
         P.stokes_fmm_eval_targets(f0, ds, dd, torch.zeros_like(tg))
     P.stokes_fmm_destroy(f0)
     s.close()
-    print("free targets (%s sources): %.2e" % (kind, err))
+    print("free targets (%s sources): %.2e; targets-only plan %.2e, %d target cells"
+          % (kind, err, err2, cells))
 
 
 def test_fmm_high_order_converges(P):
