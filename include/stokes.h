@@ -660,6 +660,10 @@ typedef struct {
                             runs on a host thread beside the GPU's work                  */
     int precond_refresh; /* Newton-Schulz products of the preconditioner refresh
                             (stokes_sim_set_precond_refresh); 0: the blocks were factorised */
+    double response_plan_ms; /* host time of the slower of the channel response's two FMM
+                                plans (residual FMM on, walls present), else 0          */
+    double plan_wait_ms; /* host time the step spent waiting for its FMM plan threads after
+                            queueing the work that does not need them                  */
 } stokes_step_stats;
 
 STOKES_API int stokes_sim_create(int device, stokes_sim **out);

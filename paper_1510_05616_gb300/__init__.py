@@ -637,7 +637,8 @@ class StepStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("residual", _c_double), ("setup_ms", _c_double),
                 ("gmres_ms", _c_double), ("total_ms", _c_double), ("refinements", _c_int),
                 ("accurate_residuals", _c_int), ("fmm_plan_ms", _c_double),
-                ("precond_refresh", _c_int)]
+                ("precond_refresh", _c_int), ("response_plan_ms", _c_double),
+                ("plan_wait_ms", _c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

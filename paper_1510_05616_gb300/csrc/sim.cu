@@ -2372,9 +2372,17 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   // host threads build this step's FMM plans
   ST(precond_build(m, dt));
   // steps 3-5: channel response of the explicit forces
+  double wait_ms = 0.0, resp_plan_ms = 0.0;
+  auto join_timed = [&wait_ms](FmmPlanJob &job) {
+    const auto tw = std::chrono::steady_clock::now();
+    const int st = job.join();
+    wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tw).count();
+    return st;
+  };
   if (resp_fmm) {
-    int pst = plan_vw.join();
-    if (!pst) pst = plan_wv.join();
+    int pst = join_timed(plan_vw);
+    if (!pst) pst = join_timed(plan_wv);
+    resp_plan_ms = std::max(plan_vw.ms, plan_wv.ms);
     if (pst) return fail(m, pst, "FMM plans of the channel response failed (%s / %s)",
                          m->ctx_v->err.c_str(), m->ctx_w->err.c_str());
     m->fmm_vw = plan_vw.take();
@@ -2385,7 +2393,7 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
   // right-hand side [S f_b + u_resp; ALC]
   double plan_ms = 0.0;
   if (use_plan) {
-    const int pst = plan_job.join();
+    const int pst = join_timed(plan_job);
     if (pst) return fail(m, pst, "FMM plan of the vesicles failed (%s)", m->ctx_v->err.c_str());
     m->fmm_v = plan_job.take();
     plan_ms = plan_job.ms;
@@ -2510,6 +2518,8 @@ int vesicle_step_warmstart(stokes_sim *m, double dt, double p_drive, int guess_m
     out->accurate_residuals = accurate;
     out->fmm_plan_ms = plan_ms;
     out->precond_refresh = m->last_refresh;
+    out->response_plan_ms = resp_plan_ms;
+    out->plan_wait_ms = wait_ms;
   }
   if (gst) return gst;
   if (n >= m->warm_modes) {
