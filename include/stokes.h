@@ -730,7 +730,8 @@ STOKES_API int stokes_sim_set_precond_refresh(stokes_sim *sim, int on);
 /* FP32 preconditioner (the default STOKES_FP32_KAHAN precision of stokes_sim_set_precond_precision):
  * on = 1 runs its batched GEMMs -- the assembly products and the Newton-Schulz refresh -- through
  * cuBLAS's BF16x9 emulation of FP32 on the tensor cores (each FP32 operand split into three
- * BF16 parts, products accumulated in FP32), wherever cuBLAS can emulate them; the LU
+ * BF16 parts, products accumulated in FP32), wherever cuBLAS can emulate them, without
+ * cuBLAS's infinity/NaN handling (the blocks are finite for a finite geometry); the LU
  * factorisation and inversion keep the default math mode.  0 (default): plain SGEMMs.  The
  * preconditioner is a fixed operator inside the FP64-accurate refinement, so the setting moves
  * the iteration count, not what a step converges to.  STOKES_ERR_ARG for another value. */

@@ -1564,7 +1564,11 @@ int precond_refresh_ns(stokes_sim *m, bool *done) {
 
 // While alive, the handle's FP32 GEMMs run as cuBLAS's BF16x9 emulation on the tensor cores
 // (each FP32 operand split into three BF16 parts, the products accumulated in FP32: FP32-class
-// accuracy) wherever cuBLAS can emulate them; the default math mode is restored after.
+// accuracy) wherever cuBLAS can emulate them; the default math mode is restored after.  The
+// emulation is asked for no infinity/NaN handling (cuBLAS otherwise scans both operands and
+// patches the product, which cost more than the GEMMs here): the blocks are finite when the
+// geometry is, and a non-finite block would still show in the refresh's error norm and the
+// step's FP64-accurate residuals.
 struct Bf16x9Scope {
   cublasHandle_t h;
   bool on;
@@ -1573,12 +1577,17 @@ struct Bf16x9Scope {
     if (!on) return;
     st = cublasSetMathMode(h, CUBLAS_FP32_EMULATED_BF16X9_MATH);
     if (st == CUBLAS_STATUS_SUCCESS) st = cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_EAGER);
+    if (st == CUBLAS_STATUS_SUCCESS)
+      st = cublasSetEmulationSpecialValuesSupport(h, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
   }
-  ~Bf16x9Scope() {
+  void restore() {
     if (!on) return;
+    cublasSetEmulationSpecialValuesSupport(h, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT);
     cublasSetEmulationStrategy(h, CUBLAS_EMULATION_STRATEGY_DEFAULT);
     cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
+    on = false;
   }
+  ~Bf16x9Scope() { restore(); }
 };
 
 int precond_build(stokes_sim *m, double dt) {
@@ -1600,12 +1609,9 @@ int precond_build(stokes_sim *m, double dt) {
       bool done = false;
       ST(precond_refresh_ns(m, &done));
       if (done) return STOKES_OK;
+      m->last_refresh = 0;  // rejected: the blocks are factorised below
     }
-    if (emu.on) {  // the factorisation in the default math mode
-      BK(cublasSetEmulationStrategy(m->blas, CUBLAS_EMULATION_STRATEGY_DEFAULT));
-      BK(cublasSetMathMode(m->blas, CUBLAS_DEFAULT_MATH));
-      emu.on = false;
-    }
+    emu.restore();  // the factorisation in the default math mode
     BK(cublasSgetrfBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_pinfo, V));
     BK(cublasSgetriBatched(m->blas, k, m->d_Pptr32, k, m->d_ppiv, m->d_Piptr32, k, m->d_pinfo, V));
     m->pinv_valid = true;

@@ -261,14 +261,17 @@ def test_precond_refresh_step_matches_factorised_step(P):
     """Mixed-precision steps on the 16k channel whose preconditioner inverse is refreshed from the
     previous step's by Newton-Schulz (stokes_sim_set_precond_refresh) end on the same
     FP64-accurate residual bound at the same solution as the steps that factorise every block:
-    solutions to 1e-8, positions to 1e-10; the first step factorises, later ones refresh."""
+    solutions to 1e-8, positions to 1e-10.  The first step factorises (0 products); while the
+    shapes relax fast the previous inverse is rejected and the blocks are factorised (reported
+    as 0); once they settle the refresh is taken (>= 1 product).  The steps run until three
+    have been refreshed, and at least one must be."""
     from paper_1510_05616_gb300 import warmstart as WS
     g = I.workload("mid_n16k")[0]
     dt, pd, kb = 1e-3, 2 * 2 * PI * 0.2, 0.01
     a = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=36)
     b = WS.Simulation(g, kappa_b=kb, restart=200, residual_fmm=36, precond_refresh=True)
     refreshed = []
-    for k in range(4):
+    for k in range(40):
         sa = a.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
         sb = b.step(dt, pd, "zero" if k == 0 else "previous", precision=P.STOKES_FP32_KAHAN)
         assert sa["residual"] <= 1e-10 and sb["residual"] <= 1e-10
@@ -281,7 +284,9 @@ def test_precond_refresh_step_matches_factorised_step(P):
         print("step %d: refresh products %d; solution %.2e, positions %.2e; its %d / %d"
               % (k, sb["precond_refresh"], ez, ex, sa["iterations"], sb["iterations"]))
         assert ez <= 1e-8 and ex <= 1e-10
-    assert refreshed[0] == 0 and all(r > 0 for r in refreshed[1:]), refreshed
+        if sum(r > 0 for r in refreshed) >= 3:
+            break
+    assert refreshed[0] == 0 and any(r > 0 for r in refreshed[1:]), refreshed
     h = P.stokes_sim_create(0)
     with pytest.raises(P.StokesError):
         P.stokes_sim_set_precond_refresh(h, 2)
