@@ -34,6 +34,7 @@
 #include <chrono>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -895,6 +896,25 @@ struct PlanHost {
   long long near_pairs = 0;
 };
 
+// Host threads of one plan build (the step builds up to three plans at once).
+constexpr int kPlanThreads = 4;
+
+// f(t, begin, end) over kPlanThreads contiguous chunks of [0, n), chunk t on its own thread
+// (small n on the calling thread alone); every chunk writes only its own outputs.
+template <class F>
+void plan_for(int n, F f) {
+  if (n < 4096) {
+    f(0, 0, n);
+    return;
+  }
+  std::thread th[kPlanThreads - 1];
+  for (int t = 1; t < kPlanThreads; ++t)
+    th[t - 1] = std::thread(f, t, int((long long)n * t / kPlanThreads),
+                            int((long long)n * (t + 1) / kPlanThreads));
+  f(0, 0, int((long long)n / kPlanThreads));
+  for (auto &x : th) x.join();
+}
+
 // The indices 0..n-1 ordered by key[i], equal keys in index order (the order of a stable
 // sort): least-significant-digit radix sort of (key, index) pairs, 11 bits per pass, over the
 // bits the keys use.
@@ -930,18 +950,20 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   const int slots = int(spos.size());
   // image sources
   const int nimg = d != 0.0 ? 3 : 1;
-  std::vector<int2> src;  // (slot, m)
-  std::vector<double2> pos;
-  const size_t live = size_t(std::count_if(snode.begin(), snode.end(), [](int v) { return v >= 0; }));
-  src.reserve(live * nimg);
-  pos.reserve(live * nimg);
-  for (int m = (nimg == 3 ? -1 : 0); m <= (nimg == 3 ? 1 : 0); ++m)
-    for (int s = 0; s < slots; ++s)
-      if (snode[s] >= 0) {
-        src.push_back(make_int2(s, m));
-        pos.push_back(make_double2(spos[s].x + m * d, spos[s].y));
-      }
-  const int ns = int(src.size());
+  std::vector<int> live;  // the slots holding a node, in slot order
+  live.reserve(slots);
+  for (int s = 0; s < slots; ++s)
+    if (snode[s] >= 0) live.push_back(s);
+  const int nl = int(live.size()), ns = nl * nimg;
+  std::vector<int2> src(ns);  // (slot, m): image m of every live slot, m = -1, 0, 1 in turn
+  std::vector<double2> pos(ns);
+  plan_for(ns, [&](int, int b, int e) {
+    for (int j = b; j < e; ++j) {
+      const int m = (nimg == 3 ? j / nl - 1 : 0), sl = live[j % nl];
+      src[j] = make_int2(sl, m);
+      pos[j] = make_double2(spos[sl].x + m * d, spos[sl].y);
+    }
+  });
   // forest of square roots over sources and targets
   double xa = 1e300, xb = -1e300, ya = 1e300, yb = -1e300;
   for (const double2 &q : pos) {
@@ -965,17 +987,24 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
     gy = std::min(gmaxy, std::max(0, int(floor((q.y - ya) / hmax))));
   };
   std::vector<unsigned long long> skey(ns), tkey(N);
-  for (int j = 0; j < ns; ++j) {
-    int gx, gy;
-    gcoord(pos[j], gx, gy);
-    skey[j] = encode(gx, gy, kLmax, f->nx);
-  }
-  for (int i = 0; i < N; ++i) {
-    int gx, gy;
-    gcoord(x[i], gx, gy);
-    tkey[i] = encode(gx, gy, kLmax, f->nx);
-  }
-  const std::vector<int> sord = order_by_key(skey), tord = order_by_key(tkey);
+  plan_for(ns, [&](int, int b, int e) {
+    for (int j = b; j < e; ++j) {
+      int gx, gy;
+      gcoord(pos[j], gx, gy);
+      skey[j] = encode(gx, gy, kLmax, f->nx);
+    }
+  });
+  plan_for(N, [&](int, int b, int e) {
+    for (int i = b; i < e; ++i) {
+      int gx, gy;
+      gcoord(x[i], gx, gy);
+      tkey[i] = encode(gx, gy, kLmax, f->nx);
+    }
+  });
+  std::vector<int> sord, tord;  // the two orders on two threads
+  std::thread tsort([&] { tord = order_by_key(tkey); });
+  sord = order_by_key(skey);
+  tsort.join();
   // depth: the shallowest with at most leaf_target sources per occupied leaf
   int L = 0;
   for (; L < kLmax; ++L) {
@@ -1032,10 +1061,15 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
     const double h = S / double(1 << l);
     return make_double2(xa + (gx + 0.5) * h, ya + (gy + 0.5) * h);
   };
+  // the level of cell i of a flattened list with level offsets off[0..L+1]
+  auto level_of = [L](const std::vector<int> &off, int i) {
+    return int(std::upper_bound(off.begin(), off.begin() + L + 2, i) - off.begin()) - 1;
+  };
   std::vector<double2> sc_ctr(nsc), tc_ctr(ntc);
   std::vector<int2> sc_rng(nsc);
-  for (int l = 0; l <= L; ++l)
-    for (int i = f->sc_off[l]; i < f->sc_off[l + 1]; ++i) {
+  plan_for(nsc, [&](int, int cb, int ce) {
+    for (int i = cb; i < ce; ++i) {
+      const int l = level_of(f->sc_off, i);
       sc_ctr[i] = centre(sk_all[i], l);
       if (l == L) {
         const int li = i - f->sc_off[L];
@@ -1048,10 +1082,17 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
         sc_rng[i] = make_int2(int(b - sk_all.begin()), int(e - sk_all.begin()));
       }
     }
-  std::vector<int> tc_par(ntc, -1), il_off(ntc + 1, 0), il_idx;
-  for (int l = 0; l <= L; ++l) {
-    const int gnx = f->nx << l, gny = f->ny << l;
-    for (int i = f->tc_off[l]; i < f->tc_off[l + 1]; ++i) {
+  });
+  // interaction lists: each chunk of target cells lists into its own part, the parts joined in
+  // cell order
+  std::vector<int> tc_par(ntc, -1), il_off(ntc + 1, 0), il_idx, il_cnt(ntc, 0);
+  std::vector<std::vector<int>> il_part(kPlanThreads);
+  plan_for(ntc, [&](int part_id, int cb, int ce) {
+    std::vector<int> &part = il_part[part_id];
+    for (int i = cb; i < ce; ++i) {
+      const int l = level_of(f->tc_off, i);
+      const int gnx = f->nx << l, gny = f->ny << l;
+      const size_t before = part.size();
       tc_ctr[i] = centre(tk_all[i], l);
       if (l > 0) tc_par[i] = find_key(tk_all, f->tc_off[l - 1], f->tc_off[l], tk_all[i] >> 2);
       int gx, gy;
@@ -1060,7 +1101,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
         for (int sidx = f->sc_off[0]; sidx < f->sc_off[1]; ++sidx) {
           int sx, sy;
           decode(sk_all[sidx], 0, f->nx, sx, sy);
-          if (std::max(abs(sx - gx), abs(sy - gy)) >= 2) il_idx.push_back(sidx);
+          if (std::max(abs(sx - gx), abs(sy - gy)) >= 2) part.push_back(sidx);
         }
       } else {
         const int px = gx >> 1, py = gy >> 1;
@@ -1072,46 +1113,60 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
                 if (cx < 0 || cy < 0 || cx >= gnx || cy >= gny) continue;
                 if (std::max(abs(cx - gx), abs(cy - gy)) <= 1) continue;
                 const int sidx = find_key(sk_all, f->sc_off[l], f->sc_off[l + 1], encode(cx, cy, l, f->nx));
-                if (sidx >= 0) il_idx.push_back(sidx);
+                if (sidx >= 0) part.push_back(sidx);
               }
       }
-      il_off[i + 1] = int(il_idx.size());
+      il_cnt[i] = int(part.size() - before);
     }
-  }
+  });
+  for (int i = 0; i < ntc; ++i) il_off[i + 1] = il_off[i] + il_cnt[i];
+  il_idx.reserve(size_t(il_off[ntc]));
+  for (const std::vector<int> &part : il_part) il_idx.insert(il_idx.end(), part.begin(), part.end());
   // near lists and target ranges of the target leaves
   const int ntl = int(tkeys[L].size());
   f->n_tleaf = ntl;
-  std::vector<int> nl_off(ntl + 1, 0), nl_idx;
+  std::vector<int> nl_off(ntl + 1, 0), nl_idx, nl_cnt(ntl, 0);
   std::vector<int2> tleaf_rng(ntl);
   const int gnx = f->nx << L, gny = f->ny << L;
-  long long near_pairs = 0;
-  for (int t = 0; t < ntl; ++t) {
-    tleaf_rng[t] = make_int2(tleaf_begin[t], tleaf_begin[t + 1]);
-    int gx, gy;
-    decode(tkeys[L][t], L, f->nx, gx, gy);
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int cx = gx + dx, cy = gy + dy;
-        if (cx < 0 || cy < 0 || cx >= gnx || cy >= gny) continue;
-        const int sidx = find_key(sk_all, f->sc_off[L], f->sc_off[L + 1], encode(cx, cy, L, f->nx));
-        if (sidx >= 0) {
-          nl_idx.push_back(sidx);
-          near_pairs += (long long)(tleaf_begin[t + 1] - tleaf_begin[t]) * (sc_rng[sidx].y - sc_rng[sidx].x);
+  std::vector<std::vector<int>> nl_part(kPlanThreads);
+  long long part_pairs[kPlanThreads] = {};
+  plan_for(ntl, [&](int part_id, int lb, int le) {
+    std::vector<int> &part = nl_part[part_id];
+    for (int t = lb; t < le; ++t) {
+      const size_t before = part.size();
+      tleaf_rng[t] = make_int2(tleaf_begin[t], tleaf_begin[t + 1]);
+      int gx, gy;
+      decode(tkeys[L][t], L, f->nx, gx, gy);
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int cx = gx + dx, cy = gy + dy;
+          if (cx < 0 || cy < 0 || cx >= gnx || cy >= gny) continue;
+          const int sidx = find_key(sk_all, f->sc_off[L], f->sc_off[L + 1], encode(cx, cy, L, f->nx));
+          if (sidx >= 0) {
+            part.push_back(sidx);
+            part_pairs[part_id] +=
+                (long long)(tleaf_begin[t + 1] - tleaf_begin[t]) * (sc_rng[sidx].y - sc_rng[sidx].x);
+          }
         }
-      }
-    nl_off[t + 1] = int(nl_idx.size());
-  }
+      nl_cnt[t] = int(part.size() - before);
+    }
+  });
+  long long near_pairs = 0;
+  for (long long q : part_pairs) near_pairs += q;
+  for (int t = 0; t < ntl; ++t) nl_off[t + 1] = nl_off[t] + nl_cnt[t];
+  nl_idx.reserve(size_t(nl_off[ntl]));
+  for (const std::vector<int> &part : nl_part) nl_idx.insert(nl_idx.end(), part.begin(), part.end());
   std::vector<int2> src_sorted(ns);
   std::vector<double2> pos_sorted(ns);
-  for (int j = 0; j < ns; ++j) {
-    src_sorted[j] = src[sord[j]];
-    pos_sorted[j] = pos[sord[j]];
-  }
   f->src_own.resize(ns);
-  for (int j = 0; j < ns; ++j) {
-    const int2 sm = src_sorted[j];
-    f->src_own[j] = sm.y == 0 ? node_curve[snode[sm.x]] : -1;
-  }
+  plan_for(ns, [&](int, int b, int e) {
+    for (int j = b; j < e; ++j) {
+      src_sorted[j] = src[sord[j]];
+      pos_sorted[j] = pos[sord[j]];
+      const int2 sm = src_sorted[j];
+      f->src_own[j] = sm.y == 0 ? node_curve[snode[sm.x]] : -1;
+    }
+  });
   f->N = N;
   f->ns = ns;
   f->tord = tord;
