@@ -899,20 +899,20 @@ struct PlanHost {
 // Host threads of one plan build (the step builds up to three plans at once).
 constexpr int kPlanThreads = 4;
 
-// f(t, begin, end) over kPlanThreads contiguous chunks of [0, n), chunk t on its own thread
-// (small n on the calling thread alone); every chunk writes only its own outputs.
+// f(t, begin, end) over `threads` (1..kPlanThreads) contiguous chunks of [0, n), chunk t on
+// its own thread (small n on the calling thread alone); every chunk writes only its own
+// outputs.
 template <class F>
-void plan_for(int n, F f) {
-  if (n < 4096) {
+void plan_for(int n, int threads, F f) {
+  if (threads <= 1 || n < 4096) {
     f(0, 0, n);
     return;
   }
   std::thread th[kPlanThreads - 1];
-  for (int t = 1; t < kPlanThreads; ++t)
-    th[t - 1] = std::thread(f, t, int((long long)n * t / kPlanThreads),
-                            int((long long)n * (t + 1) / kPlanThreads));
-  f(0, 0, int((long long)n / kPlanThreads));
-  for (auto &x : th) x.join();
+  for (int t = 1; t < threads; ++t)
+    th[t - 1] = std::thread(f, t, int((long long)n * t / threads), int((long long)n * (t + 1) / threads));
+  f(0, 0, int((long long)n / threads));
+  for (int t = 1; t < threads; ++t) th[t - 1].join();
 }
 
 // The indices 0..n-1 ordered by key[i], equal keys in index order (the order of a stable
@@ -944,8 +944,9 @@ std::vector<int> order_by_key(const std::vector<unsigned long long> &key) {
 
 void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
                const std::vector<int> &snode, const std::vector<int> &node_curve, double d,
-               int leaf_target, PlanHost &ph) {
+               int leaf_target, PlanHost &ph, int threads = kPlanThreads) {
   PlanHost *f = &ph;
+  threads = std::max(1, std::min(threads, kPlanThreads));
   const int N = int(x.size());
   const int slots = int(spos.size());
   // image sources
@@ -957,7 +958,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   const int nl = int(live.size()), ns = nl * nimg;
   std::vector<int2> src(ns);  // (slot, m): image m of every live slot, m = -1, 0, 1 in turn
   std::vector<double2> pos(ns);
-  plan_for(ns, [&](int, int b, int e) {
+  plan_for(ns, threads, [&](int, int b, int e) {
     for (int j = b; j < e; ++j) {
       const int m = (nimg == 3 ? j / nl - 1 : 0), sl = live[j % nl];
       src[j] = make_int2(sl, m);
@@ -987,24 +988,29 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
     gy = std::min(gmaxy, std::max(0, int(floor((q.y - ya) / hmax))));
   };
   std::vector<unsigned long long> skey(ns), tkey(N);
-  plan_for(ns, [&](int, int b, int e) {
+  plan_for(ns, threads, [&](int, int b, int e) {
     for (int j = b; j < e; ++j) {
       int gx, gy;
       gcoord(pos[j], gx, gy);
       skey[j] = encode(gx, gy, kLmax, f->nx);
     }
   });
-  plan_for(N, [&](int, int b, int e) {
+  plan_for(N, threads, [&](int, int b, int e) {
     for (int i = b; i < e; ++i) {
       int gx, gy;
       gcoord(x[i], gx, gy);
       tkey[i] = encode(gx, gy, kLmax, f->nx);
     }
   });
-  std::vector<int> sord, tord;  // the two orders on two threads
-  std::thread tsort([&] { tord = order_by_key(tkey); });
-  sord = order_by_key(skey);
-  tsort.join();
+  std::vector<int> sord, tord;  // the two orders, on two threads when threads > 1
+  if (threads > 1) {
+    std::thread tsort([&] { tord = order_by_key(tkey); });
+    sord = order_by_key(skey);
+    tsort.join();
+  } else {
+    sord = order_by_key(skey);
+    tord = order_by_key(tkey);
+  }
   // depth: the shallowest with at most leaf_target sources per occupied leaf
   int L = 0;
   for (; L < kLmax; ++L) {
@@ -1067,7 +1073,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   };
   std::vector<double2> sc_ctr(nsc), tc_ctr(ntc);
   std::vector<int2> sc_rng(nsc);
-  plan_for(nsc, [&](int, int cb, int ce) {
+  plan_for(nsc, threads, [&](int, int cb, int ce) {
     for (int i = cb; i < ce; ++i) {
       const int l = level_of(f->sc_off, i);
       sc_ctr[i] = centre(sk_all[i], l);
@@ -1087,7 +1093,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   // cell order
   std::vector<int> tc_par(ntc, -1), il_off(ntc + 1, 0), il_idx, il_cnt(ntc, 0);
   std::vector<std::vector<int>> il_part(kPlanThreads);
-  plan_for(ntc, [&](int part_id, int cb, int ce) {
+  plan_for(ntc, threads, [&](int part_id, int cb, int ce) {
     std::vector<int> &part = il_part[part_id];
     for (int i = cb; i < ce; ++i) {
       const int l = level_of(f->tc_off, i);
@@ -1130,7 +1136,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   const int gnx = f->nx << L, gny = f->ny << L;
   std::vector<std::vector<int>> nl_part(kPlanThreads);
   long long part_pairs[kPlanThreads] = {};
-  plan_for(ntl, [&](int part_id, int lb, int le) {
+  plan_for(ntl, threads, [&](int part_id, int lb, int le) {
     std::vector<int> &part = nl_part[part_id];
     for (int t = lb; t < le; ++t) {
       const size_t before = part.size();
@@ -1159,7 +1165,7 @@ void plan_host(const std::vector<double2> &x, const std::vector<double2> &spos,
   std::vector<int2> src_sorted(ns);
   std::vector<double2> pos_sorted(ns);
   f->src_own.resize(ns);
-  plan_for(ns, [&](int, int b, int e) {
+  plan_for(ns, threads, [&](int, int b, int e) {
     for (int j = b; j < e; ++j) {
       src_sorted[j] = src[sord[j]];
       pos_sorted[j] = pos[sord[j]];

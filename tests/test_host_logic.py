@@ -26,7 +26,8 @@ def bins():
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     out = tempfile.mkdtemp(prefix="stokes_host_")
-    names = {"fmm_plan_check": [], "fds_host_check": ["-lcublas", "-lcusolver"], "close_pairs_check": []}
+    names = {"fmm_plan_check": [], "fmm_plan_threads_check": [],
+             "fds_host_check": ["-lcublas", "-lcusolver"], "close_pairs_check": []}
 
     def build(name):
         exe = os.path.join(out, name)
@@ -37,7 +38,7 @@ def bins():
         assert r.returncode == 0, r.stderr[-2000:]
         return name, exe
 
-    with cf.ThreadPoolExecutor(3) as ex:
+    with cf.ThreadPoolExecutor(4) as ex:
         paths = dict(ex.map(build, names))
     yield paths
     shutil.rmtree(out, ignore_errors=True)
@@ -100,6 +101,15 @@ def test_fmm_plan_and_passes(bins, tmp_path, order, leaf, tol):
     u = np.fromfile(out).reshape(-1, 2)
     err = (np.abs(u - ref).max(0) / np.abs(ref).max(0)).max()
     assert err < tol, (order, leaf, err)
+
+
+def test_fmm_plan_threads_build_the_same_plan(bins):
+    """The plan built on 2, 3 and 4 host threads equals the one-thread plan in every array, bit
+    for bit, for seeded random geometries from 80 to 200,000 source slots (the threaded path
+    starts at 4,096 items), periodic and not, with padding slots."""
+    txt = run(bins["fmm_plan_threads_check"])
+    print(txt)
+    assert "ok: 36 threaded plans identical" in txt, txt
 
 
 # ---------------------------------------------------------------------------

@@ -7,7 +7,9 @@
   host factorization and the close-pair search, through the harnesses of
   ``tests/test_host_logic.py`` -- on one case each.
 Any invalid access, overflow, misaligned or out-of-range conversion stops the program with a
-non-zero exit (``-fno-sanitize-recover=all``).  The device kernels are not covered here: they
+non-zero exit (``-fno-sanitize-recover=all``).
+* The FMM plan build on several host threads (``tests/host/fmm_plan_threads_check.cu``) under
+  ThreadSanitizer: a data race between the threads stops it (``halt_on_error=1``).  The device kernels are not covered here: they
 check their own bounds and report through the device status word.
 """
 import concurrent.futures as cf
@@ -25,7 +27,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SAN = ["-fsanitize=address,undefined", "-fno-omit-frame-pointer", "-fno-sanitize-recover=all"]
 ENV = dict(os.environ, ASAN_OPTIONS="detect_leaks=1:abort_on_error=0:halt_on_error=1",
-           UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1", OMP_NUM_THREADS="2")
+           UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1", TSAN_OPTIONS="halt_on_error=1",
+           OMP_NUM_THREADS="2")
 
 
 def _run(cmd, **kw):
@@ -58,6 +61,12 @@ def san_bins():
                           "-fno-omit-frame-pointer,-fno-sanitize-recover=all",
                           os.path.join(HERE, "host", name + ".cu"), "-o", os.path.join(out, name),
                           "-lasan", "-lubsan"] + extra
+        jobs["fmm_plan_threads_tsan"] = [
+            nvcc, "-O1", "-g", "-std=c++17", "--expt-relaxed-constexpr",
+            "-I", os.path.join(ROOT, "include"), "-gencode", "arch=compute_103a,code=sm_103a",
+            "-Xcompiler=-fsanitize=thread,-fno-omit-frame-pointer",
+            os.path.join(HERE, "host", "fmm_plan_threads_check.cu"),
+            "-o", os.path.join(out, "fmm_plan_threads_tsan"), "-ltsan"]
 
     def build(item):
         name, cmd = item
@@ -121,6 +130,19 @@ def test_host_logic_under_sanitizers(san_bins, tmp_path):
     assert "invariant_violations 0" in txt
     u = np.fromfile(out).reshape(-1, 2)
     assert (np.abs(u - ref).max(0) / np.abs(ref).max(0)).max() < 1e-6
+
+
+def test_fmm_plan_threads_under_thread_sanitizer(san_bins):
+    """The threaded FMM plan build, on the four smaller cases of its host check (80 to 33,000
+    source slots; the threads start at 4,096 items), races nowhere and still equals the
+    one-thread plan."""
+    if "fmm_plan_threads_tsan" not in san_bins:
+        pytest.skip("nvcc not available")
+    r = subprocess.run([san_bins["fmm_plan_threads_tsan"], "4"], capture_output=True, text=True,
+                       env=ENV, timeout=900)
+    assert r.returncode == 0, (r.returncode, r.stdout[-2000:], r.stderr[-6000:])
+    assert "ThreadSanitizer" not in r.stderr, r.stderr[-6000:]
+    assert "ok: 24 threaded plans identical" in r.stdout, r.stdout
 
 
 def test_fds_host_under_sanitizers(san_bins, tmp_path):
