@@ -512,10 +512,15 @@ def step_system(ves_x, dt, kappa_b, mu, period, L0, close=None):
 
 
 def step(ves_x, sigma, L0, A0, dt, kappa_b, mu, period, walls=None, p_drive=0.0,
-         reparam=True, close=None):
+         reparam=True, close=None, corrections=True):
     """One semi-implicit step of Algorithm 1: forces, channel response (explicit), the
     solve of Eq. (tsteplinsys) with Eq. (ALC), x <- x + dt u, area correction, reparam.
+    corrections=False takes the uncorrected scheme the appendices compare against: the
+    plain inextensibility constraint x_s . u_s = 0 (Eq. (ALC) with L_0 = L_k, App. A) and no
+    area correction (App. B).
     Returns (new positions, new tensions, u, sigma_{k+1}, u_resp)."""
+    if not corrections:
+        L0 = [perimeter(x) for x in ves_x]
     sizes = [x.shape[0] for x in ves_x]
     fb, f = [], []
     for x, sg in zip(ves_x, sigma):
@@ -543,7 +548,8 @@ def step(ves_x, sigma, L0, A0, dt, kappa_b, mu, period, walls=None, p_drive=0.0,
     for v, x in enumerate(ves_x):
         n = x.shape[0]
         xn = x + dt * u[o:o + n]
-        xn = area_correct(xn, A0[v])
+        if corrections:
+            xn = area_correct(xn, A0[v])
         if reparam:
             xn = reparametrize(xn)
         out_x.append(xn)

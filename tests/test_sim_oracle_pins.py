@@ -4,9 +4,12 @@ Channel response: the traction kernels are the tractions of their velocity/press
 (finite differences), the exact Poiseuille flow is reproduced (Sec. 5.1 test), and the
 total flow of vesicle forces plus response is periodic in velocity and traction with the
 prescribed pressure drop.  Step: spectral differentiation, area correction, the
-arc-length correction bound of Theorem A.2, reparameterization, and the solved system.
+arc-length correction bound of Theorem A.2, the convergence orders of the paper's correction
+table (App. A, ``tests/golden/correction_convergence.txt``), reparameterization, and the
+solved system.
 """
 import math
+import os
 import warnings
 
 import numpy as np
@@ -244,6 +247,49 @@ def test_arc_length_correction_bound(S):
         errs.append(abs(S.perimeter(x[0]) - L0[0]) / L0[0])
     bound = dt * dt * C * C / (2 - dt * dt * C * C)
     assert max(errs) <= bound * 1.05 + 1e-12
+
+
+def test_correction_convergence_orders_match_the_paper(S):
+    """The paper's convergence table for the corrections (App. A; the golden fixture holds
+    it): with both the arc-length correction (Eq. (ALC)) and the area correction (App. B) the
+    arc-length error falls at second order in dt and the area stays at rounding level; with
+    neither, arc length and area drift at first order.  Here: one vesicle (16 nodes, ellipse
+    0.25 x 0.15, kappa_B = 0.01) in the pressure-driven periodic sine channel, dt = 0.01 / M to
+    t = 0.1 as in the paper, M = 1, 2, 4.  Each observed order is within 0.25 of the paper's for
+    the same pair of M, the corrected area error is below 1e-12 (the paper's: at most
+    1.2e-10), and the corrected arc-length error is at least 10x below the uncorrected one (the
+    paper's: 13x at M = 1).  A dropped or mis-signed correction term breaks the orders."""
+    tab = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "correction_convergence.txt"))
+    paper = {int(r[0]): r[1:] for r in tab}  # L_c, A_c, x_c, L_nc, A_nc, x_nc
+    d, mu, kb, pd, n = 2 * PI, 1.0, 0.01, 2.0, 16
+    lo, up = I.wall_curves(64, I.WALL_SHAPE_SMALL)
+    W = S.Walls(lo, up, d, mu, K=24, M=96)
+    t = 2 * PI * np.arange(n) / n
+    x0 = np.stack([0.5 + 0.25 * np.cos(t), 0.3 + 0.15 * np.sin(t)], 1)
+    L0, A0 = [S.perimeter(x0)], [S.area(x0)]
+
+    def errors(M, corrections):
+        x, sig, dt = [x0.copy()], [np.zeros(n)], 0.01 / M
+        for _ in range(int(round(0.1 / dt))):
+            x, sig, _, _, _ = S.step(x, sig, L0, A0, dt, kb, mu, d, walls=W, p_drive=pd,
+                                     reparam=False, corrections=corrections)
+        return abs(S.perimeter(x[0]) - L0[0]) / L0[0], abs(S.area(x[0]) - A0[0]) / A0[0]
+
+    Ms = (1, 2, 4)
+    c = {M: errors(M, True) for M in Ms}
+    nc = {M: errors(M, False) for M in Ms}
+    for M in Ms:
+        print("M %d: L_c %.3e A_c %.3e | L_nc %.3e A_nc %.3e" % (M, *c[M], *nc[M]))
+        assert c[M][1] < 1e-12 and paper[M][1] <= 1.21e-10
+        assert c[M][0] < 0.1 * nc[M][0] and paper[M][0] < 0.1 * paper[M][3]
+    order = lambda a, b: math.log2(a / b)
+    for M1, M2 in zip(Ms, Ms[1:]):
+        ours = (order(c[M1][0], c[M2][0]), order(nc[M1][0], nc[M2][0]), order(nc[M1][1], nc[M2][1]))
+        theirs = (order(paper[M1][0], paper[M2][0]), order(paper[M1][3], paper[M2][3]),
+                  order(paper[M1][4], paper[M2][4]))
+        print("M %d -> %d: orders L_c, L_nc, A_nc %s, paper %s" % (M1, M2, np.round(ours, 2),
+                                                                  np.round(theirs, 2)))
+        assert all(abs(a - b) <= 0.25 for a, b in zip(ours, theirs)), (ours, theirs)
 
 
 def test_step_operator_equals_pinned_pair_oracle(S, oracle_mod):
