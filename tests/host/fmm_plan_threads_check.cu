@@ -1,7 +1,9 @@
-// Host check of the FMM plan build's threads (tests/test_host_logic.py): builds the plan of
-// csrc/fmm.cu for seeded random geometries -- small and large, periodic and not, with padding
-// slots and free curve ids -- on one host thread and on 2, 3 and 4, and checks that every array
-// of the plan is the same bit for bit.  Usage: fmm_plan_threads_check [cases, default 6]
+// Host check of the FMM plan build's threads (tests/test_host_logic.py): the key order of the
+// plan (an LSD radix sort) equals std::stable_sort's on seeded keys -- many ties, keys up to 64
+// bits, empty and single inputs; then builds the plan of csrc/fmm.cu for seeded random
+// geometries -- small and large, periodic and not, with padding slots and free curve ids -- on
+// one host thread and on 2, 3 and 4, and checks that every array of the plan is the same bit
+// for bit.  Usage: fmm_plan_threads_check [cases, default 6]
 #include "../../paper_1510_05616_gb300/csrc/fmm.cu"
 #include <cstdio>
 #include <cstring>
@@ -30,8 +32,31 @@ static bool same_plan(const PlanHost &a, const PlanHost &b) {
          same(a.pos_sorted, b.pos_sorted) && same(a.sc_ctr, b.sc_ctr) && same(a.tc_ctr, b.tc_ctr);
 }
 
+// order_by_key against the stable sort it stands for
+static bool radix_matches_stable_sort() {
+  std::mt19937_64 rng(11);
+  const int sizes[] = {0, 1, 2, 7, 1000, 65537, 300000};
+  const int bits[] = {1, 5, 12, 22, 38, 64};
+  for (int n : sizes)
+    for (int b : bits) {
+      std::vector<unsigned long long> key(n);
+      for (auto &k : key) k = b == 64 ? rng() : rng() & ((1ull << b) - 1);
+      std::vector<int> ref(n);
+      for (int i = 0; i < n; ++i) ref[i] = i;
+      std::stable_sort(ref.begin(), ref.end(), [&](int a, int c) { return key[a] < key[c]; });
+      if (order_by_key(key) != ref) {
+        printf("MISMATCH order_by_key n %d bits %d\n", n, b);
+        return false;
+      }
+    }
+  printf("ok: order_by_key equals std::stable_sort (%zu sizes x %zu key widths)\n",
+         sizeof(sizes) / sizeof(sizes[0]), sizeof(bits) / sizeof(bits[0]));
+  return true;
+}
+
 int main(int argc, char **argv) {
   const int n_cases = argc > 1 ? std::max(1, std::min(6, atoi(argv[1]))) : 6;
+  if (!radix_matches_stable_sort()) return 1;
   const double d = 2 * M_PI;
   std::mt19937 rng(7);
   std::uniform_real_distribution<double> U(0, 1);

@@ -104,11 +104,13 @@ def test_fmm_plan_and_passes(bins, tmp_path, order, leaf, tol):
 
 
 def test_fmm_plan_threads_build_the_same_plan(bins):
-    """The plan built on 2, 3 and 4 host threads equals the one-thread plan in every array, bit
-    for bit, for seeded random geometries from 80 to 200,000 source slots (the threaded path
-    starts at 4,096 items), periodic and not, with padding slots."""
+    """The plan's key order (a radix sort) equals a stable sort's, ties and 64-bit keys
+    included, and the plan built on 2, 3 and 4 host threads equals the one-thread plan in every
+    array, bit for bit, for seeded random geometries from 80 to 200,000 source slots (the
+    threaded path starts at 4,096 items), periodic and not, with padding slots."""
     txt = run(bins["fmm_plan_threads_check"])
     print(txt)
+    assert "ok: order_by_key equals std::stable_sort" in txt, txt
     assert "ok: 36 threaded plans identical" in txt, txt
 
 
