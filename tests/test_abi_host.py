@@ -84,3 +84,44 @@ def test_binding_constants_match_header_enums():
     assert len(found) >= 15
     for name, value in found:
         assert getattr(P, name) == int(value), name
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """Every result struct of the header (stokes_fmm_info, stokes_close_info,
+    stokes_tune_result, stokes_fds_info, stokes_step_stats) has the binding's ctypes layout:
+    the same field names in the same order, and the same size and offset of every field as the
+    C compiler gives them (a field added on one side only would shift the rest)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import paper_1510_05616_gb300 as P
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    src = open(os.path.join(ROOT, "include", "stokes.h")).read()
+    structs = {m.group(2): re.findall(r"^\s*(?:int|double)\s+([\w\s,]+);", m.group(1), re.M)
+               for m in re.finditer(r"typedef struct \{(.*?)\}\s*(stokes_\w+);", src, re.S)}
+    fields = {k: [n.strip() for decl in v for n in decl.split(",")] for k, v in structs.items()}
+    binding = {"stokes_fmm_info": P.FmmInfo, "stokes_close_info": P.CloseInfo,
+               "stokes_tune_result": P.TuneResult, "stokes_fds_info": P.FdsInfo,
+               "stokes_step_stats": P.StepStats}
+    assert set(fields) == set(binding), sorted(fields)
+    prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "stokes.h"', "int main(void) {"]
+    for name, names in fields.items():
+        prog.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f in names:
+            prog.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    prog.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog))
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in binding.items():
+        assert [f for f, _ in cls._fields_] == fields[name], name
+        assert ctypes.sizeof(cls) == got[(name, "size")], name
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == got[(name, f)], (name, f)
